@@ -1,0 +1,224 @@
+/*
+ * trt.h -- C ABI of the GB300 (sm_103a) solver for thermal radiative transfer with the
+ * multilevel quasidiffusion (QD / VEF) method and multigrid in photon frequency
+ * (D. Y. Anistratov, "Nonlinear iterative projection methods with multigrid in photon
+ * frequency for thermal radiative transfer", arXiv 2011.05427).
+ *
+ * Problem (Sec. 2, Sec. 6): 1D slab [0, X]; multigroup RT equation (eq. rt) with the
+ * Fleck-Cummings opacity sigma(nu, T) = s 27/nu^3 (1 - e^{-nu/T}); material energy
+ * eps = cv T (eq. eb); isotropic Planck inflow at x = 0 and x = X (vacuum when the
+ * boundary temperature is <= 0); initial state T = T0, I_g = B_g(T0).
+ * Method (Sec. 3-5, Algorithm 3): implicit Euler; simple-corner-balance S_N sweeps;
+ * group LOQD equations on a hierarchy of frequency grids visited by V / W / F cycles;
+ * effective grey LOQD coupled to the material energy balance, one Newton step per
+ * temperature evaluation.
+ *
+ * Units: cm, sh (1e-8 s), keV, GJ.  c = 299.792458 cm/sh, aR = 0.01372 GJ/(cm^3 keV^4).
+ *
+ * Conventions for every entry point:
+ *   - returns an int status: TRT_OK (0) or a negative TRT_E* code; no exceptions cross
+ *     the ABI; after a non-fatal error (EINVAL, ENOTCONVERGED, ENUMERIC) the handle stays
+ *     usable and trt_last_error() describes the failure;
+ *   - "host" pointers are read or written with plain loads/stores; "device" pointers must
+ *     be device memory of the handle's device; the caller owns all memory it passes;
+ *   - the library allocates no device memory: all device state lives in the caller's
+ *     workspace (trt_workspace_bytes), carved at trt_create; the only allocation the
+ *     library makes is a small pinned host buffer per handle for convergence flags;
+ *   - all device work is enqueued on the stream given in trt_options (0 = legacy stream);
+ *   - array layouts (host and device):
+ *       cell arrays     [G][nx]            group-major, cell fastest
+ *       face arrays     [G][nx+1]          face f at x_{f-1/2}: f = 0 is x = 0, f = nx is X
+ *       intensity       [M][nx][2][ldG]    direction, cell, corner (0 left, 1 right), group
+ *                                          (ldG = trt_ld_groups(h) >= G, padding is zero)
+ *       directions      m < N: mu_m > 0 ascending; m >= N: mu_m = -mu_{m-N}  (M = 2N)
+ */
+#ifndef TRT_H
+#define TRT_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define TRT_OK              0
+#define TRT_EINVAL         -1   /* bad argument; nothing was enqueued                   */
+#define TRT_ENOTCONVERGED  -2   /* outer loop hit max_outer; the state is the last iterate */
+#define TRT_ENUMERIC       -3   /* a temperature came out non-positive or non-finite     */
+#define TRT_ETIMEOUT       -4   /* a bounded device wait gave up (reserved)              */
+#define TRT_ECUDA          -5   /* a CUDA runtime call failed; see trt_last_error        */
+#define TRT_ENOSPACE       -6   /* workspace smaller than trt_workspace_bytes            */
+
+/* ---- precision modes (spec pattern (1)) ---- */
+#define TRT_FP64   0   /* every step in FP64                                               */
+#define TRT_MIXED  1   /* sweeps and group LOQD in FP32; opacities, grey LOQD, MEB Newton and
+                          convergence checks in FP64                                       */
+
+/* ---- cycle types (Sec. 4, Fig. 1) ---- */
+#define TRT_CYCLE_V 0   /* S empty: two-grid method on any hierarchy                      */
+#define TRT_CYCLE_W 1   /* S = w(2), w(Gamma-1) = [Gamma-1], w(g) = w(g+1) + [g] + w(g+1)  */
+#define TRT_CYCLE_F 2   /* S = [Gamma-1, ..., 2]                                           */
+
+/* Spatial grid (Sec. 5 mesh).  x_edges: host, n_cells+1 increasing values, or NULL for a
+ * uniform mesh over [0, length_cm]. */
+typedef struct {
+    int n_cells;
+    const double *x_edges;
+    double length_cm;
+    double T_left_keV;    /* isotropic Planck inflow at x = 0; <= 0 means vacuum */
+    double T_right_keV;   /* isotropic Planck inflow at x = X; <= 0 means vacuum */
+} trt_grid;
+
+/* Angular quadrature (Sec. 6): double Gauss-Legendre, N nodes per half range, M = 2N. */
+typedef struct {
+    int N;
+} trt_angles;
+
+/* Frequency groups (eq. fine-grid, Sec. 4 hierarchy).  edges_keV: host, n_groups+1
+ * increasing values, first 0, last may be INFINITY; NULL selects 0, n_groups-2 log-spaced
+ * groups in [nu_a, nu_b], [nu_b, inf) (Sec. 6).  level_groups: host, n_levels values
+ * n^1 = n_groups > n^2 > ... > n^Gamma = 1, each dividing the previous one (uniform
+ * successive coarsening); NULL with n_levels = 0 selects {n_groups, 1}. */
+typedef struct {
+    int n_groups;
+    const double *edges_keV;
+    double nu_a, nu_b;
+    int n_levels;
+    const int *level_groups;
+} trt_groups;
+
+/* Opacity model (Sec. 6): sigma(nu, T) = scale * 27 / nu^3 * (1 - exp(-nu/T)) cm^-1. */
+typedef struct {
+    double scale;
+} trt_opacity;
+
+/* Options: precision mode, initial temperature, CUDA stream (cudaStream_t as void*),
+ * caller-owned device workspace of at least trt_workspace_bytes bytes (256-B aligned). */
+typedef struct {
+    int precision;
+    double T0_keV;
+    void *stream;
+    void *workspace;
+    size_t workspace_bytes;
+} trt_options;
+
+/* Iteration controls of Algorithm 3.  eps: outer tolerance on ||dT||/||T|| and
+ * ||dE||/||E|| (infinity norms, both must hold); eps_inner: the same per cycle; l_max:
+ * cycles per low-order phase; max_outer: low-order phases per step (the first, s = 0, has
+ * no sweep).  eps < 0 runs exactly max_outer phases of exactly l_max cycles. */
+typedef struct {
+    int type;
+    int l_max;
+    double eps;
+    double eps_inner;
+    int max_outer;
+} trt_cycle;
+
+/* Per-step counters (Sec. 6): sweeps, cycles, group-wise low-order solves (grey solves
+ * count one each), low-order phases; wall time of the step on the host clock. */
+typedef struct {
+    int n_ti, n_c, n_lo, n_outer;
+    double ms;
+    int status;
+} trt_stats;
+
+typedef struct trt_handle trt_handle;
+
+/* Bytes of device workspace trt_create needs for this problem (0 on invalid input). */
+size_t trt_workspace_bytes(const trt_grid *grid, const trt_angles *angles,
+                           const trt_groups *groups, const trt_options *opt);
+
+/* Validate the problem, carve the workspace, upload constants and the initial state
+ * (Sec. 6: T = T0, I = B_g(T0), E_g = (1/c) sum w I, F_g = sum w mu I, isotropic QD
+ * factors).  Synchronises the stream before returning.  *out is NULL on failure. */
+int trt_create(const trt_grid *grid, const trt_angles *angles, const trt_groups *groups,
+               const trt_opacity *opacity, double cv, const trt_options *opt,
+               trt_handle **out);
+
+/* One implicit time step of length dt_sh with Algorithm 3.  Blocks on the stream once per
+ * cycle to read the convergence flags.  stats may be NULL. */
+int trt_step(trt_handle *h, double dt_sh, const trt_cycle *cycle, trt_stats *stats);
+
+/* Copy the state at the current time level to host arrays (any may be NULL):
+ * T [nx], E_g [G][nx], F_g [G][nx+1] (last fine solve), grey E [nx], F [nx+1] (last grey
+ * solve).  Synchronises the stream. */
+int trt_moments(trt_handle *h, double *T, double *Eg, double *Fg, double *E, double *F);
+
+/* Host copy of the intensity [M][nx][2][ldG] as FP64 and the QD factors f_g [G][nx]. */
+int trt_intensity(trt_handle *h, double *I, double *f);
+
+/* Replace the state (host arrays, any may be NULL): temperature, E_g, F_g, intensity
+ * [M][nx][2][ldG] and the QD factors f [G][nx], fb0, fbX, C0 (= C^- at 0), CX (= C^+ at X)
+ * [G].  E_g also resets the grey E.  Used for restarts and tests. */
+int trt_set_state(trt_handle *h, const double *T, const double *Eg, const double *Fg,
+                  const double *I, const double *f, const double *fb0, const double *fbX,
+                  const double *C0, const double *CX);
+
+/* Problem dimensions: nx, N, M, G, ldG, number of grids, precision. */
+int trt_dims(const trt_handle *h, int *nx, int *N, int *M, int *G, int *ldG, int *n_levels,
+             int *precision);
+
+/* Frees host objects only (the workspace belongs to the caller).  NULL is a no-op. */
+int trt_destroy(trt_handle *h);
+
+/* Last error message of this handle (or of the last failed create when h is NULL). */
+const char *trt_last_error(const trt_handle *h);
+
+/* ======================================================================================
+ * Kernel-level entry points (device pointers, the handle's stream and dimensions).  Each
+ * runs one step of the hot path on caller-provided device buffers, so that every kernel
+ * can be checked on its own against the oracle.  They do not touch the handle's state.
+ * ====================================================================================== */
+
+/* Group physics at cell temperatures T [nx] (Sec. 2, Sec. 3.1, Sec. 6): sigma_E (=
+ * sigma_B, T_r = T), emission e_g = sigma_B,g B_g and sigma_R, each [G][nx], FP64. */
+int trt_k_opacity(trt_handle *h, const double *T, double *sigE, double *emis, double *sigR);
+
+/* One HO sweep (eq. rt, simple corner balance, implicit Euler) of every group and
+ * direction with sigma_t = sigE + 1/(c dt) and corner sources emis + I_old/(c dt), inflow
+ * from the handle's boundary temperatures, followed by the QD factors (eqs. f_g, c_g).
+ * I_old / I_new: [M][nx][2][ldG] in the handle's sweep precision (double for TRT_FP64,
+ * float for TRT_MIXED).  f [G][nx]; fb0, fbX, C0, CX [G]; all FP64. */
+int trt_k_sweep(trt_handle *h, double dt, const double *sigE, const double *emis,
+                const void *I_old, void *I_new, double *f, double *fb0, double *fbX,
+                double *C0, double *CX);
+
+/* One frequency-grid level of the low-order system, device arrays (FP64):
+ *   cell [n][nx]: phi (f or f-bar), sig (sigma_E or its average), emis (sum of
+ *                 sigma_B B over the group), Eold (E at t^{j-1}), Esum (restriction output)
+ *   face [n][nx+1]: sigR, etaR (eta-hat on E right of the face), etaL (eta-check on E left
+ *                 of the face), Fold (F at t^{j-1})
+ *   bound [n]: phib0, phibX (factor at x=0 / x=X), C0 (C^-), CX (C^+), Ein0, Fin0, EinX,
+ *              FinX (inflow moments, eq. mloqd-bcs)
+ *   solution: E [n][nx], F [n][nx+1], Eb0, EbX [n] (boundary-face energies). */
+typedef struct {
+    int n;
+    double *phi, *sig, *emis, *Eold, *Esum;
+    double *sigR, *etaR, *etaL, *Fold;
+    double *phib0, *phibX, *C0, *CX, *Ein0, *Fin0, *EinX, *FinX;
+    double *E, *F, *Eb0, *EbX;
+} trt_level;
+
+/* Solve every group of a level (eqs. mloqd-d / mloqd-d-gamma with absorption c sig and
+ * source 2 emis) in the handle's LO precision; writes E, F, Eb0, EbX. */
+int trt_k_lo_solve(trt_handle *h, double dt, trt_level *lv);
+
+/* Restrict level `src` (its coefficients and solution) onto `dst` (dst->n groups, uniform
+ * map p -> p / (src->n / dst->n)): eqs. coeff-gamma, eta-gamma, coeff-Gamma, eta-Gamma
+ * with the discrete compensation of eq. mloqd-d-gamma.  Writes every coefficient of dst
+ * and dst->Esum. */
+int trt_k_restrict(trt_handle *h, const trt_level *src, trt_level *dst);
+
+/* Grey LOQD + MEB, one Newton step (eq. eb-Gamma-d, eq. f-derivative-d) on the grey level
+ * `g` (g->n == 1) at T* = Tstar [nx], with Q = 2 g->emis, E* = g->Esum, the secant from
+ * (sig_prev, T_prev) when have_prev != 0.  Writes T [nx], g->E, g->F, g->Eb0, g->EbX.
+ * Returns TRT_ENUMERIC if a temperature is non-positive or non-finite. */
+int trt_k_grey_newton(trt_handle *h, double dt, const double *Tstar, const double *Told,
+                      const double *sig_prev, const double *T_prev, int have_prev,
+                      trt_level *g, double *T);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,676 @@
+// api.cu -- the C ABI of include/trt.h: problem set-up, workspace carving, the Algorithm 3
+// driver (one implicit time step), state access, and kernel-level entry points.
+//
+// Algorithm 3 (Sec. 4) as driven here, per time step j:
+//   s = 0: a low-order phase with the previous step's QD factors (no sweep);
+//   s > 0: opacities at T^(s) -> HO sweep -> f_g, C_g^+- -> low-order phase;
+//   low-order phase: at most l_max cycles; a cycle is the fine-grid spectrum at T^(l,s)
+//   followed by one grey LOQD + MEB Newton step per grid visit: first from the fine grid
+//   (k = 0), then for every gamma_k of the schedule S re-evaluate the fine opacities at
+//   T~^[k], restrict fine -> gamma_k, solve the coarse-group system, restrict -> grey.
+// Readings (the paper is silent or garbled): the outer loop ends when BOTH the change of T
+// and of the grey E are below eps (relative, infinity norm); the inner loop leaves early
+// on eps_inner; T~^[0] = T^(l,s); the step ends with T of the last grey solve, E_g / F_g of
+// the last fine solve and I of the last sweep; the secant derivative of the grey opacity
+// restarts at zero with every time step.
+// The host reads 7 doubles of convergence flags once per cycle (one stream sync per cycle).
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+#include "common.cuh"
+
+using namespace trt;
+
+static std::string g_create_error = "";
+
+struct trt_handle {
+    Problem p;
+    double *T, *Told, *Tcyc, *Tphase, *Ttil, *Tnew, *sig_prev, *T_prev;
+    double *Eg, *Fg, *Eg_old, *Fg_old;
+    void *I_cur, *I_alt;
+    double *f, *fb0, *fbX, *C0, *CX;
+    double *sigE, *emis, *sigR;
+    double *part, *psi_exit;
+    double *E1, *F1, *Eb0_1, *EbX_1;
+    Level crs, grey;
+    double *Ecyc, *Ephase;
+    double *flags;
+    double *hflags;
+    std::string err;
+    ~trt_handle()
+    {
+        if (hflags) cudaFreeHost(hflags);
+    }
+};
+
+namespace {
+
+struct Carver {
+    char *base;
+    size_t off;
+    template <class T>
+    T *take(size_t n)
+    {
+        off = (off + 255) / 256 * 256;
+        T *ptr = base ? reinterpret_cast<T *>(base + off) : nullptr;
+        off += std::max<size_t>(n, 1) * sizeof(T);
+        return ptr;
+    }
+};
+
+void carve_level(Carver &c, Level &L, int n, int nx)
+{
+    L.n = n;
+    L.fine = 0;
+    size_t cn = (size_t)n * nx, fn = (size_t)n * (nx + 1);
+    L.phi = c.take<double>(cn); L.sig = c.take<double>(cn); L.emis = c.take<double>(cn);
+    L.Eold = c.take<double>(cn); L.Esum = c.take<double>(cn); L.E = c.take<double>(cn);
+    L.sigR = c.take<double>(fn); L.etaR = c.take<double>(fn); L.etaL = c.take<double>(fn);
+    L.Fold = c.take<double>(fn); L.F = c.take<double>(fn);
+    L.phib0 = c.take<double>(n); L.phibX = c.take<double>(n); L.C0 = c.take<double>(n);
+    L.CX = c.take<double>(n); L.Ein0 = c.take<double>(n); L.Fin0 = c.take<double>(n);
+    L.EinX = c.take<double>(n); L.FinX = c.take<double>(n); L.Eb0 = c.take<double>(n);
+    L.EbX = c.take<double>(n);
+}
+
+void carve(trt_handle *h, Carver &c)
+{
+    Problem &p = h->p;
+    const size_t nx = p.nx, G = p.G, M = p.M;
+    const size_t rsz = (p.precision == TRT_FP64) ? sizeof(double) : sizeof(float);
+    p.h = c.take<double>(nx); p.edges = c.take<double>(G + 1);
+    p.mu = c.take<double>(M); p.w = c.take<double>(M);
+    p.Iin0 = c.take<double>(G); p.IinX = c.take<double>(G);
+    p.Ein0 = c.take<double>(G); p.Fin0 = c.take<double>(G);
+    p.EinX = c.take<double>(G); p.FinX = c.take<double>(G);
+    double **tl[] = {&h->T, &h->Told, &h->Tcyc, &h->Tphase, &h->Ttil, &h->Tnew, &h->sig_prev,
+                     &h->T_prev, &h->Ecyc, &h->Ephase};
+    for (double **q : tl) *q = c.take<double>(nx);
+    h->Eg = c.take<double>(G * nx); h->Eg_old = c.take<double>(G * nx);
+    h->Fg = c.take<double>(G * (nx + 1)); h->Fg_old = c.take<double>(G * (nx + 1));
+    const size_t nI = M * nx * 2 * (size_t)p.ldG;
+    h->I_cur = c.take<char>(nI * rsz); h->I_alt = c.take<char>(nI * rsz);
+    h->f = c.take<double>(G * nx);
+    h->fb0 = c.take<double>(G); h->fbX = c.take<double>(G);
+    h->C0 = c.take<double>(G); h->CX = c.take<double>(G);
+    h->sigE = c.take<double>(G * nx); h->emis = c.take<double>(G * nx);
+    h->sigR = c.take<double>(G * nx);
+    h->part = c.take<double>(std::max(sweep_partial_doubles(p), 4 * nx + 8));
+    h->psi_exit = c.take<double>(M * (size_t)p.ldG);
+    h->E1 = c.take<double>(G * nx); h->F1 = c.take<double>(G * (nx + 1));
+    h->Eb0_1 = c.take<double>(G); h->EbX_1 = c.take<double>(G);
+    int n2 = (p.nlev >= 3) ? p.levels[1] : 1;
+    carve_level(c, h->crs, n2, p.nx);
+    carve_level(c, h->grey, 1, p.nx);
+    h->flags = c.take<double>(8);
+}
+
+bool validate(const trt_grid *grid, const trt_angles *angles, const trt_groups *groups,
+              const trt_options *opt, Problem &p, std::vector<double> &xe,
+              std::vector<double> &edges, std::string &err)
+{
+    if (!grid || !angles || !groups || !opt) { err = "null argument"; return false; }
+    p.nx = grid->n_cells;
+    if (p.nx < 1 || p.nx > 8192) { err = "n_cells must be in [1, 8192]"; return false; }
+    p.N = angles->N;
+    if (p.N < 1 || p.N > 256) { err = "angles.N must be in [1, 256]"; return false; }
+    p.M = 2 * p.N;
+    p.G = groups->n_groups;
+    if (p.G < 1 || p.G > (1 << 16)) { err = "n_groups must be in [1, 65536]"; return false; }
+    p.ldG = (p.G + 31) / 32 * 32;
+    p.precision = opt->precision;
+    if (p.precision != TRT_FP64 && p.precision != TRT_MIXED) { err = "bad precision"; return false; }
+    xe.resize(p.nx + 1);
+    if (grid->x_edges) {
+        for (int i = 0; i <= p.nx; ++i) xe[i] = grid->x_edges[i];
+    } else {
+        if (!(grid->length_cm > 0)) { err = "length_cm must be > 0"; return false; }
+        for (int i = 0; i <= p.nx; ++i) xe[i] = grid->length_cm * i / p.nx;
+    }
+    for (int i = 0; i < p.nx; ++i)
+        if (!(xe[i + 1] > xe[i])) { err = "x_edges must increase"; return false; }
+    edges.resize(p.G + 1);
+    if (groups->edges_keV) {
+        for (int g = 0; g <= p.G; ++g) edges[g] = groups->edges_keV[g];
+    } else {
+        if (p.G < 3 || !(groups->nu_a > 0) || !(groups->nu_b > groups->nu_a)) {
+            err = "default group edges need n_groups >= 3 and 0 < nu_a < nu_b";
+            return false;
+        }
+        edges[0] = 0.0;
+        for (int k = 0; k <= p.G - 2; ++k)
+            edges[k + 1] = groups->nu_a * std::pow(groups->nu_b / groups->nu_a, (double)k / (p.G - 2));
+        edges[p.G] = INFINITY;
+    }
+    if (!(edges[0] >= 0)) { err = "group edges must be >= 0"; return false; }
+    for (int g = 0; g < p.G; ++g)
+        if (!(edges[g + 1] > edges[g])) { err = "group edges must increase"; return false; }
+    if (groups->level_groups && groups->n_levels >= 2) {
+        p.nlev = groups->n_levels;
+        if (p.nlev > 16) { err = "at most 16 grids"; return false; }
+        for (int l = 0; l < p.nlev; ++l) p.levels[l] = groups->level_groups[l];
+    } else if (!groups->level_groups && groups->n_levels == 0) {
+        p.nlev = 2;
+        p.levels[0] = p.G;
+        p.levels[1] = 1;
+    } else {
+        err = "level_groups must list n_levels >= 2 grids";
+        return false;
+    }
+    if (p.levels[0] != p.G || p.levels[p.nlev - 1] != 1) {
+        err = "grids must run from n_groups down to 1";
+        return false;
+    }
+    for (int l = 1; l < p.nlev; ++l)
+        if (p.levels[l] < 1 || p.levels[l] > p.levels[l - 1] || p.levels[l - 1] % p.levels[l]) {
+            err = "each grid must divide the previous one (uniform coarsening)";
+            return false;
+        }
+    if (!(opt->T0_keV > 0)) { err = "T0 must be > 0"; return false; }
+    p.T0 = opt->T0_keV;
+    p.Tl = grid->T_left_keV;
+    p.Tr = grid->T_right_keV;
+    p.nu_first = edges[0];
+    p.nu_last = edges[p.G];
+    p.stream = reinterpret_cast<cudaStream_t>(opt->stream);
+    return true;
+}
+
+template <typename R>
+__global__ void k_fill_intensity(R *I, const double *B, long rows, int ldG, int G)
+{
+    long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    long n = rows * ldG;
+    for (; idx < n; idx += (long)gridDim.x * blockDim.x) {
+        int g = (int)(idx % ldG);
+        I[idx] = (g < G) ? (R)B[g] : (R)0;
+    }
+}
+
+void schedule(int type, int Gamma, std::vector<int> &S)
+{
+    S.clear();
+    if (Gamma <= 2 || type == TRT_CYCLE_V) return;
+    if (type == TRT_CYCLE_F) {
+        for (int g = Gamma - 1; g >= 2; --g) S.push_back(g);
+        return;
+    }
+    // W: w(Gamma-1) = [Gamma-1]; w(g) = w(g+1) + [g] + w(g+1)
+    std::vector<int> cur{Gamma - 1};
+    for (int g = Gamma - 2; g >= 2; --g) {
+        std::vector<int> nxt(cur);
+        nxt.push_back(g);
+        nxt.insert(nxt.end(), cur.begin(), cur.end());
+        cur.swap(nxt);
+    }
+    S = cur;
+}
+
+Level fine_level(trt_handle *h)
+{
+    Level L;
+    L.n = h->p.G;
+    L.fine = 1;
+    L.phi = h->f; L.sig = h->sigE; L.emis = h->emis; L.Eold = h->Eg_old; L.Esum = nullptr;
+    L.sigR = h->sigR; L.etaR = nullptr; L.etaL = nullptr; L.Fold = h->Fg_old;
+    L.phib0 = h->fb0; L.phibX = h->fbX; L.C0 = h->C0; L.CX = h->CX;
+    L.Ein0 = h->p.Ein0; L.Fin0 = h->p.Fin0; L.EinX = h->p.EinX; L.FinX = h->p.FinX;
+    L.E = h->E1; L.F = h->F1; L.Eb0 = h->Eb0_1; L.EbX = h->EbX_1;
+    return L;
+}
+
+Level from_abi(const trt_level *l)
+{
+    Level L;
+    L.n = l->n;
+    L.fine = 0;
+    L.phi = l->phi; L.sig = l->sig; L.emis = l->emis; L.Eold = l->Eold; L.Esum = l->Esum;
+    L.sigR = l->sigR; L.etaR = l->etaR; L.etaL = l->etaL; L.Fold = l->Fold;
+    L.phib0 = l->phib0; L.phibX = l->phibX; L.C0 = l->C0; L.CX = l->CX;
+    L.Ein0 = l->Ein0; L.Fin0 = l->Fin0; L.EinX = l->EinX; L.FinX = l->FinX;
+    L.E = l->E; L.F = l->F; L.Eb0 = l->Eb0; L.EbX = l->EbX;
+    return L;
+}
+
+int fail(trt_handle *h, int code, const std::string &msg)
+{
+    if (h) h->err = msg;
+    else g_create_error = msg;
+    return code;
+}
+
+#define CK(call)                                                                           \
+    do {                                                                                   \
+        cudaError_t e__ = (call);                                                          \
+        if (e__ != cudaSuccess)                                                            \
+            return fail(h, TRT_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e__)); \
+    } while (0)
+
+cudaError_t d2d(trt_handle *h, double *dst, const double *src, size_t n)
+{
+    return cudaMemcpyAsync(dst, src, n * sizeof(double), cudaMemcpyDeviceToDevice, h->p.stream);
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t trt_workspace_bytes(const trt_grid *grid, const trt_angles *angles,
+                           const trt_groups *groups, const trt_options *opt)
+{
+    trt_handle tmp;
+    std::vector<double> xe, ed;
+    std::string err;
+    if (!validate(grid, angles, groups, opt, tmp.p, xe, ed, err)) return 0;
+    Carver c{nullptr, 0};
+    carve(&tmp, c);
+    return (c.off + 255) / 256 * 256;
+}
+
+int trt_create(const trt_grid *grid, const trt_angles *angles, const trt_groups *groups,
+               const trt_opacity *opacity, double cv, const trt_options *opt, trt_handle **out)
+{
+    if (!out) return fail(nullptr, TRT_EINVAL, "out is null");
+    *out = nullptr;
+    trt_handle *h = nullptr;   // errors during creation go to the global message (CK)
+    std::unique_ptr<trt_handle> hp(new trt_handle());
+    std::vector<double> xe, edges;
+    std::string err;
+    if (!validate(grid, angles, groups, opt, hp->p, xe, edges, err))
+        return fail(nullptr, TRT_EINVAL, err);
+    if (!opacity || !(opacity->scale > 0)) return fail(nullptr, TRT_EINVAL, "opacity scale must be > 0");
+    if (!(cv > 0)) return fail(nullptr, TRT_EINVAL, "cv must be > 0");
+    Problem &p = hp->p;
+    p.s = opacity->scale;
+    p.cv = cv;
+    Carver dry{nullptr, 0};
+    carve(hp.get(), dry);
+    const size_t need = (dry.off + 255) / 256 * 256;
+    if (!opt->workspace || (reinterpret_cast<uintptr_t>(opt->workspace) & 255))
+        return fail(nullptr, TRT_EINVAL, "workspace must be a 256-byte aligned device pointer");
+    if (opt->workspace_bytes < need)
+        return fail(nullptr, TRT_ENOSPACE, "workspace too small: need " + std::to_string(need) +
+                                               " bytes");
+    {
+        cudaError_t e = ensure_tables();
+        if (e != cudaSuccess) return fail(nullptr, TRT_ECUDA, cudaGetErrorString(e));
+    }
+    Carver c{reinterpret_cast<char *>(opt->workspace), 0};
+    trt_handle *H = hp.get();
+    carve(H, c);
+    {
+        cudaError_t e = cudaMallocHost(&H->hflags, 8 * sizeof(double));
+        if (e != cudaSuccess) return fail(nullptr, TRT_ECUDA, cudaGetErrorString(e));
+    }
+    const int nx = p.nx, G = p.G, M = p.M, N = p.N;
+    // host constants
+    std::vector<double> hh(nx), mu(M), w(M), Iin0(G, 0.0), IinX(G, 0.0);
+    std::vector<double> Ein0(G, 0.0), Fin0(G, 0.0), EinX(G, 0.0), FinX(G, 0.0);
+    for (int i = 0; i < nx; ++i) hh[i] = xe[i + 1] - xe[i];
+    {
+        std::vector<double> x(N), wx(N);
+        gauss_legendre_host(N, x.data(), wx.data());
+        for (int k = 0; k < N; ++k) {
+            mu[k] = 0.5 * (1.0 + x[k]);
+            w[k] = 0.5 * wx[k];
+            mu[N + k] = -mu[k];
+            w[N + k] = w[k];
+        }
+    }
+    if (p.Tl > 0) host_group_B(G, edges.data(), p.Tl, Iin0.data());
+    if (p.Tr > 0) host_group_B(G, edges.data(), p.Tr, IinX.data());
+    for (int g = 0; g < G; ++g)
+        for (int m = 0; m < M; ++m) {
+            if (m < N) {
+                Ein0[g] += w[m] * Iin0[g] / kC;
+                Fin0[g] += w[m] * mu[m] * Iin0[g];
+            } else {
+                EinX[g] += w[m] * IinX[g] / kC;
+                FinX[g] += w[m] * mu[m] * IinX[g];
+            }
+        }
+    // initial state (Sec. 6): T = T0, I = B_g(T0) on every corner and direction
+    std::vector<double> B0(G), T0v(nx, p.T0), Eg((size_t)G * nx), Fg((size_t)G * (nx + 1));
+    std::vector<double> f((size_t)G * nx), fb(G), C0v(G), CXv(G), Eg0(nx, 0.0), Fg0(nx + 1, 0.0);
+    host_group_B(G, edges.data(), p.T0, B0.data());
+    for (int g = 0; g < G; ++g) {
+        double s0 = 0, s1 = 0, s2 = 0, hm0 = 0, hm1 = 0, hp0 = 0, hp1 = 0;
+        for (int m = 0; m < M; ++m) {
+            s0 += w[m] * B0[g];
+            s1 += w[m] * mu[m] * B0[g];
+            s2 += w[m] * mu[m] * mu[m] * B0[g];
+            if (m >= N) { hm0 += w[m] * B0[g]; hm1 += w[m] * mu[m] * B0[g]; }
+            else { hp0 += w[m] * B0[g]; hp1 += w[m] * mu[m] * B0[g]; }
+        }
+        double fg = (s0 != 0.0) ? s2 / s0 : 1.0 / 3.0;
+        for (int i = 0; i < nx; ++i) {
+            Eg[(size_t)g * nx + i] = s0 / kC;
+            f[(size_t)g * nx + i] = fg;
+            Eg0[i] += s0 / kC;
+        }
+        for (int i = 0; i <= nx; ++i) {
+            Fg[(size_t)g * (nx + 1) + i] = s1;
+            Fg0[i] += s1;
+        }
+        fb[g] = fg;
+        C0v[g] = (hm0 != 0.0) ? hm1 / hm0 : -0.5;
+        CXv[g] = (hp0 != 0.0) ? hp1 / hp0 : 0.5;
+    }
+    auto up = [&](double *dst, const std::vector<double> &src) {
+        return cudaMemcpyAsync(dst, src.data(), src.size() * sizeof(double),
+                               cudaMemcpyHostToDevice, p.stream);
+    };
+    CK(up(p.h, hh)); CK(up(p.edges, edges)); CK(up(p.mu, mu)); CK(up(p.w, w));
+    CK(up(p.Iin0, Iin0)); CK(up(p.IinX, IinX)); CK(up(p.Ein0, Ein0)); CK(up(p.Fin0, Fin0));
+    CK(up(p.EinX, EinX)); CK(up(p.FinX, FinX));
+    CK(up(H->T, T0v)); CK(up(H->Eg, Eg)); CK(up(H->Fg, Fg)); CK(up(H->f, f));
+    CK(up(H->fb0, fb)); CK(up(H->fbX, fb)); CK(up(H->C0, C0v)); CK(up(H->CX, CXv));
+    CK(up(H->grey.E, Eg0)); CK(up(H->grey.F, Fg0));
+    CK(up(H->sigE, B0));   // B0 staged for the fill kernel
+    const long rows = (long)M * nx * 2;
+    const size_t nI = (size_t)rows * p.ldG;
+    const int nb = (int)std::min<long>(4096, (long)((nI + 255) / 256));
+    if (p.precision == TRT_FP64) {
+        k_fill_intensity<double><<<nb, 256, 0, p.stream>>>((double *)H->I_cur, H->sigE, rows, p.ldG, G);
+        k_fill_intensity<double><<<nb, 256, 0, p.stream>>>((double *)H->I_alt, H->sigE, rows, p.ldG, G);
+    } else {
+        k_fill_intensity<float><<<nb, 256, 0, p.stream>>>((float *)H->I_cur, H->sigE, rows, p.ldG, G);
+        k_fill_intensity<float><<<nb, 256, 0, p.stream>>>((float *)H->I_alt, H->sigE, rows, p.ldG, G);
+    }
+    CK(cudaGetLastError());
+    CK(cudaMemsetAsync(H->flags, 0, 8 * sizeof(double), p.stream));
+    CK(cudaStreamSynchronize(p.stream));
+    *out = hp.release();
+    return TRT_OK;
+}
+
+int trt_destroy(trt_handle *h)
+{
+    delete h;
+    return TRT_OK;
+}
+
+const char *trt_last_error(const trt_handle *h)
+{
+    return h ? h->err.c_str() : g_create_error.c_str();
+}
+
+int trt_dims(const trt_handle *h, int *nx, int *N, int *M, int *G, int *ldG, int *n_levels,
+             int *precision)
+{
+    if (!h) return TRT_EINVAL;
+    if (nx) *nx = h->p.nx;
+    if (N) *N = h->p.N;
+    if (M) *M = h->p.M;
+    if (G) *G = h->p.G;
+    if (ldG) *ldG = h->p.ldG;
+    if (n_levels) *n_levels = h->p.nlev;
+    if (precision) *precision = h->p.precision;
+    return TRT_OK;
+}
+
+int trt_step(trt_handle *h, double dt, const trt_cycle *cyc, trt_stats *stats)
+{
+    if (!h) return TRT_EINVAL;
+    if (!cyc || !(dt > 0) || cyc->l_max < 1 || cyc->max_outer < 1 || cyc->type < 0 ||
+        cyc->type > 2)
+        return fail(h, TRT_EINVAL, "bad step arguments");
+    auto t_start = std::chrono::steady_clock::now();
+    Problem &p = h->p;
+    const int nx = p.nx, G = p.G;
+    std::vector<int> S;
+    schedule(cyc->type, p.nlev, S);
+    const int K = (int)S.size();
+    const bool fixed = cyc->eps < 0;
+    const double eps = cyc->eps, eps_in = cyc->eps_inner;
+    int n_ti = 0, n_c = 0, n_lo = 0, s = 0, status = TRT_OK;
+    bool swept = false, opac_valid = false;
+    int have_prev = 0;
+
+    CK(d2d(h, h->Told, h->T, nx));
+    CK(d2d(h, h->Eg_old, h->Eg, (size_t)G * nx));
+    CK(d2d(h, h->Fg_old, h->Fg, (size_t)G * (nx + 1)));
+    CK(launch_group_sum(p, G, h->Eg_old, h->Ephase));
+    CK(cudaMemsetAsync(h->flags, 0, 8 * sizeof(double), p.stream));
+    Level fine = fine_level(h);
+
+    for (;;) {
+        if (s > 0) {
+            if (!opac_valid) CK(launch_opacity(p, h->T, h->sigE, h->emis, h->sigR));
+            opac_valid = true;
+            CK(launch_sweep(p, dt, h->sigE, h->emis, h->I_cur, h->I_alt, h->part, h->psi_exit,
+                            h->f, h->fb0, h->fbX, h->C0, h->CX));
+            ++n_ti;
+            swept = true;
+        }
+        CK(d2d(h, h->Tphase, h->T, nx));
+        CK(d2d(h, h->Tcyc, h->T, nx));
+        CK(d2d(h, h->Ecyc, h->Ephase, nx));
+        bool conv_out = false;
+        for (int l = 0; l < cyc->l_max; ++l) {
+            if (!opac_valid) CK(launch_opacity(p, h->T, h->sigE, h->emis, h->sigR));
+            opac_valid = true;
+            CK(launch_lo_solve(p, dt, fine));
+            n_lo += G;
+            CK(d2d(h, h->Ttil, h->T, nx));
+            for (int k = 0; k <= K; ++k) {
+                Level *src = &fine;
+                if (k > 0) {
+                    const int ng = p.levels[S[k - 1] - 1];
+                    CK(launch_opacity(p, h->Ttil, h->sigE, h->emis, h->sigR));
+                    opac_valid = false;
+                    h->crs.n = ng;
+                    CK(launch_restrict(p, fine, h->crs));
+                    CK(launch_lo_solve(p, dt, h->crs));
+                    n_lo += ng;
+                    src = &h->crs;
+                }
+                CK(launch_restrict(p, *src, h->grey));
+                GreyArgs a;
+                a.Tstar = h->Ttil; a.Told = h->Told; a.sig_prev = h->sig_prev; a.T_prev = h->T_prev;
+                a.T = h->Tnew; a.sig_prev_out = h->sig_prev; a.T_prev_out = h->T_prev;
+                a.have_prev = have_prev;
+                a.cv = p.cv; a.s = p.s; a.dt = dt;
+                a.nu_first = p.nu_first; a.nu_last = p.nu_last;
+                a.want_norms = (k == K);
+                a.Tcyc = h->Tcyc; a.Ecyc = h->Ecyc; a.Tphase = h->Tphase; a.Ephase = h->Ephase;
+                a.flags = h->flags;
+                CK(launch_grey(p, h->grey, a));
+                n_lo += 1;
+                have_prev = 1;
+                std::swap(h->Ttil, h->Tnew);
+            }
+            CK(d2d(h, h->T, h->Ttil, nx));
+            opac_valid = false;
+            CK(cudaMemcpyAsync(h->hflags, h->flags, 8 * sizeof(double), cudaMemcpyDeviceToHost,
+                               p.stream));
+            CK(cudaStreamSynchronize(p.stream));
+            ++n_c;
+            const double *fl = h->hflags;
+            if (fl[0] != 0.0) {
+                status = fail(h, TRT_ENUMERIC, "non-positive or non-finite temperature");
+                goto done;
+            }
+            bool conv_in = fl[1] <= eps_in * fl[2] && fl[3] <= eps_in * fl[4];
+            conv_out = fl[5] <= eps * fl[2] && fl[6] <= eps * fl[4];
+            CK(d2d(h, h->Tcyc, h->T, nx));
+            CK(d2d(h, h->Ecyc, h->grey.E, nx));
+            if (!fixed && conv_in) break;
+        }
+        CK(d2d(h, h->Ephase, h->grey.E, nx));
+        ++s;
+        if (fixed) {
+            if (s >= cyc->max_outer) break;
+        } else {
+            if (conv_out) break;
+            if (s >= cyc->max_outer) {
+                status = fail(h, TRT_ENOTCONVERGED, "outer iterations reached max_outer");
+                break;
+            }
+        }
+    }
+done:
+    CK(d2d(h, h->Eg, h->E1, (size_t)G * nx));
+    CK(d2d(h, h->Fg, h->F1, (size_t)G * (nx + 1)));
+    if (swept) std::swap(h->I_cur, h->I_alt);
+    CK(cudaStreamSynchronize(p.stream));
+    if (stats) {
+        stats->n_ti = n_ti; stats->n_c = n_c; stats->n_lo = n_lo; stats->n_outer = s;
+        stats->ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
+        stats->status = status;
+    }
+    return status;
+}
+
+int trt_moments(trt_handle *h, double *T, double *Eg, double *Fg, double *E, double *F)
+{
+    if (!h) return TRT_EINVAL;
+    const Problem &p = h->p;
+    const size_t nx = p.nx, G = p.G;
+    auto dn = [&](double *dst, const double *src, size_t n) {
+        return dst ? cudaMemcpyAsync(dst, src, n * sizeof(double), cudaMemcpyDeviceToHost, p.stream)
+                   : cudaSuccess;
+    };
+    CK(dn(T, h->T, nx));
+    CK(dn(Eg, h->Eg, G * nx));
+    CK(dn(Fg, h->Fg, G * (nx + 1)));
+    CK(dn(E, h->grey.E, nx));
+    CK(dn(F, h->grey.F, nx + 1));
+    CK(cudaStreamSynchronize(p.stream));
+    return TRT_OK;
+}
+
+int trt_intensity(trt_handle *h, double *I, double *f)
+{
+    if (!h) return TRT_EINVAL;
+    const Problem &p = h->p;
+    const size_t nI = (size_t)p.M * p.nx * 2 * p.ldG;
+    if (I) {
+        if (p.precision == TRT_FP64) {
+            CK(cudaMemcpyAsync(I, h->I_cur, nI * sizeof(double), cudaMemcpyDeviceToHost, p.stream));
+            CK(cudaStreamSynchronize(p.stream));
+        } else {
+            std::vector<float> tmp(nI);
+            CK(cudaMemcpyAsync(tmp.data(), h->I_cur, nI * sizeof(float), cudaMemcpyDeviceToHost, p.stream));
+            CK(cudaStreamSynchronize(p.stream));
+            for (size_t k = 0; k < nI; ++k) I[k] = tmp[k];
+        }
+    }
+    if (f) {
+        CK(cudaMemcpyAsync(f, h->f, (size_t)p.G * p.nx * sizeof(double), cudaMemcpyDeviceToHost,
+                           p.stream));
+        CK(cudaStreamSynchronize(p.stream));
+    }
+    return TRT_OK;
+}
+
+int trt_set_state(trt_handle *h, const double *T, const double *Eg, const double *Fg,
+                  const double *I, const double *f, const double *fb0, const double *fbX,
+                  const double *C0, const double *CX)
+{
+    if (!h) return TRT_EINVAL;
+    const Problem &p = h->p;
+    const size_t nx = p.nx, G = p.G;
+    auto upd = [&](double *dst, const double *src, size_t n) {
+        return src ? cudaMemcpyAsync(dst, src, n * sizeof(double), cudaMemcpyHostToDevice, p.stream)
+                   : cudaSuccess;
+    };
+    CK(upd(h->T, T, nx));
+    CK(upd(h->Eg, Eg, G * nx));
+    CK(upd(h->Fg, Fg, G * (nx + 1)));
+    CK(upd(h->f, f, G * nx));
+    CK(upd(h->fb0, fb0, G));
+    CK(upd(h->fbX, fbX, G));
+    CK(upd(h->C0, C0, G));
+    CK(upd(h->CX, CX, G));
+    std::vector<float> tmp;
+    if (I) {
+        const size_t nI = (size_t)p.M * p.nx * 2 * p.ldG;
+        if (p.precision == TRT_FP64) {
+            CK(cudaMemcpyAsync(h->I_cur, I, nI * sizeof(double), cudaMemcpyHostToDevice, p.stream));
+        } else {
+            tmp.resize(nI);
+            for (size_t k = 0; k < nI; ++k) tmp[k] = (float)I[k];
+            CK(cudaMemcpyAsync(h->I_cur, tmp.data(), nI * sizeof(float), cudaMemcpyHostToDevice,
+                               p.stream));
+        }
+    }
+    if (Eg) CK(launch_group_sum(h->p, (int)G, h->Eg, h->grey.E));
+    CK(cudaStreamSynchronize(p.stream));
+    return TRT_OK;
+}
+
+// ---- kernel-level entry points ----
+int trt_k_opacity(trt_handle *h, const double *T, double *sigE, double *emis, double *sigR)
+{
+    if (!h || !T || !sigE || !emis || !sigR) return TRT_EINVAL;
+    CK(launch_opacity(h->p, T, sigE, emis, sigR));
+    CK(cudaStreamSynchronize(h->p.stream));
+    return TRT_OK;
+}
+
+int trt_k_sweep(trt_handle *h, double dt, const double *sigE, const double *emis,
+                const void *I_old, void *I_new, double *f, double *fb0, double *fbX,
+                double *C0, double *CX)
+{
+    if (!h || !(dt > 0) || !sigE || !emis || !I_old || !I_new || !f || !fb0 || !fbX || !C0 || !CX)
+        return TRT_EINVAL;
+    CK(launch_sweep(h->p, dt, sigE, emis, I_old, I_new, h->part, h->psi_exit, f, fb0, fbX, C0, CX));
+    CK(cudaStreamSynchronize(h->p.stream));
+    return TRT_OK;
+}
+
+int trt_k_lo_solve(trt_handle *h, double dt, trt_level *lv)
+{
+    if (!h || !lv || !(dt > 0) || lv->n < 1) return TRT_EINVAL;
+    Level L = from_abi(lv);
+    CK(launch_lo_solve(h->p, dt, L));
+    CK(cudaStreamSynchronize(h->p.stream));
+    return TRT_OK;
+}
+
+int trt_k_restrict(trt_handle *h, const trt_level *src, trt_level *dst)
+{
+    if (!h || !src || !dst || dst->n < 1 || src->n < dst->n || src->n % dst->n) return TRT_EINVAL;
+    if (dst->n > 65535) return TRT_EINVAL;
+    Level S = from_abi(src), T = from_abi(dst);
+    CK(launch_restrict(h->p, S, T));
+    CK(cudaStreamSynchronize(h->p.stream));
+    return TRT_OK;
+}
+
+int trt_k_grey_newton(trt_handle *h, double dt, const double *Tstar, const double *Told,
+                      const double *sig_prev, const double *T_prev, int have_prev,
+                      trt_level *g, double *T)
+{
+    if (!h || !g || g->n != 1 || !(dt > 0) || !Tstar || !Told || !T) return TRT_EINVAL;
+    if (have_prev && (!sig_prev || !T_prev)) return TRT_EINVAL;
+    Level L = from_abi(g);
+    const Problem &p = h->p;
+    GreyArgs a;
+    a.Tstar = Tstar; a.Told = Told;
+    a.sig_prev = have_prev ? sig_prev : Tstar;
+    a.T_prev = have_prev ? T_prev : Tstar;
+    a.T = T;
+    a.sig_prev_out = h->part;             // scratch, not state
+    a.T_prev_out = h->part + p.nx;
+    a.have_prev = have_prev;
+    a.cv = p.cv; a.s = p.s; a.dt = dt;
+    a.nu_first = p.nu_first; a.nu_last = p.nu_last;
+    a.want_norms = 0;
+    a.Tcyc = a.Ecyc = a.Tphase = a.Ephase = nullptr;
+    a.flags = h->flags;
+    CK(cudaMemsetAsync(h->flags, 0, 8 * sizeof(double), p.stream));
+    CK(launch_grey(p, L, a));
+    CK(cudaMemcpyAsync(h->hflags, h->flags, 8 * sizeof(double), cudaMemcpyDeviceToHost, p.stream));
+    CK(cudaStreamSynchronize(p.stream));
+    if (h->hflags[0] != 0.0) return fail(h, TRT_ENUMERIC, "non-positive or non-finite temperature");
+    return TRT_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,627 @@
+// lo.cu -- low-order QD systems (K3/K4), restriction between frequency grids (K4), grey
+// LOQD + material energy balance Newton step (K5).
+//
+// One group of one level (eq. mloqd-d, eq. mloqd-d-gamma, Sec. 5) is
+//   cell i:  (dx_i/dt)(E_i - Eold_i) + F_{i+1/2} - F_{i-1/2} + dx_i a_i E_i = dx_i s_i
+//   face f:  (dx_f/(c dt))(F - Fold) + c (phiR E_right - phiL E_left) + sigR dx_f F = 0
+// with a = c sigma_E, s = 2 sigma_B B on the group levels; phiR = phi_right + eta-hat,
+// phiL = phi_left + eta-check; the boundary faces close a half cell with eq. mloqd-bcs
+// (F = c C (E_face - E_in) + F_in, the face energy eliminated).  Eliminating F face by
+// face, F_f = GD_f + PL_f E_{f-1} - PR_f E_f, gives a tridiagonal system in E that is
+// column diagonally dominant (the dx/dt term), so elimination needs no pivoting.
+//
+// GB300 mapping.  A warp owns one system.  FP64 throughput on GB300 is a small fraction of
+// FP32, so the solver keeps the FP64 work of plain Thomas elimination (one reciprocal per
+// row) but splits the serial chain: lane l eliminates its chunk of >= 2 consecutive rows
+// (a "modified Thomas" pass down and up the chunk that leaves each row coupled only to the
+// chunk's first and last unknowns), the 2 x 32 chunk-boundary unknowns form a tridiagonal
+// system solved by parallel cyclic reduction in registers with warp shuffles, and every
+// lane back-substitutes its interior rows.  Rows are built on the fly from the level's
+// fields; per-warp shared memory holds the chunk coefficients in a [row-in-chunk][lane]
+// layout (conflict free).
+#include <cmath>
+#include "common.cuh"
+
+namespace trt {
+
+namespace {
+
+struct LoCtx {
+    int nx;
+    double dt, icdt;
+    const double *h;
+    Level L;
+    const double *a_cell, *s_cell;   // grey: explicit absorption / source per cell
+};
+
+__device__ inline double sigR_face(const LoCtx &x, int q, int f)
+{
+    const int nx = x.nx;
+    if (!x.L.fine) return x.L.sigR[(size_t)q * (nx + 1) + f];
+    const double *sc = x.L.sigR + (size_t)q * nx;
+    if (f == 0) return sc[0];
+    if (f == nx) return sc[nx - 1];
+    return (sc[f - 1] * x.h[f - 1] + sc[f] * x.h[f]) / (x.h[f - 1] + x.h[f]);
+}
+
+// F_f = GD + PL E_{f-1} - PR E_f  (boundary faces: the face energy already eliminated)
+template <typename R>
+__device__ inline void face_coef(const LoCtx &x, int q, int f, R &PL, R &PR, R &GD)
+{
+    const int nx = x.nx;
+    const double *phi = x.L.phi + (size_t)q * nx;
+    R dx, phiL, phiR;
+    if (f == 0) {
+        dx = (R)(0.5 * x.h[0]);
+        phiL = (R)x.L.phib0[q];
+        phiR = (R)phi[0];
+    } else if (f == nx) {
+        dx = (R)(0.5 * x.h[nx - 1]);
+        phiL = (R)phi[nx - 1];
+        phiR = (R)x.L.phibX[q];
+    } else {
+        dx = (R)(0.5 * (x.h[f - 1] + x.h[f]));
+        phiL = (R)phi[f - 1];
+        phiR = (R)phi[f];
+    }
+    if (!x.L.fine) {
+        phiL += (R)x.L.etaL[(size_t)q * (nx + 1) + f];
+        phiR += (R)x.L.etaR[(size_t)q * (nx + 1) + f];
+    }
+    const R c = (R)kC, icdt = (R)x.icdt;
+    R D = dx * (icdt + (R)sigR_face(x, q, f));
+    R Gf = dx * (R)x.L.Fold[(size_t)q * (nx + 1) + f] * icdt;
+    if (f == 0) {
+        const R C0 = (R)x.L.C0[q];
+        D -= phiL / C0;
+        Gf += c * phiL * (R)x.L.Ein0[q] - phiL * (R)x.L.Fin0[q] / C0;
+    } else if (f == nx) {
+        const R CX = (R)x.L.CX[q];
+        D += phiR / CX;
+        Gf += -c * phiR * (R)x.L.EinX[q] + phiR * (R)x.L.FinX[q] / CX;
+    }
+    const R iD = (R)1 / D;
+    PL = c * phiL * iD;
+    PR = c * phiR * iD;
+    GD = Gf * iD;
+}
+
+template <typename R>
+__device__ inline void cell_terms(const LoCtx &x, int q, int i, R &ai, R &si)
+{
+    if (x.a_cell) {
+        ai = (R)x.a_cell[i];
+        si = (R)x.s_cell[i];
+    } else {
+        ai = (R)(kC * x.L.sig[(size_t)q * x.nx + i]);
+        si = (R)(2.0 * x.L.emis[(size_t)q * x.nx + i]);
+    }
+}
+
+// Solve system q with one warp.  sm: 3 * 32 * mmax values of R for this warp.
+// Writes E, F, Eb0, EbX of system q.
+template <typename R>
+__device__ void warp_lo_solve(const LoCtx &x, int q, R *sm, int mmax)
+{
+    const int lane = threadIdx.x & 31;
+    const int n = x.nx;
+    const R dt = (R)x.dt;
+    R *Ap = sm, *Cp = sm + 32 * mmax, *Dp = sm + 64 * mmax;
+    double *E = x.L.E + (size_t)q * n;
+    double *F = x.L.F + (size_t)q * (n + 1);
+
+    if (n == 1) {
+        if (lane == 0) {
+            R PL0, PR0, GD0, PL1, PR1, GD1, ai, si;
+            face_coef<R>(x, q, 0, PL0, PR0, GD0);
+            face_coef<R>(x, q, 1, PL1, PR1, GD1);
+            cell_terms<R>(x, q, 0, ai, si);
+            R hi = (R)x.h[0];
+            R di = hi / dt + hi * ai + PL1 + PR0;
+            R rh = hi * si + hi * (R)x.L.Eold[(size_t)q * n] / dt - GD1 + GD0;
+            R e0 = rh / di;
+            E[0] = (double)e0;
+            R F0 = GD0 - PR0 * e0, F1 = GD1 + PL1 * e0;
+            F[0] = (double)F0;
+            F[1] = (double)F1;
+            x.L.Eb0[q] = x.L.Ein0[q] + ((double)F0 - x.L.Fin0[q]) / (kC * x.L.C0[q]);
+            x.L.EbX[q] = x.L.EinX[q] + ((double)F1 - x.L.FinX[q]) / (kC * x.L.CX[q]);
+        }
+        return;
+    }
+
+    const int P = min(32, n / 2);
+    const bool act = lane < P;
+    const int r0 = act ? (lane * n) / P : n;
+    const int r1 = act ? ((lane + 1) * n) / P : n;
+    const int m = r1 - r0;
+#define SM(arr, k) arr[(k) * 32 + lane]
+
+    R x0 = 0, x1 = 0;
+    // ---- forward: rows r0..r1-1, each normalised, coupled to x_{r0} and x_{k+1} ----
+    R A0r = 0, C0r = 0, D0r = 0, A1r = 0, C1r = 0, D1r = 0;   // reduced rows
+    if (act) {
+        R PLi, PRi, GDi;
+        face_coef<R>(x, q, r0, PLi, PRi, GDi);
+        R ap = 0, cp = 0, dp = 0;
+        for (int k = 0; k < m; ++k) {
+            const int i = r0 + k;
+            R PL1, PR1, GD1, ai, si;
+            face_coef<R>(x, q, i + 1, PL1, PR1, GD1);
+            cell_terms<R>(x, q, i, ai, si);
+            const R hi = (R)x.h[i];
+            const R di = hi / dt + hi * ai + PL1 + PRi;
+            const R lo = (i > 0) ? -PLi : (R)0;
+            const R up = (i < n - 1) ? -PR1 : (R)0;
+            const R rh = hi * si + hi * (R)x.L.Eold[(size_t)q * n + i] / dt - GD1 + GDi;
+            if (k < 2) {
+                const R r = (R)1 / di;
+                ap = lo * r;
+                cp = up * r;
+                dp = rh * r;
+            } else {
+                const R r = (R)1 / (di - lo * cp);
+                dp = r * (rh - lo * dp);
+                ap = -r * lo * ap;
+                cp = r * up;
+            }
+            SM(Ap, k) = ap;
+            SM(Cp, k) = cp;
+            SM(Dp, k) = dp;
+            PLi = PL1;
+            PRi = PR1;
+            GDi = GD1;
+        }
+        // ---- backward: rows k = m-3..1 coupled to x_{r0} and x_{r1-1} ----
+        if (m >= 3) {
+            for (int k = m - 3; k >= 1; --k) {
+                const R ck = SM(Cp, k);
+                SM(Dp, k) = SM(Dp, k) - ck * SM(Dp, k + 1);
+                SM(Ap, k) = SM(Ap, k) - ck * SM(Ap, k + 1);
+                SM(Cp, k) = -ck * SM(Cp, k + 1);
+            }
+            const R c0 = SM(Cp, 0);
+            const R r = (R)1 / ((R)1 - c0 * SM(Ap, 1));
+            SM(Dp, 0) = r * (SM(Dp, 0) - c0 * SM(Dp, 1));
+            SM(Ap, 0) = r * SM(Ap, 0);
+            SM(Cp, 0) = -r * c0 * SM(Cp, 1);
+        }
+        A0r = SM(Ap, 0); C0r = SM(Cp, 0); D0r = SM(Dp, 0);
+        A1r = SM(Ap, m - 1); C1r = SM(Cp, m - 1); D1r = SM(Dp, m - 1);
+    }
+    // ---- reduced system: rows (first_l, last_l), l = 0..31, by PCR with shuffles ----
+    {
+        R B0r = 1, B1r = 1;
+        if (!act) { A0r = C0r = D0r = A1r = C1r = D1r = 0; }
+        const unsigned full = 0xffffffffu;
+        for (int s = 1; s < 64; s <<= 1) {
+            R lA0, lB0, lC0, lD0, uA0, uB0, uC0, uD0;   // neighbours of slot 0
+            R lA1, lB1, lC1, lD1, uA1, uB1, uC1, uD1;   // neighbours of slot 1
+            if (s == 1) {
+                R tA = __shfl_up_sync(full, A1r, 1), tB = __shfl_up_sync(full, B1r, 1);
+                R tC = __shfl_up_sync(full, C1r, 1), tD = __shfl_up_sync(full, D1r, 1);
+                R vA = __shfl_down_sync(full, A0r, 1), vB = __shfl_down_sync(full, B0r, 1);
+                R vC = __shfl_down_sync(full, C0r, 1), vD = __shfl_down_sync(full, D0r, 1);
+                if (lane >= 1) { lA0 = tA; lB0 = tB; lC0 = tC; lD0 = tD; }
+                else { lA0 = 0; lB0 = 1; lC0 = 0; lD0 = 0; }
+                uA0 = A1r; uB0 = B1r; uC0 = C1r; uD0 = D1r;
+                lA1 = A0r; lB1 = B0r; lC1 = C0r; lD1 = D0r;
+                if (lane <= 30) { uA1 = vA; uB1 = vB; uC1 = vC; uD1 = vD; }
+                else { uA1 = 0; uB1 = 1; uC1 = 0; uD1 = 0; }
+            } else {
+                const int t = s >> 1;
+                R a0 = __shfl_up_sync(full, A0r, t), b0 = __shfl_up_sync(full, B0r, t);
+                R c0 = __shfl_up_sync(full, C0r, t), d0 = __shfl_up_sync(full, D0r, t);
+                R a1 = __shfl_up_sync(full, A1r, t), b1 = __shfl_up_sync(full, B1r, t);
+                R c1 = __shfl_up_sync(full, C1r, t), d1 = __shfl_up_sync(full, D1r, t);
+                R e0 = __shfl_down_sync(full, A0r, t), f0 = __shfl_down_sync(full, B0r, t);
+                R g0 = __shfl_down_sync(full, C0r, t), h0 = __shfl_down_sync(full, D0r, t);
+                R e1 = __shfl_down_sync(full, A1r, t), f1 = __shfl_down_sync(full, B1r, t);
+                R g1 = __shfl_down_sync(full, C1r, t), h1 = __shfl_down_sync(full, D1r, t);
+                if (lane >= t) {
+                    lA0 = a0; lB0 = b0; lC0 = c0; lD0 = d0;
+                    lA1 = a1; lB1 = b1; lC1 = c1; lD1 = d1;
+                } else {
+                    lA0 = lA1 = 0; lB0 = lB1 = 1; lC0 = lC1 = 0; lD0 = lD1 = 0;
+                }
+                if (lane + t <= 31) {
+                    uA0 = e0; uB0 = f0; uC0 = g0; uD0 = h0;
+                    uA1 = e1; uB1 = f1; uC1 = g1; uD1 = h1;
+                } else {
+                    uA0 = uA1 = 0; uB0 = uB1 = 1; uC0 = uC1 = 0; uD0 = uD1 = 0;
+                }
+            }
+            {
+                const R al = -A0r / lB0, ga = -C0r / uB0;
+                const R nA = al * lA0, nC = ga * uC0;
+                const R nB = B0r + al * lC0 + ga * uA0, nD = D0r + al * lD0 + ga * uD0;
+                A0r = nA; B0r = nB; C0r = nC; D0r = nD;
+            }
+            {
+                const R al = -A1r / lB1, ga = -C1r / uB1;
+                const R nA = al * lA1, nC = ga * uC1;
+                const R nB = B1r + al * lC1 + ga * uA1, nD = D1r + al * lD1 + ga * uD1;
+                A1r = nA; B1r = nB; C1r = nC; D1r = nD;
+            }
+        }
+        x0 = D0r / B0r;
+        x1 = D1r / B1r;
+    }
+    // ---- back substitution of interior rows; E into Dp ----
+    if (act) {
+        for (int k = 1; k < m - 1; ++k)
+            SM(Dp, k) = SM(Dp, k) - SM(Ap, k) * x0 - SM(Cp, k) * x1;
+        SM(Dp, 0) = x0;
+        SM(Dp, m - 1) = x1;
+        for (int k = 0; k < m; ++k) E[r0 + k] = (double)SM(Dp, k);
+    }
+    __syncwarp();
+    // ---- fluxes: faces r0..r1-1, and the right boundary face by the last lane ----
+    if (act) {
+        const int r0p = (lane > 0) ? ((lane - 1) * n) / P : 0;
+        const R Eleft0 = (lane > 0) ? Dp[(r0 - r0p - 1) * 32 + lane - 1] : (R)0;
+        const int fend = (lane == P - 1) ? n : r1 - 1;
+        for (int f = r0; f <= fend; ++f) {
+            R PL, PR, GD;
+            face_coef<R>(x, q, f, PL, PR, GD);
+            R Fv = GD;
+            if (f > 0) Fv += PL * ((f == r0) ? Eleft0 : SM(Dp, f - 1 - r0));
+            if (f < n) Fv -= PR * SM(Dp, f - r0);
+            F[f] = (double)Fv;
+            if (f == 0) x.L.Eb0[q] = x.L.Ein0[q] + ((double)Fv - x.L.Fin0[q]) / (kC * x.L.C0[q]);
+            if (f == n) x.L.EbX[q] = x.L.EinX[q] + ((double)Fv - x.L.FinX[q]) / (kC * x.L.CX[q]);
+        }
+    }
+#undef SM
+}
+
+inline int lo_mmax(int nx) { return nx < 2 ? 1 : (nx + (std::min(32, nx / 2)) - 1) / std::min(32, nx / 2) + 1; }
+
+template <typename R>
+__global__ void __launch_bounds__(256) k_lo_solve(LoCtx x, int mmax)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int W = blockDim.x >> 5;
+    const int warp = threadIdx.x >> 5;
+    const int q = blockIdx.x * W + warp;
+    if (q >= x.L.n) return;
+    R *sm = reinterpret_cast<R *>(smem_raw) + (size_t)warp * 3 * 32 * mmax;
+    warp_lo_solve<R>(x, q, sm, mmax);
+}
+
+// ---------------------------------------------------------------------------------------
+// restriction (eqs. coeff-gamma, g-notation, eta-gamma / coeff-Gamma, g2G-notation,
+// eta-Gamma, and the discrete compensation of eq. mloqd-d-gamma)
+// ---------------------------------------------------------------------------------------
+constexpr int kRV1 = 18;   // pass-1 sums
+constexpr int kRV2 = 6;    // pass-2 sums
+
+struct RestrictCtx {
+    int nx, r;       // r = members per coarse group
+    const double *h;
+    Level S;         // source level (coefficients + solution)
+    Level T;         // target level (written)
+};
+
+__device__ inline double src_phi_b(const Level &S, int p, int side)
+{
+    return side == 0 ? S.phib0[p] : S.phibX[p];
+}
+
+// block (32, KS); grid (ceil((nx+1)/32), n_to)
+__global__ void k_restrict(RestrictCtx x)
+{
+    extern __shared__ __align__(16) double rsm[];
+    const int tx = threadIdx.x, ty = threadIdx.y, KS = blockDim.y;
+    const int nx = x.nx, nf = nx + 1;
+    const int i = blockIdx.x * 32 + tx;   // cell index and face index
+    const int P = blockIdx.y;
+    const int pb = P * x.r;
+    const Level &S = x.S;
+    double v[kRV1];
+#pragma unroll
+    for (int k = 0; k < kRV1; ++k) v[k] = 0.0;
+    // ---- pass 1 ----
+    for (int p = pb + ty; p < pb + x.r; p += KS) {
+        if (i < nx) {
+            size_t c = (size_t)p * nx + i;
+            double E = S.E[c];
+            double ph = S.phi[c], sg = S.sig[c];
+            v[0] += ph * E; v[1] += ph; v[2] += sg * E; v[3] += sg;
+            v[4] += S.emis[c]; v[5] += S.Eold[c]; v[6] += E;
+        }
+        if (i <= nx) {
+            double Fp = S.F[(size_t)p * nf + i];
+            double sR;
+            if (S.fine) {
+                const double *sc = S.sigR + (size_t)p * nx;
+                sR = (i == 0) ? sc[0] : (i == nx) ? sc[nx - 1]
+                     : (sc[i - 1] * x.h[i - 1] + sc[i] * x.h[i]) / (x.h[i - 1] + x.h[i]);
+            } else {
+                sR = S.sigR[(size_t)p * nf + i];
+            }
+            double aF = fabs(Fp);
+            v[7] += sR * aF; v[8] += sR; v[9] += aF;
+        }
+        if (i == 0 || i == nx) {
+            const int side = (i == 0) ? 0 : 1;
+            double Eb = side == 0 ? S.Eb0[p] : S.EbX[p];
+            double Ein = side == 0 ? S.Ein0[p] : S.EinX[p];
+            double Fin = side == 0 ? S.Fin0[p] : S.FinX[p];
+            double Cb = side == 0 ? S.C0[p] : S.CX[p];
+            double ph = src_phi_b(S, p, side);
+            double Eo = Eb - Ein;
+            v[10] += ph * Eb; v[11] += ph; v[12] += Eb;
+            v[13] += Cb * Eo; v[14] += Cb; v[15] += Eo;
+            v[16] += Ein; v[17] += Fin;
+        }
+    }
+    // reduce over ty
+    if (KS > 1) {
+        double *red = rsm + ((size_t)ty * 32 + tx) * kRV1;
+        for (int k = 0; k < kRV1; ++k) red[k] = v[k];
+        __syncthreads();
+        if (ty == 0) {
+            for (int y = 1; y < KS; ++y) {
+                const double *o = rsm + ((size_t)y * 32 + tx) * kRV1;
+                for (int k = 0; k < kRV1; ++k) v[k] += o[k];
+            }
+            double *bc = rsm + (size_t)tx * kRV1;
+            for (int k = 0; k < kRV1; ++k) bc[k] = v[k];
+        }
+        __syncthreads();
+        if (ty != 0) {
+            const double *bc = rsm + (size_t)tx * kRV1;
+            for (int k = 0; k < kRV1; ++k) v[k] = bc[k];
+        }
+        __syncthreads();
+    }
+    const double rn = (double)x.r;
+    const double sRP = (v[9] != 0.0) ? v[7] / v[9] : v[8] / rn;
+    // ---- pass 2 (faces): xi, eta sums, side energies, Fold ----
+    double u[kRV2];
+#pragma unroll
+    for (int k = 0; k < kRV2; ++k) u[k] = 0.0;
+    if (i <= nx) {
+        const double dxf = (i == 0) ? 0.5 * x.h[0] : (i == nx) ? 0.5 * x.h[nx - 1]
+                                               : 0.5 * (x.h[i - 1] + x.h[i]);
+        for (int p = pb + ty; p < pb + x.r; p += KS) {
+            size_t fp = (size_t)p * nf + i;
+            double Fp = S.F[fp];
+            double sR;
+            if (S.fine) {
+                const double *sc = S.sigR + (size_t)p * nx;
+                sR = (i == 0) ? sc[0] : (i == nx) ? sc[nx - 1]
+                     : (sc[i - 1] * x.h[i - 1] + sc[i] * x.h[i]) / (x.h[i - 1] + x.h[i]);
+            } else {
+                sR = S.sigR[fp];
+            }
+            double ER = (i == nx) ? S.EbX[p] : S.E[(size_t)p * nx + i];
+            double EL = (i == 0) ? S.Eb0[p] : S.E[(size_t)p * nx + i - 1];
+            u[0] += dxf * (sR - sRP) * Fp;
+            if (!S.fine) {
+                u[1] += S.etaR[fp] * ER;
+                u[2] += S.etaL[fp] * EL;
+            }
+            u[3] += ER; u[4] += EL; u[5] += S.Fold[fp];
+        }
+    }
+    if (KS > 1) {
+        double *red = rsm + ((size_t)ty * 32 + tx) * kRV2;
+        for (int k = 0; k < kRV2; ++k) red[k] = u[k];
+        __syncthreads();
+        if (ty == 0) {
+            for (int y = 1; y < KS; ++y) {
+                const double *o = rsm + ((size_t)y * 32 + tx) * kRV2;
+                for (int k = 0; k < kRV2; ++k) u[k] += o[k];
+            }
+        }
+    }
+    if (ty != 0) return;
+    Level &T = x.T;
+    if (i < nx) {
+        size_t c = (size_t)P * nx + i;
+        (T.phi)[c] = (v[6] != 0.0) ? v[0] / v[6] : v[1] / rn;
+        (T.sig)[c] = (v[6] != 0.0) ? v[2] / v[6] : v[3] / rn;
+        (T.emis)[c] = v[4];
+        (T.Eold)[c] = v[5];
+        T.Esum[c] = v[6];
+    }
+    if (i <= nx) {
+        size_t f = (size_t)P * nf + i;
+        double xi = u[0] + kC * (u[1] - u[2]);
+        (T.sigR)[f] = sRP;
+        (T.etaR)[f] = (xi > 0.0 && u[3] != 0.0) ? xi / (kC * u[3]) : 0.0;
+        (T.etaL)[f] = (xi < 0.0 && u[4] != 0.0) ? -xi / (kC * u[4]) : 0.0;
+        (T.Fold)[f] = u[5];
+    }
+    if (i == 0 || i == nx) {
+        double phb = (v[12] != 0.0) ? v[10] / v[12] : v[11] / rn;
+        double Cb = (v[15] != 0.0) ? v[13] / v[15] : v[14] / rn;
+        if (i == 0) {
+            (T.phib0)[P] = phb;
+            (T.C0)[P] = Cb;
+            (T.Ein0)[P] = v[16];
+            (T.Fin0)[P] = v[17];
+        } else {
+            (T.phibX)[P] = phb;
+            (T.CX)[P] = Cb;
+            (T.EinX)[P] = v[16];
+            (T.FinX)[P] = v[17];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// grey LOQD + MEB: one Newton step on the grey level (single CTA)
+// ---------------------------------------------------------------------------------------
+struct GreyCtx {
+    LoCtx lo;
+    GreyArgs a;
+    int mmax;
+};
+
+__device__ inline double block_max(double v, double *red)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    __syncthreads();
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    double r = 0.0;
+    for (int k = 0; k < nw; ++k) r = fmax(r, red[k]);
+    return r;
+}
+
+__global__ void __launch_bounds__(1024) k_grey(GreyCtx x)
+{
+    extern __shared__ __align__(16) double gsm[];
+    const int nx = x.lo.nx;
+    double *sa = gsm;            // absorption w c sig*
+    double *ss = sa + nx;        // source w Q* - (1-w) cv (T* - Told)/dt
+    double *sL = ss + nx;        // Lambda
+    double *red = sL + nx;       // [32]
+    double *wsm = red + 32;      // warp-solver scratch
+    const GreyArgs &a = x.a;
+    const Level &g = x.lo.L;
+    const double cvdt = a.cv / a.dt;
+    const double k54 = 54.0 * a.s * kCB;   // d/dT [2 sum_g e_g] telescopes to the end edges
+    for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+        const double Ts = a.Tstar[i];
+        const double sig = g.sig[i];
+        const double Q = 2.0 * g.emis[i];
+        const double x1 = a.nu_first / Ts;
+        double dQ = k54 * (1.0 + x1) * exp(-x1);
+        if (!isinf(a.nu_last)) {
+            const double xL = a.nu_last / Ts;
+            dQ -= k54 * (1.0 + xL) * exp(-xL);
+        }
+        double D = 0.0;
+        if (a.have_prev) {
+            const double Tp = a.T_prev[i];
+            if (fabs(Ts - Tp) > 1e-12 * Ts) D = (sig - a.sig_prev[i]) / (Ts - Tp);
+        }
+        const double base = cvdt + dQ;
+        double L = base - kC * D * g.Esum[i];
+        if (L < 0.5 * base) L = 0.5 * base;
+        const double w = cvdt / L;
+        sa[i] = w * kC * sig;
+        ss[i] = w * Q - (1.0 - w) * cvdt * (Ts - a.Told[i]);
+        sL[i] = L;
+        a.sig_prev_out[i] = sig;
+        a.T_prev_out[i] = Ts;
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        LoCtx lc = x.lo;
+        lc.a_cell = sa;
+        lc.s_cell = ss;
+        warp_lo_solve<double>(lc, 0, wsm, x.mmax);
+    }
+    __syncthreads();
+    double dTc = 0, Tm = 0, dEc = 0, Em = 0, dTp = 0, dEp = 0, bad = 0;
+    for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+        const double Ts = a.Tstar[i];
+        const double E = g.E[i];
+        const double T = Ts + (kC * g.sig[i] * E - 2.0 * g.emis[i] - cvdt * (Ts - a.Told[i])) / sL[i];
+        a.T[i] = T;
+        if (!(T > 0.0) || !isfinite(T) || !isfinite(E)) bad = 1.0;
+        if (a.want_norms) {
+            Tm = fmax(Tm, fabs(T));
+            Em = fmax(Em, fabs(E));
+            dTc = fmax(dTc, fabs(T - a.Tcyc[i]));
+            dEc = fmax(dEc, fabs(E - a.Ecyc[i]));
+            dTp = fmax(dTp, fabs(T - a.Tphase[i]));
+            dEp = fmax(dEp, fabs(E - a.Ephase[i]));
+        }
+    }
+    bad = block_max(bad, red);
+    if (threadIdx.x == 0 && bad != 0.0) a.flags[0] = 1.0;
+    if (a.want_norms) {
+        dTc = block_max(dTc, red);
+        Tm = block_max(Tm, red);
+        dEc = block_max(dEc, red);
+        Em = block_max(Em, red);
+        dTp = block_max(dTp, red);
+        dEp = block_max(dEp, red);
+        if (threadIdx.x == 0) {
+            a.flags[1] = dTc; a.flags[2] = Tm; a.flags[3] = dEc; a.flags[4] = Em;
+            a.flags[5] = dTp; a.flags[6] = dEp;
+        }
+    }
+}
+
+__global__ void k_group_sum(int n, int nx, const double *__restrict__ X, double *__restrict__ out)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nx) return;
+    double s = 0.0;
+    for (int q = 0; q < n; ++q) s += X[(size_t)q * nx + i];
+    out[i] = s;
+}
+
+}  // namespace
+
+cudaError_t launch_lo_solve(const Problem &p, double dt, const Level &L)
+{
+    LoCtx x;
+    x.nx = p.nx; x.dt = dt; x.icdt = 1.0 / (kC * dt); x.h = p.h; x.L = L;
+    x.a_cell = nullptr; x.s_cell = nullptr;
+    const int mmax = lo_mmax(p.nx);
+    const size_t rsz = (p.precision == TRT_FP64) ? sizeof(double) : sizeof(float);
+    const size_t per_warp = 3 * 32 * (size_t)mmax * rsz;
+    int W = (int)std::max<size_t>(1, std::min<size_t>(8, (96 * 1024) / per_warp));
+    const size_t sm = per_warp * W;
+    const unsigned nb = (unsigned)((L.n + W - 1) / W);
+    cudaError_t e;
+    if (p.precision == TRT_FP64) {
+        e = cudaFuncSetAttribute(k_lo_solve<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)sm);
+        if (e != cudaSuccess) return e;
+        k_lo_solve<double><<<nb, 32 * W, sm, p.stream>>>(x, mmax);
+    } else {
+        e = cudaFuncSetAttribute(k_lo_solve<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)sm);
+        if (e != cudaSuccess) return e;
+        k_lo_solve<float><<<nb, 32 * W, sm, p.stream>>>(x, mmax);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_restrict(const Problem &p, const Level &src, Level &dst)
+{
+    RestrictCtx x;
+    x.nx = p.nx; x.r = src.n / dst.n; x.h = p.h; x.S = src; x.T = dst;
+    int KS = 1;
+    while (KS < 8 && KS * 4 <= x.r) KS *= 2;
+    if (x.r >= 64) KS = 8;
+    dim3 block(32, KS);
+    dim3 grid((p.nx + 1 + 31) / 32, dst.n);
+    size_t sm = (KS > 1) ? sizeof(double) * KS * 32 * kRV1 : 0;
+    k_restrict<<<grid, block, sm, p.stream>>>(x);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_grey(const Problem &p, const Level &g, const GreyArgs &a)
+{
+    GreyCtx x;
+    x.lo.nx = p.nx; x.lo.dt = a.dt; x.lo.icdt = 1.0 / (kC * a.dt); x.lo.h = p.h; x.lo.L = g;
+    x.lo.a_cell = nullptr; x.lo.s_cell = nullptr;
+    x.a = a;
+    x.mmax = lo_mmax(p.nx);
+    int bs = std::min(1024, std::max(32, (p.nx + 31) / 32 * 32));
+    size_t sm = sizeof(double) * (3 * (size_t)p.nx + 32 + 3 * 32 * (size_t)x.mmax);
+    cudaError_t e = cudaFuncSetAttribute(k_grey, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)sm);
+    if (e != cudaSuccess) return e;
+    k_grey<<<1, bs, sm, p.stream>>>(x);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_group_sum(const Problem &p, int n, const double *X, double *out)
+{
+    k_group_sum<<<(p.nx + 127) / 128, 128, 0, p.stream>>>(n, p.nx, X, out);
+    return cudaGetLastError();
+}
+
+}  // namespace trt

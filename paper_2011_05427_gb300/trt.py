@@ -1,0 +1,318 @@
+"""Python binding of the C ABI in include/trt.h (argument marshalling only).
+
+Every step of the method runs in the CUDA library libtrt.so; this module allocates the
+device workspace with torch, passes raw pointers and the current torch stream, and
+converts results to numpy / torch.  If the library is missing it raises -- there is no
+CPU fallback.
+"""
+import ctypes
+import math
+import os
+from typing import Dict, Optional
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libtrt.so")
+
+TRT_OK, TRT_EINVAL, TRT_ENOTCONVERGED, TRT_ENUMERIC, TRT_ETIMEOUT, TRT_ECUDA, TRT_ENOSPACE = \
+    0, -1, -2, -3, -4, -5, -6
+TRT_FP64, TRT_MIXED = 0, 1
+CYCLES = {"V": 0, "W": 1, "F": 2}
+PRECISIONS = {"fp64": TRT_FP64, "mixed": TRT_MIXED}
+
+_dp = ctypes.POINTER(ctypes.c_double)
+_vp = ctypes.c_void_p
+
+
+class trt_grid(ctypes.Structure):
+    _fields_ = [("n_cells", ctypes.c_int), ("x_edges", _dp), ("length_cm", ctypes.c_double),
+                ("T_left_keV", ctypes.c_double), ("T_right_keV", ctypes.c_double)]
+
+
+class trt_angles(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int)]
+
+
+class trt_groups(ctypes.Structure):
+    _fields_ = [("n_groups", ctypes.c_int), ("edges_keV", _dp), ("nu_a", ctypes.c_double),
+                ("nu_b", ctypes.c_double), ("n_levels", ctypes.c_int),
+                ("level_groups", ctypes.POINTER(ctypes.c_int))]
+
+
+class trt_opacity(ctypes.Structure):
+    _fields_ = [("scale", ctypes.c_double)]
+
+
+class trt_options(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("T0_keV", ctypes.c_double), ("stream", _vp),
+                ("workspace", _vp), ("workspace_bytes", ctypes.c_size_t)]
+
+
+class trt_cycle(ctypes.Structure):
+    _fields_ = [("type", ctypes.c_int), ("l_max", ctypes.c_int), ("eps", ctypes.c_double),
+                ("eps_inner", ctypes.c_double), ("max_outer", ctypes.c_int)]
+
+
+class trt_stats(ctypes.Structure):
+    _fields_ = [("n_ti", ctypes.c_int), ("n_c", ctypes.c_int), ("n_lo", ctypes.c_int),
+                ("n_outer", ctypes.c_int), ("ms", ctypes.c_double), ("status", ctypes.c_int)]
+
+
+LEVEL_FIELDS = ("phi", "sig", "emis", "Eold", "Esum", "sigR", "etaR", "etaL", "Fold",
+                "phib0", "phibX", "C0", "CX", "Ein0", "Fin0", "EinX", "FinX",
+                "E", "F", "Eb0", "EbX")
+CELL_FIELDS = ("phi", "sig", "emis", "Eold", "Esum", "E")
+FACE_FIELDS = ("sigR", "etaR", "etaL", "Fold", "F")
+
+
+class trt_level(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int)] + [(k, _dp) for k in LEVEL_FIELDS]
+
+
+_lib = None
+
+
+def lib():
+    """Load libtrt.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with __graft_entry__.build() "
+                           "(the solver has no CPU fallback)")
+    L = ctypes.CDLL(LIB_PATH)
+    L.trt_workspace_bytes.restype = ctypes.c_size_t
+    L.trt_workspace_bytes.argtypes = [ctypes.POINTER(trt_grid), ctypes.POINTER(trt_angles),
+                                      ctypes.POINTER(trt_groups), ctypes.POINTER(trt_options)]
+    L.trt_create.restype = ctypes.c_int
+    L.trt_create.argtypes = [ctypes.POINTER(trt_grid), ctypes.POINTER(trt_angles),
+                             ctypes.POINTER(trt_groups), ctypes.POINTER(trt_opacity),
+                             ctypes.c_double, ctypes.POINTER(trt_options),
+                             ctypes.POINTER(_vp)]
+    L.trt_step.restype = ctypes.c_int
+    L.trt_step.argtypes = [_vp, ctypes.c_double, ctypes.POINTER(trt_cycle),
+                           ctypes.POINTER(trt_stats)]
+    L.trt_moments.restype = ctypes.c_int
+    L.trt_moments.argtypes = [_vp, _dp, _dp, _dp, _dp, _dp]
+    L.trt_intensity.restype = ctypes.c_int
+    L.trt_intensity.argtypes = [_vp, _dp, _dp]
+    L.trt_set_state.restype = ctypes.c_int
+    L.trt_set_state.argtypes = [_vp] + [_dp] * 9
+    L.trt_dims.restype = ctypes.c_int
+    L.trt_dims.argtypes = [_vp] + [ctypes.POINTER(ctypes.c_int)] * 7
+    L.trt_destroy.restype = ctypes.c_int
+    L.trt_destroy.argtypes = [_vp]
+    L.trt_last_error.restype = ctypes.c_char_p
+    L.trt_last_error.argtypes = [_vp]
+    L.trt_k_opacity.restype = ctypes.c_int
+    L.trt_k_opacity.argtypes = [_vp, _vp, _vp, _vp, _vp]
+    L.trt_k_sweep.restype = ctypes.c_int
+    L.trt_k_sweep.argtypes = [_vp, ctypes.c_double] + [_vp] * 9
+    L.trt_k_lo_solve.restype = ctypes.c_int
+    L.trt_k_lo_solve.argtypes = [_vp, ctypes.c_double, ctypes.POINTER(trt_level)]
+    L.trt_k_restrict.restype = ctypes.c_int
+    L.trt_k_restrict.argtypes = [_vp, ctypes.POINTER(trt_level), ctypes.POINTER(trt_level)]
+    L.trt_k_grey_newton.restype = ctypes.c_int
+    L.trt_k_grey_newton.argtypes = [_vp, ctypes.c_double, _vp, _vp, _vp, _vp, ctypes.c_int,
+                                    ctypes.POINTER(trt_level), _vp]
+    _lib = L
+    return L
+
+
+EXPORTED = ("trt_workspace_bytes", "trt_create", "trt_step", "trt_moments", "trt_intensity",
+            "trt_set_state", "trt_dims", "trt_destroy", "trt_last_error", "trt_k_opacity",
+            "trt_k_sweep", "trt_k_lo_solve", "trt_k_restrict", "trt_k_grey_newton")
+
+
+class TRTError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"trt error {code}: {msg}")
+        self.code = code
+
+
+def _ptr(a):
+    return ctypes.cast(ctypes.c_void_p(a.data_ptr()), _dp) if a is not None else None
+
+
+def _np_dp(a):
+    return a.ctypes.data_as(_dp) if a is not None else None
+
+
+class Solver:
+    """One slab on one GPU: trt_create / trt_step / trt_moments / trt_destroy."""
+
+    def __init__(self, n_cells, length_cm, N, edges, level_groups, opac_scale=1.0,
+                 cv=0.5917 * 0.01372, T0=1e-3, T_left=1.0, T_right=0.0, precision="fp64",
+                 device=None, stream=None, x_edges=None):
+        import torch
+        self.torch = torch
+        self.device = torch.device(device) if device is not None else torch.device("cuda")
+        L = lib()
+        self._edges = np.ascontiguousarray(edges, np.float64)
+        self._levels = np.ascontiguousarray(level_groups, np.int32)
+        self._xe = None if x_edges is None else np.ascontiguousarray(x_edges, np.float64)
+        self.grid = trt_grid(int(n_cells), _np_dp(self._xe), float(length_cm), float(T_left),
+                             float(T_right))
+        self.angles = trt_angles(int(N))
+        self.groups = trt_groups(self._edges.size - 1, _np_dp(self._edges), 0.0, 0.0,
+                                 self._levels.size,
+                                 self._levels.ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
+        self.opacity = trt_opacity(float(opac_scale))
+        self.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        with torch.cuda.device(self.device):
+            self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+            opt = trt_options(self.precision, float(T0), ctypes.c_void_p(self.stream.cuda_stream),
+                              None, 0)
+            nbytes = L.trt_workspace_bytes(ctypes.byref(self.grid), ctypes.byref(self.angles),
+                                           ctypes.byref(self.groups), ctypes.byref(opt))
+            if nbytes == 0:
+                raise TRTError(TRT_EINVAL, "invalid problem (trt_workspace_bytes returned 0)")
+            self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+            base = self.workspace.data_ptr()
+            aligned = (base + 255) // 256 * 256
+            opt.workspace = ctypes.c_void_p(aligned)
+            opt.workspace_bytes = nbytes
+            h = ctypes.c_void_p()
+            rc = L.trt_create(ctypes.byref(self.grid), ctypes.byref(self.angles),
+                              ctypes.byref(self.groups), ctypes.byref(self.opacity), float(cv),
+                              ctypes.byref(opt), ctypes.byref(h))
+            if rc != TRT_OK:
+                raise TRTError(rc, L.trt_last_error(None).decode())
+        self.h = h
+        self.workspace_bytes = nbytes
+        dims = [ctypes.c_int() for _ in range(7)]
+        L.trt_dims(self.h, *[ctypes.byref(d) for d in dims])
+        self.nx, self.N, self.M, self.G, self.ldG, self.n_levels, _ = [d.value for d in dims]
+
+    @classmethod
+    def from_slab(cls, slab, precision="fp64", **kw):
+        return cls(slab.n_cells, slab.length_cm, slab.N, slab.edges(), slab.levels,
+                   slab.opac_scale, slab.cv, slab.T0, slab.T_left, slab.T_right,
+                   precision=precision, **kw)
+
+    def _check(self, rc, allow=()):
+        if rc != TRT_OK and rc not in allow:
+            raise TRTError(rc, lib().trt_last_error(self.h).decode())
+        return rc
+
+    def step(self, dt, cycle="V", l_max=4, eps=1e-8, eps_inner=None, max_outer=100):
+        if eps_inner is None:
+            eps_inner = eps / 10.0 if eps > 0 else -1.0
+        c = trt_cycle(CYCLES[cycle] if isinstance(cycle, str) else int(cycle), int(l_max),
+                      float(eps), float(eps_inner), int(max_outer))
+        st = trt_stats()
+        rc = lib().trt_step(self.h, float(dt), ctypes.byref(c), ctypes.byref(st))
+        self._check(rc, allow=(TRT_ENOTCONVERGED,))
+        return dict(n_ti=st.n_ti, n_c=st.n_c, n_lo=st.n_lo, n_outer=st.n_outer, ms=st.ms,
+                    status=rc)
+
+    def moments(self) -> Dict[str, np.ndarray]:
+        T = np.zeros(self.nx)
+        Eg = np.zeros((self.G, self.nx))
+        Fg = np.zeros((self.G, self.nx + 1))
+        E = np.zeros(self.nx)
+        F = np.zeros(self.nx + 1)
+        self._check(lib().trt_moments(self.h, _np_dp(T), _np_dp(Eg), _np_dp(Fg), _np_dp(E),
+                                      _np_dp(F)))
+        return dict(T=T, Eg=Eg, Fg=Fg, E=E, F=F)
+
+    def intensity(self):
+        """(I [M][nx][2][G], f [G][nx]) as FP64 numpy arrays (group padding dropped)."""
+        I = np.zeros((self.M, self.nx, 2, self.ldG))
+        f = np.zeros((self.G, self.nx))
+        self._check(lib().trt_intensity(self.h, _np_dp(I), _np_dp(f)))
+        return I[..., :self.G].copy(), f
+
+    def set_state(self, T=None, Eg=None, Fg=None, I=None, f=None, fb0=None, fbX=None, C0=None,
+                  CX=None):
+        def c(a):
+            return None if a is None else np.ascontiguousarray(a, np.float64)
+        if I is not None:
+            Ip = np.zeros((self.M, self.nx, 2, self.ldG))
+            Ip[..., :self.G] = I
+            I = Ip
+        arrs = [c(a) for a in (T, Eg, Fg, I, f, fb0, fbX, C0, CX)]
+        self._check(lib().trt_set_state(self.h, *[_np_dp(a) for a in arrs]))
+
+    # ---- kernel-level entry points (torch CUDA tensors in, torch tensors out) ----
+    def _t(self, a, dtype=None):
+        t = self.torch
+        dtype = dtype or t.float64
+        if isinstance(a, np.ndarray):
+            a = t.from_numpy(np.ascontiguousarray(a))
+        return a.to(device=self.device, dtype=dtype).contiguous()
+
+    def k_opacity(self, T):
+        t = self.torch
+        T = self._t(T)
+        out = [t.empty((self.G, self.nx), dtype=t.float64, device=self.device) for _ in range(3)]
+        self._check(lib().trt_k_opacity(self.h, T.data_ptr(), *[o.data_ptr() for o in out]))
+        return tuple(out)
+
+    def k_sweep(self, dt, sigE, emis, I_old):
+        """I_old: [M][nx][2][G] (padded to ldG here); returns I_new [M][nx][2][G], f, fb0,
+        fbX, C0, CX as torch tensors."""
+        t = self.torch
+        rdt = t.float64 if self.precision == TRT_FP64 else t.float32
+        Ip = t.zeros((self.M, self.nx, 2, self.ldG), dtype=rdt, device=self.device)
+        Ip[..., :self.G] = self._t(I_old, rdt)
+        In = t.zeros_like(Ip)
+        f = t.empty((self.G, self.nx), dtype=t.float64, device=self.device)
+        b = [t.empty(self.G, dtype=t.float64, device=self.device) for _ in range(4)]
+        sigE, emis = self._t(sigE), self._t(emis)
+        self._check(lib().trt_k_sweep(self.h, float(dt), sigE.data_ptr(), emis.data_ptr(),
+                                      Ip.data_ptr(), In.data_ptr(), f.data_ptr(),
+                                      *[x.data_ptr() for x in b]))
+        return (In[..., :self.G], f, *b)
+
+    def _level(self, d, n):
+        t = self.torch
+        keep = {}
+        for k in LEVEL_FIELDS:
+            shape = (n, self.nx) if k in CELL_FIELDS else (n, self.nx + 1) if k in FACE_FIELDS else (n,)
+            v = d.get(k)
+            v = t.zeros(shape, dtype=t.float64, device=self.device) if v is None else self._t(v)
+            assert tuple(v.shape) == shape, (k, v.shape, shape)
+            keep[k] = v
+        lv = trt_level(n, *[_ptr(keep[k]) for k in LEVEL_FIELDS])
+        return lv, keep
+
+    def k_lo_solve(self, dt, level):
+        n = int(self._t(level["phi"]).shape[0])
+        lv, keep = self._level(level, n)
+        self._check(lib().trt_k_lo_solve(self.h, float(dt), ctypes.byref(lv)))
+        return {k: keep[k] for k in ("E", "F", "Eb0", "EbX")}
+
+    def k_restrict(self, src, n_to):
+        n = int(self._t(src["phi"]).shape[0])
+        ls, ks = self._level(src, n)
+        ld, kd = self._level({}, n_to)
+        self._check(lib().trt_k_restrict(self.h, ctypes.byref(ls), ctypes.byref(ld)))
+        return kd
+
+    def k_grey_newton(self, dt, Tstar, Told, grey, sig_prev=None, T_prev=None):
+        t = self.torch
+        lv, keep = self._level(grey, 1)
+        Ts, To = self._t(Tstar), self._t(Told)
+        have = sig_prev is not None
+        sp = self._t(sig_prev) if have else None
+        tp = self._t(T_prev) if have else None
+        T = t.empty(self.nx, dtype=t.float64, device=self.device)
+        rc = lib().trt_k_grey_newton(self.h, float(dt), Ts.data_ptr(), To.data_ptr(),
+                                     sp.data_ptr() if have else None,
+                                     tp.data_ptr() if have else None, int(have),
+                                     ctypes.byref(lv), T.data_ptr())
+        self._check(rc, allow=(TRT_ENUMERIC,))
+        return rc, T, {k: keep[k] for k in ("E", "F", "Eb0", "EbX")}
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().trt_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

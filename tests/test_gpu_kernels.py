@@ -1,0 +1,225 @@
+"""Kernel-level parity of the CUDA path against the oracle on seeded inputs.
+
+Each kernel of the hot path (opacity K1, sweep K2, LO solve K3/K4, restriction K4, grey
+Newton K5) is called through the C ABI on the same seeded inputs as the oracle and
+compared element by element.  FP64 tolerance: 1e-10 relative (the parity target of the
+FP64 path); the kernels typically agree to ~1e-14."""
+import numpy as np
+import pytest
+
+from paper_2011_05427_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+C = 299.792458
+TOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def trt():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2011_05427_gb300 import build, trt as _trt
+    build.build()
+    return _trt
+
+
+def solver(trt, nx=12, N=4, G=17, levels=None, precision="fp64", h=None, edges=None, TL=1.0,
+           TR=0.0, s=1.0):
+    edges = W.group_edges(G, 1e-5, 1e2) if edges is None else edges
+    xe = None if h is None else np.concatenate([[0.0], np.cumsum(h)])
+    return trt.Solver(nx, 6.0, N, edges, levels or [G, 1], s, W.CV_FC, 1e-3, TL, TR,
+                      precision=precision, x_edges=xe)
+
+
+def rel(a, b, floor=0.0):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    return np.max(np.abs(a - b) / np.maximum(np.abs(b), floor)) if a.size else 0.0
+
+
+# ---------------------------------------------------------------------------- K1
+@pytest.mark.parametrize("G,nx", [(17, 60), (1024, 37), (3, 1)])
+def test_opacity_parity(trt, orc, G, nx):
+    r = W.rng(1000 + G)
+    T = W.random_temperatures(r, nx, 1e-3, 1.5)
+    T[0] = 1e-3
+    edges = W.group_edges(G, 1e-5, 1e2) if G > 3 else np.array([0.0, 0.5, 2.0, np.inf])
+    s = solver(trt, nx=nx, G=G, edges=edges, levels=[G, 1], s=0.7)
+    sig, em, sR = (x.cpu().numpy() for x in s.k_opacity(T))
+    osig, oem, osR, _ = orc.physics_field(edges, T, 0.7)
+    assert rel(sig, osig) < 1e-12
+    assert rel(sR, osR) < 1e-11
+    big = oem > 1e-280
+    assert rel(em[big], oem[big]) < 1e-12
+    assert np.all(np.abs(em[~big]) < 1e-270)
+
+
+def test_opacity_sampled_full_size(trt, orc):
+    """fc_4096 sizes (1000 cells x 4096 groups), oracle on a sample of cells."""
+    cfg = W.fc_4096()
+    r = W.rng(77)
+    T = W.random_temperatures(r, cfg.n_cells, 1e-3, 1.5)
+    s = solver(trt, nx=cfg.n_cells, G=cfg.G, N=2, levels=[cfg.G, 1])
+    sig, em, sR = (x.cpu().numpy() for x in s.k_opacity(T))
+    for i in r.choice(cfg.n_cells, 6, replace=False):
+        osig, oem, osR, _ = orc.physics_field(cfg.edges(), T[i:i + 1])
+        assert rel(sig[:, i], osig[:, 0]) < 1e-12
+        assert rel(sR[:, i], osR[:, 0]) < 1e-11
+        big = oem[:, 0] > 1e-280
+        assert rel(em[big, i], oem[big, 0]) < 1e-12
+
+
+# ---------------------------------------------------------------------------- K2
+def sweep_inputs(orc, seed, nx, N, G, thick=False):
+    r = W.rng(seed)
+    h = W.random_h(r, nx)
+    sig = np.exp(r.uniform(-4, 12 if thick else 4, (G, nx)))
+    em = np.exp(r.uniform(-6, 2, (G, nx)))
+    I_old = W.random_intensity(r, 2 * N, nx, G)
+    TL = 0.9
+    return r, h, sig, em, I_old, TL
+
+
+@pytest.mark.parametrize("nx,N,G", [(1, 1, 1), (7, 2, 17), (60, 8, 17), (100, 4, 70),
+                                    (33, 16, 32), (65, 3, 40)])
+def test_sweep_parity(trt, orc, nx, N, G):
+    r, h, sig, em, I_old, TL = sweep_inputs(orc, 2000 + nx + N + G, nx, N, G, thick=True)
+    edges = W.group_edges(G, 1e-5, 1e2) if G >= 3 else np.array([0.0, np.inf])
+    s = solver(trt, nx=nx, N=N, G=G, h=h, edges=edges, TL=TL, TR=0.3)
+    dt = 1.7e-3
+    In, f, fb0, fbX, C0, CX = (x.cpu().numpy() for x in s.k_sweep(dt, sig, em, I_old))
+    mu, w = orc.double_gl(N)
+    Iin0 = orc.group_physics(edges, TL)[0]
+    IinX = orc.group_physics(edges, 0.3)[0]
+    oI, of, ofb0, ofbX, oC0, oCX = orc.sweep(h, mu, w, sig, em, 1.0 / (C * dt), I_old, Iin0, IinX)
+    assert rel(In, oI) < 1e-12
+    assert rel(f, of) < 1e-12
+    for a, b in ((fb0, ofb0), (fbX, ofbX), (C0, oC0), (CX, oCX)):
+        assert rel(a, b) < 1e-12
+
+
+def test_sweep_sampled_full_size(trt, orc):
+    """fc_1024 sizes (500 cells, 64 directions, 1024 groups): the oracle sweeps a sample
+    of groups with the same inputs."""
+    cfg = W.fc_1024()
+    nx, N, G = cfg.n_cells, cfg.N, cfg.G
+    r = W.rng(31)
+    h = cfg.h()
+    sig = np.exp(r.uniform(-4, 10, (G, nx)))
+    em = np.exp(r.uniform(-6, 2, (G, nx)))
+    I_old = W.random_intensity(r, 2 * N, nx, G)
+    s = solver(trt, nx=nx, N=N, G=G, levels=cfg.levels)
+    dt = cfg.dt
+    In, f, fb0, fbX, C0, CX = (x.cpu().numpy() for x in s.k_sweep(dt, sig, em, I_old))
+    mu, w = orc.double_gl(N)
+    edges = cfg.edges()
+    Iin0 = orc.group_physics(edges, 1.0)[0]
+    gs = np.sort(r.choice(G, 12, replace=False))
+    oI, of, ofb0, ofbX, oC0, oCX = orc.sweep(h, mu, w, np.ascontiguousarray(sig[gs]),
+                                            np.ascontiguousarray(em[gs]), 1.0 / (C * dt),
+                                            np.ascontiguousarray(I_old[..., gs]), Iin0[gs],
+                                            np.zeros(gs.size))
+    assert rel(In[..., gs], oI) < 1e-12
+    assert rel(f[gs], of) < 1e-12
+    assert rel(C0[gs], oC0) < 1e-12 and rel(fbX[gs], ofbX) < 1e-12
+
+
+# ---------------------------------------------------------------------------- K3 / K4
+def random_level(r, ng, nx, eta=True):
+    z = lambda shape: r.uniform(0, 0.2, shape) * (r.uniform(size=shape) < 0.5)
+    return dict(
+        phi=r.uniform(0.2, 0.9, (ng, nx)), sig=np.exp(r.uniform(-3, 3, (ng, nx))),
+        emis=np.exp(r.uniform(-3, 1, (ng, nx))), Eold=np.exp(r.uniform(-3, 0, (ng, nx))),
+        sigR=np.exp(r.uniform(-3, 3, (ng, nx + 1))),
+        etaR=z((ng, nx + 1)) if eta else np.zeros((ng, nx + 1)),
+        etaL=z((ng, nx + 1)) if eta else np.zeros((ng, nx + 1)),
+        Fold=r.normal(0, 1, (ng, nx + 1)),
+        phib0=r.uniform(0.3, 0.8, ng), phibX=r.uniform(0.3, 0.8, ng),
+        C0=-r.uniform(0.2, 0.8, ng), CX=r.uniform(0.2, 0.8, ng),
+        Ein0=r.uniform(0, 1, ng), Fin0=r.uniform(0, 3, ng),
+        EinX=r.uniform(0, 0.1, ng), FinX=-r.uniform(0, 0.3, ng))
+
+
+def oracle_level_solve(orc, h, dt, lv):
+    ng, nx = lv["phi"].shape
+    out = dict(E=np.zeros((ng, nx)), F=np.zeros((ng, nx + 1)), Eb0=np.zeros(ng), EbX=np.zeros(ng))
+    for q in range(ng):
+        E, F, a, b = orc.lo_solve(h, dt, C * lv["sig"][q], 2 * lv["emis"][q], lv["Eold"][q],
+                                  lv["phi"][q], lv["sigR"][q], lv["etaR"][q], lv["etaL"][q],
+                                  lv["Fold"][q], lv["phib0"][q], lv["phibX"][q], lv["C0"][q],
+                                  lv["CX"][q], lv["Ein0"][q], lv["Fin0"][q], lv["EinX"][q],
+                                  lv["FinX"][q])
+        out["E"][q], out["F"][q], out["Eb0"][q], out["EbX"][q] = E, F, a, b
+    return out
+
+
+@pytest.mark.parametrize("nx,ng", [(1, 3), (2, 5), (3, 4), (5, 9), (64, 7), (65, 33), (500, 40),
+                                   (1000, 3), (2048, 2)])
+def test_lo_solve_parity(trt, orc, nx, ng):
+    r = W.rng(3000 + nx + ng)
+    h = W.random_h(r, nx)
+    lv = random_level(r, ng, nx)
+    dt = 2e-3
+    s = solver(trt, nx=nx, N=2, G=17, h=h)
+    got = {k: v.cpu().numpy() for k, v in s.k_lo_solve(dt, lv).items()}
+    ref = oracle_level_solve(orc, h, dt, lv)
+    assert rel(got["E"], ref["E"]) < 1e-11
+    Fs = np.abs(ref["F"]).max(1, keepdims=True)
+    assert np.max(np.abs(got["F"] - ref["F"]) / Fs) < 1e-11
+    assert rel(got["Eb0"], ref["Eb0"]) < 1e-10
+    assert np.max(np.abs(got["EbX"] - ref["EbX"]) / (np.abs(ref["EbX"]) + ref["E"][:, -1])) < 1e-10
+
+
+@pytest.mark.parametrize("n_from,n_to,eta", [(16, 4, False), (12, 1, True), (1024, 256, False),
+                                             (64, 1, True), (4, 4, True)])
+def test_restrict_parity(trt, orc, n_from, n_to, eta):
+    r = W.rng(4000 + n_from + n_to)
+    nx = 37
+    h = W.random_h(r, nx)
+    lv = random_level(r, n_from, nx, eta=eta)
+    sol = oracle_level_solve(orc, h, 2e-3, lv)
+    s = solver(trt, nx=nx, N=2, G=17, h=h)
+    src = dict(lv)
+    src.update(sol)
+    got = {k: v.cpu().numpy() for k, v in s.k_restrict(src, n_to).items()}
+    cmap = np.arange(n_from) // (n_from // n_to)
+    ref, Esum = orc.restrict(h, lv, sol, cmap, n_to)
+    for k in orc.LEVEL_KEYS:
+        if k in ("etaR", "etaL"):
+            scale = np.max(np.abs(ref[k])) + 1e-300
+            assert np.max(np.abs(got[k] - ref[k])) <= 1e-10 * scale, k
+        elif k == "Fold":
+            assert np.max(np.abs(got[k] - ref[k])) <= 1e-12 * np.abs(ref[k]).max(), k
+        else:
+            assert rel(got[k], ref[k]) < 1e-12, k
+    assert rel(got["Esum"], Esum) < 1e-13
+
+
+@pytest.mark.parametrize("nx,have_prev", [(1, 0), (30, 1), (500, 0), (1000, 1)])
+def test_grey_newton_parity(trt, orc, nx, have_prev):
+    r = W.rng(5000 + nx)
+    h = W.random_h(r, nx)
+    lv = random_level(r, 1, nx)
+    lv["Esum"] = r.uniform(0.1, 1, (1, nx))
+    dt = 2e-3
+    s = solver(trt, nx=nx, N=2, G=17, h=h)
+    Ts = np.exp(r.uniform(np.log(0.01), 0.0, nx))
+    To = Ts * r.uniform(0.8, 1.0, nx)
+    sp = lv["sig"][0] * r.uniform(0.5, 1.5, nx)
+    tp = Ts * r.uniform(0.7, 1.3, nx)
+    rc, T, sol = s.k_grey_newton(dt, Ts, To, lv, sp if have_prev else None,
+                                 tp if have_prev else None)
+    edges = W.group_edges(17, 1e-5, 1e2)
+    Q = 2 * lv["emis"][0]
+    dQ = np.array([orc.emission_deriv(edges, t) for t in Ts])
+    bad, oT, oE, oF, oEb0, oEbX = orc.grey_newton(
+        h, dt, W.CV_FC, Ts, To, Q, dQ, lv["Esum"][0], lv["sig"][0], sp, tp, have_prev,
+        lv["Eold"][0], lv["phi"][0], lv["sigR"][0], lv["etaR"][0], lv["etaL"][0], lv["Fold"][0],
+        lv["phib0"][0], lv["phibX"][0], lv["C0"][0], lv["CX"][0], lv["Ein0"][0], lv["Fin0"][0],
+        lv["EinX"][0], lv["FinX"][0])
+    assert (rc != 0) == (bad != 0)
+    if not bad:
+        assert rel(T.cpu().numpy(), oT) < 1e-11
+        assert rel(sol["E"].cpu().numpy()[0], oE) < 1e-11

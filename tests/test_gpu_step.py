@@ -1,0 +1,160 @@
+"""Whole-step parity of the CUDA path (trt_step through the C ABI) against the oracle's
+Algorithm 3, plus properties that hold at any size (equilibrium, conservation)."""
+import numpy as np
+import pytest
+
+from paper_2011_05427_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def trt():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2011_05427_gb300 import build, trt as _trt
+    build.build()
+    return _trt
+
+
+def pair(trt, orc, cfg, precision="fp64"):
+    s = trt.Solver.from_slab(cfg, precision=precision)
+    o = orc.Problem(cfg.h(), cfg.N, cfg.edges(), cfg.levels, cfg.opac_scale, cfg.cv, cfg.T0,
+                    cfg.T_left, cfg.T_right)
+    return s, o
+
+
+def errors(g, r):
+    """relative T error; energy-weighted E_g error; pure relative E_g error on groups
+    holding more than 1e-20 of the cell energy."""
+    eT = np.max(np.abs(g["T"] - r["T"]) / r["T"])
+    Ecell = r["Eg"].sum(0)[None, :]
+    eE = np.max(np.abs(g["Eg"] - r["Eg"]) / Ecell)
+    sel = r["Eg"] > 1e-20 * Ecell
+    eEp = np.max(np.abs(g["Eg"] - r["Eg"])[sel] / r["Eg"][sel])
+    return eT, eE, eEp
+
+
+CASES = [
+    ("fc_small", W.fc_small(), "V", 2),
+    ("w_small", W.scaled(W.fc_small(), 20, 4, 64, levels=[64, 16, 4, 1]), "W", 2),
+    ("f_small", W.scaled(W.fc_small(), 33, 2, 64, levels=[64, 16, 4, 1]), "F", 2),
+    ("v_ragged", W.scaled(W.fc_small(), 70, 3, 40, levels=[40, 10, 1]), "V", 3),
+]
+
+
+@pytest.mark.parametrize("name,cfg,cycle,lmax", CASES, ids=[c[0] for c in CASES])
+def test_fixed_iteration_steps_fp64(trt, orc, name, cfg, cycle, lmax):
+    """Exactly 3 low-order phases (2 sweeps) of l_max cycles per step, 3 steps."""
+    s, o = pair(trt, orc, cfg)
+    for step in range(3):
+        st = s.step(cfg.dt, cycle, lmax, -1.0, max_outer=3)
+        so, c = o.step(cfg.dt, cycle, lmax, -1.0, max_outer=3)
+        assert st["status"] == 0 and so == 0
+        assert (st["n_ti"], st["n_c"], st["n_lo"]) == (c["n_ti"], c["n_c"], c["n_lo"])
+        g, r = s.moments(), o.state()
+        eT, eE, eEp = errors(g, r)
+        assert eT < 1e-10 and eE < 1e-10 and eEp < 1e-9, (step, eT, eE, eEp)
+    I, f = s.intensity()
+    r = o.state()
+    scale = r["I"].max(axis=(0, 1, 2), keepdims=True)
+    assert np.max(np.abs(I - r["I"]) / scale) < 1e-10
+    assert np.max(np.abs(f - r["f"])) < 1e-10
+
+
+def test_converged_steps_fc_small(trt, orc):
+    """fc_small, eps = 1e-8, 10 steps of the two-grid method: same iteration counts and the
+    same state to 1e-10."""
+    cfg = W.fc_small()
+    s, o = pair(trt, orc, cfg)
+    for step in range(cfg.steps):
+        st = s.step(cfg.dt, "V", cfg.l_max, cfg.eps)
+        so, c = o.step(cfg.dt, "V", cfg.l_max, cfg.eps)
+        assert st["status"] == 0 and so == 0
+        assert (st["n_ti"], st["n_c"], st["n_lo"]) == (c["n_ti"], c["n_c"], c["n_lo"])
+        eT, eE, eEp = errors(s.moments(), o.state())
+        assert eT < 1e-10 and eE < 1e-10, (step, eT, eE)
+
+
+def test_uniform_equilibrium_gpu(trt):
+    cfg = W.scaled(W.fc_small(), 16, 4, 64, levels=[64, 16, 4, 1])
+    cfg.T0 = cfg.T_left = cfg.T_right = 0.25
+    s = trt.Solver.from_slab(cfg)
+    m0 = s.moments()
+    for cyc in ("V", "W", "F"):
+        st = s.step(cfg.dt, cyc, 2, 1e-8)
+        m = s.moments()
+        assert st["n_ti"] == 0
+        assert np.allclose(m["T"], 0.25, rtol=1e-13)
+        assert np.allclose(m["Eg"], m0["Eg"], rtol=1e-12, atol=1e-14 * m0["Eg"].max())
+
+
+def test_conservation_gpu(trt):
+    """sum dx [(E - E_old) + cv (T - T_old)] = dt (F(0) - F(X)) for the grey solve."""
+    cfg = W.scaled(W.fc_small(), 40, 4, 64, levels=[64, 16, 4, 1])
+    s = trt.Solver.from_slab(cfg)
+    h = cfg.h()
+    for cyc in ("V", "W", "F", "W"):
+        before = s.moments()
+        s.step(cfg.dt, cyc, 2, 1e-8)
+        m = s.moments()
+        lhs = (h * (m["E"] - before["Eg"].sum(0))).sum() + (h * cfg.cv * (m["T"] - before["T"])).sum()
+        assert lhs == pytest.approx(cfg.dt * (m["F"][0] - m["F"][-1]), rel=1e-11)
+
+
+def test_fc_1024_full_size_step(trt, orc):
+    """fc_1024 at full size (500 cells, 64 directions, 1024 groups, 5 grids, W cycle):
+    one fixed-iteration step (2 phases, 1 sweep, 1 cycle each) against the oracle."""
+    cfg = W.fc_1024("W")
+    s, o = pair(trt, orc, cfg)
+    st = s.step(cfg.dt, "W", 1, -1.0, max_outer=2)
+    so, c = o.step(cfg.dt, "W", 1, -1.0, max_outer=2)
+    assert st["status"] == 0 and so == 0
+    assert (st["n_ti"], st["n_c"], st["n_lo"]) == (c["n_ti"], c["n_c"], c["n_lo"])
+    eT, eE, eEp = errors(s.moments(), o.state())
+    assert eT < 1e-10 and eE < 1e-10, (eT, eE)
+
+
+def test_edge_cases(trt, orc):
+    """one cell; one group on [0, inf) with grids {1, 1}; one direction per half range."""
+    for cfg in (W.scaled(W.fc_small(), 1, 4, 17, levels=[17, 1]),
+                W.scaled(W.fc_small(), 9, 1, 17, levels=[17, 1])):
+        s, o = pair(trt, orc, cfg)
+        for _ in range(2):
+            s.step(cfg.dt, "V", 2, -1.0, max_outer=3)
+            o.step(cfg.dt, "V", 2, -1.0, max_outer=3)
+        eT, eE, _ = errors(s.moments(), o.state())
+        assert eT < 1e-10 and eE < 1e-10
+    import dataclasses
+    cfg = dataclasses.replace(W.scaled(W.fc_small(), 12, 4, 1, levels=[1, 1]), T0=0.3)
+    s = trt.Solver(cfg.n_cells, 6.0, cfg.N, np.array([0.0, np.inf]), [1, 1], 1.0, cfg.cv, 0.3,
+                   1.0, 0.0)
+    from oracle import orc as _o
+    o = _o.Problem(cfg.h(), cfg.N, np.array([0.0, np.inf]), [1, 1], 1.0, cfg.cv, 0.3, 1.0, 0.0)
+    for _ in range(2):
+        s.step(cfg.dt, "V", 2, -1.0, max_outer=3)
+        o.step(cfg.dt, "V", 2, -1.0, max_outer=3)
+    eT, eE, _ = errors(s.moments(), o.state())
+    assert eT < 1e-10 and eE < 1e-10
+
+
+MIXED_CASES = [
+    ("fc_small", W.fc_small(), "V", 2),
+    ("w_small", W.scaled(W.fc_small(), 60, 8, 64, levels=[64, 16, 4, 1]), "W", 2),
+]
+
+
+@pytest.mark.parametrize("name,cfg,cycle,lmax", MIXED_CASES, ids=[c[0] for c in MIXED_CASES])
+def test_mixed_precision_vs_fp64_oracle(trt, orc, name, cfg, cycle, lmax):
+    """FP32 sweeps and group LOQD, FP64 grey + MEB: error against the FP64 oracle after
+    fixed-iteration steps."""
+    s, o = pair(trt, orc, cfg, precision="mixed")
+    worst = (0.0, 0.0)
+    for step in range(3):
+        s.step(cfg.dt, cycle, lmax, -1.0, max_outer=3)
+        o.step(cfg.dt, cycle, lmax, -1.0, max_outer=3)
+        eT, eE, _ = errors(s.moments(), o.state())
+        worst = (max(worst[0], eT), max(worst[1], eE))
+    print(f"{name}: mixed vs FP64 oracle: T {worst[0]:.2e}, E_g (energy-weighted) {worst[1]:.2e}")
+    assert worst[0] < 1e-6 and worst[1] < 1e-6
