@@ -29,7 +29,7 @@
  *       cell arrays     [G][nx]            group-major, cell fastest
  *       face arrays     [G][nx+1]          face f at x_{f-1/2}: f = 0 is x = 0, f = nx is X
  *       intensity       [M][nx][2][ldG]    direction, cell, corner (0 left, 1 right), group
- *                                          (ldG = trt_ld_groups(h) >= G, padding is zero)
+ *                                          (ldG from trt_dims, >= G, padding zero)
  *       directions      m < N: mu_m > 0 ascending; m >= N: mu_m = -mu_{m-N}  (M = 2N)
  */
 #ifndef TRT_H
@@ -116,11 +116,13 @@ typedef struct {
 } trt_cycle;
 
 /* Per-step counters (Sec. 6): sweeps, cycles, group-wise low-order solves (grey solves
- * count one each), low-order phases; wall time of the step on the host clock. */
+ * count one each), low-order phases; wall time of the step on the host clock; number of
+ * the library's kernel launches in the step. */
 typedef struct {
     int n_ti, n_c, n_lo, n_outer;
     double ms;
     int status;
+    int n_kernels;
 } trt_stats;
 
 typedef struct trt_handle trt_handle;

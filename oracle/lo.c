@@ -246,8 +246,12 @@ void orc_restrict(int nx, const double *h, int n_from, int n_to, const int *map,
  * Substituting T into the grey balance gives an absorption term linear in E:
  *   R = w (c sig* E - Q*) + (1 - w) cv (T* - Told)/dt,   w = (cv/dt)/Lambda,
  * and cv (T - Told)/dt = R holds identically, so each grey solve conserves energy.
- * Readings: D = 0 on the first grey solve of a time step or when |T* - T_prev| <=
- * 1e-12 T*.  Returns nonzero if a temperature comes out non-positive or non-finite. */
+ * Readings: D = 0 on the first grey solve of a time step, and D = 0 unless
+ * |T* - T_prev| > 1e-7 T*: the secant quotient carries a relative rounding error of about
+ * eps T / |T* - T_prev|, and in a W or F cycle successive grey solves are built on
+ * different grids, so sigma-bar jumps while T barely moves; below 1e-7 the quotient would
+ * be rounding noise amplified by up to 1e4 and more.  Returns nonzero if a temperature
+ * comes out non-positive or non-finite. */
 int orc_grey_newton(int nx, const double *h, double dt, double cv,
                     const double *Tstar, const double *Told, const double *Q,
                     const double *dQ, const double *Estar,
@@ -265,7 +269,7 @@ int orc_grey_newton(int nx, const double *h, double dt, double cv,
     double *Lam = (double *)malloc(sizeof(double) * nx);
     for (int i = 0; i < nx; ++i) {
         double D = 0.0;
-        if (have_prev && fabs(Tstar[i] - T_prev[i]) > 1e-12 * Tstar[i])
+        if (have_prev && fabs(Tstar[i] - T_prev[i]) > 1e-7 * Tstar[i])
             D = (sig[i] - sig_prev[i]) / (Tstar[i] - T_prev[i]);
         double base = cv / dt + dQ[i];
         double L = base - c * D * Estar[i];

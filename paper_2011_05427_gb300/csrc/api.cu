@@ -39,8 +39,8 @@ struct trt_handle {
     double *E1, *F1, *Eb0_1, *EbX_1;
     Level crs, grey;
     double *Ecyc, *Ephase;
-    double *flags;
-    double *hflags;
+    double *flags = nullptr;
+    double *hflags = nullptr;   // pinned host buffer, owned (freed in the destructor)
     std::string err;
     ~trt_handle()
     {
@@ -263,7 +263,7 @@ extern "C" {
 size_t trt_workspace_bytes(const trt_grid *grid, const trt_angles *angles,
                            const trt_groups *groups, const trt_options *opt)
 {
-    trt_handle tmp;
+    trt_handle tmp{};
     std::vector<double> xe, ed;
     std::string err;
     if (!validate(grid, angles, groups, opt, tmp.p, xe, ed, err)) return 0;
@@ -277,6 +277,7 @@ int trt_create(const trt_grid *grid, const trt_angles *angles, const trt_groups 
 {
     if (!out) return fail(nullptr, TRT_EINVAL, "out is null");
     *out = nullptr;
+    (void)cudaGetLastError();   // an error left by another library is not ours to report
     trt_handle *h = nullptr;   // errors during creation go to the global message (CK)
     std::unique_ptr<trt_handle> hp(new trt_handle());
     std::vector<double> xe, edges;
@@ -421,6 +422,7 @@ int trt_step(trt_handle *h, double dt, const trt_cycle *cyc, trt_stats *stats)
         cyc->type > 2)
         return fail(h, TRT_EINVAL, "bad step arguments");
     auto t_start = std::chrono::steady_clock::now();
+    (void)cudaGetLastError();
     Problem &p = h->p;
     const int nx = p.nx, G = p.G;
     std::vector<int> S;
@@ -428,7 +430,7 @@ int trt_step(trt_handle *h, double dt, const trt_cycle *cyc, trt_stats *stats)
     const int K = (int)S.size();
     const bool fixed = cyc->eps < 0;
     const double eps = cyc->eps, eps_in = cyc->eps_inner;
-    int n_ti = 0, n_c = 0, n_lo = 0, s = 0, status = TRT_OK;
+    int n_ti = 0, n_c = 0, n_lo = 0, s = 0, status = TRT_OK, nk = 0;
     bool swept = false, opac_valid = false;
     int have_prev = 0;
 
@@ -436,15 +438,20 @@ int trt_step(trt_handle *h, double dt, const trt_cycle *cyc, trt_stats *stats)
     CK(d2d(h, h->Eg_old, h->Eg, (size_t)G * nx));
     CK(d2d(h, h->Fg_old, h->Fg, (size_t)G * (nx + 1)));
     CK(launch_group_sum(p, G, h->Eg_old, h->Ephase));
+    ++nk;
     CK(cudaMemsetAsync(h->flags, 0, 8 * sizeof(double), p.stream));
     Level fine = fine_level(h);
 
     for (;;) {
         if (s > 0) {
-            if (!opac_valid) CK(launch_opacity(p, h->T, h->sigE, h->emis, h->sigR));
+            if (!opac_valid) {
+                CK(launch_opacity(p, h->T, h->sigE, h->emis, h->sigR));
+                ++nk;
+            }
             opac_valid = true;
             CK(launch_sweep(p, dt, h->sigE, h->emis, h->I_cur, h->I_alt, h->part, h->psi_exit,
                             h->f, h->fb0, h->fbX, h->C0, h->CX));
+            nk += 2;
             ++n_ti;
             swept = true;
         }
@@ -453,9 +460,13 @@ int trt_step(trt_handle *h, double dt, const trt_cycle *cyc, trt_stats *stats)
         CK(d2d(h, h->Ecyc, h->Ephase, nx));
         bool conv_out = false;
         for (int l = 0; l < cyc->l_max; ++l) {
-            if (!opac_valid) CK(launch_opacity(p, h->T, h->sigE, h->emis, h->sigR));
+            if (!opac_valid) {
+                CK(launch_opacity(p, h->T, h->sigE, h->emis, h->sigR));
+                ++nk;
+            }
             opac_valid = true;
             CK(launch_lo_solve(p, dt, fine));
+            ++nk;
             n_lo += G;
             CK(d2d(h, h->Ttil, h->T, nx));
             for (int k = 0; k <= K; ++k) {
@@ -467,6 +478,7 @@ int trt_step(trt_handle *h, double dt, const trt_cycle *cyc, trt_stats *stats)
                     h->crs.n = ng;
                     CK(launch_restrict(p, fine, h->crs));
                     CK(launch_lo_solve(p, dt, h->crs));
+                    nk += 3;
                     n_lo += ng;
                     src = &h->crs;
                 }
@@ -481,6 +493,7 @@ int trt_step(trt_handle *h, double dt, const trt_cycle *cyc, trt_stats *stats)
                 a.Tcyc = h->Tcyc; a.Ecyc = h->Ecyc; a.Tphase = h->Tphase; a.Ephase = h->Ephase;
                 a.flags = h->flags;
                 CK(launch_grey(p, h->grey, a));
+                nk += 2;   // restriction to grey + grey Newton
                 n_lo += 1;
                 have_prev = 1;
                 std::swap(h->Ttil, h->Tnew);
@@ -523,6 +536,7 @@ done:
         stats->n_ti = n_ti; stats->n_c = n_c; stats->n_lo = n_lo; stats->n_outer = s;
         stats->ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
         stats->status = status;
+        stats->n_kernels = nk;
     }
     return status;
 }

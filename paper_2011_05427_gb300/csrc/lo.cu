@@ -499,7 +499,8 @@ __global__ void __launch_bounds__(1024) k_grey(GreyCtx x)
         double D = 0.0;
         if (a.have_prev) {
             const double Tp = a.T_prev[i];
-            if (fabs(Ts - Tp) > 1e-12 * Ts) D = (sig - a.sig_prev[i]) / (Ts - Tp);
+            // secant only where |dT| is far above rounding (relative noise ~ eps T/|dT|)
+            if (fabs(Ts - Tp) > 1e-7 * Ts) D = (sig - a.sig_prev[i]) / (Ts - Tp);
         }
         const double base = cvdt + dQ;
         double L = base - kC * D * g.Esum[i];

@@ -56,7 +56,8 @@ class trt_cycle(ctypes.Structure):
 
 class trt_stats(ctypes.Structure):
     _fields_ = [("n_ti", ctypes.c_int), ("n_c", ctypes.c_int), ("n_lo", ctypes.c_int),
-                ("n_outer", ctypes.c_int), ("ms", ctypes.c_double), ("status", ctypes.c_int)]
+                ("n_outer", ctypes.c_int), ("ms", ctypes.c_double), ("status", ctypes.c_int),
+                ("n_kernels", ctypes.c_int)]
 
 
 LEVEL_FIELDS = ("phi", "sig", "emis", "Eold", "Esum", "sigR", "etaR", "etaL", "Fold",
@@ -147,7 +148,10 @@ class Solver:
                  device=None, stream=None, x_edges=None):
         import torch
         self.torch = torch
-        self.device = torch.device(device) if device is not None else torch.device("cuda")
+        dev = torch.device(device) if device is not None else torch.device("cuda")
+        if dev.index is None:   # always pass an explicit index to the CUDA runtime
+            dev = torch.device("cuda", torch.cuda.current_device())
+        self.device = dev
         L = lib()
         self._edges = np.ascontiguousarray(edges, np.float64)
         self._levels = np.ascontiguousarray(level_groups, np.int32)
@@ -160,25 +164,25 @@ class Solver:
                                  self._levels.ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
         self.opacity = trt_opacity(float(opac_scale))
         self.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
-        with torch.cuda.device(self.device):
-            self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
-            opt = trt_options(self.precision, float(T0), ctypes.c_void_p(self.stream.cuda_stream),
-                              None, 0)
-            nbytes = L.trt_workspace_bytes(ctypes.byref(self.grid), ctypes.byref(self.angles),
-                                           ctypes.byref(self.groups), ctypes.byref(opt))
-            if nbytes == 0:
-                raise TRTError(TRT_EINVAL, "invalid problem (trt_workspace_bytes returned 0)")
-            self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
-            base = self.workspace.data_ptr()
-            aligned = (base + 255) // 256 * 256
-            opt.workspace = ctypes.c_void_p(aligned)
-            opt.workspace_bytes = nbytes
-            h = ctypes.c_void_p()
-            rc = L.trt_create(ctypes.byref(self.grid), ctypes.byref(self.angles),
-                              ctypes.byref(self.groups), ctypes.byref(self.opacity), float(cv),
-                              ctypes.byref(opt), ctypes.byref(h))
-            if rc != TRT_OK:
-                raise TRTError(rc, L.trt_last_error(None).decode())
+        torch.cuda.synchronize(self.device)   # initialise torch's context on the device
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        opt = trt_options(self.precision, float(T0), ctypes.c_void_p(self.stream.cuda_stream),
+                          None, 0)
+        nbytes = L.trt_workspace_bytes(ctypes.byref(self.grid), ctypes.byref(self.angles),
+                                       ctypes.byref(self.groups), ctypes.byref(opt))
+        if nbytes == 0:
+            raise TRTError(TRT_EINVAL, "invalid problem (trt_workspace_bytes returned 0)")
+        self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+        base = self.workspace.data_ptr()
+        aligned = (base + 255) // 256 * 256
+        opt.workspace = ctypes.c_void_p(aligned)
+        opt.workspace_bytes = nbytes
+        h = ctypes.c_void_p()
+        rc = L.trt_create(ctypes.byref(self.grid), ctypes.byref(self.angles),
+                          ctypes.byref(self.groups), ctypes.byref(self.opacity), float(cv),
+                          ctypes.byref(opt), ctypes.byref(h))
+        if rc != TRT_OK:
+            raise TRTError(rc, L.trt_last_error(None).decode())
         self.h = h
         self.workspace_bytes = nbytes
         dims = [ctypes.c_int() for _ in range(7)]
@@ -205,7 +209,7 @@ class Solver:
         rc = lib().trt_step(self.h, float(dt), ctypes.byref(c), ctypes.byref(st))
         self._check(rc, allow=(TRT_ENOTCONVERGED,))
         return dict(n_ti=st.n_ti, n_c=st.n_c, n_lo=st.n_lo, n_outer=st.n_outer, ms=st.ms,
-                    status=rc)
+                    status=rc, n_kernels=st.n_kernels)
 
     def moments(self) -> Dict[str, np.ndarray]:
         T = np.zeros(self.nx)
