@@ -186,7 +186,11 @@ int trt_k_sweep(trt_handle *h, double dt, const double *sigE, const double *emis
                 const void *I_old, void *I_new, double *f, double *fb0, double *fbX,
                 double *C0, double *CX);
 
-/* One frequency-grid level of the low-order system, device arrays (FP64):
+/* One frequency-grid level of the low-order system, device arrays (FP64).
+ * fine = 0: a coarse or grey level with the arrays below.
+ * fine = 1: the fine grid in its raw form: phi = f_g, sig = sigma_E, emis = e_g, and sigR is
+ *           the CELL Rosseland opacity [n][nx] (faces take the dx-weighted mean of their two
+ *           cells, boundary half faces the cell value); etaR / etaL are ignored (zero). 
  *   cell [n][nx]: phi (f or f-bar), sig (sigma_E or its average), emis (sum of
  *                 sigma_B B over the group), Eold (E at t^{j-1}), Esum (restriction output)
  *   face [n][nx+1]: sigR, etaR (eta-hat on E right of the face), etaL (eta-check on E left
@@ -196,6 +200,7 @@ int trt_k_sweep(trt_handle *h, double dt, const double *sigE, const double *emis
  *   solution: E [n][nx], F [n][nx+1], Eb0, EbX [n] (boundary-face energies). */
 typedef struct {
     int n;
+    int fine;
     double *phi, *sig, *emis, *Eold, *Esum;
     double *sigR, *etaR, *etaL, *Fold;
     double *phib0, *phibX, *C0, *CX, *Ein0, *Fin0, *EinX, *FinX;

@@ -165,7 +165,13 @@ static double wmean(int n_from, const int *map, int P, const double *v, size_t s
  * equations are exactly the sum of the finer ones at the finer solution; at the
  * boundary half faces the face energies of the finer solution are used; C-bar is
  * weighted by the outgoing boundary energies E_face - Ein, which makes the summed
- * boundary condition exact; Ein, Fin, Eold, Fold are sums. */
+ * boundary condition exact; Ein, Fin, Eold, Fold are sums.  The |F| weight of sigR_P is
+ * |F_p| + 1e-6 c (E_p,left + E_p,right)/2: in a group near local equilibrium F_p is a
+ * difference of nearly equal terms and carries only rounding noise, which the pure |F|
+ * weight would turn into an arbitrary mean; the floor makes the mean well defined and
+ * leaves it unchanged wherever the flux is physical.  Any sigR_P keeps the coarse
+ * equations exact restrictions (xi compensates), so the converged state does not
+ * depend on this choice. */
 void orc_restrict(int nx, const double *h, int n_from, int n_to, const int *map,
                   const double *phi, const double *sig, const double *emis, const double *Eold,
                   const double *sigR, const double *etaR, const double *etaL, const double *Fold,
@@ -200,7 +206,20 @@ void orc_restrict(int nx, const double *h, int n_from, int n_to, const int *map,
             size_t cf = (size_t)P * nf + f;
             double dxf = (f == 0) ? 0.5 * h[0] : (f == nx) ? 0.5 * h[nx - 1]
                                                : 0.5 * (h[f - 1] + h[f]);
-            double sR = wmean(n_from, map, P, sigR + f, nf, F + f, nf, 1);
+            double num = 0.0, den = 0.0, sum = 0.0;
+            int cnt = 0;
+            for (int p = 0; p < n_from; ++p) {
+                if (map[p] != P) continue;
+                size_t pf = (size_t)p * nf + f;
+                double ER = (f == nx) ? EbX[p] : E[(size_t)p * nx + f];
+                double EL = (f == 0) ? Eb0[p] : E[(size_t)p * nx + f - 1];
+                double wgt = fabs(F[pf]) + 1e-6 * c * 0.5 * (EL + ER);
+                num += sigR[pf] * wgt;
+                den += wgt;
+                sum += sigR[pf];
+                ++cnt;
+            }
+            double sR = (den != 0.0) ? num / den : sum / cnt;
             double xi = 0.0, sER = 0.0, sEL = 0.0, sFo = 0.0;
             for (int p = 0; p < n_from; ++p) {
                 if (map[p] != P) continue;

@@ -228,7 +228,7 @@ Level from_abi(const trt_level *l)
 {
     Level L;
     L.n = l->n;
-    L.fine = 0;
+    L.fine = l->fine ? 1 : 0;
     L.phi = l->phi; L.sig = l->sig; L.emis = l->emis; L.Eold = l->Eold; L.Esum = l->Esum;
     L.sigR = l->sigR; L.etaR = l->etaR; L.etaL = l->etaL; L.Fold = l->Fold;
     L.phib0 = l->phib0; L.phibX = l->phibX; L.C0 = l->C0; L.CX = l->CX;

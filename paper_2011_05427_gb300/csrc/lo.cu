@@ -340,8 +340,12 @@ __global__ void k_restrict(RestrictCtx x)
             } else {
                 sR = S.sigR[(size_t)p * nf + i];
             }
-            double aF = fabs(Fp);
-            v[7] += sR * aF; v[8] += sR; v[9] += aF;
+            // |F| weight with a floor 1e-6 c E-bar: groups in local equilibrium carry
+            // rounding-noise fluxes that must not decide the mean
+            double ER = (i == nx) ? S.EbX[p] : S.E[(size_t)p * nx + i];
+            double EL = (i == 0) ? S.Eb0[p] : S.E[(size_t)p * nx + i - 1];
+            double wF = fabs(Fp) + 1e-6 * kC * 0.5 * (EL + ER);
+            v[7] += sR * wF; v[8] += sR; v[9] += wF;
         }
         if (i == 0 || i == nx) {
             const int side = (i == 0) ? 0 : 1;

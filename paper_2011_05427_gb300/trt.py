@@ -68,7 +68,7 @@ FACE_FIELDS = ("sigR", "etaR", "etaL", "Fold", "F")
 
 
 class trt_level(ctypes.Structure):
-    _fields_ = [("n", ctypes.c_int)] + [(k, _dp) for k in LEVEL_FIELDS]
+    _fields_ = [("n", ctypes.c_int), ("fine", ctypes.c_int)] + [(k, _dp) for k in LEVEL_FIELDS]
 
 
 _lib = None
@@ -270,27 +270,29 @@ class Solver:
                                       *[x.data_ptr() for x in b]))
         return (In[..., :self.G], f, *b)
 
-    def _level(self, d, n):
+    def _level(self, d, n, fine=False):
         t = self.torch
         keep = {}
         for k in LEVEL_FIELDS:
             shape = (n, self.nx) if k in CELL_FIELDS else (n, self.nx + 1) if k in FACE_FIELDS else (n,)
+            if fine and k == "sigR":
+                shape = (n, self.nx)
             v = d.get(k)
             v = t.zeros(shape, dtype=t.float64, device=self.device) if v is None else self._t(v)
             assert tuple(v.shape) == shape, (k, v.shape, shape)
             keep[k] = v
-        lv = trt_level(n, *[_ptr(keep[k]) for k in LEVEL_FIELDS])
+        lv = trt_level(n, int(fine), *[_ptr(keep[k]) for k in LEVEL_FIELDS])
         return lv, keep
 
-    def k_lo_solve(self, dt, level):
+    def k_lo_solve(self, dt, level, fine=False):
         n = int(self._t(level["phi"]).shape[0])
-        lv, keep = self._level(level, n)
+        lv, keep = self._level(level, n, fine)
         self._check(lib().trt_k_lo_solve(self.h, float(dt), ctypes.byref(lv)))
         return {k: keep[k] for k in ("E", "F", "Eb0", "EbX")}
 
-    def k_restrict(self, src, n_to):
+    def k_restrict(self, src, n_to, fine=False):
         n = int(self._t(src["phi"]).shape[0])
-        ls, ks = self._level(src, n)
+        ls, ks = self._level(src, n, fine)
         ld, kd = self._level({}, n_to)
         self._check(lib().trt_k_restrict(self.h, ctypes.byref(ls), ctypes.byref(ld)))
         return kd

@@ -182,18 +182,24 @@ def test_lo_solve_parity(trt, orc, nx, ng):
     assert np.max(np.abs(got["EbX"] - ref["EbX"]) / (np.abs(ref["EbX"]) + ref["E"][:, -1])) < 1e-10
 
 
-@pytest.mark.parametrize("n_from,n_to,eta", [(16, 4, False), (12, 1, True), (1024, 256, False),
-                                             (64, 1, True), (4, 4, True)])
-def test_restrict_parity(trt, orc, n_from, n_to, eta):
-    r = W.rng(4000 + n_from + n_to)
-    nx = 37
+@pytest.mark.parametrize("n_from,n_to,eta,nx,fine",
+                         [(16, 4, False, 37, False), (12, 1, True, 37, False),
+                          (1024, 256, False, 37, False), (64, 1, True, 37, False),
+                          (4, 4, True, 37, False), (64, 16, True, 500, False),
+                          (256, 1, True, 500, False), (64, 16, False, 500, True),
+                          (1024, 64, False, 500, True), (64, 4, False, 70, True)])
+def test_restrict_parity(trt, orc, n_from, n_to, eta, nx, fine):
+    r = W.rng(4000 + n_from + n_to + nx)
     h = W.random_h(r, nx)
     lv = random_level(r, n_from, nx, eta=eta)
+    src = dict(lv)
+    if fine:   # raw fine-grid format: cell Rosseland opacity, faces averaged
+        src["sigR"] = np.exp(r.uniform(-3, 3, (n_from, nx)))
+        lv["sigR"] = orc.fine_face_sigR(h, src["sigR"])
     sol = oracle_level_solve(orc, h, 2e-3, lv)
     s = solver(trt, nx=nx, N=2, G=17, h=h)
-    src = dict(lv)
     src.update(sol)
-    got = {k: v.cpu().numpy() for k, v in s.k_restrict(src, n_to).items()}
+    got = {k: v.cpu().numpy() for k, v in s.k_restrict(src, n_to, fine=fine).items()}
     cmap = np.arange(n_from) // (n_from // n_to)
     ref, Esum = orc.restrict(h, lv, sol, cmap, n_to)
     for k in orc.LEVEL_KEYS:

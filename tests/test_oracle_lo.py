@@ -188,15 +188,15 @@ def test_restriction_weights(orc):
     assert np.allclose(crs["phi"][1], (fine["phi"][sel] * E).sum(0) / E.sum(0))
     assert np.allclose(crs["sig"][1], (fine["sig"][sel] * E).sum(0) / E.sum(0))
     assert np.allclose(crs["emis"][1], fine["emis"][sel].sum(0))
-    aF = np.abs(sol["F"][sel])
+    ER = np.concatenate([E[:, :], sol["EbX"][sel][:, None]], axis=1)
+    EL = np.concatenate([sol["Eb0"][sel][:, None], E[:, :]], axis=1)
+    aF = np.abs(sol["F"][sel]) + 1e-6 * C * 0.5 * (EL + ER)   # |F| weight with its floor
     sR = (fine["sigR"][sel] * aF).sum(0) / aF.sum(0)
     assert np.allclose(crs["sigR"][1], sR)
     dxf = np.concatenate([[h[0] / 2], (h[:-1] + h[1:]) / 2, [h[-1] / 2]])
     xi = dxf * ((fine["sigR"][sel] - sR) * sol["F"][sel]).sum(0)
-    ER = np.concatenate([E[:, :], sol["EbX"][sel][:, None]], axis=1).sum(0)
-    EL = np.concatenate([sol["Eb0"][sel][:, None], E[:, :]], axis=1).sum(0)
-    assert np.allclose(crs["etaR"][1], np.where(xi > 0, xi / (C * ER), 0.0))
-    assert np.allclose(crs["etaL"][1], np.where(xi < 0, -xi / (C * EL), 0.0))
+    assert np.allclose(crs["etaR"][1], np.where(xi > 0, xi / (C * ER.sum(0)), 0.0))
+    assert np.allclose(crs["etaL"][1], np.where(xi < 0, -xi / (C * EL.sum(0)), 0.0))
     Eout = sol["Eb0"][sel] - fine["Ein0"][sel]
     assert crs["C0"][1] == pytest.approx((fine["C0"][sel] * Eout).sum() / Eout.sum())
 
