@@ -225,6 +225,40 @@ int trt_k_grey_newton(trt_handle *h, double dt, const double *Tstar, const doubl
                       const double *sig_prev, const double *T_prev, int have_prev,
                       trt_level *g, double *T);
 
+/* ======================================================================================
+ * Allocation-free sweep.  The paper has no counterpart: this exists for callers that can
+ * not allocate device memory -- a plug-in inside an application that owns every device
+ * allocation and lends it no allocator, or a time loop that must not call cudaMalloc (nor
+ * pay its device-wide synchronisation) once it is running.  trt_sweep_noalloc does the
+ * work of trt_k_sweep with no handle and no workspace: every input and output is a plain
+ * device pointer of the caller, and the scratch the sweep needs (per-direction-tile
+ * angular partial sums and exit intensities) lives in one file-scope static device array
+ * of TRT_STATIC_SCRATCH_BYTES, which every GPU that loads the library keeps until exit.
+ *   - sizes: nx cells, N directions per half range (M = 2N), G groups; intensities are
+ *     [M][nx][2][ldG] with ldG = G rounded up to a multiple of 32 (double for TRT_FP64,
+ *     float for TRT_MIXED); h [nx], mu, w [M] (layout of trt.h), Iin0, IinX [G] isotropic
+ *     inflow intensities, sigE, emis [G][nx]; outputs as for trt_k_sweep;
+ *   - problems whose scratch (trt_sweep_noalloc_scratch_bytes) exceeds the array are
+ *     rejected with TRT_ENOSPACE before anything is enqueued;
+ *   - the call only enqueues work on `stream` (cudaStream_t as void*) and returns; it
+ *     allocates nothing -- no cudaMalloc / cudaFree, no library allocator;
+ *   - the first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress); make that first call before any stream capture;
+ *   - all calls share the one array, which keeps whatever the last call left in it (each
+ *     call overwrites every scratch value it reads, so nothing needs clearing); calls
+ *     that overlap on the GPU -- on different streams, or from different host threads --
+ *     race on it and must be serialised by the caller;
+ *   - on failure the message is in trt_sweep_noalloc_error(). */
+#define TRT_STATIC_SCRATCH_BYTES (8u << 20)
+
+size_t trt_sweep_noalloc_scratch_bytes(int nx, int N, int G);
+int trt_sweep_noalloc(int nx, int N, int G, int precision, double dt, const double *h,
+                      const double *mu, const double *w, const double *Iin0,
+                      const double *IinX, const double *sigE, const double *emis,
+                      const void *I_old, void *I_new, double *f, double *fb0, double *fbX,
+                      double *C0, double *CX, void *stream);
+const char *trt_sweep_noalloc_error(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -117,13 +117,20 @@ def lib():
     L.trt_k_grey_newton.restype = ctypes.c_int
     L.trt_k_grey_newton.argtypes = [_vp, ctypes.c_double, _vp, _vp, _vp, _vp, ctypes.c_int,
                                     ctypes.POINTER(trt_level), _vp]
+    L.trt_sweep_noalloc_scratch_bytes.restype = ctypes.c_size_t
+    L.trt_sweep_noalloc_scratch_bytes.argtypes = [ctypes.c_int] * 3
+    L.trt_sweep_noalloc.restype = ctypes.c_int
+    L.trt_sweep_noalloc.argtypes = [ctypes.c_int] * 4 + [ctypes.c_double] + [_vp] * 15
+    L.trt_sweep_noalloc_error.restype = ctypes.c_char_p
+    L.trt_sweep_noalloc_error.argtypes = []
     _lib = L
     return L
 
 
 EXPORTED = ("trt_workspace_bytes", "trt_create", "trt_step", "trt_moments", "trt_intensity",
             "trt_set_state", "trt_dims", "trt_destroy", "trt_last_error", "trt_k_opacity",
-            "trt_k_sweep", "trt_k_lo_solve", "trt_k_restrict", "trt_k_grey_newton")
+            "trt_k_sweep", "trt_k_lo_solve", "trt_k_restrict", "trt_k_grey_newton",
+            "trt_sweep_noalloc_scratch_bytes", "trt_sweep_noalloc", "trt_sweep_noalloc_error")
 
 
 class TRTError(RuntimeError):
