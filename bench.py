@@ -131,7 +131,7 @@ def sweep_roofline(trt, s, cfg, reps=20):
     r = W.rng(5)
     T = W.random_temperatures(r, cfg.n_cells, 1e-3, 1.0)
     sig, em, _ = s.k_opacity(T)
-    rdt = torch.float64 if s.precision == trt.TRT_FP64 else torch.float32
+    rdt = torch.float32 if s.precision & trt.TRT_SWEEP_FP32 else torch.float64
     Iold = torch.rand((s.M, s.nx, 2, s.ldG), dtype=rdt, device=s.device)
     Inew = torch.empty_like(Iold)
     f = torch.empty((s.G, s.nx), dtype=torch.float64, device=s.device)
@@ -150,7 +150,7 @@ def sweep_roofline(trt, s, cfg, reps=20):
     ev1.record(s.stream)
     torch.cuda.synchronize()
     ms = ev0.elapsed_time(ev1) / reps
-    esz = 8 if s.precision == trt.TRT_FP64 else 4
+    esz = 4 if s.precision & trt.TRT_SWEEP_FP32 else 8
     upd = cfg.n_cells * cfg.M * cfg.G
     bytes_alg = upd * 4 * esz + cfg.n_cells * cfg.G * (2 * 8 + 8)
     hbm, src = peaks()
@@ -310,10 +310,20 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed", "sweep32", "lo32"])
     ap.add_argument("--cycle", default="W", choices=["V", "W"])
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--profile-step", action="store_true",
+                    help="run the warm-up steps and one more step, print nothing (for ncu)")
     args = ap.parse_args()
+    if args.profile_step:
+        from paper_2011_05427_gb300 import trt
+        cfg = W.fc_1024(args.cycle)
+        s = trt.Solver.from_slab(cfg, precision=args.precision, device="cuda:0")
+        for _ in range(args.warmup + 1):
+            s.step(cfg.dt, cfg.cycle, cfg.l_max, cfg.eps)
+        s.close()
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -50,18 +50,21 @@ extern "C" {
 #define TRT_ECUDA          -5   /* a CUDA runtime call failed; see trt_last_error        */
 #define TRT_ENOSPACE       -6   /* workspace smaller than trt_workspace_bytes            */
 
-/* ---- precision modes (spec pattern (1)) ---- */
-#define TRT_FP64   0   /* every step in FP64                                               */
-#define TRT_MIXED  1   /* sweeps and group LOQD in FP32; opacities, grey LOQD, MEB Newton and
-                          convergence checks in FP64                                       */
+/* ---- precision modes (a bit mask) ---- */
+#define TRT_FP64         0   /* every step in FP64                                          */
+#define TRT_SWEEP_FP32   1   /* HO sweeps (intensity storage and arithmetic) in FP32         */
+#define TRT_LO_FP32      2   /* fine and coarse group LOQD solves in FP32                     */
+#define TRT_MIXED        3   /* both; opacities, restriction, grey LOQD, MEB Newton and the
+                                convergence checks stay FP64                                 */
 
 /* ---- cycle types (Sec. 4, Fig. 1) ---- */
 #define TRT_CYCLE_V 0   /* S empty: two-grid method on any hierarchy                      */
 #define TRT_CYCLE_W 1   /* S = w(2), w(Gamma-1) = [Gamma-1], w(g) = w(g+1) + [g] + w(g+1)  */
 #define TRT_CYCLE_F 2   /* S = [Gamma-1, ..., 2]                                           */
 
-/* Spatial grid (Sec. 5 mesh).  x_edges: host, n_cells+1 increasing values, or NULL for a
- * uniform mesh over [0, length_cm]. */
+/* Spatial grid (Sec. 5 mesh), 1 <= n_cells <= 2048 (one warp-partitioned tridiagonal
+ * system per group must fit in shared memory).  x_edges: host, n_cells+1 increasing
+ * values, or NULL for a uniform mesh over [0, length_cm]. */
 typedef struct {
     int n_cells;
     const double *x_edges;
@@ -93,7 +96,8 @@ typedef struct {
     double scale;
 } trt_opacity;
 
-/* Options: precision mode, initial temperature, CUDA stream (cudaStream_t as void*),
+/* Options: precision (TRT_FP64 or an OR of TRT_SWEEP_FP32 / TRT_LO_FP32), initial
+ * temperature, CUDA stream (cudaStream_t as void*),
  * caller-owned device workspace of at least trt_workspace_bytes bytes (256-B aligned). */
 typedef struct {
     int precision;
@@ -180,8 +184,8 @@ int trt_k_opacity(trt_handle *h, const double *T, double *sigE, double *emis, do
 /* One HO sweep (eq. rt, simple corner balance, implicit Euler) of every group and
  * direction with sigma_t = sigE + 1/(c dt) and corner sources emis + I_old/(c dt), inflow
  * from the handle's boundary temperatures, followed by the QD factors (eqs. f_g, c_g).
- * I_old / I_new: [M][nx][2][ldG] in the handle's sweep precision (double for TRT_FP64,
- * float for TRT_MIXED).  f [G][nx]; fb0, fbX, C0, CX [G]; all FP64. */
+ * I_old / I_new: [M][nx][2][ldG] in the handle's sweep precision (float when the
+ * precision has TRT_SWEEP_FP32, else double).  f [G][nx]; fb0, fbX, C0, CX [G]; all FP64. */
 int trt_k_sweep(trt_handle *h, double dt, const double *sigE, const double *emis,
                 const void *I_old, void *I_new, double *f, double *fb0, double *fbX,
                 double *C0, double *CX);
@@ -235,8 +239,8 @@ int trt_k_grey_newton(trt_handle *h, double dt, const double *Tstar, const doubl
  * angular partial sums and exit intensities) lives in one file-scope static device array
  * of TRT_STATIC_SCRATCH_BYTES, which every GPU that loads the library keeps until exit.
  *   - sizes: nx cells, N directions per half range (M = 2N), G groups; intensities are
- *     [M][nx][2][ldG] with ldG = G rounded up to a multiple of 32 (double for TRT_FP64,
- *     float for TRT_MIXED); h [nx], mu, w [M] (layout of trt.h), Iin0, IinX [G] isotropic
+ *     [M][nx][2][ldG] with ldG = G rounded up to a multiple of 32 (float when precision
+ *     has TRT_SWEEP_FP32, else double); h [nx], mu, w [M] (layout of trt.h), Iin0, IinX [G] isotropic
  *     inflow intensities, sigE, emis [G][nx]; outputs as for trt_k_sweep;
  *   - problems whose scratch (trt_sweep_noalloc_scratch_bytes) exceeds the array are
  *     rejected with TRT_ENOSPACE before anything is enqueued;

@@ -35,6 +35,7 @@ struct trt_handle {
     void *I_cur, *I_alt;
     double *f, *fb0, *fbX, *C0, *CX;
     double *sigE, *emis, *sigR;
+    float *sig32 = nullptr, *emis32 = nullptr;   // FP32 copies for an FP32 sweep
     double *part, *psi_exit;
     double *E1, *F1, *Eb0_1, *EbX_1;
     Level crs, grey;
@@ -82,12 +83,15 @@ void carve(trt_handle *h, Carver &c)
 {
     Problem &p = h->p;
     const size_t nx = p.nx, G = p.G, M = p.M;
-    const size_t rsz = (p.precision == TRT_FP64) ? sizeof(double) : sizeof(float);
+    const size_t rsz = sweep_fp32(p.precision) ? sizeof(float) : sizeof(double);
     p.h = c.take<double>(nx); p.edges = c.take<double>(G + 1);
     p.mu = c.take<double>(M); p.w = c.take<double>(M);
     p.Iin0 = c.take<double>(G); p.IinX = c.take<double>(G);
     p.Ein0 = c.take<double>(G); p.Fin0 = c.take<double>(G);
     p.EinX = c.take<double>(G); p.FinX = c.take<double>(G);
+    p.ihf = c.take<double>(nx + 1);
+    p.rscratch_doubles = restrict_scratch_doubles((int)nx, (int)G, 1);
+    p.rscratch = p.rscratch_doubles ? c.take<double>(p.rscratch_doubles) : nullptr;
     double **tl[] = {&h->T, &h->Told, &h->Tcyc, &h->Tphase, &h->Ttil, &h->Tnew, &h->sig_prev,
                      &h->T_prev, &h->Ecyc, &h->Ephase};
     for (double **q : tl) *q = c.take<double>(nx);
@@ -100,6 +104,10 @@ void carve(trt_handle *h, Carver &c)
     h->C0 = c.take<double>(G); h->CX = c.take<double>(G);
     h->sigE = c.take<double>(G * nx); h->emis = c.take<double>(G * nx);
     h->sigR = c.take<double>(G * nx);
+    if (sweep_fp32(p.precision)) {
+        h->sig32 = c.take<float>(G * nx);
+        h->emis32 = c.take<float>(G * nx);
+    }
     h->part = c.take<double>(std::max(sweep_partial_doubles(p), 4 * nx + 8));
     h->psi_exit = c.take<double>(M * (size_t)p.ldG);
     h->E1 = c.take<double>(G * nx); h->F1 = c.take<double>(G * (nx + 1));
@@ -116,7 +124,7 @@ bool validate(const trt_grid *grid, const trt_angles *angles, const trt_groups *
 {
     if (!grid || !angles || !groups || !opt) { err = "null argument"; return false; }
     p.nx = grid->n_cells;
-    if (p.nx < 1 || p.nx > 8192) { err = "n_cells must be in [1, 8192]"; return false; }
+    if (p.nx < 1 || p.nx > 2048) { err = "n_cells must be in [1, 2048]"; return false; }
     p.N = angles->N;
     if (p.N < 1 || p.N > 256) { err = "angles.N must be in [1, 256]"; return false; }
     p.M = 2 * p.N;
@@ -124,7 +132,7 @@ bool validate(const trt_grid *grid, const trt_angles *angles, const trt_groups *
     if (p.G < 1 || p.G > (1 << 16)) { err = "n_groups must be in [1, 65536]"; return false; }
     p.ldG = (p.G + 31) / 32 * 32;
     p.precision = opt->precision;
-    if (p.precision != TRT_FP64 && p.precision != TRT_MIXED) { err = "bad precision"; return false; }
+    if (p.precision < 0 || p.precision > TRT_MIXED) { err = "bad precision"; return false; }
     xe.resize(p.nx + 1);
     if (grid->x_edges) {
         for (int i = 0; i <= p.nx; ++i) xe[i] = grid->x_edges[i];
@@ -313,6 +321,8 @@ int trt_create(const trt_grid *grid, const trt_angles *angles, const trt_groups 
     std::vector<double> hh(nx), mu(M), w(M), Iin0(G, 0.0), IinX(G, 0.0);
     std::vector<double> Ein0(G, 0.0), Fin0(G, 0.0), EinX(G, 0.0), FinX(G, 0.0);
     for (int i = 0; i < nx; ++i) hh[i] = xe[i + 1] - xe[i];
+    std::vector<double> ihf(nx + 1, 0.0);
+    for (int f = 1; f < nx; ++f) ihf[f] = 1.0 / (hh[f - 1] + hh[f]);
     {
         std::vector<double> x(N), wx(N);
         gauss_legendre_host(N, x.data(), wx.data());
@@ -366,7 +376,7 @@ int trt_create(const trt_grid *grid, const trt_angles *angles, const trt_groups 
         return cudaMemcpyAsync(dst, src.data(), src.size() * sizeof(double),
                                cudaMemcpyHostToDevice, p.stream);
     };
-    CK(up(p.h, hh)); CK(up(p.edges, edges)); CK(up(p.mu, mu)); CK(up(p.w, w));
+    CK(up(p.h, hh)); CK(up(p.ihf, ihf)); CK(up(p.edges, edges)); CK(up(p.mu, mu)); CK(up(p.w, w));
     CK(up(p.Iin0, Iin0)); CK(up(p.IinX, IinX)); CK(up(p.Ein0, Ein0)); CK(up(p.Fin0, Fin0));
     CK(up(p.EinX, EinX)); CK(up(p.FinX, FinX));
     CK(up(H->T, T0v)); CK(up(H->Eg, Eg)); CK(up(H->Fg, Fg)); CK(up(H->f, f));
@@ -376,7 +386,7 @@ int trt_create(const trt_grid *grid, const trt_angles *angles, const trt_groups 
     const long rows = (long)M * nx * 2;
     const size_t nI = (size_t)rows * p.ldG;
     const int nb = (int)std::min<long>(4096, (long)((nI + 255) / 256));
-    if (p.precision == TRT_FP64) {
+    if (!sweep_fp32(p.precision)) {
         k_fill_intensity<double><<<nb, 256, 0, p.stream>>>((double *)H->I_cur, H->sigE, rows, p.ldG, G);
         k_fill_intensity<double><<<nb, 256, 0, p.stream>>>((double *)H->I_alt, H->sigE, rows, p.ldG, G);
     } else {
@@ -432,6 +442,8 @@ int trt_step(trt_handle *h, double dt, const trt_cycle *cyc, trt_stats *stats)
     const double eps = cyc->eps, eps_in = cyc->eps_inner;
     int n_ti = 0, n_c = 0, n_lo = 0, s = 0, status = TRT_OK, nk = 0;
     bool swept = false, opac_valid = false;
+    // the LO phases evaluate opacities without the FP32 copies; the sweep needs them fresh
+    const bool sig32_valid = false;
     int have_prev = 0;
 
     CK(d2d(h, h->Told, h->T, nx));
@@ -444,13 +456,17 @@ int trt_step(trt_handle *h, double dt, const trt_cycle *cyc, trt_stats *stats)
 
     for (;;) {
         if (s > 0) {
-            if (!opac_valid) {
-                CK(launch_opacity(p, h->T, h->sigE, h->emis, h->sigR));
+            if (!opac_valid || !sig32_valid) {
+                CK(launch_opacity(p, h->T, h->sigE, h->emis, h->sigR, h->sig32, h->emis32, dt));
                 ++nk;
             }
             opac_valid = true;
-            CK(launch_sweep(p, dt, h->sigE, h->emis, h->I_cur, h->I_alt, h->part, h->psi_exit,
-                            h->f, h->fb0, h->fbX, h->C0, h->CX));
+            if (h->sig32)
+                CK(launch_sweep(p, dt, h->sig32, h->emis32, true, h->I_cur, h->I_alt, h->part,
+                                h->psi_exit, h->f, h->fb0, h->fbX, h->C0, h->CX));
+            else
+                CK(launch_sweep(p, dt, h->sigE, h->emis, false, h->I_cur, h->I_alt, h->part,
+                                h->psi_exit, h->f, h->fb0, h->fbX, h->C0, h->CX));
             nk += 2;
             ++n_ti;
             swept = true;
@@ -565,7 +581,7 @@ int trt_intensity(trt_handle *h, double *I, double *f)
     const Problem &p = h->p;
     const size_t nI = (size_t)p.M * p.nx * 2 * p.ldG;
     if (I) {
-        if (p.precision == TRT_FP64) {
+        if (!sweep_fp32(p.precision)) {
             CK(cudaMemcpyAsync(I, h->I_cur, nI * sizeof(double), cudaMemcpyDeviceToHost, p.stream));
             CK(cudaStreamSynchronize(p.stream));
         } else {
@@ -605,7 +621,7 @@ int trt_set_state(trt_handle *h, const double *T, const double *Eg, const double
     std::vector<float> tmp;
     if (I) {
         const size_t nI = (size_t)p.M * p.nx * 2 * p.ldG;
-        if (p.precision == TRT_FP64) {
+        if (!sweep_fp32(p.precision)) {
             CK(cudaMemcpyAsync(h->I_cur, I, nI * sizeof(double), cudaMemcpyHostToDevice, p.stream));
         } else {
             tmp.resize(nI);
@@ -634,7 +650,8 @@ int trt_k_sweep(trt_handle *h, double dt, const double *sigE, const double *emis
 {
     if (!h || !(dt > 0) || !sigE || !emis || !I_old || !I_new || !f || !fb0 || !fbX || !C0 || !CX)
         return TRT_EINVAL;
-    CK(launch_sweep(h->p, dt, sigE, emis, I_old, I_new, h->part, h->psi_exit, f, fb0, fbX, C0, CX));
+    CK(launch_sweep(h->p, dt, sigE, emis, false, I_old, I_new, h->part, h->psi_exit, f, fb0, fbX,
+                    C0, CX));
     CK(cudaStreamSynchronize(h->p.stream));
     return TRT_OK;
 }

@@ -21,8 +21,27 @@ struct SeriesTables {
     double pD[kSer];   // D(x)     = x^5 sum pD[n] x^n,   D(x) = int_0^x t^7 e^{2t}/(e^t-1)^3
     double Pinf;       // pi^4/15
     double Dinf;       // 2520 (zeta(6) + zeta(7))
-    double gx[8], gw[8];   // 8-point Gauss-Legendre rule on [-1, 1] (narrow groups)
+    double g4x[4], g4w[4];   // 4- and 6-point Gauss-Legendre rules on [-1, 1]
+    double g6x[6], g6w[6];   // (narrow groups, see group_integrals)
 };
+// 1/d in FP64 by Newton-Raphson, x_{k+1} = x_k (2 - d x_k), from the correctly rounded FP32
+// reciprocal: the relative error squares with each step, 2^-24 -> ~4e-15 -> rounding, so
+// two steps give the FP64 result to about an ulp at 6 FP64 operations, where an IEEE
+// division costs ~20 on GB300's FP64 pipe.  Outside the FP32 normal range it divides.
+__host__ __device__ inline double rcp64(double d)
+{
+#ifdef __CUDA_ARCH__
+    const float df = (float)d;
+    const float ad = fabsf(df);
+    if (!(ad > 1e-37f && ad < 1e37f)) return 1.0 / d;
+    double x = (double)__frcp_rn(df);
+    x = x * fma(-d, x, 2.0);
+    return x * fma(-d, x, 2.0);
+#else
+    return 1.0 / d;
+#endif
+}
+
 const SeriesTables &host_series();   // host copy (built once)
 void gauss_legendre_host(int n, double *x, double *w);   // nodes / weights on [-1, 1]
 cudaError_t ensure_tables();         // upload the tables to the current device (once)
@@ -57,6 +76,9 @@ struct GreyArgs {
     double *flags;              // [8], device
 };
 
+inline bool sweep_fp32(int precision) { return (precision & TRT_SWEEP_FP32) != 0; }
+inline bool lo_fp32(int precision) { return (precision & TRT_LO_FP32) != 0; }
+
 struct Problem {
     int nx, N, M, G, ldG, nlev, precision;
     int levels[16];
@@ -65,17 +87,26 @@ struct Problem {
     cudaStream_t stream;
     // device constants
     double *h, *edges, *mu, *w, *Iin0, *IinX, *Ein0, *Fin0, *EinX, *FinX;
+    double *ihf;        // [nx+1]: 1/(h_{f-1} + h_f) at interior faces (dx-weighted means)
+    double *rscratch;   // partial sums of the two-stage restriction
+    size_t rscratch_doubles;
 };
 
 // ---- launchers (each enqueues on p.stream; returns cudaError_t of the launch) ----
+// sig32 / emis32 (may be null): the FP32 sweep's inputs (sigma_E + 1/(c dt)) h/2 and h e/2
 cudaError_t launch_opacity(const Problem &p, const double *T, double *sigE, double *emis,
-                           double *sigR);
+                           double *sigR, float *sig32 = nullptr, float *emis32 = nullptr,
+                           double dt = 0.0);
 size_t sweep_partial_doubles(const Problem &p);
-cudaError_t launch_sweep(const Problem &p, double dt, const double *sigE, const double *emis,
-                         const void *I_old, void *I_new, double *part, double *psi_exit,
-                         double *f, double *fb0, double *fbX, double *C0, double *CX);
+// sigE / emis: [G][nx]; double sigma_E, e_g, or (sigma_fp32, FP32 sweep only) the float
+// pre-scaled (sigma_E + 1/(c dt)) h/2 and h e/2 of launch_opacity
+cudaError_t launch_sweep(const Problem &p, double dt, const void *sigE, const void *emis,
+                         bool sigma_fp32, const void *I_old, void *I_new, double *part,
+                         double *psi_exit, double *f, double *fb0, double *fbX, double *C0,
+                         double *CX);
 cudaError_t launch_lo_solve(const Problem &p, double dt, const Level &L);
 cudaError_t launch_restrict(const Problem &p, const Level &src, Level &dst);
+size_t restrict_scratch_doubles(int nx, int n_from, int n_to);
 cudaError_t launch_grey(const Problem &p, const Level &g, const GreyArgs &a);
 cudaError_t launch_group_sum(const Problem &p, int n, const double *X, double *out);
 

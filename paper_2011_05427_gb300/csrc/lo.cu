@@ -26,10 +26,17 @@ namespace trt {
 
 namespace {
 
+template <typename R>
+__device__ inline R rcpR(R d);
+template <>
+__device__ inline double rcpR<double>(double d) { return rcp64(d); }
+template <>
+__device__ inline float rcpR<float>(float d) { return __frcp_rn(d); }
+
 struct LoCtx {
     int nx;
     double dt, icdt;
-    const double *h;
+    const double *h, *ihf;
     Level L;
     const double *a_cell, *s_cell;   // grey: explicit absorption / source per cell
 };
@@ -41,7 +48,7 @@ __device__ inline double sigR_face(const LoCtx &x, int q, int f)
     const double *sc = x.L.sigR + (size_t)q * nx;
     if (f == 0) return sc[0];
     if (f == nx) return sc[nx - 1];
-    return (sc[f - 1] * x.h[f - 1] + sc[f] * x.h[f]) / (x.h[f - 1] + x.h[f]);
+    return (sc[f - 1] * x.h[f - 1] + sc[f] * x.h[f]) * x.ihf[f];
 }
 
 // F_f = GD + PL E_{f-1} - PR E_f  (boundary faces: the face energy already eliminated)
@@ -72,15 +79,15 @@ __device__ inline void face_coef(const LoCtx &x, int q, int f, R &PL, R &PR, R &
     R D = dx * (icdt + (R)sigR_face(x, q, f));
     R Gf = dx * (R)x.L.Fold[(size_t)q * (nx + 1) + f] * icdt;
     if (f == 0) {
-        const R C0 = (R)x.L.C0[q];
-        D -= phiL / C0;
-        Gf += c * phiL * (R)x.L.Ein0[q] - phiL * (R)x.L.Fin0[q] / C0;
+        const R iC0 = rcpR<R>((R)x.L.C0[q]);
+        D -= phiL * iC0;
+        Gf += c * phiL * (R)x.L.Ein0[q] - phiL * (R)x.L.Fin0[q] * iC0;
     } else if (f == nx) {
-        const R CX = (R)x.L.CX[q];
-        D += phiR / CX;
-        Gf += -c * phiR * (R)x.L.EinX[q] + phiR * (R)x.L.FinX[q] / CX;
+        const R iCX = rcpR<R>((R)x.L.CX[q]);
+        D += phiR * iCX;
+        Gf += -c * phiR * (R)x.L.EinX[q] + phiR * (R)x.L.FinX[q] * iCX;
     }
-    const R iD = (R)1 / D;
+    const R iD = rcpR<R>(D);
     PL = c * phiL * iD;
     PR = c * phiR * iD;
     GD = Gf * iD;
@@ -98,15 +105,62 @@ __device__ inline void cell_terms(const LoCtx &x, int q, int i, R &ai, R &si)
     }
 }
 
-// Solve system q with one warp.  sm: 3 * 32 * mmax values of R for this warp.
+// Solve system q with one warp.  sm: 6 * 32 * mmax values of R for this warp.
 // Writes E, F, Eb0, EbX of system q.
+//   phase A (all lanes, coalesced over cells/faces): face coefficients PL, PR, GD and the
+//           row parts dx/dt + dx a, dx s + dx Eold/dt, stored in the chunk layout
+//           [row-in-chunk][lane] so that phase B reads conflict free;
+//   phase B (each lane its chunk): modified Thomas down and up the chunk;
+//   phase C (warp): parallel cyclic reduction of the 2 x 32 chunk-boundary rows;
+//   phase D (each lane): back substitution, then the fluxes of its faces.
 template <typename R>
-__device__ void warp_lo_solve(const LoCtx &x, int q, R *sm, int mmax)
+__device__ inline void chunk_of(int f, int n, int P, int &l, int &k)
+{
+    if (f == n) {
+        l = P - 1;
+        k = n - ((P - 1) * n) / P;
+    } else {
+        l = (f * P) / n;
+        if (l + 1 < P && ((l + 1) * n) / P <= f) ++l;
+        k = f - (l * n) / P;
+    }
+}
+
+// Phase A for system q by `nthr` cooperating threads (index `t`): face coefficients and
+// row parts into the chunk layout.  n >= 2.
+template <typename R>
+__device__ void lo_stage(const LoCtx &x, int q, R *sm, int mmax, int t, int nthr)
+{
+    const int n = x.nx;
+    const R dt = (R)x.dt;
+    const int P = min(32, n / 2);
+    const int S = 32 * mmax;
+    R *PLc = sm, *PRc = sm + S, *GDc = sm + 2 * S, *Ap = sm + 3 * S, *Dp = sm + 5 * S;
+    for (int f = t; f <= n; f += nthr) {
+        int l, k;
+        chunk_of<R>(f, n, P, l, k);
+        R PL, PR, GD;
+        face_coef<R>(x, q, f, PL, PR, GD);
+        PLc[k * 32 + l] = PL;
+        PRc[k * 32 + l] = PR;
+        GDc[k * 32 + l] = GD;
+        if (f < n) {
+            R ai, si;
+            cell_terms<R>(x, q, f, ai, si);
+            const R hi = (R)x.h[f];
+            Ap[k * 32 + l] = hi / dt + hi * ai;
+            Dp[k * 32 + l] = hi * si + hi * (R)x.L.Eold[(size_t)q * n + f] / dt;
+        }
+    }
+}
+
+// staged = true: phase A already done (by the whole block) for n >= 2.
+template <typename R>
+__device__ void warp_lo_solve(const LoCtx &x, int q, R *sm, int mmax, bool staged = false)
 {
     const int lane = threadIdx.x & 31;
     const int n = x.nx;
     const R dt = (R)x.dt;
-    R *Ap = sm, *Cp = sm + 32 * mmax, *Dp = sm + 64 * mmax;
     double *E = x.L.E + (size_t)q * n;
     double *F = x.L.F + (size_t)q * (n + 1);
 
@@ -135,61 +189,69 @@ __device__ void warp_lo_solve(const LoCtx &x, int q, R *sm, int mmax)
     const int r0 = act ? (lane * n) / P : n;
     const int r1 = act ? ((lane + 1) * n) / P : n;
     const int m = r1 - r0;
-#define SM(arr, k) arr[(k) * 32 + lane]
+    const int S = 32 * mmax;
+    R *PLc = sm, *PRc = sm + S, *GDc = sm + 2 * S;
+    R *Ap = sm + 3 * S, *Cp = sm + 4 * S, *Dp = sm + 5 * S;
+#define CH(arr, k, l) arr[(k) * 32 + (l)]
+
+    // ---- phase A ----
+    if (!staged) lo_stage<R>(x, q, sm, mmax, lane, 32);
+    __syncwarp();
 
     R x0 = 0, x1 = 0;
-    // ---- forward: rows r0..r1-1, each normalised, coupled to x_{r0} and x_{k+1} ----
     R A0r = 0, C0r = 0, D0r = 0, A1r = 0, C1r = 0, D1r = 0;   // reduced rows
     if (act) {
-        R PLi, PRi, GDi;
-        face_coef<R>(x, q, r0, PLi, PRi, GDi);
+        // ---- phase B: rows r0..r1-1, each normalised, coupled to x_{r0} and x_{k+1} ----
+        R PLi = CH(PLc, 0, lane), PRi = CH(PRc, 0, lane), GDi = CH(GDc, 0, lane);
         R ap = 0, cp = 0, dp = 0;
         for (int k = 0; k < m; ++k) {
             const int i = r0 + k;
-            R PL1, PR1, GD1, ai, si;
-            face_coef<R>(x, q, i + 1, PL1, PR1, GD1);
-            cell_terms<R>(x, q, i, ai, si);
-            const R hi = (R)x.h[i];
-            const R di = hi / dt + hi * ai + PL1 + PRi;
+            R PL1, PR1, GD1;
+            if (k + 1 < m || lane == P - 1) {
+                PL1 = CH(PLc, k + 1, lane); PR1 = CH(PRc, k + 1, lane); GD1 = CH(GDc, k + 1, lane);
+            } else {
+                PL1 = CH(PLc, 0, lane + 1); PR1 = CH(PRc, 0, lane + 1); GD1 = CH(GDc, 0, lane + 1);
+            }
+            const R di = CH(Ap, k, lane) + PL1 + PRi;
+            const R rh = CH(Dp, k, lane) - GD1 + GDi;
             const R lo = (i > 0) ? -PLi : (R)0;
             const R up = (i < n - 1) ? -PR1 : (R)0;
-            const R rh = hi * si + hi * (R)x.L.Eold[(size_t)q * n + i] / dt - GD1 + GDi;
             if (k < 2) {
-                const R r = (R)1 / di;
+                const R r = rcpR<R>(di);
                 ap = lo * r;
                 cp = up * r;
                 dp = rh * r;
             } else {
-                const R r = (R)1 / (di - lo * cp);
+                const R r = rcpR<R>(di - lo * cp);
                 dp = r * (rh - lo * dp);
                 ap = -r * lo * ap;
                 cp = r * up;
             }
-            SM(Ap, k) = ap;
-            SM(Cp, k) = cp;
-            SM(Dp, k) = dp;
+            CH(Ap, k, lane) = ap;
+            CH(Cp, k, lane) = cp;
+            CH(Dp, k, lane) = dp;
             PLi = PL1;
             PRi = PR1;
             GDi = GD1;
         }
-        // ---- backward: rows k = m-3..1 coupled to x_{r0} and x_{r1-1} ----
+        // backward: rows k = m-3..1 coupled to x_{r0} and x_{r1-1}
         if (m >= 3) {
             for (int k = m - 3; k >= 1; --k) {
-                const R ck = SM(Cp, k);
-                SM(Dp, k) = SM(Dp, k) - ck * SM(Dp, k + 1);
-                SM(Ap, k) = SM(Ap, k) - ck * SM(Ap, k + 1);
-                SM(Cp, k) = -ck * SM(Cp, k + 1);
+                const R ck = CH(Cp, k, lane);
+                CH(Dp, k, lane) = CH(Dp, k, lane) - ck * CH(Dp, k + 1, lane);
+                CH(Ap, k, lane) = CH(Ap, k, lane) - ck * CH(Ap, k + 1, lane);
+                CH(Cp, k, lane) = -ck * CH(Cp, k + 1, lane);
             }
-            const R c0 = SM(Cp, 0);
-            const R r = (R)1 / ((R)1 - c0 * SM(Ap, 1));
-            SM(Dp, 0) = r * (SM(Dp, 0) - c0 * SM(Dp, 1));
-            SM(Ap, 0) = r * SM(Ap, 0);
-            SM(Cp, 0) = -r * c0 * SM(Cp, 1);
+            const R c0 = CH(Cp, 0, lane);
+            const R r = rcpR<R>((R)1 - c0 * CH(Ap, 1, lane));
+            CH(Dp, 0, lane) = r * (CH(Dp, 0, lane) - c0 * CH(Dp, 1, lane));
+            CH(Ap, 0, lane) = r * CH(Ap, 0, lane);
+            CH(Cp, 0, lane) = -r * c0 * CH(Cp, 1, lane);
         }
-        A0r = SM(Ap, 0); C0r = SM(Cp, 0); D0r = SM(Dp, 0);
-        A1r = SM(Ap, m - 1); C1r = SM(Cp, m - 1); D1r = SM(Dp, m - 1);
+        A0r = CH(Ap, 0, lane); C0r = CH(Cp, 0, lane); D0r = CH(Dp, 0, lane);
+        A1r = CH(Ap, m - 1, lane); C1r = CH(Cp, m - 1, lane); D1r = CH(Dp, m - 1, lane);
     }
-    // ---- reduced system: rows (first_l, last_l), l = 0..31, by PCR with shuffles ----
+    // ---- phase C: reduced system rows (first_l, last_l), l = 0..31, PCR with shuffles ----
     {
         R B0r = 1, B1r = 1;
         if (!act) { A0r = C0r = D0r = A1r = C1r = D1r = 0; }
@@ -232,47 +294,45 @@ __device__ void warp_lo_solve(const LoCtx &x, int q, R *sm, int mmax)
                 }
             }
             {
-                const R al = -A0r / lB0, ga = -C0r / uB0;
+                const R al = -A0r * rcpR<R>(lB0), ga = -C0r * rcpR<R>(uB0);
                 const R nA = al * lA0, nC = ga * uC0;
                 const R nB = B0r + al * lC0 + ga * uA0, nD = D0r + al * lD0 + ga * uD0;
                 A0r = nA; B0r = nB; C0r = nC; D0r = nD;
             }
             {
-                const R al = -A1r / lB1, ga = -C1r / uB1;
+                const R al = -A1r * rcpR<R>(lB1), ga = -C1r * rcpR<R>(uB1);
                 const R nA = al * lA1, nC = ga * uC1;
                 const R nB = B1r + al * lC1 + ga * uA1, nD = D1r + al * lD1 + ga * uD1;
                 A1r = nA; B1r = nB; C1r = nC; D1r = nD;
             }
         }
-        x0 = D0r / B0r;
-        x1 = D1r / B1r;
+        x0 = D0r * rcpR<R>(B0r);
+        x1 = D1r * rcpR<R>(B1r);
     }
-    // ---- back substitution of interior rows; E into Dp ----
+    // ---- phase D: back substitution (E into Dp), then the fluxes ----
     if (act) {
         for (int k = 1; k < m - 1; ++k)
-            SM(Dp, k) = SM(Dp, k) - SM(Ap, k) * x0 - SM(Cp, k) * x1;
-        SM(Dp, 0) = x0;
-        SM(Dp, m - 1) = x1;
-        for (int k = 0; k < m; ++k) E[r0 + k] = (double)SM(Dp, k);
+            CH(Dp, k, lane) = CH(Dp, k, lane) - CH(Ap, k, lane) * x0 - CH(Cp, k, lane) * x1;
+        CH(Dp, 0, lane) = x0;
+        CH(Dp, m - 1, lane) = x1;
+        for (int k = 0; k < m; ++k) E[r0 + k] = (double)CH(Dp, k, lane);
     }
     __syncwarp();
-    // ---- fluxes: faces r0..r1-1, and the right boundary face by the last lane ----
     if (act) {
-        const int r0p = (lane > 0) ? ((lane - 1) * n) / P : 0;
-        const R Eleft0 = (lane > 0) ? Dp[(r0 - r0p - 1) * 32 + lane - 1] : (R)0;
-        const int fend = (lane == P - 1) ? n : r1 - 1;
-        for (int f = r0; f <= fend; ++f) {
-            R PL, PR, GD;
-            face_coef<R>(x, q, f, PL, PR, GD);
-            R Fv = GD;
-            if (f > 0) Fv += PL * ((f == r0) ? Eleft0 : SM(Dp, f - 1 - r0));
-            if (f < n) Fv -= PR * SM(Dp, f - r0);
+        const int mprev = (lane > 0) ? r0 - ((lane - 1) * n) / P : 0;
+        const R Eleft0 = (lane > 0) ? CH(Dp, mprev - 1, lane - 1) : (R)0;
+        const int kend = (lane == P - 1) ? m : m - 1;
+        for (int k = 0; k <= kend; ++k) {
+            const int f = r0 + k;
+            R Fv = CH(GDc, k, lane);
+            if (f > 0) Fv += CH(PLc, k, lane) * ((k == 0) ? Eleft0 : CH(Dp, k - 1, lane));
+            if (f < n) Fv -= CH(PRc, k, lane) * CH(Dp, k, lane);
             F[f] = (double)Fv;
             if (f == 0) x.L.Eb0[q] = x.L.Ein0[q] + ((double)Fv - x.L.Fin0[q]) / (kC * x.L.C0[q]);
             if (f == n) x.L.EbX[q] = x.L.EinX[q] + ((double)Fv - x.L.FinX[q]) / (kC * x.L.CX[q]);
         }
     }
-#undef SM
+#undef CH
 }
 
 inline int lo_mmax(int nx) { return nx < 2 ? 1 : (nx + (std::min(32, nx / 2)) - 1) / std::min(32, nx / 2) + 1; }
@@ -285,7 +345,7 @@ __global__ void __launch_bounds__(256) k_lo_solve(LoCtx x, int mmax)
     const int warp = threadIdx.x >> 5;
     const int q = blockIdx.x * W + warp;
     if (q >= x.L.n) return;
-    R *sm = reinterpret_cast<R *>(smem_raw) + (size_t)warp * 3 * 32 * mmax;
+    R *sm = reinterpret_cast<R *>(smem_raw) + (size_t)warp * 6 * 32 * mmax;
     warp_lo_solve<R>(x, q, sm, mmax);
 }
 
@@ -298,7 +358,7 @@ constexpr int kRV2 = 6;    // pass-2 sums
 
 struct RestrictCtx {
     int nx, r;       // r = members per coarse group
-    const double *h;
+    const double *h, *ihf;
     Level S;         // source level (coefficients + solution)
     Level T;         // target level (written)
 };
@@ -308,8 +368,8 @@ __device__ inline double src_phi_b(const Level &S, int p, int side)
     return side == 0 ? S.phib0[p] : S.phibX[p];
 }
 
-// block (32, KS); grid (ceil((nx+1)/32), n_to)
-__global__ void k_restrict(RestrictCtx x)
+// block (32, KS <= 16); grid (ceil((nx+1)/32), n_to)
+__global__ void __launch_bounds__(512) k_restrict(RestrictCtx x)
 {
     extern __shared__ __align__(16) double rsm[];
     const int tx = threadIdx.x, ty = threadIdx.y, KS = blockDim.y;
@@ -336,7 +396,7 @@ __global__ void k_restrict(RestrictCtx x)
             if (S.fine) {
                 const double *sc = S.sigR + (size_t)p * nx;
                 sR = (i == 0) ? sc[0] : (i == nx) ? sc[nx - 1]
-                     : (sc[i - 1] * x.h[i - 1] + sc[i] * x.h[i]) / (x.h[i - 1] + x.h[i]);
+                     : (sc[i - 1] * x.h[i - 1] + sc[i] * x.h[i]) * x.ihf[i];
             } else {
                 sR = S.sigR[(size_t)p * nf + i];
             }
@@ -396,7 +456,7 @@ __global__ void k_restrict(RestrictCtx x)
             if (S.fine) {
                 const double *sc = S.sigR + (size_t)p * nx;
                 sR = (i == 0) ? sc[0] : (i == nx) ? sc[nx - 1]
-                     : (sc[i - 1] * x.h[i - 1] + sc[i] * x.h[i]) / (x.h[i - 1] + x.h[i]);
+                     : (sc[i - 1] * x.h[i - 1] + sc[i] * x.h[i]) * x.ihf[i];
             } else {
                 sR = S.sigR[fp];
             }
@@ -452,6 +512,134 @@ __global__ void k_restrict(RestrictCtx x)
             (T.CX)[P] = Cb;
             (T.EinX)[P] = v[16];
             (T.FinX)[P] = v[17];
+        }
+    }
+}
+
+// Two-stage restriction for wide coarse groups (r >= 64 members): stage 1 sums chunks of
+// kChunk members per (coarse group, cell / face) into partial vectors with many CTAs;
+// stage 2 adds the chunks in a fixed order and forms the coefficients.  The compensation
+// is summed in one pass, xi = dx (sum sigR F - sigR-bar sum F) + c (sum etaR E_R -
+// sum etaL E_L), which is the two-pass sum up to rounding relative to the sigR dx F terms.
+constexpr int kChunk = 32;
+constexpr int kRP = 25;
+
+struct Restrict2Ctx {
+    int nx, r, nchunk;
+    const double *h, *ihf;
+    Level S, T;
+    double *part;   // [n_to][nchunk][kRP][nx+1]
+};
+
+// block (32, 4); grid (ceil((nx+1)/32), n_to * nchunk)
+__global__ void __launch_bounds__(128) k_restrict_part(Restrict2Ctx x)
+{
+    __shared__ double red[4][32][kRP + 1];
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int nx = x.nx, nf = nx + 1;
+    const int i = blockIdx.x * 32 + tx;
+    const int P = blockIdx.y / x.nchunk, ch = blockIdx.y - P * x.nchunk;
+    const int pb = P * x.r + ch * kChunk;
+    const int pe = min(pb + kChunk, P * x.r + x.r);
+    const Level &S = x.S;
+    double v[kRP];
+#pragma unroll
+    for (int k = 0; k < kRP; ++k) v[k] = 0.0;
+    for (int p = pb + ty; p < pe; p += 4) {
+        if (i < nx) {
+            const size_t c = (size_t)p * nx + i;
+            const double E = S.E[c], ph = S.phi[c], sg = S.sig[c];
+            v[0] += ph * E; v[1] += ph; v[2] += sg * E; v[3] += sg;
+            v[4] += S.emis[c]; v[5] += S.Eold[c]; v[6] += E;
+        }
+        if (i <= nx) {
+            const size_t fp = (size_t)p * nf + i;
+            const double Fp = S.F[fp];
+            double sR;
+            if (S.fine) {
+                const double *sc = S.sigR + (size_t)p * nx;
+                sR = (i == 0) ? sc[0] : (i == nx) ? sc[nx - 1]
+                     : (sc[i - 1] * x.h[i - 1] + sc[i] * x.h[i]) * x.ihf[i];
+            } else {
+                sR = S.sigR[fp];
+            }
+            const double ER = (i == nx) ? S.EbX[p] : S.E[(size_t)p * nx + i];
+            const double EL = (i == 0) ? S.Eb0[p] : S.E[(size_t)p * nx + i - 1];
+            const double wF = fabs(Fp) + 1e-6 * kC * 0.5 * (EL + ER);
+            v[7] += sR * wF; v[8] += sR; v[9] += wF; v[10] += sR * Fp; v[11] += Fp;
+            if (!S.fine) {
+                v[12] += S.etaR[fp] * ER;
+                v[13] += S.etaL[fp] * EL;
+            }
+            v[14] += ER; v[15] += EL; v[16] += S.Fold[fp];
+        }
+        if (i == 0 || i == nx) {
+            const int side = (i == 0) ? 0 : 1;
+            const double Eb = side == 0 ? S.Eb0[p] : S.EbX[p];
+            const double Ein = side == 0 ? S.Ein0[p] : S.EinX[p];
+            const double Fin = side == 0 ? S.Fin0[p] : S.FinX[p];
+            const double Cb = side == 0 ? S.C0[p] : S.CX[p];
+            const double ph = side == 0 ? S.phib0[p] : S.phibX[p];
+            const double Eo = Eb - Ein;
+            v[17] += ph * Eb; v[18] += ph; v[19] += Eb;
+            v[20] += Cb * Eo; v[21] += Cb; v[22] += Eo;
+            v[23] += Ein; v[24] += Fin;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < kRP; ++k) red[ty][tx][k] = v[k];
+    __syncthreads();
+    if (ty == 0 && i <= nx) {
+        for (int y = 1; y < 4; ++y)
+#pragma unroll
+            for (int k = 0; k < kRP; ++k) v[k] += red[y][tx][k];
+        double *o = x.part + ((size_t)(P * x.nchunk + ch) * kRP) * nf + i;
+#pragma unroll
+        for (int k = 0; k < kRP; ++k) o[(size_t)k * nf] = v[k];
+    }
+}
+
+// block 32; grid (ceil((nx+1)/32), n_to)
+__global__ void k_restrict_final(Restrict2Ctx x)
+{
+    const int nx = x.nx, nf = nx + 1;
+    const int i = blockIdx.x * 32 + threadIdx.x;
+    const int P = blockIdx.y;
+    if (i > nx) return;
+    double v[kRP];
+#pragma unroll
+    for (int k = 0; k < kRP; ++k) v[k] = 0.0;
+    for (int ch = 0; ch < x.nchunk; ++ch) {
+        const double *o = x.part + ((size_t)(P * x.nchunk + ch) * kRP) * nf + i;
+#pragma unroll
+        for (int k = 0; k < kRP; ++k) v[k] += o[(size_t)k * nf];
+    }
+    const double rn = (double)x.r;
+    Level &T = x.T;
+    if (i < nx) {
+        const size_t c = (size_t)P * nx + i;
+        T.phi[c] = (v[6] != 0.0) ? v[0] / v[6] : v[1] / rn;
+        T.sig[c] = (v[6] != 0.0) ? v[2] / v[6] : v[3] / rn;
+        T.emis[c] = v[4];
+        T.Eold[c] = v[5];
+        T.Esum[c] = v[6];
+    }
+    const double dxf = (i == 0) ? 0.5 * x.h[0] : (i == nx) ? 0.5 * x.h[nx - 1]
+                                            : 0.5 * (x.h[i - 1] + x.h[i]);
+    const double sRP = (v[9] != 0.0) ? v[7] / v[9] : v[8] / rn;
+    const double xi = dxf * (v[10] - sRP * v[11]) + kC * (v[12] - v[13]);
+    const size_t f = (size_t)P * nf + i;
+    T.sigR[f] = sRP;
+    T.etaR[f] = (xi > 0.0 && v[14] != 0.0) ? xi / (kC * v[14]) : 0.0;
+    T.etaL[f] = (xi < 0.0 && v[15] != 0.0) ? -xi / (kC * v[15]) : 0.0;
+    T.Fold[f] = v[16];
+    if (i == 0 || i == nx) {
+        const double phb = (v[19] != 0.0) ? v[17] / v[19] : v[18] / rn;
+        const double Cb = (v[22] != 0.0) ? v[20] / v[22] : v[21] / rn;
+        if (i == 0) {
+            T.phib0[P] = phb; T.C0[P] = Cb; T.Ein0[P] = v[23]; T.Fin0[P] = v[24];
+        } else {
+            T.phibX[P] = phb; T.CX[P] = Cb; T.EinX[P] = v[23]; T.FinX[P] = v[24];
         }
     }
 }
@@ -517,12 +705,13 @@ __global__ void __launch_bounds__(1024) k_grey(GreyCtx x)
         a.T_prev_out[i] = Ts;
     }
     __syncthreads();
-    if (threadIdx.x < 32) {
-        LoCtx lc = x.lo;
-        lc.a_cell = sa;
-        lc.s_cell = ss;
-        warp_lo_solve<double>(lc, 0, wsm, x.mmax);
-    }
+    LoCtx lc = x.lo;
+    lc.a_cell = sa;
+    lc.s_cell = ss;
+    const bool staged = nx >= 2;
+    if (staged) lo_stage<double>(lc, 0, wsm, x.mmax, threadIdx.x, blockDim.x);
+    __syncthreads();
+    if (threadIdx.x < 32) warp_lo_solve<double>(lc, 0, wsm, x.mmax, staged);
     __syncthreads();
     double dTc = 0, Tm = 0, dEc = 0, Em = 0, dTp = 0, dEp = 0, bad = 0;
     for (int i = threadIdx.x; i < nx; i += blockDim.x) {
@@ -570,16 +759,18 @@ __global__ void k_group_sum(int n, int nx, const double *__restrict__ X, double 
 cudaError_t launch_lo_solve(const Problem &p, double dt, const Level &L)
 {
     LoCtx x;
-    x.nx = p.nx; x.dt = dt; x.icdt = 1.0 / (kC * dt); x.h = p.h; x.L = L;
+    x.nx = p.nx; x.dt = dt; x.icdt = 1.0 / (kC * dt); x.h = p.h; x.ihf = p.ihf; x.L = L;
     x.a_cell = nullptr; x.s_cell = nullptr;
     const int mmax = lo_mmax(p.nx);
-    const size_t rsz = (p.precision == TRT_FP64) ? sizeof(double) : sizeof(float);
-    const size_t per_warp = 3 * 32 * (size_t)mmax * rsz;
+    const size_t rsz = lo_fp32(p.precision) ? sizeof(float) : sizeof(double);
+    const size_t per_warp = 6 * 32 * (size_t)mmax * rsz;
+    // at least ~2 CTAs per SM when there are enough systems, and <= 96 KB per CTA
     int W = (int)std::max<size_t>(1, std::min<size_t>(8, (96 * 1024) / per_warp));
+    W = std::max(1, std::min(W, L.n / (2 * 152)));
     const size_t sm = per_warp * W;
     const unsigned nb = (unsigned)((L.n + W - 1) / W);
     cudaError_t e;
-    if (p.precision == TRT_FP64) {
+    if (!lo_fp32(p.precision)) {
         e = cudaFuncSetAttribute(k_lo_solve<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)sm);
         if (e != cudaSuccess) return e;
@@ -593,16 +784,38 @@ cudaError_t launch_lo_solve(const Problem &p, double dt, const Level &L)
     return cudaGetLastError();
 }
 
+size_t restrict_scratch_doubles(int nx, int n_from, int n_to)
+{
+    const int r = n_from / n_to;
+    if (r < 64) return 0;
+    const int nchunk = (r + kChunk - 1) / kChunk;
+    return (size_t)n_to * nchunk * kRP * (nx + 1);
+}
+
 cudaError_t launch_restrict(const Problem &p, const Level &src, Level &dst)
 {
+    const size_t need = restrict_scratch_doubles(p.nx, src.n, dst.n);
+    if (need > 0 && p.rscratch && need <= p.rscratch_doubles) {
+        Restrict2Ctx y;
+        y.nx = p.nx; y.r = src.n / dst.n; y.nchunk = (y.r + kChunk - 1) / kChunk;
+        y.h = p.h; y.ihf = p.ihf; y.S = src; y.T = dst; y.part = p.rscratch;
+        dim3 g1((p.nx + 1 + 31) / 32, dst.n * y.nchunk);
+        k_restrict_part<<<g1, dim3(32, 4), 0, p.stream>>>(y);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        k_restrict_final<<<dim3((p.nx + 1 + 31) / 32, dst.n), 32, 0, p.stream>>>(y);
+        return cudaGetLastError();
+    }
     RestrictCtx x;
-    x.nx = p.nx; x.r = src.n / dst.n; x.h = p.h; x.S = src; x.T = dst;
+    x.nx = p.nx; x.r = src.n / dst.n; x.h = p.h; x.ihf = p.ihf; x.S = src; x.T = dst;
     int KS = 1;
-    while (KS < 8 && KS * 4 <= x.r) KS *= 2;
-    if (x.r >= 64) KS = 8;
+    while (KS < 16 && KS * 4 <= x.r) KS *= 2;   // <= 512 threads: the register file holds them
     dim3 block(32, KS);
     dim3 grid((p.nx + 1 + 31) / 32, dst.n);
     size_t sm = (KS > 1) ? sizeof(double) * KS * 32 * kRV1 : 0;
+    cudaError_t e = cudaFuncSetAttribute(k_restrict, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)sm);
+    if (e != cudaSuccess) return e;
     k_restrict<<<grid, block, sm, p.stream>>>(x);
     return cudaGetLastError();
 }
@@ -610,12 +823,13 @@ cudaError_t launch_restrict(const Problem &p, const Level &src, Level &dst)
 cudaError_t launch_grey(const Problem &p, const Level &g, const GreyArgs &a)
 {
     GreyCtx x;
-    x.lo.nx = p.nx; x.lo.dt = a.dt; x.lo.icdt = 1.0 / (kC * a.dt); x.lo.h = p.h; x.lo.L = g;
+    x.lo.nx = p.nx; x.lo.dt = a.dt; x.lo.icdt = 1.0 / (kC * a.dt); x.lo.h = p.h; x.lo.ihf = p.ihf;
+    x.lo.L = g;
     x.lo.a_cell = nullptr; x.lo.s_cell = nullptr;
     x.a = a;
     x.mmax = lo_mmax(p.nx);
     int bs = std::min(1024, std::max(32, (p.nx + 31) / 32 * 32));
-    size_t sm = sizeof(double) * (3 * (size_t)p.nx + 32 + 3 * 32 * (size_t)x.mmax);
+    size_t sm = sizeof(double) * (3 * (size_t)p.nx + 32 + 6 * 32 * (size_t)x.mmax);
     cudaError_t e = cudaFuncSetAttribute(k_grey, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)sm);
     if (e != cudaSuccess) return e;

@@ -48,8 +48,8 @@ int trt_sweep_noalloc(int nx, int N, int G, int precision, double dt, const doub
                       const void *I_old, void *I_new, double *f, double *fb0, double *fbX,
                       double *C0, double *CX, void *stream)
 {
-    if (nx < 1 || nx > 8192 || N < 1 || N > 256 || G < 1 || !(dt > 0) ||
-        (precision != TRT_FP64 && precision != TRT_MIXED))
+    if (nx < 1 || nx > 2048 || N < 1 || N > 256 || G < 1 || !(dt > 0) ||
+        precision < 0 || precision > TRT_MIXED)
         return noalloc_fail(TRT_EINVAL, "trt_sweep_noalloc: bad sizes or precision");
     if (!h || !mu || !w || !Iin0 || !IinX || !sigE || !emis || !I_old || !I_new || !f || !fb0 ||
         !fbX || !C0 || !CX)
@@ -91,7 +91,7 @@ int trt_sweep_noalloc(int nx, int N, int G, int precision, double dt, const doub
     p.IinX = const_cast<double *>(IinX);
     double *part = scratch;
     double *psi_exit = scratch + sweep_partial_doubles(p);
-    e = launch_sweep(p, dt, sigE, emis, I_old, I_new, part, psi_exit, f, fb0, fbX, C0, CX);
+    e = launch_sweep(p, dt, sigE, emis, false, I_old, I_new, part, psi_exit, f, fb0, fbX, C0, CX);
     if (e != cudaSuccess) return noalloc_fail(TRT_ECUDA, cudaGetErrorString(e));
     return TRT_OK;
 }

@@ -51,7 +51,8 @@ void gauss_legendre_host(int n, double *x, double *w)
 static SeriesTables build_tables()
 {
     SeriesTables t{};
-    gauss_legendre_host(8, t.gx, t.gw);
+    gauss_legendre_host(4, t.g4x, t.g4w);
+    gauss_legendre_host(6, t.g6x, t.g6w);
     typedef long double LD;
     // c_n = B_n/n!: reciprocal of (e^t-1)/t = sum_k t^k/(k+1)!
     LD c[kSer], fact[kSer + 2];
@@ -162,31 +163,65 @@ __host__ __device__ inline void edge_tail(double x, double &TP, double &TN, doub
     TN = x * x * x * x / (-expm1(-x));
 }
 
+// Gauss rule on [xa, xb] for the three scaled integrands x^3 e^{xa-x}/(1-e^{-x}),
+// x^4 e^{xa-x}/(1-e^{-x})^2, x^7 e^{xa-x}/(1-e^{-x})^3.  Their nearest singularities
+// are the poles x = 2 pi i k, so an n-point rule on a half-width a converges like
+// (a/4 pi)^(2n): 4 points reach 1e-16 for xb - xa <= 1/4, 6 points for xb - xa <= 1.
+template <int NP>
+__host__ __device__ inline void gauss_group(double xa, double xb, const double *gx,
+                                            const double *gw, double &dPs, double &Ns,
+                                            double &Ds)
+{
+    // symmetric rule: the points mid -/+ hw xi_j share e^{xa-mid} and e^{+-hw xi_j}, so a
+    // pair of points costs one exponential and one reciprocal; e^{-x} follows from
+    // e^{-mid} the same way, and 1 - e^{-x} is formed directly where x >= 0.1 (relative
+    // error <= eps/x) and by expm1 below
+    const double hw = 0.5 * (xb - xa), mid = 0.5 * (xb + xa);
+    const double E0 = exp(xa - mid);
+    const bool warm = mid - hw < 37.0;              // some point has 1 - e^{-x} != 1
+    const double Em = warm ? exp(-mid) : 0.0;
+    double sp = 0.0, sn = 0.0, sd = 0.0;
+#pragma unroll
+    for (int j = NP / 2; j < NP; ++j) {
+        const double t = hw * gx[j];
+        const double ep = exp(t), em = rcp64(ep);
+#pragma unroll
+        for (int side = 0; side < 2; ++side) {
+            const double x = side ? mid + t : mid - t;
+            const double ex = side ? E0 * em : E0 * ep;          // e^{xa - x}
+            double u = 1.0;                                       // 1/(1 - e^{-x})
+            if (warm && x <= 37.0) {
+                const double omx = (x >= 0.1) ? 1.0 - Em * (side ? em : ep) : -expm1(-x);
+                u = rcp64(omx);
+            }
+            const double x3 = x * x * x;
+            const double eu = gw[j] * ex * x3 * u;
+            sp += eu;
+            sn += eu * x * u;
+            sd += eu * x3 * x * u * u;
+        }
+    }
+    dPs = hw * sp;
+    Ns = hw * sn;
+    Ds = hw * sd;
+}
+
 // e^{xa} [P]_{xa}^{xb}, e^{xa} [Nt]_{xa}^{xb}, e^{xa} [D]_{xa}^{xb}, and 1 - e^{-(xb-xa)}.
-// Narrow groups (xb - xa <= 1) integrate the three integrands directly with the 8-point
-// Gauss rule (the differences of edge values would cancel); wide groups difference the
-// closed forms.  Scaled integrands: x^3 e^{xa-x}/(1-e^{-x}), x^4 e^{xa-x}/(1-e^{-x})^2,
-// x^7 e^{xa-x}/(1-e^{-x})^3.
+// Narrow groups -- xb - xa <= 1 and <= xa/4, where differences of edge values would
+// cancel -- integrate the three integrands directly with a Gauss rule (over such a group
+// the x^7 factor varies by at most (5/4)^7 and the rest is analytic within 2 pi);
+// every other group differences the closed forms.
 __host__ __device__ inline void group_integrals(double xa, double xb, bool binf,
                                                 const SeriesTables &t, double &dPs,
                                                 double &Ns, double &Ds, double &om)
 {
     om = binf ? 1.0 : -expm1(-(xb - xa));
-    if (!binf && xb - xa <= 1.0) {
-        const double hw = 0.5 * (xb - xa), mid = 0.5 * (xb + xa);
-        double sp = 0.0, sn = 0.0, sd = 0.0;
-        for (int j = 0; j < 8; ++j) {
-            const double x = mid + hw * t.gx[j];
-            const double u = 1.0 / (-expm1(-x));
-            const double e = exp(xa - x) * t.gw[j];
-            const double x3 = x * x * x;
-            sp += e * x3 * u;
-            sn += e * x3 * x * u * u;
-            sd += e * x3 * x3 * x * u * u * u;
-        }
-        dPs = hw * sp;
-        Ns = hw * sn;
-        Ds = hw * sd;
+    const double w = xb - xa;
+    if (!binf && w <= 0.25 * xa && w <= 1.0) {
+        if (w <= 0.25)
+            gauss_group<4>(xa, xb, t.g4x, t.g4w, dPs, Ns, Ds);
+        else
+            gauss_group<6>(xa, xb, t.g6x, t.g6w, dPs, Ns, Ds);
         return;
     }
     if (xa >= kXSplit) {
@@ -241,33 +276,47 @@ __global__ void __launch_bounds__(256) k_opacity(int nx, int G, const double *__
                                                  const double *__restrict__ edges, double s,
                                                  double *__restrict__ sigE,
                                                  double *__restrict__ emis,
-                                                 double *__restrict__ sigR)
+                                                 double *__restrict__ sigR,
+                                                 float *__restrict__ sig32,
+                                                 float *__restrict__ emis32,
+                                                 const double *__restrict__ h, double icdt)
 {
     long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (long)G * nx) return;
     int g = (int)(idx / nx);
     int i = (int)(idx - (long)g * nx);
-    double Ti = T[i];
-    double xa = edges[g] / Ti;
-    double eb = edges[g + 1];
-    bool binf = isinf(eb);
-    double xb = binf ? 0.0 : eb / Ti;
+    const double Ti = T[i];
+    const double iT = rcp64(Ti);
+    const double xa = edges[g] * iT;
+    const double eb = edges[g + 1];
+    const bool binf = isinf(eb);
+    const double xb = binf ? 0.0 : eb * iT;
     double dPs, Ns, Ds, om;
     group_integrals(xa, xb, binf, c_ser, dPs, Ns, Ds, om);
     double T3 = Ti * Ti * Ti;
     double k27 = 27.0 * s;
-    sigE[idx] = k27 * om / (T3 * dPs);
-    emis[idx] = k27 * kCB * Ti * exp(-xa) * om;
-    sigR[idx] = k27 * Ns / (T3 * Ds);
+    const double iT3 = rcp64(T3);
+    const double sg = k27 * om * iT3 * rcp64(dPs);
+    const double em = k27 * kCB * Ti * exp(-xa) * om;
+    sigE[idx] = sg;
+    emis[idx] = em;
+    sigR[idx] = k27 * Ns * iT3 * rcp64(Ds);
+    if (sig32) {   // FP32 sweep inputs: sigma_t h/2 and h e/2, one rounding each
+        const double hh = 0.5 * h[i];
+        sig32[idx] = (float)(hh * (sg + icdt));
+        emis32[idx] = (float)(hh * em);
+    }
 }
 
 cudaError_t launch_opacity(const Problem &p, const double *T, double *sigE, double *emis,
-                           double *sigR)
+                           double *sigR, float *sig32, float *emis32, double dt)
 {
+    const double icdt = (dt > 0) ? 1.0 / (kC * dt) : 0.0;
     long n = (long)p.G * p.nx;
     int bs = 256;
     long nb = (n + bs - 1) / bs;
-    k_opacity<<<(unsigned)nb, bs, 0, p.stream>>>(p.nx, p.G, T, p.edges, p.s, sigE, emis, sigR);
+    k_opacity<<<(unsigned)nb, bs, 0, p.stream>>>(p.nx, p.G, T, p.edges, p.s, sigE, emis, sigR,
+                                                 sig32, emis32, p.h, icdt);
     return cudaGetLastError();
 }
 

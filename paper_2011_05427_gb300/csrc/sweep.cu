@@ -15,8 +15,10 @@
 // A CTA owns 32 consecutive groups (the lanes: the intensity layout [M][nx][2][ldG] makes
 // each warp's corner load one contiguous 128/256-byte line) and D directions of one sign
 // (one per warp), so all its warps walk the cells in the same order.  Cells go in strips
-// of S: the strip's sigma_t h/2 and (h/2) e_g (read once per CTA from the [G][nx] fields,
-// coalesced along cells) are staged in shared memory; each warp sweeps the strip and
+// of S: while a strip is swept, cp.async copies the next strip -- each warp's intensity
+// tile and the CTA's sigma_E, e_g rows -- into the other half of a double buffer, so the
+// serial recurrence never waits on global memory.  Each strip's sigma_t h/2 and
+// (h/2) e_g are tabulated once per CTA in shared memory; each warp sweeps the strip and
 // leaves psi_L + psi_R in shared memory; the CTA then reduces its D directions into the
 // two angular moments per (cell, group) -- the cross-direction reduction costs one
 // __syncthreads per strip, not one per cell.  Partial moments of the 2N/D direction tiles
@@ -27,17 +29,19 @@ namespace trt {
 
 namespace {
 
-constexpr int kStrip = 32;
+constexpr int kStrip = 16;
 constexpr int kPadG = 33;   // padded group stride of the strip tables (bank conflicts)
 
 struct SweepArgs {
     int nx, N, G, ldG, D;
     double icdt;
-    const double *h, *mu, *w, *Iin0, *IinX, *sigE, *emis;
+    const double *h, *mu, *w, *Iin0, *IinX;
+    const void *sigE, *emis;   // [G][nx], SR-typed
     const void *I_old;
     void *I_new;
-    double *part;       // [n_dt][2][G][nx]
-    double *psi_exit;   // [M][ldG]
+    void *part;       // [n_dt][2][G][nx], R-typed
+    void *psi_exit;   // [M][ldG], R-typed
+    double *f, *fb0, *fbX, *C0, *CX;
 };
 
 template <typename R>
@@ -57,18 +61,73 @@ struct Acc {   // per-tile angular sum: plain in FP64, compensated (Kahan) in FP
     }
 };
 
+// 1/d.  FP32: the correctly rounded reciprocal.  FP64: one Newton-Raphson step
+// x1 = x0 (2 - d x0) from the correctly rounded FP32 reciprocal x0; the relative error
+// squares, to about (2^-24)^2 plus rounding (~4e-15), at 4 FP64 operations instead of the
+// ~20 of an IEEE division -- FP64 issue rate is the bound of the FP64 sweep on GB300.
 template <typename R>
-__global__ void __launch_bounds__(512) k_sweep(SweepArgs a)
+__device__ inline R recip(R d);
+template <>
+__device__ inline float recip<float>(float d) { return __frcp_rn(d); }
+template <>
+__device__ inline double recip<double>(double d)
 {
+    const double x0 = (double)__frcp_rn((float)d);
+    return x0 * fma(-d, x0, 2.0);
+}
+
+// cp.async (global -> shared, completion per issuing thread): the next strip's data is
+// in flight while the current strip is swept.
+template <int B>
+__device__ inline void cp_async(void *smem, const void *gmem)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(s), "l"(gmem), "n"(B));
+}
+__device__ inline void cp_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ inline void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
+// shared-memory carve-up of k_sweep (byte offsets, 16-byte aligned sections)
+template <typename R, typename SR>
+struct SweepSmem {
+    size_t itile, rawS, rawE, sth, sq, skap, ps, swt, total;
+    __host__ __device__ SweepSmem(int D)
+    {
+        auto al = [](size_t x) { return (x + 15) / 16 * 16; };
+        size_t o = 0;
+        itile = o; o = al(o + sizeof(R) * 2 * (size_t)D * kStrip * 2 * 32);
+        rawS = o;  o = al(o + sizeof(SR) * 2 * kStrip * kPadG);
+        rawE = o;  o = al(o + sizeof(SR) * 2 * kStrip * kPadG);
+        sth = o;   o = al(o + sizeof(R) * kStrip * kPadG);
+        sq = o;    o = al(o + sizeof(R) * kStrip * kPadG);
+        skap = o;  o = al(o + sizeof(R) * kStrip);
+        ps = o;    o = al(o + sizeof(R) * (size_t)D * kStrip * kPadG);
+        swt = o;   o = al(o + sizeof(R) * 2 * D);
+        total = o;
+    }
+};
+
+// R: arithmetic and intensity type; SR: type of the fields read.  SR = double: the fields
+// are sigma_E and e_g, tabulated per strip as sigma_t h/2 and h e/2 (FP64, one rounding);
+// SR = float: the fields already are sigma_t h/2 and h e/2 in FP32 (written by the opacity
+// kernel with one rounding each) and are used as staged.
+template <typename R, typename SR>
+__global__ void __launch_bounds__(256) k_sweep(SweepArgs a)
+{
+    constexpr bool kPre = sizeof(SR) == 4;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int D = a.D;
-    R *sth = reinterpret_cast<R *>(smem_raw);   // [S][33] sigma_t h / 2
-    R *sq = sth + kStrip * kPadG;                 // [S][33] (h/2) e_g
-    R *skap = sq + kStrip * kPadG;                // [S]     h / (2 c dt)
-    R *ps = skap + kStrip;                        // [D][S][33] psi_L + psi_R
-    const size_t off_w = (sizeof(R) * (2 * kStrip * kPadG + kStrip + D * kStrip * kPadG) + 15) / 16 * 16;
-    double *swt = reinterpret_cast<double *>(smem_raw + off_w);   // [D] w/2
-    double *swm = swt + D;                                        // [D] w mu^2/2
+    const SweepSmem<R, SR> L(D);
+    R *itile = reinterpret_cast<R *>(smem_raw + L.itile);      // [2][D][S][2][32]
+    SR *rawS = reinterpret_cast<SR *>(smem_raw + L.rawS);      // [2][S][33] sigma_E
+    SR *rawE = reinterpret_cast<SR *>(smem_raw + L.rawE);      // [2][S][33] e_g
+    R *sth = reinterpret_cast<R *>(smem_raw + L.sth);          // [S][33] sigma_t h / 2
+    R *sq = reinterpret_cast<R *>(smem_raw + L.sq);            // [S][33] (h/2) e_g
+    R *skap = reinterpret_cast<R *>(smem_raw + L.skap);        // [S]     h / (2 c dt)
+    R *ps = reinterpret_cast<R *>(smem_raw + L.ps);            // [D][S][33] psi_L + psi_R
+    R *swt = reinterpret_cast<R *>(smem_raw + L.swt);          // [D] w/2
+    R *swm = swt + D;                                          // [D] w mu^2/2
 
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
@@ -83,14 +142,17 @@ __global__ void __launch_bounds__(512) k_sweep(SweepArgs a)
 
     const R *__restrict__ Iold = reinterpret_cast<const R *>(a.I_old);
     R *__restrict__ Inew = reinterpret_cast<R *>(a.I_new);
+    const SR *__restrict__ sigE = reinterpret_cast<const SR *>(a.sigE);
+    const SR *__restrict__ emis = reinterpret_cast<const SR *>(a.emis);
+    R *part = reinterpret_cast<R *>(a.part);
 
     const double mu_d = a.mu[m];
     const R am = (R)fabs(mu_d);
     const R b = (R)(0.5 * fabs(mu_d));
     const R bb = b * b;
     if (lane == 0) {
-        swt[warp] = 0.5 * a.w[m];
-        swm[warp] = 0.5 * a.w[m] * mu_d * mu_d;
+        swt[warp] = (R)(0.5 * a.w[m]);
+        swm[warp] = (R)(0.5 * a.w[m] * mu_d * mu_d);
     }
     R psi_in = (g < G) ? (R)(pos ? a.Iin0[g] : a.IinX[g]) : (R)0;
 
@@ -99,43 +161,76 @@ __global__ void __launch_bounds__(512) k_sweep(SweepArgs a)
     const R *Iold_m = Iold + (size_t)m * nx * dstride + g;
     R *Inew_m = Inew + (size_t)m * nx * dstride + g;
 
-    for (int st = 0; st < nstrip; ++st) {
-        int c0, ns;
+    auto range = [&](int st, int &c0, int &ns) {
         if (pos) {
             c0 = st * kStrip;
             ns = min(kStrip, nx - c0);
         } else {
-            int c1 = nx - st * kStrip;
+            const int c1 = nx - st * kStrip;
             c0 = max(c1 - kStrip, 0);
             ns = c1 - c0;
         }
-        __syncthreads();   // previous strip's tables are no longer read
+    };
+    auto prefetch = [&](int st, int bf) {
+        int c0, ns;
+        range(st, c0, ns);
+        R *it = itile + ((size_t)bf * D + warp) * kStrip * 64 + lane;
+        for (int cc = 0; cc < ns; ++cc) {
+            cp_async<sizeof(R)>(it + cc * 64, Iold_m + (size_t)(c0 + cc) * dstride);
+            cp_async<sizeof(R)>(it + cc * 64 + 32, Iold_m + (size_t)(c0 + cc) * dstride + ldG);
+        }
+        SR *rs = rawS + bf * kStrip * kPadG, *re = rawE + bf * kStrip * kPadG;
         for (int idx = tid; idx < 32 * kStrip; idx += nthr) {
-            int gl = idx / kStrip, cc = idx - gl * kStrip;
-            if (cc < ns) {
-                int gg = gt * 32 + gl, i = c0 + cc;
-                double hi = a.h[i];
-                double sg = 0.0, e = 0.0;
-                if (gg < G) {
-                    sg = a.sigE[(size_t)gg * nx + i];
-                    e = a.emis[(size_t)gg * nx + i];
-                }
-                sth[cc * kPadG + gl] = (R)(0.5 * hi * (sg + a.icdt));
-                sq[cc * kPadG + gl] = (R)(0.5 * hi * e);
-                if (gl == 0) skap[cc] = (R)(0.5 * hi * a.icdt);
+            const int gl = idx / kStrip, cc = idx - gl * kStrip;
+            const int gg = gt * 32 + gl;
+            if (cc < ns && gg < G) {
+                cp_async<sizeof(SR)>(rs + cc * kPadG + gl, sigE + (size_t)gg * nx + c0 + cc);
+                cp_async<sizeof(SR)>(re + cc * kPadG + gl, emis + (size_t)gg * nx + c0 + cc);
+            } else {
+                rs[cc * kPadG + gl] = (SR)0;
+                re[cc * kPadG + gl] = (SR)0;
             }
         }
+        cp_commit();
+    };
+
+    prefetch(0, 0);
+    for (int st = 0; st < nstrip; ++st) {
+        const int bf = st & 1;
+        int c0, ns;
+        range(st, c0, ns);
+        if (st + 1 < nstrip)
+            prefetch(st + 1, bf ^ 1);
+        else
+            cp_commit();   // empty group keeps the wait count uniform
+        cp_wait<1>();      // this thread's copies of strip st have landed
+        __syncthreads();   // ... and everyone's; the previous strip is fully consumed
+        const SR *rs = rawS + bf * kStrip * kPadG, *re = rawE + bf * kStrip * kPadG;
+        if (!kPre) {
+            for (int idx = tid; idx < 32 * kStrip; idx += nthr) {
+                const int gl = idx / kStrip, cc = idx - gl * kStrip;
+                if (cc < ns) {
+                    const double hh = 0.5 * a.h[c0 + cc];
+                    sth[cc * kPadG + gl] = (R)(hh * ((double)rs[cc * kPadG + gl] + a.icdt));
+                    sq[cc * kPadG + gl] = (R)(hh * (double)re[cc * kPadG + gl]);
+                }
+            }
+        }
+        if (tid < ns) skap[tid] = (R)(0.5 * a.h[c0 + tid] * a.icdt);
         __syncthreads();
+        const R *tth = kPre ? reinterpret_cast<const R *>(rs) : sth;
+        const R *tq = kPre ? reinterpret_cast<const R *>(re) : sq;
+        const R *it = itile + ((size_t)bf * D + warp) * kStrip * 64 + lane;
         R *psw = ps + warp * kStrip * kPadG;
 #pragma unroll 4
         for (int kk = 0; kk < ns; ++kk) {
             const int cc = pos ? kk : ns - 1 - kk;
             const int i = c0 + cc;
-            const R IL = Iold_m[(size_t)i * dstride];
-            const R IR = Iold_m[(size_t)i * dstride + ldG];
-            const R aa = b + sth[cc * kPadG + lane];
-            const R inv = (R)1 / (aa * aa + bb);
-            const R q = sq[cc * kPadG + lane];
+            const R IL = it[cc * 64];
+            const R IR = it[cc * 64 + 32];
+            const R aa = b + tth[cc * kPadG + lane];
+            const R inv = recip<R>(aa * aa + bb);
+            const R q = tq[cc * kPadG + lane];
             const R kap = skap[cc];
             R pL, pR;
             if (pos) {
@@ -158,47 +253,48 @@ __global__ void __launch_bounds__(512) k_sweep(SweepArgs a)
         __syncthreads();
         // angular moments of this tile: sum_d (w/2)(psi_L+psi_R), sum_d (w mu^2/2)(psi_L+psi_R)
         for (int idx = tid; idx < 32 * kStrip; idx += nthr) {
-            int gl = idx / kStrip, cc = idx - gl * kStrip;
-            int gg = gt * 32 + gl;
+            const int gl = idx / kStrip, cc = idx - gl * kStrip;
+            const int gg = gt * 32 + gl;
             if (cc < ns && gg < G) {
                 Acc<R> s0, s2;
                 for (int d = 0; d < D; ++d) {
-                    R v = ps[(d * kStrip + cc) * kPadG + gl];
-                    s0.add((R)swt[d] * v);
-                    s2.add((R)swm[d] * v);
+                    const R v = ps[(d * kStrip + cc) * kPadG + gl];
+                    s0.add(swt[d] * v);
+                    s2.add(swm[d] * v);
                 }
-                size_t o = ((size_t)(dtile * 2 + 0) * G + gg) * nx + c0 + cc;
-                a.part[o] = (double)s0.s;
-                a.part[o + (size_t)G * nx] = (double)s2.s;
+                const size_t o = ((size_t)(dtile * 2 + 0) * G + gg) * nx + c0 + cc;
+                part[o] = s0.s;
+                part[o + (size_t)G * nx] = s2.s;
             }
         }
     }
-    a.psi_exit[(size_t)m * ldG + g] = (double)psi_in;
+    reinterpret_cast<R *>(a.psi_exit)[(size_t)m * ldG + g] = psi_in;
 }
 
-// f_g = sum_t A2 / sum_t A0 per (group, cell); boundary factors per group.
+// f_g = sum_t A2 / sum_t A0 per (group, cell), in R; boundary factors per group in FP64.
+template <typename R>
 __global__ void k_sweep_finalize(int nx, int N, int G, int ldG, int ntile,
-                                 const double *__restrict__ part, const double *__restrict__ mu,
+                                 const R *__restrict__ part, const double *__restrict__ mu,
                                  const double *__restrict__ w, const double *__restrict__ Iin0,
-                                 const double *__restrict__ IinX,
-                                 const double *__restrict__ psi_exit, double *__restrict__ f,
-                                 double *fb0, double *fbX, double *C0, double *CX)
+                                 const double *__restrict__ IinX, const R *__restrict__ psi_exit,
+                                 double *__restrict__ f, double *fb0, double *fbX, double *C0,
+                                 double *CX)
 {
     long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
     const long n = (long)G * nx;
     if (idx < n) {
-        double A0 = 0.0, A2 = 0.0;
+        Acc<R> A0, A2;
         for (int t = 0; t < ntile; ++t) {
-            A0 += part[(size_t)(t * 2 + 0) * n + idx];
-            A2 += part[(size_t)(t * 2 + 1) * n + idx];
+            A0.add(part[(size_t)(t * 2 + 0) * n + idx]);
+            A2.add(part[(size_t)(t * 2 + 1) * n + idx]);
         }
-        f[idx] = (A0 != 0.0) ? A2 / A0 : 1.0 / 3.0;
+        f[idx] = (A0.s != (R)0) ? (double)(A2.s / A0.s) : 1.0 / 3.0;
     }
     if (idx < G) {
         const int g = (int)idx, M = 2 * N;
         double s0 = 0, s2 = 0, h0 = 0, h1 = 0;
         for (int m = 0; m < M; ++m) {   // x = 0: inflow for mu > 0, outflow for mu < 0
-            double psi = (m < N) ? Iin0[g] : psi_exit[(size_t)m * ldG + g];
+            double psi = (m < N) ? Iin0[g] : (double)psi_exit[(size_t)m * ldG + g];
             s0 += w[m] * psi;
             s2 += w[m] * mu[m] * mu[m] * psi;
             if (m >= N) { h0 += w[m] * psi; h1 += w[m] * mu[m] * psi; }
@@ -207,7 +303,7 @@ __global__ void k_sweep_finalize(int nx, int N, int G, int ldG, int ntile,
         C0[g] = (h0 != 0.0) ? h1 / h0 : -0.5;
         s0 = s2 = h0 = h1 = 0;
         for (int m = 0; m < M; ++m) {   // x = X: outflow for mu > 0, inflow for mu < 0
-            double psi = (m < N) ? psi_exit[(size_t)m * ldG + g] : IinX[g];
+            double psi = (m < N) ? (double)psi_exit[(size_t)m * ldG + g] : IinX[g];
             s0 += w[m] * psi;
             s2 += w[m] * mu[m] * mu[m] * psi;
             if (m < N) { h0 += w[m] * psi; h1 += w[m] * mu[m] * psi; }
@@ -217,59 +313,60 @@ __global__ void k_sweep_finalize(int nx, int N, int G, int ldG, int ntile,
     }
 }
 
-int pick_D(int N)
+// directions per CTA: 8 in FP32 (HBM bound: many directions share the staged sigma rows),
+// 4 in FP64 (FP64 issue bound: smaller tiles give more resident CTAs per SM)
+int pick_D(const Problem &p)
 {
-    for (int D = 8; D >= 1; D >>= 1)
-        if (N % D == 0) return D;
+    const int Dmax = sweep_fp32(p.precision) ? 8 : 4;
+    for (int D = Dmax; D >= 1; D >>= 1)
+        if (p.N % D == 0) return D;
     return 1;
+}
+
+template <typename R, typename SR>
+cudaError_t launch_sweep_t(const Problem &p, const SweepArgs &a)
+{
+    const int ntile = p.M / a.D;
+    dim3 grid(ntile, p.ldG / 32);
+    dim3 block(32 * a.D);
+    const size_t sm = SweepSmem<R, SR>(a.D).total;
+    cudaError_t e = cudaFuncSetAttribute(k_sweep<R, SR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)sm);
+    if (e != cudaSuccess) return e;
+    k_sweep<R, SR><<<grid, block, sm, p.stream>>>(a);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const long n = (long)p.G * p.nx;
+    const int bs = 256;
+    k_sweep_finalize<R><<<(unsigned)((n + bs - 1) / bs), bs, 0, p.stream>>>(
+        p.nx, p.N, p.G, p.ldG, ntile, reinterpret_cast<const R *>(a.part), p.mu, p.w, p.Iin0,
+        p.IinX, reinterpret_cast<const R *>(a.psi_exit), a.f, a.fb0, a.fbX, a.C0, a.CX);
+    return cudaGetLastError();
 }
 
 }  // namespace
 
 size_t sweep_partial_doubles(const Problem &p)
 {
-    int D = pick_D(p.N);
-    return (size_t)(p.M / D) * 2 * p.G * p.nx;
+    return (size_t)(p.M / pick_D(p)) * 2 * p.G * p.nx;
 }
 
-cudaError_t launch_sweep(const Problem &p, double dt, const double *sigE, const double *emis,
-                         const void *I_old, void *I_new, double *part, double *psi_exit,
-                         double *f, double *fb0, double *fbX, double *C0, double *CX)
+cudaError_t launch_sweep(const Problem &p, double dt, const void *sigE, const void *emis,
+                         bool sigma_fp32, const void *I_old, void *I_new, double *part,
+                         double *psi_exit, double *f, double *fb0, double *fbX, double *C0,
+                         double *CX)
 {
     SweepArgs a;
     a.nx = p.nx; a.N = p.N; a.G = p.G; a.ldG = p.ldG;
-    a.D = pick_D(p.N);
+    a.D = pick_D(p);
     a.icdt = 1.0 / (kC * dt);
     a.h = p.h; a.mu = p.mu; a.w = p.w; a.Iin0 = p.Iin0; a.IinX = p.IinX;
     a.sigE = sigE; a.emis = emis; a.I_old = I_old; a.I_new = I_new;
     a.part = part; a.psi_exit = psi_exit;
-    const int ntile = p.M / a.D;
-    dim3 grid(ntile, p.ldG / 32);
-    dim3 block(32 * a.D);
-    cudaError_t e;
-    if (p.precision == TRT_FP64) {
-        size_t sm = sizeof(double) * (2 * kStrip * kPadG + kStrip + a.D * kStrip * kPadG);
-        sm = (sm + 15) / 16 * 16 + sizeof(double) * 2 * a.D;
-        e = cudaFuncSetAttribute(k_sweep<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)sm);
-        if (e != cudaSuccess) return e;
-        k_sweep<double><<<grid, block, sm, p.stream>>>(a);
-    } else {
-        size_t sm = sizeof(float) * (2 * kStrip * kPadG + kStrip + a.D * kStrip * kPadG);
-        sm = (sm + 15) / 16 * 16 + sizeof(double) * 2 * a.D;
-        e = cudaFuncSetAttribute(k_sweep<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)sm);
-        if (e != cudaSuccess) return e;
-        k_sweep<float><<<grid, block, sm, p.stream>>>(a);
-    }
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    long n = (long)p.G * p.nx;
-    int bs = 256;
-    k_sweep_finalize<<<(unsigned)((n + bs - 1) / bs), bs, 0, p.stream>>>(
-        p.nx, p.N, p.G, p.ldG, ntile, part, p.mu, p.w, p.Iin0, p.IinX, psi_exit, f, fb0, fbX,
-        C0, CX);
-    return cudaGetLastError();
+    a.f = f; a.fb0 = fb0; a.fbX = fbX; a.C0 = C0; a.CX = CX;
+    if (!sweep_fp32(p.precision)) return launch_sweep_t<double, double>(p, a);
+    if (sigma_fp32) return launch_sweep_t<float, float>(p, a);
+    return launch_sweep_t<float, double>(p, a);
 }
 
 }  // namespace trt

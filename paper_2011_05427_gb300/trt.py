@@ -17,9 +17,10 @@ LIB_PATH = os.path.join(HERE, "libtrt.so")
 
 TRT_OK, TRT_EINVAL, TRT_ENOTCONVERGED, TRT_ENUMERIC, TRT_ETIMEOUT, TRT_ECUDA, TRT_ENOSPACE = \
     0, -1, -2, -3, -4, -5, -6
-TRT_FP64, TRT_MIXED = 0, 1
+TRT_FP64, TRT_SWEEP_FP32, TRT_LO_FP32, TRT_MIXED = 0, 1, 2, 3
 CYCLES = {"V": 0, "W": 1, "F": 2}
-PRECISIONS = {"fp64": TRT_FP64, "mixed": TRT_MIXED}
+PRECISIONS = {"fp64": TRT_FP64, "mixed": TRT_MIXED, "sweep32": TRT_SWEEP_FP32,
+              "lo32": TRT_LO_FP32}
 
 _dp = ctypes.POINTER(ctypes.c_double)
 _vp = ctypes.c_void_p
@@ -265,7 +266,7 @@ class Solver:
         """I_old: [M][nx][2][G] (padded to ldG here); returns I_new [M][nx][2][G], f, fb0,
         fbX, C0, CX as torch tensors."""
         t = self.torch
-        rdt = t.float64 if self.precision == TRT_FP64 else t.float32
+        rdt = t.float32 if self.precision & TRT_SWEEP_FP32 else t.float64
         Ip = t.zeros((self.M, self.nx, 2, self.ldG), dtype=rdt, device=self.device)
         Ip[..., :self.G] = self._t(I_old, rdt)
         In = t.zeros_like(Ip)

@@ -145,16 +145,17 @@ MIXED_CASES = [
 ]
 
 
+@pytest.mark.parametrize("prec", ["sweep32", "lo32", "mixed"])
 @pytest.mark.parametrize("name,cfg,cycle,lmax", MIXED_CASES, ids=[c[0] for c in MIXED_CASES])
-def test_mixed_precision_vs_fp64_oracle(trt, orc, name, cfg, cycle, lmax):
-    """FP32 sweeps and group LOQD, FP64 grey + MEB: error against the FP64 oracle after
-    fixed-iteration steps."""
-    s, o = pair(trt, orc, cfg, precision="mixed")
+def test_mixed_precision_vs_fp64_oracle(trt, orc, name, cfg, cycle, lmax, prec):
+    """FP32 sweeps and/or FP32 group LOQD, FP64 grey + MEB: error against the FP64 oracle
+    after fixed-iteration steps."""
+    s, o = pair(trt, orc, cfg, precision=prec)
     worst = (0.0, 0.0)
     for step in range(3):
         s.step(cfg.dt, cycle, lmax, -1.0, max_outer=3)
         o.step(cfg.dt, cycle, lmax, -1.0, max_outer=3)
         eT, eE, _ = errors(s.moments(), o.state())
         worst = (max(worst[0], eT), max(worst[1], eE))
-    print(f"{name}: mixed vs FP64 oracle: T {worst[0]:.2e}, E_g (energy-weighted) {worst[1]:.2e}")
+    print(f"{name} {prec}: vs FP64 oracle: T {worst[0]:.2e}, E_g (energy-weighted) {worst[1]:.2e}")
     assert worst[0] < 1e-6 and worst[1] < 1e-6
