@@ -21,6 +21,7 @@ struct SeriesTables {
     double pD[kSer];   // D(x)     = x^5 sum pD[n] x^n,   D(x) = int_0^x t^7 e^{2t}/(e^t-1)^3
     double Pinf;       // pi^4/15
     double Dinf;       // 2520 (zeta(6) + zeta(7))
+    double tP[65], tD[65];   // tail coefficients 6/k^4 and 5040 k(k+1)/2 / k^8, k = 1..64
     double g4x[4], g4w[4];   // 4- and 6-point Gauss-Legendre rules on [-1, 1]
     double g6x[6], g6w[6];   // (narrow groups, see group_integrals)
 };

@@ -337,16 +337,20 @@ __device__ void warp_lo_solve(const LoCtx &x, int q, R *sm, int mmax, bool stage
 
 inline int lo_mmax(int nx) { return nx < 2 ? 1 : (nx + (std::min(32, nx / 2)) - 1) / std::min(32, nx / 2) + 1; }
 
+// One system per CTA: all 4 warps stage the rows (phase A: the parallel part, global
+// loads and the face coefficients), then warp 0 runs the elimination.
 template <typename R>
-__global__ void __launch_bounds__(256) k_lo_solve(LoCtx x, int mmax)
+__global__ void __launch_bounds__(128) k_lo_solve(LoCtx x, int mmax)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int W = blockDim.x >> 5;
-    const int warp = threadIdx.x >> 5;
-    const int q = blockIdx.x * W + warp;
-    if (q >= x.L.n) return;
-    R *sm = reinterpret_cast<R *>(smem_raw) + (size_t)warp * 6 * 32 * mmax;
-    warp_lo_solve<R>(x, q, sm, mmax);
+    R *sm = reinterpret_cast<R *>(smem_raw);
+    const int q = blockIdx.x;
+    const bool staged = x.nx >= 2;
+    if (staged) {
+        lo_stage<R>(x, q, sm, mmax, threadIdx.x, blockDim.x);
+        __syncthreads();
+    }
+    if (threadIdx.x < 32) warp_lo_solve<R>(x, q, sm, mmax, staged);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -599,21 +603,26 @@ __global__ void __launch_bounds__(128) k_restrict_part(Restrict2Ctx x)
     }
 }
 
-// block 32; grid (ceil((nx+1)/32), n_to)
-__global__ void k_restrict_final(Restrict2Ctx x)
+// block (32, kRP); grid (ceil((nx+1)/32), n_to): thread (tx, k) adds value k of position
+// tx over the chunks in a fixed order, then row 0 forms the coefficients
+__global__ void __launch_bounds__(32 * kRP) k_restrict_final(Restrict2Ctx x)
 {
+    __shared__ double sv[kRP][33];
     const int nx = x.nx, nf = nx + 1;
-    const int i = blockIdx.x * 32 + threadIdx.x;
+    const int tx = threadIdx.x, k = threadIdx.y;
+    const int i = blockIdx.x * 32 + tx;
     const int P = blockIdx.y;
-    if (i > nx) return;
+    if (i <= nx) {
+        double acc = 0.0;
+        const double *o = x.part + ((size_t)P * x.nchunk * kRP + k) * nf + i;
+        for (int ch = 0; ch < x.nchunk; ++ch) acc += o[(size_t)ch * kRP * nf];
+        sv[k][tx] = acc;
+    }
+    __syncthreads();
+    if (k != 0 || i > nx) return;
     double v[kRP];
 #pragma unroll
-    for (int k = 0; k < kRP; ++k) v[k] = 0.0;
-    for (int ch = 0; ch < x.nchunk; ++ch) {
-        const double *o = x.part + ((size_t)(P * x.nchunk + ch) * kRP) * nf + i;
-#pragma unroll
-        for (int k = 0; k < kRP; ++k) v[k] += o[(size_t)k * nf];
-    }
+    for (int q = 0; q < kRP; ++q) v[q] = sv[q][tx];
     const double rn = (double)x.r;
     Level &T = x.T;
     if (i < nx) {
@@ -763,23 +772,19 @@ cudaError_t launch_lo_solve(const Problem &p, double dt, const Level &L)
     x.a_cell = nullptr; x.s_cell = nullptr;
     const int mmax = lo_mmax(p.nx);
     const size_t rsz = lo_fp32(p.precision) ? sizeof(float) : sizeof(double);
-    const size_t per_warp = 6 * 32 * (size_t)mmax * rsz;
-    // at least ~2 CTAs per SM when there are enough systems, and <= 96 KB per CTA
-    int W = (int)std::max<size_t>(1, std::min<size_t>(8, (96 * 1024) / per_warp));
-    W = std::max(1, std::min(W, L.n / (2 * 152)));
-    const size_t sm = per_warp * W;
-    const unsigned nb = (unsigned)((L.n + W - 1) / W);
+    const size_t sm = 6 * 32 * (size_t)mmax * rsz;
+    const unsigned nb = (unsigned)L.n;
     cudaError_t e;
     if (!lo_fp32(p.precision)) {
         e = cudaFuncSetAttribute(k_lo_solve<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)sm);
         if (e != cudaSuccess) return e;
-        k_lo_solve<double><<<nb, 32 * W, sm, p.stream>>>(x, mmax);
+        k_lo_solve<double><<<nb, 128, sm, p.stream>>>(x, mmax);
     } else {
         e = cudaFuncSetAttribute(k_lo_solve<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)sm);
         if (e != cudaSuccess) return e;
-        k_lo_solve<float><<<nb, 32 * W, sm, p.stream>>>(x, mmax);
+        k_lo_solve<float><<<nb, 128, sm, p.stream>>>(x, mmax);
     }
     return cudaGetLastError();
 }
@@ -803,7 +808,7 @@ cudaError_t launch_restrict(const Problem &p, const Level &src, Level &dst)
         k_restrict_part<<<g1, dim3(32, 4), 0, p.stream>>>(y);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
-        k_restrict_final<<<dim3((p.nx + 1 + 31) / 32, dst.n), 32, 0, p.stream>>>(y);
+        k_restrict_final<<<dim3((p.nx + 1 + 31) / 32, dst.n), dim3(32, kRP), 0, p.stream>>>(y);
         return cudaGetLastError();
     }
     RestrictCtx x;

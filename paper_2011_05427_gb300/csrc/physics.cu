@@ -51,6 +51,11 @@ void gauss_legendre_host(int n, double *x, double *w)
 static SeriesTables build_tables()
 {
     SeriesTables t{};
+    for (int k = 1; k <= 64; ++k) {
+        const double k4 = (double)k * k * k * k;
+        t.tP[k] = 6.0 / k4;
+        t.tD[k] = 5040.0 * 0.5 * k * (k + 1.0) / (k4 * k4);
+    }
     gauss_legendre_host(4, t.g4x, t.g4w);
     gauss_legendre_host(6, t.g6x, t.g6w);
     typedef long double LD;
@@ -141,26 +146,33 @@ __host__ __device__ inline void edge_series(double x, const SeriesTables &t, dou
 //   TN = e^x x^4/(e^x - 1)    = x^4 / (1 - e^{-x})
 //   TD = e^x (Dinf - D(x))    = sum_k k(k+1)/2 e^{-(k-1)x} 5040 e7(kx)/k^8
 // with e_m(y) = sum_{j<=m} y^j/j!  (integration by parts of t^n e^{-kt}).
-__host__ __device__ inline void edge_tail(double x, double &TP, double &TN, double &TD)
+__host__ __device__ inline void edge_tail(double x, const SeriesTables &t, double &TP,
+                                          double &TN, double &TD)
 {
-    double q = exp(-x);
-    double ek = 1.0;
-    double sp = 0.0, sd = 0.0;
-    for (int k = 1; k <= 64; ++k) {
-        double kk = (double)k;
-        double y = kk * x;
-        double e3 = 1.0 + y * (1.0 + y * (0.5 + y * (1.0 / 6.0)));
-        double e7 = 1.0 + y * (1.0 + y * (1.0 / 2 + y * (1.0 / 6 + y * (1.0 / 24 + y * (1.0 / 120
-                    + y * (1.0 / 720 + y * (1.0 / 5040)))))));
-        double k2 = kk * kk, k4 = k2 * k2;
-        sp += ek * 6.0 * e3 / k4;
-        sd += ek * (0.5 * kk * (kk + 1.0)) * 5040.0 * e7 / (k4 * k4);
+    const double e3 = 1.0 + x * (1.0 + x * (0.5 + x * (1.0 / 6.0)));
+    const double e7 = 1.0 + x * (1.0 + x * (1.0 / 2 + x * (1.0 / 6 + x * (1.0 / 24 + x * (1.0 / 120
+                      + x * (1.0 / 720 + x * (1.0 / 5040)))))));
+    double sp = t.tP[1] * e3, sd = t.tD[1] * e7;
+    if (x >= 40.0) {   // e^{-x} < 5e-18: one term, and 1 - e^{-x} = 1 in FP64
+        TP = sp;
+        TD = sd;
+        TN = x * x * x * x;
+        return;
+    }
+    const double q = exp(-x);
+    double ek = q;
+    for (int k = 2; k <= 64 && ek >= 1e-18; ++k) {
+        const double y = (double)k * x;
+        const double f3 = 1.0 + y * (1.0 + y * (0.5 + y * (1.0 / 6.0)));
+        const double f7 = 1.0 + y * (1.0 + y * (1.0 / 2 + y * (1.0 / 6 + y * (1.0 / 24 + y * (1.0 / 120
+                          + y * (1.0 / 720 + y * (1.0 / 5040)))))));
+        sp += ek * t.tP[k] * f3;
+        sd += ek * t.tD[k] * f7;
         ek *= q;
-        if (ek < 1e-18) break;
     }
     TP = sp;
     TD = sd;
-    TN = x * x * x * x / (-expm1(-x));
+    TN = x * x * x * x * rcp64(-expm1(-x));
 }
 
 // Gauss rule on [xa, xb] for the three scaled integrands x^3 e^{xa-x}/(1-e^{-x}),
@@ -226,9 +238,9 @@ __host__ __device__ inline void group_integrals(double xa, double xb, bool binf,
     }
     if (xa >= kXSplit) {
         double TPa, TNa, TDa, TPb = 0.0, TNb = 0.0, TDb = 0.0, r = 0.0;
-        edge_tail(xa, TPa, TNa, TDa);
+        edge_tail(xa, t, TPa, TNa, TDa);
         if (!binf) {
-            edge_tail(xb, TPb, TNb, TDb);
+            edge_tail(xb, t, TPb, TNb, TDb);
             r = exp(xa - xb);
         }
         dPs = TPa - r * TPb;
@@ -245,7 +257,7 @@ __host__ __device__ inline void group_integrals(double xa, double xb, bool binf,
             edge_series(xb, t, Pb, Nb, Db);
         } else {
             double TP, TN, TD;
-            edge_tail(xb, TP, TN, TD);
+            edge_tail(xb, t, TP, TN, TD);
             double eb = exp(-xb);
             Pb = t.Pinf - eb * TP;
             Nb = -eb * TN + 4.0 * Pb;

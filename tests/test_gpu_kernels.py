@@ -187,7 +187,8 @@ def test_lo_solve_parity(trt, orc, nx, ng):
                           (1024, 256, False, 37, False), (64, 1, True, 37, False),
                           (4, 4, True, 37, False), (64, 16, True, 500, False),
                           (256, 1, True, 500, False), (64, 16, False, 500, True),
-                          (1024, 64, False, 500, True), (64, 4, False, 70, True)])
+                          (1024, 64, False, 500, True), (64, 4, False, 70, True),
+                          (1024, 1, False, 500, True), (512, 2, True, 129, False)])
 def test_restrict_parity(trt, orc, n_from, n_to, eta, nx, fine):
     r = W.rng(4000 + n_from + n_to + nx)
     h = W.random_h(r, nx)
@@ -197,15 +198,19 @@ def test_restrict_parity(trt, orc, n_from, n_to, eta, nx, fine):
         src["sigR"] = np.exp(r.uniform(-3, 3, (n_from, nx)))
         lv["sigR"] = orc.fine_face_sigR(h, src["sigR"])
     sol = oracle_level_solve(orc, h, 2e-3, lv)
-    s = solver(trt, nx=nx, N=2, G=17, h=h)
+    # a handle with n_from groups carves the partial-sum scratch of the two-stage
+    # restriction used for coarse groups of >= 64 members
+    s = solver(trt, nx=nx, N=2, G=max(n_from, 3), h=h, levels=[max(n_from, 3), 1])
     src.update(sol)
     got = {k: v.cpu().numpy() for k, v in s.k_restrict(src, n_to, fine=fine).items()}
     cmap = np.arange(n_from) // (n_from // n_to)
     ref, Esum = orc.restrict(h, lv, sol, cmap, n_to)
     for k in orc.LEVEL_KEYS:
         if k in ("etaR", "etaL"):
+            # the two-stage path sums the compensation in one pass: equal up to rounding
+            # relative to the sigma_R dx F terms it compensates
             scale = np.max(np.abs(ref[k])) + 1e-300
-            assert np.max(np.abs(got[k] - ref[k])) <= 1e-10 * scale, k
+            assert np.max(np.abs(got[k] - ref[k])) <= 1e-9 * scale, k
         elif k == "Fold":
             assert np.max(np.abs(got[k] - ref[k])) <= 1e-12 * np.abs(ref[k]).max(), k
         else:
