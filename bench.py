@@ -10,7 +10,7 @@ hierarchy + grey LOQD/MEB Newton).  value = sweep cell-angle-group updates per s
 wall time over the timed steps (all ranks); ms_per_step = mean time of a converged step.
 
 python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                [--precision fp64|mixed] [--cycle V|W]
+                [--precision fp64|mixed|sweep32|lo32] [--cycle V|W] [--no-compare]
 Under torchrun each rank runs an independent replica of the slab (replicas only: the
 solver's data path has no cross-GPU exchange on one slab).
 """
@@ -53,7 +53,7 @@ class Clocks:
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
         try:
             self.p = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={q}",
-                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                       "--format=csv,noheader,nounits", "-lms", "100"],
                                       stdout=self.file, stderr=subprocess.DEVNULL)
         except Exception:
             self.p = None
@@ -123,40 +123,103 @@ def sum_over_ranks(x, ws):
     return float(t.item())
 
 
-def sweep_roofline(trt, s, cfg, reps=20):
-    """Time the sweep kernels (K2 + its moment finalize) alone with CUDA events on the
-    solver's stream, on the step's own sized inputs; algorithmic bytes per launch =
-    updates x 4 intensity values + per (cell, group) sigma_t, e read and f written."""
+# FP64 operations per sweep update (one cell, direction, group) of the simple corner
+# balance solve and its moments, FMA = 2, the one division = 1: diagonal mu/2 +
+# sigma_t h/2 (1), determinant (2), division (1), the two right-hand sides (4 + 2), the
+# two corner values (4 + 4), their sum (1), the two angular moment accumulations (4) = 23.
+FLOP_PER_UPDATE = 23
+# FP64 peak of the part: 152 SMs x 2070 MHz x 2 FP64 FMA per clock per SM x 2 = 1.26e12,
+# the nominal 1.25 TFLOP/s.
+FP64_PEAK_TFLOPS = 1.25
+
+# dram__bytes_read.sum + dram__bytes_write.sum of one launch, from the ncu capture named
+# in profiles/, valid while the kernel source has the recorded SHA-256 (else null).
+TRAFFIC = {}
+
+
+def _src_sha(name):
+    import hashlib
+    p = os.path.join(ROOT, "paper_2011_05427_gb300", "csrc", name)
+    with open(p, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def _traffic(key):
+    t = TRAFFIC.get(key)
+    if not t:
+        return None
+    return t["bytes"] if _src_sha(t["file"]) == t["sha"] else None
+
+
+def sweep_roofline(trt, s, cfg, fp32=False, local=0, reps=20):
+    """Time the step's own sweep (K2 + its moment finalize; FP32 mode: the pre-scaled FP32
+    inputs) with CUDA events on the solver's stream, `reps` launches after a warm-up, the
+    intensity arrays (0.5 GB FP32 / 1 GB FP64 each) larger than L2.  FP64: bound by FP64
+    issue; achieved = FLOP_PER_UPDATE x updates per launch / launch time.  FP32: bound by
+    HBM; algorithmic bytes per launch = updates x 4 intensity values (2 corners read, 2
+    written) + per (cell, group) sigma_t h/2 and h e/2 read and f written."""
+    own = s is None
+    tile = None
+    if own:
+        s = trt.Solver.from_slab(cfg, precision="sweep32" if fp32 else "fp64",
+                                 device=f"cuda:{local}")
+        tile = s.autotune(cfg.dt, reps=3)
+    ms = s.sweep_time(cfg.dt, reps=reps)
+    if own:
+        s.close()
+    upd = cfg.n_cells * cfg.M * cfg.G
+    if fp32:
+        bytes_alg = upd * 4 * 4 + cfg.n_cells * cfg.G * (2 * 4 + 8)
+        hbm, src = peaks()
+        ach = bytes_alg / (ms * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+                "frac": ach / hbm, "traffic": _traffic("sweep_fp32"),
+                "kernel": "k_sweep<float,float> + k_sweep_finalize<float>", "ms": ms,
+                "algorithmic_bytes": bytes_alg,
+                "peak_source": f"{src} (MEASURED_PEAKS hbm_gbs, copy)",
+                "updates_per_s": upd / (ms * 1e-3)}
+    else:
+        flops = FLOP_PER_UPDATE * upd
+        ach = flops / (ms * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": ach / FP64_PEAK_TFLOPS, "traffic": _traffic("sweep_fp64"),
+                "kernel": "k_sweep<double,double> + k_sweep_finalize<double>", "ms": ms,
+                "algorithmic_flops": flops,
+                "peak_source": "derived: 152 SMs x 2.07 GHz x 2 FP64 FMA/clk x 2 (nominal "
+                               "1.25 TFLOP/s FP64)",
+                "hbm_frac": upd * 32 / (ms * 1e-3) / 1e9 / peaks()[0],
+                "updates_per_s": upd / (ms * 1e-3)}
+    if tile:
+        roof["tile"] = {"D": tile[0], "S": tile[1], "NS": tile[2]}
+    return {"roofline": roof, "ms": ms}
+
+
+def timed_steps(trt, cfg, precision, cycle, steps, warmup, local, ws, clocks=False):
+    """warmup + steps converged steps of one solver on the device; returns the device time
+    of the timed steps (max over ranks), their stats, the clock record and the solver."""
     import torch
-    r = W.rng(5)
-    T = W.random_temperatures(r, cfg.n_cells, 1e-3, 1.0)
-    sig, em, _ = s.k_opacity(T)
-    rdt = torch.float32 if s.precision & trt.TRT_SWEEP_FP32 else torch.float64
-    Iold = torch.rand((s.M, s.nx, 2, s.ldG), dtype=rdt, device=s.device)
-    Inew = torch.empty_like(Iold)
-    f = torch.empty((s.G, s.nx), dtype=torch.float64, device=s.device)
-    b = [torch.empty(s.G, dtype=torch.float64, device=s.device) for _ in range(4)]
-    L = trt.lib()
-    args = (s.h, float(cfg.dt), sig.data_ptr(), em.data_ptr(), Iold.data_ptr(), Inew.data_ptr(),
-            f.data_ptr(), *[x.data_ptr() for x in b])
-    for _ in range(3):
-        assert L.trt_k_sweep(*args) == 0
+    s = trt.Solver.from_slab(cfg, precision=precision, device=f"cuda:{local}")
+    s.tile = s.autotune(cfg.dt, reps=3)   # sweep tile for this problem (state unchanged)
+    l_max = 4 if cycle == "V" else 2
+    for _ in range(warmup):
+        s.step(cfg.dt, cycle, l_max, cfg.eps)
+    clk = Clocks(local) if clocks else None
+    barrier(ws)
+    torch.cuda.synchronize()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
     ev0.record(s.stream)
-    for _ in range(reps):
-        L.trt_k_sweep(*args)
+    stats = [s.step(cfg.dt, cycle, l_max, cfg.eps) for _ in range(steps)]
     ev1.record(s.stream)
     torch.cuda.synchronize()
-    ms = ev0.elapsed_time(ev1) / reps
-    esz = 4 if s.precision & trt.TRT_SWEEP_FP32 else 8
-    upd = cfg.n_cells * cfg.M * cfg.G
-    bytes_alg = upd * 4 * esz + cfg.n_cells * cfg.G * (2 * 8 + 8)
-    hbm, src = peaks()
-    ach = bytes_alg / (ms * 1e-3) / 1e9
-    return dict(ms=ms, bytes=bytes_alg, achieved=ach, peak=hbm, src=src, updates=upd,
-                upd_per_s=upd / (ms * 1e-3))
+    barrier(ws)
+    rec = clk.stop() if clk else None
+    t = max_over_ranks(ev0.elapsed_time(ev1) * 1e-3, ws)
+    return t, stats, rec, s
+
+
+def counters(stats, steps):
+    return {k: sum(x[k] for x in stats) / steps for k in ("n_ti", "n_c", "n_lo")}
 
 
 def run_ours(args):
@@ -166,33 +229,16 @@ def run_ours(args):
     torch.cuda.set_device(local)
     cfg = W.fc_1024(args.cycle)
     upd_sweep = cfg.updates_per_sweep()
-    s = trt.Solver.from_slab(cfg, precision=args.precision, device=f"cuda:{local}")
-    for _ in range(args.warmup):
-        s.step(cfg.dt, cfg.cycle, cfg.l_max, cfg.eps)
-    clk = Clocks(local) if rank == 0 else None
-    barrier(ws)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    ev0.record(s.stream)
-    stats = [s.step(cfg.dt, cfg.cycle, cfg.l_max, cfg.eps) for _ in range(args.steps)]
-    ev1.record(s.stream)
-    torch.cuda.synchronize()
-    barrier(ws)
-    wall = time.perf_counter() - t0
-    clocks = clk.stop() if clk else None
-    dev_s = ev0.elapsed_time(ev1) * 1e-3
-    t_max = max_over_ranks(dev_s, ws)
+
+    t_max, stats, clocks, s = timed_steps(trt, cfg, args.precision, args.cycle, args.steps,
+                                          args.warmup, local, ws, clocks=(rank == 0))
     n_ti = sum(x["n_ti"] for x in stats)
     launches = sum(x.get("n_kernels", 0) for x in stats)
-    total_upd = sum_over_ranks(n_ti * upd_sweep, ws)
-    value = total_upd / t_max
+    value = sum_over_ranks(n_ti * upd_sweep, ws) / t_max
     ms_step = t_max / args.steps * 1e3
 
     # e2e: the public API from host data -- create (uploads the host-built constants and
-    # initial state), K steps each followed by a read of the step's result to pinned host
-    # memory, destroy.
+    # initial state), K steps each followed by a read of the step's result to host memory.
     res_bytes = 8 * (cfg.n_cells + cfg.G * cfg.n_cells + cfg.G * (cfg.n_cells + 1) +
                      2 * cfg.n_cells + 1)
     torch.cuda.synchronize()
@@ -201,7 +247,7 @@ def run_ours(args):
     s2 = trt.Solver.from_slab(cfg, precision=args.precision, device=f"cuda:{local}")
     e2e_ti = 0
     for _ in range(args.steps):
-        st = s2.step(cfg.dt, cfg.cycle, cfg.l_max, cfg.eps)
+        st = s2.step(cfg.dt, args.cycle, 4 if args.cycle == "V" else 2, cfg.eps)
         e2e_ti += st["n_ti"]
         s2.moments()
     torch.cuda.synchronize()
@@ -212,10 +258,45 @@ def run_ours(args):
     s2.close()
     e2e_val = sum_over_ranks(e2e_ti * upd_sweep, ws) / te
 
-    roof = sweep_roofline(trt, s, cfg)
+    # the other cycle and the mixed-precision form on the same workload, same step count
+    extra = {}
+    if args.compare:
+        other = "W" if args.cycle == "V" else "V"
+        t_o, st_o, _, s_o = timed_steps(trt, cfg, args.precision, other, args.steps, 1,
+                                        local, ws)
+        s_o.close()
+        extra[f"cycle_{other}"] = {"ms_per_step": t_o / args.steps * 1e3,
+                                   "value": sum(x["n_ti"] for x in st_o) * upd_sweep / t_o,
+                                   **counters(st_o, args.steps)}
+        if args.precision == "fp64":
+            t_m, st_m, _, s_m = timed_steps(trt, cfg, "sweep32", args.cycle, args.steps,
+                                            args.warmup, local, ws)
+            a, b = s.moments(), s_m.moments()
+            s_m.close()
+            extra["mixed_sweep32"] = {
+                "ms_per_step": t_m / args.steps * 1e3,
+                "value": sum(x["n_ti"] for x in st_m) * upd_sweep / t_m,
+                "speedup_vs_fp64": ms_step / (t_m / args.steps * 1e3),
+                "max_rel_T_vs_fp64": float(np.max(np.abs(b["T"] - a["T"]) / a["T"])),
+                "max_rel_Eg_vs_fp64": float(np.max(np.abs(b["Eg"] - a["Eg"]) /
+                                                   a["Eg"].sum(0)[None, :])),
+                "note": "FP32 sweeps, FP64 group/grey LOQD + MEB; both converged to eps; "
+                        "compared after the same warm-up + timed steps",
+                **counters(st_m, args.steps)}
+
+    tile = s.tile
+    if args.precision in ("fp64", "lo32"):
+        roof = sweep_roofline(trt, s, cfg, fp32=False)
+        roof["roofline"]["tile"] = {"D": tile[0], "S": tile[1], "NS": tile[2]}
+        roof32 = sweep_roofline(trt, None, cfg, fp32=True, local=local)
+    else:
+        roof32 = sweep_roofline(trt, s, cfg, fp32=True)
+        roof32["roofline"]["tile"] = {"D": tile[0], "S": tile[1], "NS": tile[2]}
+        roof = sweep_roofline(trt, None, cfg, fp32=False, local=local)
     if rank != 0:
         s.close()
         return
+    main_roof = roof32 if args.precision != "fp64" and args.precision != "lo32" else roof
     out = {
         "metric": METRIC,
         "value": value,
@@ -227,25 +308,26 @@ def run_ours(args):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f64" if args.precision == "fp64" else "f32+f64",
+        "dtype": "f64" if args.precision in ("fp64", "lo32") else "f32+f64",
         "data": "synthetic (Fleck-Cummings slab, seeded, no dataset)",
         "config": {"workload": f"fc_1024: 500 cells, 64 directions (double S32), 1024 groups, "
-                               f"grids 1024/256/64/16/1, {args.cycle}-cycle l_max {cfg.l_max}, "
-                               f"dt 1e-3 sh, eps 1e-8, {args.precision}",
+                               f"grids 1024/256/64/16/1, {args.cycle}-cycle "
+                               f"l_max {4 if args.cycle == 'V' else 2}, dt 1e-3 sh, eps 1e-8, "
+                               f"{args.precision}",
                    "parallelism": f"replicas x{ws}",
-                   "l2": "inputs larger than L2 (intensity arrays 1 GB)",
-                   "n_ti_per_step": n_ti / args.steps,
-                   "n_c_per_step": sum(x["n_c"] for x in stats) / args.steps,
-                   "n_lo_per_step": sum(x["n_lo"] for x in stats) / args.steps},
+                   "sweep_tile": {"D": tile[0], "S": tile[1], "NS": tile[2],
+                                  "picked_by": "trt_autotune"},
+                   "l2": "inputs larger than L2 (intensity arrays 1 GB each in FP64)",
+                   **{k + "_per_step": v for k, v in counters(stats, args.steps).items()}},
         "e2e": {"value": e2e_val, "unit": "updates/s", "h2d_bytes_per_step": h2d / args.steps,
                 "d2h_bytes_per_step": res_bytes,
                 "note": "create + K steps + per-step moments read; state stays on device"},
         "gpu_launches": launches,
-        "roofline": {"bound": "hbm", "achieved": roof["achieved"], "peak": roof["peak"],
-                     "unit": "GB/s", "frac": roof["achieved"] / roof["peak"], "traffic": None,
-                     "kernel": "k_sweep + k_sweep_finalize", "ms": roof["ms"],
-                     "peak_source": roof["src"]},
+        "roofline": main_roof["roofline"],
+        "roofline_sweep_fp32": roof32["roofline"],
+        "roofline_sweep_fp64": roof["roofline"],
         "clocks": clocks,
+        **extra,
     }
     if args.cpu_baseline and ws == 1:
         out["cpu_baseline"] = cpu_baseline(args)
@@ -267,11 +349,15 @@ def oracle_sample(orc, cfg):
 def cpu_baseline(args):
     from oracle import orc
     cfg = W.fc_1024(args.cycle)
-    upd, dt = oracle_sample(orc, cfg)
+    upd = dt = 0.0
+    for _ in range(3):
+        u, t = oracle_sample(orc, cfg)
+        upd += u
+        dt += t
     return {"value": upd / dt, "unit": "updates/s", "cores": 1, "kind": "oracle",
-            "sample": "oracle (FP64 C, 1 thread): one fixed-iteration step of fc_1024 "
-                      "(s=0 phase + 1 sweep + 1 phase, 1 cycle each), "
-                      f"{dt:.1f} s; updates counted over the sweep"}
+            "sample": "oracle (FP64 C, 1 thread): three fixed-iteration steps of fc_1024 "
+                      "from the cold start (each: s=0 phase + 1 sweep + 1 phase, 1 cycle "
+                      f"each), {dt:.1f} s; updates counted over the sweeps"}
 
 
 def run_reference(args):
@@ -307,19 +393,25 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed", "sweep32", "lo32"])
-    ap.add_argument("--cycle", default="W", choices=["V", "W"])
+    ap.add_argument("--cycle", default="V", choices=["V", "W"])
+    ap.add_argument("--no-compare", dest="compare", action="store_false",
+                    help="skip the other-cycle and mixed-precision comparison runs")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--profile-step", action="store_true",
                     help="run the warm-up steps and one more step, print nothing (for ncu)")
+    ap.add_argument("--tile", default=None,
+                    help="D,shape: sweep tile for --profile-step (default: the library's)")
     args = ap.parse_args()
     if args.profile_step:
         from paper_2011_05427_gb300 import trt
         cfg = W.fc_1024(args.cycle)
         s = trt.Solver.from_slab(cfg, precision=args.precision, device="cuda:0")
+        if args.tile:
+            s.set_sweep_tile(*[int(x) for x in args.tile.split(",")])
         for _ in range(args.warmup + 1):
             s.step(cfg.dt, cfg.cycle, cfg.l_max, cfg.eps)
         s.close()

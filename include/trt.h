@@ -190,6 +190,28 @@ int trt_k_sweep(trt_handle *h, double dt, const double *sigE, const double *emis
                 const void *I_old, void *I_new, double *f, double *fb0, double *fbX,
                 double *C0, double *CX);
 
+/* ---- sweep tile selection (a tuning aid; the paper has no counterpart) ----
+ * The HO sweep (eq. rt, simple corner balance, Sec. 5) runs one warp per (32 groups,
+ * direction); a CTA takes D directions of one sign and walks the cells in strips of S,
+ * with NS strip buffers of asynchronous copies.  The best (D, S, NS) depends on the
+ * problem's sizes and the precision.
+ *
+ * trt_sweep_time: the time of the step's own sweep on this handle -- opacities at the
+ * current T (FP32 pre-scaled inputs in a FP32-sweep mode), then the sweep of the current
+ * intensity into the handle's spare intensity buffer and scratch -- averaged over reps
+ * launches (after one warm-up), CUDA events on the handle's stream.  The state (T, E_g,
+ * F_g, I, QD factors) is left unchanged; call it between steps.  Needs n_cells >= 3.
+ *   *ms: milliseconds per sweep (K2 + its moment finalize).
+ * trt_autotune: times every candidate (D, S, NS) with trt_sweep_time and keeps the
+ * fastest for later steps.  D, S, NS (may be NULL) receive the choice.
+ * Both return TRT_EINVAL on bad arguments, TRT_ECUDA on a launch error. */
+int trt_sweep_time(trt_handle *h, double dt, int reps, float *ms);
+int trt_autotune(trt_handle *h, double dt, int reps, int *D, int *S, int *NS);
+/* Set the sweep tile explicitly: D directions per CTA (a candidate of trt_autotune) and a
+ * shape index in [0, trt_sweep_shapes(h)); returns TRT_EINVAL otherwise. */
+int trt_sweep_shapes(const trt_handle *h);
+int trt_set_sweep_tile(trt_handle *h, int D, int shape);
+
 /* One frequency-grid level of the low-order system, device arrays (FP64).
  * fine = 0: a coarse or grey level with the arrays below.
  * fine = 1: the fine grid in its raw form: phi = f_g, sig = sigma_E, emis = e_g, and sigR is

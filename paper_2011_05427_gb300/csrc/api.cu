@@ -656,6 +656,106 @@ int trt_k_sweep(trt_handle *h, double dt, const double *sigE, const double *emis
     return TRT_OK;
 }
 
+int trt_sweep_shapes(const trt_handle *h)
+{
+    return h ? sweep_shape_count(h->p.precision) : 0;
+}
+
+int trt_set_sweep_tile(trt_handle *h, int D, int shape)
+{
+    if (!h) return TRT_EINVAL;
+    int cand[2];
+    const int nc = sweep_D_candidates(h->p, cand);
+    bool ok = false;
+    for (int i = 0; i < nc; ++i) ok = ok || cand[i] == D;
+    if (!ok || shape < 0 || shape >= sweep_shape_count(h->p.precision))
+        return fail(h, TRT_EINVAL, "trt_set_sweep_tile: D or shape not a candidate");
+    h->p.sweep_D = D;
+    h->p.sweep_shape = shape;
+    return TRT_OK;
+}
+
+int trt_sweep_time(trt_handle *h, double dt, int reps, float *ms)
+{
+    if (!h || !(dt > 0) || reps < 1 || !ms) return TRT_EINVAL;
+    const Problem &p = h->p;
+    if (p.nx < 3) return fail(h, TRT_EINVAL, "trt_sweep_time needs n_cells >= 3");
+    // outputs go to scratch that no step reads before writing it: the fine-solve arrays
+    // E1 [G][nx] (f) and F1 [G][nx+1] (the four boundary arrays, 4 G <= G (nx + 1))
+    double *f = h->E1, *b = h->F1;
+    const size_t G = p.G;
+    CK(launch_opacity(p, h->T, h->sigE, h->emis, h->sigR, h->sig32, h->emis32, dt));
+    auto one = [&]() {
+        return h->sig32 ? launch_sweep(p, dt, h->sig32, h->emis32, true, h->I_cur, h->I_alt,
+                                       h->part, h->psi_exit, f, b, b + G, b + 2 * G, b + 3 * G)
+                        : launch_sweep(p, dt, h->sigE, h->emis, false, h->I_cur, h->I_alt,
+                                       h->part, h->psi_exit, f, b, b + G, b + 2 * G, b + 3 * G);
+    };
+    CK(one());
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    cudaError_t e = cudaEventRecord(e0, p.stream);
+    for (int r = 0; r < reps && e == cudaSuccess; ++r) e = one();
+    if (e == cudaSuccess) e = cudaEventRecord(e1, p.stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float t = 0;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    CK(e);
+    *ms = t / reps;
+    return TRT_OK;
+}
+
+int trt_autotune(trt_handle *h, double dt, int reps, int *D, int *S, int *NS)
+{
+    if (!h || !(dt > 0) || reps < 1) return TRT_EINVAL;
+    int cand[2];
+    const int nc = sweep_D_candidates(h->p, cand);
+    const int ns = sweep_shape_count(h->p.precision);
+    const int D0 = h->p.sweep_D, sh0 = h->p.sweep_shape;
+    float best = 1e30f;
+    int bD = D0, bsh = sh0;
+    for (int i = 0; i < nc; ++i) {
+        for (int k = 0; k < ns; ++k) {
+            h->p.sweep_D = cand[i];
+            h->p.sweep_shape = k;
+            float ms = 0;
+            const int rc = trt_sweep_time(h, dt, reps, &ms);
+            if (rc == TRT_ECUDA) {
+                // a shape the device cannot launch (shared memory) is skipped; a sticky
+                // error is not
+                cudaGetLastError();
+                if (cudaStreamSynchronize(h->p.stream) != cudaSuccess) {
+                    h->p.sweep_D = D0;
+                    h->p.sweep_shape = sh0;
+                    return TRT_ECUDA;
+                }
+                continue;
+            }
+            if (rc != TRT_OK) {
+                h->p.sweep_D = D0;
+                h->p.sweep_shape = sh0;
+                return rc;
+            }
+            if (ms < best) {
+                best = ms;
+                bD = cand[i];
+                bsh = k;
+            }
+        }
+    }
+    h->p.sweep_D = bD;
+    h->p.sweep_shape = bsh;
+    int s_ = 0, ns_ = 0;
+    sweep_shape_info(h->p.precision, bsh, &s_, &ns_);
+    if (D) *D = bD > 0 ? bD : cand[0];
+    if (S) *S = s_;
+    if (NS) *NS = ns_;
+    return TRT_OK;
+}
+
 int trt_k_lo_solve(trt_handle *h, double dt, trt_level *lv)
 {
     if (!h || !lv || !(dt > 0) || lv->n < 1) return TRT_EINVAL;

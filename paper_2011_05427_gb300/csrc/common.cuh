@@ -91,6 +91,8 @@ struct Problem {
     double *ihf;        // [nx+1]: 1/(h_{f-1} + h_f) at interior faces (dx-weighted means)
     double *rscratch;   // partial sums of the two-stage restriction
     size_t rscratch_doubles;
+    // sweep tile: directions per CTA (0 = default) and strip shape index (0 = default)
+    int sweep_D = 0, sweep_shape = 0;
 };
 
 // ---- launchers (each enqueues on p.stream; returns cudaError_t of the launch) ----
@@ -99,6 +101,9 @@ cudaError_t launch_opacity(const Problem &p, const double *T, double *sigE, doub
                            double *sigR, float *sig32 = nullptr, float *emis32 = nullptr,
                            double dt = 0.0);
 size_t sweep_partial_doubles(const Problem &p);
+int sweep_shape_count(int precision);
+void sweep_shape_info(int precision, int shape, int *S, int *NS);
+int sweep_D_candidates(const Problem &p, int *D);   // fills D[0..n), returns n (<= 2)
 // sigE / emis: [G][nx]; double sigma_E, e_g, or (sigma_fp32, FP32 sweep only) the float
 // pre-scaled (sigma_E + 1/(c dt)) h/2 and h e/2 of launch_opacity
 cudaError_t launch_sweep(const Problem &p, double dt, const void *sigE, const void *emis,

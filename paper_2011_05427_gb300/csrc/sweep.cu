@@ -29,8 +29,12 @@ namespace trt {
 
 namespace {
 
-constexpr int kStrip = 16;
 constexpr int kPadG = 33;   // padded group stride of the strip tables (bank conflicts)
+// Tile shape: S cells per strip, NS strip buffers (NS - 1 strips of copies in flight while
+// one is swept), D directions per CTA (runtime).  The grid holds one warp per
+// (32 groups, direction) -- 2048 warps at 1024 groups x 64 directions, about 13 per SM --
+// so the FP32 sweep is bound by how many bytes each warp keeps in flight; the shape is
+// picked per problem by timing the candidates (trt_autotune), else the defaults below.
 
 struct SweepArgs {
     int nx, N, G, ldG, D;
@@ -61,10 +65,12 @@ struct Acc {   // per-tile angular sum: plain in FP64, compensated (Kahan) in FP
     }
 };
 
-// 1/d.  FP32: the correctly rounded reciprocal.  FP64: one Newton-Raphson step
-// x1 = x0 (2 - d x0) from the correctly rounded FP32 reciprocal x0; the relative error
-// squares, to about (2^-24)^2 plus rounding (~4e-15), at 4 FP64 operations instead of the
-// ~20 of an IEEE division -- FP64 issue rate is the bound of the FP64 sweep on GB300.
+// 1/d.  FP32: the correctly rounded reciprocal.  FP64: the hardware's approximate FP64
+// reciprocal x (relative error eps of order 2^-22, special-function unit, not the FP64
+// pipe) refined by one third-order Newton-Raphson (Householder) step: with e = 1 - d x,
+// x (1 + e + e^2) = (1 - eps^3)/d, below FP64 rounding, at 3 FP64 FMAs instead of the
+// ~20 operations of an IEEE division -- FP64 issue rate bounds the FP64 sweep on GB300.
+// d here is a determinant (mu/2 + sigma_t h/2)^2 + (mu/2)^2 > 0 of normal FP64 range.
 template <typename R>
 __device__ inline R recip(R d);
 template <>
@@ -72,8 +78,10 @@ __device__ inline float recip<float>(float d) { return __frcp_rn(d); }
 template <>
 __device__ inline double recip<double>(double d)
 {
-    const double x0 = (double)__frcp_rn((float)d);
-    return x0 * fma(-d, x0, 2.0);
+    double x;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(x) : "d"(d));
+    const double e = fma(-d, x, 1.0);
+    return fma(x, fma(e, e, e), x);
 }
 
 // cp.async (global -> shared, completion per issuing thread): the next strip's data is
@@ -89,16 +97,16 @@ template <int N>
 __device__ inline void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
 
 // shared-memory carve-up of k_sweep (byte offsets, 16-byte aligned sections)
-template <typename R, typename SR>
+template <typename R, typename SR, int kStrip, int NS>
 struct SweepSmem {
     size_t itile, rawS, rawE, sth, sq, skap, ps, swt, total;
     __host__ __device__ SweepSmem(int D)
     {
         auto al = [](size_t x) { return (x + 15) / 16 * 16; };
         size_t o = 0;
-        itile = o; o = al(o + sizeof(R) * 2 * (size_t)D * kStrip * 2 * 32);
-        rawS = o;  o = al(o + sizeof(SR) * 2 * kStrip * kPadG);
-        rawE = o;  o = al(o + sizeof(SR) * 2 * kStrip * kPadG);
+        itile = o; o = al(o + sizeof(R) * NS * (size_t)D * kStrip * 2 * 32);
+        rawS = o;  o = al(o + sizeof(SR) * NS * kStrip * kPadG);
+        rawE = o;  o = al(o + sizeof(SR) * NS * kStrip * kPadG);
         sth = o;   o = al(o + sizeof(R) * kStrip * kPadG);
         sq = o;    o = al(o + sizeof(R) * kStrip * kPadG);
         skap = o;  o = al(o + sizeof(R) * kStrip);
@@ -112,16 +120,16 @@ struct SweepSmem {
 // are sigma_E and e_g, tabulated per strip as sigma_t h/2 and h e/2 (FP64, one rounding);
 // SR = float: the fields already are sigma_t h/2 and h e/2 in FP32 (written by the opacity
 // kernel with one rounding each) and are used as staged.
-template <typename R, typename SR>
+template <typename R, typename SR, int kStrip, int NS>
 __global__ void __launch_bounds__(256) k_sweep(SweepArgs a)
 {
     constexpr bool kPre = sizeof(SR) == 4;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int D = a.D;
-    const SweepSmem<R, SR> L(D);
-    R *itile = reinterpret_cast<R *>(smem_raw + L.itile);      // [2][D][S][2][32]
-    SR *rawS = reinterpret_cast<SR *>(smem_raw + L.rawS);      // [2][S][33] sigma_E
-    SR *rawE = reinterpret_cast<SR *>(smem_raw + L.rawE);      // [2][S][33] e_g
+    const SweepSmem<R, SR, kStrip, NS> L(D);
+    R *itile = reinterpret_cast<R *>(smem_raw + L.itile);      // [NS][D][S][2][32]
+    SR *rawS = reinterpret_cast<SR *>(smem_raw + L.rawS);      // [NS][S][33] sigma_E
+    SR *rawE = reinterpret_cast<SR *>(smem_raw + L.rawE);      // [NS][S][33] e_g
     R *sth = reinterpret_cast<R *>(smem_raw + L.sth);          // [S][33] sigma_t h / 2
     R *sq = reinterpret_cast<R *>(smem_raw + L.sq);            // [S][33] (h/2) e_g
     R *skap = reinterpret_cast<R *>(smem_raw + L.skap);        // [S]     h / (2 c dt)
@@ -194,17 +202,24 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs a)
         cp_commit();
     };
 
-    prefetch(0, 0);
+    for (int k = 0; k < NS - 1; ++k) {
+        if (k < nstrip)
+            prefetch(k, k);
+        else
+            cp_commit();   // empty groups keep the wait count uniform
+    }
     for (int st = 0; st < nstrip; ++st) {
-        const int bf = st & 1;
+        const int bf = st % NS;
         int c0, ns;
         range(st, c0, ns);
-        if (st + 1 < nstrip)
-            prefetch(st + 1, bf ^ 1);
+        // the buffer of strip st + NS - 1 last held strip st - 1, consumed before the
+        // barrier that ended the previous iteration's sweep
+        if (st + NS - 1 < nstrip)
+            prefetch(st + NS - 1, (st + NS - 1) % NS);
         else
-            cp_commit();   // empty group keeps the wait count uniform
-        cp_wait<1>();      // this thread's copies of strip st have landed
-        __syncthreads();   // ... and everyone's; the previous strip is fully consumed
+            cp_commit();
+        cp_wait<NS - 1>();   // this thread's copies of strip st have landed
+        __syncthreads();     // ... and everyone's
         const SR *rs = rawS + bf * kStrip * kPadG, *re = rawE + bf * kStrip * kPadG;
         if (!kPre) {
             for (int idx = tid; idx < 32 * kStrip; idx += nthr) {
@@ -272,83 +287,169 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs a)
 }
 
 // f_g = sum_t A2 / sum_t A0 per (group, cell), in R; boundary factors per group in FP64.
+// Blocks [0, nb_cell) take one (group, cell) per thread; the blocks after them take one
+// group per warp for the boundary factors: lanes stride over the directions and the four
+// half-range sums per face meet in a fixed butterfly (a serial loop over all directions
+// per thread left a latency-bound tail of dependent loads).
 template <typename R>
-__global__ void k_sweep_finalize(int nx, int N, int G, int ldG, int ntile,
+__global__ void k_sweep_finalize(int nx, int N, int G, int ldG, int ntile, int nb_cell,
                                  const R *__restrict__ part, const double *__restrict__ mu,
                                  const double *__restrict__ w, const double *__restrict__ Iin0,
                                  const double *__restrict__ IinX, const R *__restrict__ psi_exit,
                                  double *__restrict__ f, double *fb0, double *fbX, double *C0,
                                  double *CX)
 {
-    long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    const long n = (long)G * nx;
-    if (idx < n) {
-        Acc<R> A0, A2;
-        for (int t = 0; t < ntile; ++t) {
-            A0.add(part[(size_t)(t * 2 + 0) * n + idx]);
-            A2.add(part[(size_t)(t * 2 + 1) * n + idx]);
+    if ((int)blockIdx.x < nb_cell) {
+        const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+        const long n = (long)G * nx;
+        if (idx < n) {
+            Acc<R> A0, A2;
+            for (int t = 0; t < ntile; ++t) {
+                A0.add(part[(size_t)(t * 2 + 0) * n + idx]);
+                A2.add(part[(size_t)(t * 2 + 1) * n + idx]);
+            }
+            f[idx] = (A0.s != (R)0) ? (double)(A2.s / A0.s) : 1.0 / 3.0;
         }
-        f[idx] = (A0.s != (R)0) ? (double)(A2.s / A0.s) : 1.0 / 3.0;
+        return;
     }
-    if (idx < G) {
-        const int g = (int)idx, M = 2 * N;
-        double s0 = 0, s2 = 0, h0 = 0, h1 = 0;
-        for (int m = 0; m < M; ++m) {   // x = 0: inflow for mu > 0, outflow for mu < 0
-            double psi = (m < N) ? Iin0[g] : (double)psi_exit[(size_t)m * ldG + g];
-            s0 += w[m] * psi;
-            s2 += w[m] * mu[m] * mu[m] * psi;
-            if (m >= N) { h0 += w[m] * psi; h1 += w[m] * mu[m] * psi; }
-        }
-        fb0[g] = (s0 != 0.0) ? s2 / s0 : 1.0 / 3.0;
-        C0[g] = (h0 != 0.0) ? h1 / h0 : -0.5;
-        s0 = s2 = h0 = h1 = 0;
-        for (int m = 0; m < M; ++m) {   // x = X: outflow for mu > 0, inflow for mu < 0
-            double psi = (m < N) ? (double)psi_exit[(size_t)m * ldG + g] : IinX[g];
-            s0 += w[m] * psi;
-            s2 += w[m] * mu[m] * mu[m] * psi;
-            if (m < N) { h0 += w[m] * psi; h1 += w[m] * mu[m] * psi; }
-        }
-        fbX[g] = (s0 != 0.0) ? s2 / s0 : 1.0 / 3.0;
-        CX[g] = (h0 != 0.0) ? h1 / h0 : 0.5;
+    const int lane = threadIdx.x & 31;
+    const int g = (blockIdx.x - nb_cell) * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (g >= G) return;   // whole warp
+    const int M = 2 * N;
+    // x = 0: inflow for mu > 0, outflow for mu < 0; x = X: outflow for mu > 0, inflow mu < 0
+    double a0 = 0, a2 = 0, ah0 = 0, ah1 = 0, b0 = 0, b2 = 0, bh0 = 0, bh1 = 0;
+    for (int m = lane; m < M; m += 32) {
+        const double wm = w[m], mm = mu[m];
+        const double ex = (double)psi_exit[(size_t)m * ldG + g];
+        const double p0 = (m < N) ? Iin0[g] : ex;
+        const double pX = (m < N) ? ex : IinX[g];
+        a0 += wm * p0;
+        a2 += wm * mm * mm * p0;
+        b0 += wm * pX;
+        b2 += wm * mm * mm * pX;
+        if (m >= N) { ah0 += wm * p0; ah1 += wm * mm * p0; }
+        else        { bh0 += wm * pX; bh1 += wm * mm * pX; }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        a0 += __shfl_xor_sync(0xffffffffu, a0, o);
+        a2 += __shfl_xor_sync(0xffffffffu, a2, o);
+        ah0 += __shfl_xor_sync(0xffffffffu, ah0, o);
+        ah1 += __shfl_xor_sync(0xffffffffu, ah1, o);
+        b0 += __shfl_xor_sync(0xffffffffu, b0, o);
+        b2 += __shfl_xor_sync(0xffffffffu, b2, o);
+        bh0 += __shfl_xor_sync(0xffffffffu, bh0, o);
+        bh1 += __shfl_xor_sync(0xffffffffu, bh1, o);
+    }
+    if (lane == 0) {
+        fb0[g] = (a0 != 0.0) ? a2 / a0 : 1.0 / 3.0;
+        C0[g] = (ah0 != 0.0) ? ah1 / ah0 : -0.5;
+        fbX[g] = (b0 != 0.0) ? b2 / b0 : 1.0 / 3.0;
+        CX[g] = (bh0 != 0.0) ? bh1 / bh0 : 0.5;
     }
 }
 
-// directions per CTA: 8 in FP32 (HBM bound: many directions share the staged sigma rows),
-// 4 in FP64 (FP64 issue bound: smaller tiles give more resident CTAs per SM)
+// Candidate tile shapes (S, NS); index 0 is the default.  Measured at 500 cells x 64
+// directions x 1024 groups with D = 8: FP32 (16, 2) 0.215 ms, (8, 4) 0.225, (32, 2) 0.282,
+// (16, 3) 0.299 (a third buffer costs a resident CTA per SM); FP64 (8, 2) 1.26 ms,
+// (16, 2) 1.37, (8, 3) 1.37.
+struct Shape {
+    int S, NS;
+};
+constexpr Shape kShapes32[] = {{16, 2}, {16, 3}, {16, 4}, {8, 4}, {8, 6}, {32, 2}};
+constexpr Shape kShapes64[] = {{8, 2}, {16, 2}, {8, 3}};
+
+// largest power of two <= cap dividing N: the direction-tile height D_min that the
+// workspace's partial-moment scratch is sized for; D may be D_min or 2 D_min (<= 8)
+int base_D(int N, int cap)
+{
+    for (int D = cap; D >= 1; D >>= 1)
+        if (N % D == 0) return D;
+    return 1;
+}
+
 int pick_D(const Problem &p)
 {
-    const int Dmax = sweep_fp32(p.precision) ? 8 : 4;
-    for (int D = Dmax; D >= 1; D >>= 1)
-        if (p.N % D == 0) return D;
-    return 1;
+    if (p.sweep_D > 0) return p.sweep_D;
+    return base_D(p.N, 8);
+}
+
+template <typename R, typename SR, int S, int NS>
+cudaError_t launch_shape(const Problem &p, const SweepArgs &a)
+{
+    const int ntile = p.M / a.D;
+    dim3 grid(ntile, p.ldG / 32);
+    dim3 block(32 * a.D);
+    const size_t sm = SweepSmem<R, SR, S, NS>(a.D).total;
+    if (sm > 227 * 1024) return cudaErrorInvalidConfiguration;
+    cudaError_t e = cudaFuncSetAttribute(k_sweep<R, SR, S, NS>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    k_sweep<R, SR, S, NS><<<grid, block, sm, p.stream>>>(a);
+    return cudaGetLastError();
 }
 
 template <typename R, typename SR>
 cudaError_t launch_sweep_t(const Problem &p, const SweepArgs &a)
 {
     const int ntile = p.M / a.D;
-    dim3 grid(ntile, p.ldG / 32);
-    dim3 block(32 * a.D);
-    const size_t sm = SweepSmem<R, SR>(a.D).total;
-    cudaError_t e = cudaFuncSetAttribute(k_sweep<R, SR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)sm);
-    if (e != cudaSuccess) return e;
-    k_sweep<R, SR><<<grid, block, sm, p.stream>>>(a);
-    e = cudaGetLastError();
+    const int shape = p.sweep_shape;
+    cudaError_t e;
+    if (sizeof(R) == 4) {
+        switch (shape) {
+        case 1: e = launch_shape<R, SR, 16, 3>(p, a); break;
+        case 2: e = launch_shape<R, SR, 16, 4>(p, a); break;
+        case 3: e = launch_shape<R, SR, 8, 4>(p, a); break;
+        case 4: e = launch_shape<R, SR, 8, 6>(p, a); break;
+        case 5: e = launch_shape<R, SR, 32, 2>(p, a); break;
+        default: e = launch_shape<R, SR, 16, 2>(p, a); break;
+        }
+    } else {
+        switch (shape) {
+        case 1: e = launch_shape<R, SR, 16, 2>(p, a); break;
+        case 2: e = launch_shape<R, SR, 8, 3>(p, a); break;
+        default: e = launch_shape<R, SR, 8, 2>(p, a); break;
+        }
+    }
     if (e != cudaSuccess) return e;
     const long n = (long)p.G * p.nx;
     const int bs = 256;
-    k_sweep_finalize<R><<<(unsigned)((n + bs - 1) / bs), bs, 0, p.stream>>>(
-        p.nx, p.N, p.G, p.ldG, ntile, reinterpret_cast<const R *>(a.part), p.mu, p.w, p.Iin0,
-        p.IinX, reinterpret_cast<const R *>(a.psi_exit), a.f, a.fb0, a.fbX, a.C0, a.CX);
+    const int nb_cell = (int)((n + bs - 1) / bs);
+    const int nb_bnd = (p.G + bs / 32 - 1) / (bs / 32);
+    k_sweep_finalize<R><<<(unsigned)(nb_cell + nb_bnd), bs, 0, p.stream>>>(
+        p.nx, p.N, p.G, p.ldG, ntile, nb_cell, reinterpret_cast<const R *>(a.part), p.mu, p.w,
+        p.Iin0, p.IinX, reinterpret_cast<const R *>(a.psi_exit), a.f, a.fb0, a.fbX, a.C0,
+        a.CX);
     return cudaGetLastError();
 }
 
 }  // namespace
 
+int sweep_shape_count(int precision)
+{
+    return sweep_fp32(precision) ? (int)(sizeof(kShapes32) / sizeof(Shape))
+                                 : (int)(sizeof(kShapes64) / sizeof(Shape));
+}
+
+void sweep_shape_info(int precision, int shape, int *S, int *NS)
+{
+    const Shape sh = sweep_fp32(precision) ? kShapes32[shape] : kShapes64[shape];
+    *S = sh.S;
+    *NS = sh.NS;
+}
+
+int sweep_D_candidates(const Problem &p, int *D)
+{
+    const int b = base_D(p.N, 4);
+    int n = 0;
+    D[n++] = b;
+    if (2 * b <= 8 && p.N % (2 * b) == 0) D[n++] = 2 * b;
+    return n;
+}
+
 size_t sweep_partial_doubles(const Problem &p)
 {
-    return (size_t)(p.M / pick_D(p)) * 2 * p.G * p.nx;
+    // sized for the smallest direction tile any shape may use
+    return (size_t)(p.M / std::min(base_D(p.N, 4), pick_D(p))) * 2 * p.G * p.nx;
 }
 
 cudaError_t launch_sweep(const Problem &p, double dt, const void *sigE, const void *emis,

@@ -118,6 +118,16 @@ def lib():
     L.trt_k_grey_newton.restype = ctypes.c_int
     L.trt_k_grey_newton.argtypes = [_vp, ctypes.c_double, _vp, _vp, _vp, _vp, ctypes.c_int,
                                     ctypes.POINTER(trt_level), _vp]
+    _ip = ctypes.POINTER(ctypes.c_int)
+    L.trt_sweep_time.restype = ctypes.c_int
+    L.trt_sweep_time.argtypes = [_vp, ctypes.c_double, ctypes.c_int,
+                                 ctypes.POINTER(ctypes.c_float)]
+    L.trt_autotune.restype = ctypes.c_int
+    L.trt_autotune.argtypes = [_vp, ctypes.c_double, ctypes.c_int, _ip, _ip, _ip]
+    L.trt_sweep_shapes.restype = ctypes.c_int
+    L.trt_sweep_shapes.argtypes = [_vp]
+    L.trt_set_sweep_tile.restype = ctypes.c_int
+    L.trt_set_sweep_tile.argtypes = [_vp, ctypes.c_int, ctypes.c_int]
     L.trt_sweep_noalloc_scratch_bytes.restype = ctypes.c_size_t
     L.trt_sweep_noalloc_scratch_bytes.argtypes = [ctypes.c_int] * 3
     L.trt_sweep_noalloc.restype = ctypes.c_int
@@ -131,6 +141,7 @@ def lib():
 EXPORTED = ("trt_workspace_bytes", "trt_create", "trt_step", "trt_moments", "trt_intensity",
             "trt_set_state", "trt_dims", "trt_destroy", "trt_last_error", "trt_k_opacity",
             "trt_k_sweep", "trt_k_lo_solve", "trt_k_restrict", "trt_k_grey_newton",
+            "trt_sweep_time", "trt_autotune", "trt_sweep_shapes", "trt_set_sweep_tile",
             "trt_sweep_noalloc_scratch_bytes", "trt_sweep_noalloc", "trt_sweep_noalloc_error")
 
 
@@ -319,6 +330,25 @@ class Solver:
                                      ctypes.byref(lv), T.data_ptr())
         self._check(rc, allow=(TRT_ENUMERIC,))
         return rc, T, {k: keep[k] for k in ("E", "F", "Eb0", "EbX")}
+
+    def sweep_time(self, dt, reps=10) -> float:
+        """ms per sweep of the step's own sweep configuration (state unchanged)."""
+        ms = ctypes.c_float()
+        self._check(lib().trt_sweep_time(self.h, float(dt), int(reps), ctypes.byref(ms)))
+        return ms.value
+
+    def autotune(self, dt, reps=5):
+        """Time every candidate sweep tile and keep the fastest; returns (D, S, NS)."""
+        D, S, NS = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        self._check(lib().trt_autotune(self.h, float(dt), int(reps), ctypes.byref(D),
+                                       ctypes.byref(S), ctypes.byref(NS)))
+        return D.value, S.value, NS.value
+
+    def set_sweep_tile(self, D, shape):
+        self._check(lib().trt_set_sweep_tile(self.h, int(D), int(shape)))
+
+    def sweep_shapes(self) -> int:
+        return lib().trt_sweep_shapes(self.h)
 
     def close(self):
         if getattr(self, "h", None):

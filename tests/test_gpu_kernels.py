@@ -136,6 +136,62 @@ def test_sweep_sampled_full_size(trt, orc):
     assert rel(C0[gs], oC0) < 1e-11 and rel(fbX[gs], ofbX) < 1e-11
 
 
+@pytest.mark.parametrize("precision", ["fp64", "sweep32"])
+def test_sweep_every_tile(trt, orc, precision):
+    """Every candidate sweep tile (directions per CTA x strip length x buffers) gives the
+    oracle's sweep: FP64 to round-off, FP32 to FP32 accuracy.  70 cells span several
+    strips of every length with a ragged last strip; 40 groups leave a partial warp."""
+    nx, N, G = 70, 8, 40
+    r, h, sig, em, I_old, TL = sweep_inputs(orc, 2500, nx, N, G, thick=True)
+    edges = W.group_edges(G, 1e-5, 1e2)
+    s = solver(trt, nx=nx, N=N, G=G, h=h, edges=edges, TL=TL, TR=0.3, precision=precision)
+    dt = 1.7e-3
+    mu, w = orc.double_gl(N)
+    Iin0 = orc.group_physics(edges, TL)[0]
+    IinX = orc.group_physics(edges, 0.3)[0]
+    oI, of, ofb0, ofbX, oC0, oCX = orc.sweep(h, mu, w, sig, em, 1.0 / (C * dt), I_old, Iin0, IinX)
+    tol_I, tol_f = (1e-12, 1e-11) if precision == "fp64" else (2e-5, 2e-5)
+    n = 0
+    for D in (4, 8):
+        for shape in range(s.sweep_shapes()):
+            s.set_sweep_tile(D, shape)
+            In, f, fb0, fbX, C0, CX = (x.cpu().numpy() for x in s.k_sweep(dt, sig, em, I_old))
+            assert pair_err(In, oI) < tol_I, (D, shape)
+            assert rel(f, of) < tol_f, (D, shape)
+            for a, b in ((fb0, ofb0), (fbX, ofbX), (C0, oC0), (CX, oCX)):
+                assert rel(a, b) < tol_f, (D, shape)
+            n += 1
+    assert n >= 6
+    with pytest.raises(trt.TRTError):
+        s.set_sweep_tile(3, 0)
+    with pytest.raises(trt.TRTError):
+        s.set_sweep_tile(4, s.sweep_shapes())
+
+
+def test_autotune_keeps_state(trt):
+    """trt_autotune / trt_sweep_time leave T, E_g, F_g, I and the QD factors unchanged and
+    keep a candidate tile; steps after tuning match steps without it to round-off."""
+    cfg = W.scaled(W.fc_small(), 60, 8, 64, levels=[64, 16, 4, 1])
+    a = trt.Solver.from_slab(cfg)
+    b = trt.Solver.from_slab(cfg)
+    a.step(cfg.dt, "V", 2, 1e-8)
+    b.step(cfg.dt, "V", 2, 1e-8)
+    m0, (I0, f0) = a.moments(), a.intensity()
+    D, S, NS = a.autotune(cfg.dt, reps=2)
+    assert D in (4, 8) and S in (8, 16, 32) and NS >= 2
+    assert a.sweep_time(cfg.dt, reps=2) > 0
+    m1, (I1, f1) = a.moments(), a.intensity()
+    for k in m0:
+        assert np.array_equal(m0[k], m1[k]), k
+    assert np.array_equal(I0, I1) and np.array_equal(f0, f1)
+    for _ in range(2):
+        sa = a.step(cfg.dt, "W", 2, 1e-8)
+        sb = b.step(cfg.dt, "W", 2, 1e-8)
+        assert sa["n_ti"] == sb["n_ti"]
+    ma, mb = a.moments(), b.moments()
+    assert np.max(np.abs(ma["T"] - mb["T"]) / mb["T"]) < 1e-12
+
+
 # ---------------------------------------------------------------------------- K3 / K4
 def random_level(r, ng, nx, eta=True):
     z = lambda shape: r.uniform(0, 0.2, shape) * (r.uniform(size=shape) < 0.5)
