@@ -46,7 +46,7 @@ extern "C" {
 #define TRT_EINVAL         -1   /* bad argument; nothing was enqueued                   */
 #define TRT_ENOTCONVERGED  -2   /* outer loop hit max_outer; the state is the last iterate */
 #define TRT_ENUMERIC       -3   /* a temperature came out non-positive or non-finite     */
-#define TRT_ETIMEOUT       -4   /* a bounded device wait gave up (reserved)              */
+#define TRT_ETIMEOUT       -4   /* a bounded device wait gave up (trt_mlp.h kernels)     */
 #define TRT_ECUDA          -5   /* a CUDA runtime call failed; see trt_last_error        */
 #define TRT_ENOSPACE       -6   /* workspace smaller than trt_workspace_bytes            */
 

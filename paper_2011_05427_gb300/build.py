@@ -14,7 +14,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libtrt.so")
-SOURCES = ["physics.cu", "sweep.cu", "lo.cu", "api.cu", "noalloc.cu"]
+SOURCES = ["physics.cu", "sweep.cu", "lo.cu", "api.cu", "noalloc.cu", "mlp.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xptxas", "-v",
@@ -23,7 +23,7 @@ FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xptxas", "-v
 
 def _deps():
     hdrs = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))]
-    return hdrs + [os.path.join(ROOT, "include", "trt.h")]
+    return hdrs + [os.path.join(ROOT, "include", f) for f in ("trt.h", "trt_mlp.h")]
 
 
 def _stale(obj, src):

@@ -1,0 +1,674 @@
+// mlp.cu -- the learned closure's network on the tensor cores: a BF16 GEMM on tcgen05
+// (tensor memory accumulators, shared-memory operand descriptors, mbarrier-tracked
+// commits) with fused epilogues, and the MLP's forward, backward, Adam and feature
+// kernels built on it.  The paper has no learned component; see include/trt_mlp.h.
+//
+// GEMM tile: 128 rows x 256 columns per CTA, K in chunks of 64 through two shared-memory
+// stages.  Four warps copy each chunk with cp.async into the canonical no-swizzle K-major
+// layout of the tensor core (8-row x 16-byte core matrices, 128 contiguous bytes each; the
+// 8 core matrices of a row group along K are adjacent, 128 bytes apart, and row groups are
+// 1024 bytes apart -- either reading of the two descriptor strides stays inside the stage);
+// one thread issues four tcgen05.mma (M 128, N 256, K 16) per chunk and commits them to
+// the stage's mbarrier, which releases the stage for the chunk after next.  The 128 x 256
+// FP32 accumulator lives in 256 tensor-memory columns; in the epilogue thread t owns row
+// t (tensor-memory lane t) and reads its 256 values 32 at a time with tcgen05.ld.
+#include <cuda_bf16.h>
+#include <stdint.h>
+#include "common.cuh"
+#include "../../include/trt_mlp.h"
+
+namespace trt {
+
+namespace {
+
+typedef __nv_bfloat16 bf16;
+
+constexpr int BM = 128, BN = 256, BK = 64;
+constexpr int A_STAGE = BM * BK * 2;   // 16 KB
+constexpr int B_STAGE = BN * BK * 2;   // 32 KB
+constexpr int GEMM_SMEM = 2 * (A_STAGE + B_STAGE) + 256;
+// core-matrix (row group r, K group k) of a stage at (r * 8 + k) * 128: leading-dimension
+// (K) byte offset 128, stride-dimension (row group) byte offset 1024
+constexpr uint32_t LBO = 128, SBO = 1024;
+// instruction descriptor, kind::f16: D FP32 (bits 4-5 = 1), A and B BF16 (bits 7-9,
+// 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 at bits 17-22, M >> 4 at bits 24-28
+constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                           ((uint32_t)(BM >> 4) << 24);
+constexpr unsigned long long WAIT_NS = 1000000000ull;   // one second
+
+__device__ int g_mlp_err = 0;
+
+__device__ inline uint32_t su32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ inline unsigned long long gtime()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ inline void mbar_init(uint64_t *bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(bar)), "r"(count));
+}
+
+__device__ inline bool mbar_test(uint64_t *bar, unsigned parity)
+{
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(su32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// bounded wait on a phase of an mbarrier: false after WAIT_NS without completion
+__device__ inline bool mbar_wait(uint64_t *bar, unsigned parity)
+{
+    if (mbar_test(bar, parity)) return true;
+    const unsigned long long t0 = gtime();
+    while (!mbar_test(bar, parity))
+        if (gtime() - t0 > WAIT_NS) return false;
+    return true;
+}
+
+__device__ inline void cp16(void *dst, const void *src, unsigned bytes)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(su32(dst)), "l"(src),
+                 "r"(bytes));
+}
+__device__ inline void cp_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ inline void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
+__device__ inline void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ inline void tc_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ inline void tc_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// shared-memory operand descriptor: start >> 4 (bits 0-13), leading-dimension byte offset
+// >> 4 (16-29), stride-dimension byte offset >> 4 (32-45), descriptor version 1 (46-47),
+// base offset 0, no swizzle (61-63 = 0)
+__device__ inline uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
+{
+    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)(lbo >> 4) << 16) |
+           ((uint64_t)(sbo >> 4) << 32) | (1ull << 46);
+}
+
+__device__ inline void umma(uint32_t tmem, uint64_t a, uint64_t b, uint32_t acc)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+        "l"(a), "l"(b), "r"(IDESC), "r"(acc));
+}
+
+__device__ inline void umma_commit(uint64_t *bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     su32(bar))
+                 : "memory");
+}
+
+// 32 consecutive FP32 columns of this warp's 32 tensor-memory lanes (one per thread)
+__device__ inline void tmem_ld32(uint32_t taddr, float *v)
+{
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+          "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+          "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+struct Epi {
+    const float *bias;
+    int relu;
+    const bf16 *mask;
+    float *out32;
+    bf16 *out16, *out16T;
+    int ldT;
+    // head: z = sum_n act[n] w[n] + b, y = sigmoid(z); with a target, also
+    // dz = scale (y - t) y (1 - y), sq = (y - t)^2, dact = dz w[n] [act > 0]
+    const float *head_w;
+    const float *head_b;   // device pointer to the head's bias
+    float *head_y;
+    const float *target;
+    float scale;
+    float *dz, *sq;
+    bf16 *dact16, *dact16T;
+};
+
+__global__ void __launch_bounds__(128) k_gemm(int M, int N, int K, const bf16 *__restrict__ A,
+                                              const bf16 *__restrict__ B, Epi e)
+{
+    extern __shared__ __align__(1024) unsigned char sm[];
+    unsigned char *sA = sm;
+    unsigned char *sB = sm + 2 * A_STAGE;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(sm + 2 * (A_STAGE + B_STAGE));
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(bar + 2);
+    int *sfail = reinterpret_cast<int *>(tslot + 1);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+    const int nk = K / BK;
+
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        *sfail = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         su32(tslot)),
+                     "r"(256));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    tc_before();
+    __syncthreads();
+    tc_after();
+    const uint32_t tmem = *tslot;
+
+    // chunk c of A (128 x 64) and B (256 x 64) into stage st in 16-byte pieces: piece p
+    // is row p & 7 of core matrix (row group p >> 6, K group (p >> 3) & 7), i.e. shared
+    // offset 16 p (conflict-free); rows of A past M are zero-filled
+    auto load = [&](int c, int st) {
+        const int k0 = c * BK;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int p = tid + 128 * j;
+            const int r8 = p & 7, ki = (p >> 3) & 7, mi = p >> 6;
+            const int row = m0 + mi * 8 + r8;
+            const bf16 *src = A + (size_t)min(row, M - 1) * K + k0 + ki * 8;
+            cp16(sA + st * A_STAGE + p * 16, src, row < M ? 16u : 0u);
+        }
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            const int p = tid + 128 * j;
+            const int r8 = p & 7, ki = (p >> 3) & 7, ni = p >> 6;
+            const bf16 *src = B + (size_t)(n0 + ni * 8 + r8) * K + k0 + ki * 8;
+            cp16(sB + st * B_STAGE + p * 16, src, 16u);
+        }
+    };
+
+    load(0, 0);
+    cp_commit();
+    if (nk > 1) load(1, 1);
+    cp_commit();
+    bool ok = true;
+    for (int c = 0; c < nk; ++c) {
+        const int st = c & 1;
+        if (c + 1 < nk)
+            cp_wait<1>();
+        else
+            cp_wait<0>();
+        fence_async_smem();   // this thread's copies -> visible to the tensor core
+        __syncthreads();
+        if (*sfail) { ok = false; break; }
+        if (tid == 0) {
+            tc_after();
+            const uint32_t a0 = su32(sA + st * A_STAGE), b0 = su32(sB + st * B_STAGE);
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk)   // K = 16 per instruction: 2 core matrices
+                umma(tmem, sdesc(a0 + kk * 2 * LBO, LBO, SBO), sdesc(b0 + kk * 2 * LBO, LBO, SBO),
+                     (c | kk) != 0);
+            umma_commit(&bar[st]);
+        }
+        if (c + 2 < nk) {
+            // stage st takes chunk c + 2 once the MMAs of chunk c have read it
+            if (!mbar_wait(&bar[st], (c >> 1) & 1)) *sfail = 1;
+            __syncthreads();
+            if (*sfail) { ok = false; break; }
+            load(c + 2, st);
+            cp_commit();
+        }
+    }
+    if (ok && !mbar_wait(&bar[(nk - 1) & 1], ((nk - 1) >> 1) & 1)) ok = false;
+    ok = !__syncthreads_or(!ok);   // CTA-uniform: the tensor-memory loads are warp-collective
+    if (!ok) {
+        cp_wait<0>();
+        if (lane == 0) atomicExch(&g_mlp_err, TRT_ETIMEOUT);
+    }
+    tc_after();
+
+    const int row = m0 + tid;
+    if (ok) {
+        float dot = 0.f;
+        for (int ch = 0; ch < BN / 32; ++ch) {
+            float v[32];
+            tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + ch * 32, v);
+            if (row >= M) continue;
+            const int nb = n0 + ch * 32;
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                float a = v[j];
+                if (e.bias) a += e.bias[nb + j];
+                if (e.relu) a = fmaxf(a, 0.f);
+                v[j] = a;
+            }
+            if (e.mask) {
+                const uint4 *mk = reinterpret_cast<const uint4 *>(e.mask + (size_t)row * N + nb);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const uint4 u = mk[q];
+                    const bf16 *hb = reinterpret_cast<const bf16 *>(&u);
+#pragma unroll
+                    for (int j = 0; j < 8; ++j)
+                        if (!(__bfloat162float(hb[j]) > 0.f)) v[q * 8 + j] = 0.f;
+                }
+            }
+            if (e.out32) {
+                float4 *o = reinterpret_cast<float4 *>(e.out32 + (size_t)row * N + nb);
+#pragma unroll
+                for (int q = 0; q < 8; ++q)
+                    o[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+            }
+            if (e.out16) {
+                uint4 *o = reinterpret_cast<uint4 *>(e.out16 + (size_t)row * N + nb);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    uint4 u;
+                    bf16 *hb = reinterpret_cast<bf16 *>(&u);
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) hb[j] = __float2bfloat16_rn(v[q * 8 + j]);
+                    o[q] = u;
+                }
+            }
+            if (e.out16T) {
+#pragma unroll
+                for (int j = 0; j < 32; ++j)
+                    e.out16T[(size_t)(nb + j) * e.ldT + row] = __float2bfloat16_rn(v[j]);
+            }
+            if (e.head_w) {
+#pragma unroll
+                for (int j = 0; j < 32; ++j) dot = fmaf(v[j], e.head_w[nb + j], dot);
+            }
+        }
+        float dz = 0.f;
+        if (e.head_w && row < M) {
+            const float z = dot + *e.head_b;
+            const float y = 1.f / (1.f + __expf(-z));
+            if (e.head_y) e.head_y[row] = y;
+            if (e.target) {
+                const float d = y - e.target[row];
+                dz = e.scale * d * y * (1.f - y);
+                e.dz[row] = dz;
+                e.sq[row] = 0.5f * e.scale * d * d;
+            }
+        }
+        if (e.head_w && e.target) {
+            // second pass over the accumulator (all threads: the loads are warp-collective)
+            // for the gradient of the last hidden layer, dz w4 [h3 > 0]
+            for (int ch = 0; ch < BN / 32; ++ch) {
+                float v[32];
+                tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + ch * 32, v);
+                if (row >= M) continue;
+                const int nb = n0 + ch * 32;
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    const float a = v[j] + (e.bias ? e.bias[nb + j] : 0.f);
+                    const bf16 gb = __float2bfloat16_rn((a > 0.f) ? dz * e.head_w[nb + j] : 0.f);
+                    e.dact16[(size_t)row * N + nb + j] = gb;
+                    e.dact16T[(size_t)(nb + j) * e.ldT + row] = gb;
+                }
+            }
+        }
+    }
+    tc_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256));
+    }
+}
+
+cudaError_t gemm(int M, int N, int K, const bf16 *A, const bf16 *B, const Epi &e,
+                 cudaStream_t st)
+{
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t r = cudaFuncSetAttribute(k_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             GEMM_SMEM);
+        if (r != cudaSuccess) return r;
+        attr = true;
+    }
+    dim3 grid((M + BM - 1) / BM, N / BN);
+    k_gemm<<<grid, 128, GEMM_SMEM, st>>>(M, N, K, A, B, e);
+    return cudaGetLastError();
+}
+
+// ---- MLP pieces on CUDA cores ----
+
+// h1 = relu(W1 x + b1) per row (FP32), stored BF16 row-major and optionally transposed
+__global__ void k_layer1(int R, const float *__restrict__ x, const float *__restrict__ P,
+                         bf16 *__restrict__ h1, bf16 *__restrict__ h1T, int ldT)
+{
+    __shared__ float w[TRT_MLP_HIDDEN * 4];
+    for (int i = threadIdx.x; i < TRT_MLP_HIDDEN; i += blockDim.x) {
+        w[4 * i + 0] = P[TRT_MLP_W1 + 3 * i + 0];
+        w[4 * i + 1] = P[TRT_MLP_W1 + 3 * i + 1];
+        w[4 * i + 2] = P[TRT_MLP_W1 + 3 * i + 2];
+        w[4 * i + 3] = P[TRT_MLP_B1 + i];
+    }
+    __syncthreads();
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= R) return;
+    const float x0 = x[3 * r], x1 = x[3 * r + 1], x2 = x[3 * r + 2];
+    uint4 *o = reinterpret_cast<uint4 *>(h1 + (size_t)r * TRT_MLP_HIDDEN);
+    for (int q = 0; q < TRT_MLP_HIDDEN / 8; ++q) {
+        uint4 u;
+        bf16 *hb = reinterpret_cast<bf16 *>(&u);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int c = q * 8 + j;
+            float a = w[4 * c + 3];
+            a = fmaf(w[4 * c + 0], x0, a);
+            a = fmaf(w[4 * c + 1], x1, a);
+            a = fmaf(w[4 * c + 2], x2, a);
+            hb[j] = __float2bfloat16_rn(fmaxf(a, 0.f));
+            if (h1T) h1T[(size_t)c * ldT + r] = hb[j];
+        }
+        o[q] = u;
+    }
+}
+
+// out[c] = sum_r a[r][c] * (wr ? wr[r * ws + wo] : 1), c < ncol; a is BF16 or FP32 with row
+// stride lda; fixed summation order: 8 row slices per column, then the slices in order
+template <typename T>
+__global__ void k_colsum(int R, int ncol, const T *__restrict__ a, int lda,
+                         const float *__restrict__ wr, int ws, int wo, float *__restrict__ out)
+{
+    __shared__ float part[8][33];
+    const int cl = threadIdx.x & 31, sl = threadIdx.x >> 5;
+    const int c = blockIdx.x * 32 + cl;
+    float s = 0.f;
+    if (c < ncol)
+        for (int r = sl; r < R; r += 8) {
+            const float v = (float)a[(size_t)r * lda + c];
+            s = fmaf(v, wr ? wr[(size_t)r * ws + wo] : 1.f, s);
+        }
+    part[sl][cl] = s;
+    __syncthreads();
+    if (sl == 0 && c < ncol) {
+        float t = 0.f;
+        for (int k = 0; k < 8; ++k) t += part[k][cl];
+        out[c] = t;
+    }
+}
+
+// dW1[c][k] = sum_r d1[r][c] x[r][k]: one column sum per (c, k), written at stride 3
+__global__ void k_dw1(int R, const float *__restrict__ d1, const float *__restrict__ x,
+                      float *__restrict__ g)
+{
+    __shared__ float part[8][33];
+    const int cl = threadIdx.x & 31, sl = threadIdx.x >> 5;
+    const int c = blockIdx.x * 32 + cl, k = blockIdx.y;
+    float s = 0.f;
+    for (int r = sl; r < R; r += 8) s = fmaf(d1[(size_t)r * TRT_MLP_HIDDEN + c], x[3 * r + k], s);
+    part[sl][cl] = s;
+    __syncthreads();
+    if (sl == 0) {
+        float t = 0.f;
+        for (int q = 0; q < 8; ++q) t += part[q][cl];
+        g[TRT_MLP_W1 + 3 * c + k] = t;
+    }
+}
+
+// W2, W3 (BF16) and their transposes from the FP32 master parameters
+__global__ void k_refresh(const float *__restrict__ P, bf16 *__restrict__ w16)
+{
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;   // 2 x 65536
+    if (idx >= 2 * 65536) return;
+    const int layer = idx >> 16, o = (idx >> 8) & 255, i = idx & 255;
+    const float v = P[(layer ? TRT_MLP_W3 : TRT_MLP_W2) + o * 256 + i];
+    const bf16 b = __float2bfloat16_rn(v);
+    w16[layer * 65536 + o * 256 + i] = b;                 // W [out][in]
+    w16[(2 + layer) * 65536 + i * 256 + o] = b;           // W^T [in][out]
+}
+
+__global__ void k_adam(int n, float *__restrict__ P, const float *__restrict__ g,
+                       float *__restrict__ m, float *__restrict__ v, float lr, float b1,
+                       float b2, float eps, float c1, float c2)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    P[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+}
+
+__global__ void k_features(int nx, int G, const double *__restrict__ T,
+                           const double *__restrict__ sigE, const double *__restrict__ Eg,
+                           const double *__restrict__ Ecell, float *__restrict__ x)
+{
+    const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long)G * nx) return;
+    const int i = (int)(idx % nx);
+    const double t = fmax(T[i], 1e-30);
+    const double s = fmax(sigE[idx], 1e-300);
+    const double r = fmax(Eg[idx], 1e-300) / fmax(Ecell[i], 1e-300);
+    x[3 * idx + 0] = (float)((log(t) + 3.5) * 0.5);
+    x[3 * idx + 1] = (float)((log(s) - 10.0) * 0.1);
+    x[3 * idx + 2] = (float)((log(r) + 10.0) * 0.1);
+}
+
+inline size_t al256(size_t x) { return (x + 255) / 256 * 256; }
+
+struct Scratch {
+    bf16 *h1, *h1T, *h2, *h2T, *h3, *d3, *d3T, *d2, *d2T;
+    float *d1, *dz, *sq;
+    size_t bytes;
+};
+
+Scratch carve_scratch(void *base, int R, int training)
+{
+    Scratch s{};
+    char *p = reinterpret_cast<char *>(base);
+    size_t o = 0;
+    const size_t hb = al256((size_t)R * TRT_MLP_HIDDEN * sizeof(bf16));
+    auto take = [&](size_t n) { char *q = p ? p + o : nullptr; o += n; return q; };
+    s.h1 = reinterpret_cast<bf16 *>(take(hb));
+    s.h2 = reinterpret_cast<bf16 *>(take(hb));
+    if (training) {
+        s.h1T = reinterpret_cast<bf16 *>(take(hb));
+        s.h2T = reinterpret_cast<bf16 *>(take(hb));
+        s.h3 = reinterpret_cast<bf16 *>(take(hb));
+        s.d3 = reinterpret_cast<bf16 *>(take(hb));
+        s.d3T = reinterpret_cast<bf16 *>(take(hb));
+        s.d2 = reinterpret_cast<bf16 *>(take(hb));
+        s.d2T = reinterpret_cast<bf16 *>(take(hb));
+        s.d1 = reinterpret_cast<float *>(take(al256((size_t)R * TRT_MLP_HIDDEN * sizeof(float))));
+        s.dz = reinterpret_cast<float *>(take(al256((size_t)R * sizeof(float))));
+        s.sq = reinterpret_cast<float *>(take(al256((size_t)R * sizeof(float))));
+    }
+    s.bytes = o;
+    return s;
+}
+
+bool al16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+
+}  // namespace
+
+}  // namespace trt
+
+using namespace trt;
+
+extern "C" {
+
+int trt_gemm_bf16(int M, int N, int K, const void *A, const void *B, const float *bias, int relu,
+                  const void *mask, float *out32, void *out16, void *out16T, int ldT,
+                  void *stream)
+{
+    if (M < 1 || N < BN || N % BN || K < BK || K % BK || !A || !B) return TRT_EINVAL;
+    if (out16T && ldT < M) return TRT_EINVAL;
+    if (!al16(A) || !al16(B) || !al16(mask) || !al16(out32) || !al16(out16)) return TRT_EINVAL;
+    Epi e{};
+    e.bias = bias;
+    e.relu = relu;
+    e.mask = reinterpret_cast<const bf16 *>(mask);
+    e.out32 = out32;
+    e.out16 = reinterpret_cast<bf16 *>(out16);
+    e.out16T = reinterpret_cast<bf16 *>(out16T);
+    e.ldT = ldT;
+    cudaError_t r = gemm(M, N, K, reinterpret_cast<const bf16 *>(A),
+                         reinterpret_cast<const bf16 *>(B), e, reinterpret_cast<cudaStream_t>(stream));
+    return r == cudaSuccess ? TRT_OK : TRT_ECUDA;
+}
+
+size_t trt_mlp_scratch_bytes(int rows, int training)
+{
+    if (rows < 1) return 0;
+    return carve_scratch(nullptr, rows, training).bytes;
+}
+
+int trt_mlp_refresh(const float *params, void *w16, void *stream)
+{
+    if (!params || !w16) return TRT_EINVAL;
+    k_refresh<<<512, 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(
+        params, reinterpret_cast<bf16 *>(w16));
+    return cudaGetLastError() == cudaSuccess ? TRT_OK : TRT_ECUDA;
+}
+
+int trt_mlp_forward(int rows, const float *x, const float *params, const void *w16,
+                    void *scratch, size_t scratch_bytes, float *y, void *stream)
+{
+    if (rows < 1 || !x || !params || !w16 || !scratch || !y) return TRT_EINVAL;
+    Scratch s = carve_scratch(scratch, rows, 0);
+    if (scratch_bytes < s.bytes || !al16(scratch)) return TRT_EINVAL;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const bf16 *W = reinterpret_cast<const bf16 *>(w16);
+    k_layer1<<<(rows + 127) / 128, 128, 0, st>>>(rows, x, params, s.h1, nullptr, 0);
+    if (cudaGetLastError() != cudaSuccess) return TRT_ECUDA;
+    Epi e2{};
+    e2.bias = params + TRT_MLP_B2;
+    e2.relu = 1;
+    e2.out16 = s.h2;
+    if (gemm(rows, 256, 256, s.h1, W, e2, st) != cudaSuccess) return TRT_ECUDA;
+    Epi e3{};
+    e3.bias = params + TRT_MLP_B3;
+    e3.relu = 1;
+    e3.head_w = params + TRT_MLP_W4;
+    e3.head_b = params + TRT_MLP_B4;
+    e3.head_y = y;
+    if (gemm(rows, 256, 256, s.h2, W + 65536, e3, st) != cudaSuccess) return TRT_ECUDA;
+    return TRT_OK;
+}
+
+int trt_mlp_grad(int rows, const float *x, const float *target, const float *params,
+                 const void *w16, void *scratch, size_t scratch_bytes, float *grad, float *loss,
+                 void *stream)
+{
+    if (rows < 128 || rows % 128 || !x || !target || !params || !w16 || !scratch || !grad ||
+        !loss)
+        return TRT_EINVAL;
+    Scratch s = carve_scratch(scratch, rows, 1);
+    if (scratch_bytes < s.bytes || !al16(scratch)) return TRT_EINVAL;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const bf16 *W = reinterpret_cast<const bf16 *>(w16);
+    const bf16 *W2 = W, *W3 = W + 65536, *W2T = W + 2 * 65536, *W3T = W + 3 * 65536;
+#define CKL(x)                                            \
+    do {                                                  \
+        if ((x) != cudaSuccess) return TRT_ECUDA;         \
+    } while (0)
+    k_layer1<<<(rows + 127) / 128, 128, 0, st>>>(rows, x, params, s.h1, s.h1T, rows);
+    CKL(cudaGetLastError());
+    Epi e2{};
+    e2.bias = params + TRT_MLP_B2;
+    e2.relu = 1;
+    e2.out16 = s.h2;
+    e2.out16T = s.h2T;
+    e2.ldT = rows;
+    CKL(gemm(rows, 256, 256, s.h1, W2, e2, st));
+    Epi e3{};
+    e3.bias = params + TRT_MLP_B3;
+    e3.relu = 1;
+    e3.out16 = s.h3;
+    e3.head_w = params + TRT_MLP_W4;
+    e3.head_b = params + TRT_MLP_B4;
+    e3.target = target;
+    e3.scale = 2.f / rows;
+    e3.dz = s.dz;
+    e3.sq = s.sq;
+    e3.dact16 = s.d3;
+    e3.dact16T = s.d3T;
+    e3.ldT = rows;
+    CKL(gemm(rows, 256, 256, s.h2, W3, e3, st));
+    // d2 = (d3 W3) [h2 > 0];  dW3 = d3^T h2
+    Epi eb{};
+    eb.mask = s.h2;
+    eb.out16 = s.d2;
+    eb.out16T = s.d2T;
+    eb.ldT = rows;
+    CKL(gemm(rows, 256, 256, s.d3, W3T, eb, st));
+    Epi ew{};
+    ew.out32 = grad + TRT_MLP_W3;
+    CKL(gemm(256, 256, rows, s.d3T, s.h2T, ew, st));
+    // d1 = (d2 W2) [h1 > 0];  dW2 = d2^T h1
+    Epi e1{};
+    e1.mask = s.h1;
+    e1.out32 = s.d1;
+    CKL(gemm(rows, 256, 256, s.d2, W2T, e1, st));
+    Epi ew2{};
+    ew2.out32 = grad + TRT_MLP_W2;
+    CKL(gemm(256, 256, rows, s.d2T, s.h1T, ew2, st));
+    // biases, W1, w4, b4, loss: fixed-order column sums over the rows
+    k_colsum<bf16><<<8, 256, 0, st>>>(rows, 256, s.d3, 256, nullptr, 0, 0, grad + TRT_MLP_B3);
+    k_colsum<bf16><<<8, 256, 0, st>>>(rows, 256, s.d2, 256, nullptr, 0, 0, grad + TRT_MLP_B2);
+    k_colsum<float><<<8, 256, 0, st>>>(rows, 256, s.d1, 256, nullptr, 0, 0, grad + TRT_MLP_B1);
+    k_colsum<bf16><<<8, 256, 0, st>>>(rows, 256, s.h3, 256, s.dz, 1, 0, grad + TRT_MLP_W4);
+    k_colsum<float><<<1, 256, 0, st>>>(rows, 1, s.dz, 1, nullptr, 0, 0, grad + TRT_MLP_B4);
+    k_colsum<float><<<1, 256, 0, st>>>(rows, 1, s.sq, 1, nullptr, 0, 0, loss);
+    k_dw1<<<dim3(8, 3), 256, 0, st>>>(rows, s.d1, x, grad);
+    CKL(cudaGetLastError());
+#undef CKL
+    return TRT_OK;
+}
+
+int trt_mlp_adam(float *params, const float *grad, float *m, float *v, int t, float lr,
+                 float beta1, float beta2, float eps, void *w16, void *stream)
+{
+    if (!params || !grad || !m || !v || t < 1 || !w16) return TRT_EINVAL;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const float c1 = 1.f - powf(beta1, (float)t), c2 = 1.f - powf(beta2, (float)t);
+    k_adam<<<(TRT_MLP_NPARAM + 255) / 256, 256, 0, st>>>(TRT_MLP_NPARAM, params, grad, m, v, lr,
+                                                         beta1, beta2, eps, c1, c2);
+    if (cudaGetLastError() != cudaSuccess) return TRT_ECUDA;
+    return trt_mlp_refresh(params, w16, stream);
+}
+
+int trt_mlp_features(int nx, int G, const double *T, const double *sigE, const double *Eg,
+                     const double *E, float *x, void *stream)
+{
+    if (nx < 1 || G < 1 || !T || !sigE || !Eg || !E || !x) return TRT_EINVAL;
+    const long n = (long)G * nx;
+    k_features<<<(unsigned)((n + 255) / 256), 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(
+        nx, G, T, sigE, Eg, E, x);
+    return cudaGetLastError() == cudaSuccess ? TRT_OK : TRT_ECUDA;
+}
+
+int trt_mlp_status(void)
+{
+    int v = 0, zero = 0;
+    if (cudaDeviceSynchronize() != cudaSuccess) return TRT_ECUDA;
+    if (cudaMemcpyFromSymbol(&v, g_mlp_err, sizeof(int)) != cudaSuccess) return TRT_ECUDA;
+    if (cudaMemcpyToSymbol(g_mlp_err, &zero, sizeof(int)) != cudaSuccess) return TRT_ECUDA;
+    return v;
+}
+
+}  // extern "C"

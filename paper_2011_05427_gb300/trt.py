@@ -128,6 +128,24 @@ def lib():
     L.trt_sweep_shapes.argtypes = [_vp]
     L.trt_set_sweep_tile.restype = ctypes.c_int
     L.trt_set_sweep_tile.argtypes = [_vp, ctypes.c_int, ctypes.c_int]
+    # learned closure (include/trt_mlp.h)
+    L.trt_gemm_bf16.restype = ctypes.c_int
+    L.trt_gemm_bf16.argtypes = [ctypes.c_int] * 3 + [_vp] * 3 + [ctypes.c_int] + [_vp] * 4 + \
+        [ctypes.c_int, _vp]
+    L.trt_mlp_scratch_bytes.restype = ctypes.c_size_t
+    L.trt_mlp_scratch_bytes.argtypes = [ctypes.c_int, ctypes.c_int]
+    L.trt_mlp_refresh.restype = ctypes.c_int
+    L.trt_mlp_refresh.argtypes = [_vp] * 3
+    L.trt_mlp_forward.restype = ctypes.c_int
+    L.trt_mlp_forward.argtypes = [ctypes.c_int] + [_vp] * 4 + [ctypes.c_size_t] + [_vp] * 2
+    L.trt_mlp_grad.restype = ctypes.c_int
+    L.trt_mlp_grad.argtypes = [ctypes.c_int] + [_vp] * 5 + [ctypes.c_size_t] + [_vp] * 3
+    L.trt_mlp_adam.restype = ctypes.c_int
+    L.trt_mlp_adam.argtypes = [_vp] * 4 + [ctypes.c_int] + [ctypes.c_float] * 4 + [_vp] * 2
+    L.trt_mlp_features.restype = ctypes.c_int
+    L.trt_mlp_features.argtypes = [ctypes.c_int] * 2 + [_vp] * 6
+    L.trt_mlp_status.restype = ctypes.c_int
+    L.trt_mlp_status.argtypes = []
     L.trt_sweep_noalloc_scratch_bytes.restype = ctypes.c_size_t
     L.trt_sweep_noalloc_scratch_bytes.argtypes = [ctypes.c_int] * 3
     L.trt_sweep_noalloc.restype = ctypes.c_int
@@ -142,7 +160,9 @@ EXPORTED = ("trt_workspace_bytes", "trt_create", "trt_step", "trt_moments", "trt
             "trt_set_state", "trt_dims", "trt_destroy", "trt_last_error", "trt_k_opacity",
             "trt_k_sweep", "trt_k_lo_solve", "trt_k_restrict", "trt_k_grey_newton",
             "trt_sweep_time", "trt_autotune", "trt_sweep_shapes", "trt_set_sweep_tile",
-            "trt_sweep_noalloc_scratch_bytes", "trt_sweep_noalloc", "trt_sweep_noalloc_error")
+            "trt_sweep_noalloc_scratch_bytes", "trt_sweep_noalloc", "trt_sweep_noalloc_error",
+            "trt_gemm_bf16", "trt_mlp_scratch_bytes", "trt_mlp_refresh", "trt_mlp_forward",
+            "trt_mlp_grad", "trt_mlp_adam", "trt_mlp_features", "trt_mlp_status")
 
 
 class TRTError(RuntimeError):

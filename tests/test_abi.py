@@ -1,5 +1,5 @@
 """Host-side checks of the C ABI that need no GPU: the library loads, exports every entry
-point include/trt.h declares, and validates its arguments before touching a device."""
+point include/*.h declares, and validates its arguments before touching a device."""
 import ctypes
 import os
 import re
@@ -18,9 +18,13 @@ def L():
 
 
 def declared_symbols():
-    src = open(os.path.join(ROOT, "include", "trt.h")).read()
-    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(trt_[a-z_]+)\s*\(", src)))
+    out = set()
+    for name in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if name.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", name)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            out |= set(re.findall(r"\b(trt_[a-z0-9_]+)\s*\(", src))
+    return sorted(out)
 
 
 def test_every_declared_symbol_is_exported(L):
