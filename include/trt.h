@@ -190,6 +190,17 @@ int trt_k_sweep(trt_handle *h, double dt, const double *sigE, const double *emis
                 const void *I_old, void *I_new, double *f, double *fb0, double *fbX,
                 double *C0, double *CX);
 
+/* ---- learned closure (not in the paper; include/trt_mlp.h describes the network) ----
+ * With a closure set, every trt_step starts its s = 0 low-order phase from QD factors
+ * f_g predicted by the MLP from the step's initial state (T, sigma_E,g(T), E_g / E)
+ * instead of the previous step's f_g; the sweeps then close the iteration as usual.
+ * params (FP32 [TRT_MLP_NPARAM]) and w16 (BF16 copies, trt_mlp_refresh) are the
+ * network; scratch (>= trt_mlp_scratch_bytes(G * n_cells, 0) bytes), x (FP32
+ * [G * n_cells][3]) and y (FP32 [G * n_cells]) are work buffers.  All caller-owned device
+ * memory that must outlive the steps.  params = NULL removes the closure. */
+int trt_set_closure(trt_handle *h, const float *params, const void *w16, void *scratch,
+                    size_t scratch_bytes, float *x, float *y);
+
 /* ---- sweep tile selection (a tuning aid; the paper has no counterpart) ----
  * The HO sweep (eq. rt, simple corner balance, Sec. 5) runs one warp per (32 groups,
  * direction); a CTA takes D directions of one sign and walks the cells in strips of S,

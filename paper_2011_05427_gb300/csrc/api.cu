@@ -23,6 +23,7 @@
 #include <string>
 #include <vector>
 #include "common.cuh"
+#include "../../include/trt_mlp.h"
 
 using namespace trt;
 
@@ -42,6 +43,12 @@ struct trt_handle {
     double *Ecyc, *Ephase;
     double *flags = nullptr;
     double *hflags = nullptr;   // pinned host buffer, owned (freed in the destructor)
+    // learned closure (trt_set_closure): caller-owned device buffers, or null
+    const float *mlp_params = nullptr;
+    const void *mlp_w16 = nullptr;
+    void *mlp_scratch = nullptr;
+    size_t mlp_scratch_bytes = 0;
+    float *mlp_x = nullptr, *mlp_y = nullptr;
     std::string err;
     ~trt_handle()
     {
@@ -187,6 +194,19 @@ bool validate(const trt_grid *grid, const trt_angles *angles, const trt_groups *
     p.nu_last = edges[p.G];
     p.stream = reinterpret_cast<cudaStream_t>(opt->stream);
     return true;
+}
+
+__global__ void k_f_from_mlp(long n, const float *__restrict__ y, double *__restrict__ f)
+{
+    const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) f[i] = (double)y[i];
+}
+
+cudaError_t launch_f_from_mlp(const Problem &p, const float *y, double *f)
+{
+    const long n = (long)p.G * p.nx;
+    k_f_from_mlp<<<(unsigned)((n + 255) / 256), 256, 0, p.stream>>>(n, y, f);
+    return cudaGetLastError();
 }
 
 template <typename R>
@@ -452,6 +472,19 @@ int trt_step(trt_handle *h, double dt, const trt_cycle *cyc, trt_stats *stats)
     CK(launch_group_sum(p, G, h->Eg_old, h->Ephase));
     ++nk;
     CK(cudaMemsetAsync(h->flags, 0, 8 * sizeof(double), p.stream));
+    if (h->mlp_params) {
+        // learned warm start: the s = 0 phase takes f_g from the MLP instead of f_g^{j-1}
+        CK(launch_opacity(p, h->T, h->sigE, h->emis, h->sigR));
+        opac_valid = true;
+        const int rows = G * nx;
+        int rc = trt_mlp_features(nx, G, h->T, h->sigE, h->Eg_old, h->Ephase, h->mlp_x, p.stream);
+        if (rc == TRT_OK)
+            rc = trt_mlp_forward(rows, h->mlp_x, h->mlp_params, h->mlp_w16, h->mlp_scratch,
+                                 h->mlp_scratch_bytes, h->mlp_y, p.stream);
+        if (rc != TRT_OK) return fail(h, rc, "closure: MLP inference failed");
+        CK(launch_f_from_mlp(p, h->mlp_y, h->f));
+        nk += 6;
+    }
     Level fine = fine_level(h);
 
     for (;;) {
@@ -653,6 +686,26 @@ int trt_k_sweep(trt_handle *h, double dt, const double *sigE, const double *emis
     CK(launch_sweep(h->p, dt, sigE, emis, false, I_old, I_new, h->part, h->psi_exit, f, fb0, fbX,
                     C0, CX));
     CK(cudaStreamSynchronize(h->p.stream));
+    return TRT_OK;
+}
+
+int trt_set_closure(trt_handle *h, const float *params, const void *w16, void *scratch,
+                    size_t scratch_bytes, float *x, float *y)
+{
+    if (!h) return TRT_EINVAL;
+    if (!params) {
+        h->mlp_params = nullptr;
+        return TRT_OK;
+    }
+    const int rows = h->p.G * h->p.nx;
+    if (!w16 || !scratch || !x || !y || scratch_bytes < trt_mlp_scratch_bytes(rows, 0))
+        return fail(h, TRT_EINVAL, "trt_set_closure: missing buffer or scratch too small");
+    h->mlp_params = params;
+    h->mlp_w16 = w16;
+    h->mlp_scratch = scratch;
+    h->mlp_scratch_bytes = scratch_bytes;
+    h->mlp_x = x;
+    h->mlp_y = y;
     return TRT_OK;
 }
 

@@ -128,6 +128,8 @@ def lib():
     L.trt_sweep_shapes.argtypes = [_vp]
     L.trt_set_sweep_tile.restype = ctypes.c_int
     L.trt_set_sweep_tile.argtypes = [_vp, ctypes.c_int, ctypes.c_int]
+    L.trt_set_closure.restype = ctypes.c_int
+    L.trt_set_closure.argtypes = [_vp] * 4 + [ctypes.c_size_t] + [_vp] * 2
     # learned closure (include/trt_mlp.h)
     L.trt_gemm_bf16.restype = ctypes.c_int
     L.trt_gemm_bf16.argtypes = [ctypes.c_int] * 3 + [_vp] * 3 + [ctypes.c_int] + [_vp] * 4 + \
@@ -161,7 +163,7 @@ EXPORTED = ("trt_workspace_bytes", "trt_create", "trt_step", "trt_moments", "trt
             "trt_k_sweep", "trt_k_lo_solve", "trt_k_restrict", "trt_k_grey_newton",
             "trt_sweep_time", "trt_autotune", "trt_sweep_shapes", "trt_set_sweep_tile",
             "trt_sweep_noalloc_scratch_bytes", "trt_sweep_noalloc", "trt_sweep_noalloc_error",
-            "trt_gemm_bf16", "trt_mlp_scratch_bytes", "trt_mlp_refresh", "trt_mlp_forward",
+            "trt_set_closure", "trt_gemm_bf16", "trt_mlp_scratch_bytes", "trt_mlp_refresh", "trt_mlp_forward",
             "trt_mlp_grad", "trt_mlp_adam", "trt_mlp_features", "trt_mlp_status")
 
 
@@ -350,6 +352,22 @@ class Solver:
                                      ctypes.byref(lv), T.data_ptr())
         self._check(rc, allow=(TRT_ENUMERIC,))
         return rc, T, {k: keep[k] for k in ("E", "F", "Eb0", "EbX")}
+
+    def set_closure(self, net):
+        """Warm-start every step's s = 0 phase from the MLP `net` (paper_2011_05427_gb300.mlp.MLP);
+        None removes it."""
+        t = self.torch
+        if net is None:
+            self._check(lib().trt_set_closure(self.h, None, None, None, 0, None, None))
+            self._closure = None
+            return
+        rows = self.G * self.nx
+        x = t.empty((rows, 3), dtype=t.float32, device=self.device)
+        y = t.empty(rows, dtype=t.float32, device=self.device)
+        sc = t.empty(lib().trt_mlp_scratch_bytes(rows, 0), dtype=t.uint8, device=self.device)
+        self._check(lib().trt_set_closure(self.h, net.params.data_ptr(), net.w16.data_ptr(),
+                                          sc.data_ptr(), sc.numel(), x.data_ptr(), y.data_ptr()))
+        self._closure = (net, x, y, sc)   # keep the buffers alive
 
     def sweep_time(self, dt, reps=10) -> float:
         """ms per sweep of the step's own sweep configuration (state unchanged)."""
