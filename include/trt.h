@@ -201,6 +201,36 @@ int trt_k_sweep(trt_handle *h, double dt, const double *sigE, const double *emis
 int trt_set_closure(trt_handle *h, const float *params, const void *w16, void *scratch,
                     size_t scratch_bytes, float *x, float *y);
 
+/* ---- batched slabs (not in the paper: many independent problems at once) ----
+ * n slabs, each as trt_create would take it (grids[s], angles[s], groups[s],
+ * opacities[s], cv[s]; one trt_options for all: precision, T0, stream, workspace), step
+ * together: trt_step_batch runs Algorithm 3 for every slab in lockstep -- each kernel
+ * launch (opacities, sweep, its finalize, every group LOQD solve level, restriction, grey
+ * Newton, state copies) covers all slabs taking part in it, through device-side work lists
+ * built from per-slab flags; each stage of a step is captured once in a CUDA graph and
+ * replayed (a graph needs a non-legacy stream).  Every slab's result is that of
+ * trt_step on the same slab.  The learned closure is not available in a batch.
+ *   - workspace: one caller-owned device buffer of trt_batch_workspace_bytes; slab s owns
+ *     a slice; the batch allocates only pinned host staging buffers;
+ *   - stats: n entries (or NULL); the return value is the first failing slab's status;
+ *   - trt_batch_slab: the handle of slab s, for trt_moments / trt_intensity / trt_dims
+ *     (do not destroy it: trt_destroy_batch does);
+ *   - trt_batch_set_tile: directions per CTA D (a power of two dividing every slab's N,
+ *     <= 8) and sweep shape of the batched sweep; trt_batch_sweep_time: ms per batched
+ *     sweep (all slabs, incl. the finalize), CUDA events, QD factors left unchanged. */
+typedef struct trt_batch trt_batch;
+size_t trt_batch_workspace_bytes(int n, const trt_grid *grids, const trt_angles *angles,
+                                 const trt_groups *groups, const trt_options *opt);
+int trt_create_batch(int n, const trt_grid *grids, const trt_angles *angles,
+                     const trt_groups *groups, const trt_opacity *opacities, const double *cv,
+                     const trt_options *opt, trt_batch **out);
+int trt_step_batch(trt_batch *b, double dt_sh, const trt_cycle *cycle, trt_stats *stats);
+trt_handle *trt_batch_slab(trt_batch *b, int s);
+int trt_batch_set_tile(trt_batch *b, int D, int shape);
+int trt_batch_sweep_time(trt_batch *b, double dt, int reps, float *ms);
+int trt_destroy_batch(trt_batch *b);
+const char *trt_batch_last_error(const trt_batch *b);
+
 /* ---- sweep tile selection (a tuning aid; the paper has no counterpart) ----
  * The HO sweep (eq. rt, simple corner balance, Sec. 5) runs one warp per (32 groups,
  * direction); a CTA takes D directions of one sign and walks the cells in strips of S,

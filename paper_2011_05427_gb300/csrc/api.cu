@@ -22,39 +22,13 @@
 #include <memory>
 #include <string>
 #include <vector>
-#include "common.cuh"
+#include "handle.cuh"
 #include "../../include/trt_mlp.h"
 
 using namespace trt;
 
 static std::string g_create_error = "";
 
-struct trt_handle {
-    Problem p;
-    double *T, *Told, *Tcyc, *Tphase, *Ttil, *Tnew, *sig_prev, *T_prev;
-    double *Eg, *Fg, *Eg_old, *Fg_old;
-    void *I_cur, *I_alt;
-    double *f, *fb0, *fbX, *C0, *CX;
-    double *sigE, *emis, *sigR;
-    float *sig32 = nullptr, *emis32 = nullptr;   // FP32 copies for an FP32 sweep
-    double *part, *psi_exit;
-    double *E1, *F1, *Eb0_1, *EbX_1;
-    Level crs, grey;
-    double *Ecyc, *Ephase;
-    double *flags = nullptr;
-    double *hflags = nullptr;   // pinned host buffer, owned (freed in the destructor)
-    // learned closure (trt_set_closure): caller-owned device buffers, or null
-    const float *mlp_params = nullptr;
-    const void *mlp_w16 = nullptr;
-    void *mlp_scratch = nullptr;
-    size_t mlp_scratch_bytes = 0;
-    float *mlp_x = nullptr, *mlp_y = nullptr;
-    std::string err;
-    ~trt_handle()
-    {
-        if (hflags) cudaFreeHost(hflags);
-    }
-};
 
 namespace {
 
@@ -218,38 +192,6 @@ __global__ void k_fill_intensity(R *I, const double *B, long rows, int ldG, int 
         int g = (int)(idx % ldG);
         I[idx] = (g < G) ? (R)B[g] : (R)0;
     }
-}
-
-void schedule(int type, int Gamma, std::vector<int> &S)
-{
-    S.clear();
-    if (Gamma <= 2 || type == TRT_CYCLE_V) return;
-    if (type == TRT_CYCLE_F) {
-        for (int g = Gamma - 1; g >= 2; --g) S.push_back(g);
-        return;
-    }
-    // W: w(Gamma-1) = [Gamma-1]; w(g) = w(g+1) + [g] + w(g+1)
-    std::vector<int> cur{Gamma - 1};
-    for (int g = Gamma - 2; g >= 2; --g) {
-        std::vector<int> nxt(cur);
-        nxt.push_back(g);
-        nxt.insert(nxt.end(), cur.begin(), cur.end());
-        cur.swap(nxt);
-    }
-    S = cur;
-}
-
-Level fine_level(trt_handle *h)
-{
-    Level L;
-    L.n = h->p.G;
-    L.fine = 1;
-    L.phi = h->f; L.sig = h->sigE; L.emis = h->emis; L.Eold = h->Eg_old; L.Esum = nullptr;
-    L.sigR = h->sigR; L.etaR = nullptr; L.etaL = nullptr; L.Fold = h->Fg_old;
-    L.phib0 = h->fb0; L.phibX = h->fbX; L.C0 = h->C0; L.CX = h->CX;
-    L.Ein0 = h->p.Ein0; L.Fin0 = h->p.Fin0; L.EinX = h->p.EinX; L.FinX = h->p.FinX;
-    L.E = h->E1; L.F = h->F1; L.Eb0 = h->Eb0_1; L.EbX = h->EbX_1;
-    return L;
 }
 
 Level from_abi(const trt_level *l)
@@ -532,7 +474,7 @@ int trt_step(trt_handle *h, double dt, const trt_cycle *cyc, trt_stats *stats)
                     src = &h->crs;
                 }
                 CK(launch_restrict(p, *src, h->grey));
-                GreyArgs a;
+                GreyArgs a{};
                 a.Tstar = h->Ttil; a.Told = h->Told; a.sig_prev = h->sig_prev; a.T_prev = h->T_prev;
                 a.T = h->Tnew; a.sig_prev_out = h->sig_prev; a.T_prev_out = h->T_prev;
                 a.have_prev = have_prev;
@@ -836,7 +778,7 @@ int trt_k_grey_newton(trt_handle *h, double dt, const double *Tstar, const doubl
     if (have_prev && (!sig_prev || !T_prev)) return TRT_EINVAL;
     Level L = from_abi(g);
     const Problem &p = h->p;
-    GreyArgs a;
+    GreyArgs a{};
     a.Tstar = Tstar; a.Told = Told;
     a.sig_prev = have_prev ? sig_prev : Tstar;
     a.T_prev = have_prev ? T_prev : Tstar;

@@ -67,6 +67,9 @@ struct GreyArgs {
     const double *Tstar, *Told, *sig_prev, *T_prev;
     double *T, *sig_prev_out, *T_prev_out;
     int have_prev;
+    // when non-null, the device flag replaces have_prev (read at entry, set to 1 on exit):
+    // the batched driver keeps it per slab so that its argument blocks stay fixed
+    int *have_prev_dev;
     double cv, s, dt;
     double nu_first, nu_last;   // first and last group edge (last may be inf)
     // flags[0] |= 1 when a temperature is non-positive or non-finite (always written);

@@ -20,7 +20,7 @@
 // fields; per-warp shared memory holds the chunk coefficients in a [row-in-chunk][lane]
 // layout (conflict free).
 #include <cmath>
-#include "common.cuh"
+#include "batch.cuh"
 
 namespace trt {
 
@@ -33,13 +33,6 @@ __device__ inline double rcpR<double>(double d) { return rcp64(d); }
 template <>
 __device__ inline float rcpR<float>(float d) { return __frcp_rn(d); }
 
-struct LoCtx {
-    int nx;
-    double dt, icdt;
-    const double *h, *ihf;
-    Level L;
-    const double *a_cell, *s_cell;   // grey: explicit absorption / source per cell
-};
 
 __device__ inline double sigR_face(const LoCtx &x, int q, int f)
 {
@@ -335,22 +328,45 @@ __device__ void warp_lo_solve(const LoCtx &x, int q, R *sm, int mmax, bool stage
 #undef CH
 }
 
-inline int lo_mmax(int nx) { return nx < 2 ? 1 : (nx + (std::min(32, nx / 2)) - 1) / std::min(32, nx / 2) + 1; }
+__host__ __device__ inline int lo_mmax(int nx)
+{
+    const int P = nx / 2 < 32 ? nx / 2 : 32;
+    return nx < 2 ? 1 : (nx + P - 1) / P + 1;
+}
 
 // One system per CTA: all 4 warps stage the rows (phase A: the parallel part, global
 // loads and the face coefficients), then warp 0 runs the elimination.
 template <typename R>
-__global__ void __launch_bounds__(128) k_lo_solve(LoCtx x, int mmax)
+__device__ void lo_solve_body(const LoCtx &x, int q)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     R *sm = reinterpret_cast<R *>(smem_raw);
-    const int q = blockIdx.x;
+    const int mmax = lo_mmax(x.nx);
     const bool staged = x.nx >= 2;
     if (staged) {
         lo_stage<R>(x, q, sm, mmax, threadIdx.x, blockDim.x);
         __syncthreads();
     }
     if (threadIdx.x < 32) warp_lo_solve<R>(x, q, sm, mmax, staged);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(128) k_lo_solve(LoCtx x)
+{
+    lo_solve_body<R>(x, blockIdx.x);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(128) k_lo_solve_b(const int *__restrict__ meta, int N,
+                                                    const LoCtx *__restrict__ xs)
+{
+    for (int b = blockIdx.x;; b += gridDim.x) {
+        int s, bx, by;
+        if (!bdecode(meta, N, b, s, bx, by)) break;
+        const LoCtx x = xs[s];
+        lo_solve_body<R>(x, bx);
+        __syncthreads();
+    }
 }
 
 // ---------------------------------------------------------------------------------------
@@ -360,12 +376,6 @@ __global__ void __launch_bounds__(128) k_lo_solve(LoCtx x, int mmax)
 constexpr int kRV1 = 18;   // pass-1 sums
 constexpr int kRV2 = 6;    // pass-2 sums
 
-struct RestrictCtx {
-    int nx, r;       // r = members per coarse group
-    const double *h, *ihf;
-    Level S;         // source level (coefficients + solution)
-    Level T;         // target level (written)
-};
 
 __device__ inline double src_phi_b(const Level &S, int p, int side)
 {
@@ -373,13 +383,13 @@ __device__ inline double src_phi_b(const Level &S, int p, int side)
 }
 
 // block (32, KS <= 16); grid (ceil((nx+1)/32), n_to)
-__global__ void __launch_bounds__(512) k_restrict(RestrictCtx x)
+__device__ void restrict_body(const RestrictCtx &x, int bx, int by)
 {
     extern __shared__ __align__(16) double rsm[];
     const int tx = threadIdx.x, ty = threadIdx.y, KS = blockDim.y;
     const int nx = x.nx, nf = nx + 1;
-    const int i = blockIdx.x * 32 + tx;   // cell index and face index
-    const int P = blockIdx.y;
+    const int i = bx * 32 + tx;   // cell index and face index
+    const int P = by;
     const int pb = P * x.r;
     const Level &S = x.S;
     double v[kRV1];
@@ -486,7 +496,7 @@ __global__ void __launch_bounds__(512) k_restrict(RestrictCtx x)
         }
     }
     if (ty != 0) return;
-    Level &T = x.T;
+    const Level &T = x.T;
     if (i < nx) {
         size_t c = (size_t)P * nx + i;
         (T.phi)[c] = (v[6] != 0.0) ? v[0] / v[6] : v[1] / rn;
@@ -528,21 +538,15 @@ __global__ void __launch_bounds__(512) k_restrict(RestrictCtx x)
 constexpr int kChunk = 32;
 constexpr int kRP = 25;
 
-struct Restrict2Ctx {
-    int nx, r, nchunk;
-    const double *h, *ihf;
-    Level S, T;
-    double *part;   // [n_to][nchunk][kRP][nx+1]
-};
 
 // block (32, 4); grid (ceil((nx+1)/32), n_to * nchunk)
-__global__ void __launch_bounds__(128) k_restrict_part(Restrict2Ctx x)
+__device__ void restrict_part_body(const Restrict2Ctx &x, int bx, int by)
 {
     __shared__ double red[4][32][kRP + 1];
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int nx = x.nx, nf = nx + 1;
-    const int i = blockIdx.x * 32 + tx;
-    const int P = blockIdx.y / x.nchunk, ch = blockIdx.y - P * x.nchunk;
+    const int i = bx * 32 + tx;
+    const int P = by / x.nchunk, ch = by - P * x.nchunk;
     const int pb = P * x.r + ch * kChunk;
     const int pe = min(pb + kChunk, P * x.r + x.r);
     const Level &S = x.S;
@@ -605,13 +609,13 @@ __global__ void __launch_bounds__(128) k_restrict_part(Restrict2Ctx x)
 
 // block (32, kRP); grid (ceil((nx+1)/32), n_to): thread (tx, k) adds value k of position
 // tx over the chunks in a fixed order, then row 0 forms the coefficients
-__global__ void __launch_bounds__(32 * kRP) k_restrict_final(Restrict2Ctx x)
+__device__ void restrict_final_body(const Restrict2Ctx &x, int bx, int by)
 {
     __shared__ double sv[kRP][33];
     const int nx = x.nx, nf = nx + 1;
     const int tx = threadIdx.x, k = threadIdx.y;
-    const int i = blockIdx.x * 32 + tx;
-    const int P = blockIdx.y;
+    const int i = bx * 32 + tx;
+    const int P = by;
     if (i <= nx) {
         double acc = 0.0;
         const double *o = x.part + ((size_t)P * x.nchunk * kRP + k) * nf + i;
@@ -624,7 +628,7 @@ __global__ void __launch_bounds__(32 * kRP) k_restrict_final(Restrict2Ctx x)
 #pragma unroll
     for (int q = 0; q < kRP; ++q) v[q] = sv[q][tx];
     const double rn = (double)x.r;
-    Level &T = x.T;
+    const Level &T = x.T;
     if (i < nx) {
         const size_t c = (size_t)P * nx + i;
         T.phi[c] = (v[6] != 0.0) ? v[0] / v[6] : v[1] / rn;
@@ -656,11 +660,6 @@ __global__ void __launch_bounds__(32 * kRP) k_restrict_final(Restrict2Ctx x)
 // ---------------------------------------------------------------------------------------
 // grey LOQD + MEB: one Newton step on the grey level (single CTA)
 // ---------------------------------------------------------------------------------------
-struct GreyCtx {
-    LoCtx lo;
-    GreyArgs a;
-    int mmax;
-};
 
 __device__ inline double block_max(double v, double *red)
 {
@@ -674,8 +673,9 @@ __device__ inline double block_max(double v, double *red)
     return r;
 }
 
-__global__ void __launch_bounds__(1024) k_grey(GreyCtx x)
+__device__ void grey_body(const GreyCtx &x)
 {
+    const int have_prev = x.a.have_prev_dev ? *x.a.have_prev_dev : x.a.have_prev;
     extern __shared__ __align__(16) double gsm[];
     const int nx = x.lo.nx;
     double *sa = gsm;            // absorption w c sig*
@@ -698,7 +698,7 @@ __global__ void __launch_bounds__(1024) k_grey(GreyCtx x)
             dQ -= k54 * (1.0 + xL) * exp(-xL);
         }
         double D = 0.0;
-        if (a.have_prev) {
+        if (have_prev) {
             const double Tp = a.T_prev[i];
             // secant only where |dT| is far above rounding (relative noise ~ eps T/|dT|)
             if (fabs(Ts - Tp) > 1e-7 * Ts) D = (sig - a.sig_prev[i]) / (Ts - Tp);
@@ -752,39 +752,116 @@ __global__ void __launch_bounds__(1024) k_grey(GreyCtx x)
             a.flags[5] = dTp; a.flags[6] = dEp;
         }
     }
+    if (a.have_prev_dev && threadIdx.x == 0) *a.have_prev_dev = 1;   // after block_max barriers
 }
 
-__global__ void k_group_sum(int n, int nx, const double *__restrict__ X, double *__restrict__ out)
+__device__ void group_sum_body(const GroupSumArgs &a, int bx)
 {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= nx) return;
+    const int i = bx * blockDim.x + threadIdx.x;
+    if (i >= a.nx) return;
     double s = 0.0;
-    for (int q = 0; q < n; ++q) s += X[(size_t)q * nx + i];
-    out[i] = s;
+    for (int q = 0; q < a.n; ++q) s += a.X[(size_t)q * a.nx + i];
+    a.out[i] = s;
+}
+
+// entry points: the single-slab kernels pass blockIdx; the batched ones walk a work list
+__global__ void __launch_bounds__(512) k_restrict(RestrictCtx x)
+{
+    restrict_body(x, blockIdx.x, blockIdx.y);
+}
+__global__ void __launch_bounds__(128) k_restrict_part(Restrict2Ctx x)
+{
+    restrict_part_body(x, blockIdx.x, blockIdx.y);
+}
+__global__ void __launch_bounds__(32 * kRP) k_restrict_final(Restrict2Ctx x)
+{
+    restrict_final_body(x, blockIdx.x, blockIdx.y);
+}
+__global__ void __launch_bounds__(1024) k_grey(GreyCtx x) { grey_body(x); }
+__global__ void k_group_sum(GroupSumArgs a) { group_sum_body(a, blockIdx.x); }
+
+#define TRT_BATCHED(name, Ctx, bounds, call)                                                  \
+    __global__ void __launch_bounds__(bounds) name(const int *__restrict__ meta, int N,        \
+                                                   const Ctx *__restrict__ xs)                 \
+    {                                                                                          \
+        for (int b = blockIdx.x;; b += gridDim.x) {                                            \
+            int s, bx, by;                                                                     \
+            if (!bdecode(meta, N, b, s, bx, by)) break;                                        \
+            const Ctx x = xs[s];                                                               \
+            call;                                                                              \
+            __syncthreads();                                                                   \
+        }                                                                                      \
+    }
+TRT_BATCHED(k_restrict_b, RestrictCtx, 512, restrict_body(x, bx, by))
+TRT_BATCHED(k_restrict_part_b, Restrict2Ctx, 128, restrict_part_body(x, bx, by))
+TRT_BATCHED(k_restrict_final_b, Restrict2Ctx, 32 * kRP, restrict_final_body(x, bx, by))
+TRT_BATCHED(k_grey_b, GreyCtx, 1024, grey_body(x))
+TRT_BATCHED(k_group_sum_b, GroupSumArgs, 128, group_sum_body(x, bx))
+#undef TRT_BATCHED
+
+__global__ void __launch_bounds__(256) k_copy_b(const int *__restrict__ meta, int N,
+                                                const CopyArgs *__restrict__ xs)
+{
+    for (int b = blockIdx.x;; b += gridDim.x) {
+        int s, bx, by;
+        if (!bdecode(meta, N, b, s, bx, by)) break;
+        const CopyArgs c = xs[s];
+        const long i = (long)bx * blockDim.x + threadIdx.x;
+        if (i < c.n) c.dst[i] = c.src[i];
+    }
 }
 
 }  // namespace
 
-cudaError_t launch_lo_solve(const Problem &p, double dt, const Level &L)
+LoCtx make_lo_ctx(const Problem &p, double dt, const Level &L)
 {
     LoCtx x;
     x.nx = p.nx; x.dt = dt; x.icdt = 1.0 / (kC * dt); x.h = p.h; x.ihf = p.ihf; x.L = L;
     x.a_cell = nullptr; x.s_cell = nullptr;
-    const int mmax = lo_mmax(p.nx);
-    const size_t rsz = lo_fp32(p.precision) ? sizeof(float) : sizeof(double);
-    const size_t sm = 6 * 32 * (size_t)mmax * rsz;
+    return x;
+}
+
+static size_t lo_smem(int precision, int nx)
+{
+    const size_t rsz = lo_fp32(precision) ? sizeof(float) : sizeof(double);
+    return 6 * 32 * (size_t)lo_mmax(nx) * rsz;
+}
+
+cudaError_t launch_lo_solve(const Problem &p, double dt, const Level &L)
+{
+    const LoCtx x = make_lo_ctx(p, dt, L);
+    const size_t sm = lo_smem(p.precision, p.nx);
     const unsigned nb = (unsigned)L.n;
     cudaError_t e;
     if (!lo_fp32(p.precision)) {
         e = cudaFuncSetAttribute(k_lo_solve<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)sm);
         if (e != cudaSuccess) return e;
-        k_lo_solve<double><<<nb, 128, sm, p.stream>>>(x, mmax);
+        k_lo_solve<double><<<nb, 128, sm, p.stream>>>(x);
     } else {
         e = cudaFuncSetAttribute(k_lo_solve<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)sm);
         if (e != cudaSuccess) return e;
-        k_lo_solve<float><<<nb, 128, sm, p.stream>>>(x, mmax);
+        k_lo_solve<float><<<nb, 128, sm, p.stream>>>(x);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lo_solve_b(int precision, int max_nx, const int *meta, int N,
+                              const LoCtx *xs, int grid, cudaStream_t st)
+{
+    const size_t sm = lo_smem(precision, max_nx);
+    cudaError_t e;
+    if (!lo_fp32(precision)) {
+        e = cudaFuncSetAttribute(k_lo_solve_b<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)sm);
+        if (e != cudaSuccess) return e;
+        k_lo_solve_b<double><<<grid, 128, sm, st>>>(meta, N, xs);
+    } else {
+        e = cudaFuncSetAttribute(k_lo_solve_b<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)sm);
+        if (e != cudaSuccess) return e;
+        k_lo_solve_b<float><<<grid, 128, sm, st>>>(meta, N, xs);
     }
     return cudaGetLastError();
 }
@@ -797,13 +874,41 @@ size_t restrict_scratch_doubles(int nx, int n_from, int n_to)
     return (size_t)n_to * nchunk * kRP * (nx + 1);
 }
 
+int restrict2_nchunk(int n_from, int n_to) { return (n_from / n_to + kChunk - 1) / kChunk; }
+
+int restrict_kind(const Problem &p, int n_from, int n_to, int *KS)
+{
+    const size_t need = restrict_scratch_doubles(p.nx, n_from, n_to);
+    if (need > 0 && p.rscratch && need <= p.rscratch_doubles) return 2;
+    const int r = n_from / n_to;
+    int k = 1;
+    while (k < 16 && k * 4 <= r) k *= 2;   // <= 512 threads: the register file holds them
+    *KS = k;
+    return 1;
+}
+
+RestrictCtx make_restrict_ctx(const Problem &p, const Level &src, const Level &dst)
+{
+    RestrictCtx x;
+    x.nx = p.nx; x.r = src.n / dst.n; x.h = p.h; x.ihf = p.ihf; x.S = src; x.T = dst;
+    return x;
+}
+
+Restrict2Ctx make_restrict2_ctx(const Problem &p, const Level &src, const Level &dst)
+{
+    Restrict2Ctx y;
+    y.nx = p.nx; y.r = src.n / dst.n; y.nchunk = restrict2_nchunk(src.n, dst.n);
+    y.h = p.h; y.ihf = p.ihf; y.S = src; y.T = dst; y.part = p.rscratch;
+    return y;
+}
+
+static size_t restrict_smem(int KS) { return (KS > 1) ? sizeof(double) * KS * 32 * kRV1 : 0; }
+
 cudaError_t launch_restrict(const Problem &p, const Level &src, Level &dst)
 {
-    const size_t need = restrict_scratch_doubles(p.nx, src.n, dst.n);
-    if (need > 0 && p.rscratch && need <= p.rscratch_doubles) {
-        Restrict2Ctx y;
-        y.nx = p.nx; y.r = src.n / dst.n; y.nchunk = (y.r + kChunk - 1) / kChunk;
-        y.h = p.h; y.ihf = p.ihf; y.S = src; y.T = dst; y.part = p.rscratch;
+    int KS = 1;
+    if (restrict_kind(p, src.n, dst.n, &KS) == 2) {
+        const Restrict2Ctx y = make_restrict2_ctx(p, src, dst);
         dim3 g1((p.nx + 1 + 31) / 32, dst.n * y.nchunk);
         k_restrict_part<<<g1, dim3(32, 4), 0, p.stream>>>(y);
         cudaError_t e = cudaGetLastError();
@@ -811,30 +916,62 @@ cudaError_t launch_restrict(const Problem &p, const Level &src, Level &dst)
         k_restrict_final<<<dim3((p.nx + 1 + 31) / 32, dst.n), dim3(32, kRP), 0, p.stream>>>(y);
         return cudaGetLastError();
     }
-    RestrictCtx x;
-    x.nx = p.nx; x.r = src.n / dst.n; x.h = p.h; x.ihf = p.ihf; x.S = src; x.T = dst;
-    int KS = 1;
-    while (KS < 16 && KS * 4 <= x.r) KS *= 2;   // <= 512 threads: the register file holds them
-    dim3 block(32, KS);
+    const RestrictCtx x = make_restrict_ctx(p, src, dst);
     dim3 grid((p.nx + 1 + 31) / 32, dst.n);
-    size_t sm = (KS > 1) ? sizeof(double) * KS * 32 * kRV1 : 0;
+    const size_t sm = restrict_smem(KS);
     cudaError_t e = cudaFuncSetAttribute(k_restrict, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)sm);
     if (e != cudaSuccess) return e;
-    k_restrict<<<grid, block, sm, p.stream>>>(x);
+    k_restrict<<<grid, dim3(32, KS), sm, p.stream>>>(x);
     return cudaGetLastError();
+}
+
+cudaError_t launch_restrict_b(int KS, const int *meta, int N, const RestrictCtx *xs, int grid,
+                              cudaStream_t st)
+{
+    const size_t sm = restrict_smem(KS);
+    cudaError_t e = cudaFuncSetAttribute(k_restrict_b, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)sm);
+    if (e != cudaSuccess) return e;
+    k_restrict_b<<<grid, dim3(32, KS), sm, st>>>(meta, N, xs);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_restrict_part_b(const int *meta, int N, const Restrict2Ctx *xs, int grid,
+                                   cudaStream_t st)
+{
+    k_restrict_part_b<<<grid, dim3(32, 4), 0, st>>>(meta, N, xs);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_restrict_final_b(const int *meta, int N, const Restrict2Ctx *xs, int grid,
+                                    cudaStream_t st)
+{
+    k_restrict_final_b<<<grid, dim3(32, kRP), 0, st>>>(meta, N, xs);
+    return cudaGetLastError();
+}
+
+GreyCtx make_grey_ctx(const Problem &p, const Level &g, const GreyArgs &a)
+{
+    GreyCtx x;
+    x.lo = make_lo_ctx(p, a.dt, g);
+    x.a = a;
+    x.mmax = lo_mmax(p.nx);
+    return x;
+}
+
+static void grey_launch_shape(int nx, int &bs, size_t &sm)
+{
+    bs = std::min(1024, std::max(32, (nx + 31) / 32 * 32));
+    sm = sizeof(double) * (3 * (size_t)nx + 32 + 6 * 32 * (size_t)lo_mmax(nx));
 }
 
 cudaError_t launch_grey(const Problem &p, const Level &g, const GreyArgs &a)
 {
-    GreyCtx x;
-    x.lo.nx = p.nx; x.lo.dt = a.dt; x.lo.icdt = 1.0 / (kC * a.dt); x.lo.h = p.h; x.lo.ihf = p.ihf;
-    x.lo.L = g;
-    x.lo.a_cell = nullptr; x.lo.s_cell = nullptr;
-    x.a = a;
-    x.mmax = lo_mmax(p.nx);
-    int bs = std::min(1024, std::max(32, (p.nx + 31) / 32 * 32));
-    size_t sm = sizeof(double) * (3 * (size_t)p.nx + 32 + 6 * 32 * (size_t)x.mmax);
+    const GreyCtx x = make_grey_ctx(p, g, a);
+    int bs;
+    size_t sm;
+    grey_launch_shape(p.nx, bs, sm);
     cudaError_t e = cudaFuncSetAttribute(k_grey, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)sm);
     if (e != cudaSuccess) return e;
@@ -842,9 +979,37 @@ cudaError_t launch_grey(const Problem &p, const Level &g, const GreyArgs &a)
     return cudaGetLastError();
 }
 
+cudaError_t launch_grey_b(int max_nx, const int *meta, int N, const GreyCtx *xs, int grid,
+                          cudaStream_t st)
+{
+    int bs;
+    size_t sm;
+    grey_launch_shape(max_nx, bs, sm);
+    cudaError_t e = cudaFuncSetAttribute(k_grey_b, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)sm);
+    if (e != cudaSuccess) return e;
+    k_grey_b<<<grid, bs, sm, st>>>(meta, N, xs);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_group_sum(const Problem &p, int n, const double *X, double *out)
 {
-    k_group_sum<<<(p.nx + 127) / 128, 128, 0, p.stream>>>(n, p.nx, X, out);
+    GroupSumArgs a;
+    a.n = n; a.nx = p.nx; a.X = X; a.out = out;
+    k_group_sum<<<(p.nx + 127) / 128, 128, 0, p.stream>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_group_sum_b(const int *meta, int N, const GroupSumArgs *xs, int grid,
+                               cudaStream_t st)
+{
+    k_group_sum_b<<<grid, 128, 0, st>>>(meta, N, xs);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_copy_b(const int *meta, int N, const CopyArgs *xs, int grid, cudaStream_t st)
+{
+    k_copy_b<<<grid, 256, 0, st>>>(meta, N, xs);
     return cudaGetLastError();
 }
 

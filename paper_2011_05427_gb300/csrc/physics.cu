@@ -10,7 +10,7 @@
 // exponentially convergent tails e^{-kx} at and above it, summed with the scale e^{x_g}
 // factored out so that cold cells (x ~ 1e5) neither underflow nor lose the ratio.
 #include <cmath>
-#include "common.cuh"
+#include "batch.cuh"
 
 namespace trt {
 
@@ -284,51 +284,76 @@ void host_group_B(int G, const double *edges, double T, double *B)
 }
 
 // One thread per (group, cell); outputs [G][nx] (cell fastest, coalesced).
-__global__ void __launch_bounds__(256) k_opacity(int nx, int G, const double *__restrict__ T,
-                                                 const double *__restrict__ edges, double s,
-                                                 double *__restrict__ sigE,
-                                                 double *__restrict__ emis,
-                                                 double *__restrict__ sigR,
-                                                 float *__restrict__ sig32,
-                                                 float *__restrict__ emis32,
-                                                 const double *__restrict__ h, double icdt)
+__device__ inline void opacity_body(const OpacityArgs &a, long idx)
 {
-    long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int nx = a.nx, G = a.G;
     if (idx >= (long)G * nx) return;
     int g = (int)(idx / nx);
     int i = (int)(idx - (long)g * nx);
-    const double Ti = T[i];
+    const double Ti = a.T[i];
     const double iT = rcp64(Ti);
-    const double xa = edges[g] * iT;
-    const double eb = edges[g + 1];
+    const double xa = a.edges[g] * iT;
+    const double eb = a.edges[g + 1];
     const bool binf = isinf(eb);
     const double xb = binf ? 0.0 : eb * iT;
     double dPs, Ns, Ds, om;
     group_integrals(xa, xb, binf, c_ser, dPs, Ns, Ds, om);
     double T3 = Ti * Ti * Ti;
-    double k27 = 27.0 * s;
+    double k27 = 27.0 * a.s;
     const double iT3 = rcp64(T3);
     const double sg = k27 * om * iT3 * rcp64(dPs);
     const double em = k27 * kCB * Ti * exp(-xa) * om;
-    sigE[idx] = sg;
-    emis[idx] = em;
-    sigR[idx] = k27 * Ns * iT3 * rcp64(Ds);
-    if (sig32) {   // FP32 sweep inputs: sigma_t h/2 and h e/2, one rounding each
-        const double hh = 0.5 * h[i];
-        sig32[idx] = (float)(hh * (sg + icdt));
-        emis32[idx] = (float)(hh * em);
+    a.sigE[idx] = sg;
+    a.emis[idx] = em;
+    a.sigR[idx] = k27 * Ns * iT3 * rcp64(Ds);
+    if (a.sig32) {   // FP32 sweep inputs: sigma_t h/2 and h e/2, one rounding each
+        const double hh = 0.5 * a.h[i];
+        a.sig32[idx] = (float)(hh * (sg + a.icdt));
+        a.emis32[idx] = (float)(hh * em);
     }
 }
+
+__global__ void __launch_bounds__(256) k_opacity(OpacityArgs a)
+{
+    opacity_body(a, (long)blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+__global__ void __launch_bounds__(256) k_opacity_b(const int *__restrict__ meta, int N,
+                                                   const OpacityArgs *__restrict__ xs)
+{
+    for (int b = blockIdx.x;; b += gridDim.x) {
+        int s, bx, by;
+        if (!bdecode(meta, N, b, s, bx, by)) break;
+        const OpacityArgs a = xs[s];
+        opacity_body(a, (long)bx * blockDim.x + threadIdx.x);
+    }
+}
+
+OpacityArgs make_opacity_args(const Problem &p, const double *T, double *sigE, double *emis,
+                              double *sigR, float *sig32, float *emis32, double dt)
+{
+    OpacityArgs a;
+    a.nx = p.nx; a.G = p.G; a.T = T; a.edges = p.edges; a.s = p.s;
+    a.sigE = sigE; a.emis = emis; a.sigR = sigR; a.sig32 = sig32; a.emis32 = emis32;
+    a.h = p.h;
+    a.icdt = (dt > 0) ? 1.0 / (kC * dt) : 0.0;
+    return a;
+}
+
+int opacity_blocks(const Problem &p) { return (int)(((long)p.G * p.nx + 255) / 256); }
 
 cudaError_t launch_opacity(const Problem &p, const double *T, double *sigE, double *emis,
                            double *sigR, float *sig32, float *emis32, double dt)
 {
-    const double icdt = (dt > 0) ? 1.0 / (kC * dt) : 0.0;
-    long n = (long)p.G * p.nx;
-    int bs = 256;
-    long nb = (n + bs - 1) / bs;
-    k_opacity<<<(unsigned)nb, bs, 0, p.stream>>>(p.nx, p.G, T, p.edges, p.s, sigE, emis, sigR,
-                                                 sig32, emis32, p.h, icdt);
+    const OpacityArgs a = make_opacity_args(p, T, sigE, emis, sigR, sig32, emis32, dt);
+    k_opacity<<<(unsigned)opacity_blocks(p), 256, 0, p.stream>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_opacity_b(const int *meta, int N, const OpacityArgs *xs, int grid,
+                             cudaStream_t st)
+{
+    k_opacity_b<<<grid, 256, 0, st>>>(meta, N, xs);
     return cudaGetLastError();
 }
 

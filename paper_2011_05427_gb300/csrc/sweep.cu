@@ -23,7 +23,7 @@
 // two angular moments per (cell, group) -- the cross-direction reduction costs one
 // __syncthreads per strip, not one per cell.  Partial moments of the 2N/D direction tiles
 // are summed in a fixed order by the finalize kernel (deterministic).
-#include "common.cuh"
+#include "batch.cuh"
 
 namespace trt {
 
@@ -36,17 +36,7 @@ constexpr int kPadG = 33;   // padded group stride of the strip tables (bank con
 // so the FP32 sweep is bound by how many bytes each warp keeps in flight; the shape is
 // picked per problem by timing the candidates (trt_autotune), else the defaults below.
 
-struct SweepArgs {
-    int nx, N, G, ldG, D;
-    double icdt;
-    const double *h, *mu, *w, *Iin0, *IinX;
-    const void *sigE, *emis;   // [G][nx], SR-typed
-    const void *I_old;
-    void *I_new;
-    void *part;       // [n_dt][2][G][nx], R-typed
-    void *psi_exit;   // [M][ldG], R-typed
-    double *f, *fb0, *fbX, *C0, *CX;
-};
+
 
 template <typename R>
 struct Acc {   // per-tile angular sum: plain in FP64, compensated (Kahan) in FP32
@@ -121,7 +111,7 @@ struct SweepSmem {
 // SR = float: the fields already are sigma_t h/2 and h e/2 in FP32 (written by the opacity
 // kernel with one rounding each) and are used as staged.
 template <typename R, typename SR, int kStrip, int NS>
-__global__ void __launch_bounds__(256) k_sweep(SweepArgs a)
+__device__ void sweep_body(const SweepArgs &a, int dtile, int gt)
 {
     constexpr bool kPre = sizeof(SR) == 4;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -141,8 +131,6 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs a)
     const int warp = threadIdx.x >> 5;
     const int nthr = blockDim.x;
     const int tid = threadIdx.x;
-    const int dtile = blockIdx.x;
-    const int gt = blockIdx.y;
     const int g = gt * 32 + lane;
     const int nx = a.nx, G = a.G, ldG = a.ldG;
     const bool pos = dtile < a.N / D;
@@ -286,21 +274,42 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs a)
     reinterpret_cast<R *>(a.psi_exit)[(size_t)m * ldG + g] = psi_in;
 }
 
+template <typename R, typename SR, int kStrip, int NS>
+__global__ void __launch_bounds__(256) k_sweep(SweepArgs a)
+{
+    sweep_body<R, SR, kStrip, NS>(a, blockIdx.x, blockIdx.y);
+}
+
+// batched: a persistent grid walks the (slab, direction tile, group tile) work list
+template <typename R, typename SR, int kStrip, int NS>
+__global__ void __launch_bounds__(256) k_sweep_b(const int *__restrict__ meta, int N,
+                                                 const SweepArgs *__restrict__ xs)
+{
+    for (int b = blockIdx.x;; b += gridDim.x) {
+        int s, bx, by;
+        if (!bdecode(meta, N, b, s, bx, by)) break;
+        const SweepArgs a = xs[s];
+        sweep_body<R, SR, kStrip, NS>(a, bx, by);
+        __syncthreads();   // shared memory is reused by the next work item
+    }
+}
+
 // f_g = sum_t A2 / sum_t A0 per (group, cell), in R; boundary factors per group in FP64.
 // Blocks [0, nb_cell) take one (group, cell) per thread; the blocks after them take one
 // group per warp for the boundary factors: lanes stride over the directions and the four
 // half-range sums per face meet in a fixed butterfly (a serial loop over all directions
 // per thread left a latency-bound tail of dependent loads).
 template <typename R>
-__global__ void k_sweep_finalize(int nx, int N, int G, int ldG, int ntile, int nb_cell,
-                                 const R *__restrict__ part, const double *__restrict__ mu,
-                                 const double *__restrict__ w, const double *__restrict__ Iin0,
-                                 const double *__restrict__ IinX, const R *__restrict__ psi_exit,
-                                 double *__restrict__ f, double *fb0, double *fbX, double *C0,
-                                 double *CX)
+__device__ void finalize_body(const FinalizeArgs &x, int bx)
 {
-    if ((int)blockIdx.x < nb_cell) {
-        const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int nx = x.nx, N = x.N, G = x.G, ldG = x.ldG, ntile = x.ntile, nb_cell = x.nb_cell;
+    const R *__restrict__ part = reinterpret_cast<const R *>(x.part);
+    const R *__restrict__ psi_exit = reinterpret_cast<const R *>(x.psi_exit);
+    const double *__restrict__ mu = x.mu, *__restrict__ w = x.w;
+    const double *__restrict__ Iin0 = x.Iin0, *__restrict__ IinX = x.IinX;
+    double *f = x.f, *fb0 = x.fb0, *fbX = x.fbX, *C0 = x.C0, *CX = x.CX;
+    if (bx < nb_cell) {
+        const long idx = (long)bx * blockDim.x + threadIdx.x;
         const long n = (long)G * nx;
         if (idx < n) {
             Acc<R> A0, A2;
@@ -313,7 +322,7 @@ __global__ void k_sweep_finalize(int nx, int N, int G, int ldG, int ntile, int n
         return;
     }
     const int lane = threadIdx.x & 31;
-    const int g = (blockIdx.x - nb_cell) * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int g = (bx - nb_cell) * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (g >= G) return;   // whole warp
     const int M = 2 * N;
     // x = 0: inflow for mu > 0, outflow for mu < 0; x = X: outflow for mu > 0, inflow mu < 0
@@ -348,6 +357,24 @@ __global__ void k_sweep_finalize(int nx, int N, int G, int ldG, int ntile, int n
     }
 }
 
+template <typename R>
+__global__ void k_sweep_finalize(FinalizeArgs x)
+{
+    finalize_body<R>(x, blockIdx.x);
+}
+
+template <typename R>
+__global__ void k_sweep_finalize_b(const int *__restrict__ meta, int N,
+                                   const FinalizeArgs *__restrict__ xs)
+{
+    for (int b = blockIdx.x;; b += gridDim.x) {
+        int s, bx, by;
+        if (!bdecode(meta, N, b, s, bx, by)) break;
+        const FinalizeArgs x = xs[s];
+        finalize_body<R>(x, bx);
+    }
+}
+
 // Candidate tile shapes (S, NS); index 0 is the default.  Measured at 500 cells x 64
 // directions x 1024 groups with D = 8: FP32 (16, 2) 0.215 ms, (8, 4) 0.225, (32, 2) 0.282,
 // (16, 3) 0.299 (a third buffer costs a resident CTA per SM); FP64 (8, 2) 1.26 ms,
@@ -367,62 +394,70 @@ int base_D(int N, int cap)
     return 1;
 }
 
-int pick_D(const Problem &p)
+int finalize_bnd_blocks(int G) { return (G + 7) / 8; }   // one warp per group, 8 per block
+
+
+// one launch of shape (S, NS): the single-slab grid (direction tiles x group tiles) when
+// `a` is given, else the batched persistent grid over the work list (meta, xs)
+template <typename R, typename SR, int S, int NS>
+cudaError_t launch_shape(const SweepArgs *a, int M, int ldG, int D, const int *meta, int N,
+                         const SweepArgs *xs, int grid, cudaStream_t st)
 {
-    if (p.sweep_D > 0) return p.sweep_D;
-    return base_D(p.N, 8);
+    const size_t sm = SweepSmem<R, SR, S, NS>(D).total;
+    if (sm > 227 * 1024) return cudaErrorInvalidConfiguration;
+    if (a) {
+        cudaError_t e = cudaFuncSetAttribute(k_sweep<R, SR, S, NS>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+        k_sweep<R, SR, S, NS><<<dim3(M / D, ldG / 32), 32 * D, sm, st>>>(*a);
+    } else {
+        cudaError_t e = cudaFuncSetAttribute(k_sweep_b<R, SR, S, NS>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+        k_sweep_b<R, SR, S, NS><<<grid, 32 * D, sm, st>>>(meta, N, xs);
+    }
+    return cudaGetLastError();
 }
 
-template <typename R, typename SR, int S, int NS>
-cudaError_t launch_shape(const Problem &p, const SweepArgs &a)
+template <typename R, typename SR>
+cudaError_t dispatch_shape(int shape, const SweepArgs *a, int M, int ldG, int D, const int *meta,
+                           int N, const SweepArgs *xs, int grid, cudaStream_t st)
 {
-    const int ntile = p.M / a.D;
-    dim3 grid(ntile, p.ldG / 32);
-    dim3 block(32 * a.D);
-    const size_t sm = SweepSmem<R, SR, S, NS>(a.D).total;
-    if (sm > 227 * 1024) return cudaErrorInvalidConfiguration;
-    cudaError_t e = cudaFuncSetAttribute(k_sweep<R, SR, S, NS>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
-    k_sweep<R, SR, S, NS><<<grid, block, sm, p.stream>>>(a);
-    return cudaGetLastError();
+    if (sizeof(R) == 4) {
+        switch (shape) {
+        case 1: return launch_shape<R, SR, 16, 3>(a, M, ldG, D, meta, N, xs, grid, st);
+        case 2: return launch_shape<R, SR, 16, 4>(a, M, ldG, D, meta, N, xs, grid, st);
+        case 3: return launch_shape<R, SR, 8, 4>(a, M, ldG, D, meta, N, xs, grid, st);
+        case 4: return launch_shape<R, SR, 8, 6>(a, M, ldG, D, meta, N, xs, grid, st);
+        case 5: return launch_shape<R, SR, 32, 2>(a, M, ldG, D, meta, N, xs, grid, st);
+        default: return launch_shape<R, SR, 16, 2>(a, M, ldG, D, meta, N, xs, grid, st);
+        }
+    }
+    switch (shape) {
+    case 1: return launch_shape<R, SR, 16, 2>(a, M, ldG, D, meta, N, xs, grid, st);
+    case 2: return launch_shape<R, SR, 8, 3>(a, M, ldG, D, meta, N, xs, grid, st);
+    default: return launch_shape<R, SR, 8, 2>(a, M, ldG, D, meta, N, xs, grid, st);
+    }
 }
 
 template <typename R, typename SR>
 cudaError_t launch_sweep_t(const Problem &p, const SweepArgs &a)
 {
-    const int ntile = p.M / a.D;
-    const int shape = p.sweep_shape;
-    cudaError_t e;
-    if (sizeof(R) == 4) {
-        switch (shape) {
-        case 1: e = launch_shape<R, SR, 16, 3>(p, a); break;
-        case 2: e = launch_shape<R, SR, 16, 4>(p, a); break;
-        case 3: e = launch_shape<R, SR, 8, 4>(p, a); break;
-        case 4: e = launch_shape<R, SR, 8, 6>(p, a); break;
-        case 5: e = launch_shape<R, SR, 32, 2>(p, a); break;
-        default: e = launch_shape<R, SR, 16, 2>(p, a); break;
-        }
-    } else {
-        switch (shape) {
-        case 1: e = launch_shape<R, SR, 16, 2>(p, a); break;
-        case 2: e = launch_shape<R, SR, 8, 3>(p, a); break;
-        default: e = launch_shape<R, SR, 8, 2>(p, a); break;
-        }
-    }
+    cudaError_t e = dispatch_shape<R, SR>(p.sweep_shape, &a, p.M, p.ldG, a.D, nullptr, 0, nullptr,
+                                          0, p.stream);
     if (e != cudaSuccess) return e;
-    const long n = (long)p.G * p.nx;
-    const int bs = 256;
-    const int nb_cell = (int)((n + bs - 1) / bs);
-    const int nb_bnd = (p.G + bs / 32 - 1) / (bs / 32);
-    k_sweep_finalize<R><<<(unsigned)(nb_cell + nb_bnd), bs, 0, p.stream>>>(
-        p.nx, p.N, p.G, p.ldG, ntile, nb_cell, reinterpret_cast<const R *>(a.part), p.mu, p.w,
-        p.Iin0, p.IinX, reinterpret_cast<const R *>(a.psi_exit), a.f, a.fb0, a.fbX, a.C0,
-        a.CX);
+    const FinalizeArgs fa = make_finalize_args(p, a);
+    k_sweep_finalize<R><<<(unsigned)(fa.nb_cell + finalize_bnd_blocks(p.G)), 256, 0, p.stream>>>(fa);
     return cudaGetLastError();
 }
 
 }  // namespace
+
+int pick_D(const Problem &p)
+{
+    if (p.sweep_D > 0) return p.sweep_D;
+    return base_D(p.N, 8);
+}
 
 int sweep_shape_count(int precision)
 {
@@ -452,22 +487,68 @@ size_t sweep_partial_doubles(const Problem &p)
     return (size_t)(p.M / std::min(base_D(p.N, 4), pick_D(p))) * 2 * p.G * p.nx;
 }
 
-cudaError_t launch_sweep(const Problem &p, double dt, const void *sigE, const void *emis,
-                         bool sigma_fp32, const void *I_old, void *I_new, double *part,
-                         double *psi_exit, double *f, double *fb0, double *fbX, double *C0,
-                         double *CX)
+SweepArgs make_sweep_args(const Problem &p, double dt, const void *sigE, const void *emis,
+                          const void *I_old, void *I_new, double *part, double *psi_exit,
+                          double *f, double *fb0, double *fbX, double *C0, double *CX, int D)
 {
     SweepArgs a;
     a.nx = p.nx; a.N = p.N; a.G = p.G; a.ldG = p.ldG;
-    a.D = pick_D(p);
+    a.D = D;
     a.icdt = 1.0 / (kC * dt);
     a.h = p.h; a.mu = p.mu; a.w = p.w; a.Iin0 = p.Iin0; a.IinX = p.IinX;
     a.sigE = sigE; a.emis = emis; a.I_old = I_old; a.I_new = I_new;
     a.part = part; a.psi_exit = psi_exit;
     a.f = f; a.fb0 = fb0; a.fbX = fbX; a.C0 = C0; a.CX = CX;
+    return a;
+}
+
+FinalizeArgs make_finalize_args(const Problem &p, const SweepArgs &a)
+{
+    FinalizeArgs x;
+    x.nx = p.nx; x.N = p.N; x.G = p.G; x.ldG = p.ldG;
+    x.ntile = p.M / a.D;
+    x.nb_cell = (int)(((long)p.G * p.nx + 255) / 256);
+    x.part = a.part; x.psi_exit = a.psi_exit;
+    x.mu = p.mu; x.w = p.w; x.Iin0 = p.Iin0; x.IinX = p.IinX;
+    x.f = a.f; x.fb0 = a.fb0; x.fbX = a.fbX; x.C0 = a.C0; x.CX = a.CX;
+    return x;
+}
+
+int finalize_blocks(const Problem &p)
+{
+    return (int)(((long)p.G * p.nx + 255) / 256) + finalize_bnd_blocks(p.G);
+}
+
+cudaError_t launch_sweep(const Problem &p, double dt, const void *sigE, const void *emis,
+                         bool sigma_fp32, const void *I_old, void *I_new, double *part,
+                         double *psi_exit, double *f, double *fb0, double *fbX, double *C0,
+                         double *CX)
+{
+    const SweepArgs a = make_sweep_args(p, dt, sigE, emis, I_old, I_new, part, psi_exit, f, fb0,
+                                        fbX, C0, CX, pick_D(p));
     if (!sweep_fp32(p.precision)) return launch_sweep_t<double, double>(p, a);
     if (sigma_fp32) return launch_sweep_t<float, float>(p, a);
     return launch_sweep_t<float, double>(p, a);
+}
+
+cudaError_t launch_sweep_b(int precision, bool sigma_fp32, int D, int shape, const int *meta,
+                           int N, const SweepArgs *xs, int grid, cudaStream_t st)
+{
+    if (!sweep_fp32(precision))
+        return dispatch_shape<double, double>(shape, nullptr, 0, 0, D, meta, N, xs, grid, st);
+    if (sigma_fp32)
+        return dispatch_shape<float, float>(shape, nullptr, 0, 0, D, meta, N, xs, grid, st);
+    return dispatch_shape<float, double>(shape, nullptr, 0, 0, D, meta, N, xs, grid, st);
+}
+
+cudaError_t launch_finalize_b(int precision, const int *meta, int N, const FinalizeArgs *xs,
+                              int grid, cudaStream_t st)
+{
+    if (sweep_fp32(precision))
+        k_sweep_finalize_b<float><<<grid, 256, 0, st>>>(meta, N, xs);
+    else
+        k_sweep_finalize_b<double><<<grid, 256, 0, st>>>(meta, N, xs);
+    return cudaGetLastError();
 }
 
 }  // namespace trt

@@ -148,6 +148,24 @@ def lib():
     L.trt_mlp_features.argtypes = [ctypes.c_int] * 2 + [_vp] * 6
     L.trt_mlp_status.restype = ctypes.c_int
     L.trt_mlp_status.argtypes = []
+    # batched slabs
+    L.trt_batch_workspace_bytes.restype = ctypes.c_size_t
+    L.trt_batch_workspace_bytes.argtypes = [ctypes.c_int] + [_vp] * 4
+    L.trt_create_batch.restype = ctypes.c_int
+    L.trt_create_batch.argtypes = [ctypes.c_int] + [_vp] * 7
+    L.trt_step_batch.restype = ctypes.c_int
+    L.trt_step_batch.argtypes = [_vp, ctypes.c_double, _vp, _vp]
+    L.trt_batch_slab.restype = ctypes.c_void_p
+    L.trt_batch_slab.argtypes = [_vp, ctypes.c_int]
+    L.trt_batch_set_tile.restype = ctypes.c_int
+    L.trt_batch_set_tile.argtypes = [_vp, ctypes.c_int, ctypes.c_int]
+    L.trt_batch_sweep_time.restype = ctypes.c_int
+    L.trt_batch_sweep_time.argtypes = [_vp, ctypes.c_double, ctypes.c_int,
+                                       ctypes.POINTER(ctypes.c_float)]
+    L.trt_destroy_batch.restype = ctypes.c_int
+    L.trt_destroy_batch.argtypes = [_vp]
+    L.trt_batch_last_error.restype = ctypes.c_char_p
+    L.trt_batch_last_error.argtypes = [_vp]
     L.trt_sweep_noalloc_scratch_bytes.restype = ctypes.c_size_t
     L.trt_sweep_noalloc_scratch_bytes.argtypes = [ctypes.c_int] * 3
     L.trt_sweep_noalloc.restype = ctypes.c_int
@@ -164,7 +182,10 @@ EXPORTED = ("trt_workspace_bytes", "trt_create", "trt_step", "trt_moments", "trt
             "trt_sweep_time", "trt_autotune", "trt_sweep_shapes", "trt_set_sweep_tile",
             "trt_sweep_noalloc_scratch_bytes", "trt_sweep_noalloc", "trt_sweep_noalloc_error",
             "trt_set_closure", "trt_gemm_bf16", "trt_mlp_scratch_bytes", "trt_mlp_refresh", "trt_mlp_forward",
-            "trt_mlp_grad", "trt_mlp_adam", "trt_mlp_features", "trt_mlp_status")
+            "trt_mlp_grad", "trt_mlp_adam", "trt_mlp_features", "trt_mlp_status",
+            "trt_batch_workspace_bytes", "trt_create_batch", "trt_step_batch",
+            "trt_batch_slab", "trt_batch_set_tile", "trt_batch_sweep_time",
+            "trt_destroy_batch", "trt_batch_last_error")
 
 
 class TRTError(RuntimeError):
@@ -389,9 +410,130 @@ class Solver:
         return lib().trt_sweep_shapes(self.h)
 
     def close(self):
-        if getattr(self, "h", None):
+        if getattr(self, "h", None) and getattr(self, "_owned", True):
             lib().trt_destroy(self.h)
-            self.h = None
+        self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Many slabs stepped together (trt_create_batch / trt_step_batch).  Every slab's
+    results are read through `slab(s)`, a Solver view of the batch's handle for slab s."""
+
+    def __init__(self, slabs, precision="fp64", device=None, T0=None):
+        import torch
+        self.torch = torch
+        dev = torch.device(device) if device is not None else torch.device("cuda")
+        if dev.index is None:
+            dev = torch.device("cuda", torch.cuda.current_device())
+        self.device = dev
+        self.n = n = len(slabs)
+        self.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        L = lib()
+        self._keep = []
+        grids = (trt_grid * n)()
+        angles = (trt_angles * n)()
+        groups = (trt_groups * n)()
+        opac = (trt_opacity * n)()
+        cv = (ctypes.c_double * n)()
+        for k, sl in enumerate(slabs):
+            e = np.ascontiguousarray(sl.edges(), np.float64)
+            lv = np.ascontiguousarray(sl.levels, np.int32)
+            self._keep += [e, lv]
+            grids[k] = trt_grid(int(sl.n_cells), None, float(sl.length_cm), float(sl.T_left),
+                                float(sl.T_right))
+            angles[k] = trt_angles(int(sl.N))
+            groups[k] = trt_groups(e.size - 1, _np_dp(e), 0.0, 0.0, lv.size,
+                                   lv.ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
+            opac[k] = trt_opacity(float(sl.opac_scale))
+            cv[k] = float(sl.cv)
+        torch.cuda.synchronize(dev)
+        # a stream of its own: the batch captures its stages as CUDA graphs
+        self.stream = torch.cuda.Stream(dev)
+        t0 = float(T0 if T0 is not None else slabs[0].T0)
+        opt = trt_options(self.precision, t0, ctypes.c_void_p(self.stream.cuda_stream), None, 0)
+        nbytes = L.trt_batch_workspace_bytes(n, grids, angles, groups, ctypes.byref(opt))
+        if nbytes == 0:
+            raise TRTError(TRT_EINVAL, "invalid batch (trt_batch_workspace_bytes returned 0)")
+        self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=dev)
+        opt.workspace = ctypes.c_void_p((self.workspace.data_ptr() + 255) // 256 * 256)
+        opt.workspace_bytes = nbytes
+        self.workspace_bytes = nbytes
+        b = ctypes.c_void_p()
+        rc = L.trt_create_batch(n, grids, angles, groups, opac, cv, ctypes.byref(opt),
+                                ctypes.byref(b))
+        if rc != TRT_OK:
+            raise TRTError(rc, L.trt_last_error(None).decode())
+        self.b = b
+        self._views = [None] * n
+
+    def _check(self, rc, allow=()):
+        if rc != TRT_OK and rc not in allow:
+            raise TRTError(rc, lib().trt_batch_last_error(self.b).decode())
+        return rc
+
+    def step(self, dt, cycle="V", l_max=4, eps=1e-8, eps_inner=None, max_outer=100):
+        if eps_inner is None:
+            eps_inner = eps / 10.0 if eps > 0 else -1.0
+        c = trt_cycle(CYCLES[cycle] if isinstance(cycle, str) else int(cycle), int(l_max),
+                      float(eps), float(eps_inner), int(max_outer))
+        st = (trt_stats * self.n)()
+        rc = lib().trt_step_batch(self.b, float(dt), ctypes.byref(c), st)
+        self._check(rc, allow=(TRT_ENOTCONVERGED,))
+        return [dict(n_ti=x.n_ti, n_c=x.n_c, n_lo=x.n_lo, n_outer=x.n_outer, status=x.status,
+                     n_kernels=x.n_kernels) for x in st]
+
+    def slab(self, s) -> "Solver":
+        if self._views[s] is None:
+            v = Solver.__new__(Solver)
+            v.torch = self.torch
+            v.device = self.device
+            v.stream = self.stream
+            v.precision = self.precision
+            v.h = ctypes.c_void_p(lib().trt_batch_slab(self.b, int(s)))
+            dims = [ctypes.c_int() for _ in range(7)]
+            lib().trt_dims(v.h, *[ctypes.byref(d) for d in dims])
+            v.nx, v.N, v.M, v.G, v.ldG, v.n_levels, _ = [d.value for d in dims]
+            v._owned = False
+            self._views[s] = v
+        return self._views[s]
+
+    def set_tile(self, D, shape):
+        self._check(lib().trt_batch_set_tile(self.b, int(D), int(shape)))
+
+    def sweep_time(self, dt, reps=5) -> float:
+        ms = ctypes.c_float()
+        self._check(lib().trt_batch_sweep_time(self.b, float(dt), int(reps), ctypes.byref(ms)))
+        return ms.value
+
+    def autotune(self, dt, reps=3):
+        """Time the batched sweep for every (D, shape) every slab admits; keep the fastest."""
+        best = None
+        Ds = [D for D in (8, 4, 2) if all(self.slab(s).N % D == 0 for s in range(self.n))
+              and all(D >= min(4, self.slab(s).N & -self.slab(s).N) for s in range(self.n))]
+        nshape = 6 if self.precision & TRT_SWEEP_FP32 else 3
+        for D in Ds:
+            for sh in range(nshape):
+                self.set_tile(D, sh)
+                try:
+                    t = self.sweep_time(dt, reps)
+                except TRTError:
+                    continue
+                if best is None or t < best[0]:
+                    best = (t, D, sh)
+        self.set_tile(best[1], best[2])
+        return best
+
+    def close(self):
+        if getattr(self, "b", None):
+            self.torch.cuda.synchronize(self.device)
+            lib().trt_destroy_batch(self.b)
+            self.b = None
 
     def __del__(self):
         try:
