@@ -218,6 +218,117 @@ def timed_steps(trt, cfg, precision, cycle, steps, warmup, local, ws, clocks=Fal
     return t, stats, rec, s
 
 
+def bf16_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops"]), "measured (MEASURED_PEAKS bf16_tflops, burst)"
+    except Exception:
+        return 1900.0, "fallback"
+
+
+def mlp_bench(local, rows=512000, reps=10):
+    """Closure network on the tensor cores: inference over fc_1024's 512,000 (cell, group)
+    rows and one training step of 8192 rows, CUDA events on the network's stream."""
+    import torch
+    from paper_2011_05427_gb300 import closure, mlp
+    dev = f"cuda:{local}"
+    net = mlp.MLP(closure._init(7), device=dev)
+    g = torch.Generator(device=dev)
+    g.manual_seed(3)
+    x = torch.rand((rows, 3), generator=g, device=dev) * 2 - 1
+    for _ in range(3):
+        net.forward(x)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(net.stream)
+    for _ in range(reps):
+        net.forward(x)
+    e1.record(net.stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    flops = 2.0 * rows * (3 * 256 + 2 * 256 * 256 + 256)
+    peak, src = bf16_peak()
+    ach = flops / (ms * 1e-3) / 1e12
+    xb = torch.rand((8192, 3), generator=g, device=dev)
+    yb = torch.rand(8192, generator=g, device=dev)
+    for _ in range(3):
+        net.train_step(xb, yb, lr=0.0)
+    torch.cuda.synchronize()
+    e0.record(net.stream)
+    for _ in range(reps):
+        net.train_step(xb, yb, lr=0.0)
+    e1.record(net.stream)
+    torch.cuda.synchronize()
+    ms_train = e0.elapsed_time(e1) / reps
+    return {"roofline": {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                         "frac": ach / peak, "traffic": None,
+                         "kernel": "k_layer1 + 2 x k_gemm (tcgen05 kind::f16, BF16 in, FP32 "
+                                   "accumulate in TMEM) with fused bias/ReLU/head epilogues",
+                         "ms": ms, "algorithmic_flops": flops, "peak_source": src},
+            "rows": rows, "train_step_ms_8192_rows": ms_train}
+
+
+def batch_bench(local, steps=3, warmup=2):
+    """batch_256: 256 independent slabs (cells 50-800, 16-64 directions per half range,
+    64/256/1024 groups) stepped together, FP32 sweeps, V-cycle, converged steps."""
+    import torch
+    from paper_2011_05427_gb300 import trt
+    slabs = W.batch_256()
+    upd = [c.n_cells * 2 * c.N * c.G for c in slabs]
+    cg = sum(c.n_cells * c.G for c in slabs)
+    B = trt.Batch(slabs, precision="sweep32", device=f"cuda:{local}")
+    best = B.autotune(1e-3, reps=2)
+    ms = B.sweep_time(1e-3, reps=5)
+    byt = sum(upd) * 16 + cg * 16
+    for _ in range(warmup):
+        B.step(1e-3, "V", 4, 1e-8)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(B.stream)
+    sts = [B.step(1e-3, "V", 4, 1e-8) for _ in range(steps)]
+    e1.record(B.stream)
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) * 1e-3
+    tot = sum(x["n_ti"] * u for st in sts for x, u in zip(st, upd))
+    hbm, src = peaks()
+    out = {"workload": "batch_256 (seed 2011054270): 256 slabs, cells U{50..800}, N in "
+                       "{16,32,64}, G in {64,256,1024}, FP32 sweeps, V-cycle l_max 4, eps 1e-8",
+           "value": tot / t, "unit": "updates/s", "ms_per_step": t / steps * 1e3,
+           "updates_per_sweep": sum(upd), "workspace_gb": B.workspace_bytes / 1e9,
+           "sweep_tile": {"D": best[1], "shape": best[2]},
+           "n_ti_per_slab_step": float(np.mean([x["n_ti"] for st in sts for x in st])),
+           "n_c_per_slab_step": float(np.mean([x["n_c"] for st in sts for x in st])),
+           "roofline_batched_sweep": {"bound": "hbm", "ms": ms, "achieved": byt / (ms * 1e-3) / 1e9,
+                                      "peak": hbm, "unit": "GB/s",
+                                      "frac": byt / (ms * 1e-3) / 1e9 / hbm,
+                                      "algorithmic_bytes": byt, "peak_source": src}}
+    B.close()
+    return out
+
+
+def closure_bench(local, ms_fp64, steps=10):
+    """Learned warm start: trained on snapshots of 4 slabs x 10 steps of the method, then
+    fc_1024 stepped with FP32 sweeps with and without it."""
+    from paper_2011_05427_gb300 import closure
+    import torch
+    t0 = time.perf_counter()
+    X, Y = closure.collect(closure.training_slabs(4), 10, 16384, device=f"cuda:{local}")
+    net, hist = closure.train(X, Y, iters=1000, batch=8192, lr=1e-3, device=f"cuda:{local}")
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    r = closure.compare(W.fc_1024("V"), net, steps, precision="sweep32", device=f"cuda:{local}")
+    a, b = r["plain"], r["closure"]
+    dT = float(np.max(np.abs(a["state"]["T"] - b["state"]["T"]) / a["state"]["T"]))
+    return {"train_rows": int(len(X)), "train_loss_first_last": [hist[0][1], hist[-1][1]],
+            "collect_and_train_s": t_train,
+            "sweep32_plain": {k: a[k] for k in ("n_ti", "n_c", "ms_per_step")},
+            "sweep32_closure": {k: b[k] for k in ("n_ti", "n_c", "ms_per_step")},
+            "speedup_closure_vs_plain_fp64": ms_fp64 / b["ms_per_step"],
+            "max_rel_T_closure_vs_plain": dT, "steps": steps}
+
+
 def counters(stats, steps):
     return {k: sum(x[k] for x in stats) / steps for k in ("n_ti", "n_c", "n_lo")}
 
@@ -283,6 +394,13 @@ def run_ours(args):
                 "note": "FP32 sweeps, FP64 group/grey LOQD + MEB; both converged to eps; "
                         "compared after the same warm-up + timed steps",
                 **counters(st_m, args.steps)}
+
+        if args.mlp:
+            extra["mlp"] = mlp_bench(local)
+        if args.closure and args.precision == "fp64":
+            extra["closure"] = closure_bench(local, ms_step)
+        if args.batch and ws == 1:
+            extra["batch_256"] = batch_bench(local)
 
     tile = s.tile
     if args.precision in ("fp64", "lo32"):
@@ -399,7 +517,11 @@ def main():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed", "sweep32", "lo32"])
     ap.add_argument("--cycle", default="V", choices=["V", "W"])
     ap.add_argument("--no-compare", dest="compare", action="store_false",
-                    help="skip the other-cycle and mixed-precision comparison runs")
+                    help="skip the comparison runs (other cycle, FP32 sweeps, MLP, closure, "
+                         "batch)")
+    ap.add_argument("--no-mlp", dest="mlp", action="store_false")
+    ap.add_argument("--no-closure", dest="closure", action="store_false")
+    ap.add_argument("--no-batch", dest="batch", action="store_false")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--profile-step", action="store_true",
                     help="run the warm-up steps and one more step, print nothing (for ncu)")
