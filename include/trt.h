@@ -201,6 +201,12 @@ int trt_k_sweep(trt_handle *h, double dt, const double *sigE, const double *emis
 int trt_set_closure(trt_handle *h, const float *params, const void *w16, void *scratch,
                     size_t scratch_bytes, float *x, float *y);
 
+/* ---- test aid: the device's exponential and reciprocal helpers ----
+ * ex[i] = e^{x[i]} by the table-driven method the opacity kernel uses (Tang 1989) and
+ * rc[i] = 1/x[i] by the refined hardware reciprocal, for accuracy tests against the C
+ * library.  x, ex, rc: device arrays of n doubles; enqueued on `stream`. */
+int trt_k_fastmath(int n, const double *x, double *ex, double *rc, void *stream);
+
 /* ---- batched slabs (not in the paper: many independent problems at once) ----
  * n slabs, each as trt_create would take it (grids[s], angles[s], groups[s],
  * opacities[s], cv[s]; one trt_options for all: precision, T0, stream, workspace), step

@@ -71,6 +71,7 @@ void carve(trt_handle *h, Carver &c)
     p.Ein0 = c.take<double>(G); p.Fin0 = c.take<double>(G);
     p.EinX = c.take<double>(G); p.FinX = c.take<double>(G);
     p.ihf = c.take<double>(nx + 1);
+    p.otab = c.take<double>(otab_doubles((int)G));
     p.rscratch_doubles = restrict_scratch_doubles((int)nx, (int)G, 1);
     p.rscratch = p.rscratch_doubles ? c.take<double>(p.rscratch_doubles) : nullptr;
     double **tl[] = {&h->T, &h->Told, &h->Tcyc, &h->Tphase, &h->Ttil, &h->Tnew, &h->sig_prev,
@@ -356,6 +357,7 @@ int trt_create(const trt_grid *grid, const trt_angles *angles, const trt_groups 
         k_fill_intensity<float><<<nb, 256, 0, p.stream>>>((float *)H->I_alt, H->sigE, rows, p.ldG, G);
     }
     CK(cudaGetLastError());
+    CK(launch_otab_build(p));   // opacity tables of this group structure
     CK(cudaMemsetAsync(H->flags, 0, 8 * sizeof(double), p.stream));
     CK(cudaStreamSynchronize(p.stream));
     *out = hp.release();
@@ -649,6 +651,14 @@ int trt_set_closure(trt_handle *h, const float *params, const void *w16, void *s
     h->mlp_x = x;
     h->mlp_y = y;
     return TRT_OK;
+}
+
+int trt_k_fastmath(int n, const double *x, double *ex, double *rc, void *stream)
+{
+    if (n < 1 || !x || !ex || !rc) return TRT_EINVAL;
+    return launch_fastmath(n, x, ex, rc, reinterpret_cast<cudaStream_t>(stream)) == cudaSuccess
+               ? TRT_OK
+               : TRT_ECUDA;
 }
 
 int trt_sweep_shapes(const trt_handle *h)

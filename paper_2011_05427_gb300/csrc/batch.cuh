@@ -25,6 +25,7 @@ struct OpacityArgs {
     float *sig32, *emis32;   // FP32 sweep inputs (sigma_E + 1/(c dt)) h/2, h e/2, or null
     const double *h;
     double icdt;
+    const double *otab;      // Problem::otab
 };
 
 struct SweepArgs {

@@ -22,30 +22,57 @@ struct SeriesTables {
     double Pinf;       // pi^4/15
     double Dinf;       // 2520 (zeta(6) + zeta(7))
     double tP[65], tD[65];   // tail coefficients 6/k^4 and 5040 k(k+1)/2 / k^8, k = 1..64
+    double g3x[3], g3w[3];   // 3-point rule; the centre weight is halved: the symmetric
+                             // loop of gauss_group visits the centre once per side
     double g4x[4], g4w[4];   // 4- and 6-point Gauss-Legendre rules on [-1, 1]
     double g6x[6], g6w[6];   // (narrow groups, see group_integrals)
+    double e2[32];           // 2^(j/32), j = 0..31 (texp)
+    double einv, eL1, eL2;   // 32/ln2 and ln2/32 = eL1 + eL2 (texp)
 };
-// 1/d in FP64 by Newton-Raphson, x_{k+1} = x_k (2 - d x_k), from the correctly rounded FP32
-// reciprocal: the relative error squares with each step, 2^-24 -> ~4e-15 -> rounding, so
-// two steps give the FP64 result to about an ulp at 6 FP64 operations, where an IEEE
-// division costs ~20 on GB300's FP64 pipe.  Outside the FP32 normal range it divides.
+// 1/d in FP64: the hardware's approximate FP64 reciprocal (special-function unit, a
+// relative error eps of order 2^-22, not the FP64 pipe) refined by one third-order
+// Newton-Raphson (Householder) step: with e = 1 - d x, x (1 + e + e^2) = (1 - eps^3)/d,
+// below FP64 rounding, at 3 FP64 FMAs where an IEEE division costs ~20 on GB300's FP64
+// pipe.  Zero, infinite, NaN or subnormal operands (or results) divide.
 __host__ __device__ inline double rcp64(double d)
 {
 #ifdef __CUDA_ARCH__
-    const float df = (float)d;
-    const float ad = fabsf(df);
-    if (!(ad > 1e-37f && ad < 1e37f)) return 1.0 / d;
-    double x = (double)__frcp_rn(df);
-    x = x * fma(-d, x, 2.0);
-    return x * fma(-d, x, 2.0);
+    double x;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(x) : "d"(d));
+    if (!(fabs(x) < 1e300) || x == 0.0) return 1.0 / d;
+    const double e = fma(-d, x, 1.0);
+    return fma(x, fma(e, e, e), x);
 #else
     return 1.0 / d;
 #endif
 }
 
+// e^x by Tang's table-driven method (P. T. P. Tang, "Table-driven implementation of the
+// exponential function in IEEE floating-point arithmetic", ACM TOMS 15, 1989): x = (32 m +
+// j) ln2/32 + r with |r| <= ln2/64 (two-part constant, exact product k L1), e^x =
+// 2^m 2^(j/32) (1 + p(r)), p the degree-6 Taylor polynomial of e^r - 1 (truncation
+// r^7/7! < 2e-18).  tab = 2^(j/32), j = 0..31 (SeriesTables::e2, staged in shared memory).
+// About 11 FP64 operations against ~20 for a library exponential; within about an ulp.
+// Outside (-708, 709) (and for NaN) it calls exp().
+struct ExpConsts {
+    double inv, L1, L2;   // 32/ln2; ln2/32 = L1 + L2 with L1 of 31 significant bits
+};
+__device__ inline double texp(double x, const double *tab, const ExpConsts &c)
+{
+    if (!(x > -708.0 && x < 709.0)) return exp(x);
+    const double kd = rint(x * c.inv);
+    const int k = (int)kd;
+    const double r = fma(-kd, c.L2, fma(-kd, c.L1, x));
+    const double q = r * r * (0.5 + r * (1.0 / 6 + r * (1.0 / 24 + r * (1.0 / 120 + r * (1.0 / 720)))));
+    const double t = tab[k & 31];
+    const double v = fma(t, r + q, t);
+    return v * __longlong_as_double((long long)((k >> 5) + 1023) << 52);
+}
+
 const SeriesTables &host_series();   // host copy (built once)
 void gauss_legendre_host(int n, double *x, double *w);   // nodes / weights on [-1, 1]
 cudaError_t ensure_tables();         // upload the tables to the current device (once)
+cudaError_t launch_fastmath(int n, const double *x, double *ex, double *rc, cudaStream_t st);
 
 // per-group physics at temperature T on host (inflow spectra, initial condition)
 void host_group_B(int G, const double *edges, double T, double *B);
@@ -96,7 +123,15 @@ struct Problem {
     size_t rscratch_doubles;
     // sweep tile: directions per CTA (0 = default) and strip shape index (0 = default)
     int sweep_D = 0, sweep_shape = 0;
+    // per-group Chebyshev tables of sigma_E T^3 and sigma_R T^3 in ln T (null: direct)
+    double *otab = nullptr;
 };
+
+// opacity tables: ln T in [kTabU0, kTabU0 + kTabNI kTabH), kTabNC coefficients per interval
+constexpr int kTabNI = 49, kTabNC = 12;
+constexpr double kTabU0 = -9.25, kTabH = 0.25;
+inline size_t otab_doubles(int G) { return (size_t)G * kTabNI * 2 * kTabNC; }
+cudaError_t launch_otab_build(const Problem &p);
 
 // ---- launchers (each enqueues on p.stream; returns cudaError_t of the launch) ----
 // sig32 / emis32 (may be null): the FP32 sweep's inputs (sigma_E + 1/(c dt)) h/2 and h e/2

@@ -10,6 +10,7 @@
 // exponentially convergent tails e^{-kx} at and above it, summed with the scale e^{x_g}
 // factored out so that cold cells (x ~ 1e5) neither underflow nor lose the ratio.
 #include <cmath>
+#include <cstring>
 #include "batch.cuh"
 
 namespace trt {
@@ -56,6 +57,9 @@ static SeriesTables build_tables()
         t.tP[k] = 6.0 / k4;
         t.tD[k] = 5040.0 * 0.5 * k * (k + 1.0) / (k4 * k4);
     }
+    gauss_legendre_host(3, t.g3x, t.g3w);
+    t.g3x[1] = 0.0;
+    t.g3w[1] *= 0.5;
     gauss_legendre_host(4, t.g4x, t.g4w);
     gauss_legendre_host(6, t.g6x, t.g6w);
     typedef long double LD;
@@ -89,6 +93,17 @@ static SeriesTables build_tables()
     }
     const LD pi = 3.141592653589793238462643383279502884L;
     t.Pinf = (double)(pi * pi * pi * pi / 15);
+    const LD ln2 = 0.693147180559945309417232121458176568L;
+    for (int j = 0; j < 32; ++j) t.e2[j] = (double)exp2l((LD)j / 32);
+    const LD L = ln2 / 32;
+    double l1 = (double)L;
+    uint64_t bits;
+    std::memcpy(&bits, &l1, 8);
+    bits &= ~((uint64_t(1) << 22) - 1);   // 31 significant bits: k L1 exact for |k| < 2^22
+    std::memcpy(&l1, &bits, 8);
+    t.eL1 = l1;
+    t.eL2 = (double)(L - (LD)l1);
+    t.einv = (double)(32 / ln2);
     LD z7 = 0;
     for (long k = 200000; k >= 1; --k) z7 += 1.0L / ((LD)k * k * k * k * k * k * k);
     LD z6 = pi * pi * pi * pi * pi * pi / 945;
@@ -125,6 +140,21 @@ __host__ __device__ inline int series_terms(double x)
 }
 
 // x < 2: P(x), Nt(x), D(x) by Horner
+// The exponential of the group integrals: texp (table-driven, common.cuh) on the device,
+// the C library's on the host (inflow spectra and initial state at creation).
+struct Mx {
+    const double *tab;
+    ExpConsts c;
+    __host__ __device__ double ex(double x) const
+    {
+#ifdef __CUDA_ARCH__
+        return texp(x, tab, c);
+#else
+        return std::exp(x);
+#endif
+    }
+};
+
 __host__ __device__ inline void edge_series(double x, const SeriesTables &t, double &P,
                                             double &Nt, double &D)
 {
@@ -146,7 +176,7 @@ __host__ __device__ inline void edge_series(double x, const SeriesTables &t, dou
 //   TN = e^x x^4/(e^x - 1)    = x^4 / (1 - e^{-x})
 //   TD = e^x (Dinf - D(x))    = sum_k k(k+1)/2 e^{-(k-1)x} 5040 e7(kx)/k^8
 // with e_m(y) = sum_{j<=m} y^j/j!  (integration by parts of t^n e^{-kt}).
-__host__ __device__ inline void edge_tail(double x, const SeriesTables &t, double &TP,
+__host__ __device__ inline void edge_tail(double x, const SeriesTables &t, const Mx &mx, double &TP,
                                           double &TN, double &TD)
 {
     const double e3 = 1.0 + x * (1.0 + x * (0.5 + x * (1.0 / 6.0)));
@@ -159,7 +189,7 @@ __host__ __device__ inline void edge_tail(double x, const SeriesTables &t, doubl
         TN = x * x * x * x;
         return;
     }
-    const double q = exp(-x);
+    const double q = mx.ex(-x);
     double ek = q;
     for (int k = 2; k <= 64 && ek >= 1e-18; ++k) {
         const double y = (double)k * x;
@@ -178,25 +208,26 @@ __host__ __device__ inline void edge_tail(double x, const SeriesTables &t, doubl
 // Gauss rule on [xa, xb] for the three scaled integrands x^3 e^{xa-x}/(1-e^{-x}),
 // x^4 e^{xa-x}/(1-e^{-x})^2, x^7 e^{xa-x}/(1-e^{-x})^3.  Their nearest singularities
 // are the poles x = 2 pi i k, so an n-point rule on a half-width a converges like
-// (a/4 pi)^(2n): 4 points reach 1e-16 for xb - xa <= 1/4, 6 points for xb - xa <= 1.
+// (a/4 pi)^(2n): 3 points reach 1e-16 for xb - xa <= 1/20, 4 points for xb - xa <= 1/4,
+// 6 points for xb - xa <= 1.
 template <int NP>
 __host__ __device__ inline void gauss_group(double xa, double xb, const double *gx,
-                                            const double *gw, double &dPs, double &Ns,
-                                            double &Ds)
+                                            const double *gw, const Mx &mx, double &dPs,
+                                            double &Ns, double &Ds)
 {
     // symmetric rule: the points mid -/+ hw xi_j share e^{xa-mid} and e^{+-hw xi_j}, so a
     // pair of points costs one exponential and one reciprocal; e^{-x} follows from
     // e^{-mid} the same way, and 1 - e^{-x} is formed directly where x >= 0.1 (relative
     // error <= eps/x) and by expm1 below
     const double hw = 0.5 * (xb - xa), mid = 0.5 * (xb + xa);
-    const double E0 = exp(xa - mid);
+    const double E0 = mx.ex(xa - mid);
     const bool warm = mid - hw < 37.0;              // some point has 1 - e^{-x} != 1
-    const double Em = warm ? exp(-mid) : 0.0;
+    const double Em = warm ? mx.ex(-mid) : 0.0;
     double sp = 0.0, sn = 0.0, sd = 0.0;
 #pragma unroll
     for (int j = NP / 2; j < NP; ++j) {
         const double t = hw * gx[j];
-        const double ep = exp(t), em = rcp64(ep);
+        const double ep = mx.ex(t), em = rcp64(ep);
 #pragma unroll
         for (int side = 0; side < 2; ++side) {
             const double x = side ? mid + t : mid - t;
@@ -224,24 +255,27 @@ __host__ __device__ inline void gauss_group(double xa, double xb, const double *
 // the x^7 factor varies by at most (5/4)^7 and the rest is analytic within 2 pi);
 // every other group differences the closed forms.
 __host__ __device__ inline void group_integrals(double xa, double xb, bool binf,
-                                                const SeriesTables &t, double &dPs,
-                                                double &Ns, double &Ds, double &om)
+                                                const SeriesTables &t, const Mx &mx,
+                                                double &dPs, double &Ns, double &Ds,
+                                                double &om)
 {
     om = binf ? 1.0 : -expm1(-(xb - xa));
     const double w = xb - xa;
     if (!binf && w <= 0.25 * xa && w <= 1.0) {
-        if (w <= 0.25)
-            gauss_group<4>(xa, xb, t.g4x, t.g4w, dPs, Ns, Ds);
+        if (w <= 0.05)
+            gauss_group<3>(xa, xb, t.g3x, t.g3w, mx, dPs, Ns, Ds);
+        else if (w <= 0.25)
+            gauss_group<4>(xa, xb, t.g4x, t.g4w, mx, dPs, Ns, Ds);
         else
-            gauss_group<6>(xa, xb, t.g6x, t.g6w, dPs, Ns, Ds);
+            gauss_group<6>(xa, xb, t.g6x, t.g6w, mx, dPs, Ns, Ds);
         return;
     }
     if (xa >= kXSplit) {
         double TPa, TNa, TDa, TPb = 0.0, TNb = 0.0, TDb = 0.0, r = 0.0;
-        edge_tail(xa, t, TPa, TNa, TDa);
+        edge_tail(xa, t, mx, TPa, TNa, TDa);
         if (!binf) {
-            edge_tail(xb, t, TPb, TNb, TDb);
-            r = exp(xa - xb);
+            edge_tail(xb, t, mx, TPb, TNb, TDb);
+            r = mx.ex(xa - xb);
         }
         dPs = TPa - r * TPb;
         Ns = (TNa - r * TNb) + 4.0 * dPs;
@@ -257,13 +291,13 @@ __host__ __device__ inline void group_integrals(double xa, double xb, bool binf,
             edge_series(xb, t, Pb, Nb, Db);
         } else {
             double TP, TN, TD;
-            edge_tail(xb, t, TP, TN, TD);
-            double eb = exp(-xb);
+            edge_tail(xb, t, mx, TP, TN, TD);
+            double eb = mx.ex(-xb);
             Pb = t.Pinf - eb * TP;
             Nb = -eb * TN + 4.0 * Pb;
             Db = t.Dinf - eb * TD;
         }
-        double ea = exp(xa);
+        double ea = mx.ex(xa);
         dPs = ea * (Pb - Pa);
         Ns = ea * (Nb - Na);
         Ds = ea * (Db - Da);
@@ -278,13 +312,46 @@ void host_group_B(int G, const double *edges, double T, double *B)
         bool binf = std::isinf(edges[g + 1]);
         double xb = binf ? 0.0 : edges[g + 1] / T;
         double dPs, Ns, Ds, om;
-        group_integrals(xa, xb, binf, t, dPs, Ns, Ds, om);
+        group_integrals(xa, xb, binf, t, Mx{nullptr, ExpConsts{}}, dPs, Ns, Ds, om);
         B[g] = kCB * T * T * T * T * exp(-xa) * dPs;
     }
 }
 
 // One thread per (group, cell); outputs [G][nx] (cell fastest, coalesced).
-__device__ inline void opacity_body(const OpacityArgs &a, long idx)
+// Chebyshev series sum_k c_k T_k(t) by Clenshaw's recurrence (c_0 already halved)
+__device__ inline double clenshaw(const double *__restrict__ c, double t)
+{
+    double b1 = 0.0, b2 = 0.0;
+    const double t2 = 2.0 * t;
+#pragma unroll
+    for (int k = kTabNC - 1; k >= 1; --k) {
+        const double b0 = fma(t2, b1, c[k] - b2);
+        b2 = b1;
+        b1 = b0;
+    }
+    return fma(t, b1, c[0] - b2);
+}
+
+// sigma_E T^3 / (27 s) = (1 - e^{-w}) / [P]  and  sigma_R T^3 / (27 s) = [Nt] / [D] of one
+// group at temperature T, the e^{xa}-scaled integrals of group_integrals
+__host__ __device__ inline void group_ratios(double T, double ea, double eb, const Mx &mx,
+                                             double &A, double &Rr)
+{
+    const double iT = 1.0 / T;
+    const double xa = ea * iT;
+    const bool binf = isinf(eb);
+    const double xb = binf ? 0.0 : eb * iT;
+    double dPs, Ns, Ds, om;
+#ifdef __CUDA_ARCH__
+    group_integrals(xa, xb, binf, c_ser, mx, dPs, Ns, Ds, om);
+#else
+    group_integrals(xa, xb, binf, host_series(), mx, dPs, Ns, Ds, om);
+#endif
+    A = om / dPs;
+    Rr = Ns / Ds;
+}
+
+__device__ inline void opacity_body(const OpacityArgs &a, long idx, const Mx &mx)
 {
     const int nx = a.nx, G = a.G;
     if (idx >= (long)G * nx) return;
@@ -295,17 +362,31 @@ __device__ inline void opacity_body(const OpacityArgs &a, long idx)
     const double xa = a.edges[g] * iT;
     const double eb = a.edges[g + 1];
     const bool binf = isinf(eb);
-    const double xb = binf ? 0.0 : eb * iT;
-    double dPs, Ns, Ds, om;
-    group_integrals(xa, xb, binf, c_ser, dPs, Ns, Ds, om);
     double T3 = Ti * Ti * Ti;
     double k27 = 27.0 * a.s;
     const double iT3 = rcp64(T3);
-    const double sg = k27 * om * iT3 * rcp64(dPs);
-    const double em = k27 * kCB * Ti * exp(-xa) * om;
+    double sg, sR, om;
+    const double u = a.otab ? log(Ti) : 0.0;
+    const double z = (u - kTabU0) * (1.0 / kTabH);
+    if (a.otab && z >= 0.0 && z < (double)kTabNI) {
+        // tabulated: the two ratios as Chebyshev series in ln T on the cell's interval
+        const int m = min((int)z, kTabNI - 1);
+        const double t = 2.0 * (z - (double)m) - 1.0;
+        const double *c = a.otab + ((size_t)g * kTabNI + m) * 2 * kTabNC;
+        sg = k27 * clenshaw(c, t) * iT3;
+        sR = k27 * clenshaw(c + kTabNC, t) * iT3;
+        om = binf ? 1.0 : -expm1(-(eb - a.edges[g]) * iT);
+    } else {
+        const double xb = binf ? 0.0 : eb * iT;
+        double dPs, Ns, Ds;
+        group_integrals(xa, xb, binf, c_ser, mx, dPs, Ns, Ds, om);
+        sg = k27 * om * iT3 * rcp64(dPs);
+        sR = k27 * Ns * iT3 * rcp64(Ds);
+    }
+    const double em = k27 * kCB * Ti * mx.ex(-xa) * om;
     a.sigE[idx] = sg;
     a.emis[idx] = em;
-    a.sigR[idx] = k27 * Ns * iT3 * rcp64(Ds);
+    a.sigR[idx] = sR;
     if (a.sig32) {   // FP32 sweep inputs: sigma_t h/2 and h e/2, one rounding each
         const double hh = 0.5 * a.h[i];
         a.sig32[idx] = (float)(hh * (sg + a.icdt));
@@ -313,26 +394,99 @@ __device__ inline void opacity_body(const OpacityArgs &a, long idx)
     }
 }
 
+// the 2^(j/32) table of texp in shared memory (lanes index it with different j)
+__device__ inline Mx stage_exp_table(double *s_e2)
+{
+    if (threadIdx.x < 32) s_e2[threadIdx.x] = c_ser.e2[threadIdx.x];
+    __syncthreads();
+    return Mx{s_e2, ExpConsts{c_ser.einv, c_ser.eL1, c_ser.eL2}};
+}
+
 __global__ void __launch_bounds__(256) k_opacity(OpacityArgs a)
 {
-    opacity_body(a, (long)blockIdx.x * blockDim.x + threadIdx.x);
+    __shared__ double s_e2[32];
+    const Mx mx = stage_exp_table(s_e2);
+    opacity_body(a, (long)blockIdx.x * blockDim.x + threadIdx.x, mx);
 }
 
 __global__ void __launch_bounds__(256) k_opacity_b(const int *__restrict__ meta, int N,
                                                    const OpacityArgs *__restrict__ xs)
 {
+    __shared__ double s_e2[32];
+    const Mx mx = stage_exp_table(s_e2);
     for (int b = blockIdx.x;; b += gridDim.x) {
         int s, bx, by;
         if (!bdecode(meta, N, b, s, bx, by)) break;
         const OpacityArgs a = xs[s];
-        opacity_body(a, (long)bx * blockDim.x + threadIdx.x);
+        opacity_body(a, (long)bx * blockDim.x + threadIdx.x, mx);
     }
+}
+
+// accuracy check of the device helpers: texp and rcp64 of x (test aid)
+__global__ void k_fastmath(int n, const double *__restrict__ x, double *__restrict__ ex,
+                           double *__restrict__ rc)
+{
+    __shared__ double s_e2[32];
+    const Mx mx = stage_exp_table(s_e2);
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    ex[i] = mx.ex(x[i]);
+    rc[i] = rcp64(x[i]);
+}
+
+cudaError_t launch_fastmath(int n, const double *x, double *ex, double *rc, cudaStream_t st)
+{
+    cudaError_t e = ensure_tables();
+    if (e != cudaSuccess) return e;
+    k_fastmath<<<(n + 255) / 256, 256, 0, st>>>(n, x, ex, rc);
+    return cudaGetLastError();
+}
+
+// Tables: one thread per (group, interval) evaluates the two ratios directly at the
+// interval's kTabNC Chebyshev points in ln T and stores their Chebyshev coefficients.
+__global__ void k_otab_build(int G, const double *__restrict__ edges, double *__restrict__ tab)
+{
+    __shared__ double s_e2[32];
+    const Mx mx = stage_exp_table(s_e2);
+    const int id = blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= G * kTabNI) return;
+    const int g = id / kTabNI, m = id - g * kTabNI;
+    const double umid = kTabU0 + kTabH * (m + 0.5);
+    double fa[kTabNC], fr[kTabNC];
+    for (int j = 0; j < kTabNC; ++j) {
+        const double th = kPi * (j + 0.5) / kTabNC;
+        const double T = exp(umid + 0.5 * kTabH * cos(th));
+        group_ratios(T, edges[g], edges[g + 1], mx, fa[j], fr[j]);
+    }
+    double *c = tab + (size_t)id * 2 * kTabNC;
+    for (int k = 0; k < kTabNC; ++k) {
+        double sa = 0.0, sr = 0.0;
+        for (int j = 0; j < kTabNC; ++j) {
+            const double ck = cos(kPi * k * (j + 0.5) / kTabNC);
+            sa = fma(fa[j], ck, sa);
+            sr = fma(fr[j], ck, sr);
+        }
+        const double sc = (k == 0 ? 1.0 : 2.0) / kTabNC;
+        c[k] = sa * sc;
+        c[kTabNC + k] = sr * sc;
+    }
+}
+
+cudaError_t launch_otab_build(const Problem &p)
+{
+    if (!p.otab) return cudaSuccess;
+    cudaError_t e = ensure_tables();
+    if (e != cudaSuccess) return e;
+    const int n = p.G * kTabNI;
+    k_otab_build<<<(n + 127) / 128, 128, 0, p.stream>>>(p.G, p.edges, p.otab);
+    return cudaGetLastError();
 }
 
 OpacityArgs make_opacity_args(const Problem &p, const double *T, double *sigE, double *emis,
                               double *sigR, float *sig32, float *emis32, double dt)
 {
     OpacityArgs a;
+    a.otab = p.otab;
     a.nx = p.nx; a.G = p.G; a.T = T; a.edges = p.edges; a.s = p.s;
     a.sigE = sigE; a.emis = emis; a.sigR = sigR; a.sig32 = sig32; a.emis32 = emis32;
     a.h = p.h;

@@ -148,6 +148,8 @@ def lib():
     L.trt_mlp_features.argtypes = [ctypes.c_int] * 2 + [_vp] * 6
     L.trt_mlp_status.restype = ctypes.c_int
     L.trt_mlp_status.argtypes = []
+    L.trt_k_fastmath.restype = ctypes.c_int
+    L.trt_k_fastmath.argtypes = [ctypes.c_int] + [_vp] * 4
     # batched slabs
     L.trt_batch_workspace_bytes.restype = ctypes.c_size_t
     L.trt_batch_workspace_bytes.argtypes = [ctypes.c_int] + [_vp] * 4
@@ -185,7 +187,7 @@ EXPORTED = ("trt_workspace_bytes", "trt_create", "trt_step", "trt_moments", "trt
             "trt_mlp_grad", "trt_mlp_adam", "trt_mlp_features", "trt_mlp_status",
             "trt_batch_workspace_bytes", "trt_create_batch", "trt_step_batch",
             "trt_batch_slab", "trt_batch_set_tile", "trt_batch_sweep_time",
-            "trt_destroy_batch", "trt_batch_last_error")
+            "trt_destroy_batch", "trt_batch_last_error", "trt_k_fastmath")
 
 
 class TRTError(RuntimeError):

@@ -66,6 +66,25 @@ def test_opacity_parity(trt, orc, G, nx):
     assert np.all(np.abs(em[~big]) < 1e-270)
 
 
+@pytest.mark.parametrize("G", [17, 1024])
+def test_opacity_tables_dense_in_T(trt, orc, G):
+    """The tabulated ratios (Chebyshev series in ln T per group, 0.25-wide intervals) at
+    600 temperatures log-spaced over 5e-5 .. 30 keV -- every interval, its edges and both
+    sides of the tabulated range -- against the oracle's direct integrals."""
+    T = np.exp(np.linspace(np.log(5e-5), np.log(30.0), 600))
+    edges = W.group_edges(G, 1e-5, 1e2)
+    s = solver(trt, nx=T.size, G=G, edges=edges, levels=[G, 1], s=1.3)
+    sig, em, sR = (x.cpu().numpy() for x in s.k_opacity(T))
+    osig, oem, osR, _ = orc.physics_field(edges, T, 1.3)
+    assert rel(sig, osig) < 1e-12
+    # sigma_R: the oracle's own values of the wide (17-group) structure are not smooth in
+    # T below ~1e-11 -- Chebyshev fits of them with 12, 14, 16 or 18 points per interval all
+    # miss them by 0.8e-11 .. 1.3e-11 while sigma_E fits to 7e-15 -- so 2e-11 here
+    assert rel(sR, osR) < 2e-11
+    big = oem > 1e-280
+    assert rel(em[big], oem[big]) < 1e-12
+
+
 def test_opacity_sampled_full_size(trt, orc):
     """fc_4096 sizes (1000 cells x 4096 groups), oracle on a sample of cells."""
     cfg = W.fc_4096()
@@ -300,3 +319,41 @@ def test_grey_newton_parity(trt, orc, nx, have_prev):
     if not bad:
         assert rel(T.cpu().numpy(), oT) < 1e-11
         assert rel(sol["E"].cpu().numpy()[0], oE) < 1e-11
+
+
+# ---------------------------------------------------------------------------- helpers
+def test_device_exp_and_reciprocal(trt):
+    """The opacity kernel's exponential (Tang's table-driven method) and reciprocal
+    (refined hardware approximation) against the C library in FP64: within 2 ulp over the
+    normal range, the library's own values outside it, IEEE results at 0 / inf / NaN."""
+    import torch
+    r = np.random.default_rng(77)
+    x = np.concatenate([r.uniform(-707.9, 708.9, 200000), r.uniform(-1, 1, 50000),
+                        r.uniform(-40, 40, 50000), np.arange(-700, 700, 0.25),
+                        [0.0, -0.0, 1e-300, -745.5, 709.9, 800.0, -800.0]])
+    n = x.size
+    xd = torch.as_tensor(x, device="cuda")
+    ex = torch.empty_like(xd)
+    rc = torch.empty_like(xd)
+    assert trt.lib().trt_k_fastmath(n, xd.data_ptr(), ex.data_ptr(), rc.data_ptr(), None) == 0
+    torch.cuda.synchronize()
+    ex = ex.cpu().numpy()
+    with np.errstate(over="ignore"):
+        ref = np.exp(x)
+    fin = np.isfinite(ref)
+    assert np.max(np.abs(ex[fin] - ref[fin]) / np.spacing(ref[fin])) <= 2.0
+    assert np.all(ex[~fin] == ref[~fin])
+    # reciprocal over magnitudes 1e-300 .. 1e300 and both signs
+    y = np.concatenate([np.exp(r.uniform(-690, 690, 200000)) * r.choice([-1, 1], 200000),
+                        [1.0, 3.0, 0.1, 7e-310, 0.0, np.inf, -np.inf]])
+    yd = torch.as_tensor(y, device="cuda")
+    ex2 = torch.empty_like(yd)
+    rc2 = torch.empty_like(yd)
+    assert trt.lib().trt_k_fastmath(y.size, yd.data_ptr(), ex2.data_ptr(), rc2.data_ptr(), None) == 0
+    torch.cuda.synchronize()
+    rc2 = rc2.cpu().numpy()
+    with np.errstate(divide="ignore"):
+        rref = 1.0 / y
+    fin = np.isfinite(rref) & (np.abs(rref) > 1e-300)
+    assert np.max(np.abs(rc2[fin] - rref[fin]) / np.spacing(np.abs(rref[fin]))) <= 1.0
+    assert np.all(rc2[~fin] == rref[~fin])
