@@ -239,7 +239,7 @@ void build_stage(trt_batch *b, int id, double dt, int cycle_type)
             const Problem &p = H(s)->p;
             B.set(oo, s, make_opacity_args(p, H(s)->T, H(s)->sigE, H(s)->emis, H(s)->sigR,
                                            H(s)->sig32, H(s)->emis32, dt),
-                  opacity_blocks(p), opacity_blocks(p));
+                  opacity_blocks(p), opacity_gx(p));
         }
         const size_t isw = sg.ops.size();
         B.add(K_SWEEP, C_SWEEP);
@@ -297,7 +297,7 @@ void build_stage(trt_batch *b, int id, double dt, int cycle_type)
             const Problem &p = H(s)->p;
             B.set(o0, s, make_opacity_args(p, H(s)->T, H(s)->sigE, H(s)->emis, H(s)->sigR,
                                            nullptr, nullptr, 0.0),
-                  opacity_blocks(p), opacity_blocks(p));
+                  opacity_blocks(p), opacity_gx(p));
         }
         {
             Op &o = B.add(K_LO, C_CYCLE);
@@ -348,7 +348,7 @@ void build_stage(trt_batch *b, int id, double dt, int cycle_type)
                     const Problem &p = H(s)->p;
                     B.set(oo, s, make_opacity_args(p, Tbuf(s, k), H(s)->sigE, H(s)->emis,
                                                    H(s)->sigR, nullptr, nullptr, 0.0),
-                          opacity_blocks(p), opacity_blocks(p));
+                          opacity_blocks(p), opacity_gx(p));
                 }
                 for (int s = 0; s < n; ++s) {
                     crs[s] = H(s)->crs;

@@ -49,7 +49,7 @@ struct FinalizeArgs {
 
 struct LoCtx {
     int nx;
-    double dt, icdt;
+    double dt, icdt, idt;   // dt, 1/(c dt), 1/dt
     const double *h, *ihf;
     Level L;
     const double *a_cell, *s_cell;   // grey: explicit absorption / source per cell
@@ -120,6 +120,7 @@ inline int lo_mmax_h(int nx)
 OpacityArgs make_opacity_args(const Problem &p, const double *T, double *sigE, double *emis,
                               double *sigR, float *sig32, float *emis32, double dt);
 int opacity_blocks(const Problem &p);
+int opacity_gx(const Problem &p);   // blocks along the cells (32 cells x 8 groups each)
 SweepArgs make_sweep_args(const Problem &p, double dt, const void *sigE, const void *emis,
                           const void *I_old, void *I_new, double *part, double *psi_exit,
                           double *f, double *fb0, double *fbX, double *C0, double *CX, int D);

@@ -123,14 +123,16 @@ struct Problem {
     size_t rscratch_doubles;
     // sweep tile: directions per CTA (0 = default) and strip shape index (0 = default)
     int sweep_D = 0, sweep_shape = 0;
-    // per-group Chebyshev tables of sigma_E T^3 and sigma_R T^3 in ln T (null: direct)
+    // per-group Chebyshev tables in ln T of sigma_E T^3, sigma_R T^3 and the emission
+    // factor ln(1 - e^{-w}) (null: direct integrals)
     double *otab = nullptr;
 };
 
 // opacity tables: ln T in [kTabU0, kTabU0 + kTabNI kTabH), kTabNC coefficients per interval
 constexpr int kTabNI = 49, kTabNC = 12;
 constexpr double kTabU0 = -9.25, kTabH = 0.25;
-inline size_t otab_doubles(int G) { return (size_t)G * kTabNI * 2 * kTabNC; }
+constexpr int kTabNF = 3;   // series per interval: sigma_E T^3, sigma_R T^3, ln(1 - e^{-w})
+inline size_t otab_doubles(int G) { return (size_t)G * kTabNI * kTabNF * kTabNC; }
 cudaError_t launch_otab_build(const Problem &p);
 
 // ---- launchers (each enqueues on p.stream; returns cudaError_t of the launch) ----

@@ -125,7 +125,7 @@ template <typename R>
 __device__ void lo_stage(const LoCtx &x, int q, R *sm, int mmax, int t, int nthr)
 {
     const int n = x.nx;
-    const R dt = (R)x.dt;
+    const R idt = (R)x.idt;
     const int P = min(32, n / 2);
     const int S = 32 * mmax;
     R *PLc = sm, *PRc = sm + S, *GDc = sm + 2 * S, *Ap = sm + 3 * S, *Dp = sm + 5 * S;
@@ -141,8 +141,8 @@ __device__ void lo_stage(const LoCtx &x, int q, R *sm, int mmax, int t, int nthr
             R ai, si;
             cell_terms<R>(x, q, f, ai, si);
             const R hi = (R)x.h[f];
-            Ap[k * 32 + l] = hi / dt + hi * ai;
-            Dp[k * 32 + l] = hi * si + hi * (R)x.L.Eold[(size_t)q * n + f] / dt;
+            Ap[k * 32 + l] = hi * idt + hi * ai;
+            Dp[k * 32 + l] = hi * si + hi * (R)x.L.Eold[(size_t)q * n + f] * idt;
         }
     }
 }
@@ -153,7 +153,6 @@ __device__ void warp_lo_solve(const LoCtx &x, int q, R *sm, int mmax, bool stage
 {
     const int lane = threadIdx.x & 31;
     const int n = x.nx;
-    const R dt = (R)x.dt;
     double *E = x.L.E + (size_t)q * n;
     double *F = x.L.F + (size_t)q * (n + 1);
 
@@ -164,8 +163,8 @@ __device__ void warp_lo_solve(const LoCtx &x, int q, R *sm, int mmax, bool stage
             face_coef<R>(x, q, 1, PL1, PR1, GD1);
             cell_terms<R>(x, q, 0, ai, si);
             R hi = (R)x.h[0];
-            R di = hi / dt + hi * ai + PL1 + PR0;
-            R rh = hi * si + hi * (R)x.L.Eold[(size_t)q * n] / dt - GD1 + GD0;
+            R di = hi * (R)x.idt + hi * ai + PL1 + PR0;
+            R rh = hi * si + hi * (R)x.L.Eold[(size_t)q * n] * (R)x.idt - GD1 + GD0;
             R e0 = rh / di;
             E[0] = (double)e0;
             R F0 = GD0 - PR0 * e0, F1 = GD1 + PL1 * e0;
@@ -455,7 +454,7 @@ __device__ void restrict_body(const RestrictCtx &x, int bx, int by)
         __syncthreads();
     }
     const double rn = (double)x.r;
-    const double sRP = (v[9] != 0.0) ? v[7] / v[9] : v[8] / rn;
+    const double sRP = (v[9] != 0.0) ? v[7] * rcp64(v[9]) : v[8] / rn;
     // ---- pass 2 (faces): xi, eta sums, side energies, Fold ----
     double u[kRV2];
 #pragma unroll
@@ -499,8 +498,9 @@ __device__ void restrict_body(const RestrictCtx &x, int bx, int by)
     const Level &T = x.T;
     if (i < nx) {
         size_t c = (size_t)P * nx + i;
-        (T.phi)[c] = (v[6] != 0.0) ? v[0] / v[6] : v[1] / rn;
-        (T.sig)[c] = (v[6] != 0.0) ? v[2] / v[6] : v[3] / rn;
+        const double i6 = (v[6] != 0.0) ? rcp64(v[6]) : 0.0, irn = 1.0 / rn;
+        (T.phi)[c] = (v[6] != 0.0) ? v[0] * i6 : v[1] * irn;
+        (T.sig)[c] = (v[6] != 0.0) ? v[2] * i6 : v[3] * irn;
         (T.emis)[c] = v[4];
         (T.Eold)[c] = v[5];
         T.Esum[c] = v[6];
@@ -509,8 +509,8 @@ __device__ void restrict_body(const RestrictCtx &x, int bx, int by)
         size_t f = (size_t)P * nf + i;
         double xi = u[0] + kC * (u[1] - u[2]);
         (T.sigR)[f] = sRP;
-        (T.etaR)[f] = (xi > 0.0 && u[3] != 0.0) ? xi / (kC * u[3]) : 0.0;
-        (T.etaL)[f] = (xi < 0.0 && u[4] != 0.0) ? -xi / (kC * u[4]) : 0.0;
+        (T.etaR)[f] = (xi > 0.0 && u[3] != 0.0) ? xi * rcp64(kC * u[3]) : 0.0;
+        (T.etaL)[f] = (xi < 0.0 && u[4] != 0.0) ? -xi * rcp64(kC * u[4]) : 0.0;
         (T.Fold)[f] = u[5];
     }
     if (i == 0 || i == nx) {
@@ -631,20 +631,21 @@ __device__ void restrict_final_body(const Restrict2Ctx &x, int bx, int by)
     const Level &T = x.T;
     if (i < nx) {
         const size_t c = (size_t)P * nx + i;
-        T.phi[c] = (v[6] != 0.0) ? v[0] / v[6] : v[1] / rn;
-        T.sig[c] = (v[6] != 0.0) ? v[2] / v[6] : v[3] / rn;
+        const double i6 = (v[6] != 0.0) ? rcp64(v[6]) : 0.0, irn = 1.0 / rn;
+        T.phi[c] = (v[6] != 0.0) ? v[0] * i6 : v[1] * irn;
+        T.sig[c] = (v[6] != 0.0) ? v[2] * i6 : v[3] * irn;
         T.emis[c] = v[4];
         T.Eold[c] = v[5];
         T.Esum[c] = v[6];
     }
     const double dxf = (i == 0) ? 0.5 * x.h[0] : (i == nx) ? 0.5 * x.h[nx - 1]
                                             : 0.5 * (x.h[i - 1] + x.h[i]);
-    const double sRP = (v[9] != 0.0) ? v[7] / v[9] : v[8] / rn;
+    const double sRP = (v[9] != 0.0) ? v[7] * rcp64(v[9]) : v[8] / rn;
     const double xi = dxf * (v[10] - sRP * v[11]) + kC * (v[12] - v[13]);
     const size_t f = (size_t)P * nf + i;
     T.sigR[f] = sRP;
-    T.etaR[f] = (xi > 0.0 && v[14] != 0.0) ? xi / (kC * v[14]) : 0.0;
-    T.etaL[f] = (xi < 0.0 && v[15] != 0.0) ? -xi / (kC * v[15]) : 0.0;
+    T.etaR[f] = (xi > 0.0 && v[14] != 0.0) ? xi * rcp64(kC * v[14]) : 0.0;
+    T.etaL[f] = (xi < 0.0 && v[15] != 0.0) ? -xi * rcp64(kC * v[15]) : 0.0;
     T.Fold[f] = v[16];
     if (i == 0 || i == nx) {
         const double phb = (v[19] != 0.0) ? v[17] / v[19] : v[18] / rn;
@@ -680,7 +681,7 @@ __device__ void grey_body(const GreyCtx &x)
     const int nx = x.lo.nx;
     double *sa = gsm;            // absorption w c sig*
     double *ss = sa + nx;        // source w Q* - (1-w) cv (T* - Told)/dt
-    double *sL = ss + nx;        // Lambda
+    double *sL = ss + nx;        // 1 / Lambda
     double *red = sL + nx;       // [32]
     double *wsm = red + 32;      // warp-solver scratch
     const GreyArgs &a = x.a;
@@ -691,25 +692,27 @@ __device__ void grey_body(const GreyCtx &x)
         const double Ts = a.Tstar[i];
         const double sig = g.sig[i];
         const double Q = 2.0 * g.emis[i];
-        const double x1 = a.nu_first / Ts;
+        const double iTs = rcp64(Ts);
+        const double x1 = a.nu_first * iTs;
         double dQ = k54 * (1.0 + x1) * exp(-x1);
         if (!isinf(a.nu_last)) {
-            const double xL = a.nu_last / Ts;
+            const double xL = a.nu_last * iTs;
             dQ -= k54 * (1.0 + xL) * exp(-xL);
         }
         double D = 0.0;
         if (have_prev) {
             const double Tp = a.T_prev[i];
             // secant only where |dT| is far above rounding (relative noise ~ eps T/|dT|)
-            if (fabs(Ts - Tp) > 1e-7 * Ts) D = (sig - a.sig_prev[i]) / (Ts - Tp);
+            if (fabs(Ts - Tp) > 1e-7 * Ts) D = (sig - a.sig_prev[i]) * rcp64(Ts - Tp);
         }
         const double base = cvdt + dQ;
         double L = base - kC * D * g.Esum[i];
         if (L < 0.5 * base) L = 0.5 * base;
-        const double w = cvdt / L;
+        const double iL = rcp64(L);
+        const double w = cvdt * iL;
         sa[i] = w * kC * sig;
         ss[i] = w * Q - (1.0 - w) * cvdt * (Ts - a.Told[i]);
-        sL[i] = L;
+        sL[i] = iL;
         a.sig_prev_out[i] = sig;
         a.T_prev_out[i] = Ts;
     }
@@ -726,7 +729,7 @@ __device__ void grey_body(const GreyCtx &x)
     for (int i = threadIdx.x; i < nx; i += blockDim.x) {
         const double Ts = a.Tstar[i];
         const double E = g.E[i];
-        const double T = Ts + (kC * g.sig[i] * E - 2.0 * g.emis[i] - cvdt * (Ts - a.Told[i])) / sL[i];
+        const double T = Ts + (kC * g.sig[i] * E - 2.0 * g.emis[i] - cvdt * (Ts - a.Told[i])) * sL[i];
         a.T[i] = T;
         if (!(T > 0.0) || !isfinite(T) || !isfinite(E)) bad = 1.0;
         if (a.want_norms) {
@@ -816,7 +819,8 @@ __global__ void __launch_bounds__(256) k_copy_b(const int *__restrict__ meta, in
 LoCtx make_lo_ctx(const Problem &p, double dt, const Level &L)
 {
     LoCtx x;
-    x.nx = p.nx; x.dt = dt; x.icdt = 1.0 / (kC * dt); x.h = p.h; x.ihf = p.ihf; x.L = L;
+    x.nx = p.nx; x.dt = dt; x.icdt = 1.0 / (kC * dt); x.idt = 1.0 / dt; x.h = p.h; x.ihf = p.ihf;
+    x.L = L;
     x.a_cell = nullptr; x.s_cell = nullptr;
     return x;
 }

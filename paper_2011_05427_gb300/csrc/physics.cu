@@ -351,39 +351,69 @@ __host__ __device__ inline void group_ratios(double T, double ea, double eb, con
     Rr = Ns / Ds;
 }
 
-__device__ inline void opacity_body(const OpacityArgs &a, long idx, const Mx &mx)
+// Per-cell terms of a block's 32 cells, staged once by the block's first row of threads:
+// T, 1/T, 1/T^3 and the table interval / local coordinate of ln T (m < 0: outside).
+struct CellTerms {
+    double T[32], iT[32], iT3[32], t[32];
+    int m[32];
+};
+
+__device__ inline void stage_cells(const OpacityArgs &a, int i0, CellTerms &ct)
 {
-    const int nx = a.nx, G = a.G;
-    if (idx >= (long)G * nx) return;
-    int g = (int)(idx / nx);
-    int i = (int)(idx - (long)g * nx);
-    const double Ti = a.T[i];
-    const double iT = rcp64(Ti);
+    if (threadIdx.y == 0) {
+        const int tx = threadIdx.x, i = i0 + tx;
+        if (i < a.nx) {
+            const double Ti = a.T[i];
+            const double iT = rcp64(Ti);
+            ct.T[tx] = Ti;
+            ct.iT[tx] = iT;
+            ct.iT3[tx] = iT * iT * iT;
+            int m = -1;
+            double t = 0.0;
+            if (a.otab) {
+                const double z = (log(Ti) - kTabU0) * (1.0 / kTabH);
+                if (z >= 0.0 && z < (double)kTabNI) {
+                    m = min((int)z, kTabNI - 1);
+                    t = 2.0 * (z - (double)m) - 1.0;
+                }
+            }
+            ct.m[tx] = m;
+            ct.t[tx] = t;
+        }
+    }
+    __syncthreads();
+}
+
+// cell i0 + threadIdx.x, group g0 + threadIdx.y; outputs [G][nx] (cells contiguous)
+__device__ inline void opacity_body(const OpacityArgs &a, int i0, int g0, const CellTerms &ct,
+                                    const Mx &mx)
+{
+    const int tx = threadIdx.x;
+    const int i = i0 + tx, g = g0 + threadIdx.y;
+    if (i >= a.nx || g >= a.G) return;
+    const size_t idx = (size_t)g * a.nx + i;
+    const double Ti = ct.T[tx], iT = ct.iT[tx], iT3 = ct.iT3[tx];
     const double xa = a.edges[g] * iT;
     const double eb = a.edges[g + 1];
     const bool binf = isinf(eb);
-    double T3 = Ti * Ti * Ti;
-    double k27 = 27.0 * a.s;
-    const double iT3 = rcp64(T3);
-    double sg, sR, om;
-    const double u = a.otab ? log(Ti) : 0.0;
-    const double z = (u - kTabU0) * (1.0 / kTabH);
-    if (a.otab && z >= 0.0 && z < (double)kTabNI) {
-        // tabulated: the two ratios as Chebyshev series in ln T on the cell's interval
-        const int m = min((int)z, kTabNI - 1);
-        const double t = 2.0 * (z - (double)m) - 1.0;
-        const double *c = a.otab + ((size_t)g * kTabNI + m) * 2 * kTabNC;
+    const double k27 = 27.0 * a.s;
+    double sg, sR, em;
+    const int m = ct.m[tx];
+    if (m >= 0) {
+        // tabulated: three Chebyshev series in ln T on the cell's interval
+        const double t = ct.t[tx];
+        const double *c = a.otab + ((size_t)g * kTabNI + m) * kTabNF * kTabNC;
         sg = k27 * clenshaw(c, t) * iT3;
         sR = k27 * clenshaw(c + kTabNC, t) * iT3;
-        om = binf ? 1.0 : -expm1(-(eb - a.edges[g]) * iT);
+        em = k27 * kCB * Ti * mx.ex(clenshaw(c + 2 * kTabNC, t) - xa);
     } else {
         const double xb = binf ? 0.0 : eb * iT;
-        double dPs, Ns, Ds;
+        double dPs, Ns, Ds, om;
         group_integrals(xa, xb, binf, c_ser, mx, dPs, Ns, Ds, om);
         sg = k27 * om * iT3 * rcp64(dPs);
         sR = k27 * Ns * iT3 * rcp64(Ds);
+        em = k27 * kCB * Ti * mx.ex(-xa) * om;
     }
-    const double em = k27 * kCB * Ti * mx.ex(-xa) * om;
     a.sigE[idx] = sg;
     a.emis[idx] = em;
     a.sigR[idx] = sR;
@@ -397,28 +427,34 @@ __device__ inline void opacity_body(const OpacityArgs &a, long idx, const Mx &mx
 // the 2^(j/32) table of texp in shared memory (lanes index it with different j)
 __device__ inline Mx stage_exp_table(double *s_e2)
 {
-    if (threadIdx.x < 32) s_e2[threadIdx.x] = c_ser.e2[threadIdx.x];
+    if (threadIdx.y == 0 && threadIdx.x < 32) s_e2[threadIdx.x] = c_ser.e2[threadIdx.x];
     __syncthreads();
     return Mx{s_e2, ExpConsts{c_ser.einv, c_ser.eL1, c_ser.eL2}};
 }
 
+// block (32 cells, 8 groups); grid (ceil(nx / 32), ceil(G / 8))
 __global__ void __launch_bounds__(256) k_opacity(OpacityArgs a)
 {
     __shared__ double s_e2[32];
+    __shared__ CellTerms ct;
     const Mx mx = stage_exp_table(s_e2);
-    opacity_body(a, (long)blockIdx.x * blockDim.x + threadIdx.x, mx);
+    stage_cells(a, blockIdx.x * 32, ct);
+    opacity_body(a, blockIdx.x * 32, blockIdx.y * 8, ct, mx);
 }
 
 __global__ void __launch_bounds__(256) k_opacity_b(const int *__restrict__ meta, int N,
                                                    const OpacityArgs *__restrict__ xs)
 {
     __shared__ double s_e2[32];
+    __shared__ CellTerms ct;
     const Mx mx = stage_exp_table(s_e2);
     for (int b = blockIdx.x;; b += gridDim.x) {
         int s, bx, by;
         if (!bdecode(meta, N, b, s, bx, by)) break;
         const OpacityArgs a = xs[s];
-        opacity_body(a, (long)bx * blockDim.x + threadIdx.x, mx);
+        stage_cells(a, bx * 32, ct);
+        opacity_body(a, bx * 32, by * 8, ct, mx);
+        __syncthreads();   // the cell terms are restaged by the next work item
     }
 }
 
@@ -452,23 +488,28 @@ __global__ void k_otab_build(int G, const double *__restrict__ edges, double *__
     if (id >= G * kTabNI) return;
     const int g = id / kTabNI, m = id - g * kTabNI;
     const double umid = kTabU0 + kTabH * (m + 0.5);
-    double fa[kTabNC], fr[kTabNC];
+    double fa[kTabNC], fr[kTabNC], fe[kTabNC];
+    const bool binf = isinf(edges[g + 1]);
     for (int j = 0; j < kTabNC; ++j) {
         const double th = kPi * (j + 0.5) / kTabNC;
         const double T = exp(umid + 0.5 * kTabH * cos(th));
         group_ratios(T, edges[g], edges[g + 1], mx, fa[j], fr[j]);
+        // emission factor: e_g = 27 s C_B T e^{-xa} (1 - e^{-w}), w = (nu_b - nu_a)/T
+        fe[j] = binf ? 0.0 : log(-expm1(-(edges[g + 1] - edges[g]) / T));
     }
-    double *c = tab + (size_t)id * 2 * kTabNC;
+    double *c = tab + (size_t)id * kTabNF * kTabNC;
     for (int k = 0; k < kTabNC; ++k) {
-        double sa = 0.0, sr = 0.0;
+        double sa = 0.0, sr = 0.0, se = 0.0;
         for (int j = 0; j < kTabNC; ++j) {
             const double ck = cos(kPi * k * (j + 0.5) / kTabNC);
             sa = fma(fa[j], ck, sa);
             sr = fma(fr[j], ck, sr);
+            se = fma(fe[j], ck, se);
         }
         const double sc = (k == 0 ? 1.0 : 2.0) / kTabNC;
         c[k] = sa * sc;
         c[kTabNC + k] = sr * sc;
+        c[2 * kTabNC + k] = se * sc;
     }
 }
 
@@ -494,20 +535,21 @@ OpacityArgs make_opacity_args(const Problem &p, const double *T, double *sigE, d
     return a;
 }
 
-int opacity_blocks(const Problem &p) { return (int)(((long)p.G * p.nx + 255) / 256); }
+int opacity_gx(const Problem &p) { return (p.nx + 31) / 32; }
+int opacity_blocks(const Problem &p) { return opacity_gx(p) * ((p.G + 7) / 8); }
 
 cudaError_t launch_opacity(const Problem &p, const double *T, double *sigE, double *emis,
                            double *sigR, float *sig32, float *emis32, double dt)
 {
     const OpacityArgs a = make_opacity_args(p, T, sigE, emis, sigR, sig32, emis32, dt);
-    k_opacity<<<(unsigned)opacity_blocks(p), 256, 0, p.stream>>>(a);
+    k_opacity<<<dim3(opacity_gx(p), (p.G + 7) / 8), dim3(32, 8), 0, p.stream>>>(a);
     return cudaGetLastError();
 }
 
 cudaError_t launch_opacity_b(const int *meta, int N, const OpacityArgs *xs, int grid,
                              cudaStream_t st)
 {
-    k_opacity_b<<<grid, 256, 0, st>>>(meta, N, xs);
+    k_opacity_b<<<grid, dim3(32, 8), 0, st>>>(meta, N, xs);
     return cudaGetLastError();
 }
 
