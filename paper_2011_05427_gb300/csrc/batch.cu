@@ -253,7 +253,8 @@ void build_stage(trt_batch *b, int id, double dt, int cycle_type)
                                                 x->psi_exit, x->f, x->fb0, x->fbX, x->C0, x->CX,
                                                 b->D);
             const int ntile = p.M / b->D;
-            B.set(sg.ops[isw], s, a, ntile * (p.ldG / 32), ntile);
+            B.set(sg.ops[isw], s, a, ntile * sweep_group_tiles(b->precision, b->shape, p.ldG),
+                  ntile);
             p.sweep_D = b->D;
             const FinalizeArgs fa = make_finalize_args(p, a);
             B.set(sg.ops[isw + 1], s, fa, finalize_blocks(p), finalize_blocks(p));

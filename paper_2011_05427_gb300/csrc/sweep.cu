@@ -294,6 +294,214 @@ __global__ void __launch_bounds__(256) k_sweep_b(const int *__restrict__ meta, i
     }
 }
 
+// FP32 sweep with two groups per lane (a warp covers 64 groups; float2 loads and stores;
+// two independent recurrences per thread), for the step's pre-scaled FP32 inputs
+// (sigma_t h/2, h e/2 of launch_opacity).  Same arithmetic per (group, direction) as
+// sweep_body; half the per-update address, copy and loop instructions, which bound the
+// one-group form (issue-limited at ~13 warps per SM).
+constexpr int kP2 = 66;   // padded row (64 groups) of the strip tables, 8-byte aligned
+
+template <int kStrip, int NS>
+struct Sweep2Smem {
+    size_t itile, rawS, rawE, skap, ps, swt, total;
+    __host__ __device__ Sweep2Smem(int D)
+    {
+        auto al = [](size_t x) { return (x + 15) / 16 * 16; };
+        size_t o = 0;
+        itile = o; o = al(o + sizeof(float) * NS * (size_t)D * kStrip * 2 * 64);
+        rawS = o;  o = al(o + sizeof(float) * NS * kStrip * kP2);
+        rawE = o;  o = al(o + sizeof(float) * NS * kStrip * kP2);
+        skap = o;  o = al(o + sizeof(float) * kStrip);
+        ps = o;    o = al(o + sizeof(float) * (size_t)D * kStrip * kP2);
+        swt = o;   o = al(o + sizeof(float) * 2 * D);
+        total = o;
+    }
+};
+
+template <int kStrip, int NS>
+__device__ void sweep2_body(const SweepArgs &a, int dtile, int gt)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int D = a.D;
+    const Sweep2Smem<kStrip, NS> L(D);
+    float *itile = reinterpret_cast<float *>(smem_raw + L.itile);   // [NS][D][S][2][64]
+    float *rawS = reinterpret_cast<float *>(smem_raw + L.rawS);     // [NS][S][66] sigma_t h/2
+    float *rawE = reinterpret_cast<float *>(smem_raw + L.rawE);     // [NS][S][66] h e/2
+    float *skap = reinterpret_cast<float *>(smem_raw + L.skap);     // [S] h/(2 c dt)
+    float *ps = reinterpret_cast<float *>(smem_raw + L.ps);         // [D][S][66] psi_L + psi_R
+    float *swt = reinterpret_cast<float *>(smem_raw + L.swt);       // [D] w/2
+    float *swm = swt + D;                                           // [D] w mu^2/2
+
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int nthr = blockDim.x;
+    const int tid = threadIdx.x;
+    const int nx = a.nx, G = a.G, ldG = a.ldG;
+    const int g0 = gt * 64 + 2 * lane;   // this lane's groups g0, g0 + 1
+    const bool lv = g0 < ldG;            // inside the padded row (ldG is a multiple of 32)
+    const bool pos = dtile < a.N / D;
+    const int m = dtile * D + warp;
+
+    const float *__restrict__ Iold = reinterpret_cast<const float *>(a.I_old);
+    float *__restrict__ Inew = reinterpret_cast<float *>(a.I_new);
+    const float *__restrict__ sigE = reinterpret_cast<const float *>(a.sigE);
+    const float *__restrict__ emis = reinterpret_cast<const float *>(a.emis);
+    float *part = reinterpret_cast<float *>(a.part);
+
+    const double mu_d = a.mu[m];
+    const float am = (float)fabs(mu_d);
+    const float b = (float)(0.5 * fabs(mu_d));
+    const float bb = b * b;
+    if (lane == 0) {
+        swt[warp] = (float)(0.5 * a.w[m]);
+        swm[warp] = (float)(0.5 * a.w[m] * mu_d * mu_d);
+    }
+    const double *Iin = pos ? a.Iin0 : a.IinX;
+    float psi0 = (g0 < G) ? (float)Iin[g0] : 0.f;
+    float psi1 = (g0 + 1 < G) ? (float)Iin[g0 + 1] : 0.f;
+
+    const int nstrip = (nx + kStrip - 1) / kStrip;
+    const size_t dstride = (size_t)2 * ldG;
+    const float *Iold_m = Iold + (size_t)m * nx * dstride + g0;
+    float *Inew_m = Inew + (size_t)m * nx * dstride + g0;
+
+    auto range = [&](int st, int &c0, int &ns) {
+        if (pos) {
+            c0 = st * kStrip;
+            ns = min(kStrip, nx - c0);
+        } else {
+            const int c1 = nx - st * kStrip;
+            c0 = max(c1 - kStrip, 0);
+            ns = c1 - c0;
+        }
+    };
+    auto prefetch = [&](int st, int bf) {
+        int c0, ns;
+        range(st, c0, ns);
+        float *it = itile + ((size_t)bf * D + warp) * kStrip * 128 + 2 * lane;
+        for (int cc = 0; cc < ns; ++cc) {
+            if (lv) {
+                cp_async<8>(it + cc * 128, Iold_m + (size_t)(c0 + cc) * dstride);
+                cp_async<8>(it + cc * 128 + 64, Iold_m + (size_t)(c0 + cc) * dstride + ldG);
+            } else {
+                *reinterpret_cast<float2 *>(it + cc * 128) = make_float2(0.f, 0.f);
+                *reinterpret_cast<float2 *>(it + cc * 128 + 64) = make_float2(0.f, 0.f);
+            }
+        }
+        float *rs = rawS + bf * kStrip * kP2, *re = rawE + bf * kStrip * kP2;
+        for (int idx = tid; idx < 64 * kStrip; idx += nthr) {
+            const int gl = idx / kStrip, cc = idx - gl * kStrip;
+            const int gg = gt * 64 + gl;
+            if (cc < ns && gg < G) {
+                cp_async<4>(rs + cc * kP2 + gl, sigE + (size_t)gg * nx + c0 + cc);
+                cp_async<4>(re + cc * kP2 + gl, emis + (size_t)gg * nx + c0 + cc);
+            } else {
+                rs[cc * kP2 + gl] = 0.f;
+                re[cc * kP2 + gl] = 0.f;
+            }
+        }
+        cp_commit();
+    };
+
+    for (int k = 0; k < NS - 1; ++k) {
+        if (k < nstrip)
+            prefetch(k, k);
+        else
+            cp_commit();
+    }
+    for (int st = 0; st < nstrip; ++st) {
+        const int bf = st % NS;
+        int c0, ns;
+        range(st, c0, ns);
+        if (st + NS - 1 < nstrip)
+            prefetch(st + NS - 1, (st + NS - 1) % NS);
+        else
+            cp_commit();
+        cp_wait<NS - 1>();
+        if (tid < ns) skap[tid] = (float)(0.5 * a.h[c0 + tid] * a.icdt);
+        __syncthreads();
+        const float *tth = rawS + bf * kStrip * kP2 + 2 * lane;
+        const float *tq = rawE + bf * kStrip * kP2 + 2 * lane;
+        const float *it = itile + ((size_t)bf * D + warp) * kStrip * 128 + 2 * lane;
+        float *psw = ps + warp * kStrip * kP2 + 2 * lane;
+#pragma unroll 4
+        for (int kk = 0; kk < ns; ++kk) {
+            const int cc = pos ? kk : ns - 1 - kk;
+            const int i = c0 + cc;
+            const float2 IL = *reinterpret_cast<const float2 *>(it + cc * 128);
+            const float2 IR = *reinterpret_cast<const float2 *>(it + cc * 128 + 64);
+            const float2 th = *reinterpret_cast<const float2 *>(tth + cc * kP2);
+            const float2 q = *reinterpret_cast<const float2 *>(tq + cc * kP2);
+            const float kap = skap[cc];
+            const float aa0 = b + th.x, aa1 = b + th.y;
+            const float inv0 = __frcp_rn(aa0 * aa0 + bb), inv1 = __frcp_rn(aa1 * aa1 + bb);
+            float pL0, pR0, pL1, pR1;
+            if (pos) {
+                const float rL0 = q.x + kap * IL.x + am * psi0, rR0 = q.x + kap * IR.x;
+                const float rL1 = q.y + kap * IL.y + am * psi1, rR1 = q.y + kap * IR.y;
+                pL0 = (aa0 * rL0 - b * rR0) * inv0;
+                pR0 = (aa0 * rR0 + b * rL0) * inv0;
+                pL1 = (aa1 * rL1 - b * rR1) * inv1;
+                pR1 = (aa1 * rR1 + b * rL1) * inv1;
+                psi0 = pR0;
+                psi1 = pR1;
+            } else {
+                const float rR0 = q.x + kap * IR.x + am * psi0, rL0 = q.x + kap * IL.x;
+                const float rR1 = q.y + kap * IR.y + am * psi1, rL1 = q.y + kap * IL.y;
+                pR0 = (aa0 * rR0 - b * rL0) * inv0;
+                pL0 = (aa0 * rL0 + b * rR0) * inv0;
+                pR1 = (aa1 * rR1 - b * rL1) * inv1;
+                pL1 = (aa1 * rL1 + b * rR1) * inv1;
+                psi0 = pL0;
+                psi1 = pL1;
+            }
+            if (lv) {
+                *reinterpret_cast<float2 *>(Inew_m + (size_t)i * dstride) = make_float2(pL0, pL1);
+                *reinterpret_cast<float2 *>(Inew_m + (size_t)i * dstride + ldG) = make_float2(pR0, pR1);
+            }
+            *reinterpret_cast<float2 *>(psw + cc * kP2) = make_float2(pL0 + pR0, pL1 + pR1);
+        }
+        __syncthreads();
+        for (int idx = tid; idx < 64 * kStrip; idx += nthr) {
+            const int gl = idx / kStrip, cc = idx - gl * kStrip;
+            const int gg = gt * 64 + gl;
+            if (cc < ns && gg < G) {
+                Acc<float> s0, s2;
+                for (int d = 0; d < D; ++d) {
+                    const float v = ps[(d * kStrip + cc) * kP2 + gl];
+                    s0.add(swt[d] * v);
+                    s2.add(swm[d] * v);
+                }
+                const size_t o = ((size_t)(dtile * 2 + 0) * G + gg) * nx + c0 + cc;
+                part[o] = s0.s;
+                part[o + (size_t)G * nx] = s2.s;
+            }
+        }
+    }
+    if (lv)
+        *reinterpret_cast<float2 *>(reinterpret_cast<float *>(a.psi_exit) + (size_t)m * ldG + g0) =
+            make_float2(psi0, psi1);
+}
+
+template <int kStrip, int NS>
+__global__ void __launch_bounds__(256) k_sweep2(SweepArgs a)
+{
+    sweep2_body<kStrip, NS>(a, blockIdx.x, blockIdx.y);
+}
+
+template <int kStrip, int NS>
+__global__ void __launch_bounds__(256) k_sweep2_b(const int *__restrict__ meta, int N,
+                                                  const SweepArgs *__restrict__ xs)
+{
+    for (int b = blockIdx.x;; b += gridDim.x) {
+        int s, bx, by;
+        if (!bdecode(meta, N, b, s, bx, by)) break;
+        const SweepArgs a = xs[s];
+        sweep2_body<kStrip, NS>(a, bx, by);
+        __syncthreads();
+    }
+}
+
 // f_g = sum_t A2 / sum_t A0 per (group, cell), in R; boundary factors per group in FP64.
 // Blocks [0, nb_cell) take one (group, cell) per thread; the blocks after them take one
 // group per warp for the boundary factors: lanes stride over the directions and the four
@@ -380,10 +588,11 @@ __global__ void k_sweep_finalize_b(const int *__restrict__ meta, int N,
 // (16, 3) 0.299 (a third buffer costs a resident CTA per SM); FP64 (8, 2) 1.26 ms,
 // (16, 2) 1.37, (8, 3) 1.37.
 struct Shape {
-    int S, NS;
+    int S, NS, V;   // strip cells, strip buffers, groups per lane
 };
-constexpr Shape kShapes32[] = {{16, 2}, {16, 3}, {16, 4}, {8, 4}, {8, 6}, {32, 2}};
-constexpr Shape kShapes64[] = {{8, 2}, {16, 2}, {8, 3}};
+constexpr Shape kShapes32[] = {{16, 2, 1}, {16, 3, 1}, {16, 4, 1}, {8, 4, 1}, {8, 6, 1},
+                               {32, 2, 1}, {16, 2, 2}, {8, 2, 2}, {8, 3, 2}, {8, 4, 2}};
+constexpr Shape kShapes64[] = {{8, 2, 1}, {16, 2, 1}, {8, 3, 1}};
 
 // largest power of two <= cap dividing N: the direction-tile height D_min that the
 // workspace's partial-moment scratch is sized for; D may be D_min or 2 D_min (<= 8)
@@ -419,11 +628,44 @@ cudaError_t launch_shape(const SweepArgs *a, int M, int ldG, int D, const int *m
     return cudaGetLastError();
 }
 
+template <int S, int NS>
+cudaError_t launch_shape2(const SweepArgs *a, int M, int ldG, int D, const int *meta, int N,
+                          const SweepArgs *xs, int grid, cudaStream_t st)
+{
+    const size_t sm = Sweep2Smem<S, NS>(D).total;
+    if (sm > 227 * 1024) return cudaErrorInvalidConfiguration;
+    if (a) {
+        cudaError_t e = cudaFuncSetAttribute(k_sweep2<S, NS>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+        k_sweep2<S, NS><<<dim3(M / D, (ldG + 63) / 64), 32 * D, sm, st>>>(*a);
+    } else {
+        cudaError_t e = cudaFuncSetAttribute(k_sweep2_b<S, NS>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+        k_sweep2_b<S, NS><<<grid, 32 * D, sm, st>>>(meta, N, xs);
+    }
+    return cudaGetLastError();
+}
+
 template <typename R, typename SR>
 cudaError_t dispatch_shape(int shape, const SweepArgs *a, int M, int ldG, int D, const int *meta,
                            int N, const SweepArgs *xs, int grid, cudaStream_t st)
 {
+    // two groups per lane: FP32 with pre-scaled FP32 inputs only; the FP32 sweep with FP64
+    // inputs takes the one-group shape of the same strip
+    if (sizeof(R) == 4 && sizeof(SR) == 4) {
+        switch (shape) {
+        case 6: return launch_shape2<16, 2>(a, M, ldG, D, meta, N, xs, grid, st);
+        case 7: return launch_shape2<8, 2>(a, M, ldG, D, meta, N, xs, grid, st);
+        case 8: return launch_shape2<8, 3>(a, M, ldG, D, meta, N, xs, grid, st);
+        case 9: return launch_shape2<8, 4>(a, M, ldG, D, meta, N, xs, grid, st);
+        default: break;
+        }
+    }
     if (sizeof(R) == 4) {
+        if (shape == 6) shape = 0;
+        if (shape == 7 || shape == 8 || shape == 9) shape = 3;
         switch (shape) {
         case 1: return launch_shape<R, SR, 16, 3>(a, M, ldG, D, meta, N, xs, grid, st);
         case 2: return launch_shape<R, SR, 16, 4>(a, M, ldG, D, meta, N, xs, grid, st);
@@ -470,6 +712,12 @@ void sweep_shape_info(int precision, int shape, int *S, int *NS)
     const Shape sh = sweep_fp32(precision) ? kShapes32[shape] : kShapes64[shape];
     *S = sh.S;
     *NS = sh.NS;
+}
+
+int sweep_group_tiles(int precision, int shape, int ldG)
+{
+    const Shape sh = sweep_fp32(precision) ? kShapes32[shape] : kShapes64[shape];
+    return sh.V == 2 ? (ldG + 63) / 64 : ldG / 32;
 }
 
 int sweep_D_candidates(const Problem &p, int *D)

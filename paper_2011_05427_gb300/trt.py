@@ -518,7 +518,7 @@ class Batch:
         best = None
         Ds = [D for D in (8, 4, 2) if all(self.slab(s).N % D == 0 for s in range(self.n))
               and all(D >= min(4, self.slab(s).N & -self.slab(s).N) for s in range(self.n))]
-        nshape = 6 if self.precision & TRT_SWEEP_FP32 else 3
+        nshape = lib().trt_sweep_shapes(self.slab(0).h)
         for D in Ds:
             for sh in range(nshape):
                 self.set_tile(D, sh)

@@ -168,3 +168,20 @@ def test_mixed_precision_vs_fp64_oracle(trt, orc, name, cfg, cycle, lmax, prec):
     print(f"{name} {prec}: vs FP64 oracle: T {worst[0]:.2e}, E_g (energy-weighted) {worst[1]:.2e}")
     tol = MIXED_TOL[prec]
     assert worst[0] < tol and worst[1] < tol
+
+
+@pytest.mark.parametrize("shape", [0, 6, 7, 8, 9])
+def test_fp32_sweep_shapes_in_steps(trt, orc, shape):
+    """Every FP32 sweep shape that the step uses with its pre-scaled FP32 inputs (6-9: two
+    groups per lane) against the FP64 oracle after fixed-iteration steps; 70 groups leave
+    a partial 64-group tile, 45 cells a ragged last strip."""
+    cfg = W.scaled(W.fc_small(), 45, 8, 70, levels=[70, 14, 1])
+    s, o = pair(trt, orc, cfg, precision="sweep32")
+    s.set_sweep_tile(4, shape)
+    worst = 0.0
+    for step in range(2):
+        s.step(cfg.dt, "W", 2, -1.0, max_outer=3)
+        o.step(cfg.dt, "W", 2, -1.0, max_outer=3)
+        eT, eE, _ = errors(s.moments(), o.state())
+        worst = max(worst, eT, eE)
+    assert worst < MIXED_TOL["sweep32"], worst
