@@ -73,6 +73,13 @@ int trt_mlp_refresh(const float *params, void *w16, void *stream);
 int trt_mlp_forward(int rows, const float *x, const float *params, const void *w16,
                     void *scratch, size_t scratch_bytes, float *y, void *stream);
 
+/* Inference in one persistent kernel (one CTA per SM, 256 rows per iteration, both hidden
+ * layers on the tensor cores with the activations kept in shared memory and the weights
+ * streamed in 64-wide K chunks); same arithmetic and result as trt_mlp_forward up to the
+ * order of the FP32 accumulation.  Needs no scratch. */
+int trt_mlp_forward_fused(int rows, const float *x, const float *params, const void *w16,
+                          float *y, void *stream);
+
 /* Loss L = (1/rows) sum_r (y_r - t_r)^2 and its gradient with respect to every parameter
  * (grad [TRT_MLP_NPARAM] FP32, overwritten; *loss a device float).  rows a multiple of
  * 128.  The backward pass rounds the layer gradients to BF16 before each tensor-core

@@ -423,8 +423,8 @@ int trt_step(trt_handle *h, double dt, const trt_cycle *cyc, trt_stats *stats)
         const int rows = G * nx;
         int rc = trt_mlp_features(nx, G, h->T, h->sigE, h->Eg_old, h->Ephase, h->mlp_x, p.stream);
         if (rc == TRT_OK)
-            rc = trt_mlp_forward(rows, h->mlp_x, h->mlp_params, h->mlp_w16, h->mlp_scratch,
-                                 h->mlp_scratch_bytes, h->mlp_y, p.stream);
+            rc = trt_mlp_forward_fused(rows, h->mlp_x, h->mlp_params, h->mlp_w16, h->mlp_y,
+                                       p.stream);
         if (rc != TRT_OK) return fail(h, rc, "closure: MLP inference failed");
         CK(launch_f_from_mlp(p, h->mlp_y, h->f));
         nk += 6;

@@ -12,6 +12,7 @@
 // the stage's mbarrier, which releases the stage for the chunk after next.  The 128 x 256
 // FP32 accumulator lives in 256 tensor-memory columns; in the epilogue thread t owns row
 // t (tensor-memory lane t) and reads its 256 values 32 at a time with tcgen05.ld.
+#include <algorithm>
 #include <cuda_bf16.h>
 #include <stdint.h>
 #include "common.cuh"
@@ -335,6 +336,217 @@ __global__ void __launch_bounds__(128) k_gemm(int M, int N, int K, const bf16 *_
     }
 }
 
+// ---- fused inference: the whole network in one persistent kernel ----
+// One CTA per SM; per iteration 256 rows as two 128-row tiles.  Layer 1 (3 inputs) on CUDA
+// cores writes both tiles' h1 (BF16) into shared memory in the K-major core-matrix layout;
+// the two 256 x 256 layers run on tcgen05 with the two tiles' 128 x 256 FP32 accumulators
+// in all 512 tensor-memory columns; their weights stream through a two-slot ring of 64-wide
+// K chunks (32 KB each) shared by both tiles; the ReLU epilogue of layer 2 writes h2 back
+// over h1; the epilogue of layer 3 folds the sigmoid head.  Activations never leave shared
+// memory.  Chunk q of the weight stream (layer (q / 4) % 2, K chunk q % 4) sits in slot
+// q % 3; its MMAs commit to the slot's mbarrier; chunk q + 2 is copied once the MMAs of
+// chunk q - 1 (same slot) have completed, so two copies are in flight while the MMAs of
+// chunk q run.
+constexpr int FA_BYTES = 128 * 256 * 2;   // one activation tile
+constexpr int FW_BYTES = 256 * 64 * 2;    // one weight chunk
+constexpr int F_SLOTS = 3;
+constexpr int F_SMEM = 2 * FA_BYTES + F_SLOTS * FW_BYTES + 256;   // 229,632 bytes
+constexpr uint32_t FA_SBO = 4096;         // activation tiles: 32 K groups per row group
+
+__global__ void __launch_bounds__(256, 1) k_mlp_fused(int rows, const float *__restrict__ x,
+                                                      const float *__restrict__ P,
+                                                      const bf16 *__restrict__ W2,
+                                                      const bf16 *__restrict__ W3,
+                                                      float *__restrict__ y)
+{
+    extern __shared__ __align__(1024) unsigned char sm[];
+    unsigned char *sA0 = sm, *sA1 = sm + FA_BYTES;
+    unsigned char *sW = sm + 2 * FA_BYTES;   // F_SLOTS weight chunks
+    uint64_t *bar = reinterpret_cast<uint64_t *>(sm + 2 * FA_BYTES + F_SLOTS * FW_BYTES);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(bar + F_SLOTS);
+    int *sfail = reinterpret_cast<int *>(tslot + 1);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int half = tid >> 7, r = tid & 127;   // tile and row (= tensor-memory lane)
+    const int ntiles = (rows + 255) / 256;
+    const int mine = (int)blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    const int Q = 8 * mine;   // weight chunks this CTA consumes
+
+    if (tid == 0) {
+        for (int k = 0; k < F_SLOTS; ++k) mbar_init(&bar[k], 1);
+        *sfail = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         su32(tslot)),
+                     "r"(512));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    tc_before();
+    __syncthreads();
+    tc_after();
+    const uint32_t tmem = *tslot;
+
+    // chunk q of the weight stream -> slot q % 3 (8 pieces of 16 bytes per thread)
+    int issued = 0;
+    auto load_chunk = [&](int q) {
+        const bf16 *W = ((q >> 2) & 1) ? W3 : W2;
+        const int c = q & 3;
+        unsigned char *dst = sW + (q % F_SLOTS) * FW_BYTES;
+        ++issued;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int p = tid + 256 * j;
+            const int r8 = p & 7, ki = (p >> 3) & 7, ni = p >> 6;
+            cp16(dst + p * 16, W + (size_t)(ni * 8 + r8) * 256 + c * 64 + ki * 8, 16u);
+        }
+        cp_commit();
+    };
+    int last_waited = -1;
+    bool ok = true;
+    auto wait_commit = [&](int q) {   // the MMAs of chunk q have completed
+        if (q <= last_waited) return;
+        if (!mbar_wait(&bar[q % F_SLOTS], (q / F_SLOTS) & 1)) *sfail = 1;
+        last_waited = q;
+    };
+    // A tile element (row, k) offset: core matrix (row / 8, k / 8), row % 8 at 16 bytes
+    auto a_off = [](int row, int k8) { return (row >> 3) * FA_SBO + k8 * 128 + (row & 7) * 16; };
+
+    if (Q > 0) load_chunk(0);
+    if (Q > 1) load_chunk(1);
+    int q = 0;
+    for (int it = 0; it < mine && ok; ++it) {
+        const int row0 = ((int)blockIdx.x + it * (int)gridDim.x) * 256;
+        unsigned char *myA = half ? sA1 : sA0;
+        // ---- layer 1: h1 = relu(W1 x + b1) for row row0 + tid ----
+        {
+            const int row = row0 + tid;
+            float x0 = 0.f, x1 = 0.f, x2 = 0.f;
+            const bool rv = row < rows;
+            if (rv) {
+                x0 = x[3 * row];
+                x1 = x[3 * row + 1];
+                x2 = x[3 * row + 2];
+            }
+            for (int k8 = 0; k8 < 32; ++k8) {
+                uint4 u;
+                bf16 *hb = reinterpret_cast<bf16 *>(&u);
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const int c = k8 * 8 + j;
+                    float a = __ldg(P + TRT_MLP_B1 + c);
+                    a = fmaf(__ldg(P + TRT_MLP_W1 + 3 * c), x0, a);
+                    a = fmaf(__ldg(P + TRT_MLP_W1 + 3 * c + 1), x1, a);
+                    a = fmaf(__ldg(P + TRT_MLP_W1 + 3 * c + 2), x2, a);
+                    hb[j] = __float2bfloat16_rn(rv ? fmaxf(a, 0.f) : 0.f);
+                }
+                *reinterpret_cast<uint4 *>(myA + a_off(r, k8)) = u;
+            }
+            fence_async_smem();
+        }
+        for (int layer = 0; layer < 2 && ok; ++layer) {
+            for (int c = 0; c < 4; ++c, ++q) {
+                if (issued > q + 1)    // chunk q has landed (chunk q + 1 may be in flight)
+                    cp_wait<1>();
+                else
+                    cp_wait<0>();
+                fence_async_smem();
+                tc_before();
+                __syncthreads();
+                if (*sfail) { ok = false; break; }
+                if (tid == 0) {
+                    tc_after();
+                    const uint32_t w0 = su32(sW + (q % F_SLOTS) * FW_BYTES);
+                    const uint32_t a0 = su32(sA0), a1 = su32(sA1);
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk) {
+                        const uint64_t bd = sdesc(w0 + kk * 2 * LBO, LBO, SBO);
+                        const uint32_t ka = (c * 8 + kk * 2) * 128;
+                        umma(tmem, sdesc(a0 + ka, LBO, FA_SBO), bd, (c | kk) != 0);
+                        umma(tmem + 256, sdesc(a1 + ka, LBO, FA_SBO), bd, (c | kk) != 0);
+                    }
+                    umma_commit(&bar[q % F_SLOTS]);
+                }
+                // slot (q + 2) % 3 held chunk q - 1: free once its MMAs are done
+                if (q >= 1) wait_commit(q - 1);
+                if (q + 2 < Q) load_chunk(q + 2);
+            }
+            if (!ok) break;
+            wait_commit(q - 1);   // all MMAs of this layer are done
+            ok = !__syncthreads_or(*sfail);
+            if (!ok) break;
+            tc_after();
+            const uint32_t tb = tmem + ((uint32_t)((warp & 3) * 32) << 16) + half * 256;
+            if (layer == 0) {
+                // ---- epilogue 2: h2 = relu(acc + b2) over h1 ----
+                for (int ch = 0; ch < 8; ++ch) {
+                    float v[32];
+                    tmem_ld32(tb + ch * 32, v);
+#pragma unroll
+                    for (int qq = 0; qq < 4; ++qq) {
+                        uint4 u;
+                        bf16 *hb = reinterpret_cast<bf16 *>(&u);
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) {
+                            const int col = ch * 32 + qq * 8 + j;
+                            hb[j] = __float2bfloat16_rn(fmaxf(v[qq * 8 + j] + __ldg(P + TRT_MLP_B2 + col), 0.f));
+                        }
+                        *reinterpret_cast<uint4 *>(myA + a_off(r, ch * 4 + qq)) = u;
+                    }
+                }
+                fence_async_smem();
+            } else {
+                // ---- epilogue 3 and the head: y = sigmoid(w4 . relu(acc + b3) + b4) ----
+                float dot = 0.f;
+                for (int ch = 0; ch < 8; ++ch) {
+                    float v[32];
+                    tmem_ld32(tb + ch * 32, v);
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        const int col = ch * 32 + j;
+                        dot = fmaf(fmaxf(v[j] + __ldg(P + TRT_MLP_B3 + col), 0.f),
+                                   __ldg(P + TRT_MLP_W4 + col), dot);
+                    }
+                }
+                const int row = row0 + tid;
+                if (row < rows) y[row] = 1.f / (1.f + __expf(-(dot + __ldg(P + TRT_MLP_B4))));
+            }
+        }
+    }
+    if (!ok) {
+        cp_wait<0>();
+        if (tid == 0) atomicExch(&g_mlp_err, TRT_ETIMEOUT);
+    }
+    tc_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+    }
+}
+
+int g_num_sms = 0;
+
+cudaError_t mlp_fused(int rows, const float *x, const float *P, const bf16 *W, float *y,
+                      cudaStream_t st)
+{
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t r = cudaFuncSetAttribute(k_mlp_fused,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, F_SMEM);
+        if (r != cudaSuccess) return r;
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
+        attr = true;
+    }
+    const int ntiles = (rows + 255) / 256;
+    const int grid = std::max(1, std::min(ntiles, g_num_sms > 0 ? g_num_sms : 148));
+    k_mlp_fused<<<grid, 256, F_SMEM, st>>>(rows, x, P, W, W + 65536, y);
+    return cudaGetLastError();
+}
+
 cudaError_t gemm(int M, int N, int K, const bf16 *A, const bf16 *B, const Epi &e,
                  cudaStream_t st)
 {
@@ -543,6 +755,16 @@ int trt_mlp_refresh(const float *params, void *w16, void *stream)
     k_refresh<<<512, 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(
         params, reinterpret_cast<bf16 *>(w16));
     return cudaGetLastError() == cudaSuccess ? TRT_OK : TRT_ECUDA;
+}
+
+int trt_mlp_forward_fused(int rows, const float *x, const float *params, const void *w16,
+                          float *y, void *stream)
+{
+    if (rows < 1 || !x || !params || !w16 || !y) return TRT_EINVAL;
+    return mlp_fused(rows, x, params, reinterpret_cast<const bf16 *>(w16), y,
+                     reinterpret_cast<cudaStream_t>(stream)) == cudaSuccess
+               ? TRT_OK
+               : TRT_ECUDA;
 }
 
 int trt_mlp_forward(int rows, const float *x, const float *params, const void *w16,

@@ -59,6 +59,16 @@ class MLP:
                                               y.data_ptr(), self._s))
         return y
 
+    def forward_fused(self, x):
+        """The same network in one persistent tensor-core kernel (no scratch)."""
+        t = self.torch
+        x = t.as_tensor(x, dtype=t.float32, device=self.device).contiguous()
+        rows = x.shape[0]
+        y = t.empty(rows, dtype=t.float32, device=self.device)
+        self._check(trt.lib().trt_mlp_forward_fused(rows, x.data_ptr(), self.params.data_ptr(),
+                                                    self.w16.data_ptr(), y.data_ptr(), self._s))
+        return y
+
     def grad(self, x, target):
         """(grad [NPARAM] FP32 device tensor, loss device tensor [1]); rows % 128 == 0."""
         t = self.torch

@@ -140,6 +140,8 @@ def lib():
     L.trt_mlp_refresh.argtypes = [_vp] * 3
     L.trt_mlp_forward.restype = ctypes.c_int
     L.trt_mlp_forward.argtypes = [ctypes.c_int] + [_vp] * 4 + [ctypes.c_size_t] + [_vp] * 2
+    L.trt_mlp_forward_fused.restype = ctypes.c_int
+    L.trt_mlp_forward_fused.argtypes = [ctypes.c_int] + [_vp] * 5
     L.trt_mlp_grad.restype = ctypes.c_int
     L.trt_mlp_grad.argtypes = [ctypes.c_int] + [_vp] * 5 + [ctypes.c_size_t] + [_vp] * 3
     L.trt_mlp_adam.restype = ctypes.c_int
@@ -183,7 +185,7 @@ EXPORTED = ("trt_workspace_bytes", "trt_create", "trt_step", "trt_moments", "trt
             "trt_k_sweep", "trt_k_lo_solve", "trt_k_restrict", "trt_k_grey_newton",
             "trt_sweep_time", "trt_autotune", "trt_sweep_shapes", "trt_set_sweep_tile",
             "trt_sweep_noalloc_scratch_bytes", "trt_sweep_noalloc", "trt_sweep_noalloc_error",
-            "trt_set_closure", "trt_gemm_bf16", "trt_mlp_scratch_bytes", "trt_mlp_refresh", "trt_mlp_forward",
+            "trt_set_closure", "trt_gemm_bf16", "trt_mlp_scratch_bytes", "trt_mlp_refresh", "trt_mlp_forward", "trt_mlp_forward_fused",
             "trt_mlp_grad", "trt_mlp_adam", "trt_mlp_features", "trt_mlp_status",
             "trt_batch_workspace_bytes", "trt_create_batch", "trt_step_batch",
             "trt_batch_slab", "trt_batch_set_tile", "trt_batch_sweep_time",

@@ -73,6 +73,28 @@ def test_mlp_forward_vs_oracle(env):
     assert mlp.MLP.status() == 0
 
 
+@pytest.mark.parametrize("rows", [1, 1000, 100000])
+def test_mlp_fused_forward(env, rows):
+    """The persistent fused kernel against the three-launch path (same arithmetic, same
+    accumulation order) and the oracle; 1000 rows end in a partial 256-row tile, 100000
+    rows give every CTA several tiles."""
+    torch, mlp = env
+    p = OM.init_params(61)
+    r = np.random.default_rng(62)
+    p = p + OM.pack({"b1": r.normal(0, 0.1, 256), "b2": r.normal(0, 0.1, 256),
+                     "b3": r.normal(0, 0.1, 256), "b4": -0.3})
+    p32 = p.astype(np.float32).astype(np.float64)
+    x = r.normal(0, 1, (rows, 3)).astype(np.float32)
+    net = mlp.MLP(p32)
+    yf = net.forward_fused(x).cpu().numpy()
+    y3 = net.forward(x).cpu().numpy()
+    assert np.max(np.abs(yf - y3)) < 1e-6
+    k = min(rows, 2000)
+    ref, _ = OM.forward(p32, x[:k].astype(np.float64), "bf16")
+    assert np.max(np.abs(yf[:k] - ref)) < 2e-3
+    assert mlp.MLP.status() == 0
+
+
 def test_mlp_gradient_vs_oracle(env):
     """Gradients of the tensor-core backward pass against the oracle's backward pass with
     BF16 rounding at the same points (norm-wise per parameter block)."""
