@@ -284,6 +284,12 @@ typedef struct {
  * source 2 emis) in the handle's LO precision; writes E, F, Eb0, EbX. */
 int trt_k_lo_solve(trt_handle *h, double dt, trt_level *lv);
 
+/* Test aid: the device arrays of the handle's own levels as the last step left them --
+ * which = 0: the fine grid (its sigR field holds cell values, fine = 1), 1: the coarse
+ * grid of the last coarse visit (n = its group count), 2: the grey grid (n = 1).  The
+ * pointers stay valid while the handle lives; the arrays change with every step. */
+int trt_level_view(trt_handle *h, int which, trt_level *out);
+
 /* Restrict level `src` (its coefficients and solution) onto `dst` (dst->n groups, uniform
  * map p -> p / (src->n / dst->n)): eqs. coeff-gamma, eta-gamma, coeff-Gamma, eta-Gamma
  * with the discrete compensation of eq. mloqd-d-gamma.  Writes every coefficient of dst

@@ -761,6 +761,19 @@ int trt_autotune(trt_handle *h, double dt, int reps, int *D, int *S, int *NS)
     return TRT_OK;
 }
 
+int trt_level_view(trt_handle *h, int which, trt_level *out)
+{
+    if (!h || !out || which < 0 || which > 2) return TRT_EINVAL;
+    const Level L = which == 0 ? fine_level(h) : which == 1 ? h->crs : h->grey;
+    out->n = L.n; out->fine = L.fine;
+    out->phi = L.phi; out->sig = L.sig; out->emis = L.emis; out->Eold = L.Eold;
+    out->Esum = L.Esum; out->sigR = L.sigR; out->etaR = L.etaR; out->etaL = L.etaL;
+    out->Fold = L.Fold; out->phib0 = L.phib0; out->phibX = L.phibX; out->C0 = L.C0;
+    out->CX = L.CX; out->Ein0 = L.Ein0; out->Fin0 = L.Fin0; out->EinX = L.EinX;
+    out->FinX = L.FinX; out->E = L.E; out->F = L.F; out->Eb0 = L.Eb0; out->EbX = L.EbX;
+    return TRT_OK;
+}
+
 int trt_k_lo_solve(trt_handle *h, double dt, trt_level *lv)
 {
     if (!h || !lv || !(dt > 0) || lv->n < 1) return TRT_EINVAL;

@@ -369,6 +369,10 @@ __global__ void __launch_bounds__(128) k_lo_solve_b(const int *__restrict__ meta
 }
 
 // ---------------------------------------------------------------------------------------
+// The weighted means below divide (no reciprocal-multiply): the weights (sums of E or of
+// boundary energies over a coarse group) reach the subnormal range in cold cells, where
+// 1/w overflows while a/w stays finite.
+//
 // restriction (eqs. coeff-gamma, g-notation, eta-gamma / coeff-Gamma, g2G-notation,
 // eta-Gamma, and the discrete compensation of eq. mloqd-d-gamma)
 // ---------------------------------------------------------------------------------------
@@ -454,7 +458,7 @@ __device__ void restrict_body(const RestrictCtx &x, int bx, int by)
         __syncthreads();
     }
     const double rn = (double)x.r;
-    const double sRP = (v[9] != 0.0) ? v[7] * rcp64(v[9]) : v[8] / rn;
+    const double sRP = (v[9] != 0.0) ? v[7] / v[9] : v[8] / rn;
     // ---- pass 2 (faces): xi, eta sums, side energies, Fold ----
     double u[kRV2];
 #pragma unroll
@@ -498,9 +502,8 @@ __device__ void restrict_body(const RestrictCtx &x, int bx, int by)
     const Level &T = x.T;
     if (i < nx) {
         size_t c = (size_t)P * nx + i;
-        const double i6 = (v[6] != 0.0) ? rcp64(v[6]) : 0.0, irn = 1.0 / rn;
-        (T.phi)[c] = (v[6] != 0.0) ? v[0] * i6 : v[1] * irn;
-        (T.sig)[c] = (v[6] != 0.0) ? v[2] * i6 : v[3] * irn;
+        (T.phi)[c] = (v[6] != 0.0) ? v[0] / v[6] : v[1] / rn;
+        (T.sig)[c] = (v[6] != 0.0) ? v[2] / v[6] : v[3] / rn;
         (T.emis)[c] = v[4];
         (T.Eold)[c] = v[5];
         T.Esum[c] = v[6];
@@ -509,8 +512,8 @@ __device__ void restrict_body(const RestrictCtx &x, int bx, int by)
         size_t f = (size_t)P * nf + i;
         double xi = u[0] + kC * (u[1] - u[2]);
         (T.sigR)[f] = sRP;
-        (T.etaR)[f] = (xi > 0.0 && u[3] != 0.0) ? xi * rcp64(kC * u[3]) : 0.0;
-        (T.etaL)[f] = (xi < 0.0 && u[4] != 0.0) ? -xi * rcp64(kC * u[4]) : 0.0;
+        (T.etaR)[f] = (xi > 0.0 && u[3] != 0.0) ? xi / (kC * u[3]) : 0.0;
+        (T.etaL)[f] = (xi < 0.0 && u[4] != 0.0) ? -xi / (kC * u[4]) : 0.0;
         (T.Fold)[f] = u[5];
     }
     if (i == 0 || i == nx) {
@@ -631,21 +634,20 @@ __device__ void restrict_final_body(const Restrict2Ctx &x, int bx, int by)
     const Level &T = x.T;
     if (i < nx) {
         const size_t c = (size_t)P * nx + i;
-        const double i6 = (v[6] != 0.0) ? rcp64(v[6]) : 0.0, irn = 1.0 / rn;
-        T.phi[c] = (v[6] != 0.0) ? v[0] * i6 : v[1] * irn;
-        T.sig[c] = (v[6] != 0.0) ? v[2] * i6 : v[3] * irn;
+        T.phi[c] = (v[6] != 0.0) ? v[0] / v[6] : v[1] / rn;
+        T.sig[c] = (v[6] != 0.0) ? v[2] / v[6] : v[3] / rn;
         T.emis[c] = v[4];
         T.Eold[c] = v[5];
         T.Esum[c] = v[6];
     }
     const double dxf = (i == 0) ? 0.5 * x.h[0] : (i == nx) ? 0.5 * x.h[nx - 1]
                                             : 0.5 * (x.h[i - 1] + x.h[i]);
-    const double sRP = (v[9] != 0.0) ? v[7] * rcp64(v[9]) : v[8] / rn;
+    const double sRP = (v[9] != 0.0) ? v[7] / v[9] : v[8] / rn;
     const double xi = dxf * (v[10] - sRP * v[11]) + kC * (v[12] - v[13]);
     const size_t f = (size_t)P * nf + i;
     T.sigR[f] = sRP;
-    T.etaR[f] = (xi > 0.0 && v[14] != 0.0) ? xi * rcp64(kC * v[14]) : 0.0;
-    T.etaL[f] = (xi < 0.0 && v[15] != 0.0) ? -xi * rcp64(kC * v[15]) : 0.0;
+    T.etaR[f] = (xi > 0.0 && v[14] != 0.0) ? xi / (kC * v[14]) : 0.0;
+    T.etaL[f] = (xi < 0.0 && v[15] != 0.0) ? -xi / (kC * v[15]) : 0.0;
     T.Fold[f] = v[16];
     if (i == 0 || i == nx) {
         const double phb = (v[19] != 0.0) ? v[17] / v[19] : v[18] / rn;

@@ -73,6 +73,17 @@ class trt_level(ctypes.Structure):
 
 
 _lib = None
+_rt = None
+
+
+def _cudart():
+    """The CUDA runtime library libtrt.so links against (for test-aid copies)."""
+    global _rt
+    if _rt is None:
+        _rt = ctypes.CDLL(os.path.join("/usr/local/cuda/lib64", "libcudart.so"))
+        _rt.cudaMemcpy.restype = ctypes.c_int
+        _rt.cudaMemcpy.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int]
+    return _rt
 
 
 def lib():
@@ -113,6 +124,8 @@ def lib():
     L.trt_k_sweep.argtypes = [_vp, ctypes.c_double] + [_vp] * 9
     L.trt_k_lo_solve.restype = ctypes.c_int
     L.trt_k_lo_solve.argtypes = [_vp, ctypes.c_double, ctypes.POINTER(trt_level)]
+    L.trt_level_view.restype = ctypes.c_int
+    L.trt_level_view.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(trt_level)]
     L.trt_k_restrict.restype = ctypes.c_int
     L.trt_k_restrict.argtypes = [_vp, ctypes.POINTER(trt_level), ctypes.POINTER(trt_level)]
     L.trt_k_grey_newton.restype = ctypes.c_int
@@ -185,7 +198,7 @@ EXPORTED = ("trt_workspace_bytes", "trt_create", "trt_step", "trt_moments", "trt
             "trt_k_sweep", "trt_k_lo_solve", "trt_k_restrict", "trt_k_grey_newton",
             "trt_sweep_time", "trt_autotune", "trt_sweep_shapes", "trt_set_sweep_tile",
             "trt_sweep_noalloc_scratch_bytes", "trt_sweep_noalloc", "trt_sweep_noalloc_error",
-            "trt_set_closure", "trt_gemm_bf16", "trt_mlp_scratch_bytes", "trt_mlp_refresh", "trt_mlp_forward", "trt_mlp_forward_fused",
+            "trt_set_closure", "trt_gemm_bf16", "trt_mlp_scratch_bytes", "trt_mlp_refresh", "trt_mlp_forward", "trt_mlp_forward_fused", "trt_level_view",
             "trt_mlp_grad", "trt_mlp_adam", "trt_mlp_features", "trt_mlp_status",
             "trt_batch_workspace_bytes", "trt_create_batch", "trt_step_batch",
             "trt_batch_slab", "trt_batch_set_tile", "trt_batch_sweep_time",
@@ -393,6 +406,30 @@ class Solver:
         self._check(lib().trt_set_closure(self.h, net.params.data_ptr(), net.w16.data_ptr(),
                                           sc.data_ptr(), sc.numel(), x.data_ptr(), y.data_ptr()))
         self._closure = (net, x, y, sc)   # keep the buffers alive
+
+    def level_view(self, which):
+        """Host copies of the handle's fine (0), coarse (1) or grey (2) level arrays."""
+        lv = trt_level()
+        self._check(lib().trt_level_view(self.h, int(which), ctypes.byref(lv)))
+        n, nx = lv.n, self.nx
+        shapes = dict(phi=(n, nx), sig=(n, nx), emis=(n, nx), Eold=(n, nx), Esum=(n, nx),
+                      sigR=(n, nx) if lv.fine else (n, nx + 1), etaR=(n, nx + 1),
+                      etaL=(n, nx + 1), Fold=(n, nx + 1), phib0=(n,), phibX=(n,), C0=(n,),
+                      CX=(n,), Ein0=(n,), Fin0=(n,), EinX=(n,), FinX=(n,), E=(n, nx),
+                      F=(n, nx + 1), Eb0=(n,), EbX=(n,))
+        out = {"n": n, "fine": lv.fine}
+        self.torch.cuda.synchronize(self.device)
+        rt = _cudart()
+        for k, shp in shapes.items():
+            ptr = ctypes.cast(getattr(lv, k), ctypes.c_void_p).value
+            if not ptr:
+                continue
+            a = np.empty(shp, np.float64)
+            if rt.cudaMemcpy(ctypes.c_void_p(a.ctypes.data), ctypes.c_void_p(ptr),
+                             ctypes.c_size_t(a.nbytes), 2) != 0:   # device to host
+                raise TRTError(TRT_ECUDA, "cudaMemcpy of a level array failed")
+            out[k] = a
+        return out
 
     def sweep_time(self, dt, reps=10) -> float:
         """ms per sweep of the step's own sweep configuration (state unchanged)."""

@@ -241,7 +241,7 @@ def oracle_level_solve(orc, h, dt, lv):
 
 
 @pytest.mark.parametrize("nx,ng", [(1, 3), (2, 5), (3, 4), (5, 9), (64, 7), (65, 33), (500, 40),
-                                   (1000, 3), (2048, 2)])
+                                   (1000, 3), (2048, 2), (520, 256)])
 def test_lo_solve_parity(trt, orc, nx, ng):
     r = W.rng(3000 + nx + ng)
     h = W.random_h(r, nx)
@@ -263,7 +263,9 @@ def test_lo_solve_parity(trt, orc, nx, ng):
                           (4, 4, True, 37, False), (64, 16, True, 500, False),
                           (256, 1, True, 500, False), (64, 16, False, 500, True),
                           (1024, 64, False, 500, True), (64, 4, False, 70, True),
-                          (1024, 1, False, 500, True), (512, 2, True, 129, False)])
+                          (1024, 1, False, 500, True), (512, 2, True, 129, False),
+                          (1024, 256, False, 520, True), (256, 1, True, 520, False),
+                          (256, 64, True, 1000, False), (64, 16, True, 520, False)])
 def test_restrict_parity(trt, orc, n_from, n_to, eta, nx, fine):
     r = W.rng(4000 + n_from + n_to + nx)
     h = W.random_h(r, nx)
@@ -291,6 +293,30 @@ def test_restrict_parity(trt, orc, n_from, n_to, eta, nx, fine):
         else:
             assert rel(got[k], ref[k]) < 1e-12, k
     assert rel(got["Esum"], Esum) < 1e-13
+
+
+@pytest.mark.parametrize("n_from,n_to", [(16, 4), (256, 1)])
+def test_restrict_subnormal_weights(trt, orc, n_from, n_to):
+    """Cold cells carry group energies far below DBL_MIN: the E-weighted means of the
+    restriction must stay the ratios the oracle forms (a reciprocal of a subnormal weight
+    overflows where the ratio does not)."""
+    nx = 40
+    r = W.rng(4500 + n_from)
+    h = W.random_h(r, nx)
+    lv = random_level(r, n_from, nx, eta=True)
+    sol = oracle_level_solve(orc, h, 2e-3, lv)
+    sol["E"][:, 25:] *= 1e-305            # cells 25.. : E of order 1e-306 .. 1e-309
+    sol["E"][: n_from // n_to, 30:] *= 1e-3   # and subnormal sums in the first coarse group
+    s = solver(trt, nx=nx, N=2, G=max(n_from, 3), h=h, levels=[max(n_from, 3), 1])
+    src = dict(lv)
+    src.update(sol)
+    got = {k: v.cpu().numpy() for k, v in s.k_restrict(src, n_to, fine=False).items()}
+    cmap = np.arange(n_from) // (n_from // n_to)
+    ref, Esum = orc.restrict(h, lv, sol, cmap, n_to)
+    for k in ("phi", "sig", "sigR"):
+        assert np.all(np.isfinite(got[k])), k
+        # subnormal products keep fewer significant bits: summation order shows at ~1e-12
+        assert rel(got[k], ref[k]) < 1e-9, k
 
 
 @pytest.mark.parametrize("nx,have_prev", [(1, 0), (30, 1), (500, 0), (1000, 1)])

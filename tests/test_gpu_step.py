@@ -116,6 +116,31 @@ def test_fc_1024_full_size_step(trt, orc):
     assert eT < 1e-10 and eE < 1e-10, (eT, eE)
 
 
+def test_fc_1024_full_size_step_fp32_sweeps(trt, orc):
+    """fc_1024 at full size with FP32 sweeps: one fixed-iteration step against the FP64
+    oracle, within the FP32-sweep bound."""
+    cfg = W.fc_1024("W")
+    s, o = pair(trt, orc, cfg, precision="sweep32")
+    st = s.step(cfg.dt, "W", 1, -1.0, max_outer=2)
+    so, c = o.step(cfg.dt, "W", 1, -1.0, max_outer=2)
+    assert st["status"] == 0 and so == 0
+    eT, eE, _ = errors(s.moments(), o.state())
+    assert eT < MIXED_TOL["sweep32"] and eE < MIXED_TOL["sweep32"], (eT, eE)
+
+
+def test_w_cycle_cold_cells_many_cells(trt, orc):
+    """520 cells, 1024 groups, one coarse grid of 256: the cold half of the slab holds group
+    energies below DBL_MIN, which the coarse-grid averages divide by.  One fixed-iteration
+    W-cycle phase against the oracle."""
+    cfg = W.scaled(W.fc_4096("W"), 520, 8, 1024, levels=[1024, 256, 1])
+    s, o = pair(trt, orc, cfg)
+    st = s.step(cfg.dt, "W", 1, -1.0, max_outer=1)
+    so, c = o.step(cfg.dt, "W", 1, -1.0, max_outer=1)
+    assert st["status"] == 0 and so == 0
+    eT, eE, _ = errors(s.moments(), o.state())
+    assert eT < 1e-10 and eE < 1e-10, (eT, eE)
+
+
 def test_edge_cases(trt, orc):
     """one cell; one group on [0, inf) with grids {1, 1}; one direction per half range."""
     for cfg in (W.scaled(W.fc_small(), 1, 4, 17, levels=[17, 1]),
