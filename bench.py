@@ -335,6 +335,53 @@ def closure_bench(local, ms_fp64, steps=10):
             "max_rel_T_closure_vs_plain": dT, "steps": steps}
 
 
+def fc4096_bench(local, steps=3):
+    """fc_4096 (1000 cells, double S64 = 128 directions, 4096 groups, 7 grids, W-cycle
+    l_max 2): FP32 sweeps against the plain FP64 path, step by step from the same start;
+    per-step error of the FP32-sweep state against the FP64 state, and the FP32 sweep's
+    HBM roofline at this size."""
+    import torch
+    from paper_2011_05427_gb300 import trt
+    cfg = W.fc_4096("W")
+    dev = f"cuda:{local}"
+    out = {"workload": "fc_4096: 1000 cells, 128 directions (double S64), 4096 groups, grids "
+                       "4096/1024/256/64/16/4/1, W-cycle l_max 2, dt 1e-3 sh, eps 1e-8"}
+    errs = []
+    solvers = {}
+    for prec in ("fp64", "sweep32"):
+        s = trt.Solver.from_slab(cfg, precision=prec, device=dev)
+        s.autotune(cfg.dt, reps=2)
+        solvers[prec] = s
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    tot = {"fp64": 0.0, "sweep32": 0.0}
+    nti = {"fp64": 0, "sweep32": 0}
+    for k in range(steps):
+        for prec, s in solvers.items():
+            torch.cuda.synchronize()
+            ev[0].record(s.stream)
+            st = s.step(cfg.dt, "W", 2, cfg.eps)
+            ev[1].record(s.stream)
+            torch.cuda.synchronize()
+            tot[prec] += ev[0].elapsed_time(ev[1])
+            nti[prec] += st["n_ti"]
+        a, b = solvers["fp64"].moments(), solvers["sweep32"].moments()
+        errs.append({"step": k + 1,
+                     "max_rel_T": float(np.max(np.abs(b["T"] - a["T"]) / a["T"])),
+                     "max_rel_Eg": float(np.max(np.abs(b["Eg"] - a["Eg"]) /
+                                                a["Eg"].sum(0)[None, :]))})
+    roof = sweep_roofline(trt, solvers["sweep32"], cfg, fp32=True, reps=10)["roofline"]
+    for s in solvers.values():
+        s.close()
+    upd = cfg.updates_per_sweep()
+    out.update({"ms_per_step_fp64": tot["fp64"] / steps,
+                "ms_per_step_sweep32": tot["sweep32"] / steps,
+                "n_ti_per_step_fp64": nti["fp64"] / steps,
+                "n_ti_per_step_sweep32": nti["sweep32"] / steps,
+                "value_sweep32": nti["sweep32"] * upd / (tot["sweep32"] * 1e-3),
+                "error_sweep32_vs_fp64_per_step": errs, "roofline_sweep_fp32": roof})
+    return out
+
+
 def counters(stats, steps):
     return {k: sum(x[k] for x in stats) / steps for k in ("n_ti", "n_c", "n_lo")}
 
@@ -407,6 +454,8 @@ def run_ours(args):
             extra["closure"] = closure_bench(local, ms_step)
         if args.batch and ws == 1:
             extra["batch_256"] = batch_bench(local)
+        if args.large and ws == 1:
+            extra["fc_4096"] = fc4096_bench(local)
 
     tile = s.tile
     if args.precision in ("fp64", "lo32"):
@@ -528,6 +577,8 @@ def main():
     ap.add_argument("--no-mlp", dest="mlp", action="store_false")
     ap.add_argument("--no-closure", dest="closure", action="store_false")
     ap.add_argument("--no-batch", dest="batch", action="store_false")
+    ap.add_argument("--no-large", dest="large", action="store_false",
+                    help="skip the 4096-group comparison (fc_4096)")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--profile-step", action="store_true",
                     help="run the warm-up steps and one more step, print nothing (for ncu)")
