@@ -134,7 +134,15 @@ FP64_PEAK_TFLOPS = 1.25
 
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch, from the ncu capture named
 # in profiles/, valid while the kernel source has the recorded SHA-256 (else null).
-TRAFFIC = {}
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum, one ncu capture of the
+# sweep and its finalize on the fc_1024 workload, tile D = 8 directions per CTA), valid while
+# the kernel source hashes to `sha`; profiles/ holds the capture's summary and command.
+TRAFFIC = {
+    "sweep_fp64": {"file": "sweep.cu", "sha": "276d663750df14f9",
+                   "bytes": 540390144 + 542146560 + 66134784 + 13056},
+    "sweep_fp32": {"file": "sweep.cu", "sha": "276d663750df14f9",
+                   "bytes": 269910016 + 244672512 + 33076992 + 0},
+}
 
 
 def _src_sha(name):
@@ -582,9 +590,22 @@ def main():
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--profile-step", action="store_true",
                     help="run the warm-up steps and one more step, print nothing (for ncu)")
+    ap.add_argument("--profile-mlp", action="store_true",
+                    help="run the fused MLP inference over 512,000 rows 3 times (for ncu)")
     ap.add_argument("--tile", default=None,
                     help="D,shape: sweep tile for --profile-step (default: the library's)")
     args = ap.parse_args()
+    if args.profile_mlp:
+        import torch
+        from paper_2011_05427_gb300 import closure, mlp
+        net = mlp.MLP(closure._init(7), device="cuda:0")
+        g = torch.Generator(device="cuda:0")
+        g.manual_seed(3)
+        x = torch.rand((512000, 3), generator=g, device="cuda:0") * 2 - 1
+        for _ in range(3):
+            net.forward_fused(x)
+        torch.cuda.synchronize()
+        return
     if args.profile_step:
         from paper_2011_05427_gb300 import trt
         cfg = W.fc_1024(args.cycle)
