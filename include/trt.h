@@ -197,7 +197,8 @@ int trt_k_sweep(trt_handle *h, double dt, const double *sigE, const double *emis
  * params (FP32 [TRT_MLP_NPARAM]) and w16 (BF16 copies, trt_mlp_refresh) are the
  * network; scratch (>= trt_mlp_scratch_bytes(G * n_cells, 0) bytes), x (FP32
  * [G * n_cells][3]) and y (FP32 [G * n_cells]) are work buffers.  All caller-owned device
- * memory that must outlive the steps.  params = NULL removes the closure. */
+ * memory that must outlive the steps; params 16-byte aligned (TRT_EINVAL otherwise).
+ * params = NULL removes the closure. */
 int trt_set_closure(trt_handle *h, const float *params, const void *w16, void *scratch,
                     size_t scratch_bytes, float *x, float *y);
 

@@ -644,6 +644,8 @@ int trt_set_closure(trt_handle *h, const float *params, const void *w16, void *s
     const int rows = h->p.G * h->p.nx;
     if (!w16 || !scratch || !x || !y || scratch_bytes < trt_mlp_scratch_bytes(rows, 0))
         return fail(h, TRT_EINVAL, "trt_set_closure: missing buffer or scratch too small");
+    if (reinterpret_cast<uintptr_t>(params) & 15)
+        return fail(h, TRT_EINVAL, "trt_set_closure: params not 16-byte aligned");
     h->mlp_params = params;
     h->mlp_w16 = w16;
     h->mlp_scratch = scratch;

@@ -230,7 +230,7 @@ void build_stage(trt_batch *b, int id, double dt, int cycle_type)
         Op &o = B.add(K_GSUM, C_ALL);
         for (int s = 0; s < n; ++s) {
             GroupSumArgs a{H(s)->p.G, H(s)->p.nx, H(s)->Eg_old, H(s)->Ephase};
-            const int nb = (H(s)->p.nx + 127) / 128;
+            const int nb = (H(s)->p.nx + 31) / 32;
             B.set(o, s, a, nb, nb);
         }
     } else if (id == S_SWEEP) {

@@ -33,13 +33,21 @@ struct SeriesTables {
 // relative error eps of order 2^-22, not the FP64 pipe) refined by one third-order
 // Newton-Raphson (Householder) step: with e = 1 - d x, x (1 + e + e^2) = (1 - eps^3)/d,
 // below FP64 rounding, at 3 FP64 FMAs where an IEEE division costs ~20 on GB300's FP64
-// pipe.  Zero, infinite, NaN or subnormal operands (or results) divide.
+// pipe.  Zero, infinite, NaN or subnormal operands (or results) divide; the test reads
+// the approximation's biased exponent with integer instructions (an FP64 compare would
+// take the FP64 pipe): 1 .. 2018 (|x| < 2^996) is the refined case.  The division sits in
+// a function that is never inlined, so that the compiler branches around it instead of
+// predicating its FP64 instructions into every call.
+#ifdef __CUDA_ARCH__
+static __device__ __noinline__ double rcp64_divide(double d) { return 1.0 / d; }
+#endif
 __host__ __device__ inline double rcp64(double d)
 {
 #ifdef __CUDA_ARCH__
     double x;
     asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(x) : "d"(d));
-    if (!(fabs(x) < 1e300) || x == 0.0) return 1.0 / d;
+    const unsigned ex = ((unsigned)__double2hiint(x) >> 20) & 0x7ffu;
+    if (ex - 1u >= 2018u) return rcp64_divide(d);
     const double e = fma(-d, x, 1.0);
     return fma(x, fma(e, e, e), x);
 #else
@@ -53,13 +61,15 @@ __host__ __device__ inline double rcp64(double d)
 // 2^m 2^(j/32) (1 + p(r)), p the degree-6 Taylor polynomial of e^r - 1 (truncation
 // r^7/7! < 2e-18).  tab = 2^(j/32), j = 0..31 (SeriesTables::e2, staged in shared memory).
 // About 11 FP64 operations against ~20 for a library exponential; within about an ulp.
-// Outside (-708, 709) (and for NaN) it calls exp().
+// Outside (-708, 709) (and for NaN) it calls exp(), from a function that is never inlined
+// (a branch around the library code, not predicated FP64 instructions on every call).
 struct ExpConsts {
     double inv, L1, L2;   // 32/ln2; ln2/32 = L1 + L2 with L1 of 31 significant bits
 };
+static __device__ __noinline__ double texp_library(double x) { return exp(x); }
 __device__ inline double texp(double x, const double *tab, const ExpConsts &c)
 {
-    if (!(x > -708.0 && x < 709.0)) return exp(x);
+    if (!(x > -708.0 && x < 709.0)) return texp_library(x);
     const double kd = rint(x * c.inv);
     const int k = (int)kd;
     const double r = fma(-kd, c.L2, fma(-kd, c.L1, x));
@@ -123,8 +133,9 @@ struct Problem {
     size_t rscratch_doubles;
     // sweep tile: directions per CTA (0 = default) and strip shape index (0 = default)
     int sweep_D = 0, sweep_shape = 0;
-    // per-group Chebyshev tables in ln T of sigma_E T^3, sigma_R T^3 and the emission
-    // factor ln(1 - e^{-w}) (null: direct integrals)
+    // per-group polynomial tables in ln T (Chebyshev fits stored as monomials) of
+    // sigma_E T^3, sigma_R T^3 and the emission factor ln(1 - e^{-w}) (null: direct
+    // integrals)
     double *otab = nullptr;
 };
 

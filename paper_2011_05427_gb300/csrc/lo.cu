@@ -334,9 +334,12 @@ __host__ __device__ inline int lo_mmax(int nx)
 }
 
 // One system per CTA: all 4 warps stage the rows (phase A: the parallel part, global
-// loads and the face coefficients), then warp 0 runs the elimination.
+// loads and the face coefficients), then warp `sw` runs the elimination.  The CTA's four
+// warps sit on the SM's four sub-partitions, each with its own FP64 pipe; rotating the
+// eliminating warp with the work item spreads the serial FP64 chains of the CTAs resident
+// on an SM over all four pipes (always warp 0 would queue them all on one).
 template <typename R>
-__device__ void lo_solve_body(const LoCtx &x, int q)
+__device__ void lo_solve_body(const LoCtx &x, int q, int sw)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     R *sm = reinterpret_cast<R *>(smem_raw);
@@ -346,13 +349,14 @@ __device__ void lo_solve_body(const LoCtx &x, int q)
         lo_stage<R>(x, q, sm, mmax, threadIdx.x, blockDim.x);
         __syncthreads();
     }
-    if (threadIdx.x < 32) warp_lo_solve<R>(x, q, sm, mmax, staged);
+    if ((int)(threadIdx.x >> 5) == (sw & ((int)(blockDim.x >> 5) - 1)))
+        warp_lo_solve<R>(x, q, sm, mmax, staged);
 }
 
 template <typename R>
 __global__ void __launch_bounds__(128) k_lo_solve(LoCtx x)
 {
-    lo_solve_body<R>(x, blockIdx.x);
+    lo_solve_body<R>(x, blockIdx.x, blockIdx.x);
 }
 
 template <typename R>
@@ -363,7 +367,7 @@ __global__ void __launch_bounds__(128) k_lo_solve_b(const int *__restrict__ meta
         int s, bx, by;
         if (!bdecode(meta, N, b, s, bx, by)) break;
         const LoCtx x = xs[s];
-        lo_solve_body<R>(x, bx);
+        lo_solve_body<R>(x, bx, b);
         __syncthreads();
     }
 }
@@ -535,7 +539,12 @@ __device__ void restrict_body(const RestrictCtx &x, int bx, int by)
 
 // Two-stage restriction for wide coarse groups (r >= 64 members): stage 1 sums chunks of
 // kChunk members per (coarse group, cell / face) into partial vectors with many CTAs;
-// stage 2 adds the chunks in a fixed order and forms the coefficients.  The compensation
+// stage 2 adds the chunks in a fixed order and forms the coefficients.  Sums stage 1 does
+// not form: the member energies on either side of an interior face (sum E_R at face i is
+// sum E at cell i, sum E_L is sum E at cell i - 1: the same terms in the same order, so
+// the same bits), and the plain means that replace a weighted mean whose weights sum to
+// zero (formed by stage 2 from the members in that rare case).  Every stage-1 addition is
+// an FP64 operation, the pipe that bounds these kernels on GB300.  The compensation
 // is summed in one pass, xi = dx (sum sigR F - sigR-bar sum F) + c (sum etaR E_R -
 // sum etaL E_L), which is the two-pass sum up to rounding relative to the sigR dx F terms.
 constexpr int kChunk = 32;
@@ -559,8 +568,8 @@ __device__ void restrict_part_body(const Restrict2Ctx &x, int bx, int by)
     for (int p = pb + ty; p < pe; p += 4) {
         if (i < nx) {
             const size_t c = (size_t)p * nx + i;
-            const double E = S.E[c], ph = S.phi[c], sg = S.sig[c];
-            v[0] += ph * E; v[1] += ph; v[2] += sg * E; v[3] += sg;
+            const double E = S.E[c];
+            v[0] += S.phi[c] * E; v[2] += S.sig[c] * E;
             v[4] += S.emis[c]; v[5] += S.Eold[c]; v[6] += E;
         }
         if (i <= nx) {
@@ -577,12 +586,14 @@ __device__ void restrict_part_body(const Restrict2Ctx &x, int bx, int by)
             const double ER = (i == nx) ? S.EbX[p] : S.E[(size_t)p * nx + i];
             const double EL = (i == 0) ? S.Eb0[p] : S.E[(size_t)p * nx + i - 1];
             const double wF = fabs(Fp) + 1e-6 * kC * 0.5 * (EL + ER);
-            v[7] += sR * wF; v[8] += sR; v[9] += wF; v[10] += sR * Fp; v[11] += Fp;
+            v[7] += sR * wF; v[9] += wF; v[10] += sR * Fp; v[11] += Fp;
             if (!S.fine) {
                 v[12] += S.etaR[fp] * ER;
                 v[13] += S.etaL[fp] * EL;
             }
-            v[14] += ER; v[15] += EL; v[16] += S.Fold[fp];
+            if (i == nx) v[14] += ER;
+            if (i == 0) v[15] += EL;
+            v[16] += S.Fold[fp];
         }
         if (i == 0 || i == nx) {
             const int side = (i == 0) ? 0 : 1;
@@ -600,18 +611,22 @@ __device__ void restrict_part_body(const Restrict2Ctx &x, int bx, int by)
 #pragma unroll
     for (int k = 0; k < kRP; ++k) red[ty][tx][k] = v[k];
     __syncthreads();
-    if (ty == 0 && i <= nx) {
-        for (int y = 1; y < 4; ++y)
-#pragma unroll
-            for (int k = 0; k < kRP; ++k) v[k] += red[y][tx][k];
+    // the four rows' partials, value k by row k % 4: the additions are spread over the
+    // four warps (four sub-partitions' FP64 pipes); same order as a sum by one row
+    if (i <= nx) {
         double *o = x.part + ((size_t)(P * x.nchunk + ch) * kRP) * nf + i;
-#pragma unroll
-        for (int k = 0; k < kRP; ++k) o[(size_t)k * nf] = v[k];
+        for (int k = ty; k < kRP; k += 4) {
+            double a = red[0][tx][k];
+            for (int y = 1; y < 4; ++y) a += red[y][tx][k];
+            o[(size_t)k * nf] = a;
+        }
     }
 }
 
 // block (32, kRP); grid (ceil((nx+1)/32), n_to): thread (tx, k) adds value k of position
-// tx over the chunks in a fixed order, then row 0 forms the coefficients
+// tx over the chunks in a fixed order; then rows 0 .. 3 (one warp each, on four
+// sub-partitions) form the coefficients: row 0 the E-weighted cell means, row 1 the copied
+// cell sums, row 2 the face opacity and compensation, row 3 the boundary means.
 __device__ void restrict_final_body(const Restrict2Ctx &x, int bx, int by)
 {
     __shared__ double sv[kRP][33];
@@ -621,41 +636,76 @@ __device__ void restrict_final_body(const Restrict2Ctx &x, int bx, int by)
     const int P = by;
     if (i <= nx) {
         double acc = 0.0;
-        const double *o = x.part + ((size_t)P * x.nchunk * kRP + k) * nf + i;
+        // sum E_L at the block's first face (i > 0) is sum E at cell i - 1 of the block before
+        const int kk = (k == 15 && tx == 0 && i > 0) ? 6 : k;
+        const int ii = (kk != k) ? i - 1 : i;
+        const double *o = x.part + ((size_t)P * x.nchunk * kRP + kk) * nf + ii;
         for (int ch = 0; ch < x.nchunk; ++ch) acc += o[(size_t)ch * kRP * nf];
         sv[k][tx] = acc;
     }
     __syncthreads();
-    if (k != 0 || i > nx) return;
-    double v[kRP];
-#pragma unroll
-    for (int q = 0; q < kRP; ++q) v[q] = sv[q][tx];
+    if (k > 3 || i > nx) return;
     const double rn = (double)x.r;
     const Level &T = x.T;
-    if (i < nx) {
+    const Level &S = x.S;
+    const int p0 = P * x.r;
+    if (k == 0 && i < nx) {
         const size_t c = (size_t)P * nx + i;
-        T.phi[c] = (v[6] != 0.0) ? v[0] / v[6] : v[1] / rn;
-        T.sig[c] = (v[6] != 0.0) ? v[2] / v[6] : v[3] / rn;
-        T.emis[c] = v[4];
-        T.Eold[c] = v[5];
-        T.Esum[c] = v[6];
-    }
-    const double dxf = (i == 0) ? 0.5 * x.h[0] : (i == nx) ? 0.5 * x.h[nx - 1]
-                                            : 0.5 * (x.h[i - 1] + x.h[i]);
-    const double sRP = (v[9] != 0.0) ? v[7] / v[9] : v[8] / rn;
-    const double xi = dxf * (v[10] - sRP * v[11]) + kC * (v[12] - v[13]);
-    const size_t f = (size_t)P * nf + i;
-    T.sigR[f] = sRP;
-    T.etaR[f] = (xi > 0.0 && v[14] != 0.0) ? xi / (kC * v[14]) : 0.0;
-    T.etaL[f] = (xi < 0.0 && v[15] != 0.0) ? -xi / (kC * v[15]) : 0.0;
-    T.Fold[f] = v[16];
-    if (i == 0 || i == nx) {
-        const double phb = (v[19] != 0.0) ? v[17] / v[19] : v[18] / rn;
-        const double Cb = (v[22] != 0.0) ? v[20] / v[22] : v[21] / rn;
+        const double E = sv[6][tx];
+        double ph = 0.0, sg = 0.0;
+        if (E != 0.0) {
+            ph = sv[0][tx] / E;
+            sg = sv[2][tx] / E;
+        } else {   // no energy in the coarse group: plain means of the members
+            for (int p = p0; p < p0 + x.r; ++p) {
+                ph += S.phi[(size_t)p * nx + i];
+                sg += S.sig[(size_t)p * nx + i];
+            }
+            ph /= rn;
+            sg /= rn;
+        }
+        T.phi[c] = ph;
+        T.sig[c] = sg;
+    } else if (k == 1) {
+        if (i < nx) {
+            const size_t c = (size_t)P * nx + i;
+            T.emis[c] = sv[4][tx];
+            T.Eold[c] = sv[5][tx];
+            T.Esum[c] = sv[6][tx];
+        }
+        T.Fold[(size_t)P * nf + i] = sv[16][tx];
+    } else if (k == 2) {
+        const double v14 = (i < nx) ? sv[6][tx] : sv[14][tx];
+        const double v15 = (i > 0 && tx > 0) ? sv[6][tx - 1] : sv[15][tx];
+        const double dxf = (i == 0) ? 0.5 * x.h[0] : (i == nx) ? 0.5 * x.h[nx - 1]
+                                                : 0.5 * (x.h[i - 1] + x.h[i]);
+        double sRP = 0.0;
+        if (sv[9][tx] != 0.0) {
+            sRP = sv[7][tx] / sv[9][tx];
+        } else {   // no flux weight: plain mean of the members' face opacities
+            for (int p = p0; p < p0 + x.r; ++p) {
+                if (S.fine) {
+                    const double *sc = S.sigR + (size_t)p * nx;
+                    sRP += (i == 0) ? sc[0] : (i == nx) ? sc[nx - 1]
+                           : (sc[i - 1] * x.h[i - 1] + sc[i] * x.h[i]) * x.ihf[i];
+                } else {
+                    sRP += S.sigR[(size_t)p * nf + i];
+                }
+            }
+            sRP /= rn;
+        }
+        const double xi = dxf * (sv[10][tx] - sRP * sv[11][tx]) + kC * (sv[12][tx] - sv[13][tx]);
+        const size_t f = (size_t)P * nf + i;
+        T.sigR[f] = sRP;
+        T.etaR[f] = (xi > 0.0 && v14 != 0.0) ? xi / (kC * v14) : 0.0;
+        T.etaL[f] = (xi < 0.0 && v15 != 0.0) ? -xi / (kC * v15) : 0.0;
+    } else if (k == 3 && (i == 0 || i == nx)) {
+        const double phb = (sv[19][tx] != 0.0) ? sv[17][tx] / sv[19][tx] : sv[18][tx] / rn;
+        const double Cb = (sv[22][tx] != 0.0) ? sv[20][tx] / sv[22][tx] : sv[21][tx] / rn;
         if (i == 0) {
-            T.phib0[P] = phb; T.C0[P] = Cb; T.Ein0[P] = v[23]; T.Fin0[P] = v[24];
+            T.phib0[P] = phb; T.C0[P] = Cb; T.Ein0[P] = sv[23][tx]; T.Fin0[P] = sv[24][tx];
         } else {
-            T.phibX[P] = phb; T.CX[P] = Cb; T.EinX[P] = v[23]; T.FinX[P] = v[24];
+            T.phibX[P] = phb; T.CX[P] = Cb; T.EinX[P] = sv[23][tx]; T.FinX[P] = sv[24][tx];
         }
     }
 }
@@ -664,16 +714,42 @@ __device__ void restrict_final_body(const Restrict2Ctx &x, int bx, int by)
 // grey LOQD + MEB: one Newton step on the grey level (single CTA)
 // ---------------------------------------------------------------------------------------
 
-__device__ inline double block_max(double v, double *red)
+// Block-wide maxima of non-negative values on their IEEE encodings: for x >= 0 (and +inf)
+// the order of the doubles is the unsigned order of their bit patterns, so the reduction
+// runs on the integer pipes (a warp-wide FP64 max takes a sub-partition's FP64 pipe for 64
+// cycles on GB300).  NaN maps to 0, the value fmax would keep.  red: kGreyRed slots, at
+// least 32 per value; the maxima are returned to every thread.
+constexpr int kGreyNV = 7;
+constexpr int kGreyRed = 32 * kGreyNV;
+
+__device__ inline unsigned long long nn_bits(double v)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    return ((b & 0x7fffffffffffffffull) > 0x7ff0000000000000ull) ? 0ull : b;
+}
+
+__device__ inline unsigned long long umax64(unsigned long long a, unsigned long long b)
+{
+    return a > b ? a : b;
+}
+
+__device__ inline void block_max_bits(unsigned long long (&v)[kGreyNV], unsigned long long *red)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+#pragma unroll
+    for (int k = 0; k < kGreyNV; ++k)
+        for (int o = 16; o > 0; o >>= 1) v[k] = umax64(v[k], __shfl_xor_sync(0xffffffffu, v[k], o));
     __syncthreads();
-    if (lane == 0) red[warp] = v;
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < kGreyNV; ++k) red[k * 32 + warp] = v[k];
     __syncthreads();
-    double r = 0.0;
-    for (int k = 0; k < nw; ++k) r = fmax(r, red[k]);
-    return r;
+#pragma unroll
+    for (int k = 0; k < kGreyNV; ++k) {
+        unsigned long long r = 0ull;
+        for (int w = 0; w < nw; ++w) r = umax64(r, red[k * 32 + w]);
+        v[k] = r;
+    }
 }
 
 __device__ void grey_body(const GreyCtx &x)
@@ -684,8 +760,8 @@ __device__ void grey_body(const GreyCtx &x)
     double *sa = gsm;            // absorption w c sig*
     double *ss = sa + nx;        // source w Q* - (1-w) cv (T* - Told)/dt
     double *sL = ss + nx;        // 1 / Lambda
-    double *red = sL + nx;       // [32]
-    double *wsm = red + 32;      // warp-solver scratch
+    double *red = sL + nx;       // [kGreyRed] block maxima
+    double *wsm = red + kGreyRed;   // warp-solver scratch
     const GreyArgs &a = x.a;
     const Level &g = x.lo.L;
     const double cvdt = a.cv / a.dt;
@@ -695,8 +771,11 @@ __device__ void grey_body(const GreyCtx &x)
         const double sig = g.sig[i];
         const double Q = 2.0 * g.emis[i];
         const double iTs = rcp64(Ts);
-        const double x1 = a.nu_first * iTs;
-        double dQ = k54 * (1.0 + x1) * exp(-x1);
+        double dQ = k54;   // first edge at 0: (1 + x) e^{-x} = 1
+        if (a.nu_first != 0.0) {
+            const double x1 = a.nu_first * iTs;
+            dQ = k54 * (1.0 + x1) * exp(-x1);
+        }
         if (!isinf(a.nu_last)) {
             const double xL = a.nu_last * iTs;
             dQ -= k54 * (1.0 + xL) * exp(-xL);
@@ -727,46 +806,62 @@ __device__ void grey_body(const GreyCtx &x)
     __syncthreads();
     if (threadIdx.x < 32) warp_lo_solve<double>(lc, 0, wsm, x.mmax, staged);
     __syncthreads();
-    double dTc = 0, Tm = 0, dEc = 0, Em = 0, dTp = 0, dEp = 0, bad = 0;
+    // v: bad flag, max|T - Tcyc|, max|T|, max|E - Ecyc|, max|E|, max|T - Tphase|,
+    // max|E - Ephase| as non-negative encodings (flags[0 .. 6])
+    unsigned long long v[kGreyNV] = {};
+    const unsigned long long kInfBits = 0x7ff0000000000000ull;
     for (int i = threadIdx.x; i < nx; i += blockDim.x) {
         const double Ts = a.Tstar[i];
         const double E = g.E[i];
         const double T = Ts + (kC * g.sig[i] * E - 2.0 * g.emis[i] - cvdt * (Ts - a.Told[i])) * sL[i];
         a.T[i] = T;
-        if (!(T > 0.0) || !isfinite(T) || !isfinite(E)) bad = 1.0;
+        const long long tb = __double_as_longlong(T);
+        const unsigned long long eb = (unsigned long long)__double_as_longlong(E) & 0x7fffffffffffffffull;
+        // T > 0 and finite: sign clear, not zero, below the infinity encoding
+        if (tb <= 0 || (unsigned long long)tb >= kInfBits || eb >= kInfBits) v[0] = 1ull;
         if (a.want_norms) {
-            Tm = fmax(Tm, fabs(T));
-            Em = fmax(Em, fabs(E));
-            dTc = fmax(dTc, fabs(T - a.Tcyc[i]));
-            dEc = fmax(dEc, fabs(E - a.Ecyc[i]));
-            dTp = fmax(dTp, fabs(T - a.Tphase[i]));
-            dEp = fmax(dEp, fabs(E - a.Ephase[i]));
+            v[1] = umax64(v[1], nn_bits(fabs(T - a.Tcyc[i])));
+            v[2] = umax64(v[2], nn_bits(fabs(T)));
+            v[3] = umax64(v[3], nn_bits(fabs(E - a.Ecyc[i])));
+            v[4] = umax64(v[4], nn_bits(fabs(E)));
+            v[5] = umax64(v[5], nn_bits(fabs(T - a.Tphase[i])));
+            v[6] = umax64(v[6], nn_bits(fabs(E - a.Ephase[i])));
         }
     }
-    bad = block_max(bad, red);
-    if (threadIdx.x == 0 && bad != 0.0) a.flags[0] = 1.0;
-    if (a.want_norms) {
-        dTc = block_max(dTc, red);
-        Tm = block_max(Tm, red);
-        dEc = block_max(dEc, red);
-        Em = block_max(Em, red);
-        dTp = block_max(dTp, red);
-        dEp = block_max(dEp, red);
-        if (threadIdx.x == 0) {
-            a.flags[1] = dTc; a.flags[2] = Tm; a.flags[3] = dEc; a.flags[4] = Em;
-            a.flags[5] = dTp; a.flags[6] = dEp;
+    block_max_bits(v, reinterpret_cast<unsigned long long *>(red));
+    if (threadIdx.x == 0) {
+        if (v[0] != 0ull) a.flags[0] = 1.0;
+        if (a.want_norms) {
+            a.flags[1] = __longlong_as_double((long long)v[1]);
+            a.flags[2] = __longlong_as_double((long long)v[2]);
+            a.flags[3] = __longlong_as_double((long long)v[3]);
+            a.flags[4] = __longlong_as_double((long long)v[4]);
+            a.flags[5] = __longlong_as_double((long long)v[5]);
+            a.flags[6] = __longlong_as_double((long long)v[6]);
         }
     }
-    if (a.have_prev_dev && threadIdx.x == 0) *a.have_prev_dev = 1;   // after block_max barriers
+    if (a.have_prev_dev && threadIdx.x == 0) *a.have_prev_dev = 1;   // after the reduction's barriers
 }
 
+// out_i = sum_q X[q][i]: block of 256 threads = 32 cells x 8 rows; row y sums the groups
+// q = y (mod 8) of its cell, then one row adds the 8 partials in row order (fixed order,
+// deterministic).  A single pass over the groups per cell would leave 32 cells per warp
+// and few warps per SM on a serial FP64 chain.
 __device__ void group_sum_body(const GroupSumArgs &a, int bx)
 {
-    const int i = bx * blockDim.x + threadIdx.x;
-    if (i >= a.nx) return;
+    __shared__ double part[8][33];
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int i = bx * 32 + tx;
     double s = 0.0;
-    for (int q = 0; q < a.n; ++q) s += a.X[(size_t)q * a.nx + i];
-    a.out[i] = s;
+    if (i < a.nx)
+        for (int q = ty; q < a.n; q += 8) s += a.X[(size_t)q * a.nx + i];
+    part[ty][tx] = s;
+    __syncthreads();
+    if (ty == (bx & 7) && i < a.nx) {
+        double t = part[0][tx];
+        for (int y = 1; y < 8; ++y) t += part[y][tx];
+        a.out[i] = t;
+    }
 }
 
 // entry points: the single-slab kernels pass blockIdx; the batched ones walk a work list
@@ -783,7 +878,7 @@ __global__ void __launch_bounds__(32 * kRP) k_restrict_final(Restrict2Ctx x)
     restrict_final_body(x, blockIdx.x, blockIdx.y);
 }
 __global__ void __launch_bounds__(1024) k_grey(GreyCtx x) { grey_body(x); }
-__global__ void k_group_sum(GroupSumArgs a) { group_sum_body(a, blockIdx.x); }
+__global__ void __launch_bounds__(256) k_group_sum(GroupSumArgs a) { group_sum_body(a, blockIdx.x); }
 
 #define TRT_BATCHED(name, Ctx, bounds, call)                                                  \
     __global__ void __launch_bounds__(bounds) name(const int *__restrict__ meta, int N,        \
@@ -801,7 +896,7 @@ TRT_BATCHED(k_restrict_b, RestrictCtx, 512, restrict_body(x, bx, by))
 TRT_BATCHED(k_restrict_part_b, Restrict2Ctx, 128, restrict_part_body(x, bx, by))
 TRT_BATCHED(k_restrict_final_b, Restrict2Ctx, 32 * kRP, restrict_final_body(x, bx, by))
 TRT_BATCHED(k_grey_b, GreyCtx, 1024, grey_body(x))
-TRT_BATCHED(k_group_sum_b, GroupSumArgs, 128, group_sum_body(x, bx))
+TRT_BATCHED(k_group_sum_b, GroupSumArgs, 256, group_sum_body(x, bx))
 #undef TRT_BATCHED
 
 __global__ void __launch_bounds__(256) k_copy_b(const int *__restrict__ meta, int N,
@@ -969,7 +1064,7 @@ GreyCtx make_grey_ctx(const Problem &p, const Level &g, const GreyArgs &a)
 static void grey_launch_shape(int nx, int &bs, size_t &sm)
 {
     bs = std::min(1024, std::max(32, (nx + 31) / 32 * 32));
-    sm = sizeof(double) * (3 * (size_t)nx + 32 + 6 * 32 * (size_t)lo_mmax(nx));
+    sm = sizeof(double) * (3 * (size_t)nx + kGreyRed + 6 * 32 * (size_t)lo_mmax(nx));
 }
 
 cudaError_t launch_grey(const Problem &p, const Level &g, const GreyArgs &a)
@@ -1002,14 +1097,14 @@ cudaError_t launch_group_sum(const Problem &p, int n, const double *X, double *o
 {
     GroupSumArgs a;
     a.n = n; a.nx = p.nx; a.X = X; a.out = out;
-    k_group_sum<<<(p.nx + 127) / 128, 128, 0, p.stream>>>(a);
+    k_group_sum<<<(p.nx + 31) / 32, 256, 0, p.stream>>>(a);
     return cudaGetLastError();
 }
 
 cudaError_t launch_group_sum_b(const int *meta, int N, const GroupSumArgs *xs, int grid,
                                cudaStream_t st)
 {
-    k_group_sum_b<<<grid, 128, 0, st>>>(meta, N, xs);
+    k_group_sum_b<<<grid, 256, 0, st>>>(meta, N, xs);
     return cudaGetLastError();
 }
 

@@ -76,6 +76,13 @@ __device__ inline bool mbar_wait(uint64_t *bar, unsigned parity)
     return true;
 }
 
+// two FP32 values rounded to BF16 (nearest even) in one 32-bit word, lo in the low half
+__device__ inline uint32_t pack_bf16x2(float lo, float hi)
+{
+    const __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t *>(&h);
+}
+
 __device__ inline void cp16(void *dst, const void *src, unsigned bytes)
 {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(su32(dst)), "l"(src),
@@ -340,17 +347,26 @@ __global__ void __launch_bounds__(128) k_gemm(int M, int N, int K, const bf16 *_
 // One CTA per SM; per iteration 256 rows as two 128-row tiles.  Layer 1 (3 inputs) on CUDA
 // cores writes both tiles' h1 (BF16) into shared memory in the K-major core-matrix layout;
 // the two 256 x 256 layers run on tcgen05 with the two tiles' 128 x 256 FP32 accumulators
-// in all 512 tensor-memory columns; their weights stream through a two-slot ring of 64-wide
-// K chunks (32 KB each) shared by both tiles; the ReLU epilogue of layer 2 writes h2 back
-// over h1; the epilogue of layer 3 folds the sigmoid head.  Activations never leave shared
-// memory.  Chunk q of the weight stream (layer (q / 4) % 2, K chunk q % 4) sits in slot
-// q % 3; its MMAs commit to the slot's mbarrier; chunk q + 2 is copied once the MMAs of
-// chunk q - 1 (same slot) have completed, so two copies are in flight while the MMAs of
+// in all 512 tensor-memory columns; their weights stream through a four-slot ring of
+// 32-wide K chunks (16 KB each) shared by both tiles; the ReLU epilogue of layer 2 writes
+// h2 back over h1; the epilogue of layer 3 folds the sigmoid head.  Activations never
+// leave shared memory, and neither do the small parameters (layer-1 weights, the biases,
+// the head), copied there once per CTA: the threads of a CTA read them in lockstep
+// (broadcast), which from global memory cost an L1 miss per load at this shared-memory
+// carve-out.  Chunk q of the weight stream (layer (q / 8) % 2, K chunk q % 8) sits in slot
+// q % 4; its MMAs commit to the slot's mbarrier; chunk q + 3 is copied once the MMAs of
+// chunk q - 1 (same slot) have completed, so three copies are in flight while the MMAs of
 // chunk q run.
 constexpr int FA_BYTES = 128 * 256 * 2;   // one activation tile
-constexpr int FW_BYTES = 256 * 64 * 2;    // one weight chunk
-constexpr int F_SLOTS = 3;
-constexpr int F_SMEM = 2 * FA_BYTES + F_SLOTS * FW_BYTES + 256;   // 229,632 bytes
+constexpr int FK = 32;                    // K width of a weight chunk
+constexpr int FNC = 256 / FK;             // chunks per layer
+constexpr int FW_BYTES = 256 * FK * 2;    // one weight chunk
+constexpr int F_SLOTS = 4;
+constexpr uint32_t FW_SBO = FK / 8 * 128;   // weight chunk: row groups 512 bytes apart
+// small parameters in shared memory: W1 [256][3], b1, b2, b3, w4, b4 (1793 floats)
+constexpr int FP_W1 = 0, FP_B1 = 768, FP_B2 = 1024, FP_B3 = 1280, FP_W4 = 1536, FP_B4 = 1792;
+constexpr int FP_BYTES = 1796 * 4;
+constexpr int F_SMEM = 2 * FA_BYTES + F_SLOTS * FW_BYTES + FP_BYTES + 256;   // 204,048 bytes
 constexpr uint32_t FA_SBO = 4096;         // activation tiles: 32 K groups per row group
 
 __global__ void __launch_bounds__(256, 1) k_mlp_fused(int rows, const float *__restrict__ x,
@@ -362,7 +378,8 @@ __global__ void __launch_bounds__(256, 1) k_mlp_fused(int rows, const float *__r
     extern __shared__ __align__(1024) unsigned char sm[];
     unsigned char *sA0 = sm, *sA1 = sm + FA_BYTES;
     unsigned char *sW = sm + 2 * FA_BYTES;   // F_SLOTS weight chunks
-    uint64_t *bar = reinterpret_cast<uint64_t *>(sm + 2 * FA_BYTES + F_SLOTS * FW_BYTES);
+    float *sP = reinterpret_cast<float *>(sW + F_SLOTS * FW_BYTES);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(reinterpret_cast<unsigned char *>(sP) + FP_BYTES);
     uint32_t *tslot = reinterpret_cast<uint32_t *>(bar + F_SLOTS);
     int *sfail = reinterpret_cast<int *>(tslot + 1);
 
@@ -370,7 +387,7 @@ __global__ void __launch_bounds__(256, 1) k_mlp_fused(int rows, const float *__r
     const int half = tid >> 7, r = tid & 127;   // tile and row (= tensor-memory lane)
     const int ntiles = (rows + 255) / 256;
     const int mine = (int)blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
-    const int Q = 8 * mine;   // weight chunks this CTA consumes
+    const int Q = 2 * FNC * mine;   // weight chunks this CTA consumes
 
     if (tid == 0) {
         for (int k = 0; k < F_SLOTS; ++k) mbar_init(&bar[k], 1);
@@ -383,23 +400,31 @@ __global__ void __launch_bounds__(256, 1) k_mlp_fused(int rows, const float *__r
                      "r"(512));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
+    {   // small parameters (16-byte aligned float4 runs: W1 + b1, b2, b3 + w4)
+        const float4 *g = reinterpret_cast<const float4 *>(P);
+        float4 *d = reinterpret_cast<float4 *>(sP);
+        d[tid] = __ldg(g + TRT_MLP_W1 / 4 + tid);                                // W1, b1
+        if (tid < 64) d[FP_B2 / 4 + tid] = __ldg(g + TRT_MLP_B2 / 4 + tid);      // b2
+        if (tid < 128) d[FP_B3 / 4 + tid] = __ldg(g + TRT_MLP_B3 / 4 + tid);     // b3, w4
+        if (tid == 0) sP[FP_B4] = __ldg(P + TRT_MLP_B4);
+    }
     tc_before();
     __syncthreads();
     tc_after();
     const uint32_t tmem = *tslot;
 
-    // chunk q of the weight stream -> slot q % 3 (8 pieces of 16 bytes per thread)
+    // chunk q of the weight stream -> slot q % 4 (4 pieces of 16 bytes per thread)
     int issued = 0;
     auto load_chunk = [&](int q) {
-        const bf16 *W = ((q >> 2) & 1) ? W3 : W2;
-        const int c = q & 3;
+        const bf16 *W = ((q / FNC) & 1) ? W3 : W2;
+        const int c = q % FNC;
         unsigned char *dst = sW + (q % F_SLOTS) * FW_BYTES;
         ++issued;
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
+        for (int j = 0; j < FW_BYTES / 16 / 256; ++j) {
             const int p = tid + 256 * j;
-            const int r8 = p & 7, ki = (p >> 3) & 7, ni = p >> 6;
-            cp16(dst + p * 16, W + (size_t)(ni * 8 + r8) * 256 + c * 64 + ki * 8, 16u);
+            const int r8 = p & 7, ki = (p >> 3) & (FK / 8 - 1), ni = p / (8 * (FK / 8));
+            cp16(dst + p * 16, W + (size_t)(ni * 8 + r8) * 256 + c * FK + ki * 8, 16u);
         }
         cp_commit();
     };
@@ -413,8 +438,7 @@ __global__ void __launch_bounds__(256, 1) k_mlp_fused(int rows, const float *__r
     // A tile element (row, k) offset: core matrix (row / 8, k / 8), row % 8 at 16 bytes
     auto a_off = [](int row, int k8) { return (row >> 3) * FA_SBO + k8 * 128 + (row & 7) * 16; };
 
-    if (Q > 0) load_chunk(0);
-    if (Q > 1) load_chunk(1);
+    for (int k = 0; k < F_SLOTS - 1 && k < Q; ++k) load_chunk(k);
     int q = 0;
     for (int it = 0; it < mine && ok; ++it) {
         const int row0 = ((int)blockIdx.x + it * (int)gridDim.x) * 256;
@@ -429,25 +453,47 @@ __global__ void __launch_bounds__(256, 1) k_mlp_fused(int rows, const float *__r
                 x1 = x[3 * row + 1];
                 x2 = x[3 * row + 2];
             }
+            // 8 columns per step: their 24 weights and 8 biases as 8 broadcast float4
+            // reads of shared memory, the 8 outputs packed pairwise to BF16
+            const float4 *pw = reinterpret_cast<const float4 *>(sP + FP_W1);
+            const float4 *pb = reinterpret_cast<const float4 *>(sP + FP_B1);
+#pragma unroll 2
             for (int k8 = 0; k8 < 32; ++k8) {
-                uint4 u;
-                bf16 *hb = reinterpret_cast<bf16 *>(&u);
+                float w[24], bb[8];
 #pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    const int c = k8 * 8 + j;
-                    float a = __ldg(P + TRT_MLP_B1 + c);
-                    a = fmaf(__ldg(P + TRT_MLP_W1 + 3 * c), x0, a);
-                    a = fmaf(__ldg(P + TRT_MLP_W1 + 3 * c + 1), x1, a);
-                    a = fmaf(__ldg(P + TRT_MLP_W1 + 3 * c + 2), x2, a);
-                    hb[j] = __float2bfloat16_rn(rv ? fmaxf(a, 0.f) : 0.f);
+                for (int j = 0; j < 6; ++j) {
+                    const float4 t = pw[k8 * 6 + j];
+                    w[4 * j] = t.x; w[4 * j + 1] = t.y; w[4 * j + 2] = t.z; w[4 * j + 3] = t.w;
+                }
+#pragma unroll
+                for (int j = 0; j < 2; ++j) {
+                    const float4 t = pb[k8 * 2 + j];
+                    bb[4 * j] = t.x; bb[4 * j + 1] = t.y; bb[4 * j + 2] = t.z; bb[4 * j + 3] = t.w;
+                }
+                uint4 u;
+                uint32_t *hw = reinterpret_cast<uint32_t *>(&u);
+#pragma unroll
+                for (int j = 0; j < 8; j += 2) {
+                    float a0 = bb[j], a1 = bb[j + 1];
+                    a0 = fmaf(w[3 * j], x0, a0);
+                    a0 = fmaf(w[3 * j + 1], x1, a0);
+                    a0 = fmaf(w[3 * j + 2], x2, a0);
+                    a1 = fmaf(w[3 * j + 3], x0, a1);
+                    a1 = fmaf(w[3 * j + 4], x1, a1);
+                    a1 = fmaf(w[3 * j + 5], x2, a1);
+                    hw[j >> 1] = pack_bf16x2(rv ? fmaxf(a0, 0.f) : 0.f, rv ? fmaxf(a1, 0.f) : 0.f);
                 }
                 *reinterpret_cast<uint4 *>(myA + a_off(r, k8)) = u;
             }
             fence_async_smem();
         }
         for (int layer = 0; layer < 2 && ok; ++layer) {
-            for (int c = 0; c < 4; ++c, ++q) {
-                if (issued > q + 1)    // chunk q has landed (chunk q + 1 may be in flight)
+            for (int c = 0; c < FNC; ++c, ++q) {
+                // chunk q has landed: issued - 1 - q later groups may still be in flight
+                const int later = issued - 1 - q;
+                if (later >= 2)
+                    cp_wait<2>();
+                else if (later == 1)
                     cp_wait<1>();
                 else
                     cp_wait<0>();
@@ -460,17 +506,17 @@ __global__ void __launch_bounds__(256, 1) k_mlp_fused(int rows, const float *__r
                     const uint32_t w0 = su32(sW + (q % F_SLOTS) * FW_BYTES);
                     const uint32_t a0 = su32(sA0), a1 = su32(sA1);
 #pragma unroll
-                    for (int kk = 0; kk < 4; ++kk) {
-                        const uint64_t bd = sdesc(w0 + kk * 2 * LBO, LBO, SBO);
-                        const uint32_t ka = (c * 8 + kk * 2) * 128;
+                    for (int kk = 0; kk < FK / 16; ++kk) {
+                        const uint64_t bd = sdesc(w0 + kk * 2 * LBO, LBO, FW_SBO);
+                        const uint32_t ka = (c * (FK / 8) + kk * 2) * 128;
                         umma(tmem, sdesc(a0 + ka, LBO, FA_SBO), bd, (c | kk) != 0);
                         umma(tmem + 256, sdesc(a1 + ka, LBO, FA_SBO), bd, (c | kk) != 0);
                     }
                     umma_commit(&bar[q % F_SLOTS]);
                 }
-                // slot (q + 2) % 3 held chunk q - 1: free once its MMAs are done
+                // slot (q + 3) % 4 held chunk q - 1: free once its MMAs are done
                 if (q >= 1) wait_commit(q - 1);
-                if (q + 2 < Q) load_chunk(q + 2);
+                if (q + F_SLOTS - 1 < Q) load_chunk(q + F_SLOTS - 1);
             }
             if (!ok) break;
             wait_commit(q - 1);   // all MMAs of this layer are done
@@ -485,13 +531,15 @@ __global__ void __launch_bounds__(256, 1) k_mlp_fused(int rows, const float *__r
                     tmem_ld32(tb + ch * 32, v);
 #pragma unroll
                     for (int qq = 0; qq < 4; ++qq) {
+                        const float4 *b2 = reinterpret_cast<const float4 *>(sP + FP_B2) + ch * 8 + qq * 2;
+                        const float4 p0 = b2[0], p1 = b2[1];
+                        const float bb[8] = {p0.x, p0.y, p0.z, p0.w, p1.x, p1.y, p1.z, p1.w};
                         uint4 u;
-                        bf16 *hb = reinterpret_cast<bf16 *>(&u);
+                        uint32_t *hw = reinterpret_cast<uint32_t *>(&u);
 #pragma unroll
-                        for (int j = 0; j < 8; ++j) {
-                            const int col = ch * 32 + qq * 8 + j;
-                            hb[j] = __float2bfloat16_rn(fmaxf(v[qq * 8 + j] + __ldg(P + TRT_MLP_B2 + col), 0.f));
-                        }
+                        for (int j = 0; j < 8; j += 2)
+                            hw[j >> 1] = pack_bf16x2(fmaxf(v[qq * 8 + j] + bb[j], 0.f),
+                                                     fmaxf(v[qq * 8 + j + 1] + bb[j + 1], 0.f));
                         *reinterpret_cast<uint4 *>(myA + a_off(r, ch * 4 + qq)) = u;
                     }
                 }
@@ -503,14 +551,17 @@ __global__ void __launch_bounds__(256, 1) k_mlp_fused(int rows, const float *__r
                     float v[32];
                     tmem_ld32(tb + ch * 32, v);
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) {
-                        const int col = ch * 32 + j;
-                        dot = fmaf(fmaxf(v[j] + __ldg(P + TRT_MLP_B3 + col), 0.f),
-                                   __ldg(P + TRT_MLP_W4 + col), dot);
+                    for (int j4 = 0; j4 < 8; ++j4) {
+                        const float4 b3 = reinterpret_cast<const float4 *>(sP + FP_B3)[ch * 8 + j4];
+                        const float4 w4 = reinterpret_cast<const float4 *>(sP + FP_W4)[ch * 8 + j4];
+                        dot = fmaf(fmaxf(v[4 * j4] + b3.x, 0.f), w4.x, dot);
+                        dot = fmaf(fmaxf(v[4 * j4 + 1] + b3.y, 0.f), w4.y, dot);
+                        dot = fmaf(fmaxf(v[4 * j4 + 2] + b3.z, 0.f), w4.z, dot);
+                        dot = fmaf(fmaxf(v[4 * j4 + 3] + b3.w, 0.f), w4.w, dot);
                     }
                 }
                 const int row = row0 + tid;
-                if (row < rows) y[row] = 1.f / (1.f + __expf(-(dot + __ldg(P + TRT_MLP_B4))));
+                if (row < rows) y[row] = 1.f / (1.f + __expf(-(dot + sP[FP_B4])));
             }
         }
     }
@@ -541,6 +592,7 @@ cudaError_t mlp_fused(int rows, const float *x, const float *P, const bf16 *W, f
         cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
         attr = true;
     }
+    if (reinterpret_cast<uintptr_t>(P) & 15) return cudaErrorMisalignedAddress;   // float4 loads
     const int ntiles = (rows + 255) / 256;
     const int grid = std::max(1, std::min(ntiles, g_num_sms > 0 ? g_num_sms : 148));
     k_mlp_fused<<<grid, 256, F_SMEM, st>>>(rows, x, P, W, W + 65536, y);
@@ -761,6 +813,7 @@ int trt_mlp_forward_fused(int rows, const float *x, const float *params, const v
                           float *y, void *stream)
 {
     if (rows < 1 || !x || !params || !w16 || !y) return TRT_EINVAL;
+    if (reinterpret_cast<uintptr_t>(params) & 15) return TRT_EINVAL;
     return mlp_fused(rows, x, params, reinterpret_cast<const bf16 *>(w16), y,
                      reinterpret_cast<cudaStream_t>(stream)) == cudaSuccess
                ? TRT_OK

@@ -317,19 +317,19 @@ void host_group_B(int G, const double *edges, double T, double *B)
     }
 }
 
-// One thread per (group, cell); outputs [G][nx] (cell fastest, coalesced).
-// Chebyshev series sum_k c_k T_k(t) by Clenshaw's recurrence (c_0 already halved)
-__device__ inline double clenshaw(const double *__restrict__ c, double t)
+// One interval's series in the local coordinate t in [-1, 1], stored as monomial
+// coefficients a_0 .. a_{kTabNC-1} (converted from the Chebyshev fit when the tables are
+// built) and summed by Horner's rule: one FMA per term, half the FP64 operations of
+// Clenshaw's recurrence on the Chebyshev coefficients.  Over the tabulated functions the
+// conversion keeps the sum's rounding error within a factor ~2 of |p(t)| (the coefficients
+// of a fit that reaches FP64 accuracy in 12 terms decay much faster than the growth of the
+// Chebyshev polynomials' monomial coefficients).
+__device__ inline double horner(const double *__restrict__ a, double t)
 {
-    double b1 = 0.0, b2 = 0.0;
-    const double t2 = 2.0 * t;
+    double p = a[kTabNC - 1];
 #pragma unroll
-    for (int k = kTabNC - 1; k >= 1; --k) {
-        const double b0 = fma(t2, b1, c[k] - b2);
-        b2 = b1;
-        b1 = b0;
-    }
-    return fma(t, b1, c[0] - b2);
+    for (int k = kTabNC - 2; k >= 0; --k) p = fma(p, t, a[k]);
+    return p;
 }
 
 // sigma_E T^3 / (27 s) = (1 - e^{-w}) / [P]  and  sigma_R T^3 / (27 s) = [Nt] / [D] of one
@@ -351,16 +351,19 @@ __host__ __device__ inline void group_ratios(double T, double ea, double eb, con
     Rr = Ns / Ds;
 }
 
-// Per-cell terms of a block's 32 cells, staged once by the block's first row of threads:
-// T, 1/T, 1/T^3 and the table interval / local coordinate of ln T (m < 0: outside).
+// Per-cell terms of a block's 32 cells, staged once by one row (warp) of the block:
+// T, 1/T, 1/T^3 and the table interval / local coordinate of ln T (m < 0: outside).  The
+// staging row `sy` rotates with the block so that the staging's FP64 work (a logarithm and
+// a reciprocal per cell) lands on all four sub-partitions' FP64 pipes, not always on the
+// first.
 struct CellTerms {
     double T[32], iT[32], iT3[32], t[32];
     int m[32];
 };
 
-__device__ inline void stage_cells(const OpacityArgs &a, int i0, CellTerms &ct)
+__device__ inline void stage_cells(const OpacityArgs &a, int i0, CellTerms &ct, int sy)
 {
-    if (threadIdx.y == 0) {
+    if ((int)threadIdx.y == (sy & 3)) {
         const int tx = threadIdx.x, i = i0 + tx;
         if (i < a.nx) {
             const double Ti = a.T[i];
@@ -400,12 +403,12 @@ __device__ inline void opacity_body(const OpacityArgs &a, int i0, int g0, const 
     double sg, sR, em;
     const int m = ct.m[tx];
     if (m >= 0) {
-        // tabulated: three Chebyshev series in ln T on the cell's interval
+        // tabulated: three polynomials in ln T on the cell's interval
         const double t = ct.t[tx];
         const double *c = a.otab + ((size_t)g * kTabNI + m) * kTabNF * kTabNC;
-        sg = k27 * clenshaw(c, t) * iT3;
-        sR = k27 * clenshaw(c + kTabNC, t) * iT3;
-        em = k27 * kCB * Ti * mx.ex(clenshaw(c + 2 * kTabNC, t) - xa);
+        sg = k27 * horner(c, t) * iT3;
+        sR = k27 * horner(c + kTabNC, t) * iT3;
+        em = k27 * kCB * Ti * mx.ex(horner(c + 2 * kTabNC, t) - xa);
     } else {
         const double xb = binf ? 0.0 : eb * iT;
         double dPs, Ns, Ds, om;
@@ -438,7 +441,7 @@ __global__ void __launch_bounds__(256) k_opacity(OpacityArgs a)
     __shared__ double s_e2[32];
     __shared__ CellTerms ct;
     const Mx mx = stage_exp_table(s_e2);
-    stage_cells(a, blockIdx.x * 32, ct);
+    stage_cells(a, blockIdx.x * 32, ct, blockIdx.x + blockIdx.y);
     opacity_body(a, blockIdx.x * 32, blockIdx.y * 8, ct, mx);
 }
 
@@ -452,7 +455,7 @@ __global__ void __launch_bounds__(256) k_opacity_b(const int *__restrict__ meta,
         int s, bx, by;
         if (!bdecode(meta, N, b, s, bx, by)) break;
         const OpacityArgs a = xs[s];
-        stage_cells(a, bx * 32, ct);
+        stage_cells(a, bx * 32, ct, b);
         opacity_body(a, bx * 32, by * 8, ct, mx);
         __syncthreads();   // the cell terms are restaged by the next work item
     }
@@ -478,8 +481,9 @@ cudaError_t launch_fastmath(int n, const double *x, double *ex, double *rc, cuda
     return cudaGetLastError();
 }
 
-// Tables: one thread per (group, interval) evaluates the two ratios directly at the
-// interval's kTabNC Chebyshev points in ln T and stores their Chebyshev coefficients.
+// Tables: one thread per (group, interval) evaluates the three series directly at the
+// interval's kTabNC Chebyshev points in ln T, fits their Chebyshev coefficients and stores
+// them converted to monomial coefficients in the interval's coordinate.
 __global__ void k_otab_build(int G, const double *__restrict__ edges, double *__restrict__ tab)
 {
     __shared__ double s_e2[32];
@@ -497,7 +501,7 @@ __global__ void k_otab_build(int G, const double *__restrict__ edges, double *__
         // emission factor: e_g = 27 s C_B T e^{-xa} (1 - e^{-w}), w = (nu_b - nu_a)/T
         fe[j] = binf ? 0.0 : log(-expm1(-(edges[g + 1] - edges[g]) / T));
     }
-    double *c = tab + (size_t)id * kTabNF * kTabNC;
+    double ch[kTabNF][kTabNC];   // Chebyshev coefficients (c_0 halved)
     for (int k = 0; k < kTabNC; ++k) {
         double sa = 0.0, sr = 0.0, se = 0.0;
         for (int j = 0; j < kTabNC; ++j) {
@@ -507,10 +511,27 @@ __global__ void k_otab_build(int G, const double *__restrict__ edges, double *__
             se = fma(fe[j], ck, se);
         }
         const double sc = (k == 0 ? 1.0 : 2.0) / kTabNC;
-        c[k] = sa * sc;
-        c[kTabNC + k] = sr * sc;
-        c[2 * kTabNC + k] = se * sc;
+        ch[0][k] = sa * sc;
+        ch[1][k] = sr * sc;
+        ch[2][k] = se * sc;
     }
+    // monomial coefficients a_j = sum_k c_k [t^j] T_k(t), the highest k first; the
+    // coefficients of T_k (integers below 2^11, exact) from T_{k+1} = 2 t T_k - T_{k-1}
+    double Tc[kTabNC][kTabNC];
+    for (int k = 0; k < kTabNC; ++k)
+        for (int j = 0; j < kTabNC; ++j) Tc[k][j] = 0.0;
+    Tc[0][0] = 1.0;
+    Tc[1][1] = 1.0;
+    for (int k = 2; k < kTabNC; ++k)
+        for (int j = 0; j < kTabNC; ++j)
+            Tc[k][j] = (j > 0 ? 2.0 * Tc[k - 1][j - 1] : 0.0) - Tc[k - 2][j];
+    double *c = tab + (size_t)id * kTabNF * kTabNC;
+    for (int f = 0; f < kTabNF; ++f)
+        for (int j = 0; j < kTabNC; ++j) {
+            double aj = 0.0;
+            for (int k = kTabNC - 1; k >= j; --k) aj = fma(ch[f][k], Tc[k][j], aj);
+            c[f * kTabNC + j] = aj;
+        }
 }
 
 cudaError_t launch_otab_build(const Problem &p)

@@ -319,6 +319,33 @@ def test_restrict_subnormal_weights(trt, orc, n_from, n_to):
         assert rel(got[k], ref[k]) < 1e-9, k
 
 
+@pytest.mark.parametrize("n_from,n_to,fine", [(256, 1, False), (1024, 4, True), (64, 1, True)])
+def test_restrict_zero_weights(trt, orc, n_from, n_to, fine):
+    """A coarse group with no energy in some cells and no flux on the faces between them:
+    the weighted means fall back to the members' plain means (the two-stage path forms
+    them from the members only in this case)."""
+    nx = 70
+    r = W.rng(4700 + n_from + n_to)
+    h = W.random_h(r, nx)
+    lv = random_level(r, n_from, nx, eta=not fine)
+    src = dict(lv)
+    if fine:
+        src["sigR"] = np.exp(r.uniform(-3, 3, (n_from, nx)))
+        lv["sigR"] = orc.fine_face_sigR(h, src["sigR"])
+    sol = oracle_level_solve(orc, h, 2e-3, lv)
+    m = n_from // n_to
+    sol["E"][:m, 30:36] = 0.0          # cells 30..35 of coarse group 0: no energy
+    sol["F"][:m, 31:36] = 0.0          # faces 31..35 between them: no flux, E_L + E_R = 0
+    s = solver(trt, nx=nx, N=2, G=max(n_from, 3), h=h, levels=[max(n_from, 3), 1])
+    src.update(sol)
+    got = {k: v.cpu().numpy() for k, v in s.k_restrict(src, n_to, fine=fine).items()}
+    cmap = np.arange(n_from) // m
+    ref, Esum = orc.restrict(h, lv, sol, cmap, n_to)
+    for k in ("phi", "sig", "sigR", "phib0", "phibX", "C0", "CX", "Ein0", "EinX", "Fin0", "FinX"):
+        assert rel(got[k], ref[k]) < 1e-12, k
+    assert np.array_equal(got["Esum"][0, 30:36], np.zeros(6))
+
+
 @pytest.mark.parametrize("nx,have_prev", [(1, 0), (30, 1), (500, 0), (1000, 1)])
 def test_grey_newton_parity(trt, orc, nx, have_prev):
     r = W.rng(5000 + nx)
