@@ -47,8 +47,10 @@ extern "C" {
 #define TRT_MLP_W4 132608   /* [256]                     */
 #define TRT_MLP_B4 132864   /* [1]                       */
 #define TRT_MLP_NPARAM 132868
-/* BF16 copies made by trt_mlp_refresh: W2, W3, W2^T, W3^T, 65536 each */
-#define TRT_MLP_W16_ELEMS (4 * 65536)
+/* BF16 copies made by trt_mlp_refresh, 65536 each: W2, W3, W2^T, W3^T, and W2, W3 again
+ * in the order trt_mlp_forward_fused streams them (per 32-wide K chunk c, 8-wide K group
+ * kg and output n: element (n, k = 32 c + 8 kg + j) at 8192 c + 2048 kg + 8 n + j) */
+#define TRT_MLP_W16_ELEMS (6 * 65536)
 
 /* C = A B^T on the tensor cores (tcgen05.mma kind::f16, BF16 inputs, FP32 accumulation
  * in tensor memory), with a fused epilogue applied per element:
@@ -66,7 +68,8 @@ int trt_gemm_bf16(int M, int N, int K, const void *A, const void *B, const float
 /* Device scratch (bytes) for trt_mlp_forward / trt_mlp_grad over `rows` rows. */
 size_t trt_mlp_scratch_bytes(int rows, int training);
 
-/* BF16 copies of W2 and W3 (and their transposes) from the FP32 parameters. */
+/* BF16 copies of W2 and W3 (their transposes and their streaming images) from the FP32
+ * parameters. */
 int trt_mlp_refresh(const float *params, void *w16, void *stream);
 
 /* Inference: x [rows][3] FP32 -> y [rows] FP32 (sigmoid outputs).  rows >= 1. */

@@ -344,53 +344,121 @@ __global__ void __launch_bounds__(128) k_gemm(int M, int N, int K, const bf16 *_
 }
 
 // ---- fused inference: the whole network in one persistent kernel ----
-// One CTA per SM; per iteration 256 rows as two 128-row tiles.  Layer 1 (3 inputs) on CUDA
-// cores writes both tiles' h1 (BF16) into shared memory in the K-major core-matrix layout;
-// the two 256 x 256 layers run on tcgen05 with the two tiles' 128 x 256 FP32 accumulators
-// in all 512 tensor-memory columns; their weights stream through a four-slot ring of
-// 32-wide K chunks (16 KB each) shared by both tiles; the ReLU epilogue of layer 2 writes
-// h2 back over h1; the epilogue of layer 3 folds the sigmoid head.  Activations never
-// leave shared memory, and neither do the small parameters (layer-1 weights, the biases,
-// the head), copied there once per CTA: the threads of a CTA read them in lockstep
-// (broadcast), which from global memory cost an L1 miss per load at this shared-memory
-// carve-out.  Chunk q of the weight stream (layer (q / 8) % 2, K chunk q % 8) sits in slot
-// q % 4; its MMAs commit to the slot's mbarrier; chunk q + 3 is copied once the MMAs of
-// chunk q - 1 (same slot) have completed, so three copies are in flight while the MMAs of
-// chunk q run.
+// One CTA per SM, 288 threads: two groups of four warps and one control warp.  Each
+// iteration takes 256 rows; group g (warps 4g .. 4g+3, thread = row = tensor-memory lane)
+// owns rows 128 g .. 128 g + 127 of it, its activation tile A_g in shared memory and its
+// 128 x 256 FP32 accumulator in tensor-memory columns 256 g .. 256 g + 255.  The control
+// thread (warp 8, lane 0) streams the weights and issues every MMA, in the order
+//   layer 2 of group 0, layer 2 of group 1, layer 3 of group 0, layer 3 of group 1,
+// so that while the tensor core multiplies for one group the other group's warps run its
+// CUDA-core phase (layer 1, a ReLU/bias epilogue, the sigmoid head): the two groups work
+// half a period apart and the MMAs of one hide the epilogues of the other.
+//   Weights: 32-wide K chunks (16 KB, 256 rows x 32 K of W2 or W3) through a four-slot
+// ring.  trt_mlp_refresh stores each chunk contiguously in the order the tensor core
+// reads it (core matrices of 8 rows x 16 bytes; K groups 4096 bytes apart, row groups 128
+// bytes apart), so one cp.async.bulk of 16 KB moves a chunk and completes on the slot's
+// `full` mbarrier; the MMAs reading a slot commit to its `empty` mbarrier, which releases
+// it for the chunk S later.  Every chunk is used by one group's layer, so each weight is
+// read from L2 twice per 256 rows.
+//   Hand-offs: a group arrives on act[g] (128 arrivals) when A_g holds the next layer's
+// input (after a proxy fence: the MMAs read it through the async proxy); the control
+// thread commits the last MMA of a layer to acc[g], which the group waits on before it
+// reads the accumulator.  Small parameters (layer-1 weights, biases, head) sit in shared
+// memory.  Every mbarrier wait is bounded (one second); a wait that runs out stops the
+// kernel's work and sets the device error flag (trt_mlp_status).
 constexpr int FA_BYTES = 128 * 256 * 2;   // one activation tile
 constexpr int FK = 32;                    // K width of a weight chunk
 constexpr int FNC = 256 / FK;             // chunks per layer
 constexpr int FW_BYTES = 256 * FK * 2;    // one weight chunk
 constexpr int F_SLOTS = 4;
-constexpr uint32_t FW_SBO = FK / 8 * 128;   // weight chunk: row groups 512 bytes apart
-// small parameters in shared memory: W1 [256][3], b1, b2, b3, w4, b4 (1793 floats)
+constexpr uint32_t FW_LBO = 4096, FW_SBO = 128;   // weight chunk: K groups, row groups
+// small parameters in shared memory: W1^T [3][256], b1, b2, b3, w4, b4 (1793 floats)
 constexpr int FP_W1 = 0, FP_B1 = 768, FP_B2 = 1024, FP_B3 = 1280, FP_W4 = 1536, FP_B4 = 1792;
 constexpr int FP_BYTES = 1796 * 4;
-constexpr int F_SMEM = 2 * FA_BYTES + F_SLOTS * FW_BYTES + FP_BYTES + 256;   // 204,048 bytes
+constexpr int F_NBAR = 2 * F_SLOTS + 4;   // full[S], empty[S], act[2], acc[2]
+constexpr int F_SMEM = 2 * FA_BYTES + F_SLOTS * FW_BYTES + FP_BYTES + 8 * F_NBAR + 16;
 constexpr uint32_t FA_SBO = 4096;         // activation tiles: 32 K groups per row group
+constexpr int F_THREADS = 288;
 
-__global__ void __launch_bounds__(256, 1) k_mlp_fused(int rows, const float *__restrict__ x,
-                                                      const float *__restrict__ P,
-                                                      const bf16 *__restrict__ W2,
-                                                      const bf16 *__restrict__ W3,
-                                                      float *__restrict__ y)
+__device__ inline void mbar_init_n(uint64_t *bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(bar)), "r"(count));
+}
+__device__ inline void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(bar)) : "memory");
+}
+__device__ inline void mbar_expect(uint64_t *bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+// packed FP32 pairs (Blackwell f32x2 arithmetic: two lanes' worth of FP32 per instruction)
+__device__ inline float2 fma2(float2 a, float2 b, float2 c)
+{
+    float2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;"
+        : "=l"(*reinterpret_cast<unsigned long long *>(&d))
+        : "l"(*reinterpret_cast<const unsigned long long *>(&a)),
+          "l"(*reinterpret_cast<const unsigned long long *>(&b)),
+          "l"(*reinterpret_cast<const unsigned long long *>(&c)));
+    return d;
+}
+__device__ inline float2 add2(float2 a, float2 b)
+{
+    float2 d;
+    asm("add.rn.f32x2 %0, %1, %2;"
+        : "=l"(*reinterpret_cast<unsigned long long *>(&d))
+        : "l"(*reinterpret_cast<const unsigned long long *>(&a)),
+          "l"(*reinterpret_cast<const unsigned long long *>(&b)));
+    return d;
+}
+// relu of two FP32 values rounded to BF16 (nearest even) in one word, v.x in the low half:
+// rounding keeps the sign, so rounding after the clamp equals clamping after rounding
+__device__ inline uint32_t relu_bf16x2(float2 v)
+{
+    uint32_t d;
+    asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(v.y), "f"(v.x));
+    return d;
+}
+
+// one contiguous bulk copy global -> shared, completing on an mbarrier
+__device__ inline void bulk_copy(void *dst, const void *src, unsigned bytes, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            su32(dst)),
+        "l"(src), "r"(bytes), "r"(su32(bar))
+        : "memory");
+}
+
+__global__ void __launch_bounds__(F_THREADS, 1) k_mlp_fused(int rows, const float *__restrict__ x,
+                                                            const float *__restrict__ P,
+                                                            const bf16 *__restrict__ Wimg,
+                                                            float *__restrict__ y)
 {
     extern __shared__ __align__(1024) unsigned char sm[];
-    unsigned char *sA0 = sm, *sA1 = sm + FA_BYTES;
     unsigned char *sW = sm + 2 * FA_BYTES;   // F_SLOTS weight chunks
     float *sP = reinterpret_cast<float *>(sW + F_SLOTS * FW_BYTES);
     uint64_t *bar = reinterpret_cast<uint64_t *>(reinterpret_cast<unsigned char *>(sP) + FP_BYTES);
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(bar + F_SLOTS);
+    uint64_t *full = bar, *empty = bar + F_SLOTS, *act = bar + 2 * F_SLOTS, *acc = act + 2;
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(bar + F_NBAR);
     int *sfail = reinterpret_cast<int *>(tslot + 1);
 
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int half = tid >> 7, r = tid & 127;   // tile and row (= tensor-memory lane)
+    const int tid = threadIdx.x, warp = tid >> 5;
     const int ntiles = (rows + 255) / 256;
     const int mine = (int)blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
-    const int Q = 2 * FNC * mine;   // weight chunks this CTA consumes
 
     if (tid == 0) {
-        for (int k = 0; k < F_SLOTS; ++k) mbar_init(&bar[k], 1);
+        for (int k = 0; k < F_SLOTS; ++k) {
+            mbar_init_n(&full[k], 1);
+            mbar_init_n(&empty[k], 1);
+        }
+        for (int g = 0; g < 2; ++g) {
+            mbar_init_n(&act[g], 128);
+            mbar_init_n(&acc[g], 1);
+        }
         *sfail = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -400,177 +468,192 @@ __global__ void __launch_bounds__(256, 1) k_mlp_fused(int rows, const float *__r
                      "r"(512));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
-    {   // small parameters (16-byte aligned float4 runs: W1 + b1, b2, b3 + w4)
-        const float4 *g = reinterpret_cast<const float4 *>(P);
+    if (tid < 256) {   // small parameters (W1 transposed; float4 runs b1, b2, b3 + w4)
+        const float4 *gp = reinterpret_cast<const float4 *>(P);
         float4 *d = reinterpret_cast<float4 *>(sP);
-        d[tid] = __ldg(g + TRT_MLP_W1 / 4 + tid);                                // W1, b1
-        if (tid < 64) d[FP_B2 / 4 + tid] = __ldg(g + TRT_MLP_B2 / 4 + tid);      // b2
-        if (tid < 128) d[FP_B3 / 4 + tid] = __ldg(g + TRT_MLP_B3 / 4 + tid);     // b3, w4
+        for (int k = 0; k < 3; ++k) sP[FP_W1 + k * 256 + tid] = __ldg(P + TRT_MLP_W1 + 3 * tid + k);
+        if (tid < 64) d[FP_B1 / 4 + tid] = __ldg(gp + TRT_MLP_B1 / 4 + tid);     // b1
+        if (tid < 64) d[FP_B2 / 4 + tid] = __ldg(gp + TRT_MLP_B2 / 4 + tid);     // b2
+        if (tid < 128) d[FP_B3 / 4 + tid] = __ldg(gp + TRT_MLP_B3 / 4 + tid);    // b3, w4
         if (tid == 0) sP[FP_B4] = __ldg(P + TRT_MLP_B4);
     }
     tc_before();
     __syncthreads();
     tc_after();
     const uint32_t tmem = *tslot;
-
-    // chunk q of the weight stream -> slot q % 4 (4 pieces of 16 bytes per thread)
-    int issued = 0;
-    auto load_chunk = [&](int q) {
-        const bf16 *W = ((q / FNC) & 1) ? W3 : W2;
-        const int c = q % FNC;
-        unsigned char *dst = sW + (q % F_SLOTS) * FW_BYTES;
-        ++issued;
-#pragma unroll
-        for (int j = 0; j < FW_BYTES / 16 / 256; ++j) {
-            const int p = tid + 256 * j;
-            const int r8 = p & 7, ki = (p >> 3) & (FK / 8 - 1), ni = p / (8 * (FK / 8));
-            cp16(dst + p * 16, W + (size_t)(ni * 8 + r8) * 256 + c * FK + ki * 8, 16u);
-        }
-        cp_commit();
-    };
-    int last_waited = -1;
     bool ok = true;
-    auto wait_commit = [&](int q) {   // the MMAs of chunk q have completed
-        if (q <= last_waited) return;
-        if (!mbar_wait(&bar[q % F_SLOTS], (q / F_SLOTS) & 1)) *sfail = 1;
-        last_waited = q;
-    };
-    // A tile element (row, k) offset: core matrix (row / 8, k / 8), row % 8 at 16 bytes
-    auto a_off = [](int row, int k8) { return (row >> 3) * FA_SBO + k8 * 128 + (row & 7) * 16; };
 
-    for (int k = 0; k < F_SLOTS - 1 && k < Q; ++k) load_chunk(k);
-    int q = 0;
-    for (int it = 0; it < mine && ok; ++it) {
-        const int row0 = ((int)blockIdx.x + it * (int)gridDim.x) * 256;
-        unsigned char *myA = half ? sA1 : sA0;
-        // ---- layer 1: h1 = relu(W1 x + b1) for row row0 + tid ----
-        {
-            const int row = row0 + tid;
-            float x0 = 0.f, x1 = 0.f, x2 = 0.f;
-            const bool rv = row < rows;
-            if (rv) {
-                x0 = x[3 * row];
-                x1 = x[3 * row + 1];
-                x2 = x[3 * row + 2];
-            }
-            // 8 columns per step: their 24 weights and 8 biases as 8 broadcast float4
-            // reads of shared memory, the 8 outputs packed pairwise to BF16
-            const float4 *pw = reinterpret_cast<const float4 *>(sP + FP_W1);
-            const float4 *pb = reinterpret_cast<const float4 *>(sP + FP_B1);
-#pragma unroll 2
-            for (int k8 = 0; k8 < 32; ++k8) {
-                float w[24], bb[8];
-#pragma unroll
-                for (int j = 0; j < 6; ++j) {
-                    const float4 t = pw[k8 * 6 + j];
-                    w[4 * j] = t.x; w[4 * j + 1] = t.y; w[4 * j + 2] = t.z; w[4 * j + 3] = t.w;
-                }
-#pragma unroll
-                for (int j = 0; j < 2; ++j) {
-                    const float4 t = pb[k8 * 2 + j];
-                    bb[4 * j] = t.x; bb[4 * j + 1] = t.y; bb[4 * j + 2] = t.z; bb[4 * j + 3] = t.w;
-                }
-                uint4 u;
-                uint32_t *hw = reinterpret_cast<uint32_t *>(&u);
-#pragma unroll
-                for (int j = 0; j < 8; j += 2) {
-                    float a0 = bb[j], a1 = bb[j + 1];
-                    a0 = fmaf(w[3 * j], x0, a0);
-                    a0 = fmaf(w[3 * j + 1], x1, a0);
-                    a0 = fmaf(w[3 * j + 2], x2, a0);
-                    a1 = fmaf(w[3 * j + 3], x0, a1);
-                    a1 = fmaf(w[3 * j + 4], x1, a1);
-                    a1 = fmaf(w[3 * j + 5], x2, a1);
-                    hw[j >> 1] = pack_bf16x2(rv ? fmaxf(a0, 0.f) : 0.f, rv ? fmaxf(a1, 0.f) : 0.f);
-                }
-                *reinterpret_cast<uint4 *>(myA + a_off(r, k8)) = u;
-            }
-            fence_async_smem();
-        }
-        for (int layer = 0; layer < 2 && ok; ++layer) {
-            for (int c = 0; c < FNC; ++c, ++q) {
-                // chunk q has landed: issued - 1 - q later groups may still be in flight
-                const int later = issued - 1 - q;
-                if (later >= 2)
-                    cp_wait<2>();
-                else if (later == 1)
-                    cp_wait<1>();
-                else
-                    cp_wait<0>();
-                fence_async_smem();
-                tc_before();
-                __syncthreads();
-                if (*sfail) { ok = false; break; }
-                if (tid == 0) {
+    if (warp == 8) {
+        // ---------------- control thread: weight stream and MMAs ----------------
+        if ((tid & 31) == 0) {
+            const int Q = 4 * FNC * mine;   // chunks: 4 layer-jobs of FNC chunks per iteration
+            int produced = 0;
+            auto produce = [&](int q) {     // chunk q: job q / FNC, K chunk q % FNC
+                const int layer = (q / FNC) % 4 >= 2 ? 1 : 0;
+                const int c = q % FNC;
+                mbar_expect(&full[q % F_SLOTS], FW_BYTES);
+                bulk_copy(sW + (q % F_SLOTS) * FW_BYTES, Wimg + layer * 65536 + c * (FW_BYTES / 2),
+                          FW_BYTES, &full[q % F_SLOTS]);
+                ++produced;
+            };
+            for (int q = 0; q < F_SLOTS && q < Q; ++q) produce(q);
+            unsigned pact = 0;   // bit g: parity of act[g]'s next phase
+            int q = 0;
+            for (int it = 0; it < mine && ok; ++it) {
+                for (int job = 0; job < 4 && ok; ++job) {
+                    const int g = job & 1;
+                    if (!mbar_wait(&act[g], (pact >> g) & 1u)) { ok = false; break; }
+                    pact ^= 1u << g;
                     tc_after();
-                    const uint32_t w0 = su32(sW + (q % F_SLOTS) * FW_BYTES);
-                    const uint32_t a0 = su32(sA0), a1 = su32(sA1);
+                    const uint32_t a0 = su32(sm + g * FA_BYTES);
+                    const uint32_t d = tmem + (uint32_t)(g * 256);
+                    for (int c = 0; c < FNC; ++c, ++q) {
+                        if (!mbar_wait(&full[q % F_SLOTS], (q / F_SLOTS) & 1)) { ok = false; break; }
+                        const uint32_t w0 = su32(sW + (q % F_SLOTS) * FW_BYTES);
 #pragma unroll
-                    for (int kk = 0; kk < FK / 16; ++kk) {
-                        const uint64_t bd = sdesc(w0 + kk * 2 * LBO, LBO, FW_SBO);
-                        const uint32_t ka = (c * (FK / 8) + kk * 2) * 128;
-                        umma(tmem, sdesc(a0 + ka, LBO, FA_SBO), bd, (c | kk) != 0);
-                        umma(tmem + 256, sdesc(a1 + ka, LBO, FA_SBO), bd, (c | kk) != 0);
+                        for (int kk = 0; kk < FK / 16; ++kk) {
+                            const uint64_t bd = sdesc(w0 + kk * 2 * FW_LBO, FW_LBO, FW_SBO);
+                            const uint32_t ka = (c * (FK / 8) + kk * 2) * 128;
+                            umma(d, sdesc(a0 + ka, LBO, FA_SBO), bd, (c | kk) != 0);
+                        }
+                        umma_commit(&empty[q % F_SLOTS]);
+                        // the slot of chunk q - 1 takes chunk q - 1 + S once its MMAs are done
+                        if (q >= 1 && q - 1 + F_SLOTS < Q) {
+                            if (!mbar_wait(&empty[(q - 1) % F_SLOTS], ((q - 1) / F_SLOTS) & 1)) {
+                                ok = false;
+                                break;
+                            }
+                            produce(q - 1 + F_SLOTS);
+                        }
                     }
-                    umma_commit(&bar[q % F_SLOTS]);
+                    if (!ok) break;
+                    umma_commit(&acc[g]);   // the group's accumulator is complete
                 }
-                // slot (q + 3) % 4 held chunk q - 1: free once its MMAs are done
-                if (q >= 1) wait_commit(q - 1);
-                if (q + F_SLOTS - 1 < Q) load_chunk(q + F_SLOTS - 1);
             }
-            if (!ok) break;
-            wait_commit(q - 1);   // all MMAs of this layer are done
-            ok = !__syncthreads_or(*sfail);
-            if (!ok) break;
-            tc_after();
-            const uint32_t tb = tmem + ((uint32_t)((warp & 3) * 32) << 16) + half * 256;
-            if (layer == 0) {
-                // ---- epilogue 2: h2 = relu(acc + b2) over h1 ----
-                for (int ch = 0; ch < 8; ++ch) {
-                    float v[32];
-                    tmem_ld32(tb + ch * 32, v);
-#pragma unroll
-                    for (int qq = 0; qq < 4; ++qq) {
-                        const float4 *b2 = reinterpret_cast<const float4 *>(sP + FP_B2) + ch * 8 + qq * 2;
-                        const float4 p0 = b2[0], p1 = b2[1];
-                        const float bb[8] = {p0.x, p0.y, p0.z, p0.w, p1.x, p1.y, p1.z, p1.w};
-                        uint4 u;
-                        uint32_t *hw = reinterpret_cast<uint32_t *>(&u);
-#pragma unroll
-                        for (int j = 0; j < 8; j += 2)
-                            hw[j >> 1] = pack_bf16x2(fmaxf(v[qq * 8 + j] + bb[j], 0.f),
-                                                     fmaxf(v[qq * 8 + j + 1] + bb[j + 1], 0.f));
-                        *reinterpret_cast<uint4 *>(myA + a_off(r, ch * 4 + qq)) = u;
-                    }
-                }
-                fence_async_smem();
-            } else {
-                // ---- epilogue 3 and the head: y = sigmoid(w4 . relu(acc + b3) + b4) ----
-                float dot = 0.f;
-                for (int ch = 0; ch < 8; ++ch) {
-                    float v[32];
-                    tmem_ld32(tb + ch * 32, v);
-#pragma unroll
-                    for (int j4 = 0; j4 < 8; ++j4) {
-                        const float4 b3 = reinterpret_cast<const float4 *>(sP + FP_B3)[ch * 8 + j4];
-                        const float4 w4 = reinterpret_cast<const float4 *>(sP + FP_W4)[ch * 8 + j4];
-                        dot = fmaf(fmaxf(v[4 * j4] + b3.x, 0.f), w4.x, dot);
-                        dot = fmaf(fmaxf(v[4 * j4 + 1] + b3.y, 0.f), w4.y, dot);
-                        dot = fmaf(fmaxf(v[4 * j4 + 2] + b3.z, 0.f), w4.z, dot);
-                        dot = fmaf(fmaxf(v[4 * j4 + 3] + b3.w, 0.f), w4.w, dot);
-                    }
-                }
-                const int row = row0 + tid;
-                if (row < rows) y[row] = 1.f / (1.f + __expf(-(dot + sP[FP_B4])));
+            if (!ok) {
+                *sfail = 1;
+                // let copies in flight land before the CTA exits (bounded)
+                for (int r = q; r < produced; ++r) mbar_wait(&full[r % F_SLOTS], (r / F_SLOTS) & 1);
             }
         }
-    }
-    if (!ok) {
-        cp_wait<0>();
-        if (tid == 0) atomicExch(&g_mlp_err, TRT_ETIMEOUT);
+    } else {
+        // ---------------- a group of four warps: 128 rows ----------------
+        const int g = warp >> 2, r = tid & 127;
+        unsigned char *myA = sm + g * FA_BYTES;
+        const uint32_t tb = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(g * 256);
+        // A tile element (row, k) offset: core matrix (row / 8, k / 8), row % 8 at 16 bytes
+        auto a_off = [](int row, int k8) { return (row >> 3) * FA_SBO + k8 * 128 + (row & 7) * 16; };
+        unsigned pacc = 0;
+        auto wait_acc = [&]() {
+            if (!mbar_wait(&acc[g], pacc)) {
+                *sfail = 1;
+                return false;
+            }
+            pacc ^= 1u;
+            tc_after();
+            return true;
+        };
+        auto hand_off = [&]() {   // A_g holds the next layer's input
+            tc_before();
+            fence_async_smem();
+            mbar_arrive(&act[g]);
+        };
+        float xn0 = 0.f, xn1 = 0.f, xn2 = 0.f;   // this tile's inputs (0 past the last row)
+        {
+            const int row = (int)blockIdx.x * 256 + g * 128 + r;
+            if (mine > 0 && row < rows) {
+                xn0 = x[3 * row];
+                xn1 = x[3 * row + 1];
+                xn2 = x[3 * row + 2];
+            }
+        }
+        for (int it = 0; it < mine && ok; ++it) {
+            const int row = ((int)blockIdx.x + it * (int)gridDim.x) * 256 + g * 128 + r;
+            const bool rv = row < rows;
+            // ---- layer 1: h1 = relu(W1 x + b1) ----
+            {
+                const float2 X0 = make_float2(xn0, xn0), X1 = make_float2(xn1, xn1),
+                             X2 = make_float2(xn2, xn2);
+                // 8 columns per step: W1^T rows and b1 as broadcast float4 reads of shared
+                // memory, pairs of columns by packed FP32 FMAs, ReLU fused in the BF16 pack
+                const float4 *pw0 = reinterpret_cast<const float4 *>(sP + FP_W1);
+                const float4 *pw1 = reinterpret_cast<const float4 *>(sP + FP_W1 + 256);
+                const float4 *pw2 = reinterpret_cast<const float4 *>(sP + FP_W1 + 512);
+                const float4 *pb = reinterpret_cast<const float4 *>(sP + FP_B1);
+#pragma unroll 2
+                for (int k8 = 0; k8 < 32; ++k8) {
+                    uint4 u;
+                    uint32_t *hw = reinterpret_cast<uint32_t *>(&u);
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const float4 b = pb[k8 * 2 + h], w0 = pw0[k8 * 2 + h],
+                                     w1 = pw1[k8 * 2 + h], w2 = pw2[k8 * 2 + h];
+                        float2 a = make_float2(b.x, b.y), c = make_float2(b.z, b.w);
+                        a = fma2(make_float2(w0.x, w0.y), X0, a);
+                        c = fma2(make_float2(w0.z, w0.w), X0, c);
+                        a = fma2(make_float2(w1.x, w1.y), X1, a);
+                        c = fma2(make_float2(w1.z, w1.w), X1, c);
+                        a = fma2(make_float2(w2.x, w2.y), X2, a);
+                        c = fma2(make_float2(w2.z, w2.w), X2, c);
+                        hw[2 * h] = relu_bf16x2(a);
+                        hw[2 * h + 1] = relu_bf16x2(c);
+                    }
+                    *reinterpret_cast<uint4 *>(myA + a_off(r, k8)) = u;
+                }
+            }
+            // the next tile's inputs, in flight during the two layers
+            {
+                const int nrow = row + (int)gridDim.x * 256;
+                if (it + 1 < mine && nrow < rows) {
+                    xn0 = x[3 * nrow];
+                    xn1 = x[3 * nrow + 1];
+                    xn2 = x[3 * nrow + 2];
+                }
+            }
+            hand_off();
+            if (!(ok = wait_acc())) break;
+            // ---- epilogue of layer 2: h2 = relu(acc + b2) over h1 ----
+            for (int ch = 0; ch < 8; ++ch) {
+                float v[32];
+                tmem_ld32(tb + ch * 32, v);
+#pragma unroll
+                for (int qq = 0; qq < 4; ++qq) {
+                    const float4 *b2 = reinterpret_cast<const float4 *>(sP + FP_B2) + ch * 8 + qq * 2;
+                    const float4 p0 = b2[0], p1 = b2[1];
+                    const float *vq = v + qq * 8;
+                    uint4 u;
+                    u.x = relu_bf16x2(add2(make_float2(vq[0], vq[1]), make_float2(p0.x, p0.y)));
+                    u.y = relu_bf16x2(add2(make_float2(vq[2], vq[3]), make_float2(p0.z, p0.w)));
+                    u.z = relu_bf16x2(add2(make_float2(vq[4], vq[5]), make_float2(p1.x, p1.y)));
+                    u.w = relu_bf16x2(add2(make_float2(vq[6], vq[7]), make_float2(p1.z, p1.w)));
+                    *reinterpret_cast<uint4 *>(myA + a_off(r, ch * 4 + qq)) = u;
+                }
+            }
+            hand_off();
+            if (!(ok = wait_acc())) break;
+            // ---- epilogue of layer 3 and the head: y = sigmoid(w4 . relu(acc + b3) + b4) ----
+            float2 dot = make_float2(0.f, 0.f);   // even and odd columns
+            for (int ch = 0; ch < 8; ++ch) {
+                float v[32];
+                tmem_ld32(tb + ch * 32, v);
+#pragma unroll
+                for (int j4 = 0; j4 < 8; ++j4) {
+                    const float4 b3 = reinterpret_cast<const float4 *>(sP + FP_B3)[ch * 8 + j4];
+                    const float4 w4 = reinterpret_cast<const float4 *>(sP + FP_W4)[ch * 8 + j4];
+                    float2 a = add2(make_float2(v[4 * j4], v[4 * j4 + 1]), make_float2(b3.x, b3.y));
+                    float2 c = add2(make_float2(v[4 * j4 + 2], v[4 * j4 + 3]), make_float2(b3.z, b3.w));
+                    a = make_float2(fmaxf(a.x, 0.f), fmaxf(a.y, 0.f));
+                    c = make_float2(fmaxf(c.x, 0.f), fmaxf(c.y, 0.f));
+                    dot = fma2(a, make_float2(w4.x, w4.y), dot);
+                    dot = fma2(c, make_float2(w4.z, w4.w), dot);
+                }
+            }
+            if (rv) y[row] = 1.f / (1.f + __expf(-((dot.x + dot.y) + sP[FP_B4])));
+        }
     }
     tc_before();
     __syncthreads();
+    if (*sfail && tid == 0) atomicExch(&g_mlp_err, TRT_ETIMEOUT);
     if (warp == 0) {
         tc_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
@@ -595,7 +678,7 @@ cudaError_t mlp_fused(int rows, const float *x, const float *P, const bf16 *W, f
     if (reinterpret_cast<uintptr_t>(P) & 15) return cudaErrorMisalignedAddress;   // float4 loads
     const int ntiles = (rows + 255) / 256;
     const int grid = std::max(1, std::min(ntiles, g_num_sms > 0 ? g_num_sms : 148));
-    k_mlp_fused<<<grid, 256, F_SMEM, st>>>(rows, x, P, W, W + 65536, y);
+    k_mlp_fused<<<grid, F_THREADS, F_SMEM, st>>>(rows, x, P, W + 4 * 65536, y);
     return cudaGetLastError();
 }
 
@@ -691,7 +774,8 @@ __global__ void k_dw1(int R, const float *__restrict__ d1, const float *__restri
     }
 }
 
-// W2, W3 (BF16) and their transposes from the FP32 master parameters
+// W2, W3 (BF16), their transposes and their streaming images (the 16 KB chunks of the
+// fused kernel, each laid out as it lands in shared memory) from the FP32 parameters
 __global__ void k_refresh(const float *__restrict__ P, bf16 *__restrict__ w16)
 {
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;   // 2 x 65536
@@ -701,6 +785,8 @@ __global__ void k_refresh(const float *__restrict__ P, bf16 *__restrict__ w16)
     const bf16 b = __float2bfloat16_rn(v);
     w16[layer * 65536 + o * 256 + i] = b;                 // W [out][in]
     w16[(2 + layer) * 65536 + i * 256 + o] = b;           // W^T [in][out]
+    const int c = i >> 5, kg = (i >> 3) & 3, j = i & 7;   // chunk, K group, element
+    w16[(4 + layer) * 65536 + c * 8192 + kg * 2048 + o * 8 + j] = b;
 }
 
 __global__ void k_adam(int n, float *__restrict__ P, const float *__restrict__ g,

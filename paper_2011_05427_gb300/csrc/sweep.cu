@@ -546,10 +546,9 @@ __device__ void finalize_body(const FinalizeArgs &x, int bx)
                     }
                 }
             }
-            if (sizeof(R) == 8)   // refined reciprocal: a third of an FP64 division's operations
-                f[idx] = (A0.s != (R)0) ? (double)A2.s * rcp64((double)A0.s) : 1.0 / 3.0;
-            else
-                f[idx] = (A0.s != (R)0) ? (double)(A2.s / A0.s) : 1.0 / 3.0;
+            // a division, not a reciprocal: in cold cells both angular sums are subnormal,
+            // where 1/A0 overflows while A2/A0 stays the ratio
+            f[idx] = (A0.s != (R)0) ? (double)(A2.s / A0.s) : 1.0 / 3.0;
         }
         return;
     }

@@ -9,7 +9,7 @@ import numpy as np
 from . import trt
 
 NPARAM = 132868
-W16_ELEMS = 4 * 65536
+W16_ELEMS = 6 * 65536
 
 
 class MLP:

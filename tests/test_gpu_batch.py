@@ -92,3 +92,4 @@ def test_batch_uniform_equilibrium_and_tile(trt):
             assert sb[k]["n_ti"] == st["n_ti"]
             assert same(B.slab(k).moments(), s.moments())
     B.close()
+

@@ -155,6 +155,29 @@ def test_sweep_sampled_full_size(trt, orc):
     assert rel(C0[gs], oC0) < 1e-11 and rel(fbX[gs], ofbX) < 1e-11
 
 
+def test_sweep_subnormal_angular_sums(trt, orc):
+    """Cold optically thick cells: sources and old intensities of order 1e-305, so that the
+    angular sums of the QD factors fall to the subnormal range in the interior; f is a
+    ratio of two such sums and must stay finite and equal to the oracle's (1/sum would
+    overflow)."""
+    nx, N, G = 60, 8, 17
+    r, h, sig, em, I_old, TL = sweep_inputs(orc, 2600, nx, N, G, thick=True)
+    em = em * 1e-305
+    I_old = I_old * 1e-305
+    edges = W.group_edges(G, 1e-5, 1e2)
+    s = solver(trt, nx=nx, N=N, G=G, h=h, edges=edges, TL=1e-3, TR=1e-3)
+    dt = 1.7e-3
+    In, f, fb0, fbX, C0, CX = (x.cpu().numpy() for x in s.k_sweep(dt, sig, em, I_old))
+    mu, w = orc.double_gl(N)
+    Iin0 = orc.group_physics(edges, 1e-3)[0]
+    IinX = orc.group_physics(edges, 1e-3)[0]
+    oI, of, _, _, _, _ = orc.sweep(h, mu, w, sig, em, 1.0 / (C * dt), I_old, Iin0, IinX)
+    assert np.all(np.isfinite(f))
+    A0 = (np.abs(oI).sum(axis=(0, 2))).T   # [G][nx] scale of the angular sums
+    assert np.any((A0 > 0) & (A0 < 2.2250738585072014e-308 * 64))
+    assert rel(f, of) < 1e-6
+
+
 @pytest.mark.parametrize("precision", ["fp64", "sweep32"])
 def test_sweep_every_tile(trt, orc, precision):
     """Every candidate sweep tile (directions per CTA x strip length x buffers) gives the

@@ -210,3 +210,4 @@ def test_fp32_sweep_shapes_in_steps(trt, orc, shape):
         eT, eE, _ = errors(s.moments(), o.state())
         worst = max(worst, eT, eE)
     assert worst < MIXED_TOL["sweep32"], worst
+
