@@ -138,10 +138,10 @@ FP64_PEAK_TFLOPS = 1.25
 # sweep and its finalize on the fc_1024 workload, tile D = 8 directions per CTA), valid while
 # the kernel source hashes to `sha`; profiles/ holds the capture's summary and command.
 TRAFFIC = {
-    "sweep_fp64": {"file": "sweep.cu", "sha": "276d663750df14f9",
-                   "bytes": 540390144 + 542146560 + 66134784 + 13056},
-    "sweep_fp32": {"file": "sweep.cu", "sha": "276d663750df14f9",
-                   "bytes": 269910016 + 244672512 + 33076992 + 0},
+    "sweep_fp64": {"file": "sweep.cu", "sha": "4bc1c6ebaf808806",
+                   "bytes": 540345344 + 542153728 + 66106880 + 11776},
+    "sweep_fp32": {"file": "sweep.cu", "sha": "4bc1c6ebaf808806",
+                   "bytes": 269907968 + 244601600 + 33077248 + 0},
 }
 
 

@@ -76,10 +76,11 @@ int trt_mlp_refresh(const float *params, void *w16, void *stream);
 int trt_mlp_forward(int rows, const float *x, const float *params, const void *w16,
                     void *scratch, size_t scratch_bytes, float *y, void *stream);
 
-/* Inference in one persistent kernel (one CTA per SM, 256 rows per iteration, both hidden
- * layers on the tensor cores with the activations kept in shared memory and the weights
- * streamed in 64-wide K chunks); same arithmetic and result as trt_mlp_forward up to the
- * order of the FP32 accumulation.  Needs no scratch.  params must be 16-byte aligned (the
+/* Inference in one persistent kernel (one CTA per SM in clusters of two, 256 rows per
+ * iteration as two 128-row groups half a period apart, both hidden layers on the tensor
+ * cores with the activations kept in shared memory and the weights streamed in 32-wide K
+ * chunks from the image trt_mlp_refresh keeps in w16); same arithmetic and result as
+ * trt_mlp_forward up to the order of the FP32 accumulation.  Needs no scratch.  params must be 16-byte aligned (the
  * biases and the first and last layers' weights are read as float4): TRT_EINVAL otherwise. */
 int trt_mlp_forward_fused(int rows, const float *x, const float *params, const void *w16,
                           float *y, void *stream);

@@ -141,6 +141,34 @@ __device__ inline void tmem_ld32(uint32_t taddr, float *v)
     for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
 }
 
+// the same load without its wait (two loads may be in flight before one wait), and the
+// wait tied to the loaded registers so that no use of them is scheduled before it
+__device__ inline void tmem_ld32_issue(uint32_t taddr, uint32_t (&r)[32])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+          "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+          "=r"(r[31])
+        : "r"(taddr));
+}
+__device__ inline void tmem_wait_tied(uint32_t (&r)[32])
+{
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]), "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]), "+r"(r[29]), "+r"(r[30]), "+r"(r[31])
+                 :
+                 : "memory");
+}
+__device__ inline void reg_tie(uint32_t (&r)[32])
+{
+    asm volatile("" : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]), "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]), "+r"(r[29]), "+r"(r[30]), "+r"(r[31]));
+}
+
 struct Epi {
     const float *bias;
     int relu;
@@ -344,11 +372,11 @@ __global__ void __launch_bounds__(128) k_gemm(int M, int N, int K, const bf16 *_
 }
 
 // ---- fused inference: the whole network in one persistent kernel ----
-// One CTA per SM, 288 threads: two groups of four warps and one control warp.  Each
-// iteration takes 256 rows; group g (warps 4g .. 4g+3, thread = row = tensor-memory lane)
-// owns rows 128 g .. 128 g + 127 of it, its activation tile A_g in shared memory and its
-// 128 x 256 FP32 accumulator in tensor-memory columns 256 g .. 256 g + 255.  The control
-// thread (warp 8, lane 0) streams the weights and issues every MMA, in the order
+// One CTA per SM, 320 threads: two groups of four warps, a producer warp and an MMA warp.
+// Each iteration takes 256 rows; group g (warps 4g .. 4g+3, thread = row = tensor-memory
+// lane) owns rows 128 g .. 128 g + 127 of it, its activation tile A_g in shared memory and
+// its 128 x 256 FP32 accumulator in tensor-memory columns 256 g .. 256 g + 255.  One thread
+// (warp 8) streams the weights; one thread (warp 9) issues every MMA, in the order
 //   layer 2 of group 0, layer 2 of group 1, layer 3 of group 0, layer 3 of group 1,
 // so that while the tensor core multiplies for one group the other group's warps run its
 // CUDA-core phase (layer 1, a ReLU/bias epilogue, the sigmoid head): the two groups work
@@ -359,11 +387,18 @@ __global__ void __launch_bounds__(128) k_gemm(int M, int N, int K, const bf16 *_
 // bytes apart), so one cp.async.bulk of 16 KB moves a chunk and completes on the slot's
 // `full` mbarrier; the MMAs reading a slot commit to its `empty` mbarrier, which releases
 // it for the chunk S later.  Every chunk is used by one group's layer, so each weight is
-// read from L2 twice per 256 rows.
+// streamed twice per 256 rows; to halve what L2 delivers, CTAs run in clusters of two
+// (neighbouring SMs) that consume the same chunk sequence: the cluster's first CTA copies
+// each chunk once with a multicast bulk copy into both CTAs' slots (completing on each
+// CTA's `full` barrier), and each CTA's MMAs commit to the `empty` barriers of both, so
+// a slot is refilled only when both CTAs are done with it.  The two CTAs of a cluster run
+// the same number of iterations (the second one's last may hold no rows).
+//   The MMA thread never waits for a slot to drain (that is the producer's wait), so the
+// tensor core always has the next chunk's MMAs queued behind the running ones.
 //   Hand-offs: a group arrives on act[g] (128 arrivals) when A_g holds the next layer's
-// input (after a proxy fence: the MMAs read it through the async proxy); the control
-// thread commits the last MMA of a layer to acc[g], which the group waits on before it
-// reads the accumulator.  Small parameters (layer-1 weights, biases, head) sit in shared
+// input (after a proxy fence: the MMAs read it through the async proxy); the MMA thread
+// commits the last MMA of a layer to acc[g], which the group waits on before it reads
+// the accumulator.  Small parameters (layer-1 weights, biases, head) sit in shared
 // memory.  Every mbarrier wait is bounded (one second); a wait that runs out stops the
 // kernel's work and sets the device error flag (trt_mlp_status).
 constexpr int FA_BYTES = 128 * 256 * 2;   // one activation tile
@@ -376,9 +411,9 @@ constexpr uint32_t FW_LBO = 4096, FW_SBO = 128;   // weight chunk: K groups, row
 constexpr int FP_W1 = 0, FP_B1 = 768, FP_B2 = 1024, FP_B3 = 1280, FP_W4 = 1536, FP_B4 = 1792;
 constexpr int FP_BYTES = 1796 * 4;
 constexpr int F_NBAR = 2 * F_SLOTS + 4;   // full[S], empty[S], act[2], acc[2]
-constexpr int F_SMEM = 2 * FA_BYTES + F_SLOTS * FW_BYTES + FP_BYTES + 8 * F_NBAR + 16;
+constexpr int F_SMEM = 2 * FA_BYTES + F_SLOTS * FW_BYTES + FP_BYTES + 8 * F_NBAR + 32;
 constexpr uint32_t FA_SBO = 4096;         // activation tiles: 32 K groups per row group
-constexpr int F_THREADS = 288;
+constexpr int F_THREADS = 320;
 
 __device__ inline void mbar_init_n(uint64_t *bar, unsigned count)
 {
@@ -423,14 +458,36 @@ __device__ inline uint32_t relu_bf16x2(float2 v)
     return d;
 }
 
-// one contiguous bulk copy global -> shared, completing on an mbarrier
-__device__ inline void bulk_copy(void *dst, const void *src, unsigned bytes, uint64_t *bar)
+// one contiguous bulk copy global -> the same shared-memory offset in every CTA of the
+// cluster named by `mask`, completing (bytes) on the mbarrier at the same offset in each
+__device__ inline void bulk_copy_mc(void *dst, const void *src, unsigned bytes, uint64_t *bar,
+                                    unsigned short mask)
 {
     asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-            su32(dst)),
-        "l"(src), "r"(bytes), "r"(su32(bar))
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster"
+        " [%0], [%1], %2, [%3], %4;" ::"r"(su32(dst)),
+        "l"(src), "r"(bytes), "r"(su32(bar)), "h"(mask)
         : "memory");
+}
+// arrive on the mbarrier at this offset in every CTA of `mask` when this thread's MMAs so
+// far have completed
+__device__ inline void umma_commit_mc(uint64_t *bar, unsigned short mask)
+{
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
+        " [%0], %1;" ::"r"(su32(bar)),
+        "h"(mask)
+        : "memory");
+}
+__device__ inline void cluster_sync()
+{
+    asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
+}
+__device__ inline unsigned cluster_rank()
+{
+    unsigned r;
+    asm("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
 }
 
 __global__ void __launch_bounds__(F_THREADS, 1) k_mlp_fused(int rows, const float *__restrict__ x,
@@ -445,21 +502,27 @@ __global__ void __launch_bounds__(F_THREADS, 1) k_mlp_fused(int rows, const floa
     uint64_t *full = bar, *empty = bar + F_SLOTS, *act = bar + 2 * F_SLOTS, *acc = act + 2;
     uint32_t *tslot = reinterpret_cast<uint32_t *>(bar + F_NBAR);
     int *sfail = reinterpret_cast<int *>(tslot + 1);
+    int *sprod = sfail + 1, *scons = sfail + 2;   // chunks copied / expected (failure drain)
 
     const int tid = threadIdx.x, warp = tid >> 5;
     const int ntiles = (rows + 255) / 256;
-    const int mine = (int)blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    // both CTAs of a cluster (blocks 2c, 2c + 1) run the first one's iteration count
+    const int lead = (int)blockIdx.x & ~1;
+    const int mine = lead < ntiles ? (ntiles - 1 - lead) / (int)gridDim.x + 1 : 0;
+    const unsigned crank = cluster_rank();
 
     if (tid == 0) {
         for (int k = 0; k < F_SLOTS; ++k) {
             mbar_init_n(&full[k], 1);
-            mbar_init_n(&empty[k], 1);
+            mbar_init_n(&empty[k], 2);   // one commit from each CTA of the cluster
         }
         for (int g = 0; g < 2; ++g) {
             mbar_init_n(&act[g], 128);
             mbar_init_n(&acc[g], 1);
         }
         *sfail = 0;
+        *sprod = 0;
+        *scons = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
@@ -480,23 +543,30 @@ __global__ void __launch_bounds__(F_THREADS, 1) k_mlp_fused(int rows, const floa
     tc_before();
     __syncthreads();
     tc_after();
+    cluster_sync();   // both CTAs' barriers exist before either signals the other's
     const uint32_t tmem = *tslot;
     bool ok = true;
 
+    const int Q = 4 * FNC * mine;   // weight chunks: 4 layer-jobs of FNC chunks per iteration
     if (warp == 8) {
-        // ---------------- control thread: weight stream and MMAs ----------------
-        if ((tid & 31) == 0) {
-            const int Q = 4 * FNC * mine;   // chunks: 4 layer-jobs of FNC chunks per iteration
-            int produced = 0;
-            auto produce = [&](int q) {     // chunk q: job q / FNC, K chunk q % FNC
+        // ---------------- producer thread (first CTA of the cluster) ----------------
+        if ((tid & 31) == 0 && crank == 0) {
+            int q = 0;
+            for (; q < Q; ++q) {   // chunk q: job q / FNC, K chunk q % FNC, slot q % S
+                if (q >= F_SLOTS && !mbar_wait(&empty[q % F_SLOTS], ((q - F_SLOTS) / F_SLOTS) & 1)) {
+                    *sfail = 1;
+                    break;
+                }
                 const int layer = (q / FNC) % 4 >= 2 ? 1 : 0;
-                const int c = q % FNC;
-                mbar_expect(&full[q % F_SLOTS], FW_BYTES);
-                bulk_copy(sW + (q % F_SLOTS) * FW_BYTES, Wimg + layer * 65536 + c * (FW_BYTES / 2),
-                          FW_BYTES, &full[q % F_SLOTS]);
-                ++produced;
-            };
-            for (int q = 0; q < F_SLOTS && q < Q; ++q) produce(q);
+                bulk_copy_mc(sW + (q % F_SLOTS) * FW_BYTES,
+                             Wimg + layer * 65536 + (q % FNC) * (FW_BYTES / 2), FW_BYTES,
+                             &full[q % F_SLOTS], (unsigned short)3);
+            }
+            *sprod = q;
+        }
+    } else if (warp == 9) {
+        // ---------------- MMA thread ----------------
+        if ((tid & 31) == 0) {
             unsigned pact = 0;   // bit g: parity of act[g]'s next phase
             int q = 0;
             for (int it = 0; it < mine && ok; ++it) {
@@ -508,7 +578,14 @@ __global__ void __launch_bounds__(F_THREADS, 1) k_mlp_fused(int rows, const floa
                     const uint32_t a0 = su32(sm + g * FA_BYTES);
                     const uint32_t d = tmem + (uint32_t)(g * 256);
                     for (int c = 0; c < FNC; ++c, ++q) {
-                        if (!mbar_wait(&full[q % F_SLOTS], (q / F_SLOTS) & 1)) { ok = false; break; }
+                        // this CTA's share of chunk q's bytes (the copy may land first: the
+                        // phase completes once both the arrival and the bytes are in)
+                        mbar_expect(&full[q % F_SLOTS], FW_BYTES);
+                        if (!mbar_wait(&full[q % F_SLOTS], (q / F_SLOTS) & 1)) {
+                            ok = false;
+                            ++q;
+                            break;
+                        }
                         const uint32_t w0 = su32(sW + (q % F_SLOTS) * FW_BYTES);
 #pragma unroll
                         for (int kk = 0; kk < FK / 16; ++kk) {
@@ -516,25 +593,15 @@ __global__ void __launch_bounds__(F_THREADS, 1) k_mlp_fused(int rows, const floa
                             const uint32_t ka = (c * (FK / 8) + kk * 2) * 128;
                             umma(d, sdesc(a0 + ka, LBO, FA_SBO), bd, (c | kk) != 0);
                         }
-                        umma_commit(&empty[q % F_SLOTS]);
-                        // the slot of chunk q - 1 takes chunk q - 1 + S once its MMAs are done
-                        if (q >= 1 && q - 1 + F_SLOTS < Q) {
-                            if (!mbar_wait(&empty[(q - 1) % F_SLOTS], ((q - 1) / F_SLOTS) & 1)) {
-                                ok = false;
-                                break;
-                            }
-                            produce(q - 1 + F_SLOTS);
-                        }
+                        // the slot is free for chunk q + S once both CTAs' MMAs on it are done
+                        umma_commit_mc(&empty[q % F_SLOTS], (unsigned short)3);
                     }
                     if (!ok) break;
                     umma_commit(&acc[g]);   // the group's accumulator is complete
                 }
             }
-            if (!ok) {
-                *sfail = 1;
-                // let copies in flight land before the CTA exits (bounded)
-                for (int r = q; r < produced; ++r) mbar_wait(&full[r % F_SLOTS], (r / F_SLOTS) & 1);
-            }
+            if (!ok) *sfail = 1;
+            *scons = q;   // chunks whose bytes this CTA has expected
         }
     } else {
         // ---------------- a group of four warps: 128 rows ----------------
@@ -580,7 +647,7 @@ __global__ void __launch_bounds__(F_THREADS, 1) k_mlp_fused(int rows, const floa
                 const float4 *pw1 = reinterpret_cast<const float4 *>(sP + FP_W1 + 256);
                 const float4 *pw2 = reinterpret_cast<const float4 *>(sP + FP_W1 + 512);
                 const float4 *pb = reinterpret_cast<const float4 *>(sP + FP_B1);
-#pragma unroll 2
+#pragma unroll 4
                 for (int k8 = 0; k8 < 32; ++k8) {
                     uint4 u;
                     uint32_t *hw = reinterpret_cast<uint32_t *>(&u);
@@ -613,39 +680,55 @@ __global__ void __launch_bounds__(F_THREADS, 1) k_mlp_fused(int rows, const floa
             hand_off();
             if (!(ok = wait_acc())) break;
             // ---- epilogue of layer 2: h2 = relu(acc + b2) over h1 ----
-            for (int ch = 0; ch < 8; ++ch) {
-                float v[32];
-                tmem_ld32(tb + ch * 32, v);
+            for (int ch = 0; ch < 8; ch += 2) {   // 64 columns per tensor-memory wait
+                uint32_t ra[32], rb[32];
+                tmem_ld32_issue(tb + ch * 32, ra);
+                tmem_ld32_issue(tb + ch * 32 + 32, rb);
+                tmem_wait_tied(ra);
+                reg_tie(rb);
 #pragma unroll
-                for (int qq = 0; qq < 4; ++qq) {
-                    const float4 *b2 = reinterpret_cast<const float4 *>(sP + FP_B2) + ch * 8 + qq * 2;
-                    const float4 p0 = b2[0], p1 = b2[1];
-                    const float *vq = v + qq * 8;
-                    uint4 u;
-                    u.x = relu_bf16x2(add2(make_float2(vq[0], vq[1]), make_float2(p0.x, p0.y)));
-                    u.y = relu_bf16x2(add2(make_float2(vq[2], vq[3]), make_float2(p0.z, p0.w)));
-                    u.z = relu_bf16x2(add2(make_float2(vq[4], vq[5]), make_float2(p1.x, p1.y)));
-                    u.w = relu_bf16x2(add2(make_float2(vq[6], vq[7]), make_float2(p1.z, p1.w)));
-                    *reinterpret_cast<uint4 *>(myA + a_off(r, ch * 4 + qq)) = u;
+                for (int half = 0; half < 2; ++half) {
+                    const uint32_t *rr = half ? rb : ra;
+#pragma unroll
+                    for (int qq = 0; qq < 4; ++qq) {
+                        const float4 *b2 = reinterpret_cast<const float4 *>(sP + FP_B2) + (ch + half) * 8 + qq * 2;
+                        const float4 p0 = b2[0], p1 = b2[1];
+                        const uint32_t *vq = rr + qq * 8;
+                        uint4 u;
+                        u.x = relu_bf16x2(add2(make_float2(__uint_as_float(vq[0]), __uint_as_float(vq[1])), make_float2(p0.x, p0.y)));
+                        u.y = relu_bf16x2(add2(make_float2(__uint_as_float(vq[2]), __uint_as_float(vq[3])), make_float2(p0.z, p0.w)));
+                        u.z = relu_bf16x2(add2(make_float2(__uint_as_float(vq[4]), __uint_as_float(vq[5])), make_float2(p1.x, p1.y)));
+                        u.w = relu_bf16x2(add2(make_float2(__uint_as_float(vq[6]), __uint_as_float(vq[7])), make_float2(p1.z, p1.w)));
+                        *reinterpret_cast<uint4 *>(myA + a_off(r, (ch + half) * 4 + qq)) = u;
+                    }
                 }
             }
             hand_off();
             if (!(ok = wait_acc())) break;
             // ---- epilogue of layer 3 and the head: y = sigmoid(w4 . relu(acc + b3) + b4) ----
             float2 dot = make_float2(0.f, 0.f);   // even and odd columns
-            for (int ch = 0; ch < 8; ++ch) {
-                float v[32];
-                tmem_ld32(tb + ch * 32, v);
+            for (int ch = 0; ch < 8; ch += 2) {   // 64 columns per tensor-memory wait
+                uint32_t ra[32], rb[32];
+                tmem_ld32_issue(tb + ch * 32, ra);
+                tmem_ld32_issue(tb + ch * 32 + 32, rb);
+                tmem_wait_tied(ra);
+                reg_tie(rb);
 #pragma unroll
-                for (int j4 = 0; j4 < 8; ++j4) {
-                    const float4 b3 = reinterpret_cast<const float4 *>(sP + FP_B3)[ch * 8 + j4];
-                    const float4 w4 = reinterpret_cast<const float4 *>(sP + FP_W4)[ch * 8 + j4];
-                    float2 a = add2(make_float2(v[4 * j4], v[4 * j4 + 1]), make_float2(b3.x, b3.y));
-                    float2 c = add2(make_float2(v[4 * j4 + 2], v[4 * j4 + 3]), make_float2(b3.z, b3.w));
-                    a = make_float2(fmaxf(a.x, 0.f), fmaxf(a.y, 0.f));
-                    c = make_float2(fmaxf(c.x, 0.f), fmaxf(c.y, 0.f));
-                    dot = fma2(a, make_float2(w4.x, w4.y), dot);
-                    dot = fma2(c, make_float2(w4.z, w4.w), dot);
+                for (int half = 0; half < 2; ++half) {
+                    const uint32_t *rr = half ? rb : ra;
+#pragma unroll
+                    for (int j4 = 0; j4 < 8; ++j4) {
+                        const float4 b3 = reinterpret_cast<const float4 *>(sP + FP_B3)[(ch + half) * 8 + j4];
+                        const float4 w4 = reinterpret_cast<const float4 *>(sP + FP_W4)[(ch + half) * 8 + j4];
+                        float2 a = add2(make_float2(__uint_as_float(rr[4 * j4]), __uint_as_float(rr[4 * j4 + 1])),
+                                        make_float2(b3.x, b3.y));
+                        float2 c = add2(make_float2(__uint_as_float(rr[4 * j4 + 2]), __uint_as_float(rr[4 * j4 + 3])),
+                                        make_float2(b3.z, b3.w));
+                        a = make_float2(fmaxf(a.x, 0.f), fmaxf(a.y, 0.f));
+                        c = make_float2(fmaxf(c.x, 0.f), fmaxf(c.y, 0.f));
+                        dot = fma2(a, make_float2(w4.x, w4.y), dot);
+                        dot = fma2(c, make_float2(w4.z, w4.w), dot);
+                    }
                 }
             }
             if (rv) y[row] = 1.f / (1.f + __expf(-((dot.x + dot.y) + sP[FP_B4])));
@@ -653,7 +736,17 @@ __global__ void __launch_bounds__(F_THREADS, 1) k_mlp_fused(int rows, const floa
     }
     tc_before();
     __syncthreads();
-    if (*sfail && tid == 0) atomicExch(&g_mlp_err, TRT_ETIMEOUT);
+    if (*sfail && tid == 0) {
+        atomicExch(&g_mlp_err, TRT_ETIMEOUT);
+        // let the producer's copies in flight land (bounded): expect what the MMA thread
+        // did not, then wait
+        for (int r = *scons; r < *sprod; ++r) {
+            mbar_expect(&full[r % F_SLOTS], FW_BYTES);
+            mbar_wait(&full[r % F_SLOTS], (r / F_SLOTS) & 1);
+        }
+    }
+    // neither CTA leaves while the other may still copy into it or arrive on its barriers
+    cluster_sync();
     if (warp == 0) {
         tc_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
@@ -676,10 +769,31 @@ cudaError_t mlp_fused(int rows, const float *x, const float *P, const bf16 *W, f
         attr = true;
     }
     if (reinterpret_cast<uintptr_t>(P) & 15) return cudaErrorMisalignedAddress;   // float4 loads
+    // clusters of two CTAs, one per SM, no more clusters than fit on the GPU at once (the
+    // kernel is persistent: a cluster left for a second wave would double the time)
+    cudaLaunchConfig_t cfg = {};
+    cfg.blockDim = dim3(F_THREADS);
+    cfg.dynamicSmemBytes = F_SMEM;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 2;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    static int max_pairs = 0;
+    if (max_pairs == 0) {
+        cfg.gridDim = dim3(2);
+        int n = 0;
+        if (cudaOccupancyMaxActiveClusters(&n, k_mlp_fused, &cfg) != cudaSuccess || n < 1)
+            n = (g_num_sms > 0 ? g_num_sms : 148) / 2;
+        max_pairs = n;
+    }
     const int ntiles = (rows + 255) / 256;
-    const int grid = std::max(1, std::min(ntiles, g_num_sms > 0 ? g_num_sms : 148));
-    k_mlp_fused<<<grid, F_THREADS, F_SMEM, st>>>(rows, x, P, W + 4 * 65536, y);
-    return cudaGetLastError();
+    const int pairs = std::max(1, std::min((ntiles + 1) / 2, max_pairs));
+    cfg.gridDim = dim3(2 * pairs);
+    return cudaLaunchKernelEx(&cfg, k_mlp_fused, rows, x, P, (const bf16 *)(W + 4 * 65536), y);
 }
 
 cudaError_t gemm(int M, int N, int K, const bf16 *A, const bf16 *B, const Epi &e,
