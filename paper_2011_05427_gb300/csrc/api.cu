@@ -71,6 +71,8 @@ void carve(trt_handle *h, Carver &c)
     p.Ein0 = c.take<double>(G); p.Fin0 = c.take<double>(G);
     p.EinX = c.take<double>(G); p.FinX = c.take<double>(G);
     p.ihf = c.take<double>(nx + 1);
+    p.hf = c.take<double>(nx + 1);
+    p.lo_slot = reinterpret_cast<int *>(c.take<double>((nx + 2) / 2));
     p.otab = c.take<double>(otab_doubles((int)G));
     p.rscratch_doubles = restrict_scratch_doubles((int)nx, (int)G, 1);
     p.rscratch = p.rscratch_doubles ? c.take<double>(p.rscratch_doubles) : nullptr;
@@ -284,8 +286,26 @@ int trt_create(const trt_grid *grid, const trt_angles *angles, const trt_groups 
     std::vector<double> hh(nx), mu(M), w(M), Iin0(G, 0.0), IinX(G, 0.0);
     std::vector<double> Ein0(G, 0.0), Fin0(G, 0.0), EinX(G, 0.0), FinX(G, 0.0);
     for (int i = 0; i < nx; ++i) hh[i] = xe[i + 1] - xe[i];
-    std::vector<double> ihf(nx + 1, 0.0);
+    std::vector<double> ihf(nx + 1, 0.0), hf(nx + 1);
     for (int f = 1; f < nx; ++f) ihf[f] = 1.0 / (hh[f - 1] + hh[f]);
+    for (int f = 0; f <= nx; ++f)
+        hf[f] = (f == 0) ? 0.5 * hh[0] : (f == nx) ? 0.5 * hh[nx - 1] : 0.5 * (hh[f - 1] + hh[f]);
+    std::vector<int> lo_slot(nx + 1, 0);   // chunk layout of the partitioned LO solve
+    if (nx >= 2) {
+        const int P = std::min(32, nx / 2);
+        for (int f = 0; f <= nx; ++f) {
+            int l, k;
+            if (f == nx) {
+                l = P - 1;
+                k = nx - ((P - 1) * nx) / P;
+            } else {
+                l = (f * P) / nx;
+                if (l + 1 < P && ((l + 1) * nx) / P <= f) ++l;
+                k = f - (l * nx) / P;
+            }
+            lo_slot[f] = k * 32 + l;
+        }
+    }
     {
         std::vector<double> x(N), wx(N);
         gauss_legendre_host(N, x.data(), wx.data());
@@ -339,7 +359,9 @@ int trt_create(const trt_grid *grid, const trt_angles *angles, const trt_groups 
         return cudaMemcpyAsync(dst, src.data(), src.size() * sizeof(double),
                                cudaMemcpyHostToDevice, p.stream);
     };
-    CK(up(p.h, hh)); CK(up(p.ihf, ihf)); CK(up(p.edges, edges)); CK(up(p.mu, mu)); CK(up(p.w, w));
+    CK(up(p.h, hh)); CK(up(p.ihf, ihf)); CK(up(p.hf, hf)); CK(up(p.edges, edges)); CK(up(p.mu, mu)); CK(up(p.w, w));
+    CK(cudaMemcpyAsync(p.lo_slot, lo_slot.data(), lo_slot.size() * sizeof(int),
+                       cudaMemcpyHostToDevice, p.stream));
     CK(up(p.Iin0, Iin0)); CK(up(p.IinX, IinX)); CK(up(p.Ein0, Ein0)); CK(up(p.Fin0, Fin0));
     CK(up(p.EinX, EinX)); CK(up(p.FinX, FinX));
     CK(up(H->T, T0v)); CK(up(H->Eg, Eg)); CK(up(H->Fg, Fg)); CK(up(H->f, f));

@@ -50,7 +50,8 @@ struct FinalizeArgs {
 struct LoCtx {
     int nx;
     double dt, icdt, idt;   // dt, 1/(c dt), 1/dt
-    const double *h, *ihf;
+    const double *h, *ihf, *hf;
+    const int *lo_slot;
     Level L;
     const double *a_cell, *s_cell;   // grey: explicit absorption / source per cell
 };

@@ -129,6 +129,9 @@ struct Problem {
     // device constants
     double *h, *edges, *mu, *w, *Iin0, *IinX, *Ein0, *Fin0, *EinX, *FinX;
     double *ihf;        // [nx+1]: 1/(h_{f-1} + h_f) at interior faces (dx-weighted means)
+    double *hf;         // [nx+1]: face half-widths h_0/2, (h_{f-1} + h_f)/2, h_{nx-1}/2
+    int *lo_slot;       // [nx+1]: shared-memory slot k * 32 + l of face/row f in the
+                        // partitioned tridiagonal solve (chunk l, row k of the chunk)
     double *rscratch;   // partial sums of the two-stage restriction
     size_t rscratch_doubles;
     // sweep tile: directions per CTA (0 = default) and strip shape index (0 = default)

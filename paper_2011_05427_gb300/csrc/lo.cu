@@ -50,17 +50,15 @@ __device__ inline void face_coef(const LoCtx &x, int q, int f, R &PL, R &PR, R &
 {
     const int nx = x.nx;
     const double *phi = x.L.phi + (size_t)q * nx;
-    R dx, phiL, phiR;
+    const R dx = (R)x.hf[f];
+    R phiL, phiR;
     if (f == 0) {
-        dx = (R)(0.5 * x.h[0]);
         phiL = (R)x.L.phib0[q];
         phiR = (R)phi[0];
     } else if (f == nx) {
-        dx = (R)(0.5 * x.h[nx - 1]);
         phiL = (R)phi[nx - 1];
         phiR = (R)x.L.phibX[q];
     } else {
-        dx = (R)(0.5 * (x.h[f - 1] + x.h[f]));
         phiL = (R)phi[f - 1];
         phiR = (R)phi[f];
     }
@@ -81,20 +79,24 @@ __device__ inline void face_coef(const LoCtx &x, int q, int f, R &PL, R &PR, R &
         Gf += -c * phiR * (R)x.L.EinX[q] + phiR * (R)x.L.FinX[q] * iCX;
     }
     const R iD = rcpR<R>(D);
-    PL = c * phiL * iD;
-    PR = c * phiR * iD;
+    const R ciD = c * iD;
+    PL = phiL * ciD;
+    PR = phiR * ciD;
     GD = Gf * iD;
 }
 
+// row i of the cell equation: Ap = h (1/dt + a), Dp = h (s + Eold/dt)
 template <typename R>
-__device__ inline void cell_terms(const LoCtx &x, int q, int i, R &ai, R &si)
+__device__ inline void cell_row(const LoCtx &x, int q, int i, R &Ap, R &Dp)
 {
+    const R hi = (R)x.h[i], idt = (R)x.idt;
+    const R Eo = (R)x.L.Eold[(size_t)q * x.nx + i];
     if (x.a_cell) {
-        ai = (R)x.a_cell[i];
-        si = (R)x.s_cell[i];
+        Ap = hi * (idt + (R)x.a_cell[i]);
+        Dp = hi * fma(Eo, idt, (R)x.s_cell[i]);
     } else {
-        ai = (R)(kC * x.L.sig[(size_t)q * x.nx + i]);
-        si = (R)(2.0 * x.L.emis[(size_t)q * x.nx + i]);
+        Ap = hi * fma((R)kC, (R)x.L.sig[(size_t)q * x.nx + i], idt);
+        Dp = hi * fma(Eo, idt, (R)2 * (R)x.L.emis[(size_t)q * x.nx + i]);
     }
 }
 
@@ -106,18 +108,6 @@ __device__ inline void cell_terms(const LoCtx &x, int q, int i, R &ai, R &si)
 //   phase B (each lane its chunk): modified Thomas down and up the chunk;
 //   phase C (warp): parallel cyclic reduction of the 2 x 32 chunk-boundary rows;
 //   phase D (each lane): back substitution, then the fluxes of its faces.
-template <typename R>
-__device__ inline void chunk_of(int f, int n, int P, int &l, int &k)
-{
-    if (f == n) {
-        l = P - 1;
-        k = n - ((P - 1) * n) / P;
-    } else {
-        l = (f * P) / n;
-        if (l + 1 < P && ((l + 1) * n) / P <= f) ++l;
-        k = f - (l * n) / P;
-    }
-}
 
 // Phase A for system q by `nthr` cooperating threads (index `t`): face coefficients and
 // row parts into the chunk layout.  n >= 2.
@@ -125,25 +115,18 @@ template <typename R>
 __device__ void lo_stage(const LoCtx &x, int q, R *sm, int mmax, int t, int nthr)
 {
     const int n = x.nx;
-    const R idt = (R)x.idt;
-    const int P = min(32, n / 2);
     const int S = 32 * mmax;
     R *PLc = sm, *PRc = sm + S, *GDc = sm + 2 * S, *Ap = sm + 3 * S, *Dp = sm + 5 * S;
     for (int f = t; f <= n; f += nthr) {
-        int l, k;
-        chunk_of<R>(f, n, P, l, k);
+        // slot k * 32 + l (chunk l = the lane whose rows hold f, row k of the chunk;
+        // face n after the last chunk's last row): a table built with the problem
+        const int o = x.lo_slot[f];
         R PL, PR, GD;
         face_coef<R>(x, q, f, PL, PR, GD);
-        PLc[k * 32 + l] = PL;
-        PRc[k * 32 + l] = PR;
-        GDc[k * 32 + l] = GD;
-        if (f < n) {
-            R ai, si;
-            cell_terms<R>(x, q, f, ai, si);
-            const R hi = (R)x.h[f];
-            Ap[k * 32 + l] = hi * idt + hi * ai;
-            Dp[k * 32 + l] = hi * si + hi * (R)x.L.Eold[(size_t)q * n + f] * idt;
-        }
+        PLc[o] = PL;
+        PRc[o] = PR;
+        GDc[o] = GD;
+        if (f < n) cell_row<R>(x, q, f, Ap[o], Dp[o]);
     }
 }
 
@@ -158,13 +141,12 @@ __device__ void warp_lo_solve(const LoCtx &x, int q, R *sm, int mmax, bool stage
 
     if (n == 1) {
         if (lane == 0) {
-            R PL0, PR0, GD0, PL1, PR1, GD1, ai, si;
+            R PL0, PR0, GD0, PL1, PR1, GD1, Ap0, Dp0;
             face_coef<R>(x, q, 0, PL0, PR0, GD0);
             face_coef<R>(x, q, 1, PL1, PR1, GD1);
-            cell_terms<R>(x, q, 0, ai, si);
-            R hi = (R)x.h[0];
-            R di = hi * (R)x.idt + hi * ai + PL1 + PR0;
-            R rh = hi * si + hi * (R)x.L.Eold[(size_t)q * n] * (R)x.idt - GD1 + GD0;
+            cell_row<R>(x, q, 0, Ap0, Dp0);
+            R di = Ap0 + PL1 + PR0;
+            R rh = Dp0 - GD1 + GD0;
             R e0 = rh / di;
             E[0] = (double)e0;
             R F0 = GD0 - PR0 * e0, F1 = GD1 + PL1 * e0;
@@ -917,6 +899,8 @@ LoCtx make_lo_ctx(const Problem &p, double dt, const Level &L)
 {
     LoCtx x;
     x.nx = p.nx; x.dt = dt; x.icdt = 1.0 / (kC * dt); x.idt = 1.0 / dt; x.h = p.h; x.ihf = p.ihf;
+    x.hf = p.hf;
+    x.lo_slot = p.lo_slot;
     x.L = L;
     x.a_cell = nullptr; x.s_cell = nullptr;
     return x;
