@@ -455,6 +455,20 @@ def run_ours(args):
                 "note": "FP32 sweeps, FP64 group/grey LOQD + MEB; both converged to eps; "
                         "compared after the same warm-up + timed steps",
                 **counters(st_m, args.steps)}
+            t_x, st_x, _, s_x = timed_steps(trt, cfg, "mixed", args.cycle, args.steps,
+                                            args.warmup, local, ws)
+            c = s_x.moments()
+            s_x.close()
+            extra["mixed"] = {
+                "ms_per_step": t_x / args.steps * 1e3,
+                "value": sum(x["n_ti"] for x in st_x) * upd_sweep / t_x,
+                "speedup_vs_fp64": ms_step / (t_x / args.steps * 1e3),
+                "max_rel_T_vs_fp64": float(np.max(np.abs(c["T"] - a["T"]) / a["T"])),
+                "max_rel_Eg_vs_fp64": float(np.max(np.abs(c["Eg"] - a["Eg"]) /
+                                                   a["Eg"].sum(0)[None, :])),
+                "note": "FP32 sweeps and FP32 group LOQD eliminations refined by two "
+                        "FP64-residual steps, FP64 grey LOQD + MEB",
+                **counters(st_x, args.steps)}
 
         if args.mlp:
             extra["mlp"] = mlp_bench(local)

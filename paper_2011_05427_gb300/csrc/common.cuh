@@ -146,7 +146,12 @@ struct Problem {
 constexpr int kTabNI = 49, kTabNC = 12;
 constexpr double kTabU0 = -9.25, kTabH = 0.25;
 constexpr int kTabNF = 3;   // series per interval: sigma_E T^3, sigma_R T^3, ln(1 - e^{-w})
-inline size_t otab_doubles(int G) { return (size_t)G * kTabNI * kTabNF * kTabNC; }
+// one (group, interval) entry: the kTabLo low-order monomial coefficients of each series in
+// FP64, then its kTabNC - kTabLo high-order ones in FP32 (padded to an even count)
+constexpr int kTabLo = 7;
+constexpr int kTabHiF = ((kTabNF * (kTabNC - kTabLo) + 1) / 2) * 2;   // floats
+constexpr int kTabEntry = kTabNF * kTabLo + kTabHiF / 2;               // doubles
+inline size_t otab_doubles(int G) { return (size_t)G * kTabNI * kTabEntry; }
 cudaError_t launch_otab_build(const Problem &p);
 
 // ---- launchers (each enqueues on p.stream; returns cudaError_t of the launch) ----

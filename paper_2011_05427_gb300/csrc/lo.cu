@@ -130,34 +130,12 @@ __device__ void lo_stage(const LoCtx &x, int q, R *sm, int mmax, int t, int nthr
     }
 }
 
-// staged = true: phase A already done (by the whole block) for n >= 2.
+// Phases B-D of one system by one warp on the staged arrays in sm: the solution x ends in
+// the Dp array (chunk layout); nothing is written to global memory.  n >= 2.
 template <typename R>
-__device__ void warp_lo_solve(const LoCtx &x, int q, R *sm, int mmax, bool staged = false)
+__device__ void tri_solve(R *sm, int n, int mmax)
 {
     const int lane = threadIdx.x & 31;
-    const int n = x.nx;
-    double *E = x.L.E + (size_t)q * n;
-    double *F = x.L.F + (size_t)q * (n + 1);
-
-    if (n == 1) {
-        if (lane == 0) {
-            R PL0, PR0, GD0, PL1, PR1, GD1, Ap0, Dp0;
-            face_coef<R>(x, q, 0, PL0, PR0, GD0);
-            face_coef<R>(x, q, 1, PL1, PR1, GD1);
-            cell_row<R>(x, q, 0, Ap0, Dp0);
-            R di = Ap0 + PL1 + PR0;
-            R rh = Dp0 - GD1 + GD0;
-            R e0 = rh / di;
-            E[0] = (double)e0;
-            R F0 = GD0 - PR0 * e0, F1 = GD1 + PL1 * e0;
-            F[0] = (double)F0;
-            F[1] = (double)F1;
-            x.L.Eb0[q] = x.L.Ein0[q] + ((double)F0 - x.L.Fin0[q]) / (kC * x.L.C0[q]);
-            x.L.EbX[q] = x.L.EinX[q] + ((double)F1 - x.L.FinX[q]) / (kC * x.L.CX[q]);
-        }
-        return;
-    }
-
     const int P = min(32, n / 2);
     const bool act = lane < P;
     const int r0 = act ? (lane * n) / P : n;
@@ -167,10 +145,6 @@ __device__ void warp_lo_solve(const LoCtx &x, int q, R *sm, int mmax, bool stage
     R *PLc = sm, *PRc = sm + S, *GDc = sm + 2 * S;
     R *Ap = sm + 3 * S, *Cp = sm + 4 * S, *Dp = sm + 5 * S;
 #define CH(arr, k, l) arr[(k) * 32 + (l)]
-
-    // ---- phase A ----
-    if (!staged) lo_stage<R>(x, q, sm, mmax, lane, 32);
-    __syncwarp();
 
     R x0 = 0, x1 = 0;
     R A0r = 0, C0r = 0, D0r = 0, A1r = 0, C1r = 0, D1r = 0;   // reduced rows
@@ -289,9 +263,32 @@ __device__ void warp_lo_solve(const LoCtx &x, int q, R *sm, int mmax, bool stage
             CH(Dp, k, lane) = CH(Dp, k, lane) - CH(Ap, k, lane) * x0 - CH(Cp, k, lane) * x1;
         CH(Dp, 0, lane) = x0;
         CH(Dp, m - 1, lane) = x1;
-        for (int k = 0; k < m; ++k) E[r0 + k] = (double)CH(Dp, k, lane);
     }
     __syncwarp();
+#undef CH
+}
+
+// The outputs of system q from the solution in the Dp array and the face coefficients:
+// E, F (F_f = GD_f + PL_f E_{f-1} - PR_f E_f) and the boundary face energies.  n >= 2.
+template <typename R>
+__device__ void lo_outputs(const LoCtx &x, int q, R *sm, int mmax)
+{
+    const int lane = threadIdx.x & 31;
+    const int n = x.nx;
+    double *E = x.L.E + (size_t)q * n;
+    double *F = x.L.F + (size_t)q * (n + 1);
+    const int P = min(32, n / 2);
+    const bool act = lane < P;
+    const int r0 = act ? (lane * n) / P : n;
+    const int r1 = act ? ((lane + 1) * n) / P : n;
+    const int m = r1 - r0;
+    const int S = 32 * mmax;
+    R *PLc = sm, *PRc = sm + S, *GDc = sm + 2 * S;
+    R *Ap = sm + 3 * S, *Cp = sm + 4 * S, *Dp = sm + 5 * S;
+#define CH(arr, k, l) arr[(k) * 32 + (l)]
+
+    if (act)
+        for (int k = 0; k < m; ++k) E[r0 + k] = (double)CH(Dp, k, lane);
     if (act) {
         const int mprev = (lane > 0) ? r0 - ((lane - 1) * n) / P : 0;
         const R Eleft0 = (lane > 0) ? CH(Dp, mprev - 1, lane - 1) : (R)0;
@@ -309,10 +306,135 @@ __device__ void warp_lo_solve(const LoCtx &x, int q, R *sm, int mmax, bool stage
 #undef CH
 }
 
+// staged = true: phase A already done (by the whole block) for n >= 2.
+template <typename R>
+__device__ void warp_lo_solve(const LoCtx &x, int q, R *sm, int mmax, bool staged = false)
+{
+    const int lane = threadIdx.x & 31;
+    const int n = x.nx;
+    double *E = x.L.E + (size_t)q * n;
+    double *F = x.L.F + (size_t)q * (n + 1);
+
+    if (n == 1) {
+        if (lane == 0) {
+            R PL0, PR0, GD0, PL1, PR1, GD1, Ap0, Dp0;
+            face_coef<R>(x, q, 0, PL0, PR0, GD0);
+            face_coef<R>(x, q, 1, PL1, PR1, GD1);
+            cell_row<R>(x, q, 0, Ap0, Dp0);
+            R di = Ap0 + PL1 + PR0;
+            R rh = Dp0 - GD1 + GD0;
+            R e0 = rh / di;
+            E[0] = (double)e0;
+            R F0 = GD0 - PR0 * e0, F1 = GD1 + PL1 * e0;
+            F[0] = (double)F0;
+            F[1] = (double)F1;
+            x.L.Eb0[q] = x.L.Ein0[q] + ((double)F0 - x.L.Fin0[q]) / (kC * x.L.C0[q]);
+            x.L.EbX[q] = x.L.EinX[q] + ((double)F1 - x.L.FinX[q]) / (kC * x.L.CX[q]);
+        }
+        return;
+    }
+
+    // ---- phase A ----
+    if (!staged) lo_stage<R>(x, q, sm, mmax, lane, 32);
+    __syncwarp();
+
+    tri_solve<R>(sm, n, mmax);
+    lo_outputs<R>(x, q, sm, mmax);
+#undef CH
+}
+
 __host__ __device__ inline int lo_mmax(int nx)
 {
     const int P = nx / 2 < 32 ? nx / 2 : 32;
     return nx < 2 ? 1 : (nx + P - 1) / P + 1;
+}
+
+// FP32 group solve refined to FP64 accuracy (mixed-precision iterative refinement).  The
+// rows are staged in FP64 (s64, by the whole CTA); warp `sw` converts them to FP32 (s32),
+// eliminates in FP32 (x0), then kLoRefine times forms the residual r = b - A x of the FP64
+// rows in FP64, eliminates A d = r in FP32 and adds d to x in FP64; E = x, and the fluxes
+// follow with the FP64 face coefficients.  Each step multiplies the error by about
+// cond(A) eps_32 (the plain FP32 solve's error: 3.6e-6 in T on fc_1024, ~5e-5 in E on a
+// 1000-cell random level, where one step left 2.6e-9); the eliminations, the part that is
+// serial in cells, run on the FP32 pipes.
+// Shared memory: 6 S doubles + 6 S floats (S = 32 mmax).
+constexpr int kLoRefine = 2;
+
+__device__ void lo_solve_refined(const LoCtx &x, int q, int sw)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int n = x.nx;
+    const int mmax = lo_mmax(n);
+    const int S = 32 * mmax;
+    double *s64 = reinterpret_cast<double *>(smem_raw);
+    float *s32 = reinterpret_cast<float *>(s64 + 6 * S);
+    if (n < 2) {   // one cell: the FP64 form
+        if (threadIdx.x < 32) warp_lo_solve<double>(x, q, s64, mmax, false);
+        return;
+    }
+    lo_stage<double>(x, q, s64, mmax, threadIdx.x, blockDim.x);
+    __syncthreads();
+    if ((int)(threadIdx.x >> 5) != (sw & ((int)(blockDim.x >> 5) - 1))) return;
+    const int lane = threadIdx.x & 31;
+    const double *PL = s64, *PR = s64 + S, *GD = s64 + 2 * S, *Ap = s64 + 3 * S;
+    double *X0 = s64 + 4 * S;   // x0 in FP64 (the unused Cp slot of s64)
+    double *Dp = s64 + 5 * S;   // right-hand sides, then E
+    float *pl = s32, *pr = s32 + S, *gd = s32 + 2 * S, *ap = s32 + 3 * S, *cp = s32 + 4 * S,
+          *dp = s32 + 5 * S;
+    for (int o = lane; o < S; o += 32) {
+        pl[o] = (float)PL[o];
+        pr[o] = (float)PR[o];
+        gd[o] = (float)GD[o];
+        ap[o] = (float)Ap[o];
+        dp[o] = (float)Dp[o];
+    }
+    __syncwarp();
+    tri_solve<float>(s32, n, mmax);   // x0 in dp
+    const int P = min(32, n / 2);
+    const bool act = lane < P;
+    const int r0 = act ? (lane * n) / P : n;
+    const int m = act ? ((lane + 1) * n) / P - r0 : 0;
+#define CH(arr, k, l) arr[(k) * 32 + (l)]
+    for (int k = 0; k < m; ++k) CH(X0, k, lane) = (double)CH(dp, k, lane);
+    __syncwarp();
+    for (int step = 0; step < kLoRefine; ++step) {
+        // residual of row i = r0 + k (face i+1 is the next slot of the chunk, or the first
+        // slot of the next chunk; the last chunk keeps face n in its slot m):
+        //   r = (Dp_i - GD_{i+1} + GD_i) - (Ap_i + PL_{i+1} + PR_i) x_i
+        //       + PL_i x_{i-1} + PR_{i+1} x_{i+1}
+        for (int k = 0; k < m; ++k) {
+            const int i = r0 + k;
+            const bool wrap = (k + 1 == m) && lane != P - 1;
+            const int kn = wrap ? 0 : k + 1, ln = wrap ? lane + 1 : lane;
+            const double di = CH(Ap, k, lane) + CH(PL, kn, ln) + CH(PR, k, lane);
+            const double rh = CH(Dp, k, lane) - CH(GD, kn, ln) + CH(GD, k, lane);
+            double r = rh - di * CH(X0, k, lane);
+            if (i > 0) {
+                const int mp = (k > 0) ? 0 : r0 - ((lane - 1) * n) / P;   // rows of the chunk before
+                r = fma(CH(PL, k, lane), (k > 0) ? CH(X0, k - 1, lane) : CH(X0, mp - 1, lane - 1), r);
+            }
+            if (i < n - 1) r = fma(CH(PR, kn, ln), CH(X0, kn, ln), r);
+            CH(cp, k, lane) = (float)r;
+        }
+        __syncwarp();
+        // the correction system: the same matrix (its FP32 diagonal parts again: the
+        // elimination overwrote them), right-hand side r, no face sources
+        for (int k = 0; k <= m; ++k) {
+            if (k < m) {
+                CH(ap, k, lane) = (float)CH(Ap, k, lane);
+                CH(dp, k, lane) = CH(cp, k, lane);
+            }
+            if (k < m || lane == P - 1) CH(gd, k, lane) = 0.f;
+        }
+        __syncwarp();
+        tri_solve<float>(s32, n, mmax);   // the correction in dp
+        for (int k = 0; k < m; ++k) CH(X0, k, lane) += (double)CH(dp, k, lane);
+        __syncwarp();
+    }
+    for (int k = 0; k < m; ++k) CH(Dp, k, lane) = CH(X0, k, lane);
+    __syncwarp();
+#undef CH
+    lo_outputs<double>(x, q, s64, mmax);
 }
 
 // One system per CTA: all 4 warps stage the rows (phase A: the parallel part, global
@@ -323,6 +445,10 @@ __host__ __device__ inline int lo_mmax(int nx)
 template <typename R>
 __device__ void lo_solve_body(const LoCtx &x, int q, int sw)
 {
+    if constexpr (sizeof(R) == 4) {   // FP32 group solves: refined to FP64 accuracy
+        lo_solve_refined(x, q, sw);
+        return;
+    }
     extern __shared__ __align__(16) unsigned char smem_raw[];
     R *sm = reinterpret_cast<R *>(smem_raw);
     const int mmax = lo_mmax(x.nx);
@@ -906,10 +1032,18 @@ LoCtx make_lo_ctx(const Problem &p, double dt, const Level &L)
     return x;
 }
 
+// shared memory of one LO solve; the FP32 form with refinement keeps both copies of the
+// rows and falls back to the FP64 form where they do not fit (n_x above ~3100)
 static size_t lo_smem(int precision, int nx)
 {
-    const size_t rsz = lo_fp32(precision) ? sizeof(float) : sizeof(double);
-    return 6 * 32 * (size_t)lo_mmax(nx) * rsz;
+    const size_t S = 32 * (size_t)lo_mmax(nx);
+    if (lo_fp32(precision) && 6 * S * (sizeof(double) + sizeof(float)) <= 227 * 1024)
+        return 6 * S * (sizeof(double) + sizeof(float));
+    return 6 * S * sizeof(double);
+}
+static bool lo_refined(int precision, int nx)
+{
+    return lo_fp32(precision) && 6 * 32 * (size_t)lo_mmax(nx) * 12 <= 227 * 1024;
 }
 
 cudaError_t launch_lo_solve(const Problem &p, double dt, const Level &L)
@@ -918,7 +1052,7 @@ cudaError_t launch_lo_solve(const Problem &p, double dt, const Level &L)
     const size_t sm = lo_smem(p.precision, p.nx);
     const unsigned nb = (unsigned)L.n;
     cudaError_t e;
-    if (!lo_fp32(p.precision)) {
+    if (!lo_refined(p.precision, p.nx)) {
         e = cudaFuncSetAttribute(k_lo_solve<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)sm);
         if (e != cudaSuccess) return e;
@@ -937,7 +1071,7 @@ cudaError_t launch_lo_solve_b(int precision, int max_nx, const int *meta, int N,
 {
     const size_t sm = lo_smem(precision, max_nx);
     cudaError_t e;
-    if (!lo_fp32(precision)) {
+    if (!lo_refined(precision, max_nx)) {
         e = cudaFuncSetAttribute(k_lo_solve_b<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)sm);
         if (e != cudaSuccess) return e;

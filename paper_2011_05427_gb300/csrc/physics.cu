@@ -323,12 +323,20 @@ void host_group_B(int G, const double *edges, double T, double *B)
 // Clenshaw's recurrence on the Chebyshev coefficients.  Over the tabulated functions the
 // conversion keeps the sum's rounding error within a factor ~2 of |p(t)| (the coefficients
 // of a fit that reaches FP64 accuracy in 12 terms decay much faster than the growth of the
-// Chebyshev polynomials' monomial coefficients).
-__device__ inline double horner(const double *__restrict__ a, double t)
+// Chebyshev polynomials' monomial coefficients).  The terms from t^kTabLo on are at most
+// 3.3e-7 of |p| over the 17-, 1024- and 4096-group tables, so they are summed in FP32
+// (a_k stored in FP32, between 4e-33 and 1.2e5: normal numbers) and joined to the FP64
+// Horner sum of the low terms: a relative error of at most 3.4e-14 (CPU emulation of the
+// split on every table entry), for 4 FP32 FMAs and one conversion in place of 5 FP64 FMAs.
+__device__ inline double horner(const double *__restrict__ a, const float *__restrict__ b,
+                                double t, float tf)
 {
-    double p = a[kTabNC - 1];
+    float q = b[kTabNC - kTabLo - 1];
 #pragma unroll
-    for (int k = kTabNC - 2; k >= 0; --k) p = fma(p, t, a[k]);
+    for (int k = kTabNC - kTabLo - 2; k >= 0; --k) q = fmaf(q, tf, b[k]);
+    double p = (double)q;
+#pragma unroll
+    for (int k = kTabLo - 1; k >= 0; --k) p = fma(p, t, a[k]);
     return p;
 }
 
@@ -358,6 +366,7 @@ __host__ __device__ inline void group_ratios(double T, double ea, double eb, con
 // first.
 struct CellTerms {
     double T[32], iT[32], iT3[32], t[32];
+    float tf[32];
     int m[32];
 };
 
@@ -382,6 +391,7 @@ __device__ inline void stage_cells(const OpacityArgs &a, int i0, CellTerms &ct, 
             }
             ct.m[tx] = m;
             ct.t[tx] = t;
+            ct.tf[tx] = (float)t;
         }
     }
     __syncthreads();
@@ -405,10 +415,13 @@ __device__ inline void opacity_body(const OpacityArgs &a, int i0, int g0, const 
     if (m >= 0) {
         // tabulated: three polynomials in ln T on the cell's interval
         const double t = ct.t[tx];
-        const double *c = a.otab + ((size_t)g * kTabNI + m) * kTabNF * kTabNC;
-        sg = k27 * horner(c, t) * iT3;
-        sR = k27 * horner(c + kTabNC, t) * iT3;
-        em = k27 * kCB * Ti * mx.ex(horner(c + 2 * kTabNC, t) - xa);
+        const float tf = ct.tf[tx];
+        const double *c = a.otab + ((size_t)g * kTabNI + m) * kTabEntry;
+        const float *ch = reinterpret_cast<const float *>(c + kTabNF * kTabLo);
+        constexpr int kh = kTabNC - kTabLo;
+        sg = k27 * horner(c, ch, t, tf) * iT3;
+        sR = k27 * horner(c + kTabLo, ch + kh, t, tf) * iT3;
+        em = k27 * kCB * Ti * mx.ex(horner(c + 2 * kTabLo, ch + 2 * kh, t, tf) - xa);
     } else {
         const double xb = binf ? 0.0 : eb * iT;
         double dPs, Ns, Ds, om;
@@ -525,13 +538,18 @@ __global__ void k_otab_build(int G, const double *__restrict__ edges, double *__
     for (int k = 2; k < kTabNC; ++k)
         for (int j = 0; j < kTabNC; ++j)
             Tc[k][j] = (j > 0 ? 2.0 * Tc[k - 1][j - 1] : 0.0) - Tc[k - 2][j];
-    double *c = tab + (size_t)id * kTabNF * kTabNC;
+    double *c = tab + (size_t)id * kTabEntry;
+    float *chi = reinterpret_cast<float *>(c + kTabNF * kTabLo);
     for (int f = 0; f < kTabNF; ++f)
         for (int j = 0; j < kTabNC; ++j) {
             double aj = 0.0;
             for (int k = kTabNC - 1; k >= j; --k) aj = fma(ch[f][k], Tc[k][j], aj);
-            c[f * kTabNC + j] = aj;
+            if (j < kTabLo)
+                c[f * kTabLo + j] = aj;
+            else
+                chi[f * (kTabNC - kTabLo) + j - kTabLo] = (float)aj;
         }
+    if (kTabHiF > kTabNF * (kTabNC - kTabLo)) chi[kTabHiF - 1] = 0.f;
 }
 
 cudaError_t launch_otab_build(const Problem &p)

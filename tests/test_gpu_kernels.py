@@ -270,14 +270,17 @@ def test_lo_solve_parity(trt, orc, nx, ng):
     h = W.random_h(r, nx)
     lv = random_level(r, ng, nx)
     dt = 2e-3
-    s = solver(trt, nx=nx, N=2, G=17, h=h)
-    got = {k: v.cpu().numpy() for k, v in s.k_lo_solve(dt, lv).items()}
     ref = oracle_level_solve(orc, h, dt, lv)
-    assert rel(got["E"], ref["E"]) < 1e-11
-    Fs = np.abs(ref["F"]).max(1, keepdims=True)
-    assert np.max(np.abs(got["F"] - ref["F"]) / Fs) < 1e-11
-    assert rel(got["Eb0"], ref["Eb0"]) < 1e-10
-    assert np.max(np.abs(got["EbX"] - ref["EbX"]) / (np.abs(ref["EbX"]) + ref["E"][:, -1])) < 1e-10
+    # FP64, and FP32 eliminations refined by one FP64-residual step (FP64 accuracy up to
+    # the square of the FP32 solve's error, cond x 6e-8)
+    for precision, tol in (("fp64", 1e-11), ("lo32", 1e-9)):
+        s = solver(trt, nx=nx, N=2, G=17, h=h, precision=precision)
+        got = {k: v.cpu().numpy() for k, v in s.k_lo_solve(dt, lv).items()}
+        assert rel(got["E"], ref["E"]) < tol, precision
+        Fs = np.abs(ref["F"]).max(1, keepdims=True)
+        assert np.max(np.abs(got["F"] - ref["F"]) / Fs) < tol, precision
+        assert rel(got["Eb0"], ref["Eb0"]) < 10 * tol, precision
+        assert np.max(np.abs(got["EbX"] - ref["EbX"]) / (np.abs(ref["EbX"]) + ref["E"][:, -1])) < 10 * tol
 
 
 @pytest.mark.parametrize("n_from,n_to,eta,nx,fine",
