@@ -860,6 +860,64 @@ __device__ inline void block_max_bits(unsigned long long (&v)[kGreyNV], unsigned
     }
 }
 
+__device__ inline void grey_newton_cell(const GreyArgs &a, const Level &g, int have_prev, int i,
+                                        double &sa, double &ss, double &sL)
+{
+    const double cvdt = a.cv / a.dt;
+    const double k54 = 54.0 * a.s * kCB;
+    const double Ts = a.Tstar[i];
+    const double sig = g.sig[i];
+    const double Q = 2.0 * g.emis[i];
+    const double iTs = rcp64(Ts);
+    double dQ = k54;   // first edge at 0: (1 + x) e^{-x} = 1
+    if (a.nu_first != 0.0) {
+        const double x1 = a.nu_first * iTs;
+        dQ = k54 * (1.0 + x1) * exp(-x1);
+    }
+    if (!isinf(a.nu_last)) {
+        const double xL = a.nu_last * iTs;
+        dQ -= k54 * (1.0 + xL) * exp(-xL);
+    }
+    double D = 0.0;
+    if (have_prev) {
+        const double Tp = a.T_prev[i];
+        // secant only where |dT| is far above rounding (relative noise ~ eps T/|dT|)
+        if (fabs(Ts - Tp) > 1e-7 * Ts) D = (sig - a.sig_prev[i]) * rcp64(Ts - Tp);
+    }
+    const double base = cvdt + dQ;
+    double L = base - kC * D * g.Esum[i];
+    if (L < 0.5 * base) L = 0.5 * base;
+    const double iL = rcp64(L);
+    const double w = cvdt * iL;
+    sa = w * kC * sig;
+    ss = w * Q - (1.0 - w) * cvdt * (Ts - a.Told[i]);
+    sL = iL;
+}
+
+// T at cell i from the grey solution; the bad-value test and the norms' terms
+__device__ inline void grey_update_cell(const GreyArgs &a, const Level &g, int i, double sL,
+                                        unsigned long long (&v)[kGreyNV])
+{
+    const unsigned long long kInfBits = 0x7ff0000000000000ull;
+    const double cvdt = a.cv / a.dt;
+    const double Ts = a.Tstar[i];
+    const double E = g.E[i];
+    const double T = Ts + (kC * g.sig[i] * E - 2.0 * g.emis[i] - cvdt * (Ts - a.Told[i])) * sL;
+    a.T[i] = T;
+    const long long tb = __double_as_longlong(T);
+    const unsigned long long eb = (unsigned long long)__double_as_longlong(E) & 0x7fffffffffffffffull;
+    // T > 0 and finite: sign clear, not zero, below the infinity encoding
+    if (tb <= 0 || (unsigned long long)tb >= kInfBits || eb >= kInfBits) v[0] = 1ull;
+    if (a.want_norms) {
+        v[1] = umax64(v[1], nn_bits(fabs(T - a.Tcyc[i])));
+        v[2] = umax64(v[2], nn_bits(fabs(T)));
+        v[3] = umax64(v[3], nn_bits(fabs(E - a.Ecyc[i])));
+        v[4] = umax64(v[4], nn_bits(fabs(E)));
+        v[5] = umax64(v[5], nn_bits(fabs(T - a.Tphase[i])));
+        v[6] = umax64(v[6], nn_bits(fabs(E - a.Ephase[i])));
+    }
+}
+
 __device__ void grey_body(const GreyCtx &x)
 {
     const int have_prev = x.a.have_prev_dev ? *x.a.have_prev_dev : x.a.have_prev;
@@ -872,38 +930,10 @@ __device__ void grey_body(const GreyCtx &x)
     double *wsm = red + kGreyRed;   // warp-solver scratch
     const GreyArgs &a = x.a;
     const Level &g = x.lo.L;
-    const double cvdt = a.cv / a.dt;
-    const double k54 = 54.0 * a.s * kCB;   // d/dT [2 sum_g e_g] telescopes to the end edges
     for (int i = threadIdx.x; i < nx; i += blockDim.x) {
-        const double Ts = a.Tstar[i];
-        const double sig = g.sig[i];
-        const double Q = 2.0 * g.emis[i];
-        const double iTs = rcp64(Ts);
-        double dQ = k54;   // first edge at 0: (1 + x) e^{-x} = 1
-        if (a.nu_first != 0.0) {
-            const double x1 = a.nu_first * iTs;
-            dQ = k54 * (1.0 + x1) * exp(-x1);
-        }
-        if (!isinf(a.nu_last)) {
-            const double xL = a.nu_last * iTs;
-            dQ -= k54 * (1.0 + xL) * exp(-xL);
-        }
-        double D = 0.0;
-        if (have_prev) {
-            const double Tp = a.T_prev[i];
-            // secant only where |dT| is far above rounding (relative noise ~ eps T/|dT|)
-            if (fabs(Ts - Tp) > 1e-7 * Ts) D = (sig - a.sig_prev[i]) * rcp64(Ts - Tp);
-        }
-        const double base = cvdt + dQ;
-        double L = base - kC * D * g.Esum[i];
-        if (L < 0.5 * base) L = 0.5 * base;
-        const double iL = rcp64(L);
-        const double w = cvdt * iL;
-        sa[i] = w * kC * sig;
-        ss[i] = w * Q - (1.0 - w) * cvdt * (Ts - a.Told[i]);
-        sL[i] = iL;
-        a.sig_prev_out[i] = sig;
-        a.T_prev_out[i] = Ts;
+        grey_newton_cell(a, g, have_prev, i, sa[i], ss[i], sL[i]);
+        a.sig_prev_out[i] = g.sig[i];
+        a.T_prev_out[i] = a.Tstar[i];
     }
     __syncthreads();
     LoCtx lc = x.lo;
@@ -917,25 +947,7 @@ __device__ void grey_body(const GreyCtx &x)
     // v: bad flag, max|T - Tcyc|, max|T|, max|E - Ecyc|, max|E|, max|T - Tphase|,
     // max|E - Ephase| as non-negative encodings (flags[0 .. 6])
     unsigned long long v[kGreyNV] = {};
-    const unsigned long long kInfBits = 0x7ff0000000000000ull;
-    for (int i = threadIdx.x; i < nx; i += blockDim.x) {
-        const double Ts = a.Tstar[i];
-        const double E = g.E[i];
-        const double T = Ts + (kC * g.sig[i] * E - 2.0 * g.emis[i] - cvdt * (Ts - a.Told[i])) * sL[i];
-        a.T[i] = T;
-        const long long tb = __double_as_longlong(T);
-        const unsigned long long eb = (unsigned long long)__double_as_longlong(E) & 0x7fffffffffffffffull;
-        // T > 0 and finite: sign clear, not zero, below the infinity encoding
-        if (tb <= 0 || (unsigned long long)tb >= kInfBits || eb >= kInfBits) v[0] = 1ull;
-        if (a.want_norms) {
-            v[1] = umax64(v[1], nn_bits(fabs(T - a.Tcyc[i])));
-            v[2] = umax64(v[2], nn_bits(fabs(T)));
-            v[3] = umax64(v[3], nn_bits(fabs(E - a.Ecyc[i])));
-            v[4] = umax64(v[4], nn_bits(fabs(E)));
-            v[5] = umax64(v[5], nn_bits(fabs(T - a.Tphase[i])));
-            v[6] = umax64(v[6], nn_bits(fabs(E - a.Ephase[i])));
-        }
-    }
+    for (int i = threadIdx.x; i < nx; i += blockDim.x) grey_update_cell(a, g, i, sL[i], v);
     block_max_bits(v, reinterpret_cast<unsigned long long *>(red));
     if (threadIdx.x == 0) {
         if (v[0] != 0ull) a.flags[0] = 1.0;
