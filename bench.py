@@ -87,13 +87,17 @@ class Clocks:
                 "samples": len(sm)}
 
 
-def dist_init():
+def dist_init(backend=None):
+    """One process per GPU (torchrun's RANK / LOCAL_RANK / WORLD_SIZE).  The ranks are
+    replicas: each steps its own slab; the only collectives are the timing barrier and the
+    max / sum of scalars below (NCCL on GPUs, gloo for the host-side tests)."""
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if ws > 1:
         import torch.distributed as dist
-        dist.init_process_group("nccl")
+        if not dist.is_initialized():
+            dist.init_process_group(backend or "nccl")
     return ws, rank, local
 
 
@@ -103,24 +107,29 @@ def barrier(ws):
         dist.barrier()
 
 
-def max_over_ranks(x, ws):
+def _reduce(x, ws, op):
     if ws == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=getattr(dist.ReduceOp, op))
     return float(t.item())
+
+
+def max_over_ranks(x, ws):
+    return _reduce(x, ws, "MAX")
 
 
 def sum_over_ranks(x, ws):
-    if ws == 1:
-        return x
-    import torch
-    import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.SUM)
-    return float(t.item())
+    return _reduce(x, ws, "SUM")
+
+
+def job_throughput(units, seconds, ws):
+    """Whole-job throughput of N replicas: the units all ranks processed over the slowest
+    rank's time (weak scaling: each rank's work is fixed)."""
+    return sum_over_ranks(units, ws) / max_over_ranks(seconds, ws)
 
 
 # FP64 operations per sweep update (one cell, direction, group) of the simple corner
