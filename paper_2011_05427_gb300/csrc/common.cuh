@@ -30,7 +30,7 @@ struct SeriesTables {
     double einv, eL1, eL2;   // 32/ln2 and ln2/32 = eL1 + eL2 (texp)
 };
 // 1/d in FP64: the hardware's approximate FP64 reciprocal (special-function unit, a
-// relative error eps of order 2^-22, not the FP64 pipe) refined by one third-order
+// relative error eps below 2^-19.9 measured, not the FP64 pipe) refined by one third-order
 // Newton-Raphson (Householder) step: with e = 1 - d x, x (1 + e + e^2) = (1 - eps^3)/d,
 // below FP64 rounding, at 3 FP64 FMAs where an IEEE division costs ~20 on GB300's FP64
 // pipe.  Zero, infinite, NaN or subnormal operands (or results) divide; the test reads
