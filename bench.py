@@ -615,9 +615,20 @@ def main():
                     help="run the warm-up steps and one more step, print nothing (for ncu)")
     ap.add_argument("--profile-mlp", action="store_true",
                     help="run the fused MLP inference over 512,000 rows 3 times (for ncu)")
+    ap.add_argument("--profile-batch", type=int, default=0, metavar="N",
+                    help="step the first N slabs of batch_256 (FP32 sweeps, V-cycle): tile "
+                         "(8, 7), one warm-up step and one step (for ncu launch lists)")
     ap.add_argument("--tile", default=None,
                     help="D,shape: sweep tile for --profile-step (default: the library's)")
     args = ap.parse_args()
+    if args.profile_batch:
+        from paper_2011_05427_gb300 import trt
+        B = trt.Batch(W.batch_256(args.profile_batch), precision="sweep32", device="cuda:0")
+        B.set_tile(8, 7)
+        for _ in range(2):
+            B.step(1e-3, "V", 4, 1e-8)
+        B.close()
+        return
     if args.profile_mlp:
         import torch
         from paper_2011_05427_gb300 import closure, mlp

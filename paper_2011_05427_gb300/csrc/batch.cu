@@ -671,11 +671,6 @@ int capture_stage(trt_batch *b, int id)
     return TRT_OK;
 }
 
-void set_dyn(trt_batch *b, int cls, const std::vector<SlabState> &st, bool (*pred)(const SlabState &))
-{
-    for (int s = 0; s < b->n; ++s) b->h_dyn[cls * b->n + s] = pred(st[s]) ? 1 : 0;
-}
-
 }  // namespace
 
 extern "C" {

@@ -76,13 +76,6 @@ __device__ inline bool mbar_wait(uint64_t *bar, unsigned parity)
     return true;
 }
 
-// two FP32 values rounded to BF16 (nearest even) in one 32-bit word, lo in the low half
-__device__ inline uint32_t pack_bf16x2(float lo, float hi)
-{
-    const __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
-    return *reinterpret_cast<const uint32_t *>(&h);
-}
-
 __device__ inline void cp16(void *dst, const void *src, unsigned bytes)
 {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(su32(dst)), "l"(src),
