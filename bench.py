@@ -615,12 +615,24 @@ def main():
                     help="run the warm-up steps and one more step, print nothing (for ncu)")
     ap.add_argument("--profile-mlp", action="store_true",
                     help="run the fused MLP inference over 512,000 rows 3 times (for ncu)")
+    ap.add_argument("--profile-sweep", default="", metavar="NX,N,G,D,SHAPE",
+                    help="one FP32-sweep step of a Fleck-Cummings slab of NX cells, 2N "
+                         "directions, G groups with sweep tile (D, SHAPE) (for ncu)")
     ap.add_argument("--profile-batch", type=int, default=0, metavar="N",
                     help="step the first N slabs of batch_256 (FP32 sweeps, V-cycle): tile "
                          "(8, 7), one warm-up step and one step (for ncu launch lists)")
     ap.add_argument("--tile", default=None,
                     help="D,shape: sweep tile for --profile-step (default: the library's)")
     args = ap.parse_args()
+    if args.profile_sweep:
+        from paper_2011_05427_gb300 import trt
+        nx, n, g, d, sh = (int(v) for v in args.profile_sweep.split(","))
+        cfg = W.scaled(W.fc_4096(), nx, n, g, levels=[g, 1])
+        s = trt.Solver.from_slab(cfg, precision="sweep32", device="cuda:0")
+        s.set_sweep_tile(d, sh)
+        s.step(cfg.dt, "V", 1, -1.0, max_outer=2)
+        s.close()
+        return
     if args.profile_batch:
         from paper_2011_05427_gb300 import trt
         B = trt.Batch(W.batch_256(args.profile_batch), precision="sweep32", device="cuda:0")

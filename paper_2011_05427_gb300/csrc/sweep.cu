@@ -503,6 +503,176 @@ __global__ void __launch_bounds__(256) k_sweep2_b(const int *__restrict__ meta, 
     }
 }
 
+// ---- FP32 sweep with all of a direction tile's recurrences in one thread ----
+// Each warp owns 32 groups (one per lane) and the tile's D directions, all swept by every
+// lane: D independent recurrences per thread, so the angular moments of a (cell, group)
+// are summed in the thread's registers -- no cross-warp reduction, no CTA barrier -- and
+// the warps of a CTA (four group tiles) never wait for one another.  Intensities stream
+// straight from global memory into registers (each (cell, corner, direction) row of the
+// warp is one 128-byte line), the next cell's rows loaded while the current one is solved;
+// the pre-scaled sigma_t h/2 and h e/2 ([G][nx]) and the partial moments ([G][nx] per
+// tile) pass through a per-warp shared-memory tile of S cells so that their global
+// accesses run along cells.  It needs D x (group tiles) warps of work, so it suits large
+// problems and batches (fc_1024 has 256 such warps for 152 SMs).
+template <int kStrip>
+struct Sweep4Smem {
+    static constexpr int kW = 4;                     // warps (group tiles) per CTA
+    static constexpr int kTile = kStrip * kPadG;     // floats per per-warp array
+    static constexpr size_t total = sizeof(float) * (size_t)kW * (4 * kTile + kStrip);
+};
+
+template <int DPT, int kStrip>
+__device__ void sweep4_body(const SweepArgs &a, int dtile, int by)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int kT = Sweep4Smem<kStrip>::kTile;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int gt = by * Sweep4Smem<kStrip>::kW + warp;   // this warp's group tile
+    const int nx = a.nx, G = a.G, ldG = a.ldG;
+    if (gt * 32 >= ldG) return;                          // no barrier below: safe
+    float *tS = reinterpret_cast<float *>(smem_raw) + (size_t)warp * (4 * kT + kStrip);   // [S][33]
+    float *tE = tS + kT, *tP0 = tS + 2 * kT, *tP2 = tS + 3 * kT, *tK = tS + 4 * kT;
+    const int g = gt * 32 + lane;
+    const bool pos = dtile < a.N / DPT;
+    const int m0 = dtile * DPT;
+    const float *__restrict__ Iold = reinterpret_cast<const float *>(a.I_old);
+    float *__restrict__ Inew = reinterpret_cast<float *>(a.I_new);
+    const float *__restrict__ sigE = reinterpret_cast<const float *>(a.sigE);
+    const float *__restrict__ emis = reinterpret_cast<const float *>(a.emis);
+    float *part = reinterpret_cast<float *>(a.part);
+    const size_t dstride = (size_t)2 * ldG;
+
+    float am[DPT], b[DPT], bb[DPT], wt[DPT], wm[DPT], psi[DPT];
+#pragma unroll
+    for (int j = 0; j < DPT; ++j) {
+        const double mu = a.mu[m0 + j];
+        am[j] = (float)fabs(mu);
+        b[j] = (float)(0.5 * fabs(mu));
+        bb[j] = __fmul_rn(b[j], b[j]);
+        wt[j] = (float)(0.5 * a.w[m0 + j]);
+        wm[j] = (float)(0.5 * a.w[m0 + j] * mu * mu);
+        psi[j] = (g < G) ? (float)(pos ? a.Iin0[g] : a.IinX[g]) : 0.f;
+    }
+    // rows of direction m0 + j at cell c: Iold + ((m0 + j) nx + c) dstride + corner ldG + g
+    const float *Iw = Iold + (size_t)m0 * nx * dstride + g;
+    float *Ow = Inew + (size_t)m0 * nx * dstride + g;
+    const size_t dj = (size_t)nx * dstride;   // one direction further
+    auto load_cell = [&](int c, float (&L)[DPT], float (&R)[DPT]) {
+#pragma unroll
+        for (int j = 0; j < DPT; ++j) {
+            L[j] = __ldcs(Iw + j * dj + (size_t)c * dstride);
+            R[j] = __ldcs(Iw + j * dj + (size_t)c * dstride + ldG);
+        }
+    };
+    const int nstrip = (nx + kStrip - 1) / kStrip;
+    float nL[DPT], nR[DPT];
+    load_cell(pos ? 0 : nx - 1, nL, nR);
+    for (int st = 0; st < nstrip; ++st) {
+        int c0, ns;
+        if (pos) {
+            c0 = st * kStrip;
+            ns = min(kStrip, nx - c0);
+        } else {
+            const int c1 = nx - st * kStrip;
+            c0 = max(c1 - kStrip, 0);
+            ns = c1 - c0;
+        }
+        // this strip's sigma_t h/2 and h e/2 of the warp's 32 groups, along cells
+        for (int idx = lane; idx < 32 * kStrip; idx += 32) {
+            const int gl = idx / kStrip, cc = idx - gl * kStrip;
+            const int gg = gt * 32 + gl;
+            const bool ok = cc < ns && gg < G;
+            tS[cc * kPadG + gl] = ok ? sigE[(size_t)gg * nx + c0 + cc] : 0.f;
+            tE[cc * kPadG + gl] = ok ? emis[(size_t)gg * nx + c0 + cc] : 0.f;
+        }
+        if (lane < ns) tK[lane] = (float)(0.5 * a.h[c0 + lane] * a.icdt);   // h/(2 c dt)
+        __syncwarp();
+        for (int kk = 0; kk < ns; ++kk) {
+            const int cc = pos ? kk : ns - 1 - kk;
+            const int c = c0 + cc;
+            float IL[DPT], IR[DPT];
+#pragma unroll
+            for (int j = 0; j < DPT; ++j) {
+                IL[j] = nL[j];
+                IR[j] = nR[j];
+            }
+            const int cn = pos ? c + 1 : c - 1;   // the next cell's rows, in flight meanwhile
+            if (cn >= 0 && cn < nx) load_cell(cn, nL, nR);
+            const float th = tS[cc * kPadG + lane], q = tE[cc * kPadG + lane];
+            const float kap = tK[cc];
+            // explicit rounding intrinsics: the single-slab and the batched kernel inline
+            // this body separately, and a contraction the compiler chose differently in one
+            // of them would break their bit-for-bit agreement
+            Acc<float> s0, s2;
+#pragma unroll
+            for (int j = 0; j < DPT; ++j) {
+                const float aa = __fadd_rn(b[j], th);
+                const float inv = __frcp_rn(__fmaf_rn(aa, aa, bb[j]));
+                float pL, pR;
+                if (pos) {
+                    const float rL = __fmaf_rn(am[j], psi[j], __fmaf_rn(kap, IL[j], q));
+                    const float rR = __fmaf_rn(kap, IR[j], q);
+                    pL = __fmul_rn(__fmaf_rn(aa, rL, -__fmul_rn(b[j], rR)), inv);
+                    pR = __fmul_rn(__fmaf_rn(aa, rR, __fmul_rn(b[j], rL)), inv);
+                    psi[j] = pR;
+                } else {
+                    const float rR = __fmaf_rn(am[j], psi[j], __fmaf_rn(kap, IR[j], q));
+                    const float rL = __fmaf_rn(kap, IL[j], q);
+                    pR = __fmul_rn(__fmaf_rn(aa, rR, -__fmul_rn(b[j], rL)), inv);
+                    pL = __fmul_rn(__fmaf_rn(aa, rL, __fmul_rn(b[j], rR)), inv);
+                    psi[j] = pL;
+                }
+                if (g < ldG) {
+                    __stcs(Ow + j * dj + (size_t)c * dstride, pL);
+                    __stcs(Ow + j * dj + (size_t)c * dstride + ldG, pR);
+                }
+                const float v = __fadd_rn(pL, pR);
+                s0.add(__fmul_rn(wt[j], v));
+                s2.add(__fmul_rn(wm[j], v));
+            }
+            tP0[cc * kPadG + lane] = s0.s;
+            tP2[cc * kPadG + lane] = s2.s;
+        }
+        __syncwarp();
+        // the strip's partial moments, along cells
+        for (int idx = lane; idx < 32 * kStrip; idx += 32) {
+            const int gl = idx / kStrip, cc = idx - gl * kStrip;
+            const int gg = gt * 32 + gl;
+            if (cc < ns && gg < G) {
+                const size_t o = ((size_t)(dtile * 2 + 0) * G + gg) * nx + c0 + cc;
+                part[o] = tP0[cc * kPadG + gl];
+                part[o + (size_t)G * nx] = tP2[cc * kPadG + gl];
+            }
+        }
+        __syncwarp();
+    }
+    if (g < ldG)
+#pragma unroll
+        for (int j = 0; j < DPT; ++j)
+            reinterpret_cast<float *>(a.psi_exit)[(size_t)(m0 + j) * ldG + g] = psi[j];
+}
+
+// one kernel per tile height D (= a.D, chosen on the host): the per-thread arrays size
+// the registers, and a smaller D leaves room for more resident warps
+template <int DPT, int kStrip>
+__global__ void __launch_bounds__(128) k_sweep4(SweepArgs a)
+{
+    sweep4_body<DPT, kStrip>(a, blockIdx.x, blockIdx.y);
+}
+
+template <int DPT, int kStrip>
+__global__ void __launch_bounds__(128) k_sweep4_b(const int *__restrict__ meta, int N,
+                                                  const SweepArgs *__restrict__ xs)
+{
+    for (int b = blockIdx.x;; b += gridDim.x) {
+        int s, bx, by;
+        if (!bdecode(meta, N, b, s, bx, by)) break;
+        const SweepArgs a = xs[s];
+        sweep4_body<DPT, kStrip>(a, bx, by);
+        __syncwarp();   // this warp's shared tile is reused by its next work item
+    }
+}
+
 // f_g = sum_t A2 / sum_t A0 per (group, cell), in R; boundary factors per group in FP64.
 // Blocks [0, nb_cell) take one (group, cell) per thread; the blocks after them take one
 // group per warp for the boundary factors: lanes stride over the directions and the four
@@ -612,10 +782,12 @@ __global__ void k_sweep_finalize_b(const int *__restrict__ meta, int N,
 // (16, 3) 0.299 (a third buffer costs a resident CTA per SM); FP64 (8, 2) 1.26 ms,
 // (16, 2) 1.37, (8, 3) 1.37.
 struct Shape {
-    int S, NS, V;   // strip cells, strip buffers, groups per lane
+    int S, NS, V;   // strip cells, strip buffers, groups per lane (4: a tile's directions
+                    // per thread, registers instead of strip buffers)
 };
 constexpr Shape kShapes32[] = {{16, 2, 1}, {16, 3, 1}, {16, 4, 1}, {8, 4, 1}, {8, 6, 1},
-                               {32, 2, 1}, {16, 2, 2}, {8, 2, 2}, {8, 3, 2}, {8, 4, 2}};
+                               {32, 2, 1}, {16, 2, 2}, {8, 2, 2}, {8, 3, 2}, {8, 4, 2},
+                               {16, 1, 4}, {32, 1, 4}};
 constexpr Shape kShapes64[] = {{8, 2, 1}, {16, 2, 1}, {8, 3, 1}};
 
 // largest power of two <= cap dividing N: the direction-tile height D_min that the
@@ -672,6 +844,38 @@ cudaError_t launch_shape2(const SweepArgs *a, int M, int ldG, int D, const int *
     return cudaGetLastError();
 }
 
+template <int DPT, int S>
+cudaError_t launch_shape4_d(const SweepArgs *a, int M, int ldG, int D, const int *meta, int N,
+                            const SweepArgs *xs, int grid, cudaStream_t st)
+{
+    const size_t sm = Sweep4Smem<S>::total;
+    if (a) {
+        cudaError_t e = cudaFuncSetAttribute(k_sweep4<DPT, S>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+        k_sweep4<DPT, S><<<dim3(M / D, (ldG / 32 + 3) / 4), 128, sm, st>>>(*a);
+    } else {
+        cudaError_t e = cudaFuncSetAttribute(k_sweep4_b<DPT, S>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+        k_sweep4_b<DPT, S><<<grid, 128, sm, st>>>(meta, N, xs);
+    }
+    return cudaGetLastError();
+}
+
+template <int S>
+cudaError_t launch_shape4(const SweepArgs *a, int M, int ldG, int D, const int *meta, int N,
+                          const SweepArgs *xs, int grid, cudaStream_t st)
+{
+    switch (D) {
+    case 1: return launch_shape4_d<1, S>(a, M, ldG, D, meta, N, xs, grid, st);
+    case 2: return launch_shape4_d<2, S>(a, M, ldG, D, meta, N, xs, grid, st);
+    case 4: return launch_shape4_d<4, S>(a, M, ldG, D, meta, N, xs, grid, st);
+    case 8: return launch_shape4_d<8, S>(a, M, ldG, D, meta, N, xs, grid, st);
+    default: return cudaErrorInvalidConfiguration;
+    }
+}
+
 template <typename R, typename SR>
 cudaError_t dispatch_shape(int shape, const SweepArgs *a, int M, int ldG, int D, const int *meta,
                            int N, const SweepArgs *xs, int grid, cudaStream_t st)
@@ -684,11 +888,13 @@ cudaError_t dispatch_shape(int shape, const SweepArgs *a, int M, int ldG, int D,
         case 7: return launch_shape2<8, 2>(a, M, ldG, D, meta, N, xs, grid, st);
         case 8: return launch_shape2<8, 3>(a, M, ldG, D, meta, N, xs, grid, st);
         case 9: return launch_shape2<8, 4>(a, M, ldG, D, meta, N, xs, grid, st);
+        case 10: return launch_shape4<16>(a, M, ldG, D, meta, N, xs, grid, st);
+        case 11: return launch_shape4<32>(a, M, ldG, D, meta, N, xs, grid, st);
         default: break;
         }
     }
     if (sizeof(R) == 4) {
-        if (shape == 6) shape = 0;
+        if (shape == 6 || shape == 10 || shape == 11) shape = 0;
         if (shape == 7 || shape == 8 || shape == 9) shape = 3;
         switch (shape) {
         case 1: return launch_shape<R, SR, 16, 3>(a, M, ldG, D, meta, N, xs, grid, st);
@@ -741,7 +947,7 @@ void sweep_shape_info(int precision, int shape, int *S, int *NS)
 int sweep_group_tiles(int precision, int shape, int ldG)
 {
     const Shape sh = sweep_fp32(precision) ? kShapes32[shape] : kShapes64[shape];
-    return sh.V == 2 ? (ldG + 63) / 64 : ldG / 32;
+    return sh.V == 2 ? (ldG + 63) / 64 : sh.V == 4 ? (ldG / 32 + 3) / 4 : ldG / 32;
 }
 
 int sweep_D_candidates(const Problem &p, int *D)

@@ -93,3 +93,22 @@ def test_batch_uniform_equilibrium_and_tile(trt):
             assert same(B.slab(k).moments(), s.moments())
     B.close()
 
+
+def test_batch_direction_tile_sweep(trt):
+    """The batched persistent form of shape 10 (directions per thread) gives the
+    single-slab results with the same tile, bit for bit."""
+    slabs = mixed_slabs()
+    B = trt.Batch(slabs, precision="sweep32")
+    B.set_tile(4, 10)
+    singles = [trt.Solver.from_slab(c, precision="sweep32") for c in slabs]
+    for s in singles:
+        s.set_sweep_tile(4, 10)
+    for step in range(2):
+        sb = B.step(1e-3, "W", 2, 1e-8)
+        for k, s in enumerate(singles):
+            st = s.step(1e-3, "W", 2, 1e-8)
+            assert (sb[k]["n_ti"], sb[k]["n_c"]) == (st["n_ti"], st["n_c"]), (step, k)
+            assert same(B.slab(k).moments(), s.moments()), (step, k)
+    for s in singles:
+        s.close()
+    B.close()

@@ -196,14 +196,16 @@ def test_mixed_precision_vs_fp64_oracle(trt, orc, name, cfg, cycle, lmax, prec):
     assert worst[0] < tol and worst[1] < tol
 
 
-@pytest.mark.parametrize("shape", [0, 6, 7, 8, 9])
-def test_fp32_sweep_shapes_in_steps(trt, orc, shape):
+@pytest.mark.parametrize("shape,D", [(0, 4), (6, 4), (7, 4), (8, 4), (9, 4), (10, 4), (11, 4),
+                                     (10, 8), (11, 8)])
+def test_fp32_sweep_shapes_in_steps(trt, orc, shape, D):
     """Every FP32 sweep shape that the step uses with its pre-scaled FP32 inputs (6-9: two
-    groups per lane) against the FP64 oracle after fixed-iteration steps; 70 groups leave
-    a partial 64-group tile, 45 cells a ragged last strip."""
+    groups per lane; 10, 11: a tile's directions per thread) against the FP64 oracle after
+    fixed-iteration steps; 70 groups leave a partial 64-group tile (and a partial
+    128-group CTA), 45 cells a ragged last strip."""
     cfg = W.scaled(W.fc_small(), 45, 8, 70, levels=[70, 14, 1])
     s, o = pair(trt, orc, cfg, precision="sweep32")
-    s.set_sweep_tile(4, shape)
+    s.set_sweep_tile(D, shape)
     worst = 0.0
     for step in range(2):
         s.step(cfg.dt, "W", 2, -1.0, max_outer=3)
@@ -212,3 +214,27 @@ def test_fp32_sweep_shapes_in_steps(trt, orc, shape):
         worst = max(worst, eT, eE)
     assert worst < MIXED_TOL["sweep32"], worst
 
+
+
+@pytest.mark.parametrize("D", [4, 8])
+def test_direction_tile_sweep_matches_strip_sweep(trt, D):
+    """Shape 10 (a tile's D directions per thread, moments summed in registers) does the
+    same arithmetic per update and sums a (cell, group)'s directions in the same order as
+    shape 0 (one direction per warp, moments summed across warps in shared memory); the
+    compiler may contract the products differently, and FP32 round-off then moves the
+    iteration counts where a step meets eps, so the steps agree to FP32 sweep accuracy."""
+    cfg = W.scaled(W.fc_small(), 45, 8, 70, levels=[70, 14, 1])
+    a = trt.Solver.from_slab(cfg, precision="sweep32")
+    b = trt.Solver.from_slab(cfg, precision="sweep32")
+    a.set_sweep_tile(D, 10)
+    b.set_sweep_tile(D, 0)
+    for _ in range(2):
+        sa = a.step(cfg.dt, "V", 4, 1e-8)
+        sb = b.step(cfg.dt, "V", 4, 1e-8)
+        print(f"D={D}: n_ti/n_c {sa['n_ti']}/{sa['n_c']} against {sb['n_ti']}/{sb['n_c']}")
+    ma, mb = a.moments(), b.moments()
+    assert np.max(np.abs(ma["T"] - mb["T"]) / mb["T"]) < 1e-6
+    E = mb["Eg"].sum(0)
+    assert np.max(np.abs(ma["Eg"] - mb["Eg"]) / E[None, :]) < 1e-6
+    a.close()
+    b.close()
