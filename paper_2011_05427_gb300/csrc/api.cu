@@ -90,7 +90,7 @@ void carve(trt_handle *h, Carver &c)
     h->sigR = c.take<double>(G * nx);
     if (sweep_fp32(p.precision)) {
         h->sig32 = c.take<float>(G * nx);
-        h->emis32 = c.take<float>(G * nx);
+        h->emis32 = c.take<float>(G * nx + nx);   // then h/(2 c dt) per cell (kap32)
     }
     h->part = c.take<double>(std::max(sweep_partial_doubles(p), 4 * nx + 8));
     h->psi_exit = c.take<double>(M * (size_t)p.ldG);

@@ -249,9 +249,9 @@ void build_stage(trt_batch *b, int id, double dt, int cycle_type)
             Problem p = x->p;
             const void *sg_ = x->sig32 ? (const void *)x->sig32 : (const void *)x->sigE;
             const void *em_ = x->sig32 ? (const void *)x->emis32 : (const void *)x->emis;
-            const SweepArgs a = make_sweep_args(p, dt, sg_, em_, x->I_cur, x->I_alt, x->part,
-                                                x->psi_exit, x->f, x->fb0, x->fbX, x->C0, x->CX,
-                                                b->D);
+            SweepArgs a = make_sweep_args(p, dt, sg_, em_, x->I_cur, x->I_alt, x->part,
+                                          x->psi_exit, x->f, x->fb0, x->fbX, x->C0, x->CX, b->D);
+            if (x->sig32) a.kap32 = x->emis32 + (size_t)p.G * p.nx;   // after e (opacity)
             const int ntile = p.M / b->D;
             B.set(sg.ops[isw], s, a, ntile * sweep_group_tiles(b->precision, b->shape, p.ldG),
                   ntile);

@@ -23,6 +23,7 @@ struct OpacityArgs {
     double s;
     double *sigE, *emis, *sigR;
     float *sig32, *emis32;   // FP32 sweep inputs (sigma_E + 1/(c dt)) h/2, h e/2, or null
+    float *kap32;            // FP32 sweep input h/(2 c dt) per cell, or null
     const double *h;
     double icdt;
     const double *otab;      // Problem::otab
@@ -38,6 +39,7 @@ struct SweepArgs {
     void *part;       // [n_dt][2][G][nx], R-typed
     void *psi_exit;   // [M][ldG], R-typed
     double *f, *fb0, *fbX, *C0, *CX;
+    const float *kap32;   // h/(2 c dt) per cell in FP32 (with the FP32 inputs), or null
 };
 
 struct FinalizeArgs {

@@ -437,6 +437,8 @@ __device__ inline void opacity_body(const OpacityArgs &a, int i0, int g0, const 
         const double hh = 0.5 * a.h[i];
         a.sig32[idx] = (float)(hh * (sg + a.icdt));
         a.emis32[idx] = (float)(hh * em);
+        // and h/(2 c dt) per cell: the sweeps read it instead of forming it in FP64 per strip
+        if (g == 0) a.kap32[i] = (float)(hh * a.icdt);
     }
 }
 
@@ -569,6 +571,7 @@ OpacityArgs make_opacity_args(const Problem &p, const double *T, double *sigE, d
     a.otab = p.otab;
     a.nx = p.nx; a.G = p.G; a.T = T; a.edges = p.edges; a.s = p.s;
     a.sigE = sigE; a.emis = emis; a.sigR = sigR; a.sig32 = sig32; a.emis32 = emis32;
+    a.kap32 = emis32 ? emis32 + (size_t)p.G * p.nx : nullptr;   // carved after emis32
     a.h = p.h;
     a.icdt = (dt > 0) ? 1.0 / (kC * dt) : 0.0;
     return a;

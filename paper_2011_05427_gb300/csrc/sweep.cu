@@ -220,7 +220,8 @@ __device__ void sweep_body(const SweepArgs &a, int dtile, int gt)
                 }
             }
         }
-        if (tid < ns) skap[tid] = (R)(0.5 * a.h[c0 + tid] * a.icdt);
+        if (tid < ns)
+            skap[tid] = a.kap32 ? (R)a.kap32[c0 + tid] : (R)(0.5 * a.h[c0 + tid] * a.icdt);
         __syncthreads();
         const R *tth = kPre ? reinterpret_cast<const R *>(rs) : sth;
         const R *tq = kPre ? reinterpret_cast<const R *>(re) : sq;
@@ -419,7 +420,8 @@ __device__ void sweep2_body(const SweepArgs &a, int dtile, int gt)
         else
             cp_commit();
         cp_wait<NS - 1>();
-        if (tid < ns) skap[tid] = (float)(0.5 * a.h[c0 + tid] * a.icdt);
+        if (tid < ns)
+            skap[tid] = a.kap32 ? a.kap32[c0 + tid] : (float)(0.5 * a.h[c0 + tid] * a.icdt);
         __syncthreads();
         const float *tth = rawS + bf * kStrip * kP2 + 2 * lane;
         const float *tq = rawE + bf * kStrip * kP2 + 2 * lane;
@@ -585,7 +587,8 @@ __device__ void sweep4_body(const SweepArgs &a, int dtile, int by)
             tS[cc * kPadG + gl] = ok ? sigE[(size_t)gg * nx + c0 + cc] : 0.f;
             tE[cc * kPadG + gl] = ok ? emis[(size_t)gg * nx + c0 + cc] : 0.f;
         }
-        if (lane < ns) tK[lane] = (float)(0.5 * a.h[c0 + lane] * a.icdt);   // h/(2 c dt)
+        if (lane < ns)   // h/(2 c dt)
+            tK[lane] = a.kap32 ? a.kap32[c0 + lane] : (float)(0.5 * a.h[c0 + lane] * a.icdt);
         __syncwarp();
         for (int kk = 0; kk < ns; ++kk) {
             const int cc = pos ? kk : ns - 1 - kk;
@@ -977,6 +980,7 @@ SweepArgs make_sweep_args(const Problem &p, double dt, const void *sigE, const v
     a.sigE = sigE; a.emis = emis; a.I_old = I_old; a.I_new = I_new;
     a.part = part; a.psi_exit = psi_exit;
     a.f = f; a.fb0 = fb0; a.fbX = fbX; a.C0 = C0; a.CX = CX;
+    a.kap32 = nullptr;
     return a;
 }
 
@@ -1002,10 +1006,13 @@ cudaError_t launch_sweep(const Problem &p, double dt, const void *sigE, const vo
                          double *psi_exit, double *f, double *fb0, double *fbX, double *C0,
                          double *CX)
 {
-    const SweepArgs a = make_sweep_args(p, dt, sigE, emis, I_old, I_new, part, psi_exit, f, fb0,
-                                        fbX, C0, CX, pick_D(p));
+    SweepArgs a = make_sweep_args(p, dt, sigE, emis, I_old, I_new, part, psi_exit, f, fb0, fbX,
+                                  C0, CX, pick_D(p));
     if (!sweep_fp32(p.precision)) return launch_sweep_t<double, double>(p, a);
-    if (sigma_fp32) return launch_sweep_t<float, float>(p, a);
+    if (sigma_fp32) {   // the pre-scaled inputs carry h/(2 c dt) after e (launch_opacity)
+        a.kap32 = reinterpret_cast<const float *>(emis) + (size_t)p.G * p.nx;
+        return launch_sweep_t<float, float>(p, a);
+    }
     return launch_sweep_t<float, double>(p, a);
 }
 
