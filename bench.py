@@ -141,31 +141,51 @@ FLOP_PER_UPDATE = 23
 # the nominal 1.25 TFLOP/s.
 FP64_PEAK_TFLOPS = 1.25
 
-# dram__bytes_read.sum + dram__bytes_write.sum of one launch, from the ncu capture named
-# in profiles/, valid while the kernel source has the recorded SHA-256 (else null).
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum, one ncu capture of the
-# sweep and its finalize on the fc_1024 workload, tile D = 8 directions per CTA), valid while
-# the kernel source hashes to `sha`; profiles/ holds the capture's summary and command.
+# sweep and its finalize on the fc_1024 workload), valid while the kernel sources hash to
+# `sha` and the tuned tile (D, shape) is the captured one; profiles/ holds the capture's
+# summary and command.
 TRAFFIC = {
-    "sweep_fp64": {"file": "sweep.cu", "sha": "4bc1c6ebaf808806",
-                   "bytes": 540345344 + 542153728 + 66106880 + 11776},
-    "sweep_fp32": {"file": "sweep.cu", "sha": "4bc1c6ebaf808806",
-                   "bytes": 269907968 + 244601600 + 33077248 + 0},
+    "sweep_fp64": {"files": ("sweep.cu",), "sha": "fc7b8491192d38f9", "tile": (8, 0),
+                   "bytes": 540402176 + 542182912 + 66101504 + 42240},
+    "sweep_fp32": {"files": ("sweepf.cu", "sweep.cu"), "sha": "58cff6c8febc609d", "tile": (8, 16),
+                   "bytes": 269985536 + 242853888 + 33072640 + 0},
 }
 
 
-def _src_sha(name):
+def _src_sha(names):
     import hashlib
-    p = os.path.join(ROOT, "paper_2011_05427_gb300", "csrc", name)
-    with open(p, "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
+    h = hashlib.sha256()
+    for name in names:
+        with open(os.path.join(ROOT, "paper_2011_05427_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
 
 
-def _traffic(key):
+def _traffic(key, tile):
     t = TRAFFIC.get(key)
-    if not t:
+    if not t or t["bytes"] is None or tuple(tile) != t["tile"]:
         return None
-    return t["bytes"] if _src_sha(t["file"]) == t["sha"] else None
+    return t["bytes"] if _src_sha(t["files"]) == t["sha"] else None
+
+
+def sweep_kernel(fp32, D, shape):
+    """The kernels one sweep launches for tile (D, shape) (the library's shape table)."""
+    if not fp32:
+        S, NS = {0: (8, 2), 1: (16, 2), 2: (8, 3)}[shape]
+        return f"k_sweep<double,double,{S},{NS}> + k_sweep_finalize<double>"
+    one = {0: (16, 2), 1: (16, 3), 2: (16, 4), 3: (8, 4), 4: (8, 6), 5: (32, 2)}
+    if shape in one:
+        k = "k_sweep<float,float,%d,%d>" % one[shape]
+    elif shape in (6, 7, 8, 9):
+        k = "k_sweep2<%d,%d>" % {6: (16, 2), 7: (8, 2), 8: (8, 3), 9: (8, 4)}[shape]
+    elif shape in (10, 11):
+        k = "k_sweep4<%d,%d>" % (D, 16 if shape == 10 else 32)
+    else:   # lean sweeps: groups per lane, strip, buffers, directions per CTA
+        gpl, S, NS = {12: (1, 16, 2), 13: (1, 8, 3), 14: (1, 8, 2), 15: (2, 8, 2),
+                      16: (2, 8, 4), 17: (1, 8, 4)}[shape]
+        k = "k_sweepf<%d,%d,%d,%d>" % (gpl, S, NS, D)
+    return k + " + k_sweep_finalize<float>"
 
 
 def sweep_roofline(trt, s, cfg, fp32=False, local=0, reps=20):
@@ -181,6 +201,9 @@ def sweep_roofline(trt, s, cfg, fp32=False, local=0, reps=20):
         s = trt.Solver.from_slab(cfg, precision="sweep32" if fp32 else "fp64",
                                  device=f"cuda:{local}")
         tile = s.autotune(cfg.dt, reps=3)
+    D, shape = s.sweep_tile()
+    if D == 0:   # the library default: the largest power of two <= 8 dividing N
+        D = max(d for d in (1, 2, 4, 8) if cfg.N % d == 0)
     ms = s.sweep_time(cfg.dt, reps=reps)
     if own:
         s.close()
@@ -190,8 +213,8 @@ def sweep_roofline(trt, s, cfg, fp32=False, local=0, reps=20):
         hbm, src = peaks()
         ach = bytes_alg / (ms * 1e-3) / 1e9
         roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
-                "frac": ach / hbm, "traffic": _traffic("sweep_fp32"),
-                "kernel": "k_sweep<float,float> + k_sweep_finalize<float>", "ms": ms,
+                "frac": ach / hbm, "traffic": _traffic("sweep_fp32", (D, shape)),
+                "kernel": sweep_kernel(True, D, shape), "ms": ms,
                 "algorithmic_bytes": bytes_alg,
                 "peak_source": f"{src} (MEASURED_PEAKS hbm_gbs, copy)",
                 "updates_per_s": upd / (ms * 1e-3)}
@@ -199,15 +222,15 @@ def sweep_roofline(trt, s, cfg, fp32=False, local=0, reps=20):
         flops = FLOP_PER_UPDATE * upd
         ach = flops / (ms * 1e-3) / 1e12
         roof = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": ach / FP64_PEAK_TFLOPS, "traffic": _traffic("sweep_fp64"),
-                "kernel": "k_sweep<double,double> + k_sweep_finalize<double>", "ms": ms,
+                "frac": ach / FP64_PEAK_TFLOPS, "traffic": _traffic("sweep_fp64", (D, shape)),
+                "kernel": sweep_kernel(False, D, shape), "ms": ms,
                 "algorithmic_flops": flops,
                 "peak_source": "derived: 152 SMs x 2.07 GHz x 2 FP64 FMA/clk x 2 (nominal "
                                "1.25 TFLOP/s FP64)",
                 "hbm_frac": upd * 32 / (ms * 1e-3) / 1e9 / peaks()[0],
                 "updates_per_s": upd / (ms * 1e-3)}
     if tile:
-        roof["tile"] = {"D": tile[0], "S": tile[1], "NS": tile[2]}
+        roof["tile"] = {"D": tile[0], "S": tile[1], "NS": tile[2], "shape": shape}
     return {"roofline": roof, "ms": ms}
 
 

@@ -259,6 +259,10 @@ int trt_autotune(trt_handle *h, double dt, int reps, int *D, int *S, int *NS);
  * shape index in [0, trt_sweep_shapes(h)); returns TRT_EINVAL otherwise. */
 int trt_sweep_shapes(const trt_handle *h);
 int trt_set_sweep_tile(trt_handle *h, int D, int shape);
+/* The sweep tile the next step uses (after trt_autotune, trt_set_sweep_tile or neither):
+ * *D = directions per CTA (0: the library's default for this problem), *shape = shape index.
+ * Either pointer may be NULL.  TRT_EINVAL for a NULL handle. */
+int trt_get_sweep_tile(const trt_handle *h, int *D, int *shape);
 
 /* One frequency-grid level of the low-order system, device arrays (FP64).
  * fine = 0: a coarse or grey level with the arrays below.

@@ -72,6 +72,7 @@ void carve(trt_handle *h, Carver &c)
     p.EinX = c.take<double>(G); p.FinX = c.take<double>(G);
     p.ihf = c.take<double>(nx + 1);
     p.hf = c.take<double>(nx + 1);
+    p.dir32 = reinterpret_cast<float *>(c.take<double>(2 * M));
     p.lo_slot = reinterpret_cast<int *>(c.take<double>((nx + 2) / 2));
     p.otab = c.take<double>(otab_doubles((int)G));
     p.rscratch_doubles = restrict_scratch_doubles((int)nx, (int)G, 1);
@@ -361,6 +362,15 @@ int trt_create(const trt_grid *grid, const trt_angles *angles, const trt_groups 
     };
     CK(up(p.h, hh)); CK(up(p.ihf, ihf)); CK(up(p.hf, hf)); CK(up(p.edges, edges)); CK(up(p.mu, mu)); CK(up(p.w, w));
     CK(cudaMemcpyAsync(p.lo_slot, lo_slot.data(), lo_slot.size() * sizeof(int),
+                       cudaMemcpyHostToDevice, p.stream));
+    std::vector<float> dir32(4 * (size_t)p.M);   // the FP32 sweeps' per-direction constants
+    for (int m = 0; m < p.M; ++m) {
+        dir32[4 * m + 0] = (float)std::fabs(mu[m]);
+        dir32[4 * m + 1] = (float)(0.5 * std::fabs(mu[m]));
+        dir32[4 * m + 2] = (float)(0.5 * w[m]);
+        dir32[4 * m + 3] = (float)(0.5 * w[m] * mu[m] * mu[m]);
+    }
+    CK(cudaMemcpyAsync(p.dir32, dir32.data(), dir32.size() * sizeof(float),
                        cudaMemcpyHostToDevice, p.stream));
     CK(up(p.Iin0, Iin0)); CK(up(p.IinX, IinX)); CK(up(p.Ein0, Ein0)); CK(up(p.Fin0, Fin0));
     CK(up(p.EinX, EinX)); CK(up(p.FinX, FinX));
@@ -701,6 +711,14 @@ int trt_set_sweep_tile(trt_handle *h, int D, int shape)
         return fail(h, TRT_EINVAL, "trt_set_sweep_tile: D or shape not a candidate");
     h->p.sweep_D = D;
     h->p.sweep_shape = shape;
+    return TRT_OK;
+}
+
+int trt_get_sweep_tile(const trt_handle *h, int *D, int *shape)
+{
+    if (!h) return TRT_EINVAL;
+    if (D) *D = h->p.sweep_D;
+    if (shape) *shape = h->p.sweep_shape;
     return TRT_OK;
 }
 

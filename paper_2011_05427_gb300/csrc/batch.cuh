@@ -40,6 +40,7 @@ struct SweepArgs {
     void *psi_exit;   // [M][ldG], R-typed
     double *f, *fb0, *fbX, *C0, *CX;
     const float *kap32;   // h/(2 c dt) per cell in FP32 (with the FP32 inputs), or null
+    const float *dir32;   // [M][4] |mu|, |mu|/2, w/2, w mu^2/2 in FP32
 };
 
 struct FinalizeArgs {

@@ -130,6 +130,7 @@ struct Problem {
     double *h, *edges, *mu, *w, *Iin0, *IinX, *Ein0, *Fin0, *EinX, *FinX;
     double *ihf;        // [nx+1]: 1/(h_{f-1} + h_f) at interior faces (dx-weighted means)
     double *hf;         // [nx+1]: face half-widths h_0/2, (h_{f-1} + h_f)/2, h_{nx-1}/2
+    float *dir32;       // [M][4]: |mu|, |mu|/2, w/2, w mu^2/2 rounded once to FP32 (FP32 sweeps)
     int *lo_slot;       // [nx+1]: shared-memory slot k * 32 + l of face/row f in the
                         // partitioned tridiagonal solve (chunk l, row k of the chunk)
     double *rscratch;   // partial sums of the two-stage restriction

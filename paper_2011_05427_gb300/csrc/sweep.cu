@@ -23,7 +23,7 @@
 // two angular moments per (cell, group) -- the cross-direction reduction costs one
 // __syncthreads per strip, not one per cell.  Partial moments of the 2N/D direction tiles
 // are summed in a fixed order by the finalize kernel (deterministic).
-#include "batch.cuh"
+#include "sweep.cuh"
 
 namespace trt {
 
@@ -37,23 +37,6 @@ constexpr int kPadG = 33;   // padded group stride of the strip tables (bank con
 // picked per problem by timing the candidates (trt_autotune), else the defaults below.
 
 
-
-template <typename R>
-struct Acc {   // per-tile angular sum: plain in FP64, compensated (Kahan) in FP32
-    R s, c;
-    __device__ Acc() : s(0), c(0) {}
-    __device__ void add(R v)
-    {
-        if (sizeof(R) == 8) {
-            s += v;
-        } else {
-            R y = v - c;
-            R t = s + y;
-            c = (t - s) - y;
-            s = t;
-        }
-    }
-};
 
 // 1/d.  FP32: the correctly rounded reciprocal.  FP64: the hardware's approximate FP64
 // reciprocal x (relative error below 1e-6 = 2^-19.9, measured over [1, 2); special-function
@@ -74,18 +57,6 @@ __device__ inline double recip<double>(double d)
     const double e = fma(-d, x, 1.0);
     return fma(x, fma(e, e, e), x);
 }
-
-// cp.async (global -> shared, completion per issuing thread): the next strip's data is
-// in flight while the current strip is swept.
-template <int B>
-__device__ inline void cp_async(void *smem, const void *gmem)
-{
-    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(s), "l"(gmem), "n"(B));
-}
-__device__ inline void cp_commit() { asm volatile("cp.async.commit_group;\n" ::); }
-template <int N>
-__device__ inline void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
 
 // shared-memory carve-up of k_sweep (byte offsets, 16-byte aligned sections)
 template <typename R, typename SR, int kStrip, int NS>
@@ -677,21 +648,26 @@ __global__ void __launch_bounds__(128) k_sweep4_b(const int *__restrict__ meta, 
 }
 
 // f_g = sum_t A2 / sum_t A0 per (group, cell), in R; boundary factors per group in FP64.
-// Blocks [0, nb_cell) take one (group, cell) per thread; the blocks after them take one
-// group per warp for the boundary factors: lanes stride over the directions and the four
-// half-range sums per face meet in a fixed butterfly (a serial loop over all directions
-// per thread left a latency-bound tail of dependent loads).
+// Blocks [0, nb) with nb = ceil(G / 8) take one group per warp for the boundary factors;
+// the blocks after them take one (group, cell) per thread.  The boundary warps come first so
+// that their FP64 sums run beside the memory-bound cell blocks instead of after them: lanes
+// stride over the directions, then the eight half-range sums meet in a halving exchange
+// (lanes l and l ^ 16 trade four sums, then l ^ 8 two, l ^ 4 one, then l ^ 2 and l ^ 1 add
+// the last one), which pairs the same lanes in the same order as a full butterfly of every
+// sum -- the same totals bit for bit -- with 9 FP64 additions per lane instead of 40; lanes
+// 0, 8, 16, 24 then hold the four denominators and form the four factors side by side.
 template <typename R>
 __device__ void finalize_body(const FinalizeArgs &x, int bx)
 {
-    const int nx = x.nx, N = x.N, G = x.G, ldG = x.ldG, ntile = x.ntile, nb_cell = x.nb_cell;
+    const int nx = x.nx, N = x.N, G = x.G, ldG = x.ldG, ntile = x.ntile;
     const R *__restrict__ part = reinterpret_cast<const R *>(x.part);
     const R *__restrict__ psi_exit = reinterpret_cast<const R *>(x.psi_exit);
     const double *__restrict__ mu = x.mu, *__restrict__ w = x.w;
     const double *__restrict__ Iin0 = x.Iin0, *__restrict__ IinX = x.IinX;
     double *f = x.f, *fb0 = x.fb0, *fbX = x.fbX, *C0 = x.C0, *CX = x.CX;
-    if (bx < nb_cell) {
-        const long idx = (long)bx * blockDim.x + threadIdx.x;
+    const int nb = finalize_bnd_blocks_dev(G);
+    if (bx >= nb) {
+        const long idx = (long)(bx - nb) * blockDim.x + threadIdx.x;
         const long n = (long)G * nx;
         if (idx < n) {
             // FP32: the partials of up to 8 direction tiles are loaded before any is added,
@@ -727,38 +703,47 @@ __device__ void finalize_body(const FinalizeArgs &x, int bx)
         return;
     }
     const int lane = threadIdx.x & 31;
-    const int g = (bx - nb_cell) * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int g = bx * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (g >= G) return;   // whole warp
     const int M = 2 * N;
     // x = 0: inflow for mu > 0, outflow for mu < 0; x = X: outflow for mu > 0, inflow mu < 0
-    double a0 = 0, a2 = 0, ah0 = 0, ah1 = 0, b0 = 0, b2 = 0, bh0 = 0, bh1 = 0;
+    // q: a0, a2, ah0, ah1 (face x = 0), b0, b2, bh0, bh1 (face x = X)
+    double q[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     for (int m = lane; m < M; m += 32) {
         const double wm = w[m], mm = mu[m];
         const double ex = (double)psi_exit[(size_t)m * ldG + g];
         const double p0 = (m < N) ? Iin0[g] : ex;
         const double pX = (m < N) ? ex : IinX[g];
-        a0 += wm * p0;
-        a2 += wm * mm * mm * p0;
-        b0 += wm * pX;
-        b2 += wm * mm * mm * pX;
-        if (m >= N) { ah0 += wm * p0; ah1 += wm * mm * p0; }
-        else        { bh0 += wm * pX; bh1 += wm * mm * pX; }
+        q[0] += wm * p0;
+        q[1] += wm * mm * mm * p0;
+        q[4] += wm * pX;
+        q[5] += wm * mm * mm * pX;
+        if (m >= N) { q[2] += wm * p0; q[3] += wm * mm * p0; }
+        else        { q[6] += wm * pX; q[7] += wm * mm * pX; }
     }
-    for (int o = 16; o > 0; o >>= 1) {
-        a0 += __shfl_xor_sync(0xffffffffu, a0, o);
-        a2 += __shfl_xor_sync(0xffffffffu, a2, o);
-        ah0 += __shfl_xor_sync(0xffffffffu, ah0, o);
-        ah1 += __shfl_xor_sync(0xffffffffu, ah1, o);
-        b0 += __shfl_xor_sync(0xffffffffu, b0, o);
-        b2 += __shfl_xor_sync(0xffffffffu, b2, o);
-        bh0 += __shfl_xor_sync(0xffffffffu, bh0, o);
-        bh1 += __shfl_xor_sync(0xffffffffu, bh1, o);
+    const bool u16 = lane & 16, u8 = lane & 8, u4 = lane & 4;
+    double r4[4], r2[2];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {   // keep sums 4 u16 .. 4 u16 + 3
+        const double keep = u16 ? q[k + 4] : q[k], give = u16 ? q[k] : q[k + 4];
+        r4[k] = keep + __shfl_xor_sync(0xffffffffu, give, 16);
     }
-    if (lane == 0) {
-        fb0[g] = (a0 != 0.0) ? a2 / a0 : 1.0 / 3.0;
-        C0[g] = (ah0 != 0.0) ? ah1 / ah0 : -0.5;
-        fbX[g] = (b0 != 0.0) ? b2 / b0 : 1.0 / 3.0;
-        CX[g] = (bh0 != 0.0) ? bh1 / bh0 : 0.5;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {   // keep 4 u16 + 2 u8 + {0, 1}
+        const double keep = u8 ? r4[k + 2] : r4[k], give = u8 ? r4[k] : r4[k + 2];
+        r2[k] = keep + __shfl_xor_sync(0xffffffffu, give, 8);
+    }
+    double r = (u4 ? r2[1] : r2[0]) + __shfl_xor_sync(0xffffffffu, u4 ? r2[0] : r2[1], 4);
+    r += __shfl_xor_sync(0xffffffffu, r, 2);
+    r += __shfl_xor_sync(0xffffffffu, r, 1);
+    // lane l now holds sum (l >> 2) & 7; the numerator of lane 8k's sum is on lane 8k + 4
+    const double num = __shfl_down_sync(0xffffffffu, r, 4);
+    if ((lane & 7) == 0) {
+        const int k = lane >> 3;   // 0: f at x = 0, 1: C^-, 2: f at x = X, 3: C^+
+        const double dflt = (k & 1) ? ((k == 1) ? -0.5 : 0.5) : 1.0 / 3.0;
+        const double v = (r != 0.0) ? num / r : dflt;
+        double *dst = (k == 0) ? fb0 : (k == 1) ? C0 : (k == 2) ? fbX : CX;
+        dst[g] = v;
     }
 }
 
@@ -786,11 +771,13 @@ __global__ void k_sweep_finalize_b(const int *__restrict__ meta, int N,
 // (16, 2) 1.37, (8, 3) 1.37.
 struct Shape {
     int S, NS, V;   // strip cells, strip buffers, groups per lane (4: a tile's directions
-                    // per thread, registers instead of strip buffers)
+                    // per thread, registers instead of strip buffers; 5, 6: the lean sweep
+                    // of sweepf.cu with one, two groups per lane)
 };
 constexpr Shape kShapes32[] = {{16, 2, 1}, {16, 3, 1}, {16, 4, 1}, {8, 4, 1}, {8, 6, 1},
                                {32, 2, 1}, {16, 2, 2}, {8, 2, 2}, {8, 3, 2}, {8, 4, 2},
-                               {16, 1, 4}, {32, 1, 4}};
+                               {16, 1, 4}, {32, 1, 4}, {16, 2, 5}, {8, 3, 5}, {8, 2, 5},
+                               {8, 2, 6}, {8, 4, 6}, {8, 4, 5}};
 constexpr Shape kShapes64[] = {{8, 2, 1}, {16, 2, 1}, {8, 3, 1}};
 
 // largest power of two <= cap dividing N: the direction-tile height D_min that the
@@ -802,7 +789,7 @@ int base_D(int N, int cap)
     return 1;
 }
 
-int finalize_bnd_blocks(int G) { return (G + 7) / 8; }   // one warp per group, 8 per block
+int finalize_bnd_blocks(int G) { return finalize_bnd_blocks_dev(G); }
 
 
 // one launch of shape (S, NS): the single-slab grid (direction tiles x group tiles) when
@@ -895,10 +882,19 @@ cudaError_t dispatch_shape(int shape, const SweepArgs *a, int M, int ldG, int D,
         case 11: return launch_shape4<32>(a, M, ldG, D, meta, N, xs, grid, st);
         default: break;
         }
+        const Shape sh = kShapes32[shape];
+        if (sh.V >= 5) {   // lean kernels exist for D = 4, 8; other heights take shape 0 / 7
+            if (D == 4 || D == 8)
+                return launch_sweepf(sh.V, sh.S, sh.NS, a, M, ldG, D, meta, N, xs, grid, st);
+            if (sh.V == 6) return launch_shape2<8, 2>(a, M, ldG, D, meta, N, xs, grid, st);
+            shape = 0;
+        }
     }
     if (sizeof(R) == 4) {
-        if (shape == 6 || shape == 10 || shape == 11) shape = 0;
-        if (shape == 7 || shape == 8 || shape == 9) shape = 3;
+        if (shape == 6 || shape == 10 || shape == 11 || shape == 12 || shape == 13 || shape == 14 ||
+            shape == 17)
+            shape = 0;
+        if (shape == 7 || shape == 8 || shape == 9 || shape == 15 || shape == 16) shape = 3;
         switch (shape) {
         case 1: return launch_shape<R, SR, 16, 3>(a, M, ldG, D, meta, N, xs, grid, st);
         case 2: return launch_shape<R, SR, 16, 4>(a, M, ldG, D, meta, N, xs, grid, st);
@@ -950,7 +946,7 @@ void sweep_shape_info(int precision, int shape, int *S, int *NS)
 int sweep_group_tiles(int precision, int shape, int ldG)
 {
     const Shape sh = sweep_fp32(precision) ? kShapes32[shape] : kShapes64[shape];
-    return sh.V == 2 ? (ldG + 63) / 64 : sh.V == 4 ? (ldG / 32 + 3) / 4 : ldG / 32;
+    return (sh.V == 2 || sh.V == 6) ? (ldG + 63) / 64 : sh.V == 4 ? (ldG / 32 + 3) / 4 : ldG / 32;
 }
 
 int sweep_D_candidates(const Problem &p, int *D)
@@ -981,6 +977,7 @@ SweepArgs make_sweep_args(const Problem &p, double dt, const void *sigE, const v
     a.part = part; a.psi_exit = psi_exit;
     a.f = f; a.fb0 = fb0; a.fbX = fbX; a.C0 = C0; a.CX = CX;
     a.kap32 = nullptr;
+    a.dir32 = p.dir32;
     return a;
 }
 

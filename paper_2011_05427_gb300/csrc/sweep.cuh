@@ -1,0 +1,46 @@
+// sweep.cuh -- pieces shared by the FP64/FP32 strip sweeps (sweep.cu) and the lean FP32
+// sweep (sweepf.cu): the per-tile angular accumulator and the cp.async wrappers.
+#pragma once
+#include "batch.cuh"
+
+namespace trt {
+
+template <typename R>
+struct Acc {   // per-tile angular sum: plain in FP64, compensated (Kahan) in FP32
+    R s, c;
+    __device__ Acc() : s(0), c(0) {}
+    __device__ void add(R v)
+    {
+        if (sizeof(R) == 8) {
+            s += v;
+        } else {
+            R y = v - c;
+            R t = s + y;
+            c = (t - s) - y;
+            s = t;
+        }
+    }
+};
+
+// cp.async (global -> shared, completion per issuing thread): the next strip's data is
+// in flight while the current strip is swept.
+template <int B>
+__device__ inline void cp_async(void *smem, const void *gmem)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(s), "l"(gmem), "n"(B));
+}
+__device__ inline void cp_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ inline void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
+// boundary-factor blocks of the sweep's finalize: one warp per group, 8 per block
+__host__ __device__ inline int finalize_bnd_blocks_dev(int G) { return (G + 7) / 8; }
+
+// the lean FP32 sweep of a shape kind (5: one group per lane, 6: two), strip S, buffers NS:
+// the single-slab grid when `a` is given, else the persistent grid over the work list;
+// cudaErrorInvalidConfiguration for a tile height D it has no kernel for (D = 4, 8)
+cudaError_t launch_sweepf(int kind, int S, int NS, const SweepArgs *a, int M, int ldG, int D,
+                          const int *meta, int N, const SweepArgs *xs, int grid, cudaStream_t st);
+
+}  // namespace trt

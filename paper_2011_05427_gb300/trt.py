@@ -141,6 +141,8 @@ def lib():
     L.trt_sweep_shapes.argtypes = [_vp]
     L.trt_set_sweep_tile.restype = ctypes.c_int
     L.trt_set_sweep_tile.argtypes = [_vp, ctypes.c_int, ctypes.c_int]
+    L.trt_get_sweep_tile.restype = ctypes.c_int
+    L.trt_get_sweep_tile.argtypes = [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
     L.trt_set_closure.restype = ctypes.c_int
     L.trt_set_closure.argtypes = [_vp] * 4 + [ctypes.c_size_t] + [_vp] * 2
     # learned closure (include/trt_mlp.h)
@@ -196,7 +198,8 @@ def lib():
 EXPORTED = ("trt_workspace_bytes", "trt_create", "trt_step", "trt_moments", "trt_intensity",
             "trt_set_state", "trt_dims", "trt_destroy", "trt_last_error", "trt_k_opacity",
             "trt_k_sweep", "trt_k_lo_solve", "trt_k_restrict", "trt_k_grey_newton",
-            "trt_sweep_time", "trt_autotune", "trt_sweep_shapes", "trt_set_sweep_tile",
+            "trt_sweep_time", "trt_autotune", "trt_sweep_shapes", "trt_get_sweep_tile",
+            "trt_set_sweep_tile",
             "trt_sweep_noalloc_scratch_bytes", "trt_sweep_noalloc", "trt_sweep_noalloc_error",
             "trt_set_closure", "trt_gemm_bf16", "trt_mlp_scratch_bytes", "trt_mlp_refresh", "trt_mlp_forward", "trt_mlp_forward_fused", "trt_level_view",
             "trt_mlp_grad", "trt_mlp_adam", "trt_mlp_features", "trt_mlp_status",
@@ -449,6 +452,12 @@ class Solver:
 
     def sweep_shapes(self) -> int:
         return lib().trt_sweep_shapes(self.h)
+
+    def sweep_tile(self):
+        """The sweep tile the next step uses: (D, shape); D = 0 is the library default."""
+        D, sh = ctypes.c_int(), ctypes.c_int()
+        self._check(lib().trt_get_sweep_tile(self.h, ctypes.byref(D), ctypes.byref(sh)))
+        return D.value, sh.value
 
     def close(self):
         if getattr(self, "h", None) and getattr(self, "_owned", True):

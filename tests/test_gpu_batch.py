@@ -94,15 +94,17 @@ def test_batch_uniform_equilibrium_and_tile(trt):
     B.close()
 
 
-def test_batch_direction_tile_sweep(trt):
-    """The batched persistent form of shape 10 (directions per thread) gives the
-    single-slab results with the same tile, bit for bit."""
+@pytest.mark.parametrize("D,shape", [(4, 10), (4, 12), (4, 15)])
+def test_batch_direction_tile_sweep(trt, D, shape):
+    """The batched persistent forms of shape 10 (directions per thread) and of the lean
+    sweeps 12 (one group per lane) and 15 (two groups per lane) give the single-slab results
+    with the same tile, bit for bit."""
     slabs = mixed_slabs()
     B = trt.Batch(slabs, precision="sweep32")
-    B.set_tile(4, 10)
+    B.set_tile(D, shape)
     singles = [trt.Solver.from_slab(c, precision="sweep32") for c in slabs]
     for s in singles:
-        s.set_sweep_tile(4, 10)
+        s.set_sweep_tile(D, shape)
     for step in range(2):
         sb = B.step(1e-3, "W", 2, 1e-8)
         for k, s in enumerate(singles):

@@ -197,12 +197,14 @@ def test_mixed_precision_vs_fp64_oracle(trt, orc, name, cfg, cycle, lmax, prec):
 
 
 @pytest.mark.parametrize("shape,D", [(0, 4), (6, 4), (7, 4), (8, 4), (9, 4), (10, 4), (11, 4),
-                                     (10, 8), (11, 8)])
+                                     (10, 8), (11, 8), (12, 4), (13, 4), (14, 4), (15, 4),
+                                     (16, 4), (12, 8), (13, 8), (14, 8), (15, 8), (16, 8)])
 def test_fp32_sweep_shapes_in_steps(trt, orc, shape, D):
     """Every FP32 sweep shape that the step uses with its pre-scaled FP32 inputs (6-9: two
-    groups per lane; 10, 11: a tile's directions per thread) against the FP64 oracle after
-    fixed-iteration steps; 70 groups leave a partial 64-group tile (and a partial
-    128-group CTA), 45 cells a ragged last strip."""
+    groups per lane; 10, 11: a tile's directions per thread; 12-16: the lean sweep with one
+    or two groups per lane) against the FP64 oracle after fixed-iteration steps; 70 groups
+    leave a partial 64-group tile (and a partial 128-group CTA), 45 cells a ragged strip
+    (the last one for mu > 0; for mu < 0 the lean sweep starts with it)."""
     cfg = W.scaled(W.fc_small(), 45, 8, 70, levels=[70, 14, 1])
     s, o = pair(trt, orc, cfg, precision="sweep32")
     s.set_sweep_tile(D, shape)
@@ -216,17 +218,18 @@ def test_fp32_sweep_shapes_in_steps(trt, orc, shape, D):
 
 
 
-@pytest.mark.parametrize("D", [4, 8])
-def test_direction_tile_sweep_matches_strip_sweep(trt, D):
+@pytest.mark.parametrize("D,shape", [(4, 10), (8, 10), (4, 12), (8, 15)])
+def test_direction_tile_sweep_matches_strip_sweep(trt, D, shape):
     """Shape 10 (a tile's D directions per thread, moments summed in registers) does the
     same arithmetic per update and sums a (cell, group)'s directions in the same order as
     shape 0 (one direction per warp, moments summed across warps in shared memory); the
-    compiler may contract the products differently, and FP32 round-off then moves the
+    lean sweeps (12, 15) solve the corner system through t = a/det, s = b/det and a refined
+    approximate reciprocal.  Contractions and roundings that differ at the last bit move the
     iteration counts where a step meets eps, so the steps agree to FP32 sweep accuracy."""
     cfg = W.scaled(W.fc_small(), 45, 8, 70, levels=[70, 14, 1])
     a = trt.Solver.from_slab(cfg, precision="sweep32")
     b = trt.Solver.from_slab(cfg, precision="sweep32")
-    a.set_sweep_tile(D, 10)
+    a.set_sweep_tile(D, shape)
     b.set_sweep_tile(D, 0)
     for _ in range(2):
         sa = a.step(cfg.dt, "V", 4, 1e-8)
