@@ -703,7 +703,7 @@ int trt_sweep_shapes(const trt_handle *h)
 int trt_set_sweep_tile(trt_handle *h, int D, int shape)
 {
     if (!h) return TRT_EINVAL;
-    int cand[2];
+    int cand[3];
     const int nc = sweep_D_candidates(h->p, cand);
     bool ok = false;
     for (int i = 0; i < nc; ++i) ok = ok || cand[i] == D;
@@ -758,7 +758,7 @@ int trt_sweep_time(trt_handle *h, double dt, int reps, float *ms)
 int trt_autotune(trt_handle *h, double dt, int reps, int *D, int *S, int *NS)
 {
     if (!h || !(dt > 0) || reps < 1) return TRT_EINVAL;
-    int cand[2];
+    int cand[3];
     const int nc = sweep_D_candidates(h->p, cand);
     const int ns = sweep_shape_count(h->p.precision);
     const int D0 = h->p.sweep_D, sh0 = h->p.sweep_shape;

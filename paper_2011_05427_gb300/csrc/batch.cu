@@ -467,7 +467,7 @@ int trt_create_batch(int n, const trt_grid *grids, const trt_angles *angles,
     for (auto *x : b->h)
         while (b->D > 1 && x->p.N % b->D) b->D >>= 1;
     for (auto *x : b->h) {
-        int cand[2];
+        int cand[3];
         sweep_D_candidates(x->p, cand);
         if (b->D < cand[0]) return TRT_EINVAL;   // direction counts too different to batch
     }
@@ -803,9 +803,10 @@ trt_handle *trt_batch_slab(trt_batch *b, int s)
 
 int trt_batch_set_tile(trt_batch *b, int D, int shape)
 {
-    if (!b || D < 1 || D > 8 || (D & (D - 1))) return TRT_EINVAL;
+    if (!b || D < 1 || D > 16 || (D & (D - 1))) return TRT_EINVAL;
+    if (D == 16 && !sweep_fp32(b->precision)) return TRT_EINVAL;   // lean FP32 sweeps only
     for (auto *x : b->h) {
-        int cand[2];
+        int cand[3];
         sweep_D_candidates(x->p, cand);
         if (x->p.N % D || D < cand[0])
             return bfail(b, TRT_EINVAL, "D must divide every slab's N and be >= its smallest tile");

@@ -164,7 +164,7 @@ size_t sweep_partial_doubles(const Problem &p);
 int sweep_shape_count(int precision);
 void sweep_shape_info(int precision, int shape, int *S, int *NS);
 int sweep_group_tiles(int precision, int shape, int ldG);   // CTAs along the groups
-int sweep_D_candidates(const Problem &p, int *D);   // fills D[0..n), returns n (<= 2)
+int sweep_D_candidates(const Problem &p, int *D);   // fills D[0..n), returns n (<= 3)
 // sigE / emis: [G][nx]; double sigma_E, e_g, or (sigma_fp32, FP32 sweep only) the float
 // pre-scaled (sigma_E + 1/(c dt)) h/2 and h e/2 of launch_opacity
 cudaError_t launch_sweep(const Problem &p, double dt, const void *sigE, const void *emis,

@@ -870,6 +870,8 @@ template <typename R, typename SR>
 cudaError_t dispatch_shape(int shape, const SweepArgs *a, int M, int ldG, int D, const int *meta,
                            int N, const SweepArgs *xs, int grid, cudaStream_t st)
 {
+    if (D > 8 && !(sizeof(R) == 4 && sizeof(SR) == 4 && kShapes32[shape].V >= 5))
+        return cudaErrorInvalidConfiguration;   // 32 D threads: only the lean sweep has D = 16
     // two groups per lane: FP32 with pre-scaled FP32 inputs only; the FP32 sweep with FP64
     // inputs takes the one-group shape of the same strip
     if (sizeof(R) == 4 && sizeof(SR) == 4) {
@@ -883,8 +885,8 @@ cudaError_t dispatch_shape(int shape, const SweepArgs *a, int M, int ldG, int D,
         default: break;
         }
         const Shape sh = kShapes32[shape];
-        if (sh.V >= 5) {   // lean kernels exist for D = 4, 8; other heights take shape 0 / 7
-            if (D == 4 || D == 8)
+        if (sh.V >= 5) {   // lean kernels exist for D = 4, 8, 16; other heights take shape 0 / 7
+            if (D == 4 || D == 8 || D == 16)
                 return launch_sweepf(sh.V, sh.S, sh.NS, a, M, ldG, D, meta, N, xs, grid, st);
             if (sh.V == 6) return launch_shape2<8, 2>(a, M, ldG, D, meta, N, xs, grid, st);
             shape = 0;
@@ -955,6 +957,8 @@ int sweep_D_candidates(const Problem &p, int *D)
     int n = 0;
     D[n++] = b;
     if (2 * b <= 8 && p.N % (2 * b) == 0) D[n++] = 2 * b;
+    // 16 directions per CTA: the lean FP32 sweeps only (half the partial moments of D = 8)
+    if (sweep_fp32(p.precision) && p.N % 16 == 0) D[n++] = 16;
     return n;
 }
 

@@ -356,6 +356,7 @@ cudaError_t launch_fd(int D, const SweepArgs *a, int M, int ldG, const int *meta
     switch (D) {
     case 4: return launch_f<GPL, S, NS, 4>(a, M, ldG, meta, N, xs, grid, st);
     case 8: return launch_f<GPL, S, NS, 8>(a, M, ldG, meta, N, xs, grid, st);
+    case 16: return launch_f<GPL, S, NS, 16>(a, M, ldG, meta, N, xs, grid, st);
     default: return cudaErrorInvalidConfiguration;
     }
 }

@@ -564,7 +564,7 @@ class Batch:
     def autotune(self, dt, reps=3):
         """Time the batched sweep for every (D, shape) every slab admits; keep the fastest."""
         best = None
-        Ds = [D for D in (8, 4, 2) if all(self.slab(s).N % D == 0 for s in range(self.n))
+        Ds = [D for D in (16, 8, 4, 2) if all(self.slab(s).N % D == 0 for s in range(self.n))
               and all(D >= min(4, self.slab(s).N & -self.slab(s).N) for s in range(self.n))]
         nshape = lib().trt_sweep_shapes(self.slab(0).h)
         for D in Ds:

@@ -218,6 +218,24 @@ def test_fp32_sweep_shapes_in_steps(trt, orc, shape, D):
 
 
 
+@pytest.mark.parametrize("shape", [12, 13, 14, 15, 17])
+def test_fp32_lean_sweep_sixteen_directions(trt, orc, shape):
+    """The lean sweeps with D = 16 directions per CTA (512 threads, half the partial
+    moments of D = 8) against the FP64 oracle after fixed-iteration steps: 16 directions
+    per sign, 70 groups (a partial group tile), 45 cells (a ragged strip)."""
+    cfg = W.scaled(W.fc_small(), 45, 16, 70, levels=[70, 14, 1])
+    s, o = pair(trt, orc, cfg, precision="sweep32")
+    s.set_sweep_tile(16, shape)
+    assert s.sweep_tile() == (16, shape)
+    worst = 0.0
+    for step in range(2):
+        s.step(cfg.dt, "W", 2, -1.0, max_outer=3)
+        o.step(cfg.dt, "W", 2, -1.0, max_outer=3)
+        eT, eE, _ = errors(s.moments(), o.state())
+        worst = max(worst, eT, eE)
+    assert worst < MIXED_TOL["sweep32"], worst
+
+
 @pytest.mark.parametrize("D,shape", [(4, 10), (8, 10), (4, 12), (8, 15)])
 def test_direction_tile_sweep_matches_strip_sweep(trt, D, shape):
     """Shape 10 (a tile's D directions per thread, moments summed in registers) does the
