@@ -148,8 +148,8 @@ FP64_PEAK_TFLOPS = 1.25
 TRAFFIC = {
     "sweep_fp64": {"files": ("sweep.cu",), "sha": "fc7b8491192d38f9", "tile": (8, 0),
                    "bytes": 540402176 + 542182912 + 66101504 + 42240},
-    "sweep_fp32": {"files": ("sweepf.cu", "sweep.cu"), "sha": "58cff6c8febc609d", "tile": (8, 16),
-                   "bytes": 269985536 + 242853888 + 33072640 + 0},
+    "sweep_fp32": {"files": ("sweepf.cu", "sweep.cu"), "sha": "dd468a430b13c38d", "tile": (16, 17),
+                   "bytes": 269830656 + 225996288 + 16691712 + 0},
 }
 
 

@@ -185,7 +185,10 @@ int trt_k_opacity(trt_handle *h, const double *T, double *sigE, double *emis, do
  * direction with sigma_t = sigE + 1/(c dt) and corner sources emis + I_old/(c dt), inflow
  * from the handle's boundary temperatures, followed by the QD factors (eqs. f_g, c_g).
  * I_old / I_new: [M][nx][2][ldG] in the handle's sweep precision (float when the
- * precision has TRT_SWEEP_FP32, else double).  f [G][nx]; fb0, fbX, C0, CX [G]; all FP64. */
+ * precision has TRT_SWEEP_FP32, else double).  f [G][nx]; fb0, fbX, C0, CX [G]; all FP64.
+ * With TRT_SWEEP_FP32 the FP64 sigE and emis are first rounded once to the step's FP32
+ * sweep inputs (sigma_t h/2, h e/2 and h/(2 c dt), in the handle's scratch), so the sweep
+ * runs the same kernel and tile on the same inputs as a step would. */
 int trt_k_sweep(trt_handle *h, double dt, const double *sigE, const double *emis,
                 const void *I_old, void *I_new, double *f, double *fb0, double *fbX,
                 double *C0, double *CX);

@@ -659,8 +659,14 @@ int trt_k_sweep(trt_handle *h, double dt, const double *sigE, const double *emis
 {
     if (!h || !(dt > 0) || !sigE || !emis || !I_old || !I_new || !f || !fb0 || !fbX || !C0 || !CX)
         return TRT_EINVAL;
-    CK(launch_sweep(h->p, dt, sigE, emis, false, I_old, I_new, h->part, h->psi_exit, f, fb0, fbX,
-                    C0, CX));
+    if (h->sig32) {   // FP32 sweeps: the step's pre-scaled FP32 inputs, as a step forms them
+        CK(launch_prescale32(h->p, dt, sigE, emis, h->sig32, h->emis32));
+        CK(launch_sweep(h->p, dt, h->sig32, h->emis32, true, I_old, I_new, h->part, h->psi_exit,
+                        f, fb0, fbX, C0, CX));
+    } else {
+        CK(launch_sweep(h->p, dt, sigE, emis, false, I_old, I_new, h->part, h->psi_exit, f, fb0,
+                        fbX, C0, CX));
+    }
     CK(cudaStreamSynchronize(h->p.stream));
     return TRT_OK;
 }

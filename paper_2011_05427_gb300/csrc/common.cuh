@@ -160,6 +160,9 @@ cudaError_t launch_otab_build(const Problem &p);
 cudaError_t launch_opacity(const Problem &p, const double *T, double *sigE, double *emis,
                            double *sigR, float *sig32 = nullptr, float *emis32 = nullptr,
                            double dt = 0.0);
+// the FP32 sweep inputs (sig32, emis32 and the kap32 row after it) from FP64 sigma_E, e_g
+cudaError_t launch_prescale32(const Problem &p, double dt, const double *sigE, const double *emis,
+                              float *sig32, float *emis32);
 size_t sweep_partial_doubles(const Problem &p);
 int sweep_shape_count(int precision);
 void sweep_shape_info(int precision, int shape, int *S, int *NS);

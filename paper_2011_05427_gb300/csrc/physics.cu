@@ -577,6 +577,30 @@ OpacityArgs make_opacity_args(const Problem &p, const double *T, double *sigE, d
     return a;
 }
 
+// the FP32 sweep inputs from given FP64 sigma_E and e_g, with the expressions of k_opacity
+// (one rounding each): sigma_t h/2, h e/2, then h/(2 c dt) per cell after h e/2
+__global__ void k_prescale32(int nx, int G, const double *__restrict__ h, double icdt,
+                             const double *__restrict__ sigE, const double *__restrict__ emis,
+                             float *sig32, float *emis32)
+{
+    const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long)G * nx) return;
+    const int g = (int)(idx / nx), i = (int)(idx - (long)g * nx);
+    const double hh = 0.5 * h[i];
+    sig32[idx] = (float)(hh * (sigE[idx] + icdt));
+    emis32[idx] = (float)(hh * emis[idx]);
+    if (g == 0) emis32[(size_t)G * nx + i] = (float)(hh * icdt);
+}
+
+cudaError_t launch_prescale32(const Problem &p, double dt, const double *sigE, const double *emis,
+                              float *sig32, float *emis32)
+{
+    const long n = (long)p.G * p.nx;
+    k_prescale32<<<(unsigned)((n + 255) / 256), 256, 0, p.stream>>>(
+        p.nx, p.G, p.h, 1.0 / (kC * dt), sigE, emis, sig32, emis32);
+    return cudaGetLastError();
+}
+
 int opacity_gx(const Problem &p) { return (p.nx + 31) / 32; }
 int opacity_blocks(const Problem &p) { return opacity_gx(p) * ((p.G + 7) / 8); }
 

@@ -210,6 +210,36 @@ def test_sweep_every_tile(trt, orc, precision):
         s.set_sweep_tile(4, s.sweep_shapes())
 
 
+@pytest.mark.parametrize("nx,N,G", [(3, 8, 1), (9, 8, 33), (17, 16, 65), (70, 16, 40)])
+def test_lean_sweep_kernel_parity(trt, orc, nx, N, G):
+    """The lean FP32 sweeps (shapes 12-17) at every tile height D the problem admits (16
+    with 16 directions per sign) against the oracle's sweep, element by element, on the
+    step's FP32 inputs: fewer cells than one strip (3), a single group, partial group tiles
+    for one (33 of 64) and two groups per lane (65 of 96, a half-empty second tile), and
+    several 8-cell strips with a ragged one (70)."""
+    r, h, sig, em, I_old, TL = sweep_inputs(orc, 2700 + nx + G, nx, N, G, thick=True)
+    edges = W.group_edges(G, 1e-5, 1e2) if G >= 3 else np.array([0.0, np.inf])
+    s = solver(trt, nx=nx, N=N, G=G, h=h, edges=edges, TL=TL, TR=0.3, precision="sweep32")
+    dt = 1.7e-3
+    mu, w = orc.double_gl(N)
+    Iin0 = orc.group_physics(edges, TL)[0]
+    IinX = orc.group_physics(edges, 0.3)[0]
+    oI, of, ofb0, ofbX, oC0, oCX = orc.sweep(h, mu, w, sig, em, 1.0 / (C * dt), I_old, Iin0, IinX)
+    n = 0
+    for D in (4, 8, 16):
+        if N % D:
+            continue
+        for shape in range(12, 18):
+            s.set_sweep_tile(D, shape)
+            In, f, fb0, fbX, C0, CX = (x.cpu().numpy() for x in s.k_sweep(dt, sig, em, I_old))
+            assert pair_err(In, oI) < 2e-5, (D, shape)
+            assert rel(f, of) < 2e-5, (D, shape)
+            for a, b in ((fb0, ofb0), (fbX, ofbX), (C0, oC0), (CX, oCX)):
+                assert rel(a, b) < 2e-5, (D, shape)
+            n += 1
+    assert n >= 12
+
+
 def test_autotune_keeps_state(trt):
     """trt_autotune / trt_sweep_time leave T, E_g, F_g, I and the QD factors unchanged and
     keep a candidate tile; steps after tuning match steps without it to round-off."""
@@ -220,7 +250,7 @@ def test_autotune_keeps_state(trt):
     b.step(cfg.dt, "V", 2, 1e-8)
     m0, (I0, f0) = a.moments(), a.intensity()
     D, S, NS = a.autotune(cfg.dt, reps=2)
-    assert D in (4, 8) and S in (8, 16, 32) and NS >= 2
+    assert D in (4, 8, 16) and S in (8, 16, 32) and NS >= 2
     assert a.sweep_time(cfg.dt, reps=2) > 0
     m1, (I1, f1) = a.moments(), a.intensity()
     for k in m0:
