@@ -226,7 +226,8 @@ int trt_k_fastmath(int n, const double *x, double *ex, double *rc, void *stream)
  *   - trt_batch_slab: the handle of slab s, for trt_moments / trt_intensity / trt_dims
  *     (do not destroy it: trt_destroy_batch does);
  *   - trt_batch_set_tile: directions per CTA D (a power of two dividing every slab's N,
- *     <= 8; 16 with FP32 sweeps, run by the lean sweep shapes only) and sweep shape of the
+ *     <= 8; 16 with FP32 sweeps, run by the lean sweep shapes only; TRT_EINVAL for a pair
+ *     with no kernel or one over the CTA's shared memory) and sweep shape of the
  *     batched sweep; trt_batch_sweep_time: ms per batched
  *     sweep (all slabs, incl. the finalize), CUDA events, QD factors left unchanged. */
 typedef struct trt_batch trt_batch;
@@ -262,9 +263,9 @@ int trt_autotune(trt_handle *h, double dt, int reps, int *D, int *S, int *NS);
 /* Set the sweep tile explicitly: D directions per CTA (a candidate of trt_autotune: the
  * largest power of two <= 4 dividing N, its double if <= 8 and dividing N, and with FP32
  * sweeps 16 if it divides N) and a shape index in [0, trt_sweep_shapes(h)); returns
- * TRT_EINVAL otherwise.  A (D, shape) pair the shape has no kernel for makes the next sweep
- * fail with TRT_ECUDA (trt_autotune skips such pairs): D = 16 runs on the lean FP32 shapes
- * only. */
+ * TRT_EINVAL otherwise, and for a pair with no kernel (D = 16 runs on the lean FP32 shapes
+ * only) or whose kernel would exceed the shared memory of a CTA; trt_autotune skips such
+ * pairs. */
 int trt_sweep_shapes(const trt_handle *h);
 int trt_set_sweep_tile(trt_handle *h, int D, int shape);
 /* The sweep tile the next step uses (after trt_autotune, trt_set_sweep_tile or neither):

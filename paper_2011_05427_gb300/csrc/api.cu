@@ -713,7 +713,7 @@ int trt_set_sweep_tile(trt_handle *h, int D, int shape)
     const int nc = sweep_D_candidates(h->p, cand);
     bool ok = false;
     for (int i = 0; i < nc; ++i) ok = ok || cand[i] == D;
-    if (!ok || shape < 0 || shape >= sweep_shape_count(h->p.precision))
+    if (!ok || !sweep_tile_ok(h->p.precision, D, shape))
         return fail(h, TRT_EINVAL, "trt_set_sweep_tile: D or shape not a candidate");
     h->p.sweep_D = D;
     h->p.sweep_shape = shape;
@@ -772,6 +772,7 @@ int trt_autotune(trt_handle *h, double dt, int reps, int *D, int *S, int *NS)
     int bD = D0, bsh = sh0;
     for (int i = 0; i < nc; ++i) {
         for (int k = 0; k < ns; ++k) {
+            if (!sweep_tile_ok(h->p.precision, cand[i], k)) continue;
             h->p.sweep_D = cand[i];
             h->p.sweep_shape = k;
             float ms = 0;

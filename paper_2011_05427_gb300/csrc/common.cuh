@@ -165,6 +165,7 @@ cudaError_t launch_prescale32(const Problem &p, double dt, const double *sigE, c
                               float *sig32, float *emis32);
 size_t sweep_partial_doubles(const Problem &p);
 int sweep_shape_count(int precision);
+bool sweep_tile_ok(int precision, int D, int shape);   // a kernel exists and fits (shared memory)
 void sweep_shape_info(int precision, int shape, int *S, int *NS);
 int sweep_group_tiles(int precision, int shape, int ldG);   // CTAs along the groups
 int sweep_D_candidates(const Problem &p, int *D);   // fills D[0..n), returns n (<= 3)

@@ -932,6 +932,18 @@ int pick_D(const Problem &p)
     return base_D(p.N, 8);
 }
 
+bool sweep_tile_ok(int precision, int D, int shape)
+{
+    if (shape < 0 || shape >= sweep_shape_count(precision) || D < 1) return false;
+    if (!sweep_fp32(precision)) return D <= 8;
+    const Shape sh = kShapes32[shape];
+    if (sh.V >= 5 && (D == 4 || D == 8 || D == 16)) {
+        const size_t sm = sweepf_smem(sh.V, sh.S, sh.NS, D);
+        return sm > 0 && sm <= 227 * 1024;
+    }
+    return D <= 8;
+}
+
 int sweep_shape_count(int precision)
 {
     return sweep_fp32(precision) ? (int)(sizeof(kShapes32) / sizeof(Shape))

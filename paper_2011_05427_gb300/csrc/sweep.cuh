@@ -40,6 +40,8 @@ __host__ __device__ inline int finalize_bnd_blocks_dev(int G) { return (G + 7) /
 // the lean FP32 sweep of a shape kind (5: one group per lane, 6: two), strip S, buffers NS:
 // the single-slab grid when `a` is given, else the persistent grid over the work list;
 // cudaErrorInvalidConfiguration for a tile height D it has no kernel for (D = 4, 8, 16)
+// shared memory of a lean sweep kernel (0: no such kernel)
+size_t sweepf_smem(int kind, int S, int NS, int D);
 cudaError_t launch_sweepf(int kind, int S, int NS, const SweepArgs *a, int M, int ldG, int D,
                           const int *meta, int N, const SweepArgs *xs, int grid, cudaStream_t st);
 

@@ -21,6 +21,7 @@
 // sums take the D directions in order with the compensated accumulator of the other FP32
 // sweeps.  Every rounding is explicit (__f*_rn), so the single-slab and the batched kernel
 // agree bit for bit.
+#include <type_traits>
 #include "sweep.cuh"
 
 namespace trt {
@@ -362,6 +363,32 @@ cudaError_t launch_fd(int D, const SweepArgs *a, int M, int ldG, const int *meta
 }
 
 }  // namespace
+
+size_t sweepf_smem(int kind, int S, int NS, int D)
+{
+    auto pick = [&](auto gpl, auto s, auto ns) -> size_t {
+        constexpr int G_ = decltype(gpl)::value, S_ = decltype(s)::value, N_ = decltype(ns)::value;
+        switch (D) {
+        case 4: return SweepFSmem<G_, S_, N_, 4>::total;
+        case 8: return SweepFSmem<G_, S_, N_, 8>::total;
+        case 16: return SweepFSmem<G_, S_, N_, 16>::total;
+        default: return 0;
+        }
+    };
+    using I1 = std::integral_constant<int, 1>;
+    using I2 = std::integral_constant<int, 2>;
+    using I3 = std::integral_constant<int, 3>;
+    using I4 = std::integral_constant<int, 4>;
+    using I8 = std::integral_constant<int, 8>;
+    using I16 = std::integral_constant<int, 16>;
+    if (kind == 5 && S == 16 && NS == 2) return pick(I1(), I16(), I2());
+    if (kind == 5 && S == 8 && NS == 3) return pick(I1(), I8(), I3());
+    if (kind == 5 && S == 8 && NS == 2) return pick(I1(), I8(), I2());
+    if (kind == 5 && S == 8 && NS == 4) return pick(I1(), I8(), I4());
+    if (kind == 6 && S == 8 && NS == 2) return pick(I2(), I8(), I2());
+    if (kind == 6 && S == 8 && NS == 4) return pick(I2(), I8(), I4());
+    return 0;
+}
 
 cudaError_t launch_sweepf(int kind, int S, int NS, const SweepArgs *a, int M, int ldG, int D,
                           const int *meta, int N, const SweepArgs *xs, int grid, cudaStream_t st)

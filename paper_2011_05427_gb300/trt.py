@@ -569,8 +569,8 @@ class Batch:
         nshape = lib().trt_sweep_shapes(self.slab(0).h)
         for D in Ds:
             for sh in range(nshape):
-                self.set_tile(D, sh)
                 try:
+                    self.set_tile(D, sh)
                     t = self.sweep_time(dt, reps)
                 except TRTError:
                     continue

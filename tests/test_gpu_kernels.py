@@ -230,6 +230,10 @@ def test_lean_sweep_kernel_parity(trt, orc, nx, N, G):
         if N % D:
             continue
         for shape in range(12, 18):
+            if (D, shape) == (16, 16):   # 262 KB of shared memory: no such kernel
+                with pytest.raises(trt.TRTError):
+                    s.set_sweep_tile(D, shape)
+                continue
             s.set_sweep_tile(D, shape)
             In, f, fb0, fbX, C0, CX = (x.cpu().numpy() for x in s.k_sweep(dt, sig, em, I_old))
             assert pair_err(In, oI) < 2e-5, (D, shape)
