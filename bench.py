@@ -140,6 +140,13 @@ FLOP_PER_UPDATE = 23
 # FP64 peak of the part: 152 SMs x 2070 MHz x 2 FP64 FMA per clock per SM x 2 = 1.26e12,
 # the nominal 1.25 TFLOP/s.
 FP64_PEAK_TFLOPS = 1.25
+# FP64 instruction issue of the part: a warp-wide FP64 instruction occupies a sub-partition's
+# FP64 pipe for 64 cycles (measured), so 152 x 4 x 2.07e9 / 64 x 32 lanes = 629e9 thread
+# instructions/s; the FP64 sweep executes 17.6 of them per update (ncu, DFMA 11.0 + DMUL 4.5
+# + DADD 2.1, profiles/fp64_kernels_fc_1024.md), a mix whose FLOP ceiling is 23 / (2 x 17.6)
+# = 65% of the FMA peak.
+FP64_INST_PEAK = 152 * 4 * 2.07e9 / 64 * 32
+FP64_INST_PER_UPDATE = 17.6
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum, one ncu capture of the
 # sweep and its finalize on the fc_1024 workload), valid while the kernel sources hash to
@@ -228,6 +235,8 @@ def sweep_roofline(trt, s, cfg, fp32=False, local=0, reps=20):
                 "peak_source": "derived: 152 SMs x 2.07 GHz x 2 FP64 FMA/clk x 2 (nominal "
                                "1.25 TFLOP/s FP64)",
                 "hbm_frac": upd * 32 / (ms * 1e-3) / 1e9 / peaks()[0],
+                "fp64_inst_per_update": FP64_INST_PER_UPDATE,
+                "fp64_inst_frac": FP64_INST_PER_UPDATE * upd / (ms * 1e-3) / FP64_INST_PEAK,
                 "updates_per_s": upd / (ms * 1e-3)}
     if tile:
         roof["tile"] = {"D": tile[0], "S": tile[1], "NS": tile[2], "shape": shape}

@@ -438,6 +438,7 @@ int trt_step(trt_handle *h, double dt, const trt_cycle *cyc, trt_stats *stats)
     const double eps = cyc->eps, eps_in = cyc->eps_inner;
     int n_ti = 0, n_c = 0, n_lo = 0, s = 0, status = TRT_OK, nk = 0;
     bool swept = false, opac_valid = false;
+    bool ttil_is_T = false;   // Ttil holds T (true after every cycle: its last grey wrote both)
     // the LO phases evaluate opacities without the FP32 copies; the sweep needs them fresh
     const bool sig32_valid = false;
     int have_prev = 0;
@@ -493,7 +494,7 @@ int trt_step(trt_handle *h, double dt, const trt_cycle *cyc, trt_stats *stats)
             CK(launch_lo_solve(p, dt, fine));
             ++nk;
             n_lo += G;
-            CK(d2d(h, h->Ttil, h->T, nx));
+            if (!ttil_is_T) CK(d2d(h, h->Ttil, h->T, nx));
             for (int k = 0; k <= K; ++k) {
                 Level *src = &fine;
                 if (k > 0) {
@@ -517,13 +518,16 @@ int trt_step(trt_handle *h, double dt, const trt_cycle *cyc, trt_stats *stats)
                 a.want_norms = (k == K);
                 a.Tcyc = h->Tcyc; a.Ecyc = h->Ecyc; a.Tphase = h->Tphase; a.Ephase = h->Ephase;
                 a.flags = h->flags;
+                if (k == K) {   // the cycle's last grey visit also does the end-of-cycle copies
+                    a.T_out = h->T; a.Tcyc_out = h->Tcyc; a.Ecyc_out = h->Ecyc;
+                }
                 CK(launch_grey(p, h->grey, a));
                 nk += 2;   // restriction to grey + grey Newton
                 n_lo += 1;
                 have_prev = 1;
                 std::swap(h->Ttil, h->Tnew);
             }
-            CK(d2d(h, h->T, h->Ttil, nx));
+            ttil_is_T = true;   // the last grey visit wrote T = Ttil (T_out)
             opac_valid = false;
             CK(cudaMemcpyAsync(h->hflags, h->flags, 8 * sizeof(double), cudaMemcpyDeviceToHost,
                                p.stream));
@@ -536,8 +540,7 @@ int trt_step(trt_handle *h, double dt, const trt_cycle *cyc, trt_stats *stats)
             }
             bool conv_in = fl[1] <= eps_in * fl[2] && fl[3] <= eps_in * fl[4];
             conv_out = fl[5] <= eps * fl[2] && fl[6] <= eps * fl[4];
-            CK(d2d(h, h->Tcyc, h->T, nx));
-            CK(d2d(h, h->Ecyc, h->grey.E, nx));
+            // Tcyc = T and Ecyc = grey E were written by the last grey visit (Tcyc_out, Ecyc_out)
             if (!fixed && conv_in) break;
         }
         CK(d2d(h, h->Ephase, h->grey.E, nx));

@@ -380,16 +380,12 @@ void build_stage(trt_batch *b, int id, double dt, int cycle_type)
                 a.want_norms = (k == (int)S[s].size());
                 a.Tcyc = x->Tcyc; a.Ecyc = x->Ecyc; a.Tphase = x->Tphase; a.Ephase = x->Ephase;
                 a.flags = b->d_flags + 8 * (size_t)s;
+                if (a.want_norms) {   // the end-of-cycle copies T, Tcyc = T, Ecyc = grey E
+                    a.T_out = x->T; a.Tcyc_out = x->Tcyc; a.Ecyc_out = x->Ecyc;
+                }
                 B.set(og, s, make_grey_ctx(p, x->grey, a), 1, 1);
             }
         }
-        for (int s = 0; s < n; ++s)
-            cp[s] = CopyArgs{H(s)->T, Tbuf(s, (int)S[s].size() + 1), H(s)->p.nx};
-        B.copy(C_CYCLE, cp);
-        for (int s = 0; s < n; ++s) cp[s] = CopyArgs{H(s)->Tcyc, H(s)->T, H(s)->p.nx};
-        B.copy(C_CYCLE, cp);
-        for (int s = 0; s < n; ++s) cp[s] = CopyArgs{H(s)->Ecyc, H(s)->grey.E, H(s)->p.nx};
-        B.copy(C_CYCLE, cp);
     }
     // drop ops nobody is eligible for; fixed grids
     std::vector<Op> keep;

@@ -115,6 +115,10 @@ struct GreyArgs {
     int want_norms;
     const double *Tcyc, *Ecyc, *Tphase, *Ephase;
     double *flags;              // [8], device
+    // the end-of-cycle copies, when non-null (with want_norms): T into T_out, and after the
+    // norms have read them, T into Tcyc_out and E into Ecyc_out (the same arrays as Tcyc,
+    // Ecyc: each cell's thread reads its old value before it writes the new one)
+    double *T_out, *Tcyc_out, *Ecyc_out;
 };
 
 inline bool sweep_fp32(int precision) { return (precision & TRT_SWEEP_FP32) != 0; }

@@ -915,6 +915,9 @@ __device__ inline void grey_update_cell(const GreyArgs &a, const Level &g, int i
         v[4] = umax64(v[4], nn_bits(fabs(E)));
         v[5] = umax64(v[5], nn_bits(fabs(T - a.Tphase[i])));
         v[6] = umax64(v[6], nn_bits(fabs(E - a.Ephase[i])));
+        if (a.T_out) a.T_out[i] = T;
+        if (a.Tcyc_out) a.Tcyc_out[i] = T;
+        if (a.Ecyc_out) a.Ecyc_out[i] = E;
     }
 }
 
