@@ -26,7 +26,8 @@ struct OpacityArgs {
     float *kap32;            // FP32 sweep input h/(2 c dt) per cell, or null
     const double *h;
     double icdt;
-    const double *otab;      // Problem::otab
+    const double *otab;      // Problem::otab (sigma_E, sigma_R series scaled by 27 s)
+    double kE;               // 27 s C_B: the emission factor of the tabulated path
 };
 
 struct SweepArgs {

@@ -409,20 +409,21 @@ __device__ inline void opacity_body(const OpacityArgs &a, int i0, int g0, const 
     const double xa = a.edges[g] * iT;
     const double eb = a.edges[g + 1];
     const bool binf = isinf(eb);
-    const double k27 = 27.0 * a.s;
     double sg, sR, em;
     const int m = ct.m[tx];
     if (m >= 0) {
-        // tabulated: three polynomials in ln T on the cell's interval
+        // tabulated: three polynomials in ln T on the cell's interval (the sigma series carry
+        // the factor 27 s, kE = 27 s C_B)
         const double t = ct.t[tx];
         const float tf = ct.tf[tx];
         const double *c = a.otab + ((size_t)g * kTabNI + m) * kTabEntry;
         const float *ch = reinterpret_cast<const float *>(c + kTabNF * kTabLo);
         constexpr int kh = kTabNC - kTabLo;
-        sg = k27 * horner(c, ch, t, tf) * iT3;
-        sR = k27 * horner(c + kTabLo, ch + kh, t, tf) * iT3;
-        em = k27 * kCB * Ti * mx.ex(horner(c + 2 * kTabLo, ch + 2 * kh, t, tf) - xa);
+        sg = horner(c, ch, t, tf) * iT3;
+        sR = horner(c + kTabLo, ch + kh, t, tf) * iT3;
+        em = a.kE * Ti * mx.ex(horner(c + 2 * kTabLo, ch + 2 * kh, t, tf) - xa);
     } else {
+        const double k27 = 27.0 * a.s;
         const double xb = binf ? 0.0 : eb * iT;
         double dPs, Ns, Ds, om;
         group_integrals(xa, xb, binf, c_ser, mx, dPs, Ns, Ds, om);
@@ -497,9 +498,11 @@ cudaError_t launch_fastmath(int n, const double *x, double *ex, double *rc, cuda
 }
 
 // Tables: one thread per (group, interval) evaluates the three series directly at the
-// interval's kTabNC Chebyshev points in ln T, fits their Chebyshev coefficients and stores
-// them converted to monomial coefficients in the interval's coordinate.
-__global__ void k_otab_build(int G, const double *__restrict__ edges, double *__restrict__ tab)
+// interval's kTabNC Chebyshev points in ln T (the two opacity ratios times 27 s, so the
+// evaluation multiplies by T^-3 only), fits their Chebyshev coefficients and stores them
+// converted to monomial coefficients in the interval's coordinate.
+__global__ void k_otab_build(int G, const double *__restrict__ edges, double k27,
+                             double *__restrict__ tab)
 {
     __shared__ double s_e2[32];
     const Mx mx = stage_exp_table(s_e2);
@@ -513,6 +516,8 @@ __global__ void k_otab_build(int G, const double *__restrict__ edges, double *__
         const double th = kPi * (j + 0.5) / kTabNC;
         const double T = exp(umid + 0.5 * kTabH * cos(th));
         group_ratios(T, edges[g], edges[g + 1], mx, fa[j], fr[j]);
+        fa[j] *= k27;   // sigma_E T^3 and sigma_R T^3: the series carry the factor 27 s
+        fr[j] *= k27;
         // emission factor: e_g = 27 s C_B T e^{-xa} (1 - e^{-w}), w = (nu_b - nu_a)/T
         fe[j] = binf ? 0.0 : log(-expm1(-(edges[g + 1] - edges[g]) / T));
     }
@@ -560,7 +565,7 @@ cudaError_t launch_otab_build(const Problem &p)
     cudaError_t e = ensure_tables();
     if (e != cudaSuccess) return e;
     const int n = p.G * kTabNI;
-    k_otab_build<<<(n + 127) / 128, 128, 0, p.stream>>>(p.G, p.edges, p.otab);
+    k_otab_build<<<(n + 127) / 128, 128, 0, p.stream>>>(p.G, p.edges, 27.0 * p.s, p.otab);
     return cudaGetLastError();
 }
 
@@ -574,6 +579,7 @@ OpacityArgs make_opacity_args(const Problem &p, const double *T, double *sigE, d
     a.kap32 = emis32 ? emis32 + (size_t)p.G * p.nx : nullptr;   // carved after emis32
     a.h = p.h;
     a.icdt = (dt > 0) ? 1.0 / (kC * dt) : 0.0;
+    a.kE = 27.0 * p.s * kCB;   // the order of the direct path's k27 * kCB
     return a;
 }
 
