@@ -155,8 +155,8 @@ FP64_INST_PER_UPDATE = 17.6
 TRAFFIC = {
     "sweep_fp64": {"files": ("sweep.cu",), "sha": "2462a55a5935c5ed", "tile": (8, 0),
                    "bytes": 540350720 + 542587136 + 66101504 + 6400},
-    "sweep_fp32": {"files": ("sweepf.cu", "sweep.cu"), "sha": "dd468a430b13c38d", "tile": (16, 17),
-                   "bytes": 269830656 + 225996288 + 16691712 + 0},
+    "sweep_fp32": {"files": ("sweepf.cu", "sweep.cu"), "sha": "924cec5ff8185f24", "tile": (16, 17),
+                   "bytes": 269835776 + 225900032 + 16689152 + 0},
 }
 
 
