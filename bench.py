@@ -431,6 +431,63 @@ def fc4096_bench(local, steps=3):
     return out
 
 
+PAPER_TABLES = os.path.join(ROOT, "tests", "golden", "paper_tables.txt")
+
+
+def paper_tables_run(local=0):
+    """Sec. 6's Fleck-Cummings test (4 cm, 10 cells, 256 groups up to 1e7 keV, double S8,
+    T0 = 1 eV, 1 keV inflow, eps = 1e-6, eps_inner = 1e-7) on every grid hierarchy of Tables
+    1-2 (0.02 ns x 150 steps and 0.04 ns x 75 steps), plain FP64: the counters N_ti, N_c,
+    N_lo summed over the run next to the tables' (the stored rows are the paper's, cited in
+    the file), and whether the per-cycle count N_lo / N_c equals n^1 + sum_S n^gamma +
+    (|S| + 1) of the cycle's schedule S, as in the tables.  Context: the counts depend on
+    the readings of the paper's unspecified details."""
+    import dataclasses
+    import torch
+    from paper_2011_05427_gb300 import trt
+    sched = {"V": lambda G: [], "W": None, "F": lambda G: list(range(G - 1, 1, -1))}
+
+    def w_sched(G):   # w(Gamma) = [], w(gamma) = w(gamma + 1) + [gamma] + w(gamma + 1)
+        def w(g):
+            return [] if g >= G else w(g + 1) + [g] + w(g + 1)
+        return w(2)
+    out = []
+    for line in open(PAPER_TABLES):
+        if line.startswith("#") or not line.strip():
+            continue
+        t, dt_ns, steps, printed, Gam, grids, lmax, nti, nc, nlo, cyc = line.split()
+        grids = [int(g) for g in grids.split(",")]
+        def run(cycle):
+            cfg = dataclasses.replace(W.fc_paper(float(dt_ns)), levels=grids, cycle=cycle,
+                                      l_max=int(lmax))
+            assert cfg.steps == int(steps)
+            s = trt.Solver.from_slab(cfg, precision="fp64", device=f"cuda:{local}")
+            tot = {"N_ti": 0, "N_c": 0, "N_lo": 0}
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(cfg.steps):
+                st = s.step(cfg.dt, cfg.cycle, cfg.l_max, cfg.eps)
+                tot["N_ti"] += st["n_ti"]
+                tot["N_c"] += st["n_c"]
+                tot["N_lo"] += st["n_lo"]
+            torch.cuda.synchronize()
+            sec = time.perf_counter() - t0
+            s.close()
+            return tot, sec
+        tot, sec = run(cyc)
+        G = len(grids)
+        S = w_sched(G) if cyc == "W" else sched[cyc](G)
+        per = grids[0] + sum(grids[g - 1] for g in S) + len(S) + 1
+        row = {"table": int(t), "dt_ns": float(dt_ns), "Gamma": G, "grids": grids,
+               "cycle_printed": printed, "cycle": cyc, "l_max": int(lmax),
+               "ours": tot, "paper": {"N_ti": int(nti), "N_c": int(nc), "N_lo": int(nlo)},
+               "N_lo_per_cycle_is_schedule": tot["N_lo"] == per * tot["N_c"], "run_s": sec}
+        if printed != cyc:   # the printed cycle too, where the counters decode to another
+            row["ours_printed_cycle"] = run(printed)[0]
+        out.append(row)
+    return out
+
+
 def counters(stats, steps):
     return {k: sum(x[k] for x in stats) / steps for k in ("n_ti", "n_c", "n_lo")}
 
@@ -653,9 +710,15 @@ def main():
     ap.add_argument("--profile-batch", type=int, default=0, metavar="N",
                     help="step the first N slabs of batch_256 (FP32 sweeps, V-cycle): tile "
                          "(8, 7), one warm-up step and one step (for ncu launch lists)")
+    ap.add_argument("--paper-tables", action="store_true",
+                    help="run Sec. 6's test on the 12 grid hierarchies of Tables 1-2 and print "
+                         "the counters next to the paper's (one JSON line)")
     ap.add_argument("--tile", default=None,
                     help="D,shape: sweep tile for --profile-step (default: the library's)")
     args = ap.parse_args()
+    if args.paper_tables:
+        print(json.dumps({"paper_tables": paper_tables_run()}))
+        return
     if args.profile_sweep:
         from paper_2011_05427_gb300 import trt
         nx, n, g, d, sh = (int(v) for v in args.profile_sweep.split(","))

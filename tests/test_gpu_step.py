@@ -77,6 +77,24 @@ def test_converged_steps_fc_small(trt, orc):
         assert eT < 1e-10 and eE < 1e-10, (step, eT, eE)
 
 
+@pytest.mark.parametrize("grids,cycle,lmax", [([256, 32, 1], "W", 2),
+                                              ([256, 128, 32, 16, 8, 4, 1], "F", 1)])
+def test_paper_setup_converged_steps(trt, orc, grids, cycle, lmax):
+    """Sec. 6's own test (4 cm, 10 cells, 256 groups up to 1e7 keV, double S8, eps = 1e-6,
+    eps_inner = 1e-7) on two hierarchies of Tables 1-2 (W on 3 grids; F on 7 grids, l_max
+    1): over 3 converged steps the GPU path takes the oracle's iteration counts and state."""
+    import dataclasses
+    cfg = dataclasses.replace(W.fc_paper(0.02), levels=grids)
+    s, o = pair(trt, orc, cfg)
+    for step in range(3):
+        st = s.step(cfg.dt, cycle, lmax, cfg.eps)
+        so, c = o.step(cfg.dt, cycle, lmax, cfg.eps)
+        assert st["status"] == 0 and so == 0
+        assert (st["n_ti"], st["n_c"], st["n_lo"]) == (c["n_ti"], c["n_c"], c["n_lo"]), step
+        eT, eE, _ = errors(s.moments(), o.state())
+        assert eT < 1e-10 and eE < 1e-10, (step, eT, eE)
+
+
 def test_uniform_equilibrium_gpu(trt):
     cfg = W.scaled(W.fc_small(), 16, 4, 64, levels=[64, 16, 4, 1])
     cfg.T0 = cfg.T_left = cfg.T_right = 0.25
