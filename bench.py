@@ -488,6 +488,48 @@ def paper_tables_run(local=0):
     return out
 
 
+def adaptive_cycle_run(local=0):
+    """Fixed V, W, F cycles against the per-step controller (`cycles.CycleController`,
+    candidates V/4, W/2, F/2) on Sec. 6's test with the 7-grid hierarchy of Table 1 (150
+    steps of 0.02 ns, eps 1e-6) and on fc_1024 (20 steps of 1e-3 sh, eps 1e-8), plain FP64:
+    wall time of the whole run (host clock around the steps, synchronised), counters, and
+    the controller's picks."""
+    import dataclasses
+    import torch
+    from paper_2011_05427_gb300 import trt
+    from paper_2011_05427_gb300.cycles import CycleController
+    cases = [("fc_paper_gamma7", dataclasses.replace(W.fc_paper(0.02),
+                                                     levels=[256, 128, 32, 16, 8, 4, 1]), 150),
+             ("fc_1024", W.fc_1024("V"), 20)]
+    cands = (("V", 4), ("W", 2), ("F", 2))
+    out = []
+    for name, cfg, steps in cases:
+        res = {"workload": name, "steps": steps}
+        for mode in ("V", "W", "F", "adaptive"):
+            s = trt.Solver.from_slab(cfg, precision="fp64", device=f"cuda:{local}")
+            ctl = CycleController(cands) if mode == "adaptive" else None
+            tot = {"N_ti": 0, "N_c": 0, "N_lo": 0}
+            picks = {}
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(steps):
+                if ctl:
+                    st = ctl.step(s, cfg.dt, cfg.eps)
+                    key = f"{st['cycle']}{st['l_max']}"
+                    picks[key] = picks.get(key, 0) + 1
+                else:
+                    st = s.step(cfg.dt, mode, dict(cands)[mode], cfg.eps)
+                tot["N_ti"] += st["n_ti"]
+                tot["N_c"] += st["n_c"]
+                tot["N_lo"] += st["n_lo"]
+            torch.cuda.synchronize()
+            sec = time.perf_counter() - t0
+            s.close()
+            res[mode] = dict(tot, s=sec, **({"picks": picks} if ctl else {}))
+        out.append(res)
+    return out
+
+
 def counters(stats, steps):
     return {k: sum(x[k] for x in stats) / steps for k in ("n_ti", "n_c", "n_lo")}
 
@@ -713,9 +755,15 @@ def main():
     ap.add_argument("--paper-tables", action="store_true",
                     help="run Sec. 6's test on the 12 grid hierarchies of Tables 1-2 and print "
                          "the counters next to the paper's (one JSON line)")
+    ap.add_argument("--adaptive-cycle", action="store_true",
+                    help="fixed V/W/F cycles against the per-step cycle controller (one JSON "
+                         "line)")
     ap.add_argument("--tile", default=None,
                     help="D,shape: sweep tile for --profile-step (default: the library's)")
     args = ap.parse_args()
+    if args.adaptive_cycle:
+        print(json.dumps({"adaptive_cycle": adaptive_cycle_run()}))
+        return
     if args.paper_tables:
         print(json.dumps({"paper_tables": paper_tables_run()}))
         return
