@@ -10,10 +10,10 @@
 // recurrence from one cell to the next is two dependent FMAs.
 //
 // Layout and schedule.  A CTA owns W = 32 GPL consecutive groups (GPL per lane) and D
-// directions of one sign (one warp each).  Cells go in strips of S aligned to multiples of
-// S from cell 0 (a ragged strip is the last one for mu > 0 and the first for mu < 0); each
-// strip's intensity rows, sigma_t h/2, h e/2 and h/(2 c dt) arrive by cp.async NS - 1
-// strips ahead.  Full strips run fully unrolled for one direction sign at a time, so every
+// directions of one sign (one warp each; D = 4, 8 or 16).  Cells go in strips of S aligned
+// to multiples of S from cell 0 (a ragged strip is the last one for mu > 0 and the first
+// for mu < 0); each strip's intensity rows (16-byte copies, a warp-wide copy moving 4 / GPL
+// rows), sigma_t h/2, h e/2 and h/(2 c dt) arrive by cp.async NS - 1 strips ahead.  Full strips run fully unrolled for one direction sign at a time, so every
 // shared-memory operand is a constant offset from a per-strip base; the warp leaves
 // psi_L + psi_R of the strip in one of two buffers, and the CTA reduces the previous
 // strip's buffer into the two angular moments per (cell, group) right after the one
@@ -189,7 +189,8 @@ __device__ __forceinline__ void sweepf_run(const SweepArgs &a, int dtile, int gt
     };
 
     // the CTA's angular moments of strip (c0, ns) from buffer pb: one (cell, group) per
-    // thread and pass, directions in order; 8 consecutive cells of a group per 32-byte store
+    // thread and pass, directions in order; a warp stores S consecutive cells of each of
+    // 32 / S groups (one 4 S-byte segment per group)
     auto reduce = [&](const float *pb, int c0, int ns) {
 #pragma unroll
         for (int k = 0; k < (W * S + NT - 1) / NT; ++k) {
