@@ -73,6 +73,7 @@ void carve(trt_handle *h, Carver &c)
     p.ihf = c.take<double>(nx + 1);
     p.hf = c.take<double>(nx + 1);
     p.dir32 = reinterpret_cast<float *>(c.take<double>(2 * M));
+    p.e2tab = c.take<double>(32);
     p.lo_slot = reinterpret_cast<int *>(c.take<double>((nx + 2) / 2));
     p.otab = c.take<double>(otab_doubles((int)G));
     p.rscratch_doubles = restrict_scratch_doubles((int)nx, (int)G, 1);
@@ -372,6 +373,8 @@ int trt_create(const trt_grid *grid, const trt_angles *angles, const trt_groups 
     }
     CK(cudaMemcpyAsync(p.dir32, dir32.data(), dir32.size() * sizeof(float),
                        cudaMemcpyHostToDevice, p.stream));
+    CK(cudaMemcpyAsync(p.e2tab, host_series().e2, 32 * sizeof(double), cudaMemcpyHostToDevice,
+                       p.stream));
     CK(up(p.Iin0, Iin0)); CK(up(p.IinX, IinX)); CK(up(p.Ein0, Ein0)); CK(up(p.Fin0, Fin0));
     CK(up(p.EinX, EinX)); CK(up(p.FinX, FinX));
     CK(up(H->T, T0v)); CK(up(H->Eg, Eg)); CK(up(H->Fg, Fg)); CK(up(H->f, f));

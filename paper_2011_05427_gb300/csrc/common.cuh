@@ -119,6 +119,12 @@ struct GreyArgs {
     // norms have read them, T into Tcyc_out and E into Ecyc_out (the same arrays as Tcyc,
     // Ecyc: each cell's thread reads its old value before it writes the new one)
     double *T_out, *Tcyc_out, *Ecyc_out;
+    // set by make_grey_ctx (host, the same IEEE operations): c_v / dt and 54 s C_B, which
+    // every cell would otherwise form with an FP64 division on the grey kernel's one SM;
+    // the table and constants of texp for the two exponentials of Q'(T) per cell
+    double cvdt, k54;
+    const double *e2;
+    ExpConsts ec;
 };
 
 inline bool sweep_fp32(int precision) { return (precision & TRT_SWEEP_FP32) != 0; }
@@ -135,6 +141,7 @@ struct Problem {
     double *ihf;        // [nx+1]: 1/(h_{f-1} + h_f) at interior faces (dx-weighted means)
     double *hf;         // [nx+1]: face half-widths h_0/2, (h_{f-1} + h_f)/2, h_{nx-1}/2
     float *dir32;       // [M][4]: |mu|, |mu|/2, w/2, w mu^2/2 rounded once to FP32 (FP32 sweeps)
+    double *e2tab;      // [32]: 2^(j/32), the table of texp for kernels outside physics.cu
     int *lo_slot;       // [nx+1]: shared-memory slot k * 32 + l of face/row f in the
                         // partitioned tridiagonal solve (chunk l, row k of the chunk)
     double *rscratch;   // partial sums of the two-stage restriction

@@ -863,8 +863,8 @@ __device__ inline void block_max_bits(unsigned long long (&v)[kGreyNV], unsigned
 __device__ inline void grey_newton_cell(const GreyArgs &a, const Level &g, int have_prev, int i,
                                         double &sa, double &ss, double &sL)
 {
-    const double cvdt = a.cv / a.dt;
-    const double k54 = 54.0 * a.s * kCB;
+    const double cvdt = a.cvdt;
+    const double k54 = a.k54;
     const double Ts = a.Tstar[i];
     const double sig = g.sig[i];
     const double Q = 2.0 * g.emis[i];
@@ -872,11 +872,11 @@ __device__ inline void grey_newton_cell(const GreyArgs &a, const Level &g, int h
     double dQ = k54;   // first edge at 0: (1 + x) e^{-x} = 1
     if (a.nu_first != 0.0) {
         const double x1 = a.nu_first * iTs;
-        dQ = k54 * (1.0 + x1) * exp(-x1);
+        dQ = k54 * (1.0 + x1) * texp(-x1, a.e2, a.ec);
     }
     if (!isinf(a.nu_last)) {
         const double xL = a.nu_last * iTs;
-        dQ -= k54 * (1.0 + xL) * exp(-xL);
+        dQ -= k54 * (1.0 + xL) * texp(-xL, a.e2, a.ec);
     }
     double D = 0.0;
     if (have_prev) {
@@ -899,7 +899,7 @@ __device__ inline void grey_update_cell(const GreyArgs &a, const Level &g, int i
                                         unsigned long long (&v)[kGreyNV])
 {
     const unsigned long long kInfBits = 0x7ff0000000000000ull;
-    const double cvdt = a.cv / a.dt;
+    const double cvdt = a.cvdt;
     const double Ts = a.Tstar[i];
     const double E = g.E[i];
     const double T = Ts + (kC * g.sig[i] * E - 2.0 * g.emis[i] - cvdt * (Ts - a.Told[i])) * sL;
@@ -1190,6 +1190,11 @@ GreyCtx make_grey_ctx(const Problem &p, const Level &g, const GreyArgs &a)
     GreyCtx x;
     x.lo = make_lo_ctx(p, a.dt, g);
     x.a = a;
+    x.a.cvdt = a.cv / a.dt;
+    x.a.k54 = 54.0 * a.s * kCB;
+    const SeriesTables &t = host_series();
+    x.a.e2 = p.e2tab;
+    x.a.ec = ExpConsts{t.einv, t.eL1, t.eL2};
     x.mmax = lo_mmax(p.nx);
     return x;
 }
