@@ -440,6 +440,28 @@ def fc4096_bench(local, steps=3):
 PAPER_TABLES = os.path.join(ROOT, "tests", "golden", "paper_tables.txt")
 
 
+def cycle_schedule(cycle, Gamma):
+    """The coarse grids a cycle visits, in order (Sec. 4, Fig. 1): V the two-grid cycle
+    (none), W S = w(2) with w(Gamma) = [] and w(g) = w(g + 1) + [g] + w(g + 1), F the
+    grids Gamma - 1 down to 2."""
+    if cycle == "V":
+        return []
+    if cycle == "F":
+        return list(range(Gamma - 1, 1, -1))
+    if cycle == "W":
+        def w(g):
+            return [] if g >= Gamma else w(g + 1) + [g] + w(g + 1)
+        return w(2)
+    raise ValueError(cycle)
+
+
+def lo_solves_per_cycle(grids, cycle):
+    """Group-wise low-order solves of one cycle: the fine grid's groups, each visited coarse
+    grid's groups and one grey solve per visit (the tables' N_lo / N_c)."""
+    S = cycle_schedule(cycle, len(grids))
+    return grids[0] + sum(grids[g - 1] for g in S) + len(S) + 1
+
+
 def paper_tables_run(local=0):
     """Sec. 6's Fleck-Cummings test (4 cm, 10 cells, 256 groups up to 1e7 keV, double S8,
     T0 = 1 eV, 1 keV inflow, eps = 1e-6, eps_inner = 1e-7) on every grid hierarchy of Tables
@@ -451,12 +473,6 @@ def paper_tables_run(local=0):
     import dataclasses
     import torch
     from paper_2011_05427_gb300 import trt
-    sched = {"V": lambda G: [], "W": None, "F": lambda G: list(range(G - 1, 1, -1))}
-
-    def w_sched(G):   # w(Gamma) = [], w(gamma) = w(gamma + 1) + [gamma] + w(gamma + 1)
-        def w(g):
-            return [] if g >= G else w(g + 1) + [g] + w(g + 1)
-        return w(2)
     out = []
     for line in open(PAPER_TABLES):
         if line.startswith("#") or not line.strip():
@@ -481,9 +497,7 @@ def paper_tables_run(local=0):
             s.close()
             return tot, sec
         tot, sec = run(cyc)
-        G = len(grids)
-        S = w_sched(G) if cyc == "W" else sched[cyc](G)
-        per = grids[0] + sum(grids[g - 1] for g in S) + len(S) + 1
+        per = lo_solves_per_cycle(grids, cyc)
         row = {"table": int(t), "dt_ns": float(dt_ns), "Gamma": G, "grids": grids,
                "cycle_printed": printed, "cycle": cyc, "l_max": int(lmax),
                "ours": tot, "paper": {"N_ti": int(nti), "N_c": int(nc), "N_lo": int(nlo)},
