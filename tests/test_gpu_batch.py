@@ -94,6 +94,31 @@ def test_batch_uniform_equilibrium_and_tile(trt):
     B.close()
 
 
+def test_batch_lean_sweep_sixteen_directions(trt):
+    """The batched lean sweep with 16 directions per CTA (slabs of 16 and 32 directions per
+    sign, uneven cells and groups) gives the single-slab results bit for bit."""
+    base = W.fc_small()
+    slabs = [dataclasses.replace(W.scaled(base, nx, N, G, levels=lv, name=f"d16_{k}"),
+                                 T_left=TL, dt=1e-3)
+             for k, (nx, N, G, lv, TL) in enumerate([(37, 16, 64, [64, 16, 1], 1.0),
+                                                     (90, 32, 40, [40, 8, 1], 0.7),
+                                                     (12, 16, 130, [130, 26, 1], 1.2)])]
+    B = trt.Batch(slabs, precision="sweep32")
+    B.set_tile(16, 17)
+    singles = [trt.Solver.from_slab(c, precision="sweep32") for c in slabs]
+    for s in singles:
+        s.set_sweep_tile(16, 17)
+    for step in range(2):
+        sb = B.step(1e-3, "W", 2, 1e-8)
+        for k, s in enumerate(singles):
+            st = s.step(1e-3, "W", 2, 1e-8)
+            assert (sb[k]["n_ti"], sb[k]["n_c"]) == (st["n_ti"], st["n_c"]), (step, k)
+            assert same(B.slab(k).moments(), s.moments()), (step, k)
+    for s in singles:
+        s.close()
+    B.close()
+
+
 @pytest.mark.parametrize("D,shape", [(4, 10), (4, 12), (4, 15)])
 def test_batch_direction_tile_sweep(trt, D, shape):
     """The batched persistent forms of shape 10 (directions per thread) and of the lean
