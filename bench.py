@@ -213,7 +213,7 @@ def sweep_roofline(trt, s, cfg, fp32=False, local=0, reps=20):
     if own:
         s = trt.Solver.from_slab(cfg, precision="sweep32" if fp32 else "fp64",
                                  device=f"cuda:{local}")
-        tile = s.autotune(cfg.dt, reps=3)
+        tile = s.autotune(cfg.dt, reps=10)
     D, shape = s.sweep_tile()
     if D == 0:   # the library default: the largest power of two <= 8 dividing N
         D = max(d for d in (1, 2, 4, 8) if cfg.N % d == 0)
@@ -254,7 +254,7 @@ def timed_steps(trt, cfg, precision, cycle, steps, warmup, local, ws, clocks=Fal
     of the timed steps (max over ranks), their stats, the clock record and the solver."""
     import torch
     s = trt.Solver.from_slab(cfg, precision=precision, device=f"cuda:{local}")
-    s.tile = s.autotune(cfg.dt, reps=3)   # sweep tile for this problem (state unchanged)
+    s.tile = s.autotune(cfg.dt, reps=10)   # sweep tile for this problem (state unchanged)
     l_max = 4 if cycle == "V" else 2
     for _ in range(warmup):
         s.step(cfg.dt, cycle, l_max, cfg.eps)
@@ -339,7 +339,7 @@ def batch_bench(local, steps=3, warmup=2):
     upd = [c.n_cells * 2 * c.N * c.G for c in slabs]
     cg = sum(c.n_cells * c.G for c in slabs)
     B = trt.Batch(slabs, precision="sweep32", device=f"cuda:{local}")
-    best = B.autotune(1e-3, reps=2)
+    best = B.autotune(1e-3, reps=4)
     ms = B.sweep_time(1e-3, reps=5)
     byt = sum(upd) * 16 + cg * 16
     for _ in range(warmup):
@@ -405,7 +405,7 @@ def fc4096_bench(local, steps=3):
     solvers = {}
     for prec in ("fp64", "sweep32"):
         s = trt.Solver.from_slab(cfg, precision=prec, device=dev)
-        s.autotune(cfg.dt, reps=2)
+        s.autotune(cfg.dt, reps=4)
         solvers[prec] = s
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
     tot = {"fp64": 0.0, "sweep32": 0.0}
