@@ -27,3 +27,38 @@ def test_per_cycle_solves_decode_the_tables():
 def test_unknown_cycle_is_rejected():
     with pytest.raises(ValueError):
         bench.cycle_schedule("X", 3)
+
+
+def test_sweep_kernel_names_follow_the_shape_table():
+    assert bench.sweep_kernel(False, 8, 0).startswith("k_sweep<double,double,8,2>")
+    assert bench.sweep_kernel(True, 8, 0).startswith("k_sweep<float,float,16,2>")
+    assert bench.sweep_kernel(True, 8, 7).startswith("k_sweep2<8,2>")
+    assert bench.sweep_kernel(True, 4, 10).startswith("k_sweep4<4,16>")
+    assert bench.sweep_kernel(True, 16, 17).startswith("k_sweepf<1,8,4,16>")
+    assert bench.sweep_kernel(True, 8, 16).startswith("k_sweepf<2,8,4,8>")
+    assert all(bench.sweep_kernel(True, 8, k).endswith("k_sweep_finalize<float>")
+               for k in range(18))
+
+
+def test_traffic_is_reported_only_for_the_captured_tile_and_code():
+    for key, t in bench.TRAFFIC.items():
+        assert bench._traffic(key, t["tile"]) == t["bytes"]
+        D, shape = t["tile"]
+        assert bench._traffic(key, (D, shape + 1)) is None
+    t = dict(bench.TRAFFIC["sweep_fp32"])
+    try:
+        bench.TRAFFIC["sweep_fp32"] = dict(t, sha="0" * 16)   # code changed since the capture
+        assert bench._traffic("sweep_fp32", t["tile"]) is None
+    finally:
+        bench.TRAFFIC["sweep_fp32"] = t
+
+
+def test_code_hash_ignores_comments(tmp_path, monkeypatch):
+    d = tmp_path / "paper_2011_05427_gb300" / "csrc"
+    d.mkdir(parents=True)
+    (d / "a.cu").write_text("int x = 1;  // one\n\n// note\nint y = 2;\n")
+    (d / "b.cu").write_text("int x = 1;\nint y = 2;   // two\n")
+    (d / "c.cu").write_text("int x = 1;\nint y = 3;\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench._src_sha(("a.cu",)) == bench._src_sha(("b.cu",))
+    assert bench._src_sha(("a.cu",)) != bench._src_sha(("c.cu",))
