@@ -200,62 +200,65 @@ __device__ void tri_solve(R *sm, int n, int mmax)
         A1r = CH(Ap, m - 1, lane); C1r = CH(Cp, m - 1, lane); D1r = CH(Dp, m - 1, lane);
     }
     // ---- phase C: reduced system rows (first_l, last_l), l = 0..31, PCR with shuffles ----
+    // Every row is kept with a unit diagonal (the reduced rows of phase B already are):
+    // a level eliminates the neighbours at distance s with the factors -A and -C, then
+    // divides the row by its new diagonal -- one reciprocal per row and level instead of
+    // one per neighbour, and no diagonals to exchange.
     {
-        R B0r = 1, B1r = 1;
         if (!act) { A0r = C0r = D0r = A1r = C1r = D1r = 0; }
         const unsigned full = 0xffffffffu;
         for (int s = 1; s < 64; s <<= 1) {
-            R lA0, lB0, lC0, lD0, uA0, uB0, uC0, uD0;   // neighbours of slot 0
-            R lA1, lB1, lC1, lD1, uA1, uB1, uC1, uD1;   // neighbours of slot 1
+            R lA0, lC0, lD0, uA0, uC0, uD0;   // neighbours of slot 0 (unit diagonals)
+            R lA1, lC1, lD1, uA1, uC1, uD1;   // neighbours of slot 1
             if (s == 1) {
-                R tA = __shfl_up_sync(full, A1r, 1), tB = __shfl_up_sync(full, B1r, 1);
-                R tC = __shfl_up_sync(full, C1r, 1), tD = __shfl_up_sync(full, D1r, 1);
-                R vA = __shfl_down_sync(full, A0r, 1), vB = __shfl_down_sync(full, B0r, 1);
-                R vC = __shfl_down_sync(full, C0r, 1), vD = __shfl_down_sync(full, D0r, 1);
-                if (lane >= 1) { lA0 = tA; lB0 = tB; lC0 = tC; lD0 = tD; }
-                else { lA0 = 0; lB0 = 1; lC0 = 0; lD0 = 0; }
-                uA0 = A1r; uB0 = B1r; uC0 = C1r; uD0 = D1r;
-                lA1 = A0r; lB1 = B0r; lC1 = C0r; lD1 = D0r;
-                if (lane <= 30) { uA1 = vA; uB1 = vB; uC1 = vC; uD1 = vD; }
-                else { uA1 = 0; uB1 = 1; uC1 = 0; uD1 = 0; }
+                R tA = __shfl_up_sync(full, A1r, 1), tC = __shfl_up_sync(full, C1r, 1);
+                R tD = __shfl_up_sync(full, D1r, 1);
+                R vA = __shfl_down_sync(full, A0r, 1), vC = __shfl_down_sync(full, C0r, 1);
+                R vD = __shfl_down_sync(full, D0r, 1);
+                if (lane >= 1) { lA0 = tA; lC0 = tC; lD0 = tD; }
+                else { lA0 = 0; lC0 = 0; lD0 = 0; }
+                uA0 = A1r; uC0 = C1r; uD0 = D1r;
+                lA1 = A0r; lC1 = C0r; lD1 = D0r;
+                if (lane <= 30) { uA1 = vA; uC1 = vC; uD1 = vD; }
+                else { uA1 = 0; uC1 = 0; uD1 = 0; }
             } else {
                 const int t = s >> 1;
-                R a0 = __shfl_up_sync(full, A0r, t), b0 = __shfl_up_sync(full, B0r, t);
-                R c0 = __shfl_up_sync(full, C0r, t), d0 = __shfl_up_sync(full, D0r, t);
-                R a1 = __shfl_up_sync(full, A1r, t), b1 = __shfl_up_sync(full, B1r, t);
-                R c1 = __shfl_up_sync(full, C1r, t), d1 = __shfl_up_sync(full, D1r, t);
-                R e0 = __shfl_down_sync(full, A0r, t), f0 = __shfl_down_sync(full, B0r, t);
-                R g0 = __shfl_down_sync(full, C0r, t), h0 = __shfl_down_sync(full, D0r, t);
-                R e1 = __shfl_down_sync(full, A1r, t), f1 = __shfl_down_sync(full, B1r, t);
-                R g1 = __shfl_down_sync(full, C1r, t), h1 = __shfl_down_sync(full, D1r, t);
+                R a0 = __shfl_up_sync(full, A0r, t), c0 = __shfl_up_sync(full, C0r, t);
+                R d0 = __shfl_up_sync(full, D0r, t);
+                R a1 = __shfl_up_sync(full, A1r, t), c1 = __shfl_up_sync(full, C1r, t);
+                R d1 = __shfl_up_sync(full, D1r, t);
+                R e0 = __shfl_down_sync(full, A0r, t), g0 = __shfl_down_sync(full, C0r, t);
+                R h0 = __shfl_down_sync(full, D0r, t);
+                R e1 = __shfl_down_sync(full, A1r, t), g1 = __shfl_down_sync(full, C1r, t);
+                R h1 = __shfl_down_sync(full, D1r, t);
                 if (lane >= t) {
-                    lA0 = a0; lB0 = b0; lC0 = c0; lD0 = d0;
-                    lA1 = a1; lB1 = b1; lC1 = c1; lD1 = d1;
+                    lA0 = a0; lC0 = c0; lD0 = d0;
+                    lA1 = a1; lC1 = c1; lD1 = d1;
                 } else {
-                    lA0 = lA1 = 0; lB0 = lB1 = 1; lC0 = lC1 = 0; lD0 = lD1 = 0;
+                    lA0 = lA1 = 0; lC0 = lC1 = 0; lD0 = lD1 = 0;
                 }
                 if (lane + t <= 31) {
-                    uA0 = e0; uB0 = f0; uC0 = g0; uD0 = h0;
-                    uA1 = e1; uB1 = f1; uC1 = g1; uD1 = h1;
+                    uA0 = e0; uC0 = g0; uD0 = h0;
+                    uA1 = e1; uC1 = g1; uD1 = h1;
                 } else {
-                    uA0 = uA1 = 0; uB0 = uB1 = 1; uC0 = uC1 = 0; uD0 = uD1 = 0;
+                    uA0 = uA1 = 0; uC0 = uC1 = 0; uD0 = uD1 = 0;
                 }
             }
             {
-                const R al = -A0r * rcpR<R>(lB0), ga = -C0r * rcpR<R>(uB0);
-                const R nA = al * lA0, nC = ga * uC0;
-                const R nB = B0r + al * lC0 + ga * uA0, nD = D0r + al * lD0 + ga * uD0;
-                A0r = nA; B0r = nB; C0r = nC; D0r = nD;
+                const R al = -A0r, ga = -C0r;
+                const R r = rcpR<R>((R)1 + al * lC0 + ga * uA0);
+                const R nA = al * lA0, nC = ga * uC0, nD = D0r + al * lD0 + ga * uD0;
+                A0r = nA * r; C0r = nC * r; D0r = nD * r;
             }
             {
-                const R al = -A1r * rcpR<R>(lB1), ga = -C1r * rcpR<R>(uB1);
-                const R nA = al * lA1, nC = ga * uC1;
-                const R nB = B1r + al * lC1 + ga * uA1, nD = D1r + al * lD1 + ga * uD1;
-                A1r = nA; B1r = nB; C1r = nC; D1r = nD;
+                const R al = -A1r, ga = -C1r;
+                const R r = rcpR<R>((R)1 + al * lC1 + ga * uA1);
+                const R nA = al * lA1, nC = ga * uC1, nD = D1r + al * lD1 + ga * uD1;
+                A1r = nA * r; C1r = nC * r; D1r = nD * r;
             }
         }
-        x0 = D0r * rcpR<R>(B0r);
-        x1 = D1r * rcpR<R>(B1r);
+        x0 = D0r;
+        x1 = D1r;
     }
     // ---- phase D: back substitution (E into Dp), then the fluxes ----
     if (act) {
