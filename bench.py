@@ -143,19 +143,17 @@ FP64_PEAK_TFLOPS = 1.25
 # FP64 instruction issue of the part: a warp-wide FP64 instruction occupies a sub-partition's
 # FP64 pipe for 64 cycles (measured), so 152 x 4 x 2.07e9 / 64 x 32 lanes = 629e9 thread
 # instructions/s; the FP64 sweep executes 17.6 of them per update (ncu, DFMA 11.0 + DMUL 4.5
-# + DADD 2.1, profiles/fp64_kernels_fc_1024.md), a mix whose FLOP ceiling is 23 / (2 x 17.6)
-# = 65% of the FMA peak.
+# + DADD 2.1), a mix whose FLOP ceiling is 23 / (2 x 17.6) = 65% of the FMA peak.
 FP64_INST_PEAK = 152 * 4 * 2.07e9 / 64 * 32
 FP64_INST_PER_UPDATE = 17.6
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum, one ncu capture of the
 # sweep and its finalize on the fc_1024 workload), valid while the kernel sources hash to
-# `sha` and the tuned tile (D, shape) is the captured one; profiles/ holds the capture's
-# summary and command.
+# `sha` and the tuned tile (D, shape) is the captured one.
 TRAFFIC = {
     "sweep_fp64": {"files": ("sweep.cu",), "sha": "beb6628a865ebcb1", "tile": (8, 0),
                    "bytes": 540350720 + 542587136 + 66101504 + 6400},
-    "sweep_fp32": {"files": ("sweepf.cu", "sweep.cu"), "sha": "618ba8ba6c47c92f", "tile": (16, 17),
+    "sweep_fp32": {"files": ("sweepf.cu", "sweep.cu"), "sha": "618ba8ba6c47c92f", "tile": (16, 0),
                    "bytes": 269835776 + 225900032 + 16689152 + 0},
 }
 
@@ -187,16 +185,11 @@ def sweep_kernel(fp32, D, shape):
     if not fp32:
         S, NS = {0: (8, 2), 1: (16, 2), 2: (8, 3)}[shape]
         return f"k_sweep<double,double,{S},{NS}> + k_sweep_finalize<double>"
-    one = {0: (16, 2), 1: (16, 3), 2: (16, 4), 3: (8, 4), 4: (8, 6), 5: (32, 2)}
-    if shape in one:
-        k = "k_sweep<float,float,%d,%d>" % one[shape]
-    elif shape in (6, 7, 8, 9):
-        k = "k_sweep2<%d,%d>" % {6: (16, 2), 7: (8, 2), 8: (8, 3), 9: (8, 4)}[shape]
-    elif shape in (10, 11):
-        k = "k_sweep4<%d,%d>" % (D, 16 if shape == 10 else 32)
+    if shape == 6 or D not in (4, 8, 16):   # the strip sweep (tile heights without a lean kernel)
+        k = "k_sweep<float,float,16,2>"
     else:   # lean sweeps: groups per lane, strip, buffers, directions per CTA
-        gpl, S, NS = {12: (1, 16, 2), 13: (1, 8, 3), 14: (1, 8, 2), 15: (2, 8, 2),
-                      16: (2, 8, 4), 17: (1, 8, 4)}[shape]
+        gpl, S, NS = {0: (1, 8, 4), 1: (1, 16, 2), 2: (1, 8, 3), 3: (1, 8, 2), 4: (2, 8, 2),
+                      5: (2, 8, 4)}[shape]
         k = "k_sweepf<%d,%d,%d,%d>" % (gpl, S, NS, D)
     return k + " + k_sweep_finalize<float>"
 
@@ -745,6 +738,34 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+def launch_table(path):
+    """Per-kernel summary of an ncu launch list (`--metrics gpu__time_duration.sum --csv`):
+    launches, total device time, share and mean per launch, as a markdown table."""
+    import collections
+    import csv
+    scale = {"ns": 1e-3, "nsecond": 1e-3, "us": 1.0, "usecond": 1.0, "ms": 1e3, "msecond": 1e3}
+    with open(path) as fh:
+        rows = list(csv.reader(fh))
+    hi = next(i for i, r in enumerate(rows) if r and r[0] == "ID")
+    hdr, data = rows[hi], rows[hi + 1:]
+    ki, mi = hdr.index("Kernel Name"), hdr.index("Metric Name")
+    vi, ui = hdr.index("Metric Value"), hdr.index("Metric Unit")
+    tot, cnt = collections.defaultdict(float), collections.Counter()
+    for r in data:
+        if len(r) <= vi or r[mi] != "gpu__time_duration.sum":
+            continue
+        us = float(r[vi].replace(",", "")) * scale[r[ui]]
+        name = r[ki].split("(")[0].replace("void ", "")
+        tot[name] += us
+        cnt[name] += 1
+    T = sum(tot.values())
+    out = ["| kernel | launches | total ms | share | mean us |", "|---|---|---|---|---|"]
+    for k, v in sorted(tot.items(), key=lambda x: -x[1]):
+        out.append(f"| `{k}` | {cnt[k]} | {v / 1e3:.2f} | {100 * v / T:.1f}% | {v / cnt[k]:.1f} |")
+    out.append(f"| total | {sum(cnt.values())} | {T / 1e3:.2f} | 100% | |")
+    return "\n".join(out)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -771,7 +792,7 @@ def main():
                          "directions, G groups with sweep tile (D, SHAPE) (for ncu)")
     ap.add_argument("--profile-batch", type=int, default=0, metavar="N",
                     help="step the first N slabs of batch_256 (FP32 sweeps, V-cycle): tile "
-                         "(8, 7), one warm-up step and one step (for ncu launch lists)")
+                         "(8, 4), one warm-up step and one step (for ncu launch lists)")
     ap.add_argument("--paper-tables", action="store_true",
                     help="run Sec. 6's test on the 12 grid hierarchies of Tables 1-2 and print "
                          "the counters next to the paper's (one JSON line)")
@@ -780,7 +801,12 @@ def main():
                          "line)")
     ap.add_argument("--tile", default=None,
                     help="D,shape: sweep tile for --profile-step (default: the library's)")
+    ap.add_argument("--launch-table", default="", metavar="CSV",
+                    help="print the per-kernel table of an ncu launch list and exit")
     args = ap.parse_args()
+    if args.launch_table:
+        print(launch_table(args.launch_table))
+        return
     if args.adaptive_cycle:
         print(json.dumps({"adaptive_cycle": adaptive_cycle_run()}))
         return
@@ -799,7 +825,7 @@ def main():
     if args.profile_batch:
         from paper_2011_05427_gb300 import trt
         B = trt.Batch(W.batch_256(args.profile_batch), precision="sweep32", device="cuda:0")
-        B.set_tile(8, 7)
+        B.set_tile(8, 4)
         for _ in range(2):
             B.step(1e-3, "V", 4, 1e-8)
         B.close()

@@ -323,25 +323,31 @@ int trt_k_grey_newton(trt_handle *h, double dt, const double *Tstar, const doubl
  * not allocate device memory -- a plug-in inside an application that owns every device
  * allocation and lends it no allocator, or a time loop that must not call cudaMalloc (nor
  * pay its device-wide synchronisation) once it is running.  trt_sweep_noalloc does the
- * work of trt_k_sweep with no handle and no workspace: every input and output is a plain
- * device pointer of the caller, and the scratch the sweep needs (per-direction-tile
- * angular partial sums and exit intensities) lives in one file-scope static device array
- * of TRT_STATIC_SCRATCH_BYTES, which every GPU that loads the library keeps until exit.
+ * work of trt_k_sweep (same kernels, the library's default sweep tile) with no handle and
+ * no workspace: every input and output is a plain device pointer of the caller, and the
+ * scratch the sweep needs (per-direction-tile angular partial sums, exit intensities and,
+ * for FP32 sweeps, the per-direction FP32 constants and the pre-scaled FP32 inputs
+ * (sigma_E + 1/(c dt)) h/2, h e/2 that trt_k_sweep forms on an FP32 handle) lives in one
+ * file-scope static device array of TRT_STATIC_SCRATCH_BYTES, which every GPU that loads
+ * the library keeps until exit.
  *   - sizes: nx cells, N directions per half range (M = 2N), G groups; intensities are
  *     [M][nx][2][ldG] with ldG = G rounded up to a multiple of 32 (float when precision
- *     has TRT_SWEEP_FP32, else double); h [nx], mu, w [M] (layout of trt.h), Iin0, IinX [G] isotropic
- *     inflow intensities, sigE, emis [G][nx]; outputs as for trt_k_sweep;
- *   - problems whose scratch (trt_sweep_noalloc_scratch_bytes) exceeds the array are
- *     rejected with TRT_ENOSPACE before anything is enqueued;
+ *     has TRT_SWEEP_FP32, else double); h [nx], mu, w [M] (layout of trt.h), Iin0, IinX [G]
+ *     isotropic inflow intensities, sigE, emis [G][nx] (FP64 in both precisions); outputs
+ *     as for trt_k_sweep;
+ *   - trt_sweep_noalloc_scratch_bytes gives the scratch a call of either precision needs;
+ *     problems whose scratch exceeds the array are rejected with TRT_ENOSPACE before
+ *     anything is enqueued;
  *   - the call only enqueues work on `stream` (cudaStream_t as void*) and returns; it
  *     allocates nothing -- no cudaMalloc / cudaFree, no library allocator;
  *   - the first call on a device looks up the array's device address
  *     (cudaGetSymbolAddress); make that first call before any stream capture;
  *   - all calls share the one array, which keeps whatever the last call left in it (each
- *     call overwrites every scratch value it reads, so nothing needs clearing); calls
- *     that overlap on the GPU -- on different streams, or from different host threads --
- *     race on it and must be serialised by the caller;
- *   - on failure the message is in trt_sweep_noalloc_error(). */
+ *     call writes every scratch value before it reads it, so nothing needs clearing);
+ *     calls that overlap on the GPU -- on different streams, or from different host
+ *     threads -- race on it and must be serialised by the caller;
+ *   - on failure the message is in trt_sweep_noalloc_error(): the calling thread's last
+ *     failure, valid until that thread's next call. */
 #define TRT_STATIC_SCRATCH_BYTES (8u << 20)
 
 size_t trt_sweep_noalloc_scratch_bytes(int nx, int N, int G);

@@ -253,7 +253,7 @@ void build_stage(trt_batch *b, int id, double dt, int cycle_type)
                                           x->psi_exit, x->f, x->fb0, x->fbX, x->C0, x->CX, b->D);
             if (x->sig32) a.kap32 = x->emis32 + (size_t)p.G * p.nx;   // after e (opacity)
             const int ntile = p.M / b->D;
-            B.set(sg.ops[isw], s, a, ntile * sweep_group_tiles(b->precision, b->shape, p.ldG),
+            B.set(sg.ops[isw], s, a, ntile * sweep_group_tiles(b->precision, b->shape, b->D, p.ldG),
                   ntile);
             p.sweep_D = b->D;
             const FinalizeArgs fa = make_finalize_args(p, a);

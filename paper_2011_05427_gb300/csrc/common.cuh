@@ -178,10 +178,11 @@ size_t sweep_partial_doubles(const Problem &p);
 int sweep_shape_count(int precision);
 bool sweep_tile_ok(int precision, int D, int shape);   // a kernel exists and fits (shared memory)
 void sweep_shape_info(int precision, int shape, int *S, int *NS);
-int sweep_group_tiles(int precision, int shape, int ldG);   // CTAs along the groups
+int sweep_group_tiles(int precision, int shape, int D, int ldG);   // CTAs along the groups
 int sweep_D_candidates(const Problem &p, int *D);   // fills D[0..n), returns n (<= 3)
-// sigE / emis: [G][nx]; double sigma_E, e_g, or (sigma_fp32, FP32 sweep only) the float
-// pre-scaled (sigma_E + 1/(c dt)) h/2 and h e/2 of launch_opacity
+// sigE / emis: [G][nx]; FP64 sweeps: double sigma_E, e_g; FP32 sweeps (sigma_fp32 must be
+// set): the float pre-scaled (sigma_E + 1/(c dt)) h/2 and h e/2 of launch_opacity or
+// launch_prescale32, followed by h/(2 c dt) per cell
 cudaError_t launch_sweep(const Problem &p, double dt, const void *sigE, const void *emis,
                          bool sigma_fp32, const void *I_old, void *I_new, double *part,
                          double *psi_exit, double *f, double *fb0, double *fbX, double *C0,

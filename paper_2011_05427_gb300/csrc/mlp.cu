@@ -380,12 +380,7 @@ __global__ void __launch_bounds__(128) k_gemm(int M, int N, int K, const bf16 *_
 // bytes apart), so one cp.async.bulk of 16 KB moves a chunk and completes on the slot's
 // `full` mbarrier; the MMAs reading a slot commit to its `empty` mbarrier, which releases
 // it for the chunk S later.  Every chunk is used by one group's layer, so each weight is
-// streamed twice per 256 rows; to halve what L2 delivers, CTAs run in clusters of two
-// (neighbouring SMs) that consume the same chunk sequence: the cluster's first CTA copies
-// each chunk once with a multicast bulk copy into both CTAs' slots (completing on each
-// CTA's `full` barrier), and each CTA's MMAs commit to the `empty` barriers of both, so
-// a slot is refilled only when both CTAs are done with it.  The two CTAs of a cluster run
-// the same number of iterations (the second one's last may hold no rows).
+// streamed twice per 256 rows (from L2: the whole 256 KB image stays resident there).
 //   The MMA thread never waits for a slot to drain (that is the producer's wait), so the
 // tensor core always has the next chunk's MMAs queued behind the running ones.
 //   Hand-offs: a group arrives on act[g] (128 arrivals) when A_g holds the next layer's
@@ -451,36 +446,13 @@ __device__ inline uint32_t relu_bf16x2(float2 v)
     return d;
 }
 
-// one contiguous bulk copy global -> the same shared-memory offset in every CTA of the
-// cluster named by `mask`, completing (bytes) on the mbarrier at the same offset in each
-__device__ inline void bulk_copy_mc(void *dst, const void *src, unsigned bytes, uint64_t *bar,
-                                    unsigned short mask)
+// one contiguous bulk copy global -> this CTA's shared memory, completing (bytes) on `bar`
+__device__ inline void bulk_copy(void *dst, const void *src, unsigned bytes, uint64_t *bar)
 {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster"
-        " [%0], [%1], %2, [%3], %4;" ::"r"(su32(dst)),
-        "l"(src), "r"(bytes), "r"(su32(bar)), "h"(mask)
-        : "memory");
-}
-// arrive on the mbarrier at this offset in every CTA of `mask` when this thread's MMAs so
-// far have completed
-__device__ inline void umma_commit_mc(uint64_t *bar, unsigned short mask)
-{
-    asm volatile(
-        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
-        " [%0], %1;" ::"r"(su32(bar)),
-        "h"(mask)
-        : "memory");
-}
-__device__ inline void cluster_sync()
-{
-    asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
-}
-__device__ inline unsigned cluster_rank()
-{
-    unsigned r;
-    asm("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-    return r;
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     su32(dst)),
+                 "l"(src), "r"(bytes), "r"(su32(bar))
+                 : "memory");
 }
 
 __global__ void __launch_bounds__(F_THREADS, 1) k_mlp_fused(int rows, const float *__restrict__ x,
@@ -499,15 +471,12 @@ __global__ void __launch_bounds__(F_THREADS, 1) k_mlp_fused(int rows, const floa
 
     const int tid = threadIdx.x, warp = tid >> 5;
     const int ntiles = (rows + 255) / 256;
-    // both CTAs of a cluster (blocks 2c, 2c + 1) run the first one's iteration count
-    const int lead = (int)blockIdx.x & ~1;
-    const int mine = lead < ntiles ? (ntiles - 1 - lead) / (int)gridDim.x + 1 : 0;
-    const unsigned crank = cluster_rank();
+    const int mine = (int)blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
 
     if (tid == 0) {
         for (int k = 0; k < F_SLOTS; ++k) {
             mbar_init_n(&full[k], 1);
-            mbar_init_n(&empty[k], 2);   // one commit from each CTA of the cluster
+            mbar_init_n(&empty[k], 1);   // the commit of the MMAs that read the slot
         }
         for (int g = 0; g < 2; ++g) {
             mbar_init_n(&act[g], 128);
@@ -536,14 +505,13 @@ __global__ void __launch_bounds__(F_THREADS, 1) k_mlp_fused(int rows, const floa
     tc_before();
     __syncthreads();
     tc_after();
-    cluster_sync();   // both CTAs' barriers exist before either signals the other's
     const uint32_t tmem = *tslot;
     bool ok = true;
 
     const int Q = 4 * FNC * mine;   // weight chunks: 4 layer-jobs of FNC chunks per iteration
     if (warp == 8) {
-        // ---------------- producer thread (first CTA of the cluster) ----------------
-        if ((tid & 31) == 0 && crank == 0) {
+        // ---------------- producer thread ----------------
+        if ((tid & 31) == 0) {
             int q = 0;
             for (; q < Q; ++q) {   // chunk q: job q / FNC, K chunk q % FNC, slot q % S
                 if (q >= F_SLOTS && !mbar_wait(&empty[q % F_SLOTS], ((q - F_SLOTS) / F_SLOTS) & 1)) {
@@ -551,9 +519,9 @@ __global__ void __launch_bounds__(F_THREADS, 1) k_mlp_fused(int rows, const floa
                     break;
                 }
                 const int layer = (q / FNC) % 4 >= 2 ? 1 : 0;
-                bulk_copy_mc(sW + (q % F_SLOTS) * FW_BYTES,
-                             Wimg + layer * 65536 + (q % FNC) * (FW_BYTES / 2), FW_BYTES,
-                             &full[q % F_SLOTS], (unsigned short)3);
+                bulk_copy(sW + (q % F_SLOTS) * FW_BYTES,
+                          Wimg + layer * 65536 + (q % FNC) * (FW_BYTES / 2), FW_BYTES,
+                          &full[q % F_SLOTS]);
             }
             *sprod = q;
         }
@@ -571,8 +539,8 @@ __global__ void __launch_bounds__(F_THREADS, 1) k_mlp_fused(int rows, const floa
                     const uint32_t a0 = su32(sm + g * FA_BYTES);
                     const uint32_t d = tmem + (uint32_t)(g * 256);
                     for (int c = 0; c < FNC; ++c, ++q) {
-                        // this CTA's share of chunk q's bytes (the copy may land first: the
-                        // phase completes once both the arrival and the bytes are in)
+                        // chunk q's bytes (the copy may land first: the phase completes
+                        // once both the arrival and the bytes are in)
                         mbar_expect(&full[q % F_SLOTS], FW_BYTES);
                         if (!mbar_wait(&full[q % F_SLOTS], (q / F_SLOTS) & 1)) {
                             ok = false;
@@ -586,8 +554,8 @@ __global__ void __launch_bounds__(F_THREADS, 1) k_mlp_fused(int rows, const floa
                             const uint32_t ka = (c * (FK / 8) + kk * 2) * 128;
                             umma(d, sdesc(a0 + ka, LBO, FA_SBO), bd, (c | kk) != 0);
                         }
-                        // the slot is free for chunk q + S once both CTAs' MMAs on it are done
-                        umma_commit_mc(&empty[q % F_SLOTS], (unsigned short)3);
+                        // the slot is free for chunk q + S once the MMAs reading it are done
+                        umma_commit(&empty[q % F_SLOTS]);
                     }
                     if (!ok) break;
                     umma_commit(&acc[g]);   // the group's accumulator is complete
@@ -738,8 +706,7 @@ __global__ void __launch_bounds__(F_THREADS, 1) k_mlp_fused(int rows, const floa
             mbar_wait(&full[r % F_SLOTS], (r / F_SLOTS) & 1);
         }
     }
-    // neither CTA leaves while the other may still copy into it or arrive on its barriers
-    cluster_sync();
+    __syncthreads();   // the drain above ends before TMEM is released
     if (warp == 0) {
         tc_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
@@ -762,31 +729,12 @@ cudaError_t mlp_fused(int rows, const float *x, const float *P, const bf16 *W, f
         attr = true;
     }
     if (reinterpret_cast<uintptr_t>(P) & 15) return cudaErrorMisalignedAddress;   // float4 loads
-    // clusters of two CTAs, one per SM, no more clusters than fit on the GPU at once (the
-    // kernel is persistent: a cluster left for a second wave would double the time)
-    cudaLaunchConfig_t cfg = {};
-    cfg.blockDim = dim3(F_THREADS);
-    cfg.dynamicSmemBytes = F_SMEM;
-    cfg.stream = st;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeClusterDimension;
-    at[0].val.clusterDim.x = 2;
-    at[0].val.clusterDim.y = 1;
-    at[0].val.clusterDim.z = 1;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
-    static int max_pairs = 0;
-    if (max_pairs == 0) {
-        cfg.gridDim = dim3(2);
-        int n = 0;
-        if (cudaOccupancyMaxActiveClusters(&n, k_mlp_fused, &cfg) != cudaSuccess || n < 1)
-            n = (g_num_sms > 0 ? g_num_sms : 148) / 2;
-        max_pairs = n;
-    }
+    // one persistent CTA per SM, no more CTAs than row tiles (a CTA left for a second wave
+    // would double the time)
     const int ntiles = (rows + 255) / 256;
-    const int pairs = std::max(1, std::min((ntiles + 1) / 2, max_pairs));
-    cfg.gridDim = dim3(2 * pairs);
-    return cudaLaunchKernelEx(&cfg, k_mlp_fused, rows, x, P, (const bf16 *)(W + 4 * 65536), y);
+    const int grid = std::max(1, std::min(ntiles, g_num_sms > 0 ? g_num_sms : 148));
+    k_mlp_fused<<<grid, F_THREADS, F_SMEM, st>>>(rows, x, P, (const bf16 *)(W + 4 * 65536), y);
+    return cudaGetLastError();
 }
 
 cudaError_t gemm(int M, int N, int K, const bf16 *A, const bf16 *B, const Epi &e,

@@ -267,386 +267,6 @@ __global__ void __launch_bounds__(256) k_sweep_b(const int *__restrict__ meta, i
     }
 }
 
-// FP32 sweep with two groups per lane (a warp covers 64 groups; float2 loads and stores;
-// two independent recurrences per thread), for the step's pre-scaled FP32 inputs
-// (sigma_t h/2, h e/2 of launch_opacity).  Same arithmetic per (group, direction) as
-// sweep_body; half the per-update address, copy and loop instructions, which bound the
-// one-group form (issue-limited at ~13 warps per SM).
-constexpr int kP2 = 66;   // padded row (64 groups) of the strip tables, 8-byte aligned
-
-template <int kStrip, int NS>
-struct Sweep2Smem {
-    size_t itile, rawS, rawE, skap, ps, swt, total;
-    __host__ __device__ Sweep2Smem(int D)
-    {
-        auto al = [](size_t x) { return (x + 15) / 16 * 16; };
-        size_t o = 0;
-        itile = o; o = al(o + sizeof(float) * NS * (size_t)D * kStrip * 2 * 64);
-        rawS = o;  o = al(o + sizeof(float) * NS * kStrip * kP2);
-        rawE = o;  o = al(o + sizeof(float) * NS * kStrip * kP2);
-        skap = o;  o = al(o + sizeof(float) * kStrip);
-        ps = o;    o = al(o + sizeof(float) * (size_t)D * kStrip * kP2);
-        swt = o;   o = al(o + sizeof(float) * 2 * D);
-        total = o;
-    }
-};
-
-template <int kStrip, int NS>
-__device__ void sweep2_body(const SweepArgs &a, int dtile, int gt)
-{
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int D = a.D;
-    const Sweep2Smem<kStrip, NS> L(D);
-    float *itile = reinterpret_cast<float *>(smem_raw + L.itile);   // [NS][D][S][2][64]
-    float *rawS = reinterpret_cast<float *>(smem_raw + L.rawS);     // [NS][S][66] sigma_t h/2
-    float *rawE = reinterpret_cast<float *>(smem_raw + L.rawE);     // [NS][S][66] h e/2
-    float *skap = reinterpret_cast<float *>(smem_raw + L.skap);     // [S] h/(2 c dt)
-    float *ps = reinterpret_cast<float *>(smem_raw + L.ps);         // [D][S][66] psi_L + psi_R
-    float *swt = reinterpret_cast<float *>(smem_raw + L.swt);       // [D] w/2
-    float *swm = swt + D;                                           // [D] w mu^2/2
-
-    const int lane = threadIdx.x & 31;
-    const int warp = threadIdx.x >> 5;
-    const int nthr = blockDim.x;
-    const int tid = threadIdx.x;
-    const int nx = a.nx, G = a.G, ldG = a.ldG;
-    const int g0 = gt * 64 + 2 * lane;   // this lane's groups g0, g0 + 1
-    const bool lv = g0 < ldG;            // inside the padded row (ldG is a multiple of 32)
-    const bool pos = dtile < a.N / D;
-    const int m = dtile * D + warp;
-
-    const float *__restrict__ Iold = reinterpret_cast<const float *>(a.I_old);
-    float *__restrict__ Inew = reinterpret_cast<float *>(a.I_new);
-    const float *__restrict__ sigE = reinterpret_cast<const float *>(a.sigE);
-    const float *__restrict__ emis = reinterpret_cast<const float *>(a.emis);
-    float *part = reinterpret_cast<float *>(a.part);
-
-    const double mu_d = a.mu[m];
-    const float am = (float)fabs(mu_d);
-    const float b = (float)(0.5 * fabs(mu_d));
-    const float bb = b * b;
-    if (lane == 0) {
-        swt[warp] = (float)(0.5 * a.w[m]);
-        swm[warp] = (float)(0.5 * a.w[m] * mu_d * mu_d);
-    }
-    const double *Iin = pos ? a.Iin0 : a.IinX;
-    float psi0 = (g0 < G) ? (float)Iin[g0] : 0.f;
-    float psi1 = (g0 + 1 < G) ? (float)Iin[g0 + 1] : 0.f;
-
-    const int nstrip = (nx + kStrip - 1) / kStrip;
-    const size_t dstride = (size_t)2 * ldG;
-    const float *Iold_m = Iold + (size_t)m * nx * dstride + g0;
-    float *Inew_m = Inew + (size_t)m * nx * dstride + g0;
-
-    auto range = [&](int st, int &c0, int &ns) {
-        if (pos) {
-            c0 = st * kStrip;
-            ns = min(kStrip, nx - c0);
-        } else {
-            const int c1 = nx - st * kStrip;
-            c0 = max(c1 - kStrip, 0);
-            ns = c1 - c0;
-        }
-    };
-    auto prefetch = [&](int st, int bf) {
-        int c0, ns;
-        range(st, c0, ns);
-        float *it = itile + ((size_t)bf * D + warp) * kStrip * 128 + 2 * lane;
-        for (int cc = 0; cc < ns; ++cc) {
-            if (lv) {
-                cp_async<8>(it + cc * 128, Iold_m + (size_t)(c0 + cc) * dstride);
-                cp_async<8>(it + cc * 128 + 64, Iold_m + (size_t)(c0 + cc) * dstride + ldG);
-            } else {
-                *reinterpret_cast<float2 *>(it + cc * 128) = make_float2(0.f, 0.f);
-                *reinterpret_cast<float2 *>(it + cc * 128 + 64) = make_float2(0.f, 0.f);
-            }
-        }
-        float *rs = rawS + bf * kStrip * kP2, *re = rawE + bf * kStrip * kP2;
-        for (int idx = tid; idx < 64 * kStrip; idx += nthr) {
-            const int gl = idx / kStrip, cc = idx - gl * kStrip;
-            const int gg = gt * 64 + gl;
-            if (cc < ns && gg < G) {
-                cp_async<4>(rs + cc * kP2 + gl, sigE + (size_t)gg * nx + c0 + cc);
-                cp_async<4>(re + cc * kP2 + gl, emis + (size_t)gg * nx + c0 + cc);
-            } else {
-                rs[cc * kP2 + gl] = 0.f;
-                re[cc * kP2 + gl] = 0.f;
-            }
-        }
-        cp_commit();
-    };
-
-    for (int k = 0; k < NS - 1; ++k) {
-        if (k < nstrip)
-            prefetch(k, k);
-        else
-            cp_commit();
-    }
-    for (int st = 0; st < nstrip; ++st) {
-        const int bf = st % NS;
-        int c0, ns;
-        range(st, c0, ns);
-        if (st + NS - 1 < nstrip)
-            prefetch(st + NS - 1, (st + NS - 1) % NS);
-        else
-            cp_commit();
-        cp_wait<NS - 1>();
-        if (tid < ns)
-            skap[tid] = a.kap32 ? a.kap32[c0 + tid] : (float)(0.5 * a.h[c0 + tid] * a.icdt);
-        __syncthreads();
-        const float *tth = rawS + bf * kStrip * kP2 + 2 * lane;
-        const float *tq = rawE + bf * kStrip * kP2 + 2 * lane;
-        const float *it = itile + ((size_t)bf * D + warp) * kStrip * 128 + 2 * lane;
-        float *psw = ps + warp * kStrip * kP2 + 2 * lane;
-#pragma unroll 4
-        for (int kk = 0; kk < ns; ++kk) {
-            const int cc = pos ? kk : ns - 1 - kk;
-            const int i = c0 + cc;
-            const float2 IL = *reinterpret_cast<const float2 *>(it + cc * 128);
-            const float2 IR = *reinterpret_cast<const float2 *>(it + cc * 128 + 64);
-            const float2 th = *reinterpret_cast<const float2 *>(tth + cc * kP2);
-            const float2 q = *reinterpret_cast<const float2 *>(tq + cc * kP2);
-            const float kap = skap[cc];
-            const float aa0 = b + th.x, aa1 = b + th.y;
-            const float inv0 = __frcp_rn(aa0 * aa0 + bb), inv1 = __frcp_rn(aa1 * aa1 + bb);
-            float pL0, pR0, pL1, pR1;
-            if (pos) {
-                const float rL0 = q.x + kap * IL.x + am * psi0, rR0 = q.x + kap * IR.x;
-                const float rL1 = q.y + kap * IL.y + am * psi1, rR1 = q.y + kap * IR.y;
-                pL0 = (aa0 * rL0 - b * rR0) * inv0;
-                pR0 = (aa0 * rR0 + b * rL0) * inv0;
-                pL1 = (aa1 * rL1 - b * rR1) * inv1;
-                pR1 = (aa1 * rR1 + b * rL1) * inv1;
-                psi0 = pR0;
-                psi1 = pR1;
-            } else {
-                const float rR0 = q.x + kap * IR.x + am * psi0, rL0 = q.x + kap * IL.x;
-                const float rR1 = q.y + kap * IR.y + am * psi1, rL1 = q.y + kap * IL.y;
-                pR0 = (aa0 * rR0 - b * rL0) * inv0;
-                pL0 = (aa0 * rL0 + b * rR0) * inv0;
-                pR1 = (aa1 * rR1 - b * rL1) * inv1;
-                pL1 = (aa1 * rL1 + b * rR1) * inv1;
-                psi0 = pL0;
-                psi1 = pL1;
-            }
-            if (lv) {
-                *reinterpret_cast<float2 *>(Inew_m + (size_t)i * dstride) = make_float2(pL0, pL1);
-                *reinterpret_cast<float2 *>(Inew_m + (size_t)i * dstride + ldG) = make_float2(pR0, pR1);
-            }
-            *reinterpret_cast<float2 *>(psw + cc * kP2) = make_float2(pL0 + pR0, pL1 + pR1);
-        }
-        __syncthreads();
-        for (int idx = tid; idx < 64 * kStrip; idx += nthr) {
-            const int gl = idx / kStrip, cc = idx - gl * kStrip;
-            const int gg = gt * 64 + gl;
-            if (cc < ns && gg < G) {
-                Acc<float> s0, s2;
-                for (int d = 0; d < D; ++d) {
-                    const float v = ps[(d * kStrip + cc) * kP2 + gl];
-                    s0.add(swt[d] * v);
-                    s2.add(swm[d] * v);
-                }
-                const size_t o = ((size_t)(dtile * 2 + 0) * G + gg) * nx + c0 + cc;
-                part[o] = s0.s;
-                part[o + (size_t)G * nx] = s2.s;
-            }
-        }
-    }
-    if (lv)
-        *reinterpret_cast<float2 *>(reinterpret_cast<float *>(a.psi_exit) + (size_t)m * ldG + g0) =
-            make_float2(psi0, psi1);
-}
-
-template <int kStrip, int NS>
-__global__ void __launch_bounds__(256) k_sweep2(SweepArgs a)
-{
-    sweep2_body<kStrip, NS>(a, blockIdx.x, blockIdx.y);
-}
-
-template <int kStrip, int NS>
-__global__ void __launch_bounds__(256) k_sweep2_b(const int *__restrict__ meta, int N,
-                                                  const SweepArgs *__restrict__ xs)
-{
-    for (int b = blockIdx.x;; b += gridDim.x) {
-        int s, bx, by;
-        if (!bdecode(meta, N, b, s, bx, by)) break;
-        const SweepArgs a = xs[s];
-        sweep2_body<kStrip, NS>(a, bx, by);
-        __syncthreads();
-    }
-}
-
-// ---- FP32 sweep with all of a direction tile's recurrences in one thread ----
-// Each warp owns 32 groups (one per lane) and the tile's D directions, all swept by every
-// lane: D independent recurrences per thread, so the angular moments of a (cell, group)
-// are summed in the thread's registers -- no cross-warp reduction, no CTA barrier -- and
-// the warps of a CTA (four group tiles) never wait for one another.  Intensities stream
-// straight from global memory into registers (each (cell, corner, direction) row of the
-// warp is one 128-byte line), the next cell's rows loaded while the current one is solved;
-// the pre-scaled sigma_t h/2 and h e/2 ([G][nx]) and the partial moments ([G][nx] per
-// tile) pass through a per-warp shared-memory tile of S cells so that their global
-// accesses run along cells.  It needs D x (group tiles) warps of work, so it suits large
-// problems and batches (fc_1024 has 256 such warps for 152 SMs).
-template <int kStrip>
-struct Sweep4Smem {
-    static constexpr int kW = 4;                     // warps (group tiles) per CTA
-    static constexpr int kTile = kStrip * kPadG;     // floats per per-warp array
-    static constexpr size_t total = sizeof(float) * (size_t)kW * (4 * kTile + kStrip);
-};
-
-template <int DPT, int kStrip>
-__device__ void sweep4_body(const SweepArgs &a, int dtile, int by)
-{
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    constexpr int kT = Sweep4Smem<kStrip>::kTile;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int gt = by * Sweep4Smem<kStrip>::kW + warp;   // this warp's group tile
-    const int nx = a.nx, G = a.G, ldG = a.ldG;
-    if (gt * 32 >= ldG) return;                          // no barrier below: safe
-    float *tS = reinterpret_cast<float *>(smem_raw) + (size_t)warp * (4 * kT + kStrip);   // [S][33]
-    float *tE = tS + kT, *tP0 = tS + 2 * kT, *tP2 = tS + 3 * kT, *tK = tS + 4 * kT;
-    const int g = gt * 32 + lane;
-    const bool pos = dtile < a.N / DPT;
-    const int m0 = dtile * DPT;
-    const float *__restrict__ Iold = reinterpret_cast<const float *>(a.I_old);
-    float *__restrict__ Inew = reinterpret_cast<float *>(a.I_new);
-    const float *__restrict__ sigE = reinterpret_cast<const float *>(a.sigE);
-    const float *__restrict__ emis = reinterpret_cast<const float *>(a.emis);
-    float *part = reinterpret_cast<float *>(a.part);
-    const size_t dstride = (size_t)2 * ldG;
-
-    float am[DPT], b[DPT], bb[DPT], wt[DPT], wm[DPT], psi[DPT];
-#pragma unroll
-    for (int j = 0; j < DPT; ++j) {
-        const double mu = a.mu[m0 + j];
-        am[j] = (float)fabs(mu);
-        b[j] = (float)(0.5 * fabs(mu));
-        bb[j] = __fmul_rn(b[j], b[j]);
-        wt[j] = (float)(0.5 * a.w[m0 + j]);
-        wm[j] = (float)(0.5 * a.w[m0 + j] * mu * mu);
-        psi[j] = (g < G) ? (float)(pos ? a.Iin0[g] : a.IinX[g]) : 0.f;
-    }
-    // rows of direction m0 + j at cell c: Iold + ((m0 + j) nx + c) dstride + corner ldG + g
-    const float *Iw = Iold + (size_t)m0 * nx * dstride + g;
-    float *Ow = Inew + (size_t)m0 * nx * dstride + g;
-    const size_t dj = (size_t)nx * dstride;   // one direction further
-    auto load_cell = [&](int c, float (&L)[DPT], float (&R)[DPT]) {
-#pragma unroll
-        for (int j = 0; j < DPT; ++j) {
-            L[j] = __ldcs(Iw + j * dj + (size_t)c * dstride);
-            R[j] = __ldcs(Iw + j * dj + (size_t)c * dstride + ldG);
-        }
-    };
-    const int nstrip = (nx + kStrip - 1) / kStrip;
-    float nL[DPT], nR[DPT];
-    load_cell(pos ? 0 : nx - 1, nL, nR);
-    for (int st = 0; st < nstrip; ++st) {
-        int c0, ns;
-        if (pos) {
-            c0 = st * kStrip;
-            ns = min(kStrip, nx - c0);
-        } else {
-            const int c1 = nx - st * kStrip;
-            c0 = max(c1 - kStrip, 0);
-            ns = c1 - c0;
-        }
-        // this strip's sigma_t h/2 and h e/2 of the warp's 32 groups, along cells
-        for (int idx = lane; idx < 32 * kStrip; idx += 32) {
-            const int gl = idx / kStrip, cc = idx - gl * kStrip;
-            const int gg = gt * 32 + gl;
-            const bool ok = cc < ns && gg < G;
-            tS[cc * kPadG + gl] = ok ? sigE[(size_t)gg * nx + c0 + cc] : 0.f;
-            tE[cc * kPadG + gl] = ok ? emis[(size_t)gg * nx + c0 + cc] : 0.f;
-        }
-        if (lane < ns)   // h/(2 c dt)
-            tK[lane] = a.kap32 ? a.kap32[c0 + lane] : (float)(0.5 * a.h[c0 + lane] * a.icdt);
-        __syncwarp();
-        for (int kk = 0; kk < ns; ++kk) {
-            const int cc = pos ? kk : ns - 1 - kk;
-            const int c = c0 + cc;
-            float IL[DPT], IR[DPT];
-#pragma unroll
-            for (int j = 0; j < DPT; ++j) {
-                IL[j] = nL[j];
-                IR[j] = nR[j];
-            }
-            const int cn = pos ? c + 1 : c - 1;   // the next cell's rows, in flight meanwhile
-            if (cn >= 0 && cn < nx) load_cell(cn, nL, nR);
-            const float th = tS[cc * kPadG + lane], q = tE[cc * kPadG + lane];
-            const float kap = tK[cc];
-            // explicit rounding intrinsics: the single-slab and the batched kernel inline
-            // this body separately, and a contraction the compiler chose differently in one
-            // of them would break their bit-for-bit agreement
-            Acc<float> s0, s2;
-#pragma unroll
-            for (int j = 0; j < DPT; ++j) {
-                const float aa = __fadd_rn(b[j], th);
-                const float inv = __frcp_rn(__fmaf_rn(aa, aa, bb[j]));
-                float pL, pR;
-                if (pos) {
-                    const float rL = __fmaf_rn(am[j], psi[j], __fmaf_rn(kap, IL[j], q));
-                    const float rR = __fmaf_rn(kap, IR[j], q);
-                    pL = __fmul_rn(__fmaf_rn(aa, rL, -__fmul_rn(b[j], rR)), inv);
-                    pR = __fmul_rn(__fmaf_rn(aa, rR, __fmul_rn(b[j], rL)), inv);
-                    psi[j] = pR;
-                } else {
-                    const float rR = __fmaf_rn(am[j], psi[j], __fmaf_rn(kap, IR[j], q));
-                    const float rL = __fmaf_rn(kap, IL[j], q);
-                    pR = __fmul_rn(__fmaf_rn(aa, rR, -__fmul_rn(b[j], rL)), inv);
-                    pL = __fmul_rn(__fmaf_rn(aa, rL, __fmul_rn(b[j], rR)), inv);
-                    psi[j] = pL;
-                }
-                if (g < ldG) {
-                    __stcs(Ow + j * dj + (size_t)c * dstride, pL);
-                    __stcs(Ow + j * dj + (size_t)c * dstride + ldG, pR);
-                }
-                const float v = __fadd_rn(pL, pR);
-                s0.add(__fmul_rn(wt[j], v));
-                s2.add(__fmul_rn(wm[j], v));
-            }
-            tP0[cc * kPadG + lane] = s0.s;
-            tP2[cc * kPadG + lane] = s2.s;
-        }
-        __syncwarp();
-        // the strip's partial moments, along cells
-        for (int idx = lane; idx < 32 * kStrip; idx += 32) {
-            const int gl = idx / kStrip, cc = idx - gl * kStrip;
-            const int gg = gt * 32 + gl;
-            if (cc < ns && gg < G) {
-                const size_t o = ((size_t)(dtile * 2 + 0) * G + gg) * nx + c0 + cc;
-                part[o] = tP0[cc * kPadG + gl];
-                part[o + (size_t)G * nx] = tP2[cc * kPadG + gl];
-            }
-        }
-        __syncwarp();
-    }
-    if (g < ldG)
-#pragma unroll
-        for (int j = 0; j < DPT; ++j)
-            reinterpret_cast<float *>(a.psi_exit)[(size_t)(m0 + j) * ldG + g] = psi[j];
-}
-
-// one kernel per tile height D (= a.D, chosen on the host): the per-thread arrays size
-// the registers, and a smaller D leaves room for more resident warps
-template <int DPT, int kStrip>
-__global__ void __launch_bounds__(128) k_sweep4(SweepArgs a)
-{
-    sweep4_body<DPT, kStrip>(a, blockIdx.x, blockIdx.y);
-}
-
-template <int DPT, int kStrip>
-__global__ void __launch_bounds__(128) k_sweep4_b(const int *__restrict__ meta, int N,
-                                                  const SweepArgs *__restrict__ xs)
-{
-    for (int b = blockIdx.x;; b += gridDim.x) {
-        int s, bx, by;
-        if (!bdecode(meta, N, b, s, bx, by)) break;
-        const SweepArgs a = xs[s];
-        sweep4_body<DPT, kStrip>(a, bx, by);
-        __syncwarp();   // this warp's shared tile is reused by its next work item
-    }
-}
-
 // f_g = sum_t A2 / sum_t A0 per (group, cell), in R; boundary factors per group in FP64.
 // Blocks [0, nb) with nb = ceil(G / 8) take one group per warp for the boundary factors;
 // the blocks after them take one (group, cell) per thread.  The boundary warps come first so
@@ -765,19 +385,20 @@ __global__ void k_sweep_finalize_b(const int *__restrict__ meta, int N,
     }
 }
 
-// Candidate tile shapes (S, NS); index 0 is the default.  Measured at 500 cells x 64
-// directions x 1024 groups with D = 8: FP32 (16, 2) 0.215 ms, (8, 4) 0.225, (32, 2) 0.282,
-// (16, 3) 0.299 (a third buffer costs a resident CTA per SM); FP64 (8, 2) 1.26 ms,
-// (16, 2) 1.37, (8, 3) 1.37.
+// Candidate tile shapes (S, NS, kind); index 0 is the default.  FP32: the lean sweeps of
+// sweepf.cu (kind 5: one group per lane, 6: two), which exist for D = 4, 8 and 16, and the
+// strip sweep of this file (kind 1), which serves every other tile height (N not a
+// multiple of 4).  Measured at 500 cells x 64 directions x 1024 groups: lean one group per
+// lane D = 16 (8, 4) 0.100 ms with the finalize, (16, 2) 0.104; two groups per lane
+// D = 8 (8, 4) 0.108 (it wins on some batches); the strip sweep D = 8 (16, 2) 0.209.
+// FP64 (strip sweep): (8, 2) 1.26 ms, (16, 2) 1.37, (8, 3) 1.37.
 struct Shape {
-    int S, NS, V;   // strip cells, strip buffers, groups per lane (4: a tile's directions
-                    // per thread, registers instead of strip buffers; 5, 6: the lean sweep
-                    // of sweepf.cu with one, two groups per lane)
+    int S, NS, V;   // strip cells, strip buffers, kind (1: strip sweep; 5, 6: lean sweep
+                    // with one, two groups per lane)
 };
-constexpr Shape kShapes32[] = {{16, 2, 1}, {16, 3, 1}, {16, 4, 1}, {8, 4, 1}, {8, 6, 1},
-                               {32, 2, 1}, {16, 2, 2}, {8, 2, 2}, {8, 3, 2}, {8, 4, 2},
-                               {16, 1, 4}, {32, 1, 4}, {16, 2, 5}, {8, 3, 5}, {8, 2, 5},
-                               {8, 2, 6}, {8, 4, 6}, {8, 4, 5}};
+constexpr Shape kShapes32[] = {{8, 4, 5}, {16, 2, 5}, {8, 3, 5}, {8, 2, 5},
+                               {8, 2, 6}, {8, 4, 6}, {16, 2, 1}};
+constexpr int kStrip32 = 6;   // the FP32 strip sweep's index (tile heights without a lean kernel)
 constexpr Shape kShapes64[] = {{8, 2, 1}, {16, 2, 1}, {8, 3, 1}};
 
 // largest power of two <= cap dividing N: the direction-tile height D_min that the
@@ -814,110 +435,30 @@ cudaError_t launch_shape(const SweepArgs *a, int M, int ldG, int D, const int *m
     return cudaGetLastError();
 }
 
-template <int S, int NS>
-cudaError_t launch_shape2(const SweepArgs *a, int M, int ldG, int D, const int *meta, int N,
-                          const SweepArgs *xs, int grid, cudaStream_t st)
-{
-    const size_t sm = Sweep2Smem<S, NS>(D).total;
-    if (sm > 227 * 1024) return cudaErrorInvalidConfiguration;
-    if (a) {
-        cudaError_t e = cudaFuncSetAttribute(k_sweep2<S, NS>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        if (e != cudaSuccess) return e;
-        k_sweep2<S, NS><<<dim3(M / D, (ldG + 63) / 64), 32 * D, sm, st>>>(*a);
-    } else {
-        cudaError_t e = cudaFuncSetAttribute(k_sweep2_b<S, NS>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        if (e != cudaSuccess) return e;
-        k_sweep2_b<S, NS><<<grid, 32 * D, sm, st>>>(meta, N, xs);
-    }
-    return cudaGetLastError();
-}
-
-template <int DPT, int S>
-cudaError_t launch_shape4_d(const SweepArgs *a, int M, int ldG, int D, const int *meta, int N,
-                            const SweepArgs *xs, int grid, cudaStream_t st)
-{
-    const size_t sm = Sweep4Smem<S>::total;
-    if (a) {
-        cudaError_t e = cudaFuncSetAttribute(k_sweep4<DPT, S>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        if (e != cudaSuccess) return e;
-        k_sweep4<DPT, S><<<dim3(M / D, (ldG / 32 + 3) / 4), 128, sm, st>>>(*a);
-    } else {
-        cudaError_t e = cudaFuncSetAttribute(k_sweep4_b<DPT, S>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        if (e != cudaSuccess) return e;
-        k_sweep4_b<DPT, S><<<grid, 128, sm, st>>>(meta, N, xs);
-    }
-    return cudaGetLastError();
-}
-
-template <int S>
-cudaError_t launch_shape4(const SweepArgs *a, int M, int ldG, int D, const int *meta, int N,
-                          const SweepArgs *xs, int grid, cudaStream_t st)
-{
-    switch (D) {
-    case 1: return launch_shape4_d<1, S>(a, M, ldG, D, meta, N, xs, grid, st);
-    case 2: return launch_shape4_d<2, S>(a, M, ldG, D, meta, N, xs, grid, st);
-    case 4: return launch_shape4_d<4, S>(a, M, ldG, D, meta, N, xs, grid, st);
-    case 8: return launch_shape4_d<8, S>(a, M, ldG, D, meta, N, xs, grid, st);
-    default: return cudaErrorInvalidConfiguration;
-    }
-}
-
-template <typename R, typename SR>
+template <typename R>
 cudaError_t dispatch_shape(int shape, const SweepArgs *a, int M, int ldG, int D, const int *meta,
                            int N, const SweepArgs *xs, int grid, cudaStream_t st)
 {
-    if (D > 8 && !(sizeof(R) == 4 && sizeof(SR) == 4 && kShapes32[shape].V >= 5))
-        return cudaErrorInvalidConfiguration;   // 32 D threads: only the lean sweep has D = 16
-    // two groups per lane: FP32 with pre-scaled FP32 inputs only; the FP32 sweep with FP64
-    // inputs takes the one-group shape of the same strip
-    if (sizeof(R) == 4 && sizeof(SR) == 4) {
-        switch (shape) {
-        case 6: return launch_shape2<16, 2>(a, M, ldG, D, meta, N, xs, grid, st);
-        case 7: return launch_shape2<8, 2>(a, M, ldG, D, meta, N, xs, grid, st);
-        case 8: return launch_shape2<8, 3>(a, M, ldG, D, meta, N, xs, grid, st);
-        case 9: return launch_shape2<8, 4>(a, M, ldG, D, meta, N, xs, grid, st);
-        case 10: return launch_shape4<16>(a, M, ldG, D, meta, N, xs, grid, st);
-        case 11: return launch_shape4<32>(a, M, ldG, D, meta, N, xs, grid, st);
-        default: break;
-        }
+    if (sizeof(R) == 4) {   // FP32: pre-scaled FP32 inputs (sigma_t h/2, h e/2)
         const Shape sh = kShapes32[shape];
-        if (sh.V >= 5) {   // lean kernels exist for D = 4, 8, 16; other heights take shape 0 / 7
-            if (D == 4 || D == 8 || D == 16)
-                return launch_sweepf(sh.V, sh.S, sh.NS, a, M, ldG, D, meta, N, xs, grid, st);
-            if (sh.V == 6) return launch_shape2<8, 2>(a, M, ldG, D, meta, N, xs, grid, st);
-            shape = 0;
-        }
+        if (sh.V >= 5 && (D == 4 || D == 8 || D == 16))
+            return launch_sweepf(sh.V, sh.S, sh.NS, a, M, ldG, D, meta, N, xs, grid, st);
+        if (D > 8) return cudaErrorInvalidConfiguration;   // 32 D threads: lean sweeps only
+        return launch_shape<float, float, 16, 2>(a, M, ldG, D, meta, N, xs, grid, st);
     }
-    if (sizeof(R) == 4) {
-        if (shape == 6 || shape == 10 || shape == 11 || shape == 12 || shape == 13 || shape == 14 ||
-            shape == 17)
-            shape = 0;
-        if (shape == 7 || shape == 8 || shape == 9 || shape == 15 || shape == 16) shape = 3;
-        switch (shape) {
-        case 1: return launch_shape<R, SR, 16, 3>(a, M, ldG, D, meta, N, xs, grid, st);
-        case 2: return launch_shape<R, SR, 16, 4>(a, M, ldG, D, meta, N, xs, grid, st);
-        case 3: return launch_shape<R, SR, 8, 4>(a, M, ldG, D, meta, N, xs, grid, st);
-        case 4: return launch_shape<R, SR, 8, 6>(a, M, ldG, D, meta, N, xs, grid, st);
-        case 5: return launch_shape<R, SR, 32, 2>(a, M, ldG, D, meta, N, xs, grid, st);
-        default: return launch_shape<R, SR, 16, 2>(a, M, ldG, D, meta, N, xs, grid, st);
-        }
-    }
+    if (D > 8) return cudaErrorInvalidConfiguration;
     switch (shape) {
-    case 1: return launch_shape<R, SR, 16, 2>(a, M, ldG, D, meta, N, xs, grid, st);
-    case 2: return launch_shape<R, SR, 8, 3>(a, M, ldG, D, meta, N, xs, grid, st);
-    default: return launch_shape<R, SR, 8, 2>(a, M, ldG, D, meta, N, xs, grid, st);
+    case 1: return launch_shape<double, double, 16, 2>(a, M, ldG, D, meta, N, xs, grid, st);
+    case 2: return launch_shape<double, double, 8, 3>(a, M, ldG, D, meta, N, xs, grid, st);
+    default: return launch_shape<double, double, 8, 2>(a, M, ldG, D, meta, N, xs, grid, st);
     }
 }
 
-template <typename R, typename SR>
+template <typename R>
 cudaError_t launch_sweep_t(const Problem &p, const SweepArgs &a)
 {
-    cudaError_t e = dispatch_shape<R, SR>(p.sweep_shape, &a, p.M, p.ldG, a.D, nullptr, 0, nullptr,
-                                          0, p.stream);
+    cudaError_t e = dispatch_shape<R>(p.sweep_shape, &a, p.M, p.ldG, a.D, nullptr, 0, nullptr, 0,
+                                      p.stream);
     if (e != cudaSuccess) return e;
     const FinalizeArgs fa = make_finalize_args(p, a);
     k_sweep_finalize<R><<<(unsigned)(fa.nb_cell + finalize_bnd_blocks(p.G)), 256, 0, p.stream>>>(fa);
@@ -957,10 +498,11 @@ void sweep_shape_info(int precision, int shape, int *S, int *NS)
     *NS = sh.NS;
 }
 
-int sweep_group_tiles(int precision, int shape, int ldG)
+int sweep_group_tiles(int precision, int shape, int D, int ldG)
 {
-    const Shape sh = sweep_fp32(precision) ? kShapes32[shape] : kShapes64[shape];
-    return (sh.V == 2 || sh.V == 6) ? (ldG + 63) / 64 : sh.V == 4 ? (ldG / 32 + 3) / 4 : ldG / 32;
+    if (!sweep_fp32(precision)) return ldG / 32;
+    const bool lean = kShapes32[shape].V >= 5 && (D == 4 || D == 8 || D == 16);
+    return lean && kShapes32[shape].V == 6 ? (ldG + 63) / 64 : ldG / 32;
 }
 
 int sweep_D_candidates(const Problem &p, int *D)
@@ -1021,22 +563,20 @@ cudaError_t launch_sweep(const Problem &p, double dt, const void *sigE, const vo
 {
     SweepArgs a = make_sweep_args(p, dt, sigE, emis, I_old, I_new, part, psi_exit, f, fb0, fbX,
                                   C0, CX, pick_D(p));
-    if (!sweep_fp32(p.precision)) return launch_sweep_t<double, double>(p, a);
-    if (sigma_fp32) {   // the pre-scaled inputs carry h/(2 c dt) after e (launch_opacity)
-        a.kap32 = reinterpret_cast<const float *>(emis) + (size_t)p.G * p.nx;
-        return launch_sweep_t<float, float>(p, a);
-    }
-    return launch_sweep_t<float, double>(p, a);
+    if (!sweep_fp32(p.precision)) return launch_sweep_t<double>(p, a);
+    if (!sigma_fp32 || !p.dir32) return cudaErrorInvalidValue;   // FP32 sweeps: FP32 inputs
+    // the pre-scaled inputs carry h/(2 c dt) after e (launch_opacity, launch_prescale32)
+    a.kap32 = reinterpret_cast<const float *>(emis) + (size_t)p.G * p.nx;
+    return launch_sweep_t<float>(p, a);
 }
 
 cudaError_t launch_sweep_b(int precision, bool sigma_fp32, int D, int shape, const int *meta,
                            int N, const SweepArgs *xs, int grid, cudaStream_t st)
 {
     if (!sweep_fp32(precision))
-        return dispatch_shape<double, double>(shape, nullptr, 0, 0, D, meta, N, xs, grid, st);
-    if (sigma_fp32)
-        return dispatch_shape<float, float>(shape, nullptr, 0, 0, D, meta, N, xs, grid, st);
-    return dispatch_shape<float, double>(shape, nullptr, 0, 0, D, meta, N, xs, grid, st);
+        return dispatch_shape<double>(shape, nullptr, 0, 0, D, meta, N, xs, grid, st);
+    if (!sigma_fp32) return cudaErrorInvalidValue;
+    return dispatch_shape<float>(shape, nullptr, 0, 0, D, meta, N, xs, grid, st);
 }
 
 cudaError_t launch_finalize_b(int precision, const int *meta, int N, const FinalizeArgs *xs,

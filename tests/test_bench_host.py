@@ -31,26 +31,27 @@ def test_unknown_cycle_is_rejected():
 
 def test_sweep_kernel_names_follow_the_shape_table():
     assert bench.sweep_kernel(False, 8, 0).startswith("k_sweep<double,double,8,2>")
-    assert bench.sweep_kernel(True, 8, 0).startswith("k_sweep<float,float,16,2>")
-    assert bench.sweep_kernel(True, 8, 7).startswith("k_sweep2<8,2>")
-    assert bench.sweep_kernel(True, 4, 10).startswith("k_sweep4<4,16>")
-    assert bench.sweep_kernel(True, 16, 17).startswith("k_sweepf<1,8,4,16>")
-    assert bench.sweep_kernel(True, 8, 16).startswith("k_sweepf<2,8,4,8>")
+    assert bench.sweep_kernel(True, 8, 6).startswith("k_sweep<float,float,16,2>")
+    assert bench.sweep_kernel(True, 2, 0).startswith("k_sweep<float,float,16,2>")
+    assert bench.sweep_kernel(True, 16, 0).startswith("k_sweepf<1,8,4,16>")
+    assert bench.sweep_kernel(True, 8, 5).startswith("k_sweepf<2,8,4,8>")
     assert all(bench.sweep_kernel(True, 8, k).endswith("k_sweep_finalize<float>")
-               for k in range(18))
+               for k in range(7))
 
 
 def test_traffic_is_reported_only_for_the_captured_tile_and_code():
-    for key, t in bench.TRAFFIC.items():
-        assert bench._traffic(key, t["tile"]) == t["bytes"]
-        D, shape = t["tile"]
-        assert bench._traffic(key, (D, shape + 1)) is None
-    t = dict(bench.TRAFFIC["sweep_fp32"])
+    key = "sweep_fp32"
+    t = dict(bench.TRAFFIC[key])
     try:
-        bench.TRAFFIC["sweep_fp32"] = dict(t, sha="0" * 16)   # code changed since the capture
-        assert bench._traffic("sweep_fp32", t["tile"]) is None
+        sha = bench._src_sha(t["files"])
+        bench.TRAFFIC[key] = dict(t, sha=sha, bytes=123)
+        D, shape = t["tile"]
+        assert bench._traffic(key, (D, shape)) == 123
+        assert bench._traffic(key, (D, shape + 1)) is None
+        bench.TRAFFIC[key] = dict(t, sha="0" * 16, bytes=123)   # code changed since the capture
+        assert bench._traffic(key, (D, shape)) is None
     finally:
-        bench.TRAFFIC["sweep_fp32"] = t
+        bench.TRAFFIC[key] = t
 
 
 def test_code_hash_ignores_comments(tmp_path, monkeypatch):
