@@ -312,11 +312,13 @@ int trt_k_restrict(trt_handle *h, const trt_level *src, trt_level *dst);
 
 /* Grey LOQD + MEB, one Newton step (eq. eb-Gamma-d, eq. f-derivative-d) on the grey level
  * `g` (g->n == 1) at T* = Tstar [nx], with Q = 2 g->emis, E* = g->Esum, the secant from
- * (sig_prev, T_prev) when have_prev != 0.  Writes T [nx], g->E, g->F, g->Eb0, g->EbX.
+ * (sig_prev, T_prev) when have_prev != 0 where T* != T_prev and |T* - T_prev| >
+ * secant_cut T* (a step passes 0 when the previous grey solve was built on the same grid,
+ * 1e-7 across grids).  Writes T [nx], g->E, g->F, g->Eb0, g->EbX.
  * Returns TRT_ENUMERIC if a temperature is non-positive or non-finite. */
 int trt_k_grey_newton(trt_handle *h, double dt, const double *Tstar, const double *Told,
                       const double *sig_prev, const double *T_prev, int have_prev,
-                      trt_level *g, double *T);
+                      double secant_cut, trt_level *g, double *T);
 
 /* ======================================================================================
  * Allocation-free sweep.  The paper has no counterpart: this exists for callers that can

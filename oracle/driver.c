@@ -30,6 +30,8 @@
 #include <string.h>
 #include "oracle.h"
 
+extern double orc_secant_cut;   /* lo.c: cross-grid secant cut-off (reading) */
+
 #define MAXLEV 16
 
 struct orc_problem {
@@ -371,7 +373,8 @@ int orc_step(orc_problem *p, double dt, int cycle_type, int l_max, double eps,
                     dQ[i] = orc_emission_deriv(G, p->edges, Ttil[i], p->s);
                 }
                 int bad = orc_grey_newton(nx, p->h, dt, p->cv, Ttil, Told, Q, dQ, grey.Esum,
-                                          grey.sig, sigprev, Tprev, have_prev, grey.Eold,
+                                          grey.sig, sigprev, Tprev, have_prev,
+                                          K == 0 ? 0.0 : orc_secant_cut, grey.Eold,
                                           grey.phi, grey.sigR, grey.etaR, grey.etaL, grey.Fold,
                                           grey.phib0[0], grey.phibX[0], grey.C0[0], grey.CX[0],
                                           grey.Ein0[0], grey.Fin0[0], grey.EinX[0],

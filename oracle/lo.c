@@ -32,6 +32,19 @@
 #include <string.h>
 #include "oracle.h"
 
+/* The two conditioning readings (|F| floor of the Rosseland weights, secant cut-off of the
+ * Newton step between grey solves built on different grids), adjustable by
+ * orc_set_readings so that a test can show that the converged state does not depend on
+ * them. */
+static double orc_flux_floor = 1e-6;
+double orc_secant_cut = 1e-7;
+
+void orc_set_readings(double flux_floor, double secant_cut)
+{
+    orc_flux_floor = flux_floor;
+    orc_secant_cut = secant_cut;
+}
+
 /* Thomas algorithm (Gaussian elimination without pivoting for a tridiagonal matrix). */
 void orc_tridiag(int n, const double *lo, const double *di, const double *up,
                  const double *rhs, double *x)
@@ -213,7 +226,7 @@ void orc_restrict(int nx, const double *h, int n_from, int n_to, const int *map,
                 size_t pf = (size_t)p * nf + f;
                 double ER = (f == nx) ? EbX[p] : E[(size_t)p * nx + f];
                 double EL = (f == 0) ? Eb0[p] : E[(size_t)p * nx + f - 1];
-                double wgt = fabs(F[pf]) + 1e-6 * c * 0.5 * (EL + ER);
+                double wgt = fabs(F[pf]) + orc_flux_floor * c * 0.5 * (EL + ER);
                 num += sigR[pf] * wgt;
                 den += wgt;
                 sum += sigR[pf];
@@ -265,17 +278,20 @@ void orc_restrict(int nx, const double *h, int n_from, int n_to, const int *map,
  * Substituting T into the grey balance gives an absorption term linear in E:
  *   R = w (c sig* E - Q*) + (1 - w) cv (T* - Told)/dt,   w = (cv/dt)/Lambda,
  * and cv (T - Told)/dt = R holds identically, so each grey solve conserves energy.
- * Readings: D = 0 on the first grey solve of a time step, and D = 0 unless
- * |T* - T_prev| > 1e-7 T*: the secant quotient carries a relative rounding error of about
- * eps T / |T* - T_prev|, and in a W or F cycle successive grey solves are built on
- * different grids, so sigma-bar jumps while T barely moves; below 1e-7 the quotient would
- * be rounding noise amplified by up to 1e4 and more.  Returns nonzero if a temperature
- * comes out non-positive or non-finite. */
+ * Readings: D = 0 on the first grey solve of a time step and where T* = T_prev.  The
+ * previous grey solve may have been built on another grid (W and F cycles visit a
+ * different grid before every grey solve; two-grid and V cycles build every one on the
+ * fine grid); sigma-bar then also jumps with the grid while T barely moves, and the
+ * quotient is taken only where |T* - T_prev| > secant_cut T* (the caller passes 1e-7 for
+ * such a pair, 0 for two solves on the same grid): its relative rounding error is about
+ * eps T / |T* - T_prev|, and below 1e-7 the cross-grid quotient would be rounding noise
+ * amplified by up to 1e4 and more.  Returns nonzero if a temperature comes out
+ * non-positive or non-finite. */
 int orc_grey_newton(int nx, const double *h, double dt, double cv,
                     const double *Tstar, const double *Told, const double *Q,
                     const double *dQ, const double *Estar,
                     const double *sig, const double *sig_prev, const double *T_prev, int have_prev,
-                    const double *Eold,
+                    double secant_cut, const double *Eold,
                     const double *phi, const double *sigR, const double *etaR,
                     const double *etaL, const double *Fold,
                     double phib0, double phibX, double C0, double CX,
@@ -288,7 +304,8 @@ int orc_grey_newton(int nx, const double *h, double dt, double cv,
     double *Lam = (double *)malloc(sizeof(double) * nx);
     for (int i = 0; i < nx; ++i) {
         double D = 0.0;
-        if (have_prev && fabs(Tstar[i] - T_prev[i]) > 1e-7 * Tstar[i])
+        if (have_prev && Tstar[i] != T_prev[i] &&
+            fabs(Tstar[i] - T_prev[i]) > secant_cut * Tstar[i])
             D = (sig[i] - sig_prev[i]) / (Tstar[i] - T_prev[i]);
         double base = cv / dt + dQ[i];
         double L = base - c * D * Estar[i];

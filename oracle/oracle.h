@@ -85,12 +85,18 @@ int orc_grey_newton(int nx, const double *h, double dt, double cv,
                     const double *Tstar, const double *Told, const double *Q,
                     const double *dQ, const double *Estar,
                     const double *sig, const double *sig_prev, const double *T_prev, int have_prev,
-                    const double *Eold,
+                    double secant_cut, const double *Eold,
                     const double *phi, const double *sigR, const double *etaR,
                     const double *etaL, const double *Fold,
                     double phib0, double phibX, double C0, double CX,
                     double Ein0, double Fin0, double EinX, double FinX,
                     double *T, double *E, double *F, double *Eb0, double *EbX);
+
+/* The |F| floor of the Rosseland weights (default 1e-6: weight |F_p| + floor c E-bar_p) and
+ * the secant cut-off of the Newton step between grey solves built on different grids
+ * (default 1e-7: D = 0 unless |T* - T_prev| > cut T*), both readings where the paper is
+ * silent; settable so that tests can vary them. */
+void orc_set_readings(double flux_floor, double secant_cut);
 
 /* ---- cycle schedules (Sec. 4, Fig. 1, Alg. 3) ---- */
 int orc_schedule(int type, int Gamma, int *S);   /* type 0=V, 1=W, 2=F; returns K */

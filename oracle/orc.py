@@ -50,6 +50,8 @@ def lib():
         L.orc_step.restype = ctypes.c_int
         L.orc_grey_newton.restype = ctypes.c_int
         L.orc_schedule.restype = ctypes.c_int
+        L.orc_set_readings.restype = None
+        L.orc_set_readings.argtypes = [ctypes.c_double, ctypes.c_double]
         _lib = L
     return _lib
 
@@ -68,6 +70,12 @@ def _ipt(a):
 
 def _d(x):
     return ctypes.c_double(float(x))
+
+
+def set_readings(flux_floor=1e-6, secant_cut=1e-7):
+    """Set the |F| floor of the Rosseland weights and the Newton secant cut-off (the
+    defaults are the readings every other caller uses)."""
+    lib().orc_set_readings(flux_floor, secant_cut)
 
 
 def c_light():
@@ -217,7 +225,7 @@ def restrict(h, level, sol, cmap, n_to):
 
 def grey_newton(h, dt, cv, Tstar, Told, Q, dQ, Estar, sig, sig_prev, T_prev, have_prev,
                 Eold, phi, sigR, etaR, etaL, Fold, phib0, phibX, C0, CX,
-                Ein0, Fin0, EinX, FinX):
+                Ein0, Fin0, EinX, FinX, secant_cut=1e-7):
     h = np.ascontiguousarray(h, np.float64)
     nx = h.size
     T = np.zeros(nx)
@@ -228,7 +236,7 @@ def grey_newton(h, dt, cv, Tstar, Told, Q, dQ, Estar, sig, sig_prev, T_prev, hav
     c = lambda a: _p(np.ascontiguousarray(a, np.float64))
     bad = lib().orc_grey_newton(nx, _p(h), _d(dt), _d(cv), c(Tstar), c(Told), c(Q), c(dQ),
                                 c(Estar), c(sig), c(sig_prev), c(T_prev), int(have_prev),
-                                c(Eold), c(phi), c(sigR), c(etaR), c(etaL), c(Fold),
+                                _d(secant_cut), c(Eold), c(phi), c(sigR), c(etaR), c(etaL), c(Fold),
                                 _d(phib0), _d(phibX), _d(C0), _d(CX), _d(Ein0), _d(Fin0),
                                 _d(EinX), _d(FinX), _p(T), _p(E), _p(F),
                                 ctypes.byref(Eb0), ctypes.byref(EbX))

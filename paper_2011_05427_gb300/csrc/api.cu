@@ -516,6 +516,7 @@ int trt_step(trt_handle *h, double dt, const trt_cycle *cyc, trt_stats *stats)
                 a.Tstar = h->Ttil; a.Told = h->Told; a.sig_prev = h->sig_prev; a.T_prev = h->T_prev;
                 a.T = h->Tnew; a.sig_prev_out = h->sig_prev; a.T_prev_out = h->T_prev;
                 a.have_prev = have_prev;
+                a.secant_cut = K == 0 ? 0.0 : kSecantCut;   // grey solves on one grid / across grids
                 a.cv = p.cv; a.s = p.s; a.dt = dt;
                 a.nu_first = p.nu_first; a.nu_last = p.nu_last;
                 a.want_norms = (k == K);
@@ -850,7 +851,7 @@ int trt_k_restrict(trt_handle *h, const trt_level *src, trt_level *dst)
 
 int trt_k_grey_newton(trt_handle *h, double dt, const double *Tstar, const double *Told,
                       const double *sig_prev, const double *T_prev, int have_prev,
-                      trt_level *g, double *T)
+                      double secant_cut, trt_level *g, double *T)
 {
     if (!h || !g || g->n != 1 || !(dt > 0) || !Tstar || !Told || !T) return TRT_EINVAL;
     if (have_prev && (!sig_prev || !T_prev)) return TRT_EINVAL;
@@ -864,6 +865,7 @@ int trt_k_grey_newton(trt_handle *h, double dt, const double *Tstar, const doubl
     a.sig_prev_out = h->part;             // scratch, not state
     a.T_prev_out = h->part + p.nx;
     a.have_prev = have_prev;
+    a.secant_cut = secant_cut;
     a.cv = p.cv; a.s = p.s; a.dt = dt;
     a.nu_first = p.nu_first; a.nu_last = p.nu_last;
     a.want_norms = 0;

@@ -375,6 +375,7 @@ void build_stage(trt_batch *b, int id, double dt, int cycle_type)
                 a.sig_prev_out = x->sig_prev; a.T_prev_out = x->T_prev;
                 a.have_prev = 0;
                 a.have_prev_dev = b->d_have_prev + s;
+                a.secant_cut = S[s].empty() ? 0.0 : kSecantCut;
                 a.cv = p.cv; a.s = p.s; a.dt = dt;
                 a.nu_first = p.nu_first; a.nu_last = p.nu_last;
                 a.want_norms = (k == (int)S[s].size());

@@ -13,6 +13,10 @@ constexpr double kPi = 3.14159265358979323846;
 constexpr double kCB = 15.0 * kAR * kC / (2.0 * kPi * kPi * kPi * kPi);
 constexpr int kSer = 48;            // power-series terms for the Planck-type integrals, x < 2
 constexpr double kXSplit = 2.0;     // series below, exponential tails at and above
+// secant of the grey Newton step between grey solves built on different grids (W, F
+// cycles): taken only where |T* - T_prev| > kSecantCut T* (Sec. 5, eq. f-derivative-d;
+// a reading, the paper is silent on the degenerate quotient)
+constexpr double kSecantCut = 1e-7;
 
 // Planck-type integral constants (physics.cu): series coefficients and totals.
 struct SeriesTables {
@@ -104,6 +108,10 @@ struct GreyArgs {
     const double *Tstar, *Told, *sig_prev, *T_prev;
     double *T, *sig_prev_out, *T_prev_out;
     int have_prev;
+    // the secant of the Newton step is taken where T* != T_prev and |T* - T_prev| >
+    // secant_cut T*: 0 when the previous grey solve was built on the same grid (two-grid
+    // and V cycles), 1e-7 across grids (W, F: sigma-bar also jumps with the grid)
+    double secant_cut;
     // when non-null, the device flag replaces have_prev (read at entry, set to 1 on exit):
     // the batched driver keeps it per slab so that its argument blocks stay fixed
     int *have_prev_dev;

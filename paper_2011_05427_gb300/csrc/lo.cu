@@ -884,8 +884,8 @@ __device__ inline void grey_newton_cell(const GreyArgs &a, const Level &g, int h
     double D = 0.0;
     if (have_prev) {
         const double Tp = a.T_prev[i];
-        // secant only where |dT| is far above rounding (relative noise ~ eps T/|dT|)
-        if (fabs(Ts - Tp) > 1e-7 * Ts) D = (sig - a.sig_prev[i]) * rcp64(Ts - Tp);
+        // across grids only where |dT| is far above rounding (relative noise ~ eps T/|dT|)
+        if (Ts != Tp && fabs(Ts - Tp) > a.secant_cut * Ts) D = (sig - a.sig_prev[i]) * rcp64(Ts - Tp);
     }
     const double base = cvdt + dQ;
     double L = base - kC * D * g.Esum[i];

@@ -130,7 +130,7 @@ def lib():
     L.trt_k_restrict.argtypes = [_vp, ctypes.POINTER(trt_level), ctypes.POINTER(trt_level)]
     L.trt_k_grey_newton.restype = ctypes.c_int
     L.trt_k_grey_newton.argtypes = [_vp, ctypes.c_double, _vp, _vp, _vp, _vp, ctypes.c_int,
-                                    ctypes.POINTER(trt_level), _vp]
+                                    ctypes.c_double, ctypes.POINTER(trt_level), _vp]
     _ip = ctypes.POINTER(ctypes.c_int)
     L.trt_sweep_time.restype = ctypes.c_int
     L.trt_sweep_time.argtypes = [_vp, ctypes.c_double, ctypes.c_int,
@@ -379,7 +379,7 @@ class Solver:
         self._check(lib().trt_k_restrict(self.h, ctypes.byref(ls), ctypes.byref(ld)))
         return kd
 
-    def k_grey_newton(self, dt, Tstar, Told, grey, sig_prev=None, T_prev=None):
+    def k_grey_newton(self, dt, Tstar, Told, grey, sig_prev=None, T_prev=None, secant_cut=1e-7):
         t = self.torch
         lv, keep = self._level(grey, 1)
         Ts, To = self._t(Tstar), self._t(Told)
@@ -390,7 +390,7 @@ class Solver:
         rc = lib().trt_k_grey_newton(self.h, float(dt), Ts.data_ptr(), To.data_ptr(),
                                      sp.data_ptr() if have else None,
                                      tp.data_ptr() if have else None, int(have),
-                                     ctypes.byref(lv), T.data_ptr())
+                                     float(secant_cut), ctypes.byref(lv), T.data_ptr())
         self._check(rc, allow=(TRT_ENUMERIC,))
         return rc, T, {k: keep[k] for k in ("E", "F", "Eb0", "EbX")}
 

@@ -406,8 +406,12 @@ def test_restrict_zero_weights(trt, orc, n_from, n_to, fine):
     assert np.array_equal(got["Esum"][0, 30:36], np.zeros(6))
 
 
-@pytest.mark.parametrize("nx,have_prev", [(1, 0), (30, 1), (500, 0), (1000, 1)])
-def test_grey_newton_parity(trt, orc, nx, have_prev):
+@pytest.mark.parametrize("nx,have_prev,cut", [(1, 0, 1e-7), (30, 1, 1e-7), (500, 0, 1e-7),
+                                              (1000, 1, 1e-7), (1000, 1, 0.0)])
+def test_grey_newton_parity(trt, orc, nx, have_prev, cut):
+    """The grey Newton step against the oracle's, with and without a secant; the previous
+    temperatures put cells on both sides of the cross-grid cut-off and some exactly at T*
+    (no secant at any cut-off)."""
     r = W.rng(5000 + nx)
     h = W.random_h(r, nx)
     lv = random_level(r, 1, nx)
@@ -418,8 +422,10 @@ def test_grey_newton_parity(trt, orc, nx, have_prev):
     To = Ts * r.uniform(0.8, 1.0, nx)
     sp = lv["sig"][0] * r.uniform(0.5, 1.5, nx)
     tp = Ts * r.uniform(0.7, 1.3, nx)
+    tp[1::4] = Ts[1::4] * (1 + r.uniform(-3e-8, 3e-8, tp[1::4].size))   # below the cut-off
+    tp[2::8] = Ts[2::8]                                                 # no change at all
     rc, T, sol = s.k_grey_newton(dt, Ts, To, lv, sp if have_prev else None,
-                                 tp if have_prev else None)
+                                 tp if have_prev else None, secant_cut=cut)
     edges = W.group_edges(17, 1e-5, 1e2)
     Q = 2 * lv["emis"][0]
     dQ = np.array([orc.emission_deriv(edges, t) for t in Ts])
@@ -427,7 +433,7 @@ def test_grey_newton_parity(trt, orc, nx, have_prev):
         h, dt, W.CV_FC, Ts, To, Q, dQ, lv["Esum"][0], lv["sig"][0], sp, tp, have_prev,
         lv["Eold"][0], lv["phi"][0], lv["sigR"][0], lv["etaR"][0], lv["etaL"][0], lv["Fold"][0],
         lv["phib0"][0], lv["phibX"][0], lv["C0"][0], lv["CX"][0], lv["Ein0"][0], lv["Fin0"][0],
-        lv["EinX"][0], lv["FinX"][0])
+        lv["EinX"][0], lv["FinX"][0], secant_cut=cut)
     assert (rc != 0) == (bad != 0)
     if not bad:
         assert rel(T.cpu().numpy(), oT) < 1e-11
