@@ -241,6 +241,11 @@ __device__ void sweep_body(const SweepArgs &a, int dtile, int gt)
                 const size_t o = ((size_t)(dtile * 2 + 0) * G + gg) * nx + c0 + cc;
                 part[o] = s0.s;
                 part[o + (size_t)G * nx] = s2.s;
+                if (sizeof(R) == 4) {   // FP32: the low parts (-c) after every tile's planes
+                    const size_t lo_off = (size_t)(2 * a.N / D) * 2 * G * nx;
+                    part[lo_off + o] = -s0.c;
+                    part[lo_off + o + (size_t)G * nx] = -s2.c;
+                }
             }
         }
     }
@@ -290,35 +295,46 @@ __device__ void finalize_body(const FinalizeArgs &x, int bx)
         const long idx = (long)(bx - nb) * blockDim.x + threadIdx.x;
         const long n = (long)G * nx;
         if (idx < n) {
-            // FP32: the partials of up to 8 direction tiles are loaded before any is added,
-            // so each thread has 16 loads in flight instead of one dependent pair per tile
-            // (the FP64 form is bound by its FP64 additions and keeps the plain loop)
-            Acc<R> A0, A2;
             if (sizeof(R) == 8) {
+                Acc<R> A0, A2;
                 for (int t = 0; t < ntile; ++t) {
                     A0.add(part[(size_t)(t * 2 + 0) * n + idx]);
                     A2.add(part[(size_t)(t * 2 + 1) * n + idx]);
                 }
-            } else for (int t0 = 0; t0 < ntile; t0 += 8) {
-                R v0[8], v2[8];
+                // a division, not a reciprocal: in cold cells both angular sums are
+                // subnormal, where 1/A0 overflows while A2/A0 stays the ratio
+                f[idx] = (A0.s != (R)0) ? (double)(A2.s / A0.s) : 1.0 / 3.0;
+            } else {
+                // FP32: the tiles' (high, low) pairs summed as unevaluated FP32 sums (an
+                // exact two-sum per high part, the low parts added plainly), then the ratio
+                // of the two moments in FP64, which leaves f one FP64 rounding instead of
+                // the FP32 roundings of the partials and of an FP32 division
+                const size_t lo = (size_t)ntile * 2 * n;
+                float S0 = 0.f, E0 = 0.f, S2 = 0.f, E2 = 0.f;
+                for (int t0 = 0; t0 < ntile; t0 += 8) {
+                    float h0[8], l0[8], h2[8], l2[8];   // loads in flight before the adds
 #pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    if (t0 + j < ntile) {
-                        v0[j] = part[(size_t)((t0 + j) * 2 + 0) * n + idx];
-                        v2[j] = part[(size_t)((t0 + j) * 2 + 1) * n + idx];
+                    for (int j = 0; j < 8; ++j) {
+                        if (t0 + j < ntile) {
+                            const size_t o = (size_t)((t0 + j) * 2) * n + idx;
+                            h0[j] = part[o];
+                            h2[j] = part[o + n];
+                            l0[j] = part[lo + o];
+                            l2[j] = part[lo + o + n];
+                        }
+                    }
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        if (t0 + j < ntile) {
+                            two_sum_acc(S0, E0, h0[j], l0[j]);
+                            two_sum_acc(S2, E2, h2[j], l2[j]);
+                        }
                     }
                 }
-#pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    if (t0 + j < ntile) {
-                        A0.add(v0[j]);
-                        A2.add(v2[j]);
-                    }
-                }
+                const double a0 = (double)S0 + (double)E0, a2 = (double)S2 + (double)E2;
+                // FP32 partials are normal or subnormal floats: their FP64 sums are normal
+                f[idx] = (a0 != 0.0) ? a2 * rcp64(a0) : 1.0 / 3.0;
             }
-            // a division, not a reciprocal: in cold cells both angular sums are subnormal,
-            // where 1/A0 overflows while A2/A0 stays the ratio
-            f[idx] = (A0.s != (R)0) ? (double)(A2.s / A0.s) : 1.0 / 3.0;
         }
         return;
     }

@@ -22,6 +22,17 @@ struct Acc {   // per-tile angular sum: plain in FP64, compensated (Kahan) in FP
     }
 };
 
+// (S, E) += hi + lo for unevaluated FP32 sums S + E: hi enters by an exact two-sum (Knuth),
+// its rounding error and lo go to E
+__device__ inline void two_sum_acc(float &S, float &E, float hi, float lo)
+{
+    const float s = __fadd_rn(S, hi);
+    const float bb = __fsub_rn(s, S);
+    const float err = __fadd_rn(__fsub_rn(S, __fsub_rn(s, bb)), __fsub_rn(hi, bb));
+    S = s;
+    E = __fadd_rn(E, __fadd_rn(err, lo));
+}
+
 // cp.async (global -> shared, completion per issuing thread): the next strip's data is
 // in flight while the current strip is swept.
 template <int B>

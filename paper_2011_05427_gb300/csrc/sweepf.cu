@@ -116,6 +116,7 @@ __device__ __forceinline__ void sweepf_run(const SweepArgs &a, int dtile, int gt
     const float *__restrict__ emis = reinterpret_cast<const float *>(a.emis);
     const float *__restrict__ kap32 = a.kap32;
     float *part = reinterpret_cast<float *>(a.part);
+    const size_t lo_off = (size_t)(2 * a.N / D) * 2 * G * nx;   // low parts of the partials
     const unsigned ds = 2u * (unsigned)ldG;   // one cell of one direction, in floats
     const size_t mrow = (size_t)m * nx * ds;
     // copy source of this lane: row rr (cell rr / 2, corner rr % 2), chunk ch
@@ -206,9 +207,14 @@ __device__ __forceinline__ void sweepf_run(const SweepArgs &a, int dtile, int gt
                         s0.add(__fmul_rn(wt[d], v));
                         s2.add(__fmul_rn(wm[d], v));
                     }
+                    // the compensated sums as (high, low) pairs: the high parts in the
+                    // tile's plane, the low parts (-c) in a second set of planes after
+                    // every tile's (the finalize adds them in FP64)
                     const size_t o = ((size_t)(dtile * 2 + 0) * G + gg) * nx + c0 + cc;
                     part[o] = s0.s;
                     part[o + (size_t)G * nx] = s2.s;
+                    part[lo_off + o] = -s0.c;
+                    part[lo_off + o + (size_t)G * nx] = -s2.c;
                 }
             }
         }
@@ -223,19 +229,28 @@ __device__ __forceinline__ void sweepf_run(const SweepArgs &a, int dtile, int gt
         float pL[GPL], pR[GPL], v[GPL];
 #pragma unroll
         for (int j = 0; j < GPL; ++j) {
-            const float aa = __fadd_rn(b, V::th(f, j));
+            const float th = V::th(f, j);
+            const float aa = __fadd_rn(b, th);
             const float x = rcp_nr(__fmaf_rn(aa, aa, bb));
             const float t = __fmul_rn(aa, x), s = __fmul_rn(b, x);
             const float kL = __fmaf_rn(kap, V::get(IL, j), V::q(f, j));
             const float kR = __fmaf_rn(kap, V::get(IR, j), V::q(f, j));
+            // the outflow is tau psi_in + q with tau = |mu| s = 1 - eps, eps = th (th + |mu|)
+            // / det.  In a thin cell (eps < 1/2) it is formed as psi_in + (q - eps psi_in):
+            // tau's rounding would otherwise repeat in every cell of a streaming path
+            // (coherently where the cells are alike); in a thick cell as s r + t k, whose
+            // relative error stays small when tau is.
+            const float eps = __fmul_rn(__fmul_rn(th, __fadd_rn(th, am)), x);
             if (POS) {
                 const float rL = __fmaf_rn(am, psi[j], kL);
-                pR[j] = __fmaf_rn(s, rL, __fmul_rn(t, kR));
+                const float inc = __fadd_rn(psi[j], __fmaf_rn(-eps, psi[j], __fmaf_rn(s, kL, __fmul_rn(t, kR))));
+                pR[j] = eps < 0.5f ? inc : __fmaf_rn(s, rL, __fmul_rn(t, kR));
                 pL[j] = __fmaf_rn(t, rL, -__fmul_rn(s, kR));
                 psi[j] = pR[j];
             } else {
                 const float rR = __fmaf_rn(am, psi[j], kR);
-                pL[j] = __fmaf_rn(s, rR, __fmul_rn(t, kL));
+                const float inc = __fadd_rn(psi[j], __fmaf_rn(-eps, psi[j], __fmaf_rn(s, kR, __fmul_rn(t, kL))));
+                pL[j] = eps < 0.5f ? inc : __fmaf_rn(s, rR, __fmul_rn(t, kL));
                 pR[j] = __fmaf_rn(t, rR, -__fmul_rn(s, kL));
                 psi[j] = pL[j];
             }

@@ -139,3 +139,27 @@ def test_batch_sweep_shapes(trt, D, shape):
     for s in singles:
         s.close()
     B.close()
+
+
+@pytest.mark.parametrize("cycle,lmax", [("V", 4), ("W", 2)])
+def test_batch_slabs_match_oracle(trt, orc, cycle, lmax):
+    """Three slabs of the heterogeneous batch (37 cells, 8 directions per sign, 64 groups on
+    4 grids; 90 cells, 16, 64 groups on 3 grids, opacity x1.7; 55 cells, 4, 17 groups on 2)
+    stepped together, each against the oracle's Algorithm 3 on the same slab: converged
+    steps (eps 1e-8) with the oracle's counters, T and E_g to 1e-10."""
+    slabs = [mixed_slabs()[k] for k in (0, 1, 3)]
+    B = trt.Batch(slabs)
+    oracles = [orc.Problem(c.h(), c.N, c.edges(), c.levels, c.opac_scale, c.cv, c.T0, c.T_left,
+                           c.T_right) for c in slabs]
+    for step in range(2):
+        sb = B.step(1e-3, cycle, lmax, 1e-8)
+        for k, o in enumerate(oracles):
+            so, c = o.step(1e-3, cycle, lmax, 1e-8)
+            assert so == 0 and sb[k]["status"] == 0
+            assert (sb[k]["n_ti"], sb[k]["n_c"], sb[k]["n_lo"]) == \
+                (c["n_ti"], c["n_c"], c["n_lo"]), (step, k)
+            g, r = B.slab(k).moments(), o.state()
+            eT = np.max(np.abs(g["T"] - r["T"]) / r["T"])
+            eE = np.max(np.abs(g["Eg"] - r["Eg"]) / r["Eg"].sum(0)[None, :])
+            assert eT < 1e-10 and eE < 1e-10, (step, k, eT, eE)
+    B.close()

@@ -97,7 +97,10 @@ def test_mlp_fused_forward(env, rows):
 
 def test_mlp_gradient_vs_oracle(env):
     """Gradients of the tensor-core backward pass against the oracle's backward pass with
-    BF16 rounding at the same points (norm-wise per parameter block)."""
+    BF16 rounding at the same points, element by element: every element within 5e-4 of its
+    parameter block's largest gradient (measured up to 7.7e-5: FP32 accumulation order,
+    and BF16 roundings of stored activations that flip with it), and the block norms
+    within 2e-3."""
     torch, mlp = env
     r = np.random.default_rng(31)
     p = OM.init_params(30) + OM.pack({"b1": r.normal(0, 0.1, 256), "b2": r.normal(0, 0.1, 256),
@@ -115,6 +118,11 @@ def test_mlp_gradient_vs_oracle(env):
                     ("b3", 256), ("w4", 256), ("b4", 1)):
         o = OM.OFF[name]
         a, b = g[o:o + n], gr[o:o + n]
+        scale = np.abs(b).max() + 1e-30
+        elem = np.abs(a - b) / scale
+        print(f"{name}: max element error {elem.max():.2e}, 99th percentile "
+              f"{np.quantile(elem, 0.99):.2e} of the block's largest gradient")
+        assert elem.max() <= 5e-4, name
         assert np.linalg.norm(a - b) <= 2e-3 * np.linalg.norm(b) + 1e-12, name
     assert mlp.MLP.status() == 0
 

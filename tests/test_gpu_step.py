@@ -143,7 +143,7 @@ def test_fc_1024_full_size_step_fp32_sweeps(trt, orc):
     so, c = o.step(cfg.dt, "W", 1, -1.0, max_outer=2)
     assert st["status"] == 0 and so == 0
     eT, eE, _ = errors(s.moments(), o.state())
-    assert eT < MIXED_TOL["sweep32"] and eE < MIXED_TOL["sweep32"], (eT, eE)
+    assert eT < MIXED_TOL["sweep32"][0] and eE < MIXED_TOL["sweep32"][1], (eT, eE)
 
 
 def test_w_cycle_cold_cells_many_cells(trt, orc):
@@ -188,13 +188,17 @@ MIXED_CASES = [
 ]
 
 
-# Measured error bounds against the FP64 oracle after 3 fixed-iteration steps.  FP32
-# sweeps alone stay below 1e-6 (observed up to 5.7e-7 in T).  The FP32 group LOQD solves
-# are refined by one FP64-residual step: without it each solve carried the system's
-# condition number times the FP32 unit round-off (3.6e-6 .. 7.3e-6 in T); with it they
-# are FP64 solves to within the refinement's square of that, so FP32 LO alone stays at
-# the FP64 path's agreement and the mixed form at the FP32 sweeps'.
-MIXED_TOL = {"sweep32": 1e-6, "lo32": 1e-9, "mixed": 1e-6}
+# Error bounds against the FP64 oracle after 3 fixed-iteration steps, (T, energy-weighted
+# E_g).  FP32 sweeps: measured up to 5.0e-8 in T and 1.5e-7 in E_g (the QD factors within
+# about one FP32 ulp).  The FP32 group LOQD solves are refined by FP64-residual steps:
+# without it each solve carried the system's condition number times the FP32 unit
+# round-off (3.6e-6 .. 7.3e-6 in T); with it they are FP64 solves to within the
+# refinement's square of that, so FP32 LO alone stays at the FP64 path's agreement and the
+# mixed form at the FP32 sweeps'.
+MIXED_TOL = {"sweep32": (1e-7, 2e-7), "lo32": (1e-9, 1e-9), "mixed": (1e-7, 2e-7)}
+# every FP32 sweep shape, the strip sweep of tile heights without a lean kernel included
+# (it forms the outflow as s r + t k in every cell): T and E_g after fixed-iteration steps
+SHAPE_TOL = 1e-6
 
 
 @pytest.mark.parametrize("prec", ["sweep32", "lo32", "mixed"])
@@ -210,8 +214,37 @@ def test_mixed_precision_vs_fp64_oracle(trt, orc, name, cfg, cycle, lmax, prec):
         eT, eE, _ = errors(s.moments(), o.state())
         worst = (max(worst[0], eT), max(worst[1], eE))
     print(f"{name} {prec}: vs FP64 oracle: T {worst[0]:.2e}, E_g (energy-weighted) {worst[1]:.2e}")
-    tol = MIXED_TOL[prec]
-    assert worst[0] < tol and worst[1] < tol
+    tol_T, tol_E = MIXED_TOL[prec]
+    assert worst[0] < tol_T and worst[1] < tol_E
+
+
+# The precision form's bounds on converged steps (eps 1e-8) against the FP64 oracle stepping
+# the same slab: T within 1e-7; the energy-weighted E_g within 2e-7.  The E_g bound is the
+# limit of FP32-stored intensities: the QD factors come out within about one FP32 ulp
+# (6e-8), and where one group holds nearly all of a cold cell's energy (streaming
+# radiation ahead of the wave) E_g inherits that error (measured up to 1.1e-7).
+CONVERGED_MIXED_TOL_T = 1e-7
+CONVERGED_MIXED_TOL_E = 2e-7
+
+
+@pytest.mark.parametrize("prec", ["sweep32", "mixed"])
+@pytest.mark.parametrize("name,cfg,cycle,lmax", MIXED_CASES, ids=[c[0] for c in MIXED_CASES])
+def test_mixed_precision_converged_vs_fp64_oracle(trt, orc, name, cfg, cycle, lmax, prec):
+    """FP32 sweeps (and FP32 group LOQD eliminations in `mixed`) with FP64 grey + MEB,
+    five converged steps against the FP64 oracle's converged steps: T within 1e-7 and the
+    energy-weighted E_g within 2e-7 every step; the pure relative E_g error on groups
+    holding more than 1e-20 of their cell's energy is reported."""
+    s, o = pair(trt, orc, cfg, precision=prec)
+    worst = [0.0, 0.0, 0.0]
+    for step in range(5):
+        st = s.step(cfg.dt, cycle, lmax, 1e-8)
+        so, _ = o.step(cfg.dt, cycle, lmax, 1e-8)
+        assert st["status"] == 0 and so == 0
+        e = errors(s.moments(), o.state())
+        worst = [max(a, b) for a, b in zip(worst, e)]
+        assert e[0] < CONVERGED_MIXED_TOL_T and e[1] < CONVERGED_MIXED_TOL_E, (step, e)
+    print(f"{name} {prec} converged: vs FP64 oracle: T {worst[0]:.2e}, E_g energy-weighted "
+          f"{worst[1]:.2e}, pure relative {worst[2]:.2e}")
 
 
 @pytest.mark.parametrize("shape,D", [(0, 4), (1, 4), (2, 4), (3, 4), (4, 4), (5, 4), (6, 4),
@@ -231,7 +264,7 @@ def test_fp32_sweep_shapes_in_steps(trt, orc, shape, D):
         o.step(cfg.dt, "W", 2, -1.0, max_outer=3)
         eT, eE, _ = errors(s.moments(), o.state())
         worst = max(worst, eT, eE)
-    assert worst < MIXED_TOL["sweep32"], worst
+    assert worst < SHAPE_TOL, worst
 
 
 
@@ -250,7 +283,7 @@ def test_fp32_lean_sweep_sixteen_directions(trt, orc, shape):
         o.step(cfg.dt, "W", 2, -1.0, max_outer=3)
         eT, eE, _ = errors(s.moments(), o.state())
         worst = max(worst, eT, eE)
-    assert worst < MIXED_TOL["sweep32"], worst
+    assert worst < SHAPE_TOL, worst
 
 
 @pytest.mark.parametrize("D,shape", [(4, 0), (8, 0), (4, 1), (8, 4)])
