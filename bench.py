@@ -142,10 +142,12 @@ FLOP_PER_UPDATE = 23
 FP64_PEAK_TFLOPS = 1.25
 # FP64 instruction issue of the part: a warp-wide FP64 instruction occupies a sub-partition's
 # FP64 pipe for 64 cycles (measured), so 152 x 4 x 2.07e9 / 64 x 32 lanes = 629e9 thread
-# instructions/s; the FP64 sweep executes 17.6 of them per update (ncu, DFMA 11.0 + DMUL 4.5
-# + DADD 2.1), a mix whose FLOP ceiling is 23 / (2 x 17.6) = 65% of the FMA peak.
+# instructions/s.  FP64 thread instructions per update (ncu, DFMA + DMUL + DADD over the
+# updates of one fc_1024 launch): the strip sweep 17.6 (11.0 + 4.5 + 2.1), the paired sweep
+# 13.5 (9.0 + 3.0 + 1.5: t and s formed once per pair of directions); the FLOP ceiling of
+# a mix is 23 / (2 x instructions) of the FMA peak.
 FP64_INST_PEAK = 152 * 4 * 2.07e9 / 64 * 32
-FP64_INST_PER_UPDATE = 17.6
+FP64_INST_PER_UPDATE = {"strip": 17.6, "pair": 13.5}
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum, one ncu capture of the
 # sweep and its finalize on the fc_1024 workload), valid while the kernel sources hash to
@@ -183,6 +185,9 @@ def _traffic(key, tile):
 def sweep_kernel(fp32, D, shape):
     """The kernels one sweep launches for tile (D, shape) (the library's shape table)."""
     if not fp32:
+        if shape in (3, 4):   # paired sweep: its pre-scaled inputs, the sweep, the finalize
+            S, NS = {3: (8, 2), 4: (4, 2)}[shape]
+            return f"k_prescale64 + k_sweep_pair<{S},{NS}> + k_sweep_finalize<double>"
         S, NS = {0: (8, 2), 1: (16, 2), 2: (8, 3)}[shape]
         return f"k_sweep<double,double,{S},{NS}> + k_sweep_finalize<double>"
     if shape == 6 or D not in (4, 8, 16):   # the strip sweep (tile heights without a lean kernel)
@@ -225,6 +230,7 @@ def sweep_roofline(trt, s, cfg, fp32=False, local=0, reps=20):
                 "peak_source": f"{src} (MEASURED_PEAKS hbm_gbs, copy)",
                 "updates_per_s": upd / (ms * 1e-3)}
     else:
+        kind64 = "pair" if shape in (3, 4) else "strip"
         flops = FLOP_PER_UPDATE * upd
         ach = flops / (ms * 1e-3) / 1e12
         roof = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
@@ -234,8 +240,8 @@ def sweep_roofline(trt, s, cfg, fp32=False, local=0, reps=20):
                 "peak_source": "derived: 152 SMs x 2.07 GHz x 2 FP64 FMA/clk x 2 (nominal "
                                "1.25 TFLOP/s FP64)",
                 "hbm_frac": upd * 32 / (ms * 1e-3) / 1e9 / peaks()[0],
-                "fp64_inst_per_update": FP64_INST_PER_UPDATE,
-                "fp64_inst_frac": FP64_INST_PER_UPDATE * upd / (ms * 1e-3) / FP64_INST_PEAK,
+                "fp64_inst_per_update": FP64_INST_PER_UPDATE[kind64],
+                "fp64_inst_frac": FP64_INST_PER_UPDATE[kind64] * upd / (ms * 1e-3) / FP64_INST_PEAK,
                 "updates_per_s": upd / (ms * 1e-3)}
     if tile:
         roof["tile"] = {"D": tile[0], "S": tile[1], "NS": tile[2], "shape": shape}

@@ -14,7 +14,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libtrt.so")
-SOURCES = ["physics.cu", "sweep.cu", "sweepf.cu", "lo.cu", "api.cu", "noalloc.cu", "mlp.cu", "batch.cu"]
+SOURCES = ["physics.cu", "sweep.cu", "sweepf.cu", "sweep64.cu", "lo.cu", "api.cu", "noalloc.cu", "mlp.cu", "batch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xptxas", "-v",

@@ -93,6 +93,9 @@ void carve(trt_handle *h, Carver &c)
     if (sweep_fp32(p.precision)) {
         h->sig32 = c.take<float>(G * nx);
         h->emis32 = c.take<float>(G * nx + nx);   // then h/(2 c dt) per cell (kap32)
+    } else {   // the paired FP64 sweep's t, s and pre-scaled inputs
+        p.ts64 = c.take<double>((size_t)p.N * nx * 2 * p.ldG);
+        p.tab64 = c.take<double>(2 * nx * (size_t)p.ldG + nx);
     }
     h->part = c.take<double>(std::max(sweep_partial_doubles(p), 4 * nx + 8));
     h->psi_exit = c.take<double>(M * (size_t)p.ldG);

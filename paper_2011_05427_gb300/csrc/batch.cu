@@ -808,7 +808,7 @@ int trt_batch_set_tile(trt_batch *b, int D, int shape)
         if (x->p.N % D || D < cand[0])
             return bfail(b, TRT_EINVAL, "D must divide every slab's N and be >= its smallest tile");
     }
-    if (!sweep_tile_ok(b->precision, D, shape)) return TRT_EINVAL;
+    if (!sweep_tile_ok(b->precision, D, shape, true)) return TRT_EINVAL;
     b->D = D;
     b->shape = shape;
     b->built = false;

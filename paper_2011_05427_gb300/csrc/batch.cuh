@@ -42,6 +42,8 @@ struct SweepArgs {
     double *f, *fb0, *fbX, *C0, *CX;
     const float *kap32;   // h/(2 c dt) per cell in FP32 (with the FP32 inputs), or null
     const float *dir32;   // [M][4] |mu|, |mu|/2, w/2, w mu^2/2 in FP32
+    double *ts;           // paired FP64 sweep: t, s per (|mu|, cell, group), or null
+    double *tab64;        // paired FP64 sweep: its pre-scaled inputs (2 nx ldG + nx), or null
 };
 
 struct FinalizeArgs {

@@ -156,6 +156,9 @@ struct Problem {
     size_t rscratch_doubles;
     // sweep tile: directions per CTA (0 = default) and strip shape index (0 = default)
     int sweep_D = 0, sweep_shape = 0;
+    // scratch of the paired FP64 sweep (FP64 handles; null elsewhere): t, s per (|mu|,
+    // cell, group) [N][nx][2][ldG], and the pre-scaled inputs [2][nx][ldG] + [nx]
+    double *ts64 = nullptr, *tab64 = nullptr;
     // per-group polynomial tables in ln T (Chebyshev fits stored as monomials) of
     // sigma_E T^3, sigma_R T^3 and the emission factor ln(1 - e^{-w}) (null: direct
     // integrals)
@@ -184,7 +187,8 @@ cudaError_t launch_prescale32(const Problem &p, double dt, const double *sigE, c
                               float *sig32, float *emis32);
 size_t sweep_partial_doubles(const Problem &p);
 int sweep_shape_count(int precision);
-bool sweep_tile_ok(int precision, int D, int shape);   // a kernel exists and fits (shared memory)
+// a kernel exists and fits (shared memory); `batched`: the batched sweep has one too
+bool sweep_tile_ok(int precision, int D, int shape, bool batched = false);
 void sweep_shape_info(int precision, int shape, int *S, int *NS);
 int sweep_group_tiles(int precision, int shape, int D, int ldG);   // CTAs along the groups
 int sweep_D_candidates(const Problem &p, int *D);   // fills D[0..n), returns n (<= 3)

@@ -407,15 +407,16 @@ __global__ void k_sweep_finalize_b(const int *__restrict__ meta, int N,
 // multiple of 4).  Measured at 500 cells x 64 directions x 1024 groups: lean one group per
 // lane D = 16 (8, 4) 0.100 ms with the finalize, (16, 2) 0.104; two groups per lane
 // D = 8 (8, 4) 0.108 (it wins on some batches); the strip sweep D = 8 (16, 2) 0.209.
-// FP64 (strip sweep): (8, 2) 1.26 ms, (16, 2) 1.37, (8, 3) 1.37.
+// FP64 (strip sweep): (8, 2) 1.26 ms, (16, 2) 1.37, (8, 3) 1.37; the paired sweep of
+// sweep64.cu (single slab, D = 4) as shapes 3 and 4.
 struct Shape {
     int S, NS, V;   // strip cells, strip buffers, kind (1: strip sweep; 5, 6: lean sweep
-                    // with one, two groups per lane)
+                    // with one, two groups per lane; 7: paired FP64 sweep)
 };
 constexpr Shape kShapes32[] = {{8, 4, 5}, {16, 2, 5}, {8, 3, 5}, {8, 2, 5},
                                {8, 2, 6}, {8, 4, 6}, {16, 2, 1}};
 constexpr int kStrip32 = 6;   // the FP32 strip sweep's index (tile heights without a lean kernel)
-constexpr Shape kShapes64[] = {{8, 2, 1}, {16, 2, 1}, {8, 3, 1}};
+constexpr Shape kShapes64[] = {{8, 2, 1}, {16, 2, 1}, {8, 3, 1}, {8, 2, 7}, {4, 2, 7}};
 
 // largest power of two <= cap dividing N: the direction-tile height D_min that the
 // workspace's partial-moment scratch is sized for; D may be D_min or 2 D_min (<= 8)
@@ -463,6 +464,9 @@ cudaError_t dispatch_shape(int shape, const SweepArgs *a, int M, int ldG, int D,
         return launch_shape<float, float, 16, 2>(a, M, ldG, D, meta, N, xs, grid, st);
     }
     if (D > 8) return cudaErrorInvalidConfiguration;
+    if (kShapes64[shape].V == 7)   // paired sweep: single slab only
+        return a ? launch_sweep_pair(kShapes64[shape].S, kShapes64[shape].NS, *a, M, ldG, st)
+                 : cudaErrorInvalidConfiguration;
     switch (shape) {
     case 1: return launch_shape<double, double, 16, 2>(a, M, ldG, D, meta, N, xs, grid, st);
     case 2: return launch_shape<double, double, 8, 3>(a, M, ldG, D, meta, N, xs, grid, st);
@@ -489,10 +493,15 @@ int pick_D(const Problem &p)
     return base_D(p.N, 8);
 }
 
-bool sweep_tile_ok(int precision, int D, int shape)
+bool sweep_tile_ok(int precision, int D, int shape, bool batched)
 {
     if (shape < 0 || shape >= sweep_shape_count(precision) || D < 1) return false;
-    if (!sweep_fp32(precision)) return D <= 8;
+    if (!sweep_fp32(precision)) {
+        if (kShapes64[shape].V == 7)
+            return !batched && D == 4 &&
+                   pair_sweep_smem(kShapes64[shape].S, kShapes64[shape].NS) <= 227 * 1024;
+        return D <= 8;
+    }
     const Shape sh = kShapes32[shape];
     if (sh.V >= 5 && (D == 4 || D == 8 || D == 16)) {
         const size_t sm = sweepf_smem(sh.V, sh.S, sh.NS, D);
@@ -552,6 +561,8 @@ SweepArgs make_sweep_args(const Problem &p, double dt, const void *sigE, const v
     a.f = f; a.fb0 = fb0; a.fbX = fbX; a.C0 = C0; a.CX = CX;
     a.kap32 = nullptr;
     a.dir32 = p.dir32;
+    a.ts = p.ts64;
+    a.tab64 = p.tab64;
     return a;
 }
 

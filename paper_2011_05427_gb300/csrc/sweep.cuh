@@ -53,6 +53,11 @@ __host__ __device__ inline int finalize_bnd_blocks_dev(int G) { return (G + 7) /
 // cudaErrorInvalidConfiguration for a tile height D it has no kernel for (D = 4, 8, 16)
 // shared memory of a lean sweep kernel (0: no such kernel)
 size_t sweepf_smem(int kind, int S, int NS, int D);
+// the paired FP64 sweep of sweep64.cu (single slab, D = 4 directions of each sign per CTA;
+// strip S, buffers NS): k_prescale64 of the raw sigma_E, e_g of `a` into a.tab64, then the
+// sweep; shared memory of a shape (0: no such kernel)
+size_t pair_sweep_smem(int S, int NS);
+cudaError_t launch_sweep_pair(int S, int NS, const SweepArgs &a, int M, int ldG, cudaStream_t st);
 cudaError_t launch_sweepf(int kind, int S, int NS, const SweepArgs *a, int M, int ldG, int D,
                           const int *meta, int N, const SweepArgs *xs, int grid, cudaStream_t st);
 

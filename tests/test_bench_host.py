@@ -31,6 +31,7 @@ def test_unknown_cycle_is_rejected():
 
 def test_sweep_kernel_names_follow_the_shape_table():
     assert bench.sweep_kernel(False, 8, 0).startswith("k_sweep<double,double,8,2>")
+    assert "k_sweep_pair<4,2>" in bench.sweep_kernel(False, 4, 4)
     assert bench.sweep_kernel(True, 8, 6).startswith("k_sweep<float,float,16,2>")
     assert bench.sweep_kernel(True, 2, 0).startswith("k_sweep<float,float,16,2>")
     assert bench.sweep_kernel(True, 16, 0).startswith("k_sweepf<1,8,4,16>")

@@ -129,6 +129,33 @@ def test_sweep_parity(trt, orc, nx, N, G):
         assert rel(a, b) < 1e-11
 
 
+@pytest.mark.parametrize("nx,N,G", [(1, 4, 1), (2, 4, 17), (3, 8, 33), (9, 4, 40), (70, 8, 70),
+                                    (101, 16, 64)])
+@pytest.mark.parametrize("shape", [3, 4])
+def test_paired_fp64_sweep_parity(trt, orc, nx, N, G, shape):
+    """The paired FP64 sweep (the mu > 0 and mu < 0 sweeps of one |mu| meet in the middle,
+    each forming t, s for its first half and using the other's for the second) against
+    the oracle's sweep to round-off: one cell (the mu > 0 half empty), two and three cells,
+    odd cell counts (unequal halves), partial strips and group tiles, several direction
+    tiles; strips of 8 (shape 3) and of 4 (shape 4)."""
+    r, h, sig, em, I_old, TL = sweep_inputs(orc, 2600 + nx + N + G, nx, N, G, thick=True)
+    edges = W.group_edges(G, 1e-5, 1e2) if G >= 3 else np.array([0.0, np.inf])
+    s = solver(trt, nx=nx, N=N, G=G, h=h, edges=edges, TL=TL, TR=0.3)
+    s.set_sweep_tile(4, shape)
+    dt = 1.7e-3
+    mu, w = orc.double_gl(N)
+    Iin0 = orc.group_physics(edges, TL)[0]
+    IinX = orc.group_physics(edges, 0.3)[0]
+    oI, of, ofb0, ofbX, oC0, oCX = orc.sweep(h, mu, w, sig, em, 1.0 / (C * dt), I_old, Iin0, IinX)
+    for call in range(2):   # the second call runs over the first call's scratch
+        In, f, fb0, fbX, C0, CX = (x.cpu().numpy() for x in s.k_sweep(dt, sig, em, I_old))
+        assert pair_err(In, oI) < 1e-12, call
+        assert rel(f, of) < 1e-11
+        for a, b in ((fb0, ofb0), (fbX, ofbX), (C0, oC0), (CX, oCX)):
+            assert rel(a, b) < 1e-11
+    s.close()
+
+
 def test_sweep_sampled_full_size(trt, orc):
     """fc_1024 sizes (500 cells, 64 directions, 1024 groups): the oracle sweeps a sample
     of groups with the same inputs."""
@@ -182,7 +209,8 @@ def test_sweep_subnormal_angular_sums(trt, orc):
 def test_sweep_every_tile(trt, orc, precision):
     """Every candidate sweep tile (directions per CTA x strip length x buffers) gives the
     oracle's sweep: FP64 to round-off, FP32 to FP32 accuracy.  70 cells span several
-    strips of every length with a ragged last strip; 40 groups leave a partial warp."""
+    strips of every length with a ragged last strip (and, in the paired FP64 sweep, two
+    halves of 35 cells); 40 groups leave a partial warp."""
     nx, N, G = 70, 8, 40
     r, h, sig, em, I_old, TL = sweep_inputs(orc, 2500, nx, N, G, thick=True)
     edges = W.group_edges(G, 1e-5, 1e2)
@@ -196,6 +224,10 @@ def test_sweep_every_tile(trt, orc, precision):
     n = 0
     for D in (4, 8):
         for shape in range(s.sweep_shapes()):
+            if precision == "fp64" and shape >= 3 and D != 4:   # the paired sweep: D = 4 only
+                with pytest.raises(trt.TRTError):
+                    s.set_sweep_tile(D, shape)
+                continue
             s.set_sweep_tile(D, shape)
             In, f, fb0, fbX, C0, CX = (x.cpu().numpy() for x in s.k_sweep(dt, sig, em, I_old))
             assert pair_err(In, oI) < tol_I, (D, shape)

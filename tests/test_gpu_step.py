@@ -44,6 +44,23 @@ CASES = [
 ]
 
 
+@pytest.mark.parametrize("shape", [3, 4])
+def test_paired_fp64_sweep_in_converged_steps(trt, orc, shape):
+    """Converged FP64 steps with the paired sweep against the oracle: its counters and T,
+    E_g to 1e-10 (45 cells: halves of 22 and 23; 8 directions per sign; 70 groups)."""
+    cfg = W.scaled(W.fc_small(), 45, 8, 70, levels=[70, 14, 1])
+    s, o = pair(trt, orc, cfg)
+    s.set_sweep_tile(4, shape)
+    for step in range(3):
+        st = s.step(cfg.dt, "W", 2, 1e-8)
+        so, c = o.step(cfg.dt, "W", 2, 1e-8)
+        assert st["status"] == 0 and so == 0
+        assert (st["n_ti"], st["n_c"], st["n_lo"]) == (c["n_ti"], c["n_c"], c["n_lo"]), step
+        eT, eE, _ = errors(s.moments(), o.state())
+        assert eT < 1e-10 and eE < 1e-10, (step, eT, eE)
+    s.close()
+
+
 @pytest.mark.parametrize("name,cfg,cycle,lmax", CASES, ids=[c[0] for c in CASES])
 def test_fixed_iteration_steps_fp64(trt, orc, name, cfg, cycle, lmax):
     """Exactly 3 low-order phases (2 sweeps) of l_max cycles per step, 3 steps."""
