@@ -700,18 +700,68 @@ def oracle_sample(orc, cfg):
     return c["n_ti"] * cfg.updates_per_sweep(), dt
 
 
+def cpu_model():
+    """The host CPU's model string (lscpu, else /proc/cpuinfo), or None."""
+    import subprocess
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                if line.lower().startswith(("model name", "cpu model")):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return None
+
+
+def oracle_config1_ms(orc, steps=10):
+    """ms per converged step of the oracle on the 60-cell, 17-group Fleck-Cummings slab
+    (two-grid cycles, eps 1e-8), over `steps` steps from the cold start."""
+    cfg = W.fc_small()
+    p = orc.Problem(cfg.h(), cfg.N, cfg.edges(), cfg.levels, cfg.opac_scale, cfg.cv, cfg.T0,
+                    cfg.T_left, cfg.T_right)
+    t = time.perf_counter()
+    for _ in range(steps):
+        p.step(cfg.dt, "V", cfg.l_max, cfg.eps)
+    return (time.perf_counter() - t) / steps * 1e3
+
+
 def cpu_baseline(args):
+    """The oracle on the host cores: fc_1024 fixed-iteration samples (updates/s) on one
+    thread and on all cores (its group-parallel loops under OpenMP), and ms per converged
+    step of the 60-cell slab on both."""
     from oracle import orc
     cfg = W.fc_1024(args.cycle)
-    upd = dt = 0.0
-    for _ in range(3):
-        u, t = oracle_sample(orc, cfg)
-        upd += u
-        dt += t
-    return {"value": upd / dt, "unit": "updates/s", "cores": 1, "kind": "oracle",
-            "sample": "oracle (FP64 C, 1 thread): three fixed-iteration steps of fc_1024 "
-                      "from the cold start (each: s=0 phase + 1 sweep + 1 phase, 1 cycle "
-                      f"each), {dt:.1f} s; updates counted over the sweeps"}
+    nproc = os.cpu_count() or 1
+    res = {}
+    for threads in (1, nproc):
+        orc.set_threads(threads)
+        upd = dt = 0.0
+        for _ in range(3 if threads == 1 else 6):
+            u, t = oracle_sample(orc, cfg)
+            upd += u
+            dt += t
+        res[threads] = (upd / dt, dt, oracle_config1_ms(orc))
+    orc.set_threads(1)
+    v1, t1, c1 = res[1]
+    vn, tn, cn = res[nproc]
+    return {"value": vn, "unit": "updates/s", "cores": nproc, "kind": "oracle",
+            "sample": f"oracle (FP64 C, OpenMP over groups, {nproc} threads): six fixed-"
+                      "iteration steps of fc_1024 from the cold start (each: s=0 phase + 1 "
+                      f"sweep + 1 phase, 1 cycle each), {tn:.1f} s; updates counted over the "
+                      "sweeps",
+            "cpu_model": cpu_model(), "nproc": nproc,
+            "single_thread": {"value": v1, "unit": "updates/s", "cores": 1,
+                              "sample": f"three of the same steps, {t1:.1f} s"},
+            "ms_per_step_config1": {"1_thread": c1, f"{nproc}_threads": cn,
+                                    "workload": "fc_small: 60 cells, double S8, 17 groups, "
+                                                "two-grid, eps 1e-8, 10 converged steps"}}
 
 
 def run_reference(args):
@@ -721,6 +771,8 @@ def run_reference(args):
         return
     from oracle import orc
     cfg = W.fc_1024(args.cycle)
+    nproc = os.cpu_count() or 1
+    orc.set_threads(nproc)
     for _ in range(args.warmup):
         oracle_sample(orc, cfg)
     tot_u = 0.0
@@ -736,8 +788,10 @@ def run_reference(args):
            "scaling": "weak", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic (Fleck-Cummings slab, seeded, no dataset)",
            "config": {"workload": "fc_1024 (oracle sample: one fixed-iteration step, s=0 phase "
-                                  "+ 1 sweep + 1 phase)", "parallelism": "1 host thread"},
-           "cpu_baseline": {"kind": "oracle", "cores": 1, "value": v, "unit": "updates/s",
+                                  "+ 1 sweep + 1 phase)",
+                      "parallelism": f"{nproc} host threads (OpenMP over groups)"},
+           "cpu_baseline": {"kind": "oracle", "cores": nproc, "value": v, "unit": "updates/s",
+                            "cpu_model": cpu_model(),
                             "sample": "each step: one fixed-iteration step of fc_1024"},
            "e2e": {"value": v, "unit": "updates/s", "h2d_bytes_per_step": 0,
                    "d2h_bytes_per_step": 0}}

@@ -32,6 +32,21 @@
 
 extern double orc_secant_cut;   /* lo.c: cross-grid secant cut-off (reading) */
 
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+int orc_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
+}
+
 #define MAXLEV 16
 
 struct orc_problem {
@@ -179,7 +194,11 @@ static void physics_all(const orc_problem *p, const double *T, double *sig, doub
                         double *sigR_cell)
 {
     int nx = p->nx, G = p->G;
+    /* cells are independent: with OpenMP each thread takes whole cells */
+#pragma omp parallel
+    {
     double *sB = dalloc(G), *em = dalloc(G), *sR = dalloc(G);
+#pragma omp for schedule(static)
     for (int i = 0; i < nx; ++i) {
         orc_group_physics(G, p->edges, T[i], p->s, NULL, sB, em, sR);
         for (int g = 0; g < G; ++g) {
@@ -189,6 +208,7 @@ static void physics_all(const orc_problem *p, const double *T, double *sig, doub
         }
     }
     free(sB); free(em); free(sR);
+    }
 }
 
 static double inf_norm_diff(int n, const double *a, const double *b)
@@ -236,7 +256,11 @@ static void level_solve(const orc_problem *p, level *L, int ng, double dt)
 {
     int nx = p->nx, nf = nx + 1;
     const double c = orc_c();
+    /* the groups' systems are independent: with OpenMP each thread solves whole groups */
+#pragma omp parallel
+    {
     double *a = dalloc(nx), *s = dalloc(nx);
+#pragma omp for schedule(static)
     for (int q = 0; q < ng; ++q) {
         for (int i = 0; i < nx; ++i) {
             a[i] = c * L->sig[(size_t)q * nx + i];
@@ -250,6 +274,7 @@ static void level_solve(const orc_problem *p, level *L, int ng, double dt)
                      L->E + (size_t)q * nx, L->F + (size_t)q * nf, &L->Eb0[q], &L->EbX[q]);
     }
     free(a); free(s);
+    }
 }
 
 static void restrict_level(const orc_problem *p, const level *A, int nA, const int *map,

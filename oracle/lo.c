@@ -199,6 +199,8 @@ void orc_restrict(int nx, const double *h, int n_from, int n_to, const int *map,
 {
     const double c = orc_c();
     const int nf = nx + 1;
+    /* coarse groups are independent (each sums its own fine groups in order) */
+#pragma omp parallel for schedule(static)
     for (int P = 0; P < n_to; ++P) {
         for (int i = 0; i < nx; ++i) {
             size_t ci = (size_t)P * nx + i;

@@ -7,8 +7,10 @@
  * baseline leg of the benchmark may load it.  It shares no code, header, table or
  * constant generator with the CUDA library, and the CUDA library never calls it.
  *
- * Everything is double precision, single threaded, written in the order and
- * notation of the paper.  Each function names the section / equation it follows.
+ * Everything is double precision, written in the order and
+ * notation of the paper (loops over independent groups or cells may run on several
+ * threads with OpenMP, with the same results).  Each function names the section /
+ * equation it follows.
  * Units: cm, sh (1e-8 s), keV, GJ ("jerk").
  *
  * Array layouts (interface formats, shared with the tests only):
@@ -97,6 +99,11 @@ int orc_grey_newton(int nx, const double *h, double dt, double cv,
  * (default 1e-7: D = 0 unless |T* - T_prev| > cut T*), both readings where the paper is
  * silent; settable so that tests can vary them. */
 void orc_set_readings(double flux_floor, double secant_cut);
+
+/* Threads of the group-parallel loops (sweep over groups, group physics over cells,
+ * group systems, coarse groups of a restriction) when built with OpenMP; n <= 0 leaves the
+ * count.  Returns the count in effect (1 without OpenMP).  Results do not depend on it. */
+int orc_set_threads(int n);
 
 /* ---- cycle schedules (Sec. 4, Fig. 1, Alg. 3) ---- */
 int orc_schedule(int type, int Gamma, int *S);   /* type 0=V, 1=W, 2=F; returns K */

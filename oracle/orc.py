@@ -50,6 +50,8 @@ def lib():
         L.orc_step.restype = ctypes.c_int
         L.orc_grey_newton.restype = ctypes.c_int
         L.orc_schedule.restype = ctypes.c_int
+        L.orc_set_threads.restype = ctypes.c_int
+        L.orc_set_threads.argtypes = [ctypes.c_int]
         L.orc_set_readings.restype = None
         L.orc_set_readings.argtypes = [ctypes.c_double, ctypes.c_double]
         _lib = L
@@ -70,6 +72,11 @@ def _ipt(a):
 
 def _d(x):
     return ctypes.c_double(float(x))
+
+
+def set_threads(n):
+    """Threads of the oracle's group-parallel loops (n <= 0: unchanged); returns the count."""
+    return lib().orc_set_threads(int(n))
 
 
 def set_readings(flux_floor=1e-6, secant_cut=1e-7):

@@ -32,10 +32,15 @@ void orc_sweep(int nx, const double *h, int M, const double *mu, const double *w
                const double *I_old, const double *Iin_left, const double *Iin_right,
                double *I_new, double *f, double *fb0, double *fbX, double *C0, double *CX)
 {
+    /* groups are independent: with OpenMP each thread sweeps whole groups with its own
+     * scratch, in the same order as one thread (the results do not depend on the count) */
+#pragma omp parallel
+    {
     double *A0 = (double *)calloc((size_t)nx, sizeof(double));   /* sum_m w psi_bar      */
     double *A2 = (double *)calloc((size_t)nx, sizeof(double));   /* sum_m w mu^2 psi_bar */
     double *out = (double *)malloc(sizeof(double) * M);         /* outflow face values  */
 
+#pragma omp for schedule(static)
     for (int g = 0; g < G; ++g) {
         for (int i = 0; i < nx; ++i) { A0[i] = 0.0; A2[i] = 0.0; }
         for (int m = 0; m < M; ++m) {
@@ -111,4 +116,5 @@ void orc_sweep(int nx, const double *h, int M, const double *mu, const double *w
     free(A0);
     free(A2);
     free(out);
+    }
 }

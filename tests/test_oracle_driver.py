@@ -224,3 +224,19 @@ def test_converged_state_is_discrete_fixed_point(orc, cycle, levels, lmax):
         assert np.abs(meb / scale).max() < 1e-10
         # the grey energy equals the sum of the fine group energies
         assert np.allclose(s["E"], E.sum(0), rtol=1e-11)
+
+
+def test_oracle_threads_do_not_change_results(orc):
+    """The oracle's group-parallel loops (OpenMP) give the single-thread results bit for
+    bit: a W-cycle step on 4 grids with 1 and with 4 threads."""
+    states = []
+    for threads in (1, 4):
+        orc.set_threads(threads)
+        p, _ = small_problem(orc, levels=(8, 4, 2, 1))
+        for _ in range(2):
+            st, c = p.step(2e-3, "W", 2, 1e-8)
+            assert st == 0
+        states.append(p.state())
+    orc.set_threads(1)
+    for k in ("T", "Eg", "Fg", "I"):
+        assert np.array_equal(states[0][k], states[1][k]), k
