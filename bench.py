@@ -389,7 +389,7 @@ def closure_bench(local, ms_fp64, steps=10):
             "max_rel_T_closure_vs_plain": dT, "steps": steps}
 
 
-def fc4096_bench(local, steps=3):
+def fc4096_bench(local, steps=10):
     """fc_4096 (1000 cells, double S64 = 128 directions, 4096 groups, 7 grids, W-cycle
     l_max 2): FP32 sweeps against the plain FP64 path, step by step from the same start;
     per-step error of the FP32-sweep state against the FP64 state, and the FP32 sweep's
@@ -432,8 +432,38 @@ def fc4096_bench(local, steps=3):
                 "n_ti_per_step_fp64": nti["fp64"] / steps,
                 "n_ti_per_step_sweep32": nti["sweep32"] / steps,
                 "value_sweep32": nti["sweep32"] * upd / (tot["sweep32"] * 1e-3),
-                "error_sweep32_vs_fp64_per_step": errs, "roofline_sweep_fp32": roof})
+                "error_sweep32_vs_fp64_per_step": errs,
+                "max_rel_T_over_steps": max(e["max_rel_T"] for e in errs),
+                "max_rel_Eg_over_steps": max(e["max_rel_Eg"] for e in errs),
+                "roofline_sweep_fp32": roof})
     return out
+
+
+def mixed_vs_oracle(local, precision):
+    """One fixed-iteration fc_1024 step (s = 0 phase, one sweep, one more phase; one V cycle
+    each) of the GPU path in `precision` against the FP64 oracle (on all host cores):
+    T, the energy-weighted E_g, and the pure relative E_g on groups holding more than 1e-20
+    of their cell's energy."""
+    from oracle import orc
+    from paper_2011_05427_gb300 import trt
+    cfg = W.fc_1024("V")
+    orc.set_threads(os.cpu_count() or 1)
+    s = trt.Solver.from_slab(cfg, precision=precision, device=f"cuda:{local}")
+    o = orc.Problem(cfg.h(), cfg.N, cfg.edges(), cfg.levels, cfg.opac_scale, cfg.cv, cfg.T0,
+                    cfg.T_left, cfg.T_right)
+    s.step(cfg.dt, "V", 1, -1.0, max_outer=2)
+    o.step(cfg.dt, "V", 1, -1.0, max_outer=2)
+    orc.set_threads(1)
+    g, r = s.moments(), o.state()
+    s.close()
+    Ec = r["Eg"].sum(0)[None, :]
+    sel = r["Eg"] > 1e-20 * Ec
+    return {"max_rel_T_vs_oracle": float(np.max(np.abs(g["T"] - r["T"]) / r["T"])),
+            "max_rel_Eg_vs_oracle": float(np.max(np.abs(g["Eg"] - r["Eg"]) / Ec)),
+            "max_pure_rel_Eg_vs_oracle": float(np.max(np.abs(g["Eg"] - r["Eg"])[sel] /
+                                                      r["Eg"][sel])),
+            "sample": "one fixed-iteration fc_1024 step from the cold start (s=0 phase, one "
+                      "sweep, one phase; one V cycle each), GPU against the FP64 oracle"}
 
 
 PAPER_TABLES = os.path.join(ROOT, "tests", "golden", "paper_tables.txt")
@@ -614,6 +644,8 @@ def run_ours(args):
                 "note": "FP32 sweeps, FP64 group/grey LOQD + MEB; both converged to eps; "
                         "compared after the same warm-up + timed steps",
                 **counters(st_m, args.steps)}
+            if ws == 1 and args.cpu_baseline:
+                extra["mixed_sweep32"]["vs_oracle"] = mixed_vs_oracle(local, "sweep32")
             t_x, st_x, _, s_x = timed_steps(trt, cfg, "mixed", args.cycle, args.steps,
                                             args.warmup, local, ws)
             c = s_x.moments()
