@@ -60,7 +60,10 @@ struct orc_problem {
     /* state at t^j */
     double *T, *Eg, *Fg, *I, *f, *fb0, *fbX, *C0, *CX;
     double *E, *F;             /* grey energy / flux of the last grey solve */
+    int tr_mode;               /* opacities at (T, T_r = (E/aR)^{1/4}) instead of T_r = T */
 };
+
+void orc_set_tr_mode(orc_problem *p, int on) { if (p) p->tr_mode = on ? 1 : 0; }
 
 static double *dalloc(size_t n) { return (double *)calloc(n, sizeof(double)); }
 
@@ -190,24 +193,31 @@ void orc_set_state(orc_problem *p, const double *T, const double *Eg, const doub
 }
 
 /* group opacities of every cell at temperatures T (Sec. 2) -> [G][nx] */
-static void physics_all(const orc_problem *p, const double *T, double *sig, double *emis,
-                        double *sigR_cell)
+static void physics_all(const orc_problem *p, const double *T, const double *Erad, double *sig,
+                        double *emis, double *sigR_cell)
 {
     int nx = p->nx, G = p->G;
+    const double aR = orc_aR();
     /* cells are independent: with OpenMP each thread takes whole cells */
 #pragma omp parallel
     {
-    double *sB = dalloc(G), *em = dalloc(G), *sR = dalloc(G);
+    double *sB = dalloc(G), *em = dalloc(G), *sR = dalloc(G), *sE = dalloc(G);
 #pragma omp for schedule(static)
     for (int i = 0; i < nx; ++i) {
         orc_group_physics(G, p->edges, T[i], p->s, NULL, sB, em, sR);
+        const double *sEi = sB;   /* sigma_E = sigma_B under T_r = T */
+        if (p->tr_mode && Erad[i] > 0.0 && isfinite(Erad[i])) {
+            /* T_r from the latest grey energy: E = aR T_r^4 */
+            orc_group_opacity_tr(G, p->edges, T[i], pow(Erad[i] / aR, 0.25), p->s, sE, sR);
+            sEi = sE;
+        }
         for (int g = 0; g < G; ++g) {
-            sig[(size_t)g * nx + i] = sB[g];     /* sigma_E = sigma_B (T_r = T) */
+            sig[(size_t)g * nx + i] = sEi[g];
             emis[(size_t)g * nx + i] = em[g];
             sigR_cell[(size_t)g * nx + i] = sR[g];
         }
     }
-    free(sB); free(em); free(sR);
+    free(sB); free(em); free(sR); free(sE);
     }
 }
 
@@ -351,7 +361,7 @@ int orc_step(orc_problem *p, double dt, int cycle_type, int l_max, double eps,
     for (;;) {
         /* ---- transport (outer) iteration ---- */
         if (s_it > 0) {
-            physics_all(p, Tcur, sig, emis, sigRc);
+            physics_all(p, Tcur, Egrey, sig, emis, sigRc);
             orc_sweep(nx, p->h, M, p->mu, p->w, G, sig, emis, 1.0 / (c * dt), I_old,
                       p->Iin0, p->IinX, p->I, p->f, p->fb0, p->fbX, p->C0, p->CX);
             ++n_ti;
@@ -361,7 +371,7 @@ int orc_step(orc_problem *p, double dt, int cycle_type, int l_max, double eps,
         memcpy(Ecyc, Ephase, sizeof(double) * nx);
         for (int l = 0; l < l_max; ++l) {
             /* fine-grid spectrum at T^(l,s) (eq. mloqd-d) */
-            physics_all(p, Tcyc, sig, emis, sigRc);
+            physics_all(p, Tcyc, Egrey, sig, emis, sigRc);
             fine_coeffs(p, &fine, sig, emis, sigRc, Eg_old, Fg_old);
             level_solve(p, &fine, G, dt);
             n_lo += G;
@@ -374,7 +384,7 @@ int orc_step(orc_problem *p, double dt, int cycle_type, int l_max, double eps,
                     int gam = S[k - 1];
                     int ngam = p->ng[gam - 1];
                     level tmp;
-                    physics_all(p, Ttil, sig, emis, sigRc);
+                    physics_all(p, Ttil, Egrey, sig, emis, sigRc);
                     /* fine coefficients at T~, weighted with this cycle's fine solution */
                     level_alloc(&tmp, G, nx);
                     fine_coeffs(p, &tmp, sig, emis, sigRc, Eg_old, Fg_old);

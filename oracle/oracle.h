@@ -42,6 +42,9 @@ double orc_planck_P(double x);                             /* int_0^x t^3/(e^t-1
 double orc_rosseland_D_quad(double xa, double xb);         /* int x^7 e^{2x}/(e^x-1)^3, scaled by e^{xa} */
 void orc_group_physics(int G, const double *edges, double T, double s,
                        double *B, double *sigB, double *emis, double *sigR);
+/* sigma_E,g(T, T_r) and sigma_R,g(T, T_r) (Sec. 2, Sec. 3.1) for a radiation temperature T_r */
+void orc_group_opacity_tr(int G, const double *edges, double T, double Tr, double s,
+                          double *sigE, double *sigR);
 double orc_emission_total(int G, const double *edges, double T, double s);   /* Q = 2 sum_g e_g */
 double orc_emission_deriv(int G, const double *edges, double T, double s);   /* dQ/dT          */
 
@@ -121,6 +124,10 @@ void orc_set_state(orc_problem *p, const double *T, const double *Eg, const doub
                    const double *I, const double *f, const double *fb0, const double *fbX,
                    const double *C0, const double *CX);
 void orc_destroy(orc_problem *p);
+/* T_r option: 0 (default) T_r = T; 1: the opacities sigma_E,g, sigma_R,g are evaluated at
+ * (T, T_r) with T_r = (E/aR)^{1/4}, E the latest grey energy of the step (at the step's
+ * start the sum of the group energies), the emission at T as before. */
+void orc_set_tr_mode(orc_problem *p, int on);
 
 #ifdef __cplusplus
 }

@@ -50,6 +50,8 @@ def lib():
         L.orc_step.restype = ctypes.c_int
         L.orc_grey_newton.restype = ctypes.c_int
         L.orc_schedule.restype = ctypes.c_int
+        L.orc_set_tr_mode.restype = None
+        L.orc_set_tr_mode.argtypes = [ctypes.c_void_p, ctypes.c_int]
         L.orc_set_threads.restype = ctypes.c_int
         L.orc_set_threads.argtypes = [ctypes.c_int]
         L.orc_set_readings.restype = None
@@ -126,6 +128,15 @@ def group_physics(edges, T, s=1.0):
     out = [np.zeros(G) for _ in range(4)]
     lib().orc_group_physics(G, _p(edges), _d(T), _d(s), *[_p(o) for o in out])
     return tuple(out)
+
+
+def group_opacity_tr(edges, T, Tr, s=1.0):
+    """sigma_E,g(T, T_r), sigma_R,g(T, T_r) at one cell (radiation temperature T_r)."""
+    edges = np.ascontiguousarray(edges, dtype=np.float64)
+    G = edges.size - 1
+    sE, sR = np.zeros(G), np.zeros(G)
+    lib().orc_group_opacity_tr(G, _p(edges), _d(T), _d(Tr), _d(s), _p(sE), _p(sR))
+    return sE, sR
 
 
 def physics_field(edges, T, s=1.0):
@@ -277,6 +288,10 @@ class Problem:
         if not self._ptr:
             raise ValueError("orc_create rejected the problem")
         self._ptr = ctypes.c_void_p(self._ptr)
+
+    def set_tr_mode(self, on=True):
+        """Opacities at (T, T_r) with T_r = (E/a_R)^{1/4} from the latest grey energy."""
+        lib().orc_set_tr_mode(self._ptr, int(bool(on)))
 
     def step(self, dt, cycle="V", l_max=4, eps=1e-8, eps_inner=None, max_outer=100):
         if eps_inner is None:

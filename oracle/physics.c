@@ -11,7 +11,8 @@
  * Readings (the paper is silent):
  *   - units cm, sh, keV, GJ; c = 299.792458 cm/sh; aR = 0.01372 GJ cm^-3 keV^-4.
  *   - T_r = T, hence sigma_E,g = sigma_B,g (Algorithm 3 updates the transport
- *     operator from T alone).
+ *     operator from T alone); with the T_r option (orc_set_tr_mode) T_r = (E/aR)^{1/4} from
+ *     the latest grey energy and sigma_E,g, sigma_R,g follow Sec. 2 / Sec. 3.1 at (T, T_r).
  *   - the 2-pi-multiplied Planck function is B(nu,T) = CB nu^3/(e^{nu/T}-1) with
  *     CB = 15 aR c / (2 pi^4), so that sum_g B_g = aR c T^4 / 2.
  */
@@ -218,6 +219,57 @@ void orc_group_physics(int G, const double *edges, double T, double s,
             double Ds = orc_rosseland_D_quad(xa, xb);
             sigR[g] = s * 27.0 * Ns / (T3 * Ds);
         }
+    }
+}
+
+/* ---------------------------------------------------------------------------
+ * Group opacities at a radiation temperature T_r != T (Sec. 2, sigma_E,g(T, T_r); Sec. 3.1,
+ * sigma_R,g(T, T_r)).  With x = nu/T_r and rho = T_r/T (so nu/T = rho x):
+ *   sigma_E = int sigma(nu,T) B(nu,T_r) / int B(nu,T_r)
+ *           = s 27 J_g / (T_r^3 (P(x_{g+1}) - P(x_g))),  J_g = int (1 - e^{-rho x})/(e^x - 1) dx
+ *   sigma_R = int dB/dT|_{T_r} / int (1/sigma(nu,T)) dB/dT|_{T_r}
+ *           = s 27 N_g / (T_r^3 D_g),  N_g as at T (at x = nu/T_r),
+ *             D_g = int x^7 e^x / ((1 - e^{-rho x}) (e^x - 1)^2) dx
+ * J_g and D_g by composite 8-point Gauss-Legendre over [x_g, min(x_{g+1}, x_g + 64)] on
+ * panels of width <= 2 (for rho > 1 graded near x = 0, where 1 - e^{-rho x} changes on the
+ * scale 1/rho; the last panel takes the remainder up to 1.5 widths), both scaled by e^{x_g}
+ * like the T_r = T forms (at rho = 1 the integrands are e^{-x} and x^7 e^{2x}/(e^x - 1)^3).
+ * ------------------------------------------------------------------------- */
+void orc_group_opacity_tr(int G, const double *edges, double T, double Tr, double s,
+                          double *sigE, double *sigR)
+{
+    static double gx[8], gw[8];
+    static int ready = 0;
+    if (!ready) { orc_gauss_legendre(8, gx, gw); ready = 1; }
+    const double rho = Tr / T;
+    const double Tr3 = Tr * Tr * Tr;
+    for (int g = 0; g < G; ++g) {
+        double xa = edges[g] / Tr;
+        double xb = isinf(edges[g + 1]) ? INFINITY : edges[g + 1] / Tr;
+        double hi = xb < xa + 64.0 ? xb : xa + 64.0;
+        double Js = 0.0, Ds = 0.0;
+        /* panels: width 2, except that for rho > 1 the factor 1 - e^{-rho x} varies on the
+         * scale 1/rho near x = 0: there the width is max(1/rho, a/2) at the panel start a */
+        double a = xa;
+        while (a < hi) {
+            double wmax = (rho > 1.0) ? fmin(2.0, fmax(1.0 / rho, 0.5 * a)) : 2.0;
+            double b = (hi - a <= 1.5 * wmax) ? hi : a + wmax;
+            double width = b - a;
+            for (int q = 0; q < 8; ++q) {
+                double x = a + 0.5 * width * (1.0 + gx[q]);
+                double e = exp(xa - x);                 /* e^{xa} e^{-x}   */
+                double om = -expm1(-x);                  /* 1 - e^{-x}      */
+                double orh = -expm1(-rho * x);           /* 1 - e^{-rho x}  */
+                double wq = 0.5 * width * gw[q];
+                Js += wq * e * orh / om;                 /* e^{xa} (1-e^{-rho x})/(e^x-1) */
+                Ds += wq * pow(x, 7) * e / (orh * om * om);
+            }
+            a = b;
+        }
+        double dPs = planck_dP_scaled(xa, xb);
+        sigE[g] = s * 27.0 * Js / (Tr3 * dPs);
+        double Ns = rosseland_edge(xa, xa) - rosseland_edge(xb, xa) + 4.0 * dPs;
+        sigR[g] = s * 27.0 * Ns / (Tr3 * Ds);
     }
 }
 
