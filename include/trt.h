@@ -91,9 +91,14 @@ typedef struct {
     const int *level_groups;
 } trt_groups;
 
-/* Opacity model (Sec. 6): sigma(nu, T) = scale * 27 / nu^3 * (1 - exp(-nu/T)) cm^-1. */
+/* Opacity model (Sec. 6): sigma(nu, T) = scale * 27 / nu^3 * (1 - exp(-nu/T)) cm^-1.
+ * tr_mode = 0: the group opacities at T_r = T (sigma_E,g = sigma_B,g); 1: sigma_E,g(T, T_r)
+ * (Sec. 2) and sigma_R,g(T, T_r) (Sec. 3.1) at the radiation temperature T_r = (E/a_R)^{1/4}
+ * of the latest grey energy E of the step (at its start the sum of the group energies);
+ * single slabs only (trt_create_batch rejects it). */
 typedef struct {
     double scale;
+    int tr_mode;
 } trt_opacity;
 
 /* Options: precision (TRT_FP64 or an OR of TRT_SWEEP_FP32 / TRT_LO_FP32), initial
@@ -316,6 +321,12 @@ int trt_k_restrict(trt_handle *h, const trt_level *src, trt_level *dst);
  * secant_cut T* (a step passes 0 when the previous grey solve was built on the same grid,
  * 1e-7 across grids).  Writes T [nx], g->E, g->F, g->Eb0, g->EbX.
  * Returns TRT_ENUMERIC if a temperature is non-positive or non-finite. */
+/* The opacities at (T, T_r) of a T_r handle (tr_mode = 1): T [nx], radiation energies
+ * Erad [nx] (T_r = (Erad/a_R)^{1/4}; Erad <= 0 or non-finite: T_r = T), outputs as
+ * trt_k_opacity.  TRT_EINVAL on a handle without the T_r option. */
+int trt_k_opacity_tr(trt_handle *h, const double *T, const double *Erad, double *sigE,
+                     double *emis, double *sigR);
+
 int trt_k_grey_newton(trt_handle *h, double dt, const double *Tstar, const double *Told,
                       const double *sig_prev, const double *T_prev, int have_prev,
                       double secant_cut, trt_level *g, double *T);

@@ -266,6 +266,7 @@ int trt_create(const trt_grid *grid, const trt_angles *angles, const trt_groups 
     if (!(cv > 0)) return fail(nullptr, TRT_EINVAL, "cv must be > 0");
     Problem &p = hp->p;
     p.s = opacity->scale;
+    p.tr_mode = opacity->tr_mode ? 1 : 0;
     p.cv = cv;
     Carver dry{nullptr, 0};
     carve(hp.get(), dry);
@@ -454,10 +455,14 @@ int trt_step(trt_handle *h, double dt, const trt_cycle *cyc, trt_stats *stats)
     CK(d2d(h, h->Fg_old, h->Fg, (size_t)G * (nx + 1)));
     CK(launch_group_sum(p, G, h->Eg_old, h->Ephase));
     ++nk;
+    // T_r option: the grey energy the opacities read, until the step's first grey solve
+    // writes it: the sum of the group energies
+    const double *Erad = p.tr_mode ? h->grey.E : nullptr;
+    if (p.tr_mode) CK(d2d(h, h->grey.E, h->Ephase, nx));
     CK(cudaMemsetAsync(h->flags, 0, 8 * sizeof(double), p.stream));
     if (h->mlp_params) {
         // learned warm start: the s = 0 phase takes f_g from the MLP instead of f_g^{j-1}
-        CK(launch_opacity(p, h->T, h->sigE, h->emis, h->sigR));
+        CK(launch_opacity(p, h->T, h->sigE, h->emis, h->sigR, nullptr, nullptr, 0.0, Erad));
         opac_valid = true;
         const int rows = G * nx;
         int rc = trt_mlp_features(nx, G, h->T, h->sigE, h->Eg_old, h->Ephase, h->mlp_x, p.stream);
@@ -473,7 +478,8 @@ int trt_step(trt_handle *h, double dt, const trt_cycle *cyc, trt_stats *stats)
     for (;;) {
         if (s > 0) {
             if (!opac_valid || !sig32_valid) {
-                CK(launch_opacity(p, h->T, h->sigE, h->emis, h->sigR, h->sig32, h->emis32, dt));
+                CK(launch_opacity(p, h->T, h->sigE, h->emis, h->sigR, h->sig32, h->emis32, dt,
+                                  Erad));
                 ++nk;
             }
             opac_valid = true;
@@ -493,7 +499,8 @@ int trt_step(trt_handle *h, double dt, const trt_cycle *cyc, trt_stats *stats)
         bool conv_out = false;
         for (int l = 0; l < cyc->l_max; ++l) {
             if (!opac_valid) {
-                CK(launch_opacity(p, h->T, h->sigE, h->emis, h->sigR));
+                CK(launch_opacity(p, h->T, h->sigE, h->emis, h->sigR, nullptr, nullptr, 0.0,
+                                  Erad));
                 ++nk;
             }
             opac_valid = true;
@@ -505,7 +512,8 @@ int trt_step(trt_handle *h, double dt, const trt_cycle *cyc, trt_stats *stats)
                 Level *src = &fine;
                 if (k > 0) {
                     const int ng = p.levels[S[k - 1] - 1];
-                    CK(launch_opacity(p, h->Ttil, h->sigE, h->emis, h->sigR));
+                    CK(launch_opacity(p, h->Ttil, h->sigE, h->emis, h->sigR, nullptr, nullptr,
+                                      0.0, Erad));
                     opac_valid = false;
                     h->crs.n = ng;
                     CK(launch_restrict(p, fine, h->crs));
@@ -659,6 +667,15 @@ int trt_k_opacity(trt_handle *h, const double *T, double *sigE, double *emis, do
 {
     if (!h || !T || !sigE || !emis || !sigR) return TRT_EINVAL;
     CK(launch_opacity(h->p, T, sigE, emis, sigR));
+    CK(cudaStreamSynchronize(h->p.stream));
+    return TRT_OK;
+}
+
+int trt_k_opacity_tr(trt_handle *h, const double *T, const double *Erad, double *sigE,
+                     double *emis, double *sigR)
+{
+    if (!h || !T || !Erad || !sigE || !emis || !sigR || !h->p.tr_mode) return TRT_EINVAL;
+    CK(launch_opacity(h->p, T, sigE, emis, sigR, nullptr, nullptr, 0.0, Erad));
     CK(cudaStreamSynchronize(h->p.stream));
     return TRT_OK;
 }

@@ -445,6 +445,8 @@ int trt_create_batch(int n, const trt_grid *grids, const trt_angles *angles,
     b->st = reinterpret_cast<cudaStream_t>(opt->stream);
     char *base = reinterpret_cast<char *>(opt->workspace);
     size_t off = 0;
+    for (int s = 0; s < n; ++s)   // the T_r option is single-slab only
+        if (opacities[s].tr_mode) return TRT_EINVAL;
     for (int s = 0; s < n; ++s) {
         trt_options o = *opt;
         const size_t w = trt_workspace_bytes(&grids[s], &angles[s], &groups[s], opt);

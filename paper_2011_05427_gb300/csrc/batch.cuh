@@ -28,6 +28,7 @@ struct OpacityArgs {
     double icdt;
     const double *otab;      // Problem::otab (sigma_E, sigma_R series scaled by 27 s)
     double kE;               // 27 s C_B: the emission factor of the tabulated path
+    const double *Erad;      // radiation energy per cell: sigma_E, sigma_R at T_r, or null
 };
 
 struct SweepArgs {
@@ -125,7 +126,8 @@ inline int lo_mmax_h(int nx)
     return nx < 2 ? 1 : (nx + (std::min(32, nx / 2)) - 1) / std::min(32, nx / 2) + 1;
 }
 OpacityArgs make_opacity_args(const Problem &p, const double *T, double *sigE, double *emis,
-                              double *sigR, float *sig32, float *emis32, double dt);
+                              double *sigR, float *sig32, float *emis32, double dt,
+                              const double *Erad = nullptr);
 int opacity_blocks(const Problem &p);
 int opacity_gx(const Problem &p);   // blocks along the cells (32 cells x 8 groups each)
 SweepArgs make_sweep_args(const Problem &p, double dt, const void *sigE, const void *emis,

@@ -30,6 +30,7 @@ struct SeriesTables {
                              // loop of gauss_group visits the centre once per side
     double g4x[4], g4w[4];   // 4- and 6-point Gauss-Legendre rules on [-1, 1]
     double g6x[6], g6w[6];   // (narrow groups, see group_integrals)
+    double g8x[8], g8w[8];   // 8-point rule of the opacities at a radiation temperature
     double e2[32];           // 2^(j/32), j = 0..31 (texp)
     double einv, eL1, eL2;   // 32/ln2 and ln2/32 = eL1 + eL2 (texp)
 };
@@ -140,6 +141,7 @@ inline bool lo_fp32(int precision) { return (precision & TRT_LO_FP32) != 0; }
 
 struct Problem {
     int nx, N, M, G, ldG, nlev, precision;
+    int tr_mode = 0;   // opacities at (T, T_r) from the latest grey energy (trt_opacity)
     int levels[16];
     double s, cv, T0, Tl, Tr;
     double nu_first, nu_last;
@@ -179,9 +181,11 @@ cudaError_t launch_otab_build(const Problem &p);
 
 // ---- launchers (each enqueues on p.stream; returns cudaError_t of the launch) ----
 // sig32 / emis32 (may be null): the FP32 sweep's inputs (sigma_E + 1/(c dt)) h/2 and h e/2
+// Erad (may be null): per-cell radiation energy; with the T_r option the absorption and
+// Rosseland opacities are taken at T_r = (Erad/a_R)^{1/4}
 cudaError_t launch_opacity(const Problem &p, const double *T, double *sigE, double *emis,
                            double *sigR, float *sig32 = nullptr, float *emis32 = nullptr,
-                           double dt = 0.0);
+                           double dt = 0.0, const double *Erad = nullptr);
 // the FP32 sweep inputs (sig32, emis32 and the kap32 row after it) from FP64 sigma_E, e_g
 cudaError_t launch_prescale32(const Problem &p, double dt, const double *sigE, const double *emis,
                               float *sig32, float *emis32);

@@ -3,7 +3,7 @@
 // Sec. 2 / Sec. 3.1 / Sec. 6 of the paper: with x = nu/T,
 //   B_g     = CB T^4 [P(x_{g+1}) - P(x_g)],           P(x) = int_0^x t^3/(e^t-1) dt
 //   e_g     = int sigma B = s 27 CB T (e^{-x_g} - e^{-x_{g+1}})   (sigma B = 27 s CB e^{-nu/T})
-//   sigma_B = e_g / B_g = sigma_E          (T_r = T)
+//   sigma_B = e_g / B_g = sigma_E          (T_r = T; the T_r option: opacity_tr)
 //   sigma_R = s 27 N_g / (T^3 D_g),  N_g = [-x^4/(e^x-1) + 4 P(x)],  D_g = [int t^7 e^{2t}/(e^t-1)^3]
 // Every per-edge integral is evaluated in closed form: a power series below x = 2 (radius
 // of convergence 2 pi; the coefficients follow from t/(e^t-1) = sum B_n t^n / n!), and
@@ -62,6 +62,7 @@ static SeriesTables build_tables()
     t.g3w[1] *= 0.5;
     gauss_legendre_host(4, t.g4x, t.g4w);
     gauss_legendre_host(6, t.g6x, t.g6w);
+    gauss_legendre_host(8, t.g8x, t.g8w);
     typedef long double LD;
     // c_n = B_n/n!: reciprocal of (e^t-1)/t = sum_k t^k/(k+1)!
     LD c[kSer], fact[kSer + 2];
@@ -366,6 +367,7 @@ __host__ __device__ inline void group_ratios(double T, double ea, double eb, con
 // first.
 struct CellTerms {
     double T[32], iT[32], iT3[32], t[32];
+    double Tr[32], rho[32];   // T_r option: the radiation temperature, T_r / T
     float tf[32];
     int m[32];
 };
@@ -392,9 +394,56 @@ __device__ inline void stage_cells(const OpacityArgs &a, int i0, CellTerms &ct, 
             ct.m[tx] = m;
             ct.t[tx] = t;
             ct.tf[tx] = (float)t;
+            if (a.Erad) {   // T_r = (E/a_R)^{1/4}; T_r = T without a usable energy
+                const double E = a.Erad[i];
+                const double Tr = (E > 0.0 && isfinite(E)) ? sqrt(sqrt(E / kAR)) : Ti;
+                ct.Tr[tx] = Tr;
+                ct.rho[tx] = Tr * iT;
+            }
         }
     }
     __syncthreads();
+}
+
+// sigma_E,g(T, T_r) and sigma_R,g(T, T_r) (Sec. 2, Sec. 3.1) for sigma = 27 s/nu^3 (1 -
+// e^{-nu/T}); with x = nu/T_r and rho = T_r/T:
+//   sigma_E = 27 s J / (T_r^3 [P(x_{g+1}) - P(x_g)]),  J = int (1 - e^{-rho x})/(e^x - 1) dx
+//   sigma_R = 27 s N / (T_r^3 D),  N the T_r = T numerator at x = nu/T_r,
+//             D = int x^7 e^x / ((1 - e^{-rho x}) (e^x - 1)^2) dx
+// J and D by the 8-point Gauss rule on panels over [x_g, min(x_{g+1}, x_g + 64)], width 2 or,
+// for rho > 1, max(1/rho, a/2) from a panel start a below 4 (1 - e^{-rho x} changes on the
+// scale 1/rho near 0), the last panel taking the remainder up to 1.5 widths; both scaled
+// by e^{x_g} like the Planck difference, so cold groups neither underflow nor lose the
+// ratio.  About 40 FP64 operations per node: far dearer than the tabulated T_r = T path.
+__device__ void opacity_tr(double nu_a, double nu_b, bool binf, double Tr, double rho,
+                           double k27, const Mx &mx, double &sg, double &sR)
+{
+    const double iTr = 1.0 / Tr;
+    const double xa = nu_a * iTr;
+    const double xb = binf ? 0.0 : nu_b * iTr;
+    double dPs, Ns, Ds0, om;
+    group_integrals(xa, xb, binf, c_ser, mx, dPs, Ns, Ds0, om);
+    const double hi = binf ? xa + 64.0 : fmin(xb, xa + 64.0);
+    double Js = 0.0, Ds = 0.0, a = xa;
+    while (a < hi) {
+        const double wmax = (rho > 1.0) ? fmin(2.0, fmax(1.0 / rho, 0.5 * a)) : 2.0;
+        const double b = (hi - a <= 1.5 * wmax) ? hi : a + wmax;
+        const double hw = 0.5 * (b - a);
+        for (int q = 0; q < 8; ++q) {
+            const double x = a + hw * (1.0 + c_ser.g8x[q]);
+            const double e = exp(xa - x);
+            const double o1 = -expm1(-x);
+            const double orh = -expm1(-rho * x);
+            const double wq = hw * c_ser.g8w[q];
+            Js += wq * e * orh / o1;
+            const double x2 = x * x, x7 = x2 * x2 * x2 * x;
+            Ds += wq * x7 * e / (orh * o1 * o1);
+        }
+        a = b;
+    }
+    const double Tr3 = Tr * Tr * Tr;
+    sg = k27 * Js / (Tr3 * dPs);
+    sR = k27 * Ns / (Tr3 * Ds);
 }
 
 // cell i0 + threadIdx.x, group g0 + threadIdx.y; outputs [G][nx] (cells contiguous)
@@ -431,6 +480,8 @@ __device__ inline void opacity_body(const OpacityArgs &a, int i0, int g0, const 
         sR = k27 * Ns * iT3 * rcp64(Ds);
         em = k27 * kCB * Ti * mx.ex(-xa) * om;
     }
+    if (a.Erad)   // T_r option: absorption and Rosseland opacities at the radiation temperature
+        opacity_tr(a.edges[g], eb, binf, ct.Tr[tx], ct.rho[tx], 27.0 * a.s, mx, sg, sR);
     a.sigE[idx] = sg;
     a.emis[idx] = em;
     a.sigR[idx] = sR;
@@ -570,9 +621,11 @@ cudaError_t launch_otab_build(const Problem &p)
 }
 
 OpacityArgs make_opacity_args(const Problem &p, const double *T, double *sigE, double *emis,
-                              double *sigR, float *sig32, float *emis32, double dt)
+                              double *sigR, float *sig32, float *emis32, double dt,
+                              const double *Erad)
 {
     OpacityArgs a;
+    a.Erad = p.tr_mode ? Erad : nullptr;
     a.otab = p.otab;
     a.nx = p.nx; a.G = p.G; a.T = T; a.edges = p.edges; a.s = p.s;
     a.sigE = sigE; a.emis = emis; a.sigR = sigR; a.sig32 = sig32; a.emis32 = emis32;
@@ -611,9 +664,10 @@ int opacity_gx(const Problem &p) { return (p.nx + 31) / 32; }
 int opacity_blocks(const Problem &p) { return opacity_gx(p) * ((p.G + 7) / 8); }
 
 cudaError_t launch_opacity(const Problem &p, const double *T, double *sigE, double *emis,
-                           double *sigR, float *sig32, float *emis32, double dt)
+                           double *sigR, float *sig32, float *emis32, double dt,
+                           const double *Erad)
 {
-    const OpacityArgs a = make_opacity_args(p, T, sigE, emis, sigR, sig32, emis32, dt);
+    const OpacityArgs a = make_opacity_args(p, T, sigE, emis, sigR, sig32, emis32, dt, Erad);
     k_opacity<<<dim3(opacity_gx(p), (p.G + 7) / 8), dim3(32, 8), 0, p.stream>>>(a);
     return cudaGetLastError();
 }

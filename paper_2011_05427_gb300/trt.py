@@ -42,7 +42,7 @@ class trt_groups(ctypes.Structure):
 
 
 class trt_opacity(ctypes.Structure):
-    _fields_ = [("scale", ctypes.c_double)]
+    _fields_ = [("scale", ctypes.c_double), ("tr_mode", ctypes.c_int)]
 
 
 class trt_options(ctypes.Structure):
@@ -120,6 +120,8 @@ def lib():
     L.trt_last_error.argtypes = [_vp]
     L.trt_k_opacity.restype = ctypes.c_int
     L.trt_k_opacity.argtypes = [_vp, _vp, _vp, _vp, _vp]
+    L.trt_k_opacity_tr.restype = ctypes.c_int
+    L.trt_k_opacity_tr.argtypes = [_vp] * 6
     L.trt_k_sweep.restype = ctypes.c_int
     L.trt_k_sweep.argtypes = [_vp, ctypes.c_double] + [_vp] * 9
     L.trt_k_lo_solve.restype = ctypes.c_int
@@ -197,7 +199,8 @@ def lib():
 
 EXPORTED = ("trt_workspace_bytes", "trt_create", "trt_step", "trt_moments", "trt_intensity",
             "trt_set_state", "trt_dims", "trt_destroy", "trt_last_error", "trt_k_opacity",
-            "trt_k_sweep", "trt_k_lo_solve", "trt_k_restrict", "trt_k_grey_newton",
+            "trt_k_opacity_tr", "trt_k_sweep", "trt_k_lo_solve", "trt_k_restrict",
+            "trt_k_grey_newton",
             "trt_sweep_time", "trt_autotune", "trt_sweep_shapes", "trt_get_sweep_tile",
             "trt_set_sweep_tile",
             "trt_sweep_noalloc_scratch_bytes", "trt_sweep_noalloc", "trt_sweep_noalloc_error",
@@ -227,7 +230,7 @@ class Solver:
 
     def __init__(self, n_cells, length_cm, N, edges, level_groups, opac_scale=1.0,
                  cv=0.5917 * 0.01372, T0=1e-3, T_left=1.0, T_right=0.0, precision="fp64",
-                 device=None, stream=None, x_edges=None):
+                 device=None, stream=None, x_edges=None, tr_mode=False):
         import torch
         self.torch = torch
         dev = torch.device(device) if device is not None else torch.device("cuda")
@@ -244,7 +247,7 @@ class Solver:
         self.groups = trt_groups(self._edges.size - 1, _np_dp(self._edges), 0.0, 0.0,
                                  self._levels.size,
                                  self._levels.ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
-        self.opacity = trt_opacity(float(opac_scale))
+        self.opacity = trt_opacity(float(opac_scale), int(bool(tr_mode)))
         self.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         torch.cuda.synchronize(self.device)   # initialise torch's context on the device
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
@@ -334,6 +337,15 @@ class Solver:
         T = self._t(T)
         out = [t.empty((self.G, self.nx), dtype=t.float64, device=self.device) for _ in range(3)]
         self._check(lib().trt_k_opacity(self.h, T.data_ptr(), *[o.data_ptr() for o in out]))
+        return tuple(out)
+
+    def k_opacity_tr(self, T, Erad):
+        """sigma_E, e_g, sigma_R at (T, T_r = (Erad/a_R)^{1/4}) (a T_r handle only)."""
+        t = self.torch
+        T, Erad = self._t(T), self._t(Erad)
+        out = [t.empty((self.G, self.nx), dtype=t.float64, device=self.device) for _ in range(3)]
+        self._check(lib().trt_k_opacity_tr(self.h, T.data_ptr(), Erad.data_ptr(),
+                                           *[o.data_ptr() for o in out]))
         return tuple(out)
 
     def k_sweep(self, dt, sigE, emis, I_old):
@@ -475,7 +487,7 @@ class Batch:
     """Many slabs stepped together (trt_create_batch / trt_step_batch).  Every slab's
     results are read through `slab(s)`, a Solver view of the batch's handle for slab s."""
 
-    def __init__(self, slabs, precision="fp64", device=None, T0=None):
+    def __init__(self, slabs, precision="fp64", device=None, T0=None, tr_mode=False):
         import torch
         self.torch = torch
         dev = torch.device(device) if device is not None else torch.device("cuda")
@@ -500,7 +512,7 @@ class Batch:
             angles[k] = trt_angles(int(sl.N))
             groups[k] = trt_groups(e.size - 1, _np_dp(e), 0.0, 0.0, lv.size,
                                    lv.ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
-            opac[k] = trt_opacity(float(sl.opac_scale))
+            opac[k] = trt_opacity(float(sl.opac_scale), int(bool(tr_mode)))
             cv[k] = float(sl.cv)
         torch.cuda.synchronize(dev)
         # a stream of its own: the batch captures its stages as CUDA graphs
