@@ -138,8 +138,22 @@ def job_throughput(units, seconds, ws):
 # two corner values (4 + 4), their sum (1), the two angular moment accumulations (4) = 23.
 FLOP_PER_UPDATE = 23
 # FP64 peak of the part: 152 SMs x 2070 MHz x 2 FP64 FMA per clock per SM x 2 = 1.26e12,
-# the nominal 1.25 TFLOP/s.
+# the nominal 1.25 TFLOP/s; the bench measures it in the run (trt_fp64_peak) and keeps the
+# nominal figure only if the probe fails.
 FP64_PEAK_TFLOPS = 1.25
+_fp64_peak_cache = {}
+
+
+def fp64_peak(trt, local=0):
+    """(peak TFLOP/s, source): the FP64 FMA rate measured in this run, else the nominal."""
+    if local not in _fp64_peak_cache:
+        try:
+            v = max(trt.fp64_peak(device=f"cuda:{local}") for _ in range(3))
+            _fp64_peak_cache[local] = (v, "measured in this run: FP64 FMA chains on every SM "
+                                          "(trt_fp64_peak), best of 3")
+        except Exception as e:   # keep the bench line; say where the peak came from
+            _fp64_peak_cache[local] = (FP64_PEAK_TFLOPS, f"nominal (probe failed: {e})")
+    return _fp64_peak_cache[local]
 # FP64 instruction issue of the part: a warp-wide FP64 instruction occupies a sub-partition's
 # FP64 pipe for 64 cycles (measured), so 152 x 4 x 2.07e9 / 64 x 32 lanes = 629e9 thread
 # instructions/s.  FP64 thread instructions per update (ncu, DFMA + DMUL + DADD over the
@@ -153,10 +167,12 @@ FP64_INST_PER_UPDATE = {"strip": 17.6, "pair": 13.5}
 # sweep and its finalize on the fc_1024 workload), valid while the kernel sources hash to
 # `sha` and the tuned tile (D, shape) is the captured one.
 TRAFFIC = {
-    "sweep_fp64": {"files": ("sweep.cu",), "sha": "beb6628a865ebcb1", "tile": (8, 0),
-                   "bytes": 540350720 + 542587136 + 66101504 + 6400},
-    "sweep_fp32": {"files": ("sweepf.cu", "sweep.cu"), "sha": "618ba8ba6c47c92f", "tile": (16, 0),
-                   "bytes": 269835776 + 225900032 + 16689152 + 0},
+    # k_prescale64 + k_sweep_pair<4,2> + k_sweep_finalize<double>: the t, s scratch and the
+    # 16 partial-moment tiles make it 1.72 x the algorithmic bytes (FP64-bound, not HBM)
+    "sweep_fp64": {"files": ("sweep64.cu", "sweep.cu"), "sha": "e14763fc5f6fec5a", "tile": (4, 4),
+                   "bytes": 8201472 + 785856768 + 881715968 + 131645952 + 573696},
+    "sweep_fp32": {"files": ("sweepf.cu", "sweep.cu"), "sha": "29aacd9f5b8a6ba4", "tile": (16, 0),
+                   "bytes": 270045184 + 242778112 + 33105664 + 0},
 }
 
 
@@ -233,12 +249,13 @@ def sweep_roofline(trt, s, cfg, fp32=False, local=0, reps=20):
         kind64 = "pair" if shape in (3, 4) else "strip"
         flops = FLOP_PER_UPDATE * upd
         ach = flops / (ms * 1e-3) / 1e12
-        roof = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": ach / FP64_PEAK_TFLOPS, "traffic": _traffic("sweep_fp64", (D, shape)),
+        pk, pk_src = fp64_peak(trt, local)
+        roof = {"bound": "alu", "achieved": ach, "peak": pk, "unit": "TFLOP/s",
+                "frac": ach / pk, "traffic": _traffic("sweep_fp64", (D, shape)),
                 "kernel": sweep_kernel(False, D, shape), "ms": ms,
                 "algorithmic_flops": flops,
-                "peak_source": "derived: 152 SMs x 2.07 GHz x 2 FP64 FMA/clk x 2 (nominal "
-                               "1.25 TFLOP/s FP64)",
+                "peak_source": pk_src,
+                "peak_nominal": FP64_PEAK_TFLOPS,
                 "hbm_frac": upd * 32 / (ms * 1e-3) / 1e9 / peaks()[0],
                 "fp64_inst_per_update": FP64_INST_PER_UPDATE[kind64],
                 "fp64_inst_frac": FP64_INST_PER_UPDATE[kind64] * upd / (ms * 1e-3) / FP64_INST_PEAK,

@@ -216,6 +216,12 @@ int trt_set_closure(trt_handle *h, const float *params, const void *w16, void *s
  * library.  x, ex, rc: device arrays of n doubles; enqueued on `stream`. */
 int trt_k_fastmath(int n, const double *x, double *ex, double *rc, void *stream);
 
+/* ---- measurement aid: the device's FP64 FMA rate (the FP64 kernels' roofline) ----
+ * Times one launch of independent FP64 FMA chains (8 per thread, `reps` steps each, 8 CTAs
+ * of 256 threads per SM) with CUDA events on `stream` and writes the rate in TFLOP/s (2
+ * flops per FMA) to *tflops.  No counterpart in the paper.  Synchronises the stream. */
+int trt_fp64_peak(int reps, void *stream, double *tflops);
+
 /* ---- batched slabs (not in the paper: many independent problems at once) ----
  * n slabs, each as trt_create would take it (grids[s], angles[s], groups[s],
  * opacities[s], cv[s]; one trt_options for all: precision, T0, stream, workspace), step

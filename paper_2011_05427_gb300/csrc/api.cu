@@ -720,6 +720,18 @@ int trt_set_closure(trt_handle *h, const float *params, const void *w16, void *s
     return TRT_OK;
 }
 
+int trt_fp64_peak(int reps, void *stream, double *tflops)
+{
+    if (reps < 1 || !tflops) return TRT_EINVAL;
+    float ms = 0.f;
+    long long fmas = 0;
+    if (fp64_probe(reps, reinterpret_cast<cudaStream_t>(stream), &ms, &fmas) != cudaSuccess ||
+        !(ms > 0.f))
+        return TRT_ECUDA;
+    *tflops = 2.0 * (double)fmas / (ms * 1e-3) / 1e12;
+    return TRT_OK;
+}
+
 int trt_k_fastmath(int n, const double *x, double *ex, double *rc, void *stream)
 {
     if (n < 1 || !x || !ex || !rc) return TRT_EINVAL;

@@ -88,6 +88,8 @@ const SeriesTables &host_series();   // host copy (built once)
 void gauss_legendre_host(int n, double *x, double *w);   // nodes / weights on [-1, 1]
 cudaError_t ensure_tables();         // upload the tables to the current device (once)
 cudaError_t launch_fastmath(int n, const double *x, double *ex, double *rc, cudaStream_t st);
+// FP64 FMA rate probe: one timed launch of `reps` FMA steps per chain; FMAs executed in *fmas
+cudaError_t fp64_probe(int reps, cudaStream_t st, float *ms, long long *fmas);
 
 // per-group physics at temperature T on host (inflow spectra, initial condition)
 void host_group_B(int G, const double *edges, double T, double *B);

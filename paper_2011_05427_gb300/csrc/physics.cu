@@ -548,6 +548,47 @@ cudaError_t launch_fastmath(int n, const double *x, double *ex, double *rc, cuda
     return cudaGetLastError();
 }
 
+// FP64 FMA throughput probe: every thread runs 8 independent FMA chains of `reps` steps
+// (x <- x * a + b with |a| < 1, so the values stay finite), the chains summed into out so
+// that none is dead code.  Grid: 8 CTAs of 256 threads per SM, enough warps on every
+// sub-partition to keep its FP64 pipe issuing.
+__global__ void __launch_bounds__(256) k_fp64_probe(int reps, double a, double b, double *out)
+{
+    double x[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) x[k] = 1e-3 * (threadIdx.x + k);
+    for (int r = 0; r < reps; ++r) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) x[k] = fma(x[k], a, b);
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) s += x[k];
+    if (s == 123.456) out[0] = s;   // never true for these inputs; keeps the chains live
+}
+
+cudaError_t fp64_probe(int reps, cudaStream_t st, float *ms, long long *fmas)
+{
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int grid = 8 * sms;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    k_fp64_probe<<<grid, 256, 0, st>>>(reps / 4, 0.999, 1e-4, nullptr);   // warm-up
+    cudaEventRecord(e0, st);
+    k_fp64_probe<<<grid, 256, 0, st>>>(reps, 0.999, 1e-4, nullptr);
+    cudaEventRecord(e1, st);
+    cudaError_t e = cudaEventSynchronize(e1);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    *fmas = (long long)grid * 256 * 8 * reps;
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
 // Tables: one thread per (group, interval) evaluates the three series directly at the
 // interval's kTabNC Chebyshev points in ln T (the two opacity ratios times 27 s, so the
 // evaluation multiplies by T^-3 only), fits their Chebyshev coefficients and stores them

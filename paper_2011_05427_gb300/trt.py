@@ -167,6 +167,8 @@ def lib():
     L.trt_mlp_features.argtypes = [ctypes.c_int] * 2 + [_vp] * 6
     L.trt_mlp_status.restype = ctypes.c_int
     L.trt_mlp_status.argtypes = []
+    L.trt_fp64_peak.restype = ctypes.c_int
+    L.trt_fp64_peak.argtypes = [ctypes.c_int, _vp, ctypes.POINTER(ctypes.c_double)]
     L.trt_k_fastmath.restype = ctypes.c_int
     L.trt_k_fastmath.argtypes = [ctypes.c_int] + [_vp] * 4
     # batched slabs
@@ -199,7 +201,7 @@ def lib():
 
 EXPORTED = ("trt_workspace_bytes", "trt_create", "trt_step", "trt_moments", "trt_intensity",
             "trt_set_state", "trt_dims", "trt_destroy", "trt_last_error", "trt_k_opacity",
-            "trt_k_opacity_tr", "trt_k_sweep", "trt_k_lo_solve", "trt_k_restrict",
+            "trt_k_opacity_tr", "trt_fp64_peak", "trt_k_sweep", "trt_k_lo_solve", "trt_k_restrict",
             "trt_k_grey_newton",
             "trt_sweep_time", "trt_autotune", "trt_sweep_shapes", "trt_get_sweep_tile",
             "trt_set_sweep_tile",
@@ -209,6 +211,20 @@ EXPORTED = ("trt_workspace_bytes", "trt_create", "trt_step", "trt_moments", "trt
             "trt_batch_workspace_bytes", "trt_create_batch", "trt_step_batch",
             "trt_batch_slab", "trt_batch_set_tile", "trt_batch_sweep_time",
             "trt_destroy_batch", "trt_batch_last_error", "trt_k_fastmath")
+
+
+def fp64_peak(reps=4000, device=None):
+    """The device's FP64 FMA rate in TFLOP/s, measured by trt_fp64_peak on the current
+    torch stream of `device`."""
+    import torch
+    dev = torch.device(device) if device is not None else torch.device("cuda")
+    st = torch.cuda.current_stream(dev)
+    out = ctypes.c_double()
+    with torch.cuda.device(dev):
+        rc = lib().trt_fp64_peak(int(reps), ctypes.c_void_p(st.cuda_stream), ctypes.byref(out))
+    if rc != TRT_OK:
+        raise TRTError(rc, "trt_fp64_peak failed")
+    return out.value
 
 
 class TRTError(RuntimeError):

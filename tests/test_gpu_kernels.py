@@ -508,3 +508,11 @@ def test_device_exp_and_reciprocal(trt):
     fin = np.isfinite(rref) & (np.abs(rref) > 1e-300)
     assert np.max(np.abs(rc2[fin] - rref[fin]) / np.spacing(np.abs(rref[fin]))) <= 1.0
     assert np.all(rc2[~fin] == rref[~fin])
+
+
+def test_fp64_peak_probe(trt):
+    """The FP64 FMA rate probe (the FP64 kernels' roofline denominator) reads the part's
+    FP64 rate: GB300's 152 SMs x 2 FP64 FMA per clock x ~2 GHz x 2 flops, ~1.2 TFLOP/s."""
+    v = max(trt.fp64_peak() for _ in range(3))
+    print(f"FP64 FMA rate {v:.3f} TFLOP/s")
+    assert 0.5 < v < 2.0
