@@ -154,12 +154,14 @@ def fp64_peak(trt, local=0):
         except Exception as e:   # keep the bench line; say where the peak came from
             _fp64_peak_cache[local] = (FP64_PEAK_TFLOPS, f"nominal (probe failed: {e})")
     return _fp64_peak_cache[local]
-# FP64 instruction issue of the part: a warp-wide FP64 instruction occupies a sub-partition's
-# FP64 pipe for 64 cycles (measured), so 152 x 4 x 2.07e9 / 64 x 32 lanes = 629e9 thread
-# instructions/s.  FP64 thread instructions per update (ncu, DFMA + DMUL + DADD over the
-# updates of one fc_1024 launch): the strip sweep 17.6 (11.0 + 4.5 + 2.1), the paired sweep
-# 13.5 (9.0 + 3.0 + 1.5: t and s formed once per pair of directions); the FLOP ceiling of
-# a mix is 23 / (2 x instructions) of the FMA peak.
+# FP64 instruction issue of the part: one warp-wide FP64 instruction occupies a
+# sub-partition's FP64 pipe for 64 cycles when one warp runs (measured), 76 when all four
+# sub-partitions are busy, i.e. the FMA rate trt_fp64_peak measures (~1.056 TFLOP/s, 84%
+# of the nominal 1.25); the instruction-rate fraction below divides by that measured rate.
+# FP64 thread instructions per update (ncu, DFMA + DMUL + DADD over the updates of one
+# fc_1024 launch): the strip sweep 17.6 (11.0 + 4.5 + 2.1), the paired sweep 13.5 (9.0 +
+# 3.0 + 1.5: t and s formed once per pair of directions); the FLOP ceiling of a mix is
+# 23 / (2 x instructions) of the FMA rate.
 FP64_INST_PEAK = 152 * 4 * 2.07e9 / 64 * 32
 FP64_INST_PER_UPDATE = {"strip": 17.6, "pair": 13.5}
 
@@ -258,7 +260,8 @@ def sweep_roofline(trt, s, cfg, fp32=False, local=0, reps=20):
                 "peak_nominal": FP64_PEAK_TFLOPS,
                 "hbm_frac": upd * 32 / (ms * 1e-3) / 1e9 / peaks()[0],
                 "fp64_inst_per_update": FP64_INST_PER_UPDATE[kind64],
-                "fp64_inst_frac": FP64_INST_PER_UPDATE[kind64] * upd / (ms * 1e-3) / FP64_INST_PEAK,
+                "fp64_inst_frac": FP64_INST_PER_UPDATE[kind64] * upd / (ms * 1e-3) /
+                                  (pk * 1e12 / 2),
                 "updates_per_s": upd / (ms * 1e-3)}
     if tile:
         roof["tile"] = {"D": tile[0], "S": tile[1], "NS": tile[2], "shape": shape}

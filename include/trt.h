@@ -217,9 +217,10 @@ int trt_set_closure(trt_handle *h, const float *params, const void *w16, void *s
 int trt_k_fastmath(int n, const double *x, double *ex, double *rc, void *stream);
 
 /* ---- measurement aid: the device's FP64 FMA rate (the FP64 kernels' roofline) ----
- * Times one launch of independent FP64 FMA chains (8 per thread, `reps` steps each, 8 CTAs
- * of 256 threads per SM) with CUDA events on `stream` and writes the rate in TFLOP/s (2
- * flops per FMA) to *tflops.  No counterpart in the paper.  Synchronises the stream. */
+ * Times one launch of independent FP64 FMA chains (8 per thread, `reps` steps each, as many
+ * CTAs of 256 threads as every SM holds at once) with CUDA events on `stream` and writes
+ * the rate in TFLOP/s (2 flops per FMA) to *tflops.  No counterpart in the paper.
+ * Synchronises the stream. */
 int trt_fp64_peak(int reps, void *stream, double *tflops);
 
 /* ---- batched slabs (not in the paper: many independent problems at once) ----

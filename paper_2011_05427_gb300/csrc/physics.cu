@@ -9,6 +9,7 @@
 // of convergence 2 pi; the coefficients follow from t/(e^t-1) = sum B_n t^n / n!), and
 // exponentially convergent tails e^{-kx} at and above it, summed with the scale e^{x_g}
 // factored out so that cold cells (x ~ 1e5) neither underflow nor lose the ratio.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include "batch.cuh"
@@ -550,8 +551,8 @@ cudaError_t launch_fastmath(int n, const double *x, double *ex, double *rc, cuda
 
 // FP64 FMA throughput probe: every thread runs 8 independent FMA chains of `reps` steps
 // (x <- x * a + b with |a| < 1, so the values stay finite), the chains summed into out so
-// that none is dead code.  Grid: 8 CTAs of 256 threads per SM, enough warps on every
-// sub-partition to keep its FP64 pipe issuing.
+// that none is dead code.  Grid: as many CTAs of 256 threads as fit on every SM at once
+// (one full wave), enough warps on every sub-partition to keep its FP64 pipe issuing.
 __global__ void __launch_bounds__(256) k_fp64_probe(int reps, double a, double b, double *out)
 {
     double x[8];
@@ -569,10 +570,12 @@ __global__ void __launch_bounds__(256) k_fp64_probe(int reps, double a, double b
 
 cudaError_t fp64_probe(int reps, cudaStream_t st, float *ms, long long *fmas)
 {
-    int dev = 0, sms = 0;
+    int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int grid = 8 * sms;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fp64_probe, 256, 0);
+    if (e != cudaSuccess) return e;
+    const int grid = std::max(1, per_sm) * sms;
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
@@ -580,7 +583,7 @@ cudaError_t fp64_probe(int reps, cudaStream_t st, float *ms, long long *fmas)
     cudaEventRecord(e0, st);
     k_fp64_probe<<<grid, 256, 0, st>>>(reps, 0.999, 1e-4, nullptr);
     cudaEventRecord(e1, st);
-    cudaError_t e = cudaEventSynchronize(e1);
+    e = cudaEventSynchronize(e1);
     if (e == cudaSuccess) e = cudaEventElapsedTime(ms, e0, e1);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
