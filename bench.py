@@ -53,10 +53,19 @@ class Clocks:
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
         try:
             self.p = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={q}",
-                                       "--format=csv,noheader,nounits", "-lms", "100"],
+                                       "--format=csv,noheader,nounits", "-lms", "20"],
                                       stdout=self.file, stderr=subprocess.DEVNULL)
         except Exception:
             self.p = None
+
+    def ready(self, limit_s=2.0):
+        """Wait (at most limit_s) until the sampler has written its first sample, so that
+        the samples that follow fall into the region timed next."""
+        t0 = time.perf_counter()
+        while self.p is not None and time.perf_counter() - t0 < limit_s:
+            if self.p.poll() is not None or os.path.getsize(self.file.name) > 0:
+                return
+            time.sleep(0.01)
 
     def stop(self):
         if self.p is None:
@@ -278,6 +287,8 @@ def timed_steps(trt, cfg, precision, cycle, steps, warmup, local, ws, clocks=Fal
     for _ in range(warmup):
         s.step(cfg.dt, cycle, l_max, cfg.eps)
     clk = Clocks(local) if clocks else None
+    if clk:
+        clk.ready()
     barrier(ws)
     torch.cuda.synchronize()
     ev0 = torch.cuda.Event(enable_timing=True)

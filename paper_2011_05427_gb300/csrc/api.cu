@@ -13,7 +13,9 @@
 // on eps_inner; T~^[0] = T^(l,s); the step ends with T of the last grey solve, E_g / F_g of
 // the last fine solve and I of the last sweep; the secant derivative of the grey opacity
 // restarts at zero with every time step.
-// The host reads 7 doubles of convergence flags once per cycle (one stream sync per cycle).
+// The cycles of a phase are enqueued together: the last grey visit of each cycle tests the
+// inner criterion on the device and gates the cycles after it, and the host reads the
+// convergence flags once per phase (one stream sync per phase).
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -104,7 +106,8 @@ void carve(trt_handle *h, Carver &c)
     int n2 = (p.nlev >= 3) ? p.levels[1] : 1;
     carve_level(c, h->crs, n2, p.nx);
     carve_level(c, h->grey, 1, p.nx);
-    h->flags = c.take<double>(8);
+    h->flags = c.take<double>(10);
+    h->ctl = reinterpret_cast<int *>(h->flags + 8);
 }
 
 bool validate(const trt_grid *grid, const trt_angles *angles, const trt_groups *groups,
@@ -188,6 +191,33 @@ cudaError_t launch_f_from_mlp(const Problem &p, const float *y, double *f)
 {
     const long n = (long)p.G * p.nx;
     k_f_from_mlp<<<(unsigned)((n + 255) / 256), 256, 0, p.stream>>>(n, y, f);
+    return cudaGetLastError();
+}
+
+// Start of a low-order phase of Algorithm 3: the references of its convergence tests
+// (Tphase = Tcyc = T; Ephase, Ecyc = the grey E of the phase before, or Ephase as it is in
+// the step's first phase) and the inner-loop gate opened.
+__global__ void k_phase_start(int nx, int from_grey, const double *__restrict__ T,
+                              const double *__restrict__ Egrey, double *Tphase, double *Tcyc,
+                              double *Ephase, double *Ecyc, int *ctl)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < nx) {
+        const double t = T[i];
+        const double e = from_grey ? Egrey[i] : Ephase[i];
+        Tphase[i] = t;
+        Tcyc[i] = t;
+        Ephase[i] = e;
+        Ecyc[i] = e;
+    }
+    if (i == 0) ctl[0] = 0;
+}
+
+cudaError_t launch_phase_start(const trt_handle *h, bool from_grey)
+{
+    const int nx = h->p.nx;
+    k_phase_start<<<(nx + 255) / 256, 256, 0, h->p.stream>>>(
+        nx, from_grey ? 1 : 0, h->T, h->grey.E, h->Tphase, h->Tcyc, h->Ephase, h->Ecyc, h->ctl);
     return cudaGetLastError();
 }
 
@@ -284,7 +314,7 @@ int trt_create(const trt_grid *grid, const trt_angles *angles, const trt_groups 
     trt_handle *H = hp.get();
     carve(H, c);
     {
-        cudaError_t e = cudaMallocHost(&H->hflags, 8 * sizeof(double));
+        cudaError_t e = cudaMallocHost(&H->hflags, 10 * sizeof(double));
         if (e != cudaSuccess) return fail(nullptr, TRT_ECUDA, cudaGetErrorString(e));
     }
     const int nx = p.nx, G = p.G, M = p.M, N = p.N;
@@ -397,7 +427,7 @@ int trt_create(const trt_grid *grid, const trt_angles *angles, const trt_groups 
     }
     CK(cudaGetLastError());
     CK(launch_otab_build(p));   // opacity tables of this group structure
-    CK(cudaMemsetAsync(H->flags, 0, 8 * sizeof(double), p.stream));
+    CK(cudaMemsetAsync(H->flags, 0, 10 * sizeof(double), p.stream));
     CK(cudaStreamSynchronize(p.stream));
     *out = hp.release();
     return TRT_OK;
@@ -445,10 +475,13 @@ int trt_step(trt_handle *h, double dt, const trt_cycle *cyc, trt_stats *stats)
     const double eps = cyc->eps, eps_in = cyc->eps_inner;
     int n_ti = 0, n_c = 0, n_lo = 0, s = 0, status = TRT_OK, nk = 0;
     bool swept = false, opac_valid = false;
-    bool ttil_is_T = false;   // Ttil holds T (true after every cycle: its last grey wrote both)
-    // the LO phases evaluate opacities without the FP32 copies; the sweep needs them fresh
-    const bool sig32_valid = false;
     int have_prev = 0;
+    // the gate is set only around the cycle launches; cleared on every way out
+    struct GateOff {
+        Problem &p;
+        ~GateOff() { p.gate = nullptr; }
+    } gate_off{p};
+    p.gate = nullptr;
 
     CK(d2d(h, h->Told, h->T, nx));
     CK(d2d(h, h->Eg_old, h->Eg, (size_t)G * nx));
@@ -459,7 +492,7 @@ int trt_step(trt_handle *h, double dt, const trt_cycle *cyc, trt_stats *stats)
     // writes it: the sum of the group energies
     const double *Erad = p.tr_mode ? h->grey.E : nullptr;
     if (p.tr_mode) CK(d2d(h, h->grey.E, h->Ephase, nx));
-    CK(cudaMemsetAsync(h->flags, 0, 8 * sizeof(double), p.stream));
+    CK(cudaMemsetAsync(h->flags, 0, 10 * sizeof(double), p.stream));   // flags and ctl
     if (h->mlp_params) {
         // learned warm start: the s = 0 phase takes f_g from the MLP instead of f_g^{j-1}
         CK(launch_opacity(p, h->T, h->sigE, h->emis, h->sigR, nullptr, nullptr, 0.0, Erad));
@@ -474,14 +507,15 @@ int trt_step(trt_handle *h, double dt, const trt_cycle *cyc, trt_stats *stats)
         nk += 6;
     }
     Level fine = fine_level(h);
+    // LO solves of one cycle: every fine group, the coarse groups of the schedule's grids
+    // and one grey solve per visit
+    int lo_per_cycle = G + K + 1;
+    for (int k = 0; k < K; ++k) lo_per_cycle += p.levels[S[k] - 1];
 
     for (;;) {
         if (s > 0) {
-            if (!opac_valid || !sig32_valid) {
-                CK(launch_opacity(p, h->T, h->sigE, h->emis, h->sigR, h->sig32, h->emis32, dt,
-                                  Erad));
-                ++nk;
-            }
+            CK(launch_opacity(p, h->T, h->sigE, h->emis, h->sigR, h->sig32, h->emis32, dt, Erad));
+            ++nk;
             opac_valid = true;
             if (h->sig32)
                 CK(launch_sweep(p, dt, h->sig32, h->emis32, true, h->I_cur, h->I_alt, h->part,
@@ -493,10 +527,13 @@ int trt_step(trt_handle *h, double dt, const trt_cycle *cyc, trt_stats *stats)
             ++n_ti;
             swept = true;
         }
-        CK(d2d(h, h->Tphase, h->T, nx));
-        CK(d2d(h, h->Tcyc, h->T, nx));
-        CK(d2d(h, h->Ecyc, h->Ephase, nx));
-        bool conv_out = false;
+        // the phase's references (Ephase from the grey E of the phase before) and its gate
+        CK(launch_phase_start(h, s > 0));
+        ++nk;
+        // All l_max cycles are enqueued at once; the cycle kernels return at entry once the
+        // cycle before has met the inner test (or found a bad temperature), as decided by
+        // its last grey visit on the device, so the host waits once per phase.
+        p.gate = h->ctl;
         for (int l = 0; l < cyc->l_max; ++l) {
             if (!opac_valid) {
                 CK(launch_opacity(p, h->T, h->sigE, h->emis, h->sigR, nullptr, nullptr, 0.0,
@@ -506,26 +543,27 @@ int trt_step(trt_handle *h, double dt, const trt_cycle *cyc, trt_stats *stats)
             opac_valid = true;
             CK(launch_lo_solve(p, dt, fine));
             ++nk;
-            n_lo += G;
-            if (!ttil_is_T) CK(d2d(h, h->Ttil, h->T, nx));
+            // grey visit k reads T~^[k] and writes T~^[k+1]: T~^[0] = T, the last visit
+            // writes T, the ones between alternate over Ttil and Tnew
             for (int k = 0; k <= K; ++k) {
+                double *Tst = (k == 0) ? h->T : (((k - 1) & 1) ? h->Tnew : h->Ttil);
+                double *Tout = (k == K) ? h->T : ((k & 1) ? h->Tnew : h->Ttil);
                 Level *src = &fine;
                 if (k > 0) {
                     const int ng = p.levels[S[k - 1] - 1];
-                    CK(launch_opacity(p, h->Ttil, h->sigE, h->emis, h->sigR, nullptr, nullptr,
-                                      0.0, Erad));
+                    CK(launch_opacity(p, Tst, h->sigE, h->emis, h->sigR, nullptr, nullptr, 0.0,
+                                      Erad));
                     opac_valid = false;
                     h->crs.n = ng;
                     CK(launch_restrict(p, fine, h->crs));
                     CK(launch_lo_solve(p, dt, h->crs));
                     nk += 3;
-                    n_lo += ng;
                     src = &h->crs;
                 }
                 CK(launch_restrict(p, *src, h->grey));
                 GreyArgs a{};
-                a.Tstar = h->Ttil; a.Told = h->Told; a.sig_prev = h->sig_prev; a.T_prev = h->T_prev;
-                a.T = h->Tnew; a.sig_prev_out = h->sig_prev; a.T_prev_out = h->T_prev;
+                a.Tstar = Tst; a.Told = h->Told; a.sig_prev = h->sig_prev; a.T_prev = h->T_prev;
+                a.T = Tout; a.sig_prev_out = h->sig_prev; a.T_prev_out = h->T_prev;
                 a.have_prev = have_prev;
                 a.secant_cut = K == 0 ? 0.0 : kSecantCut;   // grey solves on one grid / across grids
                 a.cv = p.cv; a.s = p.s; a.dt = dt;
@@ -533,32 +571,28 @@ int trt_step(trt_handle *h, double dt, const trt_cycle *cyc, trt_stats *stats)
                 a.want_norms = (k == K);
                 a.Tcyc = h->Tcyc; a.Ecyc = h->Ecyc; a.Tphase = h->Tphase; a.Ephase = h->Ephase;
                 a.flags = h->flags;
-                if (k == K) {   // the cycle's last grey visit also does the end-of-cycle copies
-                    a.T_out = h->T; a.Tcyc_out = h->Tcyc; a.Ecyc_out = h->Ecyc;
+                if (k == K) {   // the cycle's last visit: end-of-cycle copies, inner-loop control
+                    a.Tcyc_out = h->Tcyc; a.Ecyc_out = h->Ecyc;
+                    a.ctl = h->ctl; a.eps_in = eps_in; a.fixed = fixed ? 1 : 0;
                 }
                 CK(launch_grey(p, h->grey, a));
                 nk += 2;   // restriction to grey + grey Newton
-                n_lo += 1;
                 have_prev = 1;
-                std::swap(h->Ttil, h->Tnew);
             }
-            ttil_is_T = true;   // the last grey visit wrote T = Ttil (T_out)
             opac_valid = false;
-            CK(cudaMemcpyAsync(h->hflags, h->flags, 8 * sizeof(double), cudaMemcpyDeviceToHost,
-                               p.stream));
-            CK(cudaStreamSynchronize(p.stream));
-            ++n_c;
-            const double *fl = h->hflags;
-            if (fl[0] != 0.0) {
-                status = fail(h, TRT_ENUMERIC, "non-positive or non-finite temperature");
-                goto done;
-            }
-            bool conv_in = fl[1] <= eps_in * fl[2] && fl[3] <= eps_in * fl[4];
-            conv_out = fl[5] <= eps * fl[2] && fl[6] <= eps * fl[4];
-            // Tcyc = T and Ecyc = grey E were written by the last grey visit (Tcyc_out, Ecyc_out)
-            if (!fixed && conv_in) break;
         }
-        CK(d2d(h, h->Ephase, h->grey.E, nx));
+        p.gate = nullptr;
+        CK(cudaMemcpyAsync(h->hflags, h->flags, 10 * sizeof(double), cudaMemcpyDeviceToHost,
+                           p.stream));
+        CK(cudaStreamSynchronize(p.stream));
+        const double *fl = h->hflags;
+        n_c = reinterpret_cast<const int *>(fl + 8)[1];   // cycles run in the step so far
+        if (fl[0] != 0.0) {
+            status = fail(h, TRT_ENUMERIC, "non-positive or non-finite temperature");
+            goto done;
+        }
+        // the outer test on the phase's last cycle (the flags of the cycles that ran)
+        const bool conv_out = fl[5] <= eps * fl[2] && fl[6] <= eps * fl[4];
         ++s;
         if (fixed) {
             if (s >= cyc->max_outer) break;
@@ -571,6 +605,7 @@ int trt_step(trt_handle *h, double dt, const trt_cycle *cyc, trt_stats *stats)
         }
     }
 done:
+    n_lo = n_c * lo_per_cycle;
     CK(d2d(h, h->Eg, h->E1, (size_t)G * nx));
     CK(d2d(h, h->Fg, h->F1, (size_t)G * (nx + 1)));
     if (swept) std::swap(h->I_cur, h->I_alt);

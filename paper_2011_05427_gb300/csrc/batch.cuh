@@ -29,6 +29,7 @@ struct OpacityArgs {
     const double *otab;      // Problem::otab (sigma_E, sigma_R series scaled by 27 s)
     double kE;               // 27 s C_B: the emission factor of the tabulated path
     const double *Erad;      // radiation energy per cell: sigma_E, sigma_R at T_r, or null
+    const int *gate;         // Problem::gate (single-slab kernel only)
 };
 
 struct SweepArgs {
@@ -61,6 +62,7 @@ struct LoCtx {
     const int *lo_slot;
     Level L;
     const double *a_cell, *s_cell;   // grey: explicit absorption / source per cell
+    const int *gate;                 // Problem::gate (single-slab kernels only)
 };
 
 struct RestrictCtx {
@@ -68,6 +70,7 @@ struct RestrictCtx {
     const double *h, *ihf;
     Level S;         // source level (coefficients + solution)
     Level T;         // target level (written)
+    const int *gate;
 };
 
 struct Restrict2Ctx {
@@ -75,6 +78,7 @@ struct Restrict2Ctx {
     const double *h, *ihf;
     Level S, T;
     double *part;   // [n_to][nchunk][kRP][nx+1]
+    const int *gate;
 };
 
 struct GreyCtx {

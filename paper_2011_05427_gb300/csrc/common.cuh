@@ -65,23 +65,35 @@ __host__ __device__ inline double rcp64(double d)
 // j) ln2/32 + r with |r| <= ln2/64 (two-part constant, exact product k L1), e^x =
 // 2^m 2^(j/32) (1 + p(r)), p the degree-6 Taylor polynomial of e^r - 1 (truncation
 // r^7/7! < 2e-18).  tab = 2^(j/32), j = 0..31 (SeriesTables::e2, staged in shared memory).
-// About 11 FP64 operations against ~20 for a library exponential; within about an ulp.
-// Outside (-708, 709) (and for NaN) it calls exp(), from a function that is never inlined
-// (a branch around the library code, not predicated FP64 instructions on every call).
+// Within about an ulp.  GB300 runs FP64 compares and FP64 <-> integer conversions on the
+// FP64 pipe, so the range tests read the high word of x with integer instructions, the
+// rounding of x 32/ln2 adds and subtracts 1.5 2^52 (the integer then sits in the low word
+// of the sum), and 2^m is added to the exponent field of the result (normal for |x| < 704,
+// where |m| <= 1016): about 12 FP64 operations.  x <= -746 gives 0 (e^x is below half the
+// smallest subnormal: the correctly rounded value); anything else outside (-704, 704) and
+// NaN call exp() from a function that is never inlined (a branch around the library code,
+// not predicated FP64 instructions on every call).
 struct ExpConsts {
     double inv, L1, L2;   // 32/ln2; ln2/32 = L1 + L2 with L1 of 31 significant bits
 };
 static __device__ __noinline__ double texp_library(double x) { return exp(x); }
 __device__ inline double texp(double x, const double *tab, const ExpConsts &c)
 {
-    if (!(x > -708.0 && x < 709.0)) return texp_library(x);
-    const double kd = rint(x * c.inv);
-    const int k = (int)kd;
+    const int hi = __double2hiint(x);
+    const unsigned ahi = (unsigned)hi & 0x7fffffffu;
+    if (ahi >= 0x40860000u) {   // |x| >= 704, inf or NaN
+        if (hi < 0 && ahi >= 0x40875000u && ahi < 0x7ff00000u) return 0.0;   // -746 >= x > -inf
+        return texp_library(x);
+    }
+    const double kMagic = 6755399441055744.0;   // 1.5 2^52
+    const double sk = fma(x, c.inv, kMagic);
+    const int k = __double2loint(sk);           // rint(x 32/ln2)
+    const double kd = sk - kMagic;
     const double r = fma(-kd, c.L2, fma(-kd, c.L1, x));
     const double q = r * r * (0.5 + r * (1.0 / 6 + r * (1.0 / 24 + r * (1.0 / 120 + r * (1.0 / 720)))));
     const double t = tab[k & 31];
     const double v = fma(t, r + q, t);
-    return v * __longlong_as_double((long long)((k >> 5) + 1023) << 52);
+    return __longlong_as_double(__double_as_longlong(v) + ((long long)(k >> 5) << 52));
 }
 
 const SeriesTables &host_series();   // host copy (built once)
@@ -130,6 +142,14 @@ struct GreyArgs {
     // norms have read them, T into Tcyc_out and E into Ecyc_out (the same arrays as Tcyc,
     // Ecyc: each cell's thread reads its old value before it writes the new one)
     double *T_out, *Tcyc_out, *Ecyc_out;
+    // inner-loop control of one Algorithm 3 phase on the device (with want_norms), when
+    // non-null: ctl[1] counts the cycles that ran, and ctl[0] (the gate that the cycle's
+    // kernels of the single-slab driver test at entry) is set once the cycle found a bad
+    // temperature or, unless fixed, met the inner test max|T-Tcyc| <= eps_in max|T| and
+    // max|E-Ecyc| <= eps_in max|E| -- the host's test, in the same FP64 operations
+    int *ctl;
+    double eps_in;
+    int fixed;
     // set by make_grey_ctx (host, the same IEEE operations): c_v / dt and 54 s C_B, which
     // every cell would otherwise form with an FP64 division on the grey kernel's one SM;
     // the table and constants of texp for the two exponentials of Q'(T) per cell
@@ -144,6 +164,9 @@ inline bool lo_fp32(int precision) { return (precision & TRT_LO_FP32) != 0; }
 struct Problem {
     int nx, N, M, G, ldG, nlev, precision;
     int tr_mode = 0;   // opacities at (T, T_r) from the latest grey energy (trt_opacity)
+    // single-slab cycle kernels return at entry while *gate != 0 (null: always run); the
+    // step driver points it at the phase's inner-loop control word between launches
+    const int *gate = nullptr;
     int levels[16];
     double s, cv, T0, Tl, Tr;
     double nu_first, nu_last;
@@ -170,12 +193,12 @@ struct Problem {
 };
 
 // opacity tables: ln T in [kTabU0, kTabU0 + kTabNI kTabH), kTabNC coefficients per interval
-constexpr int kTabNI = 49, kTabNC = 12;
-constexpr double kTabU0 = -9.25, kTabH = 0.25;
+constexpr int kTabNI = 98, kTabNC = 9;
+constexpr double kTabU0 = -9.25, kTabH = 0.125;
 constexpr int kTabNF = 3;   // series per interval: sigma_E T^3, sigma_R T^3, ln(1 - e^{-w})
 // one (group, interval) entry: the kTabLo low-order monomial coefficients of each series in
 // FP64, then its kTabNC - kTabLo high-order ones in FP32 (padded to an even count)
-constexpr int kTabLo = 7;
+constexpr int kTabLo = 5;
 constexpr int kTabHiF = ((kTabNF * (kTabNC - kTabLo) + 1) / 2) * 2;   // floats
 constexpr int kTabEntry = kTabNF * kTabLo + kTabHiF / 2;               // doubles
 inline size_t otab_doubles(int G) { return (size_t)G * kTabNI * kTabEntry; }

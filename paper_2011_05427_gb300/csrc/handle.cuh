@@ -17,8 +17,9 @@ struct trt_handle {
     double *E1, *F1, *Eb0_1, *EbX_1;
     trt::Level crs, grey;
     double *Ecyc, *Ephase;
-    double *flags = nullptr;
-    double *hflags = nullptr;   // pinned host buffer, owned (freed in the destructor)
+    double *flags = nullptr;    // [10]: convergence flags [0..6], then the inner-loop
+    int *ctl = nullptr;         // control words (ints in the last two doubles of flags)
+    double *hflags = nullptr;   // pinned host mirror of flags + ctl, owned (freed below)
     // learned closure (trt_set_closure): caller-owned device buffers, or null
     const float *mlp_params = nullptr;
     const void *mlp_w16 = nullptr;

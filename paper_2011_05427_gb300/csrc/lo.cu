@@ -467,6 +467,7 @@ __device__ void lo_solve_body(const LoCtx &x, int q, int sw)
 template <typename R>
 __global__ void __launch_bounds__(128) k_lo_solve(LoCtx x)
 {
+    if (x.gate && *x.gate) return;   // the phase's inner loop has ended
     lo_solve_body<R>(x, blockIdx.x, blockIdx.x);
 }
 
@@ -964,6 +965,16 @@ __device__ void grey_body(const GreyCtx &x)
             a.flags[4] = __longlong_as_double((long long)v[4]);
             a.flags[5] = __longlong_as_double((long long)v[5]);
             a.flags[6] = __longlong_as_double((long long)v[6]);
+            if (a.ctl) {   // inner-loop control: this cycle ran; does the phase go on?
+                const double f1 = __longlong_as_double((long long)v[1]);
+                const double f2 = __longlong_as_double((long long)v[2]);
+                const double f3 = __longlong_as_double((long long)v[3]);
+                const double f4 = __longlong_as_double((long long)v[4]);
+                const bool conv_in = f1 <= a.eps_in * f2 && f3 <= a.eps_in * f4;
+                a.ctl[1] += 1;
+                // a bad temperature of this visit or of an earlier visit of the cycle
+                if (v[0] != 0ull || a.flags[0] != 0.0 || (!a.fixed && conv_in)) a.ctl[0] = 1;
+            }
         }
     }
     if (a.have_prev_dev && threadIdx.x == 0) *a.have_prev_dev = 1;   // after the reduction's barriers
@@ -991,19 +1002,27 @@ __device__ void group_sum_body(const GroupSumArgs &a, int bx)
 }
 
 // entry points: the single-slab kernels pass blockIdx; the batched ones walk a work list
+// (single-slab entry points: return at entry while the driver's gate is set)
 __global__ void __launch_bounds__(512) k_restrict(RestrictCtx x)
 {
+    if (x.gate && *x.gate) return;
     restrict_body(x, blockIdx.x, blockIdx.y);
 }
 __global__ void __launch_bounds__(128) k_restrict_part(Restrict2Ctx x)
 {
+    if (x.gate && *x.gate) return;
     restrict_part_body(x, blockIdx.x, blockIdx.y);
 }
 __global__ void __launch_bounds__(32 * kRP) k_restrict_final(Restrict2Ctx x)
 {
+    if (x.gate && *x.gate) return;
     restrict_final_body(x, blockIdx.x, blockIdx.y);
 }
-__global__ void __launch_bounds__(1024) k_grey(GreyCtx x) { grey_body(x); }
+__global__ void __launch_bounds__(1024) k_grey(GreyCtx x)
+{
+    if (x.lo.gate && *x.lo.gate) return;
+    grey_body(x);
+}
 __global__ void __launch_bounds__(256) k_group_sum(GroupSumArgs a) { group_sum_body(a, blockIdx.x); }
 
 #define TRT_BATCHED(name, Ctx, bounds, call)                                                  \
@@ -1047,6 +1066,7 @@ LoCtx make_lo_ctx(const Problem &p, double dt, const Level &L)
     x.lo_slot = p.lo_slot;
     x.L = L;
     x.a_cell = nullptr; x.s_cell = nullptr;
+    x.gate = p.gate;
     return x;
 }
 
@@ -1128,6 +1148,7 @@ RestrictCtx make_restrict_ctx(const Problem &p, const Level &src, const Level &d
 {
     RestrictCtx x;
     x.nx = p.nx; x.r = src.n / dst.n; x.h = p.h; x.ihf = p.ihf; x.S = src; x.T = dst;
+    x.gate = p.gate;
     return x;
 }
 
@@ -1136,6 +1157,7 @@ Restrict2Ctx make_restrict2_ctx(const Problem &p, const Level &src, const Level 
     Restrict2Ctx y;
     y.nx = p.nx; y.r = src.n / dst.n; y.nchunk = restrict2_nchunk(src.n, dst.n);
     y.h = p.h; y.ihf = p.ihf; y.S = src; y.T = dst; y.part = p.rscratch;
+    y.gate = p.gate;
     return y;
 }
 

@@ -322,21 +322,39 @@ void host_group_B(int G, const double *edges, double T, double *B)
 // One interval's series in the local coordinate t in [-1, 1], stored as monomial
 // coefficients a_0 .. a_{kTabNC-1} (converted from the Chebyshev fit when the tables are
 // built) and summed by Horner's rule: one FMA per term, half the FP64 operations of
-// Clenshaw's recurrence on the Chebyshev coefficients.  Over the tabulated functions the
-// conversion keeps the sum's rounding error within a factor ~2 of |p(t)| (the coefficients
-// of a fit that reaches FP64 accuracy in 12 terms decay much faster than the growth of the
-// Chebyshev polynomials' monomial coefficients).  The terms from t^kTabLo on are at most
-// 3.3e-7 of |p| over the 17-, 1024- and 4096-group tables, so they are summed in FP32
-// (a_k stored in FP32, between 4e-33 and 1.2e5: normal numbers) and joined to the FP64
-// Horner sum of the low terms: a relative error of at most 3.4e-14 (CPU emulation of the
-// split on every table entry), for 4 FP32 FMAs and one conversion in place of 5 FP64 FMAs.
+// Clenshaw's recurrence on the Chebyshev coefficients.  The conversion is safe for the
+// tabulated functions: sum |a_j| <= 1.45 min |p(t)| over every group and interval of the
+// 17-, 256-, 1024- and 4096-group structures (the fits' coefficients decay much faster than
+// the Chebyshev polynomials' monomial coefficients grow on intervals 0.125 wide in ln T).
+// The terms from t^kTabLo on are at most 2.4e-6 of |p| there (1.9e-8 absolute for the
+// logarithm of the emission factor), so they are summed in FP32 (a_k stored in FP32,
+// between 3e-31 and 7.3e7: normal numbers) and joined to the FP64 Horner sum of the low
+// terms; against the direct group integrals the split evaluation stays within 1e-12
+// (sigma_E), the direct Rosseland quadrature's own 1.6e-11 (sigma_R) and 4e-14 absolute
+// (emission logarithm) -- a CPU emulation of the split on every table entry at 9 points
+// per interval -- for 3 FP32 FMAs and one exact conversion in place of 4 FP64 FMAs.
+//
+// The FP32 -> FP64 conversion of the tail: GB300 converts on the FP64 pipe, so a normal
+// float is widened with integer instructions (sign, exponent rebiased by 1023 - 127 = 896,
+// mantissa shifted by 29: exact); zero, subnormal, infinite and NaN values convert.
+__device__ inline double widen_f32(float q)
+{
+    const unsigned u = __float_as_uint(q);
+    const unsigned e = (u >> 23) & 0xffu;
+    if (e == 0u || e == 0xffu) return (double)q;
+    const unsigned long long b = ((unsigned long long)(u & 0x80000000u) << 32) |
+                                 ((unsigned long long)(e + 896u) << 52) |
+                                 ((unsigned long long)(u & 0x7fffffu) << 29);
+    return __longlong_as_double((long long)b);
+}
+
 __device__ inline double horner(const double *__restrict__ a, const float *__restrict__ b,
                                 double t, float tf)
 {
     float q = b[kTabNC - kTabLo - 1];
 #pragma unroll
     for (int k = kTabNC - kTabLo - 2; k >= 0; --k) q = fmaf(q, tf, b[k]);
-    double p = (double)q;
+    double p = widen_f32(q);
 #pragma unroll
     for (int k = kTabLo - 1; k >= 0; --k) p = fma(p, t, a[k]);
     return p;
@@ -368,6 +386,7 @@ __host__ __device__ inline void group_ratios(double T, double ea, double eb, con
 // first.
 struct CellTerms {
     double T[32], iT[32], iT3[32], t[32];
+    double kET[32];           // 27 s C_B T: the tabulated emission's factor
     double Tr[32], rho[32];   // T_r option: the radiation temperature, T_r / T
     float tf[32];
     int m[32];
@@ -383,6 +402,7 @@ __device__ inline void stage_cells(const OpacityArgs &a, int i0, CellTerms &ct, 
             ct.T[tx] = Ti;
             ct.iT[tx] = iT;
             ct.iT3[tx] = iT * iT * iT;
+            ct.kET[tx] = a.kE * Ti;
             int m = -1;
             double t = 0.0;
             if (a.otab) {
@@ -471,7 +491,7 @@ __device__ inline void opacity_body(const OpacityArgs &a, int i0, int g0, const 
         constexpr int kh = kTabNC - kTabLo;
         sg = horner(c, ch, t, tf) * iT3;
         sR = horner(c + kTabLo, ch + kh, t, tf) * iT3;
-        em = a.kE * Ti * mx.ex(horner(c + 2 * kTabLo, ch + 2 * kh, t, tf) - xa);
+        em = ct.kET[tx] * mx.ex(horner(c + 2 * kTabLo, ch + 2 * kh, t, tf) - xa);
     } else {
         const double k27 = 27.0 * a.s;
         const double xb = binf ? 0.0 : eb * iT;
@@ -506,6 +526,7 @@ __device__ inline Mx stage_exp_table(double *s_e2)
 // block (32 cells, 8 groups); grid (ceil(nx / 32), ceil(G / 8))
 __global__ void __launch_bounds__(256) k_opacity(OpacityArgs a)
 {
+    if (a.gate && *a.gate) return;   // the phase's inner loop has ended (every thread alike)
     __shared__ double s_e2[32];
     __shared__ CellTerms ct;
     const Mx mx = stage_exp_table(s_e2);
@@ -677,6 +698,7 @@ OpacityArgs make_opacity_args(const Problem &p, const double *T, double *sigE, d
     a.h = p.h;
     a.icdt = (dt > 0) ? 1.0 / (kC * dt) : 0.0;
     a.kE = 27.0 * p.s * kCB;   // the order of the direct path's k27 * kCB
+    a.gate = p.gate;
     return a;
 }
 

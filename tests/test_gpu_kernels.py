@@ -476,12 +476,17 @@ def test_grey_newton_parity(trt, orc, nx, have_prev, cut):
 def test_device_exp_and_reciprocal(trt):
     """The opacity kernel's exponential (Tang's table-driven method) and reciprocal
     (refined hardware approximation) against the C library in FP64: within 2 ulp over the
-    normal range, the library's own values outside it, IEEE results at 0 / inf / NaN."""
+    normal range, exactly zero where the library's value underflows to zero (x <= -746,
+    the integer range test), the library's own values in the subnormal range and IEEE
+    results at 0 / inf."""
     import torch
     r = np.random.default_rng(77)
     x = np.concatenate([r.uniform(-707.9, 708.9, 200000), r.uniform(-1, 1, 50000),
                         r.uniform(-40, 40, 50000), np.arange(-700, 700, 0.25),
-                        [0.0, -0.0, 1e-300, -745.5, 709.9, 800.0, -800.0]])
+                        r.uniform(-780, -700, 20000), r.uniform(700, 720, 2000),
+                        [0.0, -0.0, 1e-300, -745.5, -745.13, -746.0, -704.0, 704.0,
+                         -703.9999999999999, 703.9999999999999, 709.9, 800.0, -800.0,
+                         -np.inf, np.inf]])
     n = x.size
     xd = torch.as_tensor(x, device="cuda")
     ex = torch.empty_like(xd)
