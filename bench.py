@@ -277,13 +277,27 @@ def sweep_roofline(trt, s, cfg, fp32=False, local=0, reps=20):
     return {"roofline": roof, "ms": ms}
 
 
-def timed_steps(trt, cfg, precision, cycle, steps, warmup, local, ws, clocks=False):
+# Algorithm 3's l_max (cycles per low-order phase) for each form and cycle: the fastest of
+# l_max = 1 .. 4 per converged fc_1024 step as measured by --lmax-sweep on a GB300.  FP64
+# sweeps are dear, so the FP64 form spends more cycles per sweep (V: l_max 3); FP32 sweeps
+# are cheap next to a cycle (V: l_max 2).  W and F take l_max 1: one such cycle already
+# visits every grid.
+def tuned_lmax(precision, cycle):
+    if cycle != "V":
+        return 1
+    return 3 if precision in ("fp64", "lo32") else 2
+
+
+def timed_steps(trt, cfg, precision, cycle, steps, warmup, local, ws, clocks=False,
+                l_max=None):
     """warmup + steps converged steps of one solver on the device; returns the device time
     of the timed steps (max over ranks), their stats, the clock record and the solver."""
     import torch
     s = trt.Solver.from_slab(cfg, precision=precision, device=f"cuda:{local}")
     s.tile = s.autotune(cfg.dt, reps=10)   # sweep tile for this problem (state unchanged)
-    l_max = 4 if cycle == "V" else 2
+    if l_max is None:
+        l_max = tuned_lmax(precision, cycle)
+    s.l_max = l_max
     for _ in range(warmup):
         s.step(cfg.dt, cycle, l_max, cfg.eps)
     clk = Clocks(local) if clocks else None
@@ -401,7 +415,8 @@ def batch_bench(local, steps=3, warmup=2):
 
 def closure_bench(local, ms_fp64, steps=10):
     """Learned warm start: trained on snapshots of 4 slabs x 10 steps of the method, then
-    fc_1024 stepped with FP32 sweeps with and without it."""
+    fc_1024 stepped with FP32 sweeps (at their tuned l_max) with and without it."""
+    import dataclasses
     from paper_2011_05427_gb300 import closure
     import torch
     t0 = time.perf_counter()
@@ -409,7 +424,8 @@ def closure_bench(local, ms_fp64, steps=10):
     net, hist = closure.train(X, Y, iters=1000, batch=8192, lr=1e-3, device=f"cuda:{local}")
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
-    r = closure.compare(W.fc_1024("V"), net, steps, precision="sweep32", device=f"cuda:{local}")
+    cfg = dataclasses.replace(W.fc_1024("V"), l_max=tuned_lmax("sweep32", "V"))
+    r = closure.compare(cfg, net, steps, precision="sweep32", device=f"cuda:{local}")
     a, b = r["plain"], r["closure"]
     dT = float(np.max(np.abs(a["state"]["T"] - b["state"]["T"]) / a["state"]["T"]))
     return {"train_rows": int(len(X)), "train_loss_first_last": [hist[0][1], hist[-1][1]],
@@ -417,7 +433,7 @@ def closure_bench(local, ms_fp64, steps=10):
             "sweep32_plain": {k: a[k] for k in ("n_ti", "n_c", "ms_per_step")},
             "sweep32_closure": {k: b[k] for k in ("n_ti", "n_c", "ms_per_step")},
             "speedup_closure_vs_plain_fp64": ms_fp64 / b["ms_per_step"],
-            "max_rel_T_closure_vs_plain": dT, "steps": steps}
+            "max_rel_T_closure_vs_plain": dT, "steps": steps, "l_max": cfg.l_max}
 
 
 def fc4096_bench(local, steps=10):
@@ -610,6 +626,27 @@ def adaptive_cycle_run(local=0):
     return out
 
 
+def lmax_sweep_run(local=0, steps=10, warmup=3):
+    """ms per converged fc_1024 step, sweeps and cycles for each form (FP64, FP32 sweeps),
+    cycle and l_max: the measurement behind tuned_lmax.  Each run's final state is compared
+    with the FP64 V-cycle l_max 4 state after the same steps."""
+    from paper_2011_05427_gb300 import trt
+    cfg = W.fc_1024("V")
+    cands = [("V", 1), ("V", 2), ("V", 3), ("V", 4), ("W", 1), ("W", 2), ("F", 1), ("F", 2)]
+    out, states = [], []
+    for prec in ("fp64", "sweep32"):
+        for cyc, lm in cands:
+            t, st, _, s = timed_steps(trt, cfg, prec, cyc, steps, warmup, local, 1, l_max=lm)
+            states.append(s.moments()["T"])
+            s.close()
+            out.append({"precision": prec, "cycle": cyc, "l_max": lm,
+                        "ms": t / steps * 1e3, **counters(st, steps)})
+    ref = states[cands.index(("V", 4))]
+    for r, T in zip(out, states):
+        r["max_rel_T_vs_fp64_V4"] = float(np.max(np.abs(T - ref) / ref))
+    return out
+
+
 def counters(stats, steps):
     return {k: sum(x[k] for x in stats) / steps for k in ("n_ti", "n_c", "n_lo")}
 
@@ -622,8 +659,9 @@ def run_ours(args):
     cfg = W.fc_1024(args.cycle)
     upd_sweep = cfg.updates_per_sweep()
 
+    lm = tuned_lmax(args.precision, args.cycle)
     t_max, stats, clocks, s = timed_steps(trt, cfg, args.precision, args.cycle, args.steps,
-                                          args.warmup, local, ws, clocks=(rank == 0))
+                                          args.warmup, local, ws, clocks=(rank == 0), l_max=lm)
     n_ti = sum(x["n_ti"] for x in stats)
     launches = sum(x.get("n_kernels", 0) for x in stats)
     value = sum_over_ranks(n_ti * upd_sweep, ws) / t_max
@@ -639,7 +677,7 @@ def run_ours(args):
     s2 = trt.Solver.from_slab(cfg, precision=args.precision, device=f"cuda:{local}")
     e2e_ti = 0
     for _ in range(args.steps):
-        st = s2.step(cfg.dt, args.cycle, 4 if args.cycle == "V" else 2, cfg.eps)
+        st = s2.step(cfg.dt, args.cycle, lm, cfg.eps)
         e2e_ti += st["n_ti"]
         s2.moments()
     torch.cuda.synchronize()
@@ -653,32 +691,43 @@ def run_ours(args):
     # the other cycle and the mixed-precision form on the same workload, same step count
     extra = {}
     if args.compare:
-        other = "W" if args.cycle == "V" else "V"
-        t_o, st_o, _, s_o = timed_steps(trt, cfg, args.precision, other, args.steps, 1,
-                                        local, ws)
-        s_o.close()
-        extra[f"cycle_{other}"] = {"ms_per_step": t_o / args.steps * 1e3,
-                                   "value": sum(x["n_ti"] for x in st_o) * upd_sweep / t_o,
-                                   **counters(st_o, args.steps)}
+        for other in [c for c in ("V", "W", "F") if c != args.cycle]:
+            lo = tuned_lmax(args.precision, other)
+            t_o, st_o, _, s_o = timed_steps(trt, cfg, args.precision, other, args.steps, 1,
+                                            local, ws, l_max=lo)
+            s_o.close()
+            extra[f"cycle_{other}"] = {"ms_per_step": t_o / args.steps * 1e3, "l_max": lo,
+                                       "value": sum(x["n_ti"] for x in st_o) * upd_sweep / t_o,
+                                       **counters(st_o, args.steps)}
         if args.precision == "fp64":
+            lm32 = tuned_lmax("sweep32", args.cycle)
             t_m, st_m, _, s_m = timed_steps(trt, cfg, "sweep32", args.cycle, args.steps,
-                                            args.warmup, local, ws)
+                                            args.warmup, local, ws, l_max=lm32)
             a, b = s.moments(), s_m.moments()
             s_m.close()
+            # the same form at the FP64 form's l_max: the speed-up at equal iteration settings
+            t_e, st_e, _, s_e = timed_steps(trt, cfg, "sweep32", args.cycle, args.steps,
+                                            args.warmup, local, ws, l_max=lm)
+            s_e.close()
             extra["mixed_sweep32"] = {
                 "ms_per_step": t_m / args.steps * 1e3,
+                "l_max": lm32,
                 "value": sum(x["n_ti"] for x in st_m) * upd_sweep / t_m,
                 "speedup_vs_fp64": ms_step / (t_m / args.steps * 1e3),
                 "max_rel_T_vs_fp64": float(np.max(np.abs(b["T"] - a["T"]) / a["T"])),
                 "max_rel_Eg_vs_fp64": float(np.max(np.abs(b["Eg"] - a["Eg"]) /
                                                    a["Eg"].sum(0)[None, :])),
-                "note": "FP32 sweeps, FP64 group/grey LOQD + MEB; both converged to eps; "
-                        "compared after the same warm-up + timed steps",
+                "at_fp64_l_max": {"l_max": lm, "ms_per_step": t_e / args.steps * 1e3,
+                                  "speedup_vs_fp64": ms_step / (t_e / args.steps * 1e3),
+                                  **counters(st_e, args.steps)},
+                "note": "FP32 sweeps, FP64 group/grey LOQD + MEB; each form at its own tuned "
+                        "l_max, both converged to eps; compared after the same warm-up + "
+                        "timed steps",
                 **counters(st_m, args.steps)}
             if ws == 1 and args.cpu_baseline:
                 extra["mixed_sweep32"]["vs_oracle"] = mixed_vs_oracle(local, "sweep32")
             t_x, st_x, _, s_x = timed_steps(trt, cfg, "mixed", args.cycle, args.steps,
-                                            args.warmup, local, ws)
+                                            args.warmup, local, ws, l_max=lm32)
             c = s_x.moments()
             s_x.close()
             extra["mixed"] = {
@@ -688,6 +737,7 @@ def run_ours(args):
                 "max_rel_T_vs_fp64": float(np.max(np.abs(c["T"] - a["T"]) / a["T"])),
                 "max_rel_Eg_vs_fp64": float(np.max(np.abs(c["Eg"] - a["Eg"]) /
                                                    a["Eg"].sum(0)[None, :])),
+                "l_max": lm32,
                 "note": "FP32 sweeps and FP32 group LOQD eliminations refined by two "
                         "FP64-residual steps, FP64 grey LOQD + MEB",
                 **counters(st_x, args.steps)}
@@ -729,8 +779,8 @@ def run_ours(args):
         "data": "synthetic (Fleck-Cummings slab, seeded, no dataset)",
         "config": {"workload": f"fc_1024: 500 cells, 64 directions (double S32), 1024 groups, "
                                f"grids 1024/256/64/16/1, {args.cycle}-cycle "
-                               f"l_max {4 if args.cycle == 'V' else 2}, dt 1e-3 sh, eps 1e-8, "
-                               f"{args.precision}",
+                               f"l_max {lm}, dt 1e-3 sh, eps 1e-8, {args.precision}",
+                   "l_max": lm,
                    "parallelism": f"replicas x{ws}",
                    "sweep_tile": {"D": tile[0], "S": tile[1], "NS": tile[2],
                                   "picked_by": "trt_autotune"},
@@ -896,7 +946,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed", "sweep32", "lo32"])
-    ap.add_argument("--cycle", default="V", choices=["V", "W"])
+    ap.add_argument("--cycle", default="V", choices=["V", "W", "F"])
     ap.add_argument("--no-compare", dest="compare", action="store_false",
                     help="skip the comparison runs (other cycle, FP32 sweeps, MLP, closure, "
                          "batch)")
@@ -922,6 +972,9 @@ def main():
     ap.add_argument("--adaptive-cycle", action="store_true",
                     help="fixed V/W/F cycles against the per-step cycle controller (one JSON "
                          "line)")
+    ap.add_argument("--lmax-sweep", action="store_true",
+                    help="ms per converged fc_1024 step for each form, cycle and l_max (one "
+                         "JSON line)")
     ap.add_argument("--tile", default=None,
                     help="D,shape: sweep tile for --profile-step (default: the library's)")
     ap.add_argument("--launch-table", default="", metavar="CSV",
@@ -935,6 +988,9 @@ def main():
         return
     if args.paper_tables:
         print(json.dumps({"paper_tables": paper_tables_run()}))
+        return
+    if args.lmax_sweep:
+        print(json.dumps({"lmax_sweep": lmax_sweep_run()}))
         return
     if args.profile_sweep:
         from paper_2011_05427_gb300 import trt
@@ -971,7 +1027,7 @@ def main():
         if args.tile:
             s.set_sweep_tile(*[int(x) for x in args.tile.split(",")])
         for _ in range(args.warmup + 1):
-            s.step(cfg.dt, cfg.cycle, cfg.l_max, cfg.eps)
+            s.step(cfg.dt, cfg.cycle, tuned_lmax(args.precision, args.cycle), cfg.eps)
         s.close()
         return
     if args.impl == "reference":

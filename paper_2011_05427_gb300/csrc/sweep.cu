@@ -301,9 +301,11 @@ __device__ void finalize_body(const FinalizeArgs &x, int bx)
                     A0.add(part[(size_t)(t * 2 + 0) * n + idx]);
                     A2.add(part[(size_t)(t * 2 + 1) * n + idx]);
                 }
-                // a division, not a reciprocal: in cold cells both angular sums are
-                // subnormal, where 1/A0 overflows while A2/A0 stays the ratio
-                f[idx] = (A0.s != (R)0) ? (double)(A2.s / A0.s) : 1.0 / 3.0;
+                // A2 times the refined reciprocal of A0 (within an ulp of the quotient, a
+                // quarter of a division's FP64 operations), or the division where 1/A0
+                // leaves the normal range: in cold cells both angular sums are subnormal,
+                // where 1/A0 overflows while A2/A0 stays the ratio
+                f[idx] = (A0.s != (R)0) ? ratio64((double)A2.s, (double)A0.s) : 1.0 / 3.0;
             } else {
                 // FP32: the tiles' (high, low) pairs summed as unevaluated FP32 sums (an
                 // exact two-sum per high part, the low parts added plainly), then the ratio

@@ -22,6 +22,21 @@ struct Acc {   // per-tile angular sum: plain in FP64, compensated (Kahan) in FP
     }
 };
 
+// a / b for b != 0: a times the hardware reciprocal of b refined by one third-order step
+// (below FP64 rounding) while that reciprocal is a normal number of moderate exponent,
+// else the IEEE division (in a function that is never inlined: a branch around it, not
+// predicated FP64 instructions); the exponent test runs on integer instructions
+static __device__ __noinline__ double div64_slow(double a, double b) { return a / b; }
+__device__ inline double ratio64(double a, double b)
+{
+    double x;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(x) : "d"(b));
+    const unsigned ex = ((unsigned)__double2hiint(x) >> 20) & 0x7ffu;
+    if (ex - 1u >= 2018u) return div64_slow(a, b);
+    const double e = fma(-b, x, 1.0);
+    return a * fma(x, fma(e, e, e), x);
+}
+
 // (S, E) += hi + lo for unevaluated FP32 sums S + E: hi enters by an exact two-sum (Knuth),
 // its rounding error and lo go to E
 __device__ inline void two_sum_acc(float &S, float &E, float hi, float lo)
