@@ -74,6 +74,10 @@ void carve(trt_handle *h, Carver &c)
     p.EinX = c.take<double>(G); p.FinX = c.take<double>(G);
     p.ihf = c.take<double>(nx + 1);
     p.hf = c.take<double>(nx + 1);
+    p.hc = c.take<double>(nx); p.h2 = c.take<double>(nx);
+    p.fwl = c.take<double>(nx + 1); p.fwr = c.take<double>(nx + 1);
+    p.hidt = c.take<double>(nx); p.dxicdt = c.take<double>(nx + 1);
+    p.lo_dt = 0.0;
     p.dir32 = reinterpret_cast<float *>(c.take<double>(2 * M));
     p.e2tab = c.take<double>(32);
     p.lo_slot = reinterpret_cast<int *>(c.take<double>((nx + 2) / 2));
@@ -326,6 +330,15 @@ int trt_create(const trt_grid *grid, const trt_angles *angles, const trt_groups 
     for (int f = 1; f < nx; ++f) ihf[f] = 1.0 / (hh[f - 1] + hh[f]);
     for (int f = 0; f <= nx; ++f)
         hf[f] = (f == 0) ? 0.5 * hh[0] : (f == nx) ? 0.5 * hh[nx - 1] : 0.5 * (hh[f - 1] + hh[f]);
+    std::vector<double> hc(nx), h2(nx), fwl(nx + 1, 0.0), fwr(nx + 1, 0.0);
+    for (int i = 0; i < nx; ++i) {
+        hc[i] = kC * hh[i];
+        h2[i] = 2.0 * hh[i];
+    }
+    for (int f = 1; f < nx; ++f) {
+        fwl[f] = hf[f] * ihf[f] * hh[f - 1];
+        fwr[f] = hf[f] * ihf[f] * hh[f];
+    }
     std::vector<int> lo_slot(nx + 1, 0);   // chunk layout of the partitioned LO solve
     if (nx >= 2) {
         const int P = std::min(32, nx / 2);
@@ -396,6 +409,7 @@ int trt_create(const trt_grid *grid, const trt_angles *angles, const trt_groups 
                                cudaMemcpyHostToDevice, p.stream);
     };
     CK(up(p.h, hh)); CK(up(p.ihf, ihf)); CK(up(p.hf, hf)); CK(up(p.edges, edges)); CK(up(p.mu, mu)); CK(up(p.w, w));
+    CK(up(p.hc, hc)); CK(up(p.h2, h2)); CK(up(p.fwl, fwl)); CK(up(p.fwr, fwr));
     CK(cudaMemcpyAsync(p.lo_slot, lo_slot.data(), lo_slot.size() * sizeof(int),
                        cudaMemcpyHostToDevice, p.stream));
     std::vector<float> dir32(4 * (size_t)p.M);   // the FP32 sweeps' per-direction constants
@@ -483,6 +497,7 @@ int trt_step(trt_handle *h, double dt, const trt_cycle *cyc, trt_stats *stats)
     } gate_off{p};
     p.gate = nullptr;
 
+    CK(ensure_lo_consts(p, dt));   // the LO rows' h/dt and hf/(c dt)
     CK(d2d(h, h->Told, h->T, nx));
     CK(d2d(h, h->Eg_old, h->Eg, (size_t)G * nx));
     CK(d2d(h, h->Fg_old, h->Fg, (size_t)G * (nx + 1)));
@@ -901,6 +916,7 @@ int trt_k_lo_solve(trt_handle *h, double dt, trt_level *lv)
 {
     if (!h || !lv || !(dt > 0) || lv->n < 1) return TRT_EINVAL;
     Level L = from_abi(lv);
+    CK(ensure_lo_consts(h->p, dt));
     CK(launch_lo_solve(h->p, dt, L));
     CK(cudaStreamSynchronize(h->p.stream));
     return TRT_OK;
@@ -923,6 +939,7 @@ int trt_k_grey_newton(trt_handle *h, double dt, const double *Tstar, const doubl
     if (!h || !g || g->n != 1 || !(dt > 0) || !Tstar || !Told || !T) return TRT_EINVAL;
     if (have_prev && (!sig_prev || !T_prev)) return TRT_EINVAL;
     Level L = from_abi(g);
+    CK(ensure_lo_consts(h->p, dt));
     const Problem &p = h->p;
     GreyArgs a{};
     a.Tstar = Tstar; a.Told = Told;

@@ -688,6 +688,7 @@ int trt_step_batch(trt_batch *b, double dt, const trt_cycle *cyc, trt_stats *sta
     // rebuild every step
     int rc = build_all(b, dt, cyc->type);
     if (rc != TRT_OK) return rc;
+    for (int s = 0; s < n; ++s) BCK(ensure_lo_consts(b->h[s]->p, dt));   // LO row constants
     const int cyc_id = S_CYCLE0 + cyc->type;
     std::vector<SlabState> st(n);
     std::vector<std::vector<int>> S(n);

@@ -59,6 +59,7 @@ struct LoCtx {
     int nx;
     double dt, icdt, idt;   // dt, 1/(c dt), 1/dt
     const double *h, *ihf, *hf;
+    const double *hc, *h2, *fwl, *fwr, *hidt, *dxicdt;   // Problem's LO row constants
     const int *lo_slot;
     Level L;
     const double *a_cell, *s_cell;   // grey: explicit absorption / source per cell

@@ -175,6 +175,13 @@ struct Problem {
     double *h, *edges, *mu, *w, *Iin0, *IinX, *Ein0, *Fin0, *EinX, *FinX;
     double *ihf;        // [nx+1]: 1/(h_{f-1} + h_f) at interior faces (dx-weighted means)
     double *hf;         // [nx+1]: face half-widths h_0/2, (h_{f-1} + h_f)/2, h_{nx-1}/2
+    // constants of the LO rows (lo.cu), so that a row spends no FP64 operation on them: per
+    // cell c h and 2 h; per interior face f the weights hf h_{f-1} / (h_{f-1} + h_f) and
+    // hf h_f / (h_{f-1} + h_f) of the cell opacities in dx sigma_R,face; and for the step
+    // length lo_dt (ensure_lo_consts) h/dt per cell and hf/(c dt) per face
+    double *hc, *h2, *fwl, *fwr;
+    double *hidt, *dxicdt;
+    double lo_dt = 0.0;
     float *dir32;       // [M][4]: |mu|, |mu|/2, w/2, w mu^2/2 rounded once to FP32 (FP32 sweeps)
     double *e2tab;      // [32]: 2^(j/32), the table of texp for kernels outside physics.cu
     int *lo_slot;       // [nx+1]: shared-memory slot k * 32 + l of face/row f in the
@@ -229,6 +236,8 @@ cudaError_t launch_sweep(const Problem &p, double dt, const void *sigE, const vo
                          double *psi_exit, double *f, double *fb0, double *fbX, double *C0,
                          double *CX);
 cudaError_t launch_lo_solve(const Problem &p, double dt, const Level &L);
+// h/dt and hf/(c dt) of the LO rows for step length dt (a launch when dt changed)
+cudaError_t ensure_lo_consts(Problem &p, double dt);
 cudaError_t launch_restrict(const Problem &p, const Level &src, Level &dst);
 size_t restrict_scratch_doubles(int nx, int n_from, int n_to);
 cudaError_t launch_grey(const Problem &p, const Level &g, const GreyArgs &a);

@@ -67,8 +67,24 @@ __device__ inline void face_coef(const LoCtx &x, int q, int f, R &PL, R &PR, R &
         phiR += (R)x.L.etaR[(size_t)q * (nx + 1) + f];
     }
     const R c = (R)kC, icdt = (R)x.icdt;
-    R D = dx * (icdt + (R)sigR_face(x, q, f));
-    R Gf = dx * (R)x.L.Fold[(size_t)q * (nx + 1) + f] * icdt;
+    R D, Gf;
+    if constexpr (sizeof(R) == 8) {
+        // dx (1/(c dt) + sigma_R,face) and dx Fold/(c dt) from the row constants: the face
+        // opacity's dx-weighted mean folded into one FMA per cell opacity
+        const double dxi = x.dxicdt[f];
+        if (!x.L.fine) {
+            D = fma((double)dx, x.L.sigR[(size_t)q * (nx + 1) + f], dxi);
+        } else {
+            const double *sc = x.L.sigR + (size_t)q * nx;
+            D = (f == 0)    ? fma((double)dx, sc[0], dxi)
+                : (f == nx) ? fma((double)dx, sc[nx - 1], dxi)
+                            : fma(x.fwl[f], sc[f - 1], fma(x.fwr[f], sc[f], dxi));
+        }
+        Gf = x.L.Fold[(size_t)q * (nx + 1) + f] * dxi;
+    } else {
+        D = dx * (icdt + (R)sigR_face(x, q, f));
+        Gf = dx * (R)x.L.Fold[(size_t)q * (nx + 1) + f] * icdt;
+    }
     if (f == 0) {
         const R iC0 = rcpR<R>((R)x.L.C0[q]);
         D -= phiL * iC0;
@@ -91,6 +107,17 @@ __device__ inline void cell_row(const LoCtx &x, int q, int i, R &Ap, R &Dp)
 {
     const R hi = (R)x.h[i], idt = (R)x.idt;
     const R Eo = (R)x.L.Eold[(size_t)q * x.nx + i];
+    if constexpr (sizeof(R) == 8) {   // from the row constants h/dt, c h, 2 h
+        const double hidt = x.hidt[i];
+        if (x.a_cell) {
+            Ap = fma(x.h[i], x.a_cell[i], hidt);
+            Dp = fma(hidt, Eo, x.h[i] * x.s_cell[i]);
+        } else {
+            Ap = fma(x.hc[i], x.L.sig[(size_t)q * x.nx + i], hidt);
+            Dp = fma(hidt, Eo, x.h2[i] * x.L.emis[(size_t)q * x.nx + i]);
+        }
+        return;
+    }
     if (x.a_cell) {
         Ap = hi * (idt + (R)x.a_cell[i]);
         Dp = hi * fma(Eo, idt, (R)x.s_cell[i]);
@@ -885,8 +912,13 @@ __device__ inline void grey_newton_cell(const GreyArgs &a, const Level &g, int h
     double D = 0.0;
     if (have_prev) {
         const double Tp = a.T_prev[i];
-        // across grids only where |dT| is far above rounding (relative noise ~ eps T/|dT|)
-        if (Ts != Tp && fabs(Ts - Tp) > a.secant_cut * Ts) D = (sig - a.sig_prev[i]) * rcp64(Ts - Tp);
+        // T* != T_prev on the encodings (positive finite values: integer instructions, not
+        // an FP64 compare); across grids only where |dT| is far above rounding (relative
+        // noise ~ eps T/|dT|)
+        const bool moved = __double_as_longlong(Ts) != __double_as_longlong(Tp);
+        const bool cut = __double_as_longlong(a.secant_cut) != 0ll;
+        if (moved && (!cut || fabs(Ts - Tp) > a.secant_cut * Ts))
+            D = (sig - a.sig_prev[i]) * rcp64(Ts - Tp);
     }
     const double base = cvdt + dQ;
     double L = base - kC * D * g.Esum[i];
@@ -1058,11 +1090,33 @@ __global__ void __launch_bounds__(256) k_copy_b(const int *__restrict__ meta, in
 
 }  // namespace
 
+namespace {
+__global__ void k_lo_consts(int nx, const double *__restrict__ h, const double *__restrict__ hf,
+                            double idt, double icdt, double *hidt, double *dxicdt)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < nx) hidt[i] = h[i] * idt;
+    if (i <= nx) dxicdt[i] = hf[i] * icdt;
+}
+}  // namespace
+
+cudaError_t ensure_lo_consts(Problem &p, double dt)
+{
+    if (p.lo_dt == dt) return cudaSuccess;
+    k_lo_consts<<<(p.nx + 1 + 255) / 256, 256, 0, p.stream>>>(p.nx, p.h, p.hf, 1.0 / dt,
+                                                                1.0 / (kC * dt), p.hidt, p.dxicdt);
+    const cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) p.lo_dt = dt;
+    return e;
+}
+
+// (the LO row constants hidt, dxicdt must be those of dt: ensure_lo_consts first)
 LoCtx make_lo_ctx(const Problem &p, double dt, const Level &L)
 {
     LoCtx x;
     x.nx = p.nx; x.dt = dt; x.icdt = 1.0 / (kC * dt); x.idt = 1.0 / dt; x.h = p.h; x.ihf = p.ihf;
     x.hf = p.hf;
+    x.hc = p.hc; x.h2 = p.h2; x.fwl = p.fwl; x.fwr = p.fwr; x.hidt = p.hidt; x.dxicdt = p.dxicdt;
     x.lo_slot = p.lo_slot;
     x.L = L;
     x.a_cell = nullptr; x.s_cell = nullptr;
