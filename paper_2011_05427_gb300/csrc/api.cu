@@ -77,6 +77,7 @@ void carve(trt_handle *h, Carver &c)
     p.hc = c.take<double>(nx); p.h2 = c.take<double>(nx);
     p.fwl = c.take<double>(nx + 1); p.fwr = c.take<double>(nx + 1);
     p.hidt = c.take<double>(nx); p.dxicdt = c.take<double>(nx + 1);
+    p.cterm = c.take<double>(8 * nx);   // [7][nx] doubles, nx floats, nx ints
     p.lo_dt = 0.0;
     p.dir32 = reinterpret_cast<float *>(c.take<double>(2 * M));
     p.e2tab = c.take<double>(32);

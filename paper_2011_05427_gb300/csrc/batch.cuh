@@ -30,6 +30,7 @@ struct OpacityArgs {
     double kE;               // 27 s C_B: the emission factor of the tabulated path
     const double *Erad;      // radiation energy per cell: sigma_E, sigma_R at T_r, or null
     const int *gate;         // Problem::gate (single-slab kernel only)
+    double *cterm;           // Problem::cterm: per-cell terms (single-slab kernel only)
 };
 
 struct SweepArgs {

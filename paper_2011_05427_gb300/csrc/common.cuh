@@ -182,6 +182,9 @@ struct Problem {
     double *hc, *h2, *fwl, *fwr;
     double *hidt, *dxicdt;
     double lo_dt = 0.0;
+    // per-cell terms of the single-slab opacity evaluation (physics.cu): [7][nx] doubles,
+    // then nx floats and nx ints
+    double *cterm;
     float *dir32;       // [M][4]: |mu|, |mu|/2, w/2, w mu^2/2 rounded once to FP32 (FP32 sweeps)
     double *e2tab;      // [32]: 2^(j/32), the table of texp for kernels outside physics.cu
     int *lo_slot;       // [nx+1]: shared-memory slot k * 32 + l of face/row f in the

@@ -379,49 +379,91 @@ __host__ __device__ inline void group_ratios(double T, double ea, double eb, con
     Rr = Ns / Ds;
 }
 
-// Per-cell terms of a block's 32 cells, staged once by one row (warp) of the block:
-// T, 1/T, 1/T^3 and the table interval / local coordinate of ln T (m < 0: outside).  The
-// staging row `sy` rotates with the block so that the staging's FP64 work (a logarithm and
-// a reciprocal per cell) lands on all four sub-partitions' FP64 pipes, not always on the
-// first.
+// Per-cell terms of the opacity evaluation: T, 1/T, 1/T^3, 27 s C_B T, the table interval
+// m and local coordinate t of ln T (m < 0: outside the tables), and with the T_r option
+// T_r and T_r / T.  The single-slab kernel reads them from an array that k_cell_terms
+// fills once per evaluation (a logarithm and a reciprocal per cell, instead of once per
+// block of 8 groups); the batched kernel stages its block's 32 cells with one row (warp),
+// rotating with the block over the four sub-partitions.  Both use cell_vals: the same
+// operations, the same bits.
+struct CellVals {
+    double T, iT, iT3, t, kET, Tr, rho;
+    float tf;
+    int m;
+};
+
+__device__ inline CellVals cell_vals(const OpacityArgs &a, int i)
+{
+    CellVals v;
+    const double Ti = a.T[i];
+    const double iT = rcp64(Ti);
+    v.T = Ti;
+    v.iT = iT;
+    v.iT3 = iT * iT * iT;
+    v.kET = a.kE * Ti;
+    int m = -1;
+    double t = 0.0;
+    if (a.otab) {
+        const double z = (log(Ti) - kTabU0) * (1.0 / kTabH);
+        if (z >= 0.0 && z < (double)kTabNI) {
+            m = min((int)z, kTabNI - 1);
+            t = 2.0 * (z - (double)m) - 1.0;
+        }
+    }
+    v.m = m;
+    v.t = t;
+    v.tf = (float)t;
+    v.Tr = Ti;
+    v.rho = 1.0;
+    if (a.Erad) {   // T_r = (E/a_R)^{1/4}; T_r = T without a usable energy
+        const double E = a.Erad[i];
+        const double Tr = (E > 0.0 && isfinite(E)) ? sqrt(sqrt(E / kAR)) : Ti;
+        v.Tr = Tr;
+        v.rho = Tr * iT;
+    }
+    return v;
+}
+
+// the per-cell arrays of the single-slab kernel: [7][nx] doubles (T, 1/T, 1/T^3, t, 27 s
+// C_B T, T_r, T_r/T), then tf [nx] floats and m [nx] ints
+struct CellArrays {
+    double *d;
+    float *f;
+    int *m;
+    int nx;
+    __device__ void put(int i, const CellVals &v) const
+    {
+        d[i] = v.T; d[nx + i] = v.iT; d[2 * nx + i] = v.iT3; d[3 * nx + i] = v.t;
+        d[4 * nx + i] = v.kET; d[5 * nx + i] = v.Tr; d[6 * nx + i] = v.rho;
+        f[i] = v.tf;
+        m[i] = v.m;
+    }
+    __device__ CellVals get(int i) const
+    {
+        CellVals v;
+        v.T = d[i]; v.iT = d[nx + i]; v.iT3 = d[2 * nx + i]; v.t = d[3 * nx + i];
+        v.kET = d[4 * nx + i]; v.Tr = d[5 * nx + i]; v.rho = d[6 * nx + i];
+        v.tf = f[i];
+        v.m = m[i];
+        return v;
+    }
+};
+
+__device__ inline CellArrays cell_arrays(const OpacityArgs &a)
+{
+    return CellArrays{a.cterm, reinterpret_cast<float *>(a.cterm + 7 * (size_t)a.nx),
+                      reinterpret_cast<int *>(a.cterm + 7 * (size_t)a.nx) + a.nx, a.nx};
+}
+
 struct CellTerms {
-    double T[32], iT[32], iT3[32], t[32];
-    double kET[32];           // 27 s C_B T: the tabulated emission's factor
-    double Tr[32], rho[32];   // T_r option: the radiation temperature, T_r / T
-    float tf[32];
-    int m[32];
+    CellVals v[32];
 };
 
 __device__ inline void stage_cells(const OpacityArgs &a, int i0, CellTerms &ct, int sy)
 {
     if ((int)threadIdx.y == (sy & 3)) {
         const int tx = threadIdx.x, i = i0 + tx;
-        if (i < a.nx) {
-            const double Ti = a.T[i];
-            const double iT = rcp64(Ti);
-            ct.T[tx] = Ti;
-            ct.iT[tx] = iT;
-            ct.iT3[tx] = iT * iT * iT;
-            ct.kET[tx] = a.kE * Ti;
-            int m = -1;
-            double t = 0.0;
-            if (a.otab) {
-                const double z = (log(Ti) - kTabU0) * (1.0 / kTabH);
-                if (z >= 0.0 && z < (double)kTabNI) {
-                    m = min((int)z, kTabNI - 1);
-                    t = 2.0 * (z - (double)m) - 1.0;
-                }
-            }
-            ct.m[tx] = m;
-            ct.t[tx] = t;
-            ct.tf[tx] = (float)t;
-            if (a.Erad) {   // T_r = (E/a_R)^{1/4}; T_r = T without a usable energy
-                const double E = a.Erad[i];
-                const double Tr = (E > 0.0 && isfinite(E)) ? sqrt(sqrt(E / kAR)) : Ti;
-                ct.Tr[tx] = Tr;
-                ct.rho[tx] = Tr * iT;
-            }
-        }
+        if (i < a.nx) ct.v[tx] = cell_vals(a, i);
     }
     __syncthreads();
 }
@@ -467,31 +509,28 @@ __device__ void opacity_tr(double nu_a, double nu_b, bool binf, double Tr, doubl
     sR = k27 * Ns / (Tr3 * Ds);
 }
 
-// cell i0 + threadIdx.x, group g0 + threadIdx.y; outputs [G][nx] (cells contiguous)
-__device__ inline void opacity_body(const OpacityArgs &a, int i0, int g0, const CellTerms &ct,
+// cell i, group g with the cell's terms v; outputs [G][nx] (cells contiguous)
+__device__ inline void opacity_body(const OpacityArgs &a, int i, int g, const CellVals &v,
                                     const Mx &mx)
 {
-    const int tx = threadIdx.x;
-    const int i = i0 + tx, g = g0 + threadIdx.y;
-    if (i >= a.nx || g >= a.G) return;
     const size_t idx = (size_t)g * a.nx + i;
-    const double Ti = ct.T[tx], iT = ct.iT[tx], iT3 = ct.iT3[tx];
+    const double Ti = v.T, iT = v.iT, iT3 = v.iT3;
     const double xa = a.edges[g] * iT;
     const double eb = a.edges[g + 1];
     const bool binf = isinf(eb);
     double sg, sR, em;
-    const int m = ct.m[tx];
+    const int m = v.m;
     if (m >= 0) {
         // tabulated: three polynomials in ln T on the cell's interval (the sigma series carry
         // the factor 27 s, kE = 27 s C_B)
-        const double t = ct.t[tx];
-        const float tf = ct.tf[tx];
+        const double t = v.t;
+        const float tf = v.tf;
         const double *c = a.otab + ((size_t)g * kTabNI + m) * kTabEntry;
         const float *ch = reinterpret_cast<const float *>(c + kTabNF * kTabLo);
         constexpr int kh = kTabNC - kTabLo;
         sg = horner(c, ch, t, tf) * iT3;
         sR = horner(c + kTabLo, ch + kh, t, tf) * iT3;
-        em = ct.kET[tx] * mx.ex(horner(c + 2 * kTabLo, ch + 2 * kh, t, tf) - xa);
+        em = v.kET * mx.ex(horner(c + 2 * kTabLo, ch + 2 * kh, t, tf) - xa);
     } else {
         const double k27 = 27.0 * a.s;
         const double xb = binf ? 0.0 : eb * iT;
@@ -502,7 +541,7 @@ __device__ inline void opacity_body(const OpacityArgs &a, int i0, int g0, const 
         em = k27 * kCB * Ti * mx.ex(-xa) * om;
     }
     if (a.Erad)   // T_r option: absorption and Rosseland opacities at the radiation temperature
-        opacity_tr(a.edges[g], eb, binf, ct.Tr[tx], ct.rho[tx], 27.0 * a.s, mx, sg, sR);
+        opacity_tr(a.edges[g], eb, binf, v.Tr, v.rho, 27.0 * a.s, mx, sg, sR);
     a.sigE[idx] = sg;
     a.emis[idx] = em;
     a.sigR[idx] = sR;
@@ -523,15 +562,24 @@ __device__ inline Mx stage_exp_table(double *s_e2)
     return Mx{s_e2, ExpConsts{c_ser.einv, c_ser.eL1, c_ser.eL2}};
 }
 
-// block (32 cells, 8 groups); grid (ceil(nx / 32), ceil(G / 8))
+// the per-cell terms of one evaluation (single slab)
+__global__ void k_cell_terms(OpacityArgs a)
+{
+    if (a.gate && *a.gate) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < a.nx) cell_arrays(a).put(i, cell_vals(a, i));
+}
+
+// block (32 cells, 8 groups); grid (ceil(nx / 32), ceil(G / 8)); the cells' terms from
+// k_cell_terms
 __global__ void __launch_bounds__(256) k_opacity(OpacityArgs a)
 {
     if (a.gate && *a.gate) return;   // the phase's inner loop has ended (every thread alike)
     __shared__ double s_e2[32];
-    __shared__ CellTerms ct;
     const Mx mx = stage_exp_table(s_e2);
-    stage_cells(a, blockIdx.x * 32, ct, blockIdx.x + blockIdx.y);
-    opacity_body(a, blockIdx.x * 32, blockIdx.y * 8, ct, mx);
+    const int i = blockIdx.x * 32 + threadIdx.x, g = blockIdx.y * 8 + threadIdx.y;
+    if (i >= a.nx || g >= a.G) return;
+    opacity_body(a, i, g, cell_arrays(a).get(i), mx);
 }
 
 __global__ void __launch_bounds__(256) k_opacity_b(const int *__restrict__ meta, int N,
@@ -545,7 +593,8 @@ __global__ void __launch_bounds__(256) k_opacity_b(const int *__restrict__ meta,
         if (!bdecode(meta, N, b, s, bx, by)) break;
         const OpacityArgs a = xs[s];
         stage_cells(a, bx * 32, ct, b);
-        opacity_body(a, bx * 32, by * 8, ct, mx);
+        const int i = bx * 32 + threadIdx.x, g = by * 8 + threadIdx.y;
+        if (i < a.nx && g < a.G) opacity_body(a, i, g, ct.v[threadIdx.x], mx);
         __syncthreads();   // the cell terms are restaged by the next work item
     }
 }
@@ -699,6 +748,7 @@ OpacityArgs make_opacity_args(const Problem &p, const double *T, double *sigE, d
     a.icdt = (dt > 0) ? 1.0 / (kC * dt) : 0.0;
     a.kE = 27.0 * p.s * kCB;   // the order of the direct path's k27 * kCB
     a.gate = p.gate;
+    a.cterm = p.cterm;
     return a;
 }
 
@@ -734,6 +784,7 @@ cudaError_t launch_opacity(const Problem &p, const double *T, double *sigE, doub
                            const double *Erad)
 {
     const OpacityArgs a = make_opacity_args(p, T, sigE, emis, sigR, sig32, emis32, dt, Erad);
+    k_cell_terms<<<(p.nx + 127) / 128, 128, 0, p.stream>>>(a);
     k_opacity<<<dim3(opacity_gx(p), (p.G + 7) / 8), dim3(32, 8), 0, p.stream>>>(a);
     return cudaGetLastError();
 }
