@@ -96,6 +96,20 @@ __device__ inline double texp(double x, const double *tab, const ExpConsts &c)
     return __longlong_as_double(__double_as_longlong(v) + ((long long)(k >> 5) << 52));
 }
 
+// FP32 -> FP64 without the FP64 pipe (GB300 converts there): a normal float is widened
+// with integer instructions (sign, exponent rebiased by 1023 - 127 = 896, mantissa shifted
+// by 29: exact); zero, subnormal, infinite and NaN values convert.
+__device__ inline double widen_f32(float q)
+{
+    const unsigned u = __float_as_uint(q);
+    const unsigned e = (u >> 23) & 0xffu;
+    if (e == 0u || e == 0xffu) return (double)q;
+    const unsigned long long b = ((unsigned long long)(u & 0x80000000u) << 32) |
+                                 ((unsigned long long)(e + 896u) << 52) |
+                                 ((unsigned long long)(u & 0x7fffffu) << 29);
+    return __longlong_as_double((long long)b);
+}
+
 const SeriesTables &host_series();   // host copy (built once)
 void gauss_legendre_host(int n, double *x, double *w);   // nodes / weights on [-1, 1]
 cudaError_t ensure_tables();         // upload the tables to the current device (once)

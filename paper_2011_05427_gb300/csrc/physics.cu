@@ -332,22 +332,8 @@ void host_group_B(int G, const double *edges, double T, double *B)
 // terms; against the direct group integrals the split evaluation stays within 1e-12
 // (sigma_E), the direct Rosseland quadrature's own 1.6e-11 (sigma_R) and 4e-14 absolute
 // (emission logarithm) -- a CPU emulation of the split on every table entry at 9 points
-// per interval -- for 3 FP32 FMAs and one exact conversion in place of 4 FP64 FMAs.
-//
-// The FP32 -> FP64 conversion of the tail: GB300 converts on the FP64 pipe, so a normal
-// float is widened with integer instructions (sign, exponent rebiased by 1023 - 127 = 896,
-// mantissa shifted by 29: exact); zero, subnormal, infinite and NaN values convert.
-__device__ inline double widen_f32(float q)
-{
-    const unsigned u = __float_as_uint(q);
-    const unsigned e = (u >> 23) & 0xffu;
-    if (e == 0u || e == 0xffu) return (double)q;
-    const unsigned long long b = ((unsigned long long)(u & 0x80000000u) << 32) |
-                                 ((unsigned long long)(e + 896u) << 52) |
-                                 ((unsigned long long)(u & 0x7fffffu) << 29);
-    return __longlong_as_double((long long)b);
-}
-
+// per interval -- for 3 FP32 FMAs and one exact conversion in place of 4 FP64 FMAs (the
+// tail widened with integer instructions, widen_f32).
 __device__ inline double horner(const double *__restrict__ a, const float *__restrict__ b,
                                 double t, float tf)
 {

@@ -295,47 +295,49 @@ __device__ void finalize_body(const FinalizeArgs &x, int bx)
         const long idx = (long)(bx - nb) * blockDim.x + threadIdx.x;
         const long n = (long)G * nx;
         if (idx < n) {
-            if (sizeof(R) == 8) {
-                Acc<R> A0, A2;
-                for (int t = 0; t < ntile; ++t) {
-                    A0.add(part[(size_t)(t * 2 + 0) * n + idx]);
-                    A2.add(part[(size_t)(t * 2 + 1) * n + idx]);
+            if constexpr (sizeof(R) == 8) {
+                // the tiles summed in order (tile count unrolled where it is a power of two
+                // up to 16: every load issued before the first addition), then A2 times the
+                // refined reciprocal of A0 (ratio64)
+                const double *p = reinterpret_cast<const double *>(part) + idx;
+                switch (ntile) {
+                case 1: f[idx] = sum_tiles_ratio<1>(p, n); break;
+                case 2: f[idx] = sum_tiles_ratio<2>(p, n); break;
+                case 4: f[idx] = sum_tiles_ratio<4>(p, n); break;
+                case 8: f[idx] = sum_tiles_ratio<8>(p, n); break;
+                case 16: f[idx] = sum_tiles_ratio<16>(p, n); break;
+                default: {
+                    double A0 = 0.0, A2 = 0.0;
+                    for (int t = 0; t < ntile; ++t) {
+                        A0 += p[(size_t)(t * 2) * n];
+                        A2 += p[(size_t)(t * 2 + 1) * n];
+                    }
+                    f[idx] = (A0 != 0.0) ? ratio64(A2, A0) : 1.0 / 3.0;
                 }
-                // A2 times the refined reciprocal of A0 (within an ulp of the quotient, a
-                // quarter of a division's FP64 operations), or the division where 1/A0
-                // leaves the normal range: in cold cells both angular sums are subnormal,
-                // where 1/A0 overflows while A2/A0 stays the ratio
-                f[idx] = (A0.s != (R)0) ? ratio64((double)A2.s, (double)A0.s) : 1.0 / 3.0;
+                }
             } else {
                 // FP32: the tiles' (high, low) pairs summed as unevaluated FP32 sums (an
                 // exact two-sum per high part, the low parts added plainly), then the ratio
-                // of the two moments in FP64, which leaves f one FP64 rounding instead of
-                // the FP32 roundings of the partials and of an FP32 division
-                const size_t lo = (size_t)ntile * 2 * n;
-                float S0 = 0.f, E0 = 0.f, S2 = 0.f, E2 = 0.f;
-                for (int t0 = 0; t0 < ntile; t0 += 8) {
-                    float h0[8], l0[8], h2[8], l2[8];   // loads in flight before the adds
-#pragma unroll
-                    for (int j = 0; j < 8; ++j) {
-                        if (t0 + j < ntile) {
-                            const size_t o = (size_t)((t0 + j) * 2) * n + idx;
-                            h0[j] = part[o];
-                            h2[j] = part[o + n];
-                            l0[j] = part[lo + o];
-                            l2[j] = part[lo + o + n];
-                        }
+                // of the two unevaluated sums to about 2^-46 (pair_ratio) instead of the FP32
+                // roundings of the partials and of an FP32 division
+                const float *p = reinterpret_cast<const float *>(part) + idx;
+                switch (ntile) {   // the tile count unrolled: no guards, loads in flight
+                case 1: f[idx] = sum_pairs_ratio<1>(p, n); break;
+                case 2: f[idx] = sum_pairs_ratio<2>(p, n); break;
+                case 4: f[idx] = sum_pairs_ratio<4>(p, n); break;
+                case 8: f[idx] = sum_pairs_ratio<8>(p, n); break;
+                case 16: f[idx] = sum_pairs_ratio<16>(p, n); break;
+                default: {
+                    const size_t lo = (size_t)ntile * 2 * n;
+                    float S0 = 0.f, E0 = 0.f, S2 = 0.f, E2 = 0.f;
+                    for (int t = 0; t < ntile; ++t) {
+                        const size_t o = (size_t)(t * 2) * n;
+                        two_sum_acc(S0, E0, p[o], p[lo + o]);
+                        two_sum_acc(S2, E2, p[o + n], p[lo + o + n]);
                     }
-#pragma unroll
-                    for (int j = 0; j < 8; ++j) {
-                        if (t0 + j < ntile) {
-                            two_sum_acc(S0, E0, h0[j], l0[j]);
-                            two_sum_acc(S2, E2, h2[j], l2[j]);
-                        }
-                    }
+                    f[idx] = pair_ratio(S2, E2, S0, E0);
                 }
-                const double a0 = (double)S0 + (double)E0, a2 = (double)S2 + (double)E2;
-                // FP32 partials are normal or subnormal floats: their FP64 sums are normal
-                f[idx] = (a0 != 0.0) ? a2 * rcp64(a0) : 1.0 / 3.0;
+                }
             }
         }
         return;

@@ -37,6 +37,79 @@ __device__ inline double ratio64(double a, double b)
     return a * fma(x, fma(e, e, e), x);
 }
 
+// (S2 + E2) / (S0 + E0) for unevaluated FP32 sums (|E| far below |S|) in FP32 arithmetic:
+// q = S2/S0 rounded, the remainder (S2 + E2) - q (S0 + E0) with the exact product q S0 =
+// ph + pl (S2 - ph is exact: ph is within a rounding of S2), d = remainder / (S0 + E0), and
+// q + d widened to FP64 (one FP64 addition): within about 2^-46 of the quotient.  Zero,
+// subnormal or non-finite S0 go to the FP64 form (a function never inlined); zero sums
+// give 1/3.
+static __device__ __noinline__ double pair_ratio_fp64(float S2, float E2, float S0, float E0)
+{
+    const double a0 = (double)S0 + (double)E0, a2 = (double)S2 + (double)E2;
+    return (a0 != 0.0) ? a2 / a0 : 1.0 / 3.0;
+}
+__device__ inline double pair_ratio(float S2, float E2, float S0, float E0)
+{
+    const unsigned e = (__float_as_uint(S0) >> 23) & 0xffu;
+    if (e == 0u || e == 0xffu) return pair_ratio_fp64(S2, E2, S0, E0);
+    const float q = __fdiv_rn(S2, S0);
+    const float ph = __fmul_rn(q, S0);
+    const float pl = __fmaf_rn(q, S0, -ph);
+    const float r = __fadd_rn(__fsub_rn(__fsub_rn(S2, ph), pl), __fsub_rn(E2, __fmul_rn(q, E0)));
+    const float d = __fdiv_rn(r, __fadd_rn(S0, E0));
+    return widen_f32(q) + widen_f32(d);
+}
+
+// f of one (group, cell) from NT direction tiles of FP64 partial moments (tile t's at
+// p[2 t n] and p[(2 t + 1) n]), summed in tile order; A2/A0 as A2 times the refined
+// reciprocal of A0 (a quarter of a division's FP64 operations), or the division where 1/A0
+// leaves the normal range (in cold cells both sums are subnormal, where 1/A0 overflows
+// while A2/A0 stays the ratio); zero sums give 1/3
+template <int NT>
+__device__ inline double sum_tiles_ratio(const double *__restrict__ p, size_t n)
+{
+    double a0[NT], a2[NT];
+#pragma unroll
+    for (int t = 0; t < NT; ++t) {
+        a0[t] = p[(size_t)(2 * t) * n];
+        a2[t] = p[(size_t)(2 * t + 1) * n];
+    }
+    double A0 = 0.0, A2 = 0.0;
+#pragma unroll
+    for (int t = 0; t < NT; ++t) {
+        A0 += a0[t];
+        A2 += a2[t];
+    }
+    return (A0 != 0.0) ? ratio64(A2, A0) : 1.0 / 3.0;
+}
+
+// forward declaration (defined below)
+__device__ inline void two_sum_acc(float &S, float &E, float hi, float lo);
+
+// f of one (group, cell) from NT direction tiles of FP32 (high, low) partial moments: p
+// points at tile 0's zeroth moment, tile t's moments at p[2 t n] and p[(2 t + 1) n], their
+// low parts NT 2 n further; every load is issued before the first addition
+template <int NT>
+__device__ inline double sum_pairs_ratio(const float *__restrict__ p, size_t n)
+{
+    float h0[NT], h2[NT], l0[NT], l2[NT];
+    const size_t lo = (size_t)NT * 2 * n;
+#pragma unroll
+    for (int t = 0; t < NT; ++t) {
+        h0[t] = p[(size_t)(2 * t) * n];
+        h2[t] = p[(size_t)(2 * t + 1) * n];
+        l0[t] = p[lo + (size_t)(2 * t) * n];
+        l2[t] = p[lo + (size_t)(2 * t + 1) * n];
+    }
+    float S0 = 0.f, E0 = 0.f, S2 = 0.f, E2 = 0.f;
+#pragma unroll
+    for (int t = 0; t < NT; ++t) {
+        two_sum_acc(S0, E0, h0[t], l0[t]);
+        two_sum_acc(S2, E2, h2[t], l2[t]);
+    }
+    return pair_ratio(S2, E2, S0, E0);
+}
+
 // (S, E) += hi + lo for unevaluated FP32 sums S + E: hi enters by an exact two-sum (Knuth),
 // its rounding error and lo go to E
 __device__ inline void two_sum_acc(float &S, float &E, float hi, float lo)
