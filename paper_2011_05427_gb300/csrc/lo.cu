@@ -686,14 +686,18 @@ __device__ void restrict_body(const RestrictCtx &x, int bx, int by)
 // an FP64 operation, the pipe that bounds these kernels on GB300.  The compensation
 // is summed in one pass, xi = dx (sum sigR F - sigR-bar sum F) + c (sum etaR E_R -
 // sum etaL E_L), which is the two-pass sum up to rounding relative to the sigR dx F terms.
-constexpr int kChunk = 32;
+constexpr int kChunk = 64;
 constexpr int kRP = 25;
+constexpr int kPartRows = 8;   // rows (warps) of a stage-1 block: kChunk / kPartRows members each
+constexpr size_t kPartSmem = sizeof(double) * kPartRows * 32 * (kRP + 1);
 
 
-// block (32, 4); grid (ceil((nx+1)/32), n_to * nchunk)
+// block (32, kPartRows); grid (ceil((nx+1)/32), n_to * nchunk); kPartSmem bytes of dynamic
+// shared memory
 __device__ void restrict_part_body(const Restrict2Ctx &x, int bx, int by)
 {
-    __shared__ double red[4][32][kRP + 1];
+    extern __shared__ __align__(16) double red_raw[];
+    double (*red)[32][kRP + 1] = reinterpret_cast<double (*)[32][kRP + 1]>(red_raw);
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int nx = x.nx, nf = nx + 1;
     const int i = bx * 32 + tx;
@@ -704,7 +708,7 @@ __device__ void restrict_part_body(const Restrict2Ctx &x, int bx, int by)
     double v[kRP];
 #pragma unroll
     for (int k = 0; k < kRP; ++k) v[k] = 0.0;
-    for (int p = pb + ty; p < pe; p += 4) {
+    for (int p = pb + ty; p < pe; p += kPartRows) {
         if (i < nx) {
             const size_t c = (size_t)p * nx + i;
             const double E = S.E[c];
@@ -750,13 +754,14 @@ __device__ void restrict_part_body(const Restrict2Ctx &x, int bx, int by)
 #pragma unroll
     for (int k = 0; k < kRP; ++k) red[ty][tx][k] = v[k];
     __syncthreads();
-    // the four rows' partials, value k by row k % 4: the additions are spread over the
-    // four warps (four sub-partitions' FP64 pipes); same order as a sum by one row
+    // the rows' partials, value k by row k % kPartRows: the additions are spread over the
+    // warps (all four sub-partitions' FP64 pipes); same order as a sum by one row
     if (i <= nx) {
         double *o = x.part + ((size_t)(P * x.nchunk + ch) * kRP) * nf + i;
-        for (int k = ty; k < kRP; k += 4) {
+        for (int k = ty; k < kRP; k += kPartRows) {
             double a = red[0][tx][k];
-            for (int y = 1; y < 4; ++y) a += red[y][tx][k];
+#pragma unroll
+            for (int y = 1; y < kPartRows; ++y) a += red[y][tx][k];
             o[(size_t)k * nf] = a;
         }
     }
@@ -1040,7 +1045,7 @@ __global__ void __launch_bounds__(512) k_restrict(RestrictCtx x)
     if (x.gate && *x.gate) return;
     restrict_body(x, blockIdx.x, blockIdx.y);
 }
-__global__ void __launch_bounds__(128) k_restrict_part(Restrict2Ctx x)
+__global__ void __launch_bounds__(32 * kPartRows) k_restrict_part(Restrict2Ctx x)
 {
     if (x.gate && *x.gate) return;
     restrict_part_body(x, blockIdx.x, blockIdx.y);
@@ -1070,7 +1075,7 @@ __global__ void __launch_bounds__(256) k_group_sum(GroupSumArgs a) { group_sum_b
         }                                                                                      \
     }
 TRT_BATCHED(k_restrict_b, RestrictCtx, 512, restrict_body(x, bx, by))
-TRT_BATCHED(k_restrict_part_b, Restrict2Ctx, 128, restrict_part_body(x, bx, by))
+TRT_BATCHED(k_restrict_part_b, Restrict2Ctx, 32 * kPartRows, restrict_part_body(x, bx, by))
 TRT_BATCHED(k_restrict_final_b, Restrict2Ctx, 32 * kRP, restrict_final_body(x, bx, by))
 TRT_BATCHED(k_grey_b, GreyCtx, 1024, grey_body(x))
 TRT_BATCHED(k_group_sum_b, GroupSumArgs, 256, group_sum_body(x, bx))
@@ -1223,8 +1228,12 @@ cudaError_t launch_restrict(const Problem &p, const Level &src, Level &dst)
     if (restrict_kind(p, src.n, dst.n, &KS) == 2) {
         const Restrict2Ctx y = make_restrict2_ctx(p, src, dst);
         dim3 g1((p.nx + 1 + 31) / 32, dst.n * y.nchunk);
-        k_restrict_part<<<g1, dim3(32, 4), 0, p.stream>>>(y);
-        cudaError_t e = cudaGetLastError();
+        cudaError_t e = cudaFuncSetAttribute(k_restrict_part,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)kPartSmem);
+        if (e != cudaSuccess) return e;
+        k_restrict_part<<<g1, dim3(32, kPartRows), kPartSmem, p.stream>>>(y);
+        e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         k_restrict_final<<<dim3((p.nx + 1 + 31) / 32, dst.n), dim3(32, kRP), 0, p.stream>>>(y);
         return cudaGetLastError();
@@ -1253,7 +1262,11 @@ cudaError_t launch_restrict_b(int KS, const int *meta, int N, const RestrictCtx 
 cudaError_t launch_restrict_part_b(const int *meta, int N, const Restrict2Ctx *xs, int grid,
                                    cudaStream_t st)
 {
-    k_restrict_part_b<<<grid, dim3(32, 4), 0, st>>>(meta, N, xs);
+    cudaError_t e = cudaFuncSetAttribute(k_restrict_part_b,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kPartSmem);
+    if (e != cudaSuccess) return e;
+    k_restrict_part_b<<<grid, dim3(32, kPartRows), kPartSmem, st>>>(meta, N, xs);
     return cudaGetLastError();
 }
 
