@@ -312,15 +312,20 @@ class Solver:
         return dict(n_ti=st.n_ti, n_c=st.n_c, n_lo=st.n_lo, n_outer=st.n_outer, ms=st.ms,
                     status=rc, n_kernels=st.n_kernels)
 
-    def moments(self) -> Dict[str, np.ndarray]:
+    def moments(self, groups=True) -> Dict[str, np.ndarray]:
+        """T, the grey E and F and, with groups, the group E_g and F_g of the current state
+        (trt_moments; groups=False reads only the cell and face fields of the grey level)."""
         T = np.zeros(self.nx)
-        Eg = np.zeros((self.G, self.nx))
-        Fg = np.zeros((self.G, self.nx + 1))
+        Eg = np.zeros((self.G, self.nx)) if groups else None
+        Fg = np.zeros((self.G, self.nx + 1)) if groups else None
         E = np.zeros(self.nx)
         F = np.zeros(self.nx + 1)
         self._check(lib().trt_moments(self.h, _np_dp(T), _np_dp(Eg), _np_dp(Fg), _np_dp(E),
                                       _np_dp(F)))
-        return dict(T=T, Eg=Eg, Fg=Fg, E=E, F=F)
+        out = dict(T=T, E=E, F=F)
+        if groups:
+            out.update(Eg=Eg, Fg=Fg)
+        return out
 
     def intensity(self):
         """(I [M][nx][2][G], f [G][nx]) as FP64 numpy arrays (group padding dropped)."""
