@@ -61,26 +61,61 @@ __device__ inline double pair_ratio(float S2, float E2, float S0, float E0)
 }
 
 // f of one (group, cell) from NT direction tiles of FP64 partial moments (tile t's at
-// p[2 t n] and p[(2 t + 1) n]), summed in tile order; A2/A0 as A2 times the refined
-// reciprocal of A0 (a quarter of a division's FP64 operations), or the division where 1/A0
-// leaves the normal range (in cold cells both sums are subnormal, where 1/A0 overflows
-// while A2/A0 stays the ratio); zero sums give 1/3
+// p[2 t n] and p[(2 t + 1) n]).  GB300 adds FP64 numbers at 1/64 of the FP32 rate, so the
+// tiles are added as fixed-point integers on the integer pipes: every value's significand
+// (hidden bit included) shifted to the largest exponent emax of the element's 2 NT values
+// and summed exactly in 64 bits (at most 16 values below 2^53: no overflow); each value
+// loses only its bits below 2^(emax - 52), so each sum is within NT units of the largest
+// value's last place -- order-independent, no FP64 addition.  A2/A0 then is the ratio of
+// the two integer sums (the common scale cancels): two conversions and A2 times the refined
+// reciprocal of A0.  Subnormal values enter with their own significand at the least
+// exponent (exactly their value); a zero zeroth sum gives 1/3; elements holding an infinity
+// or NaN take the FP64 sum (in tile order) and division.
+static __device__ __noinline__ double sum_tiles_ratio_fp64(const double *__restrict__ p,
+                                                           size_t n, int nt)
+{
+    double A0 = 0.0, A2 = 0.0;
+    for (int t = 0; t < nt; ++t) {
+        A0 += p[(size_t)(2 * t) * n];
+        A2 += p[(size_t)(2 * t + 1) * n];
+    }
+    return (A0 != 0.0) ? A2 / A0 : 1.0 / 3.0;
+}
+__device__ inline long long fixed_point(unsigned long long b, int emax)
+{
+    int e = (int)((b >> 52) & 0x7ffull);
+    unsigned long long M = b & 0xfffffffffffffull;
+    if (e == 0)
+        e = 1;   // subnormal (or zero): significand without the hidden bit, exponent 1
+    else
+        M |= 1ull << 52;
+    const int d = emax - e;
+    if (d > 63) return 0;
+    const long long v = (long long)(M >> d);
+    return (b >> 63) ? -v : v;
+}
 template <int NT>
 __device__ inline double sum_tiles_ratio(const double *__restrict__ p, size_t n)
 {
-    double a0[NT], a2[NT];
+    unsigned long long b0[NT], b2[NT];
 #pragma unroll
     for (int t = 0; t < NT; ++t) {
-        a0[t] = p[(size_t)(2 * t) * n];
-        a2[t] = p[(size_t)(2 * t + 1) * n];
+        b0[t] = (unsigned long long)__double_as_longlong(p[(size_t)(2 * t) * n]);
+        b2[t] = (unsigned long long)__double_as_longlong(p[(size_t)(2 * t + 1) * n]);
     }
-    double A0 = 0.0, A2 = 0.0;
+    int emax = 1;   // subnormal values count at exponent 1
+#pragma unroll
+    for (int t = 0; t < NT; ++t)
+        emax = max(emax, max((int)((b0[t] >> 52) & 0x7ffull), (int)((b2[t] >> 52) & 0x7ffull)));
+    if (emax == 0x7ff) return sum_tiles_ratio_fp64(p, n, NT);
+    long long S0 = 0, S2 = 0;
 #pragma unroll
     for (int t = 0; t < NT; ++t) {
-        A0 += a0[t];
-        A2 += a2[t];
+        S0 += fixed_point(b0[t], emax);
+        S2 += fixed_point(b2[t], emax);
     }
-    return (A0 != 0.0) ? ratio64(A2, A0) : 1.0 / 3.0;
+    if (S0 == 0) return 1.0 / 3.0;
+    return ratio64(__ll2double_rn(S2), __ll2double_rn(S0));
 }
 
 // forward declaration (defined below)
