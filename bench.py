@@ -179,11 +179,11 @@ FP64_INST_PER_UPDATE = {"strip": 17.6, "pair": 13.5}
 # `sha` and the tuned tile (D, shape) is the captured one.
 TRAFFIC = {
     # k_prescale64 + k_sweep_pair<4,2> + k_sweep_finalize<double>: the t, s scratch and the
-    # 16 partial-moment tiles make it 1.72 x the algorithmic bytes (FP64-bound, not HBM)
-    "sweep_fp64": {"files": ("sweep64.cu", "sweep.cu"), "sha": "e14763fc5f6fec5a", "tile": (4, 4),
-                   "bytes": 8201472 + 785856768 + 881715968 + 131645952 + 573696},
-    "sweep_fp32": {"files": ("sweepf.cu", "sweep.cu"), "sha": "29aacd9f5b8a6ba4", "tile": (16, 0),
-                   "bytes": 270045184 + 242778112 + 33105664 + 0},
+    # 16 partial-moment tiles make it 1.70 x the algorithmic bytes (FP64-bound, not HBM)
+    "sweep_fp64": {"files": ("sweep64.cu", "sweep.cu"), "sha": "d3297fe5e08672f6", "tile": (4, 4),
+                   "bytes": 8201472 + 785473536 + 881783040 + 131673600 + 1181184},
+    "sweep_fp32": {"files": ("sweepf.cu", "sweep.cu"), "sha": "c7e5b75c05e6ea67", "tile": (16, 0),
+                   "bytes": 270064640 + 242938368 + 33097984 + 256},
 }
 
 
