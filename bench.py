@@ -574,7 +574,7 @@ def paper_tables_run(local=0):
             return tot, sec
         tot, sec = run(cyc)
         per = lo_solves_per_cycle(grids, cyc)
-        row = {"table": int(t), "dt_ns": float(dt_ns), "Gamma": G, "grids": grids,
+        row = {"table": int(t), "dt_ns": float(dt_ns), "Gamma": int(Gam), "grids": grids,
                "cycle_printed": printed, "cycle": cyc, "l_max": int(lmax),
                "ours": tot, "paper": {"N_ti": int(nti), "N_c": int(nc), "N_lo": int(nlo)},
                "N_lo_per_cycle_is_schedule": tot["N_lo"] == per * tot["N_c"], "run_s": sec}
@@ -585,11 +585,11 @@ def paper_tables_run(local=0):
 
 
 def adaptive_cycle_run(local=0):
-    """Fixed V, W, F cycles against the per-step controller (`cycles.CycleController`,
-    candidates V/4, W/2, F/2) on Sec. 6's test with the 7-grid hierarchy of Table 1 (150
-    steps of 0.02 ns, eps 1e-6) and on fc_1024 (20 steps of 1e-3 sh, eps 1e-8), plain FP64:
-    wall time of the whole run (host clock around the steps, synchronised), counters, and
-    the controller's picks."""
+    """Fixed V (l_max 3), W and F (l_max 1) cycles against the per-step controller
+    (`cycles.CycleController`, candidates V/3, V/2, V/4, F/1, W/1) on Sec. 6's test with the
+    7-grid hierarchy of Table 1 (150 steps of 0.02 ns, eps 1e-6) and on fc_1024 (20 steps of
+    1e-3 sh, eps 1e-8), plain FP64: wall time of the whole run (host clock around the steps,
+    synchronised), counters, and the controller's picks."""
     import dataclasses
     import torch
     from paper_2011_05427_gb300 import trt
@@ -597,7 +597,8 @@ def adaptive_cycle_run(local=0):
     cases = [("fc_paper_gamma7", dataclasses.replace(W.fc_paper(0.02),
                                                      levels=[256, 128, 32, 16, 8, 4, 1]), 150),
              ("fc_1024", W.fc_1024("V"), 20)]
-    cands = (("V", 4), ("W", 2), ("F", 2))
+    cands = (("V", 3), ("V", 2), ("V", 4), ("F", 1), ("W", 1))
+    fixed = {"V": 3, "W": 1, "F": 1}
     out = []
     for name, cfg, steps in cases:
         res = {"workload": name, "steps": steps}
@@ -614,7 +615,7 @@ def adaptive_cycle_run(local=0):
                     key = f"{st['cycle']}{st['l_max']}"
                     picks[key] = picks.get(key, 0) + 1
                 else:
-                    st = s.step(cfg.dt, mode, dict(cands)[mode], cfg.eps)
+                    st = s.step(cfg.dt, mode, fixed[mode], cfg.eps)
                 tot["N_ti"] += st["n_ti"]
                 tot["N_c"] += st["n_c"]
                 tot["N_lo"] += st["n_lo"]
