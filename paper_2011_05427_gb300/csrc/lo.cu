@@ -935,14 +935,162 @@ __device__ inline void grey_newton_cell(const GreyArgs &a, const Level &g, int h
     sL = iL;
 }
 
-// T at cell i from the grey solution; the bad-value test and the norms' terms
+// The grey level's tridiagonal system (n >= 2) by P = min(128, n/2, block) threads: GB300
+// runs a warp's FP64 instructions on its own sub-partition's FP64 pipe only, so the group
+// systems' one-warp partitioned elimination (32 chunks of ~16 rows: a serial chain of ~500
+// FP64 instructions at 64 cycles each) would keep the SM's other three pipes idle for
+// ~20 us on the grey level, where a single system is solved at a time.  Here every
+// thread eliminates a chunk of ~4 rows (the modified Thomas pass down and up the chunk of
+// tri_solve: rows coupled only to the chunk's first and last unknowns), the 2P chunk-
+// boundary rows are solved by parallel cyclic reduction in shared memory (rows kept with
+// unit diagonals, ceil(log2 2P) levels of one block barrier each), and every thread
+// back-substitutes its chunk's interior.  sm: PL, PR, GD [n + 1], Ap, Cp, Dp [n], then the
+// reduced rows' A, C, D in two buffers [2][3][2P].  All threads of the block call it; the
+// solution is left in Dp.
+__host__ __device__ inline int grey_chunks(int n, int block)
+{
+    int P = n / 2;
+    if (P > 128) P = 128;
+    if (P > block) P = block;
+    return P < 1 ? 1 : P;
+}
+
+__device__ void grey_tri_solve(const LoCtx &x, double *sm, int n)
+{
+    const int P = grey_chunks(n, (int)blockDim.x), nr = 2 * P;
+    double *PL = sm, *PR = PL + (n + 1), *GD = PR + (n + 1);
+    double *Ap = GD + (n + 1), *Cp = Ap + n, *Dp = Cp + n;
+    double *rb = Dp + n;   // [2][3][nr]
+    const int t = threadIdx.x;
+    for (int f = t; f <= n; f += blockDim.x) {
+        double pl, pr, gd;
+        face_coef<double>(x, 0, f, pl, pr, gd);
+        PL[f] = pl;
+        PR[f] = pr;
+        GD[f] = gd;
+        if (f < n) cell_row<double>(x, 0, f, Ap[f], Dp[f]);
+    }
+    __syncthreads();
+    const int r0 = (t < P) ? (int)(((long long)t * n) / P) : n;
+    const int r1 = (t < P) ? (int)(((long long)(t + 1) * n) / P) : n;
+    const int m = r1 - r0;
+    if (t < P) {
+        // down the chunk: row k >= 1 coupled to x_{r0} (a) and x_{r0+k+1} (c); row 0 to
+        // x_{r0-1} and x_{r0+1}
+        double PLi = PL[r0], PRi = PR[r0], GDi = GD[r0];
+        double ap = 0.0, cp = 0.0, dp = 0.0;
+        for (int k = 0; k < m; ++k) {
+            const int i = r0 + k;
+            const double PL1 = PL[i + 1], PR1 = PR[i + 1], GD1 = GD[i + 1];
+            const double di = Ap[i] + PL1 + PRi;
+            const double rh = Dp[i] - GD1 + GDi;
+            const double lo = (i > 0) ? -PLi : 0.0;
+            const double up = (i < n - 1) ? -PR1 : 0.0;
+            if (k < 2) {
+                const double r = rcp64(di);
+                ap = lo * r;
+                cp = up * r;
+                dp = rh * r;
+            } else {
+                const double r = rcp64(di - lo * cp);
+                dp = r * (rh - lo * dp);
+                ap = -r * lo * ap;
+                cp = r * up;
+            }
+            Ap[i] = ap;
+            Cp[i] = cp;
+            Dp[i] = dp;
+            PLi = PL1;
+            PRi = PR1;
+            GDi = GD1;
+        }
+        // up the chunk: rows 1 .. m-2 coupled to x_{r0} and x_{r1-1}; row 0 to x_{r0-1}
+        // and x_{r1-1}
+        if (m >= 3) {
+            for (int k = m - 3; k >= 1; --k) {
+                const int i = r0 + k;
+                const double ck = Cp[i];
+                Dp[i] = Dp[i] - ck * Dp[i + 1];
+                Ap[i] = Ap[i] - ck * Ap[i + 1];
+                Cp[i] = -ck * Cp[i + 1];
+            }
+            const double c0 = Cp[r0];
+            const double r = rcp64(1.0 - c0 * Ap[r0 + 1]);
+            Dp[r0] = r * (Dp[r0] - c0 * Dp[r0 + 1]);
+            Ap[r0] = r * Ap[r0];
+            Cp[r0] = -r * c0 * Cp[r0 + 1];
+        }
+        // reduced rows 2t (the chunk's first row) and 2t + 1 (its last)
+        rb[2 * t] = Ap[r0];
+        rb[nr + 2 * t] = Cp[r0];
+        rb[2 * nr + 2 * t] = Dp[r0];
+        rb[2 * t + 1] = Ap[r1 - 1];
+        rb[nr + 2 * t + 1] = Cp[r1 - 1];
+        rb[2 * nr + 2 * t + 1] = Dp[r1 - 1];
+    }
+    __syncthreads();
+    // parallel cyclic reduction of the 2P reduced rows: a level eliminates the neighbours at
+    // distance s with the factors -A and -C and divides by the new diagonal
+    int cur = 0;
+    for (int s = 1; s < nr; s <<= 1) {
+        const double *A = rb + (size_t)cur * 3 * nr, *C = A + nr, *D = C + nr;
+        double *nA = rb + (size_t)(cur ^ 1) * 3 * nr, *nC = nA + nr, *nD = nC + nr;
+        if (t < P) {
+#pragma unroll
+            for (int j = 2 * t; j <= 2 * t + 1; ++j) {
+                const bool hl = j >= s, hu = j + s < nr;
+                const double lA = hl ? A[j - s] : 0.0, lC = hl ? C[j - s] : 0.0;
+                const double lD = hl ? D[j - s] : 0.0;
+                const double uA = hu ? A[j + s] : 0.0, uC = hu ? C[j + s] : 0.0;
+                const double uD = hu ? D[j + s] : 0.0;
+                const double al = -A[j], ga = -C[j];
+                const double r = rcp64(1.0 + al * lC + ga * uA);
+                nA[j] = al * lA * r;
+                nC[j] = ga * uC * r;
+                nD[j] = (D[j] + al * lD + ga * uD) * r;
+            }
+        }
+        cur ^= 1;
+        __syncthreads();
+    }
+    // back substitution of the chunk's interior rows
+    if (t < P) {
+        const double *D = rb + (size_t)cur * 3 * nr + 2 * nr;
+        const double x0 = D[2 * t], x1 = D[2 * t + 1];
+        for (int k = 1; k < m - 1; ++k) {
+            const int i = r0 + k;
+            Dp[i] = Dp[i] - Ap[i] * x0 - Cp[i] * x1;
+        }
+        Dp[r0] = x0;
+        Dp[r1 - 1] = x1;
+    }
+    __syncthreads();
+}
+
+// the grey level's outputs from the solution in Dp (grey_tri_solve's layout): E, the face
+// fluxes F_f = GD_f + PL_f E_{f-1} - PR_f E_f and the boundary face energies
+__device__ void grey_outputs(const LoCtx &x, const double *sm, int n)
+{
+    const double *PL = sm, *PR = PL + (n + 1), *GD = PR + (n + 1);
+    const double *Dp = GD + (n + 1) + 2 * n;
+    for (int f = threadIdx.x; f <= n; f += blockDim.x) {
+        if (f < n) x.L.E[f] = Dp[f];
+        double Fv = GD[f];
+        if (f > 0) Fv += PL[f] * Dp[f - 1];
+        if (f < n) Fv -= PR[f] * Dp[f];
+        x.L.F[f] = Fv;
+        if (f == 0) x.L.Eb0[0] = x.L.Ein0[0] + (Fv - x.L.Fin0[0]) * rcp64(kC * x.L.C0[0]);
+        if (f == n) x.L.EbX[0] = x.L.EinX[0] + (Fv - x.L.FinX[0]) * rcp64(kC * x.L.CX[0]);
+    }
+}
+
+// T at cell i from the grey solution E; the bad-value test and the norms' terms
 __device__ inline void grey_update_cell(const GreyArgs &a, const Level &g, int i, double sL,
-                                        unsigned long long (&v)[kGreyNV])
+                                        double E, unsigned long long (&v)[kGreyNV])
 {
     const unsigned long long kInfBits = 0x7ff0000000000000ull;
     const double cvdt = a.cvdt;
     const double Ts = a.Tstar[i];
-    const double E = g.E[i];
     const double T = Ts + (kC * g.sig[i] * E - 2.0 * g.emis[i] - cvdt * (Ts - a.Told[i])) * sL;
     a.T[i] = T;
     const long long tb = __double_as_longlong(T);
@@ -971,7 +1119,7 @@ __device__ void grey_body(const GreyCtx &x)
     double *ss = sa + nx;        // source w Q* - (1-w) cv (T* - Told)/dt
     double *sL = ss + nx;        // 1 / Lambda
     double *red = sL + nx;       // [kGreyRed] block maxima
-    double *wsm = red + kGreyRed;   // warp-solver scratch
+    double *wsm = red + kGreyRed;   // solver scratch (grey_tri_solve)
     const GreyArgs &a = x.a;
     const Level &g = x.lo.L;
     for (int i = threadIdx.x; i < nx; i += blockDim.x) {
@@ -983,15 +1131,19 @@ __device__ void grey_body(const GreyCtx &x)
     LoCtx lc = x.lo;
     lc.a_cell = sa;
     lc.s_cell = ss;
-    const bool staged = nx >= 2;
-    if (staged) lo_stage<double>(lc, 0, wsm, x.mmax, threadIdx.x, blockDim.x);
-    __syncthreads();
-    if (threadIdx.x < 32) warp_lo_solve<double>(lc, 0, wsm, x.mmax, staged);
-    __syncthreads();
+    const double *Esol = wsm + 3 * (size_t)(nx + 1) + 2 * (size_t)nx;   // grey_tri_solve's Dp
+    if (nx >= 2) {
+        grey_tri_solve(lc, wsm, nx);
+        grey_outputs(lc, wsm, nx);
+    } else {
+        if (threadIdx.x < 32) warp_lo_solve<double>(lc, 0, wsm, x.mmax, false);
+        __syncthreads();
+        Esol = g.E;
+    }
     // v: bad flag, max|T - Tcyc|, max|T|, max|E - Ecyc|, max|E|, max|T - Tphase|,
     // max|E - Ephase| as non-negative encodings (flags[0 .. 6])
     unsigned long long v[kGreyNV] = {};
-    for (int i = threadIdx.x; i < nx; i += blockDim.x) grey_update_cell(a, g, i, sL[i], v);
+    for (int i = threadIdx.x; i < nx; i += blockDim.x) grey_update_cell(a, g, i, sL[i], Esol[i], v);
     block_max_bits(v, reinterpret_cast<unsigned long long *>(red));
     if (threadIdx.x == 0) {
         if (v[0] != 0ull) a.flags[0] = 1.0;
@@ -1294,7 +1446,9 @@ GreyCtx make_grey_ctx(const Problem &p, const Level &g, const GreyArgs &a)
 static void grey_launch_shape(int nx, int &bs, size_t &sm)
 {
     bs = std::min(1024, std::max(32, (nx + 31) / 32 * 32));
-    sm = sizeof(double) * (3 * (size_t)nx + kGreyRed + 6 * 32 * (size_t)lo_mmax(nx));
+    // Newton terms, block maxima, then grey_tri_solve's rows and reduced rows
+    sm = sizeof(double) * (3 * (size_t)nx + kGreyRed + 3 * (size_t)(nx + 1) + 3 * (size_t)nx +
+                           6 * 256);
 }
 
 cudaError_t launch_grey(const Problem &p, const Level &g, const GreyArgs &a)
