@@ -862,7 +862,8 @@ __device__ void restrict_final_body(const Restrict2Ctx &x, int bx, int by)
 // the order of the doubles is the unsigned order of their bit patterns, so the reduction
 // runs on the integer pipes (a warp-wide FP64 max takes a sub-partition's FP64 pipe for 64
 // cycles on GB300).  NaN maps to 0, the value fmax would keep.  red: kGreyRed slots, at
-// least 32 per value; the maxima are returned to every thread.
+// least 32 per value; the maxima are returned to thread 0 (each warp reduces its lanes by
+// shuffles, then warp 0 reduces the warps' results the same way).
 constexpr int kGreyNV = 7;
 constexpr int kGreyRed = 32 * kGreyNV;
 
@@ -888,11 +889,13 @@ __device__ inline void block_max_bits(unsigned long long (&v)[kGreyNV], unsigned
 #pragma unroll
         for (int k = 0; k < kGreyNV; ++k) red[k * 32 + warp] = v[k];
     __syncthreads();
+    if (warp == 0) {
 #pragma unroll
-    for (int k = 0; k < kGreyNV; ++k) {
-        unsigned long long r = 0ull;
-        for (int w = 0; w < nw; ++w) r = umax64(r, red[k * 32 + w]);
-        v[k] = r;
+        for (int k = 0; k < kGreyNV; ++k) {
+            unsigned long long r = (lane < nw) ? red[k * 32 + lane] : 0ull;
+            for (int o = 16; o > 0; o >>= 1) r = umax64(r, __shfl_xor_sync(0xffffffffu, r, o));
+            v[k] = r;
+        }
     }
 }
 
