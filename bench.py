@@ -436,6 +436,40 @@ def closure_bench(local, ms_fp64, steps=10):
             "max_rel_T_closure_vs_plain": dT, "steps": steps, "l_max": cfg.l_max}
 
 
+def closure_config5_run(local=0, n_slabs=20, steps=100, eval_steps=200):
+    """The learned closure at the stated size: snapshots of n_slabs x steps = 2000 converged
+    steps of batch-family slabs (cells, angles, inflow temperature and opacity scale drawn
+    as in batch_256; 1024 groups on the fc_1024 hierarchy; FP32 sweeps), 16384 random rows
+    per step, the network trained by its tensor-core kernels (two passes over the rows),
+    then fc_1024 stepped eval_steps times with FP32 sweeps at their tuned l_max with and
+    without the warm start."""
+    import dataclasses
+    import torch
+    from paper_2011_05427_gb300 import closure
+    dev = f"cuda:{local}"
+    t0 = time.perf_counter()
+    X, Y = closure.collect(closure.training_slabs(n_slabs), steps, 16384, precision="sweep32",
+                           device=dev)
+    torch.cuda.synchronize()
+    t_collect = time.perf_counter() - t0
+    iters = max(1000, 2 * len(X) // 8192)
+    t0 = time.perf_counter()
+    net, hist = closure.train(X, Y, iters=iters, batch=8192, lr=1e-3, device=dev)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    cfg = dataclasses.replace(W.fc_1024("V"), l_max=tuned_lmax("sweep32", "V"))
+    r = closure.compare(cfg, net, eval_steps, precision="sweep32", device=dev)
+    a, b = r["plain"], r["closure"]
+    dT = float(np.max(np.abs(a["state"]["T"] - b["state"]["T"]) / a["state"]["T"]))
+    return {"training": {"slab_steps": n_slabs * steps, "rows": int(len(X)), "iters": iters,
+                         "loss_first_last": [hist[0][1], hist[-1][1]],
+                         "collect_s": t_collect, "train_s": t_train},
+            "eval_steps": eval_steps, "l_max": cfg.l_max,
+            "plain": {k: a[k] for k in ("n_ti", "n_c", "n_lo", "ms_per_step")},
+            "closure": {k: b[k] for k in ("n_ti", "n_c", "n_lo", "ms_per_step")},
+            "max_rel_T_closure_vs_plain": dT}
+
+
 def fc4096_bench(local, steps=10):
     """fc_4096 (1000 cells, double S64 = 128 directions, 4096 groups, 7 grids, W-cycle
     l_max 2): FP32 sweeps against the plain FP64 path, step by step from the same start;
@@ -974,6 +1008,9 @@ def main():
     ap.add_argument("--adaptive-cycle", action="store_true",
                     help="fixed V/W/F cycles against the per-step cycle controller (one JSON "
                          "line)")
+    ap.add_argument("--closure-config5", action="store_true",
+                    help="the learned closure trained on 2000 batch-family steps and evaluated "
+                         "over 200 fc_1024 steps (one JSON line)")
     ap.add_argument("--lmax-sweep", action="store_true",
                     help="ms per converged fc_1024 step for each form, cycle and l_max (one "
                          "JSON line)")
@@ -993,6 +1030,9 @@ def main():
         return
     if args.lmax_sweep:
         print(json.dumps({"lmax_sweep": lmax_sweep_run()}))
+        return
+    if args.closure_config5:
+        print(json.dumps({"closure_config5": closure_config5_run()}))
         return
     if args.profile_sweep:
         from paper_2011_05427_gb300 import trt

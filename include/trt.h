@@ -156,7 +156,8 @@ int trt_step(trt_handle *h, double dt_sh, const trt_cycle *cycle, trt_stats *sta
  * solve).  Synchronises the stream. */
 int trt_moments(trt_handle *h, double *T, double *Eg, double *Fg, double *E, double *F);
 
-/* Host copy of the intensity [M][nx][2][ldG] as FP64 and the QD factors f_g [G][nx]. */
+/* Host copy of the intensity [M][nx][2][ldG] as FP64 and the QD factors f_g [G][nx]; either
+ * pointer may be NULL (that array is not copied). */
 int trt_intensity(trt_handle *h, double *I, double *f);
 
 /* Replace the state (host arrays, any may be NULL): temperature, E_g, F_g, intensity

@@ -43,7 +43,7 @@ def collect(slabs, steps, rows_per_step, seed=0, precision="fp64", device="cuda:
             T = torch.as_tensor(s.moments()["T"], dtype=torch.float64, device=s.device)
             x = _features(s, T).cpu().numpy()
             s.step(cfg.dt, cfg.cycle, cfg.l_max, cfg.eps)
-            f = s.intensity()[1].reshape(-1)
+            f = s.qd_factors().reshape(-1)
             idx = r.choice(f.size, min(rows_per_step, f.size), replace=False)
             xs.append(x[idx])
             ys.append(f[idx].astype(np.float32))

@@ -327,6 +327,12 @@ class Solver:
             out.update(Eg=Eg, Fg=Fg)
         return out
 
+    def qd_factors(self):
+        """The cell QD factors f [G][nx] of the last sweep (FP64 numpy array)."""
+        f = np.zeros((self.G, self.nx))
+        self._check(lib().trt_intensity(self.h, None, _np_dp(f)))
+        return f
+
     def intensity(self):
         """(I [M][nx][2][G], f [G][nx]) as FP64 numpy arrays (group padding dropped)."""
         I = np.zeros((self.M, self.nx, 2, self.ldG))
