@@ -438,12 +438,16 @@ def test_restrict_zero_weights(trt, orc, n_from, n_to, fine):
     assert np.array_equal(got["Esum"][0, 30:36], np.zeros(6))
 
 
-@pytest.mark.parametrize("nx,have_prev,cut", [(1, 0, 1e-7), (30, 1, 1e-7), (500, 0, 1e-7),
-                                              (1000, 1, 1e-7), (1000, 1, 0.0)])
+@pytest.mark.parametrize("nx,have_prev,cut", [(1, 0, 1e-7), (2, 1, 0.0), (3, 0, 1e-7),
+                                              (5, 1, 1e-7), (30, 1, 1e-7), (257, 1, 0.0),
+                                              (500, 0, 1e-7), (1000, 1, 1e-7), (1000, 1, 0.0),
+                                              (2048, 1, 0.0)])
 def test_grey_newton_parity(trt, orc, nx, have_prev, cut):
     """The grey Newton step against the oracle's, with and without a secant; the previous
     temperatures put cells on both sides of the cross-grid cut-off and some exactly at T*
-    (no secant at any cut-off)."""
+    (no secant at any cut-off).  Cell counts from 1 to 2048 give the grey solve one chunk of
+    2 or 3 rows, a few chunks, and 128 chunks of 2 to 16 rows; T, E, the face fluxes and the
+    boundary energies are compared."""
     r = W.rng(5000 + nx)
     h = W.random_h(r, nx)
     lv = random_level(r, 1, nx)
@@ -470,6 +474,10 @@ def test_grey_newton_parity(trt, orc, nx, have_prev, cut):
     if not bad:
         assert rel(T.cpu().numpy(), oT) < 1e-11
         assert rel(sol["E"].cpu().numpy()[0], oE) < 1e-11
+        F = sol["F"].cpu().numpy()[0]
+        assert np.max(np.abs(F - oF)) < 1e-11 * np.max(np.abs(oF))   # F changes sign
+        assert rel(sol["Eb0"].cpu().numpy()[0], oEb0) < 1e-11
+        assert rel(sol["EbX"].cpu().numpy()[0], oEbX) < 1e-11
 
 
 # ---------------------------------------------------------------------------- helpers
