@@ -98,12 +98,17 @@ __device__ inline double texp(double x, const double *tab, const ExpConsts &c)
 
 // FP32 -> FP64 without the FP64 pipe (GB300 converts there): a normal float is widened
 // with integer instructions (sign, exponent rebiased by 1023 - 127 = 896, mantissa shifted
-// by 29: exact); zero, subnormal, infinite and NaN values convert.
+// by 29: exact), a zero keeps its sign; subnormal, infinite and NaN values convert, in a
+// function that is never inlined (a branch around the conversion, not a predicated
+// conversion on every call).
+static __device__ __noinline__ double widen_f32_convert(float q) { return (double)q; }
 __device__ inline double widen_f32(float q)
 {
     const unsigned u = __float_as_uint(q);
     const unsigned e = (u >> 23) & 0xffu;
-    if (e == 0u || e == 0xffu) return (double)q;
+    if ((u & 0x7fffffffu) == 0u)
+        return __longlong_as_double((long long)((unsigned long long)u << 32));   // +0 or -0
+    if (e == 0u || e == 0xffu) return widen_f32_convert(q);
     const unsigned long long b = ((unsigned long long)(u & 0x80000000u) << 32) |
                                  ((unsigned long long)(e + 896u) << 52) |
                                  ((unsigned long long)(u & 0x7fffffu) << 29);
