@@ -10,7 +10,7 @@ hierarchy + grey LOQD/MEB Newton).  value = sweep cell-angle-group updates per s
 wall time over the timed steps (all ranks); ms_per_step = mean time of a converged step.
 
 python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                [--precision fp64|mixed|sweep32|lo32] [--cycle V|W] [--no-compare]
+                [--precision fp64|mixed|sweep32|lo32|lopair|sweep32_lopair] [--cycle V|W] [--no-compare]
 Under torchrun each rank runs an independent replica of the slab (replicas only: the
 solver's data path has no cross-GPU exchange on one slab).
 """
@@ -285,7 +285,7 @@ def sweep_roofline(trt, s, cfg, fp32=False, local=0, reps=20):
 def tuned_lmax(precision, cycle):
     if cycle != "V":
         return 1
-    return 3 if precision in ("fp64", "lo32") else 2
+    return 3 if precision in ("fp64", "lo32", "lopair") else 2
 
 
 def timed_steps(trt, cfg, precision, cycle, steps, warmup, local, ws, clocks=False,
@@ -984,7 +984,8 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed", "sweep32", "lo32"])
+    ap.add_argument("--precision", default="fp64",
+                    choices=["fp64", "mixed", "sweep32", "lo32", "lopair", "sweep32_lopair"])
     ap.add_argument("--cycle", default="V", choices=["V", "W", "F"])
     ap.add_argument("--no-compare", dest="compare", action="store_false",
                     help="skip the comparison runs (other cycle, FP32 sweeps, MLP, closure, "

@@ -56,6 +56,9 @@ extern "C" {
 #define TRT_LO_FP32      2   /* fine and coarse group LOQD solves in FP32                     */
 #define TRT_MIXED        3   /* both; opacities, restriction, grey LOQD, MEB Newton and the
                                 convergence checks stay FP64                                 */
+#define TRT_LO_PAIR      4   /* fine and coarse group LOQD solves in FP32-pair arithmetic
+                                (~47 significant bits, FP32's exponent range; FP64 in and
+                                out); excludes TRT_LO_FP32; with TRT_SWEEP_FP32: 5           */
 
 /* ---- cycle types (Sec. 4, Fig. 1) ---- */
 #define TRT_CYCLE_V 0   /* S empty: two-grid method on any hierarchy                      */

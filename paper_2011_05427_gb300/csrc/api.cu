@@ -83,6 +83,8 @@ void carve(trt_handle *h, Carver &c)
     p.e2tab = c.take<double>(32);
     p.lo_slot = reinterpret_cast<int *>(c.take<double>((nx + 2) / 2));
     p.otab = c.take<double>(otab_doubles((int)G));
+    p.otabp = lo_pair(p.precision) ? c.take<double>(otab_doubles((int)G) + G + 1) : nullptr;
+    p.cpair = lo_pair(p.precision) ? c.take<double>(5 * nx) : nullptr;
     p.rscratch_doubles = restrict_scratch_doubles((int)nx, (int)G, 1);
     p.rscratch = p.rscratch_doubles ? c.take<double>(p.rscratch_doubles) : nullptr;
     double **tl[] = {&h->T, &h->Told, &h->Tcyc, &h->Tphase, &h->Ttil, &h->Tnew, &h->sig_prev,
@@ -129,7 +131,7 @@ bool validate(const trt_grid *grid, const trt_angles *angles, const trt_groups *
     if (p.G < 1 || p.G > (1 << 16)) { err = "n_groups must be in [1, 65536]"; return false; }
     p.ldG = (p.G + 31) / 32 * 32;
     p.precision = opt->precision;
-    if (p.precision < 0 || p.precision > TRT_MIXED) { err = "bad precision"; return false; }
+    if (!precision_ok(p.precision)) { err = "bad precision"; return false; }
     xe.resize(p.nx + 1);
     if (grid->x_edges) {
         for (int i = 0; i <= p.nx; ++i) xe[i] = grid->x_edges[i];

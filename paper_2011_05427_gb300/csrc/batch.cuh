@@ -13,6 +13,7 @@
 #pragma once
 #include <algorithm>
 #include "common.cuh"
+#include "pair.cuh"
 
 namespace trt {
 
@@ -31,6 +32,11 @@ struct OpacityArgs {
     const double *Erad;      // radiation energy per cell: sigma_E, sigma_R at T_r, or null
     const int *gate;         // Problem::gate (single-slab kernel only)
     double *cterm;           // Problem::cterm: per-cell terms (single-slab kernel only)
+    // the pair form (TRT_LO_PAIR), when otabp is non-null: Problem::otabp and ::cpair (the
+    // latter single-slab only), and 1/(c dt) split into two floats on the host
+    const fpair *otabp;
+    fpair *cpair;
+    float icdt_h, icdt_l;
 };
 
 struct SweepArgs {

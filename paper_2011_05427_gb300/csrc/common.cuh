@@ -179,6 +179,12 @@ struct GreyArgs {
 
 inline bool sweep_fp32(int precision) { return (precision & TRT_SWEEP_FP32) != 0; }
 inline bool lo_fp32(int precision) { return (precision & TRT_LO_FP32) != 0; }
+inline bool lo_pair(int precision) { return (precision & TRT_LO_PAIR) != 0; }
+inline bool precision_ok(int precision)
+{
+    return precision >= 0 && precision <= (TRT_SWEEP_FP32 | TRT_LO_PAIR) &&
+           !(lo_fp32(precision) && lo_pair(precision));
+}
 
 struct Problem {
     int nx, N, M, G, ldG, nlev, precision;
@@ -219,6 +225,10 @@ struct Problem {
     // sigma_E T^3, sigma_R T^3 and the emission factor ln(1 - e^{-w}) (null: direct
     // integrals)
     double *otab = nullptr;
+    // with TRT_LO_PAIR: the tables with their FP64 coefficients as FP32 pairs, then the G+1
+    // group edges as pairs (otab_doubles(G) + G + 1 doubles), and per-cell pair terms of the
+    // opacity evaluation [5][nx] (t, 1/T, 1/T^3, 27 s C_B T, h/2); null otherwise
+    double *otabp = nullptr, *cpair = nullptr;
 };
 
 // opacity tables: ln T in [kTabU0, kTabU0 + kTabNI kTabH), kTabNC coefficients per interval

@@ -21,6 +21,7 @@
 // layout (conflict free).
 #include <cmath>
 #include "batch.cuh"
+#include "pair.cuh"
 
 namespace trt {
 
@@ -32,6 +33,45 @@ template <>
 __device__ inline double rcpR<double>(double d) { return rcp64(d); }
 template <>
 __device__ inline float rcpR<float>(float d) { return __frcp_rn(d); }
+template <>
+__device__ inline fpair rcpR<fpair>(fpair d) { return prcp(d); }
+
+// Source terms of a group system (Eold, the emission, Fold, the boundary inflows) and its
+// solution (E, F) in the pair form are held scaled by 2^-ks, ks the group's largest source
+// exponent (lo_src_exp): the system is linear in them, and FP32's exponent range would
+// otherwise cut the small groups' precision (values below 2^-103) or zero them (below
+// 2^-126).  The coefficients are not scaled.  FP64 and FP32: ks is unused.
+template <typename R>
+__device__ inline R src_in(double v, int ks)
+{
+    if constexpr (is_pair<R>) return pr_split(v, ks);
+    else return (R)v;
+}
+template <typename R>
+__device__ inline double sol_out(R v, int ks)
+{
+    if constexpr (is_pair<R>) return pr_join(v, ks);
+    else return (double)v;
+}
+__device__ inline int bexp64(double v) { return (__double2hiint(v) >> 20) & 0x7ff; }
+// the largest biased exponent of group q's source terms over this thread's cells and faces
+// (threads t, t + nthr, ...); 0 when they are all zero
+__device__ inline int lo_src_exp(const LoCtx &x, int q, int t, int nthr)
+{
+    const int n = x.nx;
+    int m = 0;
+    for (int i = t; i <= n; i += nthr) {
+        if (i < n) {
+            m = max(m, bexp64(x.L.Eold[(size_t)q * n + i]));
+            m = max(m, bexp64(x.a_cell ? x.s_cell[i] : x.L.emis[(size_t)q * n + i]));
+        }
+        m = max(m, bexp64(x.L.Fold[(size_t)q * (n + 1) + i]));
+    }
+    if (t == 0)
+        m = max(max(m, max(bexp64(x.L.Ein0[q]), bexp64(x.L.Fin0[q]))),
+                max(bexp64(x.L.EinX[q]), bexp64(x.L.FinX[q])));
+    return m;
+}
 
 
 __device__ inline double sigR_face(const LoCtx &x, int q, int f)
@@ -44,9 +84,11 @@ __device__ inline double sigR_face(const LoCtx &x, int q, int f)
     return (sc[f - 1] * x.h[f - 1] + sc[f] * x.h[f]) * x.ihf[f];
 }
 
-// F_f = GD + PL E_{f-1} - PR E_f  (boundary faces: the face energy already eliminated)
-template <typename R>
-__device__ inline void face_coef(const LoCtx &x, int q, int f, R &PL, R &PR, R &GD)
+// F_f = GD + PL E_{f-1} - PR E_f  (boundary faces: the face energy already eliminated).
+// kW: GD is instead W = dx/(c dt) / D, the factor of Fold in GD, without the boundary
+// inflow terms (the first pass of the pair staging, before the source scale is known).
+template <typename R, bool kW = false>
+__device__ inline void face_coef(const LoCtx &x, int q, int f, R &PL, R &PR, R &GD, int ks = 0)
 {
     const int nx = x.nx;
     const double *phi = x.L.phi + (size_t)q * nx;
@@ -66,33 +108,37 @@ __device__ inline void face_coef(const LoCtx &x, int q, int f, R &PL, R &PR, R &
         phiL += (R)x.L.etaL[(size_t)q * (nx + 1) + f];
         phiR += (R)x.L.etaR[(size_t)q * (nx + 1) + f];
     }
-    const R c = (R)kC, icdt = (R)x.icdt;
+    const R c = (R)kC;
     R D, Gf;
-    if constexpr (sizeof(R) == 8) {
+    if constexpr (!std::is_same<R, float>::value) {
         // dx (1/(c dt) + sigma_R,face) and dx Fold/(c dt) from the row constants: the face
         // opacity's dx-weighted mean folded into one FMA per cell opacity
-        const double dxi = x.dxicdt[f];
+        const R dxi = (R)x.dxicdt[f];
         if (!x.L.fine) {
-            D = fma((double)dx, x.L.sigR[(size_t)q * (nx + 1) + f], dxi);
+            D = fma(dx, (R)x.L.sigR[(size_t)q * (nx + 1) + f], dxi);
         } else {
             const double *sc = x.L.sigR + (size_t)q * nx;
-            D = (f == 0)    ? fma((double)dx, sc[0], dxi)
-                : (f == nx) ? fma((double)dx, sc[nx - 1], dxi)
-                            : fma(x.fwl[f], sc[f - 1], fma(x.fwr[f], sc[f], dxi));
+            D = (f == 0)    ? fma(dx, (R)sc[0], dxi)
+                : (f == nx) ? fma(dx, (R)sc[nx - 1], dxi)
+                            : fma((R)x.fwl[f], (R)sc[f - 1], fma((R)x.fwr[f], (R)sc[f], dxi));
         }
-        Gf = x.L.Fold[(size_t)q * (nx + 1) + f] * dxi;
+        if constexpr (kW) Gf = dxi;
+        else Gf = src_in<R>(x.L.Fold[(size_t)q * (nx + 1) + f], ks) * dxi;
     } else {
+        const R icdt = (R)x.icdt;
         D = dx * (icdt + (R)sigR_face(x, q, f));
         Gf = dx * (R)x.L.Fold[(size_t)q * (nx + 1) + f] * icdt;
     }
     if (f == 0) {
         const R iC0 = rcpR<R>((R)x.L.C0[q]);
         D -= phiL * iC0;
-        Gf += c * phiL * (R)x.L.Ein0[q] - phiL * (R)x.L.Fin0[q] * iC0;
+        if constexpr (!kW)
+            Gf += c * phiL * src_in<R>(x.L.Ein0[q], ks) - phiL * src_in<R>(x.L.Fin0[q], ks) * iC0;
     } else if (f == nx) {
         const R iCX = rcpR<R>((R)x.L.CX[q]);
         D += phiR * iCX;
-        Gf += -c * phiR * (R)x.L.EinX[q] + phiR * (R)x.L.FinX[q] * iCX;
+        if constexpr (!kW)
+            Gf += -c * phiR * src_in<R>(x.L.EinX[q], ks) + phiR * src_in<R>(x.L.FinX[q], ks) * iCX;
     }
     const R iD = rcpR<R>(D);
     const R ciD = c * iD;
@@ -103,21 +149,22 @@ __device__ inline void face_coef(const LoCtx &x, int q, int f, R &PL, R &PR, R &
 
 // row i of the cell equation: Ap = h (1/dt + a), Dp = h (s + Eold/dt)
 template <typename R>
-__device__ inline void cell_row(const LoCtx &x, int q, int i, R &Ap, R &Dp)
+__device__ inline void cell_row(const LoCtx &x, int q, int i, R &Ap, R &Dp, int ks = 0)
 {
-    const R hi = (R)x.h[i], idt = (R)x.idt;
-    const R Eo = (R)x.L.Eold[(size_t)q * x.nx + i];
-    if constexpr (sizeof(R) == 8) {   // from the row constants h/dt, c h, 2 h
-        const double hidt = x.hidt[i];
+    const R Eo = src_in<R>(x.L.Eold[(size_t)q * x.nx + i], ks);
+    if constexpr (!std::is_same<R, float>::value) {   // from the row constants h/dt, c h, 2 h
+        const R hidt = (R)x.hidt[i];
         if (x.a_cell) {
-            Ap = fma(x.h[i], x.a_cell[i], hidt);
-            Dp = fma(hidt, Eo, x.h[i] * x.s_cell[i]);
+            const R hc = (R)x.h[i];
+            Ap = fma(hc, (R)x.a_cell[i], hidt);
+            Dp = fma(hidt, Eo, hc * src_in<R>(x.s_cell[i], ks));
         } else {
-            Ap = fma(x.hc[i], x.L.sig[(size_t)q * x.nx + i], hidt);
-            Dp = fma(hidt, Eo, x.h2[i] * x.L.emis[(size_t)q * x.nx + i]);
+            Ap = fma((R)x.hc[i], (R)x.L.sig[(size_t)q * x.nx + i], hidt);
+            Dp = fma(hidt, Eo, (R)x.h2[i] * src_in<R>(x.L.emis[(size_t)q * x.nx + i], ks));
         }
         return;
     }
+    const R hi = (R)x.h[i], idt = (R)x.idt;
     if (x.a_cell) {
         Ap = hi * (idt + (R)x.a_cell[i]);
         Dp = hi * fma(Eo, idt, (R)x.s_cell[i]);
@@ -139,7 +186,7 @@ __device__ inline void cell_row(const LoCtx &x, int q, int i, R &Ap, R &Dp)
 // Phase A for system q by `nthr` cooperating threads (index `t`): face coefficients and
 // row parts into the chunk layout.  n >= 2.
 template <typename R>
-__device__ void lo_stage(const LoCtx &x, int q, R *sm, int mmax, int t, int nthr)
+__device__ void lo_stage(const LoCtx &x, int q, R *sm, int mmax, int t, int nthr, int ks = 0)
 {
     const int n = x.nx;
     const int S = 32 * mmax;
@@ -149,12 +196,79 @@ __device__ void lo_stage(const LoCtx &x, int q, R *sm, int mmax, int t, int nthr
         // face n after the last chunk's last row): a table built with the problem
         const int o = x.lo_slot[f];
         R PL, PR, GD;
-        face_coef<R>(x, q, f, PL, PR, GD);
+        face_coef<R>(x, q, f, PL, PR, GD, ks);
         PLc[o] = PL;
         PRc[o] = PR;
         GDc[o] = GD;
-        if (f < n) cell_row<R>(x, q, f, Ap[o], Dp[o]);
+        if (f < n) cell_row<R>(x, q, f, Ap[o], Dp[o], ks);
     }
+}
+
+// Phase A in the pair form by the CTA (t = threadIdx.x), with the group's source scale
+// (src_in): pass 1 forms the coefficients PL, PR, Ap and the face factor W of Fold (a 7th
+// array after the six of the solve) and parks the raw FP64 sources in slots the
+// elimination fills later (Fold in GD's, Eold in Dp's, the emission in Cp's) while it
+// takes their largest exponent; the CTA's maximum gives ks; pass 2 splits the parked
+// sources at that scale into GD and Dp (the boundary faces are formed again whole, with
+// their inflow terms).  Each slot is written and read again by one thread, so only the
+// reduction needs a barrier.  Returns ks.  n >= 2.
+__device__ int lo_stage_pair(const LoCtx &x, int q, fpair *sm, int mmax)
+{
+    const int n = x.nx;
+    const int S = 32 * mmax;
+    const int t = threadIdx.x, nthr = blockDim.x;
+    fpair *PLc = sm, *PRc = sm + S, *GDc = sm + 2 * S, *Ap = sm + 3 * S, *Cp = sm + 4 * S,
+          *Dp = sm + 5 * S, *Wc = sm + 6 * S;
+    double *rawF = reinterpret_cast<double *>(GDc), *rawE = reinterpret_cast<double *>(Dp),
+           *rawS = reinterpret_cast<double *>(Cp);
+    int m = 0;
+    for (int f = t; f <= n; f += nthr) {
+        const int o = x.lo_slot[f];
+        fpair PL, PR, W;
+        face_coef<fpair, true>(x, q, f, PL, PR, W);
+        PLc[o] = PL;
+        PRc[o] = PR;
+        Wc[o] = W;
+        const double Fo = x.L.Fold[(size_t)q * (n + 1) + f];
+        rawF[o] = Fo;
+        m = max(m, bexp64(Fo));
+        if (f < n) {
+            const double Eo = x.L.Eold[(size_t)q * n + f];
+            const double sv = x.a_cell ? x.s_cell[f] : x.L.emis[(size_t)q * n + f];
+            rawE[o] = Eo;
+            rawS[o] = sv;
+            m = max(m, max(bexp64(Eo), bexp64(sv)));
+            const fpair hidt = (fpair)x.hidt[f];
+            Ap[o] = x.a_cell ? fma((fpair)x.h[f], (fpair)x.a_cell[f], hidt)
+                             : fma((fpair)x.hc[f], (fpair)x.L.sig[(size_t)q * n + f], hidt);
+        }
+    }
+    if (t == 0)
+        m = max(max(m, max(bexp64(x.L.Ein0[q]), bexp64(x.L.Fin0[q]))),
+                max(bexp64(x.L.EinX[q]), bexp64(x.L.FinX[q])));
+    __shared__ int kw[32];
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((t & 31) == 0) kw[t >> 5] = m;
+    __syncthreads();
+    m = 0;
+    for (int w = 0; w < (nthr >> 5); ++w) m = max(m, kw[w]);
+    const int ks = (m == 0) ? 0 : m - 1023;
+    for (int f = t; f <= n; f += nthr) {
+        const int o = x.lo_slot[f];
+        if (f == 0 || f == n) {
+            fpair PL, PR, GD;
+            face_coef<fpair>(x, q, f, PL, PR, GD, ks);
+            GDc[o] = GD;
+        } else {
+            GDc[o] = pr_split(rawF[o], ks) * Wc[o];
+        }
+        if (f < n) {
+            const fpair sv = pr_split(rawS[o], ks);
+            const fpair Eo = pr_split(rawE[o], ks);
+            Dp[o] = fma((fpair)x.hidt[f], Eo, (x.a_cell ? (fpair)x.h[f] : (fpair)x.h2[f]) * sv);
+        }
+    }
+    return ks;
 }
 
 // Phases B-D of one system by one warp on the staged arrays in sm: the solution x ends in
@@ -238,10 +352,10 @@ __device__ void tri_solve(R *sm, int n, int mmax)
             R lA0, lC0, lD0, uA0, uC0, uD0;   // neighbours of slot 0 (unit diagonals)
             R lA1, lC1, lD1, uA1, uC1, uD1;   // neighbours of slot 1
             if (s == 1) {
-                R tA = __shfl_up_sync(full, A1r, 1), tC = __shfl_up_sync(full, C1r, 1);
-                R tD = __shfl_up_sync(full, D1r, 1);
-                R vA = __shfl_down_sync(full, A0r, 1), vC = __shfl_down_sync(full, C0r, 1);
-                R vD = __shfl_down_sync(full, D0r, 1);
+                R tA = shfl_up(full, A1r, 1), tC = shfl_up(full, C1r, 1);
+                R tD = shfl_up(full, D1r, 1);
+                R vA = shfl_down(full, A0r, 1), vC = shfl_down(full, C0r, 1);
+                R vD = shfl_down(full, D0r, 1);
                 if (lane >= 1) { lA0 = tA; lC0 = tC; lD0 = tD; }
                 else { lA0 = 0; lC0 = 0; lD0 = 0; }
                 uA0 = A1r; uC0 = C1r; uD0 = D1r;
@@ -250,14 +364,14 @@ __device__ void tri_solve(R *sm, int n, int mmax)
                 else { uA1 = 0; uC1 = 0; uD1 = 0; }
             } else {
                 const int t = s >> 1;
-                R a0 = __shfl_up_sync(full, A0r, t), c0 = __shfl_up_sync(full, C0r, t);
-                R d0 = __shfl_up_sync(full, D0r, t);
-                R a1 = __shfl_up_sync(full, A1r, t), c1 = __shfl_up_sync(full, C1r, t);
-                R d1 = __shfl_up_sync(full, D1r, t);
-                R e0 = __shfl_down_sync(full, A0r, t), g0 = __shfl_down_sync(full, C0r, t);
-                R h0 = __shfl_down_sync(full, D0r, t);
-                R e1 = __shfl_down_sync(full, A1r, t), g1 = __shfl_down_sync(full, C1r, t);
-                R h1 = __shfl_down_sync(full, D1r, t);
+                R a0 = shfl_up(full, A0r, t), c0 = shfl_up(full, C0r, t);
+                R d0 = shfl_up(full, D0r, t);
+                R a1 = shfl_up(full, A1r, t), c1 = shfl_up(full, C1r, t);
+                R d1 = shfl_up(full, D1r, t);
+                R e0 = shfl_down(full, A0r, t), g0 = shfl_down(full, C0r, t);
+                R h0 = shfl_down(full, D0r, t);
+                R e1 = shfl_down(full, A1r, t), g1 = shfl_down(full, C1r, t);
+                R h1 = shfl_down(full, D1r, t);
                 if (lane >= t) {
                     lA0 = a0; lC0 = c0; lD0 = d0;
                     lA1 = a1; lC1 = c1; lD1 = d1;
@@ -301,7 +415,7 @@ __device__ void tri_solve(R *sm, int n, int mmax)
 // The outputs of system q from the solution in the Dp array and the face coefficients:
 // E, F (F_f = GD_f + PL_f E_{f-1} - PR_f E_f) and the boundary face energies.  n >= 2.
 template <typename R>
-__device__ void lo_outputs(const LoCtx &x, int q, R *sm, int mmax)
+__device__ void lo_outputs(const LoCtx &x, int q, R *sm, int mmax, int ks = 0)
 {
     const int lane = threadIdx.x & 31;
     const int n = x.nx;
@@ -318,7 +432,7 @@ __device__ void lo_outputs(const LoCtx &x, int q, R *sm, int mmax)
 #define CH(arr, k, l) arr[(k) * 32 + (l)]
 
     if (act)
-        for (int k = 0; k < m; ++k) E[r0 + k] = (double)CH(Dp, k, lane);
+        for (int k = 0; k < m; ++k) E[r0 + k] = sol_out<R>(CH(Dp, k, lane), ks);
     if (act) {
         const int mprev = (lane > 0) ? r0 - ((lane - 1) * n) / P : 0;
         const R Eleft0 = (lane > 0) ? CH(Dp, mprev - 1, lane - 1) : (R)0;
@@ -328,17 +442,57 @@ __device__ void lo_outputs(const LoCtx &x, int q, R *sm, int mmax)
             R Fv = CH(GDc, k, lane);
             if (f > 0) Fv += CH(PLc, k, lane) * ((k == 0) ? Eleft0 : CH(Dp, k - 1, lane));
             if (f < n) Fv -= CH(PRc, k, lane) * CH(Dp, k, lane);
-            F[f] = (double)Fv;
-            if (f == 0) x.L.Eb0[q] = x.L.Ein0[q] + ((double)Fv - x.L.Fin0[q]) / (kC * x.L.C0[q]);
-            if (f == n) x.L.EbX[q] = x.L.EinX[q] + ((double)Fv - x.L.FinX[q]) / (kC * x.L.CX[q]);
+            const double Fd = sol_out<R>(Fv, ks);
+            F[f] = Fd;
+            if (f == 0) x.L.Eb0[q] = x.L.Ein0[q] + (Fd - x.L.Fin0[q]) / (kC * x.L.C0[q]);
+            if (f == n) x.L.EbX[q] = x.L.EinX[q] + (Fd - x.L.FinX[q]) / (kC * x.L.CX[q]);
         }
     }
 #undef CH
 }
 
+// The outputs of system q by every thread of the CTA, from the solution (chunk layout, in
+// the Dp array) and the face coefficients: consecutive threads take consecutive cells and
+// faces (coalesced stores), each slot found through the slot table.  The boundary face
+// energies as in lo_outputs (the pair form in pair arithmetic, at the source scale).
+// n >= 2; called after a barrier that follows the elimination.
+template <typename R>
+__device__ void lo_outputs_cta(const LoCtx &x, int q, const R *sm, int mmax, int ks)
+{
+    const int n = x.nx;
+    const int S = 32 * mmax;
+    const R *PLc = sm, *PRc = sm + S, *GDc = sm + 2 * S, *Dp = sm + 5 * S;
+    double *E = x.L.E + (size_t)q * n;
+    double *F = x.L.F + (size_t)q * (n + 1);
+    for (int f = threadIdx.x; f <= n; f += blockDim.x) {
+        const int o = x.lo_slot[f];
+        R Fv = GDc[o];
+        if (f > 0) Fv += PLc[o] * Dp[x.lo_slot[f - 1]];
+        if (f < n) {
+            const R Ef = Dp[o];
+            Fv -= PRc[o] * Ef;
+            E[f] = sol_out<R>(Ef, ks);
+        }
+        F[f] = sol_out<R>(Fv, ks);
+        if (f == 0 || f == n) {
+            const double Ein = f == 0 ? x.L.Ein0[q] : x.L.EinX[q];
+            const double Fin = f == 0 ? x.L.Fin0[q] : x.L.FinX[q];
+            const double Cb = f == 0 ? x.L.C0[q] : x.L.CX[q];
+            double Eb;
+            if constexpr (is_pair<R>)
+                Eb = pr_join(src_in<R>(Ein, ks) +
+                                 (Fv - src_in<R>(Fin, ks)) * rcpR<R>((R)kC * (R)Cb), ks);
+            else
+                Eb = Ein + ((double)Fv - Fin) / (kC * Cb);
+            (f == 0 ? x.L.Eb0 : x.L.EbX)[q] = Eb;
+        }
+    }
+}
+
 // staged = true: phase A already done (by the whole block) for n >= 2.
 template <typename R>
-__device__ void warp_lo_solve(const LoCtx &x, int q, R *sm, int mmax, bool staged = false)
+__device__ void warp_lo_solve(const LoCtx &x, int q, R *sm, int mmax, bool staged = false,
+                              int ks = 0)
 {
     const int lane = threadIdx.x & 31;
     const int n = x.nx;
@@ -348,28 +502,29 @@ __device__ void warp_lo_solve(const LoCtx &x, int q, R *sm, int mmax, bool stage
     if (n == 1) {
         if (lane == 0) {
             R PL0, PR0, GD0, PL1, PR1, GD1, Ap0, Dp0;
-            face_coef<R>(x, q, 0, PL0, PR0, GD0);
-            face_coef<R>(x, q, 1, PL1, PR1, GD1);
-            cell_row<R>(x, q, 0, Ap0, Dp0);
+            face_coef<R>(x, q, 0, PL0, PR0, GD0, ks);
+            face_coef<R>(x, q, 1, PL1, PR1, GD1, ks);
+            cell_row<R>(x, q, 0, Ap0, Dp0, ks);
             R di = Ap0 + PL1 + PR0;
             R rh = Dp0 - GD1 + GD0;
             R e0 = rh / di;
-            E[0] = (double)e0;
+            E[0] = sol_out<R>(e0, ks);
             R F0 = GD0 - PR0 * e0, F1 = GD1 + PL1 * e0;
-            F[0] = (double)F0;
-            F[1] = (double)F1;
-            x.L.Eb0[q] = x.L.Ein0[q] + ((double)F0 - x.L.Fin0[q]) / (kC * x.L.C0[q]);
-            x.L.EbX[q] = x.L.EinX[q] + ((double)F1 - x.L.FinX[q]) / (kC * x.L.CX[q]);
+            const double F0d = sol_out<R>(F0, ks), F1d = sol_out<R>(F1, ks);
+            F[0] = F0d;
+            F[1] = F1d;
+            x.L.Eb0[q] = x.L.Ein0[q] + (F0d - x.L.Fin0[q]) / (kC * x.L.C0[q]);
+            x.L.EbX[q] = x.L.EinX[q] + (F1d - x.L.FinX[q]) / (kC * x.L.CX[q]);
         }
         return;
     }
 
     // ---- phase A ----
-    if (!staged) lo_stage<R>(x, q, sm, mmax, lane, 32);
+    if (!staged) lo_stage<R>(x, q, sm, mmax, lane, 32, ks);
     __syncwarp();
 
     tri_solve<R>(sm, n, mmax);
-    lo_outputs<R>(x, q, sm, mmax);
+    lo_outputs<R>(x, q, sm, mmax, ks);
 #undef CH
 }
 
@@ -468,14 +623,15 @@ __device__ void lo_solve_refined(const LoCtx &x, int q, int sw)
 }
 
 // One system per CTA: all 4 warps stage the rows (phase A: the parallel part, global
-// loads and the face coefficients), then warp `sw` runs the elimination.  The CTA's four
-// warps sit on the SM's four sub-partitions, each with its own FP64 pipe; rotating the
-// eliminating warp with the work item spreads the serial FP64 chains of the CTAs resident
-// on an SM over all four pipes (always warp 0 would queue them all on one).
+// loads and the face coefficients), warp `sw` runs the elimination, and all 4 warps form
+// and store the outputs.  The CTA's four warps sit on the SM's four sub-partitions, each
+// with its own FP64 pipe; rotating the eliminating warp with the work item spreads the
+// serial chains of the CTAs resident on an SM over all four (always warp 0 would queue
+// them all on one).
 template <typename R>
 __device__ void lo_solve_body(const LoCtx &x, int q, int sw)
 {
-    if constexpr (sizeof(R) == 4) {   // FP32 group solves: refined to FP64 accuracy
+    if constexpr (std::is_same<R, float>::value) {   // FP32 group solves: refined to FP64 accuracy
         lo_solve_refined(x, q, sw);
         return;
     }
@@ -483,12 +639,29 @@ __device__ void lo_solve_body(const LoCtx &x, int q, int sw)
     R *sm = reinterpret_cast<R *>(smem_raw);
     const int mmax = lo_mmax(x.nx);
     const bool staged = x.nx >= 2;
+    const bool solver = (int)(threadIdx.x >> 5) == (sw & ((int)(blockDim.x >> 5) - 1));
     if (staged) {
-        lo_stage<R>(x, q, sm, mmax, threadIdx.x, blockDim.x);
+        int ks = 0;
+        if constexpr (is_pair<R>) ks = lo_stage_pair(x, q, sm, mmax);
+        else lo_stage<R>(x, q, sm, mmax, threadIdx.x, blockDim.x);
         __syncthreads();
+        if (solver) tri_solve<R>(sm, x.nx, mmax);
+        __syncthreads();
+        lo_outputs_cta<R>(x, q, sm, mmax, ks);
+        return;
     }
-    if ((int)(threadIdx.x >> 5) == (sw & ((int)(blockDim.x >> 5) - 1)))
-        warp_lo_solve<R>(x, q, sm, mmax, staged);
+    int ks = 0;   // one cell: one lane (the pair form's source scale from every thread)
+    if constexpr (is_pair<R>) {
+        __shared__ int kw[32];
+        int m = lo_src_exp(x, q, threadIdx.x, blockDim.x);
+        for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if ((threadIdx.x & 31) == 0) kw[threadIdx.x >> 5] = m;
+        __syncthreads();
+        m = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = max(m, kw[w]);
+        ks = (m == 0) ? 0 : m - 1023;
+    }
+    if (solver) warp_lo_solve<R>(x, q, sm, mmax, false, ks);
 }
 
 template <typename R>
@@ -1291,6 +1464,7 @@ static size_t lo_smem(int precision, int nx)
     const size_t S = 32 * (size_t)lo_mmax(nx);
     if (lo_fp32(precision) && 6 * S * (sizeof(double) + sizeof(float)) <= 227 * 1024)
         return 6 * S * (sizeof(double) + sizeof(float));
+    if (lo_pair(precision)) return 7 * S * sizeof(double);   // + the face factors of Fold
     return 6 * S * sizeof(double);
 }
 static bool lo_refined(int precision, int nx)
@@ -1304,7 +1478,12 @@ cudaError_t launch_lo_solve(const Problem &p, double dt, const Level &L)
     const size_t sm = lo_smem(p.precision, p.nx);
     const unsigned nb = (unsigned)L.n;
     cudaError_t e;
-    if (!lo_refined(p.precision, p.nx)) {
+    if (lo_pair(p.precision)) {
+        e = cudaFuncSetAttribute(k_lo_solve<fpair>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)sm);
+        if (e != cudaSuccess) return e;
+        k_lo_solve<fpair><<<nb, 128, sm, p.stream>>>(x);
+    } else if (!lo_refined(p.precision, p.nx)) {
         e = cudaFuncSetAttribute(k_lo_solve<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)sm);
         if (e != cudaSuccess) return e;
@@ -1323,7 +1502,12 @@ cudaError_t launch_lo_solve_b(int precision, int max_nx, const int *meta, int N,
 {
     const size_t sm = lo_smem(precision, max_nx);
     cudaError_t e;
-    if (!lo_refined(precision, max_nx)) {
+    if (lo_pair(precision)) {
+        e = cudaFuncSetAttribute(k_lo_solve_b<fpair>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)sm);
+        if (e != cudaSuccess) return e;
+        k_lo_solve_b<fpair><<<grid, 128, sm, st>>>(meta, N, xs);
+    } else if (!lo_refined(precision, max_nx)) {
         e = cudaFuncSetAttribute(k_lo_solve_b<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)sm);
         if (e != cudaSuccess) return e;

@@ -441,15 +441,30 @@ __device__ inline CellArrays cell_arrays(const OpacityArgs &a)
                       reinterpret_cast<int *>(a.cterm + 7 * (size_t)a.nx) + a.nx, a.nx};
 }
 
+// the pair form's per-cell terms (TRT_LO_PAIR): t, 1/T, 1/T^3, 27 s C_B T, h/2 split from
+// the FP64 terms of cell_vals
+struct CellPair {
+    fpair t, iT, iT3, kET, hh;
+};
+__device__ inline CellPair cell_pair(const OpacityArgs &a, int i, const CellVals &v)
+{
+    return CellPair{fpair(v.t), fpair(v.iT), fpair(v.iT3), fpair(v.kET), fpair(0.5 * a.h[i])};
+}
+
 struct CellTerms {
     CellVals v[32];
+    CellPair p[32];
 };
 
 __device__ inline void stage_cells(const OpacityArgs &a, int i0, CellTerms &ct, int sy)
 {
     if ((int)threadIdx.y == (sy & 3)) {
         const int tx = threadIdx.x, i = i0 + tx;
-        if (i < a.nx) ct.v[tx] = cell_vals(a, i);
+        if (i < a.nx) {
+            const CellVals v = cell_vals(a, i);
+            ct.v[tx] = v;
+            if (a.otabp) ct.p[tx] = cell_pair(a, i, v);
+        }
     }
     __syncthreads();
 }
@@ -540,6 +555,55 @@ __device__ inline void opacity_body(const OpacityArgs &a, int i, int g, const Ce
     }
 }
 
+// The same quantities in FP32-pair arithmetic (TRT_LO_PAIR; outputs FP64): the three
+// Horner sums with their FP64 coefficients as pairs (the FP32 tails as in horner), sigma =
+// sum / T^3, and the emission 27 s C_B T e^w, w = (the emission factor's logarithm) -
+// nu_g/T, by pr_exp as a pair times 2^k -- the power of two goes into the exponent of the
+// FP64 result (pr_join), so e_g keeps FP64's range.  Relative errors: about 1e-14 in the
+// opacities, about 3 2^-47 max(1, |w|) in e_g (w's: nu_g, 1/T and their product each
+// rounded to a pair; 1.6e-11 at the smallest e_g that FP64 holds, e^-746).  Cells outside
+// the tables and the T_r option take opacity_body.
+__device__ inline fpair horner_pair(const fpair *__restrict__ a, const float *__restrict__ b,
+                                   fpair t, float tf)
+{
+    float q = b[kTabNC - kTabLo - 1];
+#pragma unroll
+    for (int k = kTabNC - kTabLo - 2; k >= 0; --k) q = fmaf(q, tf, b[k]);
+    fpair p(q, 0.f);
+#pragma unroll
+    for (int k = kTabLo - 1; k >= 0; --k) p = fma(p, t, a[k]);
+    return p;
+}
+
+__device__ inline void opacity_body_pair(const OpacityArgs &a, int i, int g, const CellVals &v,
+                                         const CellPair &cp, const fpair *e2p, const Mx &mx)
+{
+    if (v.m < 0 || a.Erad) {
+        opacity_body(a, i, g, v, mx);
+        return;
+    }
+    const size_t idx = (size_t)g * a.nx + i;
+    const fpair *c = a.otabp + ((size_t)g * kTabNI + v.m) * kTabEntry;
+    const float *ch = reinterpret_cast<const float *>(c + kTabNF * kTabLo);
+    constexpr int kh = kTabNC - kTabLo;
+    const fpair sg = horner_pair(c, ch, cp.t, v.tf) * cp.iT3;
+    const fpair sR = horner_pair(c + kTabLo, ch + kh, cp.t, v.tf) * cp.iT3;
+    const fpair xa = a.otabp[(size_t)a.G * kTabNI * kTabEntry + g] * cp.iT;
+    int k;
+    const fpair em = cp.kET * pr_exp(horner_pair(c + 2 * kTabLo, ch + 2 * kh, cp.t, v.tf) - xa,
+                                     k, e2p);
+    a.sigE[idx] = pr_join(sg, 0);
+    a.emis[idx] = pr_join(em, k);
+    a.sigR[idx] = pr_join(sR, 0);
+    if (a.sig32) {   // FP32 sweep inputs: sigma_t h/2 and h e/2, each rounded once from a pair
+        const fpair st = (sg + fpair(a.icdt_h, a.icdt_l)) * cp.hh;
+        a.sig32[idx] = __fadd_rn(st.h, st.l);
+        const fpair eh = em * cp.hh;
+        a.emis32[idx] = pr_ldexpf(__fadd_rn(eh.h, eh.l), k);
+        if (g == 0) a.kap32[i] = (float)(0.5 * a.h[i] * a.icdt);
+    }
+}
+
 // the 2^(j/32) table of texp in shared memory (lanes index it with different j)
 __device__ inline Mx stage_exp_table(double *s_e2)
 {
@@ -548,12 +612,30 @@ __device__ inline Mx stage_exp_table(double *s_e2)
     return Mx{s_e2, ExpConsts{c_ser.einv, c_ser.eL1, c_ser.eL2}};
 }
 
-// the per-cell terms of one evaluation (single slab)
+// the same table as pairs (the pair form); called after stage_exp_table's barrier
+__device__ inline void stage_exp_pairs(fpair *s_e2p)
+{
+    if (threadIdx.y == 0 && threadIdx.x < 32) s_e2p[threadIdx.x] = fpair(c_ser.e2[threadIdx.x]);
+    __syncthreads();
+}
+
+// the per-cell terms of one evaluation (single slab); the pair form's too
 __global__ void k_cell_terms(OpacityArgs a)
 {
     if (a.gate && *a.gate) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < a.nx) cell_arrays(a).put(i, cell_vals(a, i));
+    if (i >= a.nx) return;
+    const CellVals v = cell_vals(a, i);
+    cell_arrays(a).put(i, v);
+    if (a.cpair) {
+        const CellPair cp = cell_pair(a, i, v);
+        const int n = a.nx;
+        a.cpair[i] = cp.t;
+        a.cpair[n + i] = cp.iT;
+        a.cpair[2 * n + i] = cp.iT3;
+        a.cpair[3 * n + i] = cp.kET;
+        a.cpair[4 * n + i] = cp.hh;
+    }
 }
 
 // block (32 cells, 8 groups); grid (ceil(nx / 32), ceil(G / 8)); the cells' terms from
@@ -562,25 +644,41 @@ __global__ void __launch_bounds__(256) k_opacity(OpacityArgs a)
 {
     if (a.gate && *a.gate) return;   // the phase's inner loop has ended (every thread alike)
     __shared__ double s_e2[32];
+    __shared__ fpair s_e2p[32];
     const Mx mx = stage_exp_table(s_e2);
+    if (a.otabp) stage_exp_pairs(s_e2p);
     const int i = blockIdx.x * 32 + threadIdx.x, g = blockIdx.y * 8 + threadIdx.y;
     if (i >= a.nx || g >= a.G) return;
-    opacity_body(a, i, g, cell_arrays(a).get(i), mx);
+    if (a.otabp) {
+        const int n = a.nx;
+        const CellPair cp{a.cpair[i], a.cpair[n + i], a.cpair[2 * n + i], a.cpair[3 * n + i],
+                          a.cpair[4 * n + i]};
+        opacity_body_pair(a, i, g, cell_arrays(a).get(i), cp, s_e2p, mx);
+    } else {
+        opacity_body(a, i, g, cell_arrays(a).get(i), mx);
+    }
 }
 
 __global__ void __launch_bounds__(256) k_opacity_b(const int *__restrict__ meta, int N,
                                                    const OpacityArgs *__restrict__ xs)
 {
     __shared__ double s_e2[32];
+    __shared__ fpair s_e2p[32];
     __shared__ CellTerms ct;
     const Mx mx = stage_exp_table(s_e2);
+    stage_exp_pairs(s_e2p);
     for (int b = blockIdx.x;; b += gridDim.x) {
         int s, bx, by;
         if (!bdecode(meta, N, b, s, bx, by)) break;
         const OpacityArgs a = xs[s];
         stage_cells(a, bx * 32, ct, b);
         const int i = bx * 32 + threadIdx.x, g = by * 8 + threadIdx.y;
-        if (i < a.nx && g < a.G) opacity_body(a, i, g, ct.v[threadIdx.x], mx);
+        if (i < a.nx && g < a.G) {
+            if (a.otabp)
+                opacity_body_pair(a, i, g, ct.v[threadIdx.x], ct.p[threadIdx.x], s_e2p, mx);
+            else
+                opacity_body(a, i, g, ct.v[threadIdx.x], mx);
+        }
         __syncthreads();   // the cell terms are restaged by the next work item
     }
 }
@@ -710,6 +808,22 @@ __global__ void k_otab_build(int G, const double *__restrict__ edges, double k27
     if (kTabHiF > kTabNF * (kTabNC - kTabLo)) chi[kTabHiF - 1] = 0.f;
 }
 
+// the pair copy of the tables (TRT_LO_PAIR): each entry's FP64 coefficients split into
+// pairs, its FP32 tail copied; then the group edges as pairs
+__global__ void k_otab_pair(int G, const double *__restrict__ tab,
+                            const double *__restrict__ edges, fpair *__restrict__ tp)
+{
+    const long id = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long n = (long)G * kTabNI * kTabEntry;
+    if (id < n) {
+        const int j = (int)(id % kTabEntry);
+        if (j < kTabNF * kTabLo) tp[id] = fpair(tab[id]);
+        else reinterpret_cast<double *>(tp)[id] = tab[id];   // the FP32 tail, bit for bit
+    } else if (id < n + G + 1) {
+        tp[id] = fpair(edges[id - n]);
+    }
+}
+
 cudaError_t launch_otab_build(const Problem &p)
 {
     if (!p.otab) return cudaSuccess;
@@ -717,6 +831,11 @@ cudaError_t launch_otab_build(const Problem &p)
     if (e != cudaSuccess) return e;
     const int n = p.G * kTabNI;
     k_otab_build<<<(n + 127) / 128, 128, 0, p.stream>>>(p.G, p.edges, 27.0 * p.s, p.otab);
+    e = cudaGetLastError();
+    if (e != cudaSuccess || !p.otabp) return e;
+    const long np = (long)n * kTabEntry + p.G + 1;
+    k_otab_pair<<<(unsigned)((np + 255) / 256), 256, 0, p.stream>>>(
+        p.G, p.otab, p.edges, reinterpret_cast<fpair *>(p.otabp));
     return cudaGetLastError();
 }
 
@@ -735,6 +854,10 @@ OpacityArgs make_opacity_args(const Problem &p, const double *T, double *sigE, d
     a.kE = 27.0 * p.s * kCB;   // the order of the direct path's k27 * kCB
     a.gate = p.gate;
     a.cterm = p.cterm;
+    a.otabp = (p.otab && p.otabp) ? reinterpret_cast<const fpair *>(p.otabp) : nullptr;
+    a.cpair = reinterpret_cast<fpair *>(p.cpair);
+    a.icdt_h = (float)a.icdt;
+    a.icdt_l = (float)(a.icdt - (double)a.icdt_h);
     return a;
 }
 

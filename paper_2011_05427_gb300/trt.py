@@ -17,10 +17,11 @@ LIB_PATH = os.path.join(HERE, "libtrt.so")
 
 TRT_OK, TRT_EINVAL, TRT_ENOTCONVERGED, TRT_ENUMERIC, TRT_ETIMEOUT, TRT_ECUDA, TRT_ENOSPACE = \
     0, -1, -2, -3, -4, -5, -6
-TRT_FP64, TRT_SWEEP_FP32, TRT_LO_FP32, TRT_MIXED = 0, 1, 2, 3
+TRT_FP64, TRT_SWEEP_FP32, TRT_LO_FP32, TRT_MIXED, TRT_LO_PAIR = 0, 1, 2, 3, 4
 CYCLES = {"V": 0, "W": 1, "F": 2}
 PRECISIONS = {"fp64": TRT_FP64, "mixed": TRT_MIXED, "sweep32": TRT_SWEEP_FP32,
-              "lo32": TRT_LO_FP32}
+              "lo32": TRT_LO_FP32, "lopair": TRT_LO_PAIR,
+              "sweep32_lopair": TRT_SWEEP_FP32 | TRT_LO_PAIR}
 
 _dp = ctypes.POINTER(ctypes.c_double)
 _vp = ctypes.c_void_p

@@ -212,17 +212,18 @@ MIXED_CASES = [
 # round-off (3.6e-6 .. 7.3e-6 in T); with it they are FP64 solves to within the
 # refinement's square of that, so FP32 LO alone stays at the FP64 path's agreement and the
 # mixed form at the FP32 sweeps'.
-MIXED_TOL = {"sweep32": (1e-7, 2e-7), "lo32": (1e-9, 1e-9), "mixed": (1e-7, 2e-7)}
+MIXED_TOL = {"sweep32": (1e-7, 2e-7), "lo32": (1e-9, 1e-9), "mixed": (1e-7, 2e-7),
+             "lopair": (1e-9, 1e-9), "sweep32_lopair": (1e-7, 2e-7)}
 # every FP32 sweep shape, the strip sweep of tile heights without a lean kernel included
 # (it forms the outflow as s r + t k in every cell): T and E_g after fixed-iteration steps
 SHAPE_TOL = 1e-6
 
 
-@pytest.mark.parametrize("prec", ["sweep32", "lo32", "mixed"])
+@pytest.mark.parametrize("prec", ["sweep32", "lo32", "mixed", "lopair", "sweep32_lopair"])
 @pytest.mark.parametrize("name,cfg,cycle,lmax", MIXED_CASES, ids=[c[0] for c in MIXED_CASES])
 def test_mixed_precision_vs_fp64_oracle(trt, orc, name, cfg, cycle, lmax, prec):
-    """FP32 sweeps and/or FP32 group LOQD, FP64 grey + MEB: error against the FP64 oracle
-    after fixed-iteration steps."""
+    """FP32 sweeps and/or FP32 (or FP32-pair) group LOQD, FP64 grey + MEB: error against
+    the FP64 oracle after fixed-iteration steps."""
     s, o = pair(trt, orc, cfg, precision=prec)
     worst = (0.0, 0.0)
     for step in range(3):
@@ -244,7 +245,7 @@ CONVERGED_MIXED_TOL_T = 1e-7
 CONVERGED_MIXED_TOL_E = 2e-7
 
 
-@pytest.mark.parametrize("prec", ["sweep32", "mixed"])
+@pytest.mark.parametrize("prec", ["sweep32", "mixed", "sweep32_lopair"])
 @pytest.mark.parametrize("name,cfg,cycle,lmax", MIXED_CASES, ids=[c[0] for c in MIXED_CASES])
 def test_mixed_precision_converged_vs_fp64_oracle(trt, orc, name, cfg, cycle, lmax, prec):
     """FP32 sweeps (and FP32 group LOQD eliminations in `mixed`) with FP64 grey + MEB,
