@@ -416,9 +416,10 @@ def batch_bench(local, steps=3, warmup=2):
     return out
 
 
-def closure_bench(local, ms_fp64, steps=10):
+def closure_bench(local, ms_fp64, steps=10, precision="sweep32_lopair"):
     """Learned warm start: trained on snapshots of 4 slabs x 10 steps of the method, then
-    fc_1024 stepped with FP32 sweeps (at their tuned l_max) with and without it."""
+    fc_1024 stepped in the fastest precision form (FP32 sweeps, pair low-order kernels, at
+    its tuned l_max) with and without it."""
     import dataclasses
     from paper_2011_05427_gb300 import closure
     import torch
@@ -427,14 +428,15 @@ def closure_bench(local, ms_fp64, steps=10):
     net, hist = closure.train(X, Y, iters=1000, batch=8192, lr=1e-3, device=f"cuda:{local}")
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
-    cfg = dataclasses.replace(W.fc_1024("V"), l_max=tuned_lmax("sweep32", "V"))
-    r = closure.compare(cfg, net, steps, precision="sweep32", device=f"cuda:{local}")
+    cfg = dataclasses.replace(W.fc_1024("V"), l_max=tuned_lmax(precision, "V"))
+    r = closure.compare(cfg, net, steps, precision=precision, device=f"cuda:{local}")
     a, b = r["plain"], r["closure"]
     dT = float(np.max(np.abs(a["state"]["T"] - b["state"]["T"]) / a["state"]["T"]))
     return {"train_rows": int(len(X)), "train_loss_first_last": [hist[0][1], hist[-1][1]],
             "collect_and_train_s": t_train,
-            "sweep32_plain": {k: a[k] for k in ("n_ti", "n_c", "ms_per_step")},
-            "sweep32_closure": {k: b[k] for k in ("n_ti", "n_c", "ms_per_step")},
+            "precision": precision,
+            "plain": {k: a[k] for k in ("n_ti", "n_c", "ms_per_step")},
+            "closure": {k: b[k] for k in ("n_ti", "n_c", "ms_per_step")},
             "speedup_closure_vs_plain_fp64": ms_fp64 / b["ms_per_step"],
             "max_rel_T_closure_vs_plain": dT, "steps": steps, "l_max": cfg.l_max}
 
@@ -779,6 +781,25 @@ def run_ours(args):
                 "note": "FP32 sweeps and FP32 group LOQD eliminations refined by two "
                         "FP64-residual steps, FP64 grey LOQD + MEB",
                 **counters(st_x, args.steps)}
+            # FP32 sweeps with the group LOQD solves and opacities in FP32-pair arithmetic
+            t_p, st_p, _, s_p = timed_steps(trt, cfg, "sweep32_lopair", args.cycle, args.steps,
+                                            args.warmup, local, ws, l_max=lm32)
+            d = s_p.moments()
+            s_p.close()
+            extra["mixed_sweep32_lopair"] = {
+                "ms_per_step": t_p / args.steps * 1e3,
+                "value": sum(x["n_ti"] for x in st_p) * upd_sweep / t_p,
+                "speedup_vs_fp64": ms_step / (t_p / args.steps * 1e3),
+                "max_rel_T_vs_fp64": float(np.max(np.abs(d["T"] - a["T"]) / a["T"])),
+                "max_rel_Eg_vs_fp64": float(np.max(np.abs(d["Eg"] - a["Eg"]) /
+                                                   a["Eg"].sum(0)[None, :])),
+                "l_max": lm32,
+                "note": "FP32 sweeps; group LOQD solves and opacities in FP32-pair arithmetic "
+                        "(FP64 in and out); restriction, grey LOQD + MEB in FP64",
+                **counters(st_p, args.steps)}
+            if ws == 1 and args.cpu_baseline:
+                extra["mixed_sweep32_lopair"]["vs_oracle"] = mixed_vs_oracle(local,
+                                                                             "sweep32_lopair")
 
         if args.mlp:
             extra["mlp"] = mlp_bench(local)

@@ -85,6 +85,7 @@ void carve(trt_handle *h, Carver &c)
     p.otab = c.take<double>(otab_doubles((int)G));
     p.otabp = lo_pair(p.precision) ? c.take<double>(otab_doubles((int)G) + G + 1) : nullptr;
     p.cpair = lo_pair(p.precision) ? c.take<double>(5 * nx) : nullptr;
+    p.lopc = lo_pair(p.precision) ? c.take<double>(8 * (nx + 1)) : nullptr;
     p.rscratch_doubles = restrict_scratch_doubles((int)nx, (int)G, 1);
     p.rscratch = p.rscratch_doubles ? c.take<double>(p.rscratch_doubles) : nullptr;
     double **tl[] = {&h->T, &h->Told, &h->Tcyc, &h->Tphase, &h->Ttil, &h->Tnew, &h->sig_prev,

@@ -68,6 +68,7 @@ struct LoCtx {
     const double *h, *ihf, *hf;
     const double *hc, *h2, *fwl, *fwr, *hidt, *dxicdt;   // Problem's LO row constants
     const int *lo_slot;
+    const fpair *pc;   // Problem::lopc (the pair form's row constants), or null
     Level L;
     const double *a_cell, *s_cell;   // grey: explicit absorption / source per cell
     const int *gate;                 // Problem::gate (single-slab kernels only)

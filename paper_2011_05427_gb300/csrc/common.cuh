@@ -229,6 +229,9 @@ struct Problem {
     // group edges as pairs (otab_doubles(G) + G + 1 doubles), and per-cell pair terms of the
     // opacity evaluation [5][nx] (t, 1/T, 1/T^3, 27 s C_B T, h/2); null otherwise
     double *otabp = nullptr, *cpair = nullptr;
+    // with TRT_LO_PAIR: the LO row constants as pairs, [8][nx+1] (hf, dxicdt, fwl, fwr per
+    // face; hidt, hc, h2, h per cell), written with hidt and dxicdt; null otherwise
+    double *lopc = nullptr;
 };
 
 // opacity tables: ln T in [kTabU0, kTabU0 + kTabNI kTabH), kTabNC coefficients per interval

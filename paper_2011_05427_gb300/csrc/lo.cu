@@ -53,6 +53,14 @@ __device__ inline double sol_out(R v, int ks)
     if constexpr (is_pair<R>) return pr_join(v, ks);
     else return (double)v;
 }
+// row constant j of kind k (the Problem::lopc order: 0 hf, 1 dxicdt, 2 fwl, 3 fwr, 4 hidt,
+// 5 hc, 6 h2, 7 h): the pair form reads the pair copy, the others the FP64 array d
+template <typename R>
+__device__ inline R lc(const LoCtx &x, int k, int j, const double *d)
+{
+    if constexpr (is_pair<R>) return x.pc[(size_t)k * (x.nx + 1) + j];
+    else return (R)d[j];
+}
 __device__ inline int bexp64(double v) { return (__double2hiint(v) >> 20) & 0x7ff; }
 // the largest biased exponent of group q's source terms over this thread's cells and faces
 // (threads t, t + nthr, ...); 0 when they are all zero
@@ -92,7 +100,7 @@ __device__ inline void face_coef(const LoCtx &x, int q, int f, R &PL, R &PR, R &
 {
     const int nx = x.nx;
     const double *phi = x.L.phi + (size_t)q * nx;
-    const R dx = (R)x.hf[f];
+    const R dx = lc<R>(x, 0, f, x.hf);
     R phiL, phiR;
     if (f == 0) {
         phiL = (R)x.L.phib0[q];
@@ -113,14 +121,15 @@ __device__ inline void face_coef(const LoCtx &x, int q, int f, R &PL, R &PR, R &
     if constexpr (!std::is_same<R, float>::value) {
         // dx (1/(c dt) + sigma_R,face) and dx Fold/(c dt) from the row constants: the face
         // opacity's dx-weighted mean folded into one FMA per cell opacity
-        const R dxi = (R)x.dxicdt[f];
+        const R dxi = lc<R>(x, 1, f, x.dxicdt);
         if (!x.L.fine) {
             D = fma(dx, (R)x.L.sigR[(size_t)q * (nx + 1) + f], dxi);
         } else {
             const double *sc = x.L.sigR + (size_t)q * nx;
             D = (f == 0)    ? fma(dx, (R)sc[0], dxi)
                 : (f == nx) ? fma(dx, (R)sc[nx - 1], dxi)
-                            : fma((R)x.fwl[f], (R)sc[f - 1], fma((R)x.fwr[f], (R)sc[f], dxi));
+                            : fma(lc<R>(x, 2, f, x.fwl), (R)sc[f - 1],
+                                  fma(lc<R>(x, 3, f, x.fwr), (R)sc[f], dxi));
         }
         if constexpr (kW) Gf = dxi;
         else Gf = src_in<R>(x.L.Fold[(size_t)q * (nx + 1) + f], ks) * dxi;
@@ -153,14 +162,14 @@ __device__ inline void cell_row(const LoCtx &x, int q, int i, R &Ap, R &Dp, int 
 {
     const R Eo = src_in<R>(x.L.Eold[(size_t)q * x.nx + i], ks);
     if constexpr (!std::is_same<R, float>::value) {   // from the row constants h/dt, c h, 2 h
-        const R hidt = (R)x.hidt[i];
+        const R hidt = lc<R>(x, 4, i, x.hidt);
         if (x.a_cell) {
-            const R hc = (R)x.h[i];
+            const R hc = lc<R>(x, 7, i, x.h);
             Ap = fma(hc, (R)x.a_cell[i], hidt);
             Dp = fma(hidt, Eo, hc * src_in<R>(x.s_cell[i], ks));
         } else {
-            Ap = fma((R)x.hc[i], (R)x.L.sig[(size_t)q * x.nx + i], hidt);
-            Dp = fma(hidt, Eo, (R)x.h2[i] * src_in<R>(x.L.emis[(size_t)q * x.nx + i], ks));
+            Ap = fma(lc<R>(x, 5, i, x.hc), (R)x.L.sig[(size_t)q * x.nx + i], hidt);
+            Dp = fma(hidt, Eo, lc<R>(x, 6, i, x.h2) * src_in<R>(x.L.emis[(size_t)q * x.nx + i], ks));
         }
         return;
     }
@@ -238,9 +247,9 @@ __device__ int lo_stage_pair(const LoCtx &x, int q, fpair *sm, int mmax)
             rawE[o] = Eo;
             rawS[o] = sv;
             m = max(m, max(bexp64(Eo), bexp64(sv)));
-            const fpair hidt = (fpair)x.hidt[f];
-            Ap[o] = x.a_cell ? fma((fpair)x.h[f], (fpair)x.a_cell[f], hidt)
-                             : fma((fpair)x.hc[f], (fpair)x.L.sig[(size_t)q * n + f], hidt);
+            const fpair hidt = lc<fpair>(x, 4, f, x.hidt);
+            Ap[o] = x.a_cell ? fma(lc<fpair>(x, 7, f, x.h), (fpair)x.a_cell[f], hidt)
+                             : fma(lc<fpair>(x, 5, f, x.hc), (fpair)x.L.sig[(size_t)q * n + f], hidt);
         }
     }
     if (t == 0)
@@ -265,7 +274,8 @@ __device__ int lo_stage_pair(const LoCtx &x, int q, fpair *sm, int mmax)
         if (f < n) {
             const fpair sv = pr_split(rawS[o], ks);
             const fpair Eo = pr_split(rawE[o], ks);
-            Dp[o] = fma((fpair)x.hidt[f], Eo, (x.a_cell ? (fpair)x.h[f] : (fpair)x.h2[f]) * sv);
+            Dp[o] = fma(lc<fpair>(x, 4, f, x.hidt), Eo,
+                        (x.a_cell ? lc<fpair>(x, 7, f, x.h) : lc<fpair>(x, 6, f, x.h2)) * sv);
         }
     }
     return ks;
@@ -664,8 +674,10 @@ __device__ void lo_solve_body(const LoCtx &x, int q, int sw)
     if (solver) warp_lo_solve<R>(x, q, sm, mmax, false, ks);
 }
 
+// 7 CTAs per SM (at most 72 registers): one wave of 1064 holds every group of a 1024-group
+// level
 template <typename R>
-__global__ void __launch_bounds__(128) k_lo_solve(LoCtx x)
+__global__ void __launch_bounds__(128, 7) k_lo_solve(LoCtx x)
 {
     if (x.gate && *x.gate) return;   // the phase's inner loop has ended
     lo_solve_body<R>(x, blockIdx.x, blockIdx.x);
@@ -1424,20 +1436,45 @@ __global__ void __launch_bounds__(256) k_copy_b(const int *__restrict__ meta, in
 }  // namespace
 
 namespace {
+// h/dt per cell and hf/(c dt) per face; with pc (the pair form) every row constant again
+// as a pair, [8][nx+1]: hf, dxicdt, fwl, fwr (faces), hidt, hc, h2, h (cells)
 __global__ void k_lo_consts(int nx, const double *__restrict__ h, const double *__restrict__ hf,
-                            double idt, double icdt, double *hidt, double *dxicdt)
+                            double idt, double icdt, double *hidt, double *dxicdt,
+                            const double *__restrict__ hc, const double *__restrict__ h2,
+                            const double *__restrict__ fwl, const double *__restrict__ fwr,
+                            fpair *pc)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < nx) hidt[i] = h[i] * idt;
-    if (i <= nx) dxicdt[i] = hf[i] * icdt;
+    const size_t n1 = (size_t)nx + 1;
+    if (i < nx) {
+        const double v = h[i] * idt;
+        hidt[i] = v;
+        if (pc) {
+            pc[4 * n1 + i] = fpair(v);
+            pc[5 * n1 + i] = fpair(hc[i]);
+            pc[6 * n1 + i] = fpair(h2[i]);
+            pc[7 * n1 + i] = fpair(h[i]);
+        }
+    }
+    if (i <= nx) {
+        const double v = hf[i] * icdt;
+        dxicdt[i] = v;
+        if (pc) {
+            pc[i] = fpair(hf[i]);
+            pc[n1 + i] = fpair(v);
+            pc[2 * n1 + i] = fpair(fwl[i]);
+            pc[3 * n1 + i] = fpair(fwr[i]);
+        }
+    }
 }
 }  // namespace
 
 cudaError_t ensure_lo_consts(Problem &p, double dt)
 {
     if (p.lo_dt == dt) return cudaSuccess;
-    k_lo_consts<<<(p.nx + 1 + 255) / 256, 256, 0, p.stream>>>(p.nx, p.h, p.hf, 1.0 / dt,
-                                                                1.0 / (kC * dt), p.hidt, p.dxicdt);
+    k_lo_consts<<<(p.nx + 1 + 255) / 256, 256, 0, p.stream>>>(
+        p.nx, p.h, p.hf, 1.0 / dt, 1.0 / (kC * dt), p.hidt, p.dxicdt, p.hc, p.h2, p.fwl, p.fwr,
+        reinterpret_cast<fpair *>(p.lopc));
     const cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) p.lo_dt = dt;
     return e;
@@ -1451,6 +1488,7 @@ LoCtx make_lo_ctx(const Problem &p, double dt, const Level &L)
     x.hf = p.hf;
     x.hc = p.hc; x.h2 = p.h2; x.fwl = p.fwl; x.fwr = p.fwr; x.hidt = p.hidt; x.dxicdt = p.dxicdt;
     x.lo_slot = p.lo_slot;
+    x.pc = reinterpret_cast<const fpair *>(p.lopc);
     x.L = L;
     x.a_cell = nullptr; x.s_cell = nullptr;
     x.gate = p.gate;

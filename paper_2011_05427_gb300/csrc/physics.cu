@@ -561,8 +561,9 @@ __device__ inline void opacity_body(const OpacityArgs &a, int i, int g, const Ce
 // nu_g/T, by pr_exp as a pair times 2^k -- the power of two goes into the exponent of the
 // FP64 result (pr_join), so e_g keeps FP64's range.  Relative errors: about 1e-14 in the
 // opacities, about 3 2^-47 max(1, |w|) in e_g (w's: nu_g, 1/T and their product each
-// rounded to a pair; 1.6e-11 at the smallest e_g that FP64 holds, e^-746).  Cells outside
-// the tables and the T_r option take opacity_body.
+// rounded to a pair; 1.6e-11 at the smallest e_g that FP64 holds, e^-746).  m, tf: the
+// cell's table interval (>= 0) and FP32 local coordinate; cells outside the tables and the
+// T_r option take opacity_body (the callers' choice).
 __device__ inline fpair horner_pair(const fpair *__restrict__ a, const float *__restrict__ b,
                                    fpair t, float tf)
 {
@@ -575,22 +576,18 @@ __device__ inline fpair horner_pair(const fpair *__restrict__ a, const float *__
     return p;
 }
 
-__device__ inline void opacity_body_pair(const OpacityArgs &a, int i, int g, const CellVals &v,
-                                         const CellPair &cp, const fpair *e2p, const Mx &mx)
+__device__ inline void opacity_body_pair(const OpacityArgs &a, int i, int g, int m, float tf,
+                                         const CellPair &cp, const fpair *e2p)
 {
-    if (v.m < 0 || a.Erad) {
-        opacity_body(a, i, g, v, mx);
-        return;
-    }
     const size_t idx = (size_t)g * a.nx + i;
-    const fpair *c = a.otabp + ((size_t)g * kTabNI + v.m) * kTabEntry;
+    const fpair *c = a.otabp + ((size_t)g * kTabNI + m) * kTabEntry;
     const float *ch = reinterpret_cast<const float *>(c + kTabNF * kTabLo);
     constexpr int kh = kTabNC - kTabLo;
-    const fpair sg = horner_pair(c, ch, cp.t, v.tf) * cp.iT3;
-    const fpair sR = horner_pair(c + kTabLo, ch + kh, cp.t, v.tf) * cp.iT3;
+    const fpair sg = horner_pair(c, ch, cp.t, tf) * cp.iT3;
+    const fpair sR = horner_pair(c + kTabLo, ch + kh, cp.t, tf) * cp.iT3;
     const fpair xa = a.otabp[(size_t)a.G * kTabNI * kTabEntry + g] * cp.iT;
     int k;
-    const fpair em = cp.kET * pr_exp(horner_pair(c + 2 * kTabLo, ch + 2 * kh, cp.t, v.tf) - xa,
+    const fpair em = cp.kET * pr_exp(horner_pair(c + 2 * kTabLo, ch + 2 * kh, cp.t, tf) - xa,
                                      k, e2p);
     a.sigE[idx] = pr_join(sg, 0);
     a.emis[idx] = pr_join(em, k);
@@ -649,13 +646,15 @@ __global__ void __launch_bounds__(256) k_opacity(OpacityArgs a)
     if (a.otabp) stage_exp_pairs(s_e2p);
     const int i = blockIdx.x * 32 + threadIdx.x, g = blockIdx.y * 8 + threadIdx.y;
     if (i >= a.nx || g >= a.G) return;
-    if (a.otabp) {
+    const CellArrays ca = cell_arrays(a);
+    const int m = ca.m[i];
+    if (a.otabp && m >= 0 && !a.Erad) {
         const int n = a.nx;
         const CellPair cp{a.cpair[i], a.cpair[n + i], a.cpair[2 * n + i], a.cpair[3 * n + i],
                           a.cpair[4 * n + i]};
-        opacity_body_pair(a, i, g, cell_arrays(a).get(i), cp, s_e2p, mx);
+        opacity_body_pair(a, i, g, m, ca.f[i], cp, s_e2p);
     } else {
-        opacity_body(a, i, g, cell_arrays(a).get(i), mx);
+        opacity_body(a, i, g, ca.get(i), mx);
     }
 }
 
@@ -674,10 +673,11 @@ __global__ void __launch_bounds__(256) k_opacity_b(const int *__restrict__ meta,
         stage_cells(a, bx * 32, ct, b);
         const int i = bx * 32 + threadIdx.x, g = by * 8 + threadIdx.y;
         if (i < a.nx && g < a.G) {
-            if (a.otabp)
-                opacity_body_pair(a, i, g, ct.v[threadIdx.x], ct.p[threadIdx.x], s_e2p, mx);
+            const CellVals &v = ct.v[threadIdx.x];
+            if (a.otabp && v.m >= 0 && !a.Erad)
+                opacity_body_pair(a, i, g, v.m, v.tf, ct.p[threadIdx.x], s_e2p);
             else
-                opacity_body(a, i, g, ct.v[threadIdx.x], mx);
+                opacity_body(a, i, g, v, mx);
         }
         __syncthreads();   // the cell terms are restaged by the next work item
     }

@@ -42,7 +42,7 @@ def same(a, b):
 
 @pytest.mark.parametrize("cycle,lmax,eps,max_outer", [("V", 4, 1e-8, 100), ("W", 2, 1e-8, 100),
                                                       ("F", 2, 1e-8, 100), ("W", 1, -1.0, 3)])
-@pytest.mark.parametrize("precision", ["fp64", "sweep32"])
+@pytest.mark.parametrize("precision", ["fp64", "sweep32", "sweep32_lopair"])
 def test_batch_equals_single_slabs(trt, cycle, lmax, eps, max_outer, precision):
     slabs = mixed_slabs()
     B = trt.Batch(slabs, precision=precision)
