@@ -209,6 +209,7 @@ __global__ void k_phase_start(int nx, int from_grey, const double *__restrict__ 
                               const double *__restrict__ Egrey, double *Tphase, double *Tcyc,
                               double *Ephase, double *Ecyc, int *ctl)
 {
+    griddep_wait();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < nx) {
         const double t = T[i];
@@ -224,9 +225,9 @@ __global__ void k_phase_start(int nx, int from_grey, const double *__restrict__ 
 cudaError_t launch_phase_start(const trt_handle *h, bool from_grey)
 {
     const int nx = h->p.nx;
-    k_phase_start<<<(nx + 255) / 256, 256, 0, h->p.stream>>>(
-        nx, from_grey ? 1 : 0, h->T, h->grey.E, h->Tphase, h->Tcyc, h->Ephase, h->Ecyc, h->ctl);
-    return cudaGetLastError();
+    return launch_pdl(k_phase_start, dim3((nx + 255) / 256), dim3(256), 0, h->p.stream, nx,
+                      from_grey ? 1 : 0, (const double *)h->T, (const double *)h->grey.E,
+                      h->Tphase, h->Tcyc, h->Ephase, h->Ecyc, h->ctl);
 }
 
 template <typename R>
@@ -323,6 +324,8 @@ int trt_create(const trt_grid *grid, const trt_angles *angles, const trt_groups 
     carve(H, c);
     {
         cudaError_t e = cudaMallocHost(&H->hflags, 10 * sizeof(double));
+        if (e != cudaSuccess) return fail(nullptr, TRT_ECUDA, cudaGetErrorString(e));
+        e = cudaEventCreateWithFlags(&H->ev_flags, cudaEventDisableTiming);
         if (e != cudaSuccess) return fail(nullptr, TRT_ECUDA, cudaGetErrorString(e));
     }
     const int nx = p.nx, G = p.G, M = p.M, N = p.N;
@@ -445,6 +448,7 @@ int trt_create(const trt_grid *grid, const trt_angles *angles, const trt_groups 
     }
     CK(cudaGetLastError());
     CK(launch_otab_build(p));   // opacity tables of this group structure
+    CK(launch_lo_pair_consts(p));
     CK(cudaMemsetAsync(H->flags, 0, 10 * sizeof(double), p.stream));
     CK(cudaStreamSynchronize(p.stream));
     *out = hp.release();
@@ -531,10 +535,15 @@ int trt_step(trt_handle *h, double dt, const trt_cycle *cyc, trt_stats *stats)
     int lo_per_cycle = G + K + 1;
     for (int k = 0; k < K; ++k) lo_per_cycle += p.levels[S[k] - 1];
 
+    bool opac_next = false;   // the phase's opacities already enqueued (below)
     for (;;) {
         if (s > 0) {
-            CK(launch_opacity(p, h->T, h->sigE, h->emis, h->sigR, h->sig32, h->emis32, dt, Erad));
-            ++nk;
+            if (!opac_next) {
+                CK(launch_opacity(p, h->T, h->sigE, h->emis, h->sigR, h->sig32, h->emis32, dt,
+                                  Erad));
+                ++nk;
+            }
+            opac_next = false;
             opac_valid = true;
             if (h->sig32)
                 CK(launch_sweep(p, dt, h->sig32, h->emis32, true, h->I_cur, h->I_alt, h->part,
@@ -603,7 +612,18 @@ int trt_step(trt_handle *h, double dt, const trt_cycle *cyc, trt_stats *stats)
         p.gate = nullptr;
         CK(cudaMemcpyAsync(h->hflags, h->flags, 10 * sizeof(double), cudaMemcpyDeviceToHost,
                            p.stream));
-        CK(cudaStreamSynchronize(p.stream));
+        CK(cudaEventRecord(h->ev_flags, p.stream));
+        // The next phase's opacity evaluation at the phase's final T goes in before the host
+        // reads the flags, so that it runs during the round trip.  A step that ends here
+        // begins the next one by evaluating the opacities at the same T, so nothing reads
+        // these values; the T_r option is left out (the panel loop of its quadrature needs
+        // a valid temperature, and a bad one is only known from the flags).
+        if (!p.tr_mode && s + 1 < cyc->max_outer) {
+            CK(launch_opacity(p, h->T, h->sigE, h->emis, h->sigR, h->sig32, h->emis32, dt, Erad));
+            ++nk;
+            opac_next = true;
+        }
+        CK(cudaEventSynchronize(h->ev_flags));
         const double *fl = h->hflags;
         n_c = reinterpret_cast<const int *>(fl + 8)[1];   // cycles run in the step so far
         if (fl[0] != 0.0) {

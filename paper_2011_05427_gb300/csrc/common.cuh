@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string>
+#include <utility>
 #include "../../include/trt.h"
 
 namespace trt {
@@ -113,6 +114,31 @@ __device__ inline double widen_f32(float q)
                                  ((unsigned long long)(e + 896u) << 52) |
                                  ((unsigned long long)(u & 0x7fffffu) << 29);
     return __longlong_as_double((long long)b);
+}
+
+// Programmatic dependent launch for the kernels of one low-order cycle, which run back to
+// back on one stream: the launch of kernel k+1 is processed while kernel k drains, and
+// k+1's first statement, griddep_wait(), holds every thread until k has completed and its
+// writes are visible.  A kernel launched this way must call griddep_wait() before it reads
+// or writes global memory (a no-op when the kernel was launched plainly).
+#ifdef __CUDACC__
+__device__ inline void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+#endif
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                       Args &&...args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k, std::forward<Args>(args)...);
 }
 
 const SeriesTables &host_series();   // host copy (built once)
@@ -230,7 +256,8 @@ struct Problem {
     // opacity evaluation [5][nx] (t, 1/T, 1/T^3, 27 s C_B T, h/2); null otherwise
     double *otabp = nullptr, *cpair = nullptr;
     // with TRT_LO_PAIR: the LO row constants as pairs, [8][nx+1] (hf, dxicdt, fwl, fwr per
-    // face; hidt, hc, h2, h per cell), written with hidt and dxicdt; null otherwise
+    // face; hidt, hc, h2, h per cell): the step-independent rows once per handle
+    // (launch_lo_pair_consts), hidt and dxicdt with ensure_lo_consts; null otherwise
     double *lopc = nullptr;
 };
 
@@ -273,6 +300,8 @@ cudaError_t launch_sweep(const Problem &p, double dt, const void *sigE, const vo
 cudaError_t launch_lo_solve(const Problem &p, double dt, const Level &L);
 // h/dt and hf/(c dt) of the LO rows for step length dt (a launch when dt changed)
 cudaError_t ensure_lo_consts(Problem &p, double dt);
+// the step-independent pair row constants (Problem::lopc; once per handle, TRT_LO_PAIR)
+cudaError_t launch_lo_pair_consts(const Problem &p);
 cudaError_t launch_restrict(const Problem &p, const Level &src, Level &dst);
 size_t restrict_scratch_doubles(int nx, int n_from, int n_to);
 cudaError_t launch_grey(const Problem &p, const Level &g, const GreyArgs &a);

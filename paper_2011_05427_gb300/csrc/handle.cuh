@@ -20,6 +20,7 @@ struct trt_handle {
     double *flags = nullptr;    // [10]: convergence flags [0..6], then the inner-loop
     int *ctl = nullptr;         // control words (ints in the last two doubles of flags)
     double *hflags = nullptr;   // pinned host mirror of flags + ctl, owned (freed below)
+    cudaEvent_t ev_flags = nullptr;   // recorded after each phase's flags copy, owned
     // learned closure (trt_set_closure): caller-owned device buffers, or null
     const float *mlp_params = nullptr;
     const void *mlp_w16 = nullptr;
@@ -30,6 +31,7 @@ struct trt_handle {
     ~trt_handle()
     {
         if (hflags) cudaFreeHost(hflags);
+        if (ev_flags) cudaEventDestroy(ev_flags);
     }
 };
 

@@ -679,6 +679,7 @@ __device__ void lo_solve_body(const LoCtx &x, int q, int sw)
 template <typename R>
 __global__ void __launch_bounds__(128, 7) k_lo_solve(LoCtx x)
 {
+    griddep_wait();
     if (x.gate && *x.gate) return;   // the phase's inner loop has ended
     lo_solve_body<R>(x, blockIdx.x, blockIdx.x);
 }
@@ -1382,21 +1383,25 @@ __device__ void group_sum_body(const GroupSumArgs &a, int bx)
 // (single-slab entry points: return at entry while the driver's gate is set)
 __global__ void __launch_bounds__(512) k_restrict(RestrictCtx x)
 {
+    griddep_wait();
     if (x.gate && *x.gate) return;
     restrict_body(x, blockIdx.x, blockIdx.y);
 }
 __global__ void __launch_bounds__(32 * kPartRows) k_restrict_part(Restrict2Ctx x)
 {
+    griddep_wait();
     if (x.gate && *x.gate) return;
     restrict_part_body(x, blockIdx.x, blockIdx.y);
 }
 __global__ void __launch_bounds__(32 * kRP) k_restrict_final(Restrict2Ctx x)
 {
+    griddep_wait();
     if (x.gate && *x.gate) return;
     restrict_final_body(x, blockIdx.x, blockIdx.y);
 }
 __global__ void __launch_bounds__(1024) k_grey(GreyCtx x)
 {
+    griddep_wait();
     if (x.lo.gate && *x.lo.gate) return;
     grey_body(x);
 }
@@ -1436,44 +1441,61 @@ __global__ void __launch_bounds__(256) k_copy_b(const int *__restrict__ meta, in
 }  // namespace
 
 namespace {
-// h/dt per cell and hf/(c dt) per face; with pc (the pair form) every row constant again
-// as a pair, [8][nx+1]: hf, dxicdt, fwl, fwr (faces), hidt, hc, h2, h (cells)
+// h/dt per cell and hf/(c dt) per face (for step length dt); with pc (the pair form) the
+// same two rows of Problem::lopc
 __global__ void k_lo_consts(int nx, const double *__restrict__ h, const double *__restrict__ hf,
-                            double idt, double icdt, double *hidt, double *dxicdt,
-                            const double *__restrict__ hc, const double *__restrict__ h2,
-                            const double *__restrict__ fwl, const double *__restrict__ fwr,
-                            fpair *pc)
+                            double idt, double icdt, double *hidt, double *dxicdt, fpair *pc)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const size_t n1 = (size_t)nx + 1;
     if (i < nx) {
         const double v = h[i] * idt;
         hidt[i] = v;
-        if (pc) {
-            pc[4 * n1 + i] = fpair(v);
-            pc[5 * n1 + i] = fpair(hc[i]);
-            pc[6 * n1 + i] = fpair(h2[i]);
-            pc[7 * n1 + i] = fpair(h[i]);
-        }
+        if (pc) pc[4 * n1 + i] = fpair(v);
     }
     if (i <= nx) {
         const double v = hf[i] * icdt;
         dxicdt[i] = v;
-        if (pc) {
-            pc[i] = fpair(hf[i]);
-            pc[n1 + i] = fpair(v);
-            pc[2 * n1 + i] = fpair(fwl[i]);
-            pc[3 * n1 + i] = fpair(fwr[i]);
-        }
+        if (pc) pc[n1 + i] = fpair(v);
     }
 }
+
+// the step-independent rows of Problem::lopc ([8][nx+1] pairs): hf, fwl, fwr (faces), hc,
+// h2, h (cells); once per handle
+__global__ void k_lo_pair_consts(int nx, const double *__restrict__ h, const double *__restrict__ hf,
+                                 const double *__restrict__ hc, const double *__restrict__ h2,
+                                 const double *__restrict__ fwl, const double *__restrict__ fwr,
+                                 fpair *pc)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const size_t n1 = (size_t)nx + 1;
+    if (i < nx) {
+        pc[5 * n1 + i] = fpair(hc[i]);
+        pc[6 * n1 + i] = fpair(h2[i]);
+        pc[7 * n1 + i] = fpair(h[i]);
+    }
+    if (i <= nx) {
+        pc[i] = fpair(hf[i]);
+        pc[2 * n1 + i] = fpair(fwl[i]);
+        pc[3 * n1 + i] = fpair(fwr[i]);
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_lo_pair_consts(const Problem &p)
+{
+    if (!p.lopc) return cudaSuccess;
+    k_lo_pair_consts<<<(p.nx + 1 + 255) / 256, 256, 0, p.stream>>>(
+        p.nx, p.h, p.hf, p.hc, p.h2, p.fwl, p.fwr, reinterpret_cast<fpair *>(p.lopc));
+    return cudaGetLastError();
+}
 
 cudaError_t ensure_lo_consts(Problem &p, double dt)
 {
     if (p.lo_dt == dt) return cudaSuccess;
     k_lo_consts<<<(p.nx + 1 + 255) / 256, 256, 0, p.stream>>>(
-        p.nx, p.h, p.hf, 1.0 / dt, 1.0 / (kC * dt), p.hidt, p.dxicdt, p.hc, p.h2, p.fwl, p.fwr,
+        p.nx, p.h, p.hf, 1.0 / dt, 1.0 / (kC * dt), p.hidt, p.dxicdt,
         reinterpret_cast<fpair *>(p.lopc));
     const cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) p.lo_dt = dt;
@@ -1520,19 +1542,18 @@ cudaError_t launch_lo_solve(const Problem &p, double dt, const Level &L)
         e = cudaFuncSetAttribute(k_lo_solve<fpair>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)sm);
         if (e != cudaSuccess) return e;
-        k_lo_solve<fpair><<<nb, 128, sm, p.stream>>>(x);
+        return launch_pdl(k_lo_solve<fpair>, dim3(nb), dim3(128), sm, p.stream, x);
     } else if (!lo_refined(p.precision, p.nx)) {
         e = cudaFuncSetAttribute(k_lo_solve<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)sm);
         if (e != cudaSuccess) return e;
-        k_lo_solve<double><<<nb, 128, sm, p.stream>>>(x);
+        return launch_pdl(k_lo_solve<double>, dim3(nb), dim3(128), sm, p.stream, x);
     } else {
         e = cudaFuncSetAttribute(k_lo_solve<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)sm);
         if (e != cudaSuccess) return e;
-        k_lo_solve<float><<<nb, 128, sm, p.stream>>>(x);
+        return launch_pdl(k_lo_solve<float>, dim3(nb), dim3(128), sm, p.stream, x);
     }
-    return cudaGetLastError();
 }
 
 cudaError_t launch_lo_solve_b(int precision, int max_nx, const int *meta, int N,
@@ -1609,11 +1630,10 @@ cudaError_t launch_restrict(const Problem &p, const Level &src, Level &dst)
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)kPartSmem);
         if (e != cudaSuccess) return e;
-        k_restrict_part<<<g1, dim3(32, kPartRows), kPartSmem, p.stream>>>(y);
-        e = cudaGetLastError();
+        e = launch_pdl(k_restrict_part, g1, dim3(32, kPartRows), kPartSmem, p.stream, y);
         if (e != cudaSuccess) return e;
-        k_restrict_final<<<dim3((p.nx + 1 + 31) / 32, dst.n), dim3(32, kRP), 0, p.stream>>>(y);
-        return cudaGetLastError();
+        return launch_pdl(k_restrict_final, dim3((p.nx + 1 + 31) / 32, dst.n), dim3(32, kRP), 0,
+                          p.stream, y);
     }
     const RestrictCtx x = make_restrict_ctx(p, src, dst);
     dim3 grid((p.nx + 1 + 31) / 32, dst.n);
@@ -1621,8 +1641,7 @@ cudaError_t launch_restrict(const Problem &p, const Level &src, Level &dst)
     cudaError_t e = cudaFuncSetAttribute(k_restrict, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)sm);
     if (e != cudaSuccess) return e;
-    k_restrict<<<grid, dim3(32, KS), sm, p.stream>>>(x);
-    return cudaGetLastError();
+    return launch_pdl(k_restrict, grid, dim3(32, KS), sm, p.stream, x);
 }
 
 cudaError_t launch_restrict_b(int KS, const int *meta, int N, const RestrictCtx *xs, int grid,
@@ -1685,8 +1704,7 @@ cudaError_t launch_grey(const Problem &p, const Level &g, const GreyArgs &a)
     cudaError_t e = cudaFuncSetAttribute(k_grey, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)sm);
     if (e != cudaSuccess) return e;
-    k_grey<<<1, bs, sm, p.stream>>>(x);
-    return cudaGetLastError();
+    return launch_pdl(k_grey, dim3(1), dim3(bs), sm, p.stream, x);
 }
 
 cudaError_t launch_grey_b(int max_nx, const int *meta, int N, const GreyCtx *xs, int grid,

@@ -619,6 +619,7 @@ __device__ inline void stage_exp_pairs(fpair *s_e2p)
 // the per-cell terms of one evaluation (single slab); the pair form's too
 __global__ void k_cell_terms(OpacityArgs a)
 {
+    griddep_wait();
     if (a.gate && *a.gate) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= a.nx) return;
@@ -639,6 +640,7 @@ __global__ void k_cell_terms(OpacityArgs a)
 // k_cell_terms
 __global__ void __launch_bounds__(256) k_opacity(OpacityArgs a)
 {
+    griddep_wait();
     if (a.gate && *a.gate) return;   // the phase's inner loop has ended (every thread alike)
     __shared__ double s_e2[32];
     __shared__ fpair s_e2p[32];
@@ -893,9 +895,9 @@ cudaError_t launch_opacity(const Problem &p, const double *T, double *sigE, doub
                            const double *Erad)
 {
     const OpacityArgs a = make_opacity_args(p, T, sigE, emis, sigR, sig32, emis32, dt, Erad);
-    k_cell_terms<<<(p.nx + 127) / 128, 128, 0, p.stream>>>(a);
-    k_opacity<<<dim3(opacity_gx(p), (p.G + 7) / 8), dim3(32, 8), 0, p.stream>>>(a);
-    return cudaGetLastError();
+    cudaError_t e = launch_pdl(k_cell_terms, dim3((p.nx + 127) / 128), dim3(128), 0, p.stream, a);
+    if (e != cudaSuccess) return e;
+    return launch_pdl(k_opacity, dim3(opacity_gx(p), (p.G + 7) / 8), dim3(32, 8), 0, p.stream, a);
 }
 
 cudaError_t launch_opacity_b(const int *meta, int N, const OpacityArgs *xs, int grid,

@@ -255,6 +255,7 @@ __device__ void sweep_body(const SweepArgs &a, int dtile, int gt)
 template <typename R, typename SR, int kStrip, int NS>
 __global__ void __launch_bounds__(256) k_sweep(SweepArgs a)
 {
+    griddep_wait();
     sweep_body<R, SR, kStrip, NS>(a, blockIdx.x, blockIdx.y);
 }
 
@@ -390,6 +391,7 @@ __device__ void finalize_body(const FinalizeArgs &x, int bx)
 template <typename R>
 __global__ void k_sweep_finalize(FinalizeArgs x)
 {
+    griddep_wait();
     finalize_body<R>(x, blockIdx.x);
 }
 
@@ -446,7 +448,7 @@ cudaError_t launch_shape(const SweepArgs *a, int M, int ldG, int D, const int *m
         cudaError_t e = cudaFuncSetAttribute(k_sweep<R, SR, S, NS>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
-        k_sweep<R, SR, S, NS><<<dim3(M / D, ldG / 32), 32 * D, sm, st>>>(*a);
+        return launch_pdl(k_sweep<R, SR, S, NS>, dim3(M / D, ldG / 32), dim3(32 * D), sm, st, *a);
     } else {
         cudaError_t e = cudaFuncSetAttribute(k_sweep_b<R, SR, S, NS>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
@@ -485,7 +487,10 @@ cudaError_t launch_sweep_t(const Problem &p, const SweepArgs &a)
                                       p.stream);
     if (e != cudaSuccess) return e;
     const FinalizeArgs fa = make_finalize_args(p, a);
-    k_sweep_finalize<R><<<(unsigned)(fa.nb_cell + finalize_bnd_blocks(p.G)), 256, 0, p.stream>>>(fa);
+    cudaError_t ef = launch_pdl(k_sweep_finalize<R>,
+                                dim3((unsigned)(fa.nb_cell + finalize_bnd_blocks(p.G))), dim3(256),
+                                0, p.stream, fa);
+    if (ef != cudaSuccess) return ef;
     return cudaGetLastError();
 }
 

@@ -70,6 +70,7 @@ struct PairSmem {
 template <int S, int NS>
 __global__ void __launch_bounds__(64 * kPD) k_sweep_pair(SweepArgs a)
 {
+    griddep_wait();
     using L = PairSmem<S, NS>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -257,6 +258,7 @@ __global__ void k_prescale64(int nx, int G, int ldG, const double *__restrict__ 
                              const double *__restrict__ sigE, const double *__restrict__ emis,
                              double *th64, double *q64)
 {
+    griddep_wait();
     __shared__ double sth[32][33], sq[32][33];
     const int c0 = blockIdx.x * 32, g0 = blockIdx.y * 32;
     const int tx = threadIdx.x, ty = threadIdx.y;   // 32 x 8
@@ -299,9 +301,9 @@ cudaError_t launch_sweep_pair(int S, int NS, const SweepArgs &a, int M, int ldG,
     const double *emis = reinterpret_cast<const double *>(a.emis);
     double *tab64 = a.tab64;
     const int nx = a.nx, G = a.G;
-    k_prescale64<<<dim3((nx + 31) / 32, (ldG + 31) / 32), dim3(32, 8), 0, st>>>(
-        nx, G, ldG, a.h, a.icdt, sigE, emis, tab64, tab64 + (size_t)nx * ldG);
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e = launch_pdl(k_prescale64, dim3((nx + 31) / 32, (ldG + 31) / 32), dim3(32, 8),
+                               0, st, nx, G, ldG, (const double *)a.h, a.icdt, sigE, emis, tab64,
+                               tab64 + (size_t)nx * ldG);
     if (e != cudaSuccess) return e;
     SweepArgs x = a;
     x.sigE = tab64;
@@ -311,8 +313,7 @@ cudaError_t launch_sweep_pair(int S, int NS, const SweepArgs &a, int M, int ldG,
         cudaError_t r = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)sm);
         if (r != cudaSuccess) return r;
-        kern<<<grid, 64 * kPD, sm, st>>>(x);
-        return cudaGetLastError();
+        return launch_pdl(kern, grid, dim3(64 * kPD), sm, st, x);
     };
     if (S == 8 && NS == 2) return go(k_sweep_pair<8, 2>, PairSmem<8, 2>::total);
     if (S == 4 && NS == 2) return go(k_sweep_pair<4, 2>, PairSmem<4, 2>::total);

@@ -329,6 +329,7 @@ template <int GPL, int S, int NS, int D>
 __global__ void __launch_bounds__(32 * D, (SweepFSmem<GPL, S, NS, D>::minb))
 k_sweepf(SweepArgs a)
 {
+    griddep_wait();
     sweepf_body<GPL, S, NS, D>(a, blockIdx.x, blockIdx.y);
 }
 
@@ -356,7 +357,8 @@ cudaError_t launch_f(const SweepArgs *a, int M, int ldG, const int *meta, int N,
         cudaError_t e = cudaFuncSetAttribute(k_sweepf<GPL, S, NS, D>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
-        k_sweepf<GPL, S, NS, D><<<dim3(M / D, (ldG + W - 1) / W), 32 * D, sm, st>>>(*a);
+        return launch_pdl(k_sweepf<GPL, S, NS, D>, dim3(M / D, (ldG + W - 1) / W), dim3(32 * D),
+                          sm, st, *a);
     } else {
         cudaError_t e = cudaFuncSetAttribute(k_sweepf_b<GPL, S, NS, D>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);

@@ -360,6 +360,7 @@ def test_lo_solve_parity(trt, orc, nx, ng):
         assert np.max(np.abs(got["EbX"] - ref["EbX"]) / (np.abs(ref["EbX"]) + ref["E"][:, -1])) < 10 * tol
 
 
+@pytest.mark.parametrize("precision", ["fp64", "lopair"])
 @pytest.mark.parametrize("n_from,n_to,eta,nx,fine",
                          [(16, 4, False, 37, False), (12, 1, True, 37, False),
                           (1024, 256, False, 37, False), (64, 1, True, 37, False),
@@ -369,7 +370,9 @@ def test_lo_solve_parity(trt, orc, nx, ng):
                           (1024, 1, False, 500, True), (512, 2, True, 129, False),
                           (1024, 256, False, 520, True), (256, 1, True, 520, False),
                           (256, 64, True, 1000, False), (64, 16, True, 520, False)])
-def test_restrict_parity(trt, orc, n_from, n_to, eta, nx, fine):
+def test_restrict_parity(trt, orc, n_from, n_to, eta, nx, fine, precision):
+    # the restriction is FP64 in every precision form: the pair form's handle (row constants
+    # in pairs) runs it unchanged
     r = W.rng(4000 + n_from + n_to + nx)
     h = W.random_h(r, nx)
     lv = random_level(r, n_from, nx, eta=eta)
@@ -380,7 +383,8 @@ def test_restrict_parity(trt, orc, n_from, n_to, eta, nx, fine):
     sol = oracle_level_solve(orc, h, 2e-3, lv)
     # a handle with n_from groups carves the partial-sum scratch of the two-stage
     # restriction used for coarse groups of >= 64 members
-    s = solver(trt, nx=nx, N=2, G=max(n_from, 3), h=h, levels=[max(n_from, 3), 1])
+    s = solver(trt, nx=nx, N=2, G=max(n_from, 3), h=h, levels=[max(n_from, 3), 1],
+               precision=precision)
     src.update(sol)
     got = {k: v.cpu().numpy() for k, v in s.k_restrict(src, n_to, fine=fine).items()}
     cmap = np.arange(n_from) // (n_from // n_to)
@@ -391,6 +395,53 @@ def test_restrict_parity(trt, orc, n_from, n_to, eta, nx, fine):
             # relative to the sigma_R dx F terms it compensates
             scale = np.max(np.abs(ref[k])) + 1e-300
             assert np.max(np.abs(got[k] - ref[k])) <= 1e-9 * scale, k
+        elif k == "Fold":
+            assert np.max(np.abs(got[k] - ref[k])) <= 1e-12 * np.abs(ref[k]).max(), k
+        else:
+            assert rel(got[k], ref[k]) < 1e-12, k
+    assert rel(got["Esum"], Esum) < 1e-13
+
+
+@pytest.mark.parametrize("precision", ["fp64", "lopair"])
+@pytest.mark.parametrize("fine", [False, True])
+def test_restrict_wide_range(trt, orc, fine, precision):
+    """The two-stage restriction on values hundreds of decades apart: member energies over
+    1e-300 .. 1 (neighbouring cells too), emission up to 1e100 above E (a temperature that
+    has just risen), Eold and Fold independent of E, against the FP64 oracle, 1024 members
+    to one coarse group (the restriction is FP64 in every precision form)."""
+    nx, n_from, n_to = 97, 1024, 1
+    r = W.rng(4321 + fine)
+    h = W.random_h(r, nx)
+    lv = random_level(r, n_from, nx, eta=not fine)   # a fine level has no compensation
+    E = np.exp(r.uniform(-690, 0, (n_from, nx)))
+    lv["emis"] = E * np.exp(r.uniform(0, 230, (n_from, nx)))
+    lv["Eold"] = np.exp(r.uniform(-690, 0, (n_from, nx)))
+    lv["Fold"] = r.normal(0, 1, (n_from, nx + 1)) * np.exp(r.uniform(-600, 0, (n_from, nx + 1)))
+    src = dict(lv)
+    if fine:
+        src["sigR"] = np.exp(r.uniform(-3, 3, (n_from, nx)))
+        lv["sigR"] = orc.fine_face_sigR(h, src["sigR"])
+    Ef = np.concatenate([E[:, :1], E], axis=1)
+    sol = dict(E=E, F=r.uniform(-1, 1, (n_from, nx + 1)) * Ef * C,
+               Eb0=E[:, 0] * r.uniform(0.5, 1.5, n_from), EbX=E[:, -1] * r.uniform(0.5, 1.5, n_from))
+    s = solver(trt, nx=nx, N=2, G=n_from, h=h, levels=[n_from, 1], precision=precision)
+    src.update(sol)
+    got = {k: v.cpu().numpy() for k, v in s.k_restrict(src, n_to, fine=fine).items()}
+    ref, Esum = orc.restrict(h, lv, sol, np.zeros(n_from, int), n_to)
+    # the two-stage path forms the compensation xi in one pass: equal to the oracle's
+    # two-pass form up to rounding relative to the terms dx sigR F and c eta E it is made
+    # of, and eta = xi / (c sum E_side) carries that rounding over the side's energy
+    dxf = np.concatenate([[h[0] / 2], (h[:-1] + h[1:]) / 2, [h[-1] / 2]])
+    ER = np.concatenate([E, sol["EbX"][:, None]], axis=1)
+    EL = np.concatenate([sol["Eb0"][:, None], E], axis=1)
+    terms = dxf * np.sum(np.abs(lv["sigR"] * sol["F"]), 0) + \
+        C * np.sum(np.abs(lv["etaR"] * ER) + np.abs(lv["etaL"] * EL), 0)
+    for k in orc.LEVEL_KEYS:
+        assert np.all(np.isfinite(got[k])), k
+        if k in ("etaR", "etaL"):
+            side = ER if k == "etaR" else EL
+            bound = 1e-12 * terms / (C * np.sum(side, 0)) + 1e-9 * np.max(np.abs(ref[k]))
+            assert np.all(np.abs(got[k] - ref[k])[0] <= bound), k
         elif k == "Fold":
             assert np.max(np.abs(got[k] - ref[k])) <= 1e-12 * np.abs(ref[k]).max(), k
         else:
