@@ -111,6 +111,7 @@ void carve(trt_handle *h, Carver &c)
     h->psi_exit = c.take<double>(M * (size_t)p.ldG);
     h->E1 = c.take<double>(G * nx); h->F1 = c.take<double>(G * (nx + 1));
     h->Eb0_1 = c.take<double>(G); h->EbX_1 = c.take<double>(G);
+    h->gpre = c.take<double>(3 * nx);
     int n2 = (p.nlev >= 3) ? p.levels[1] : 1;
     carve_level(c, h->crs, n2, p.nx);
     carve_level(c, h->grey, 1, p.nx);
@@ -588,7 +589,6 @@ int trt_step(trt_handle *h, double dt, const trt_cycle *cyc, trt_stats *stats)
                     nk += 3;
                     src = &h->crs;
                 }
-                CK(launch_restrict(p, *src, h->grey));
                 GreyArgs a{};
                 a.Tstar = Tst; a.Told = h->Told; a.sig_prev = h->sig_prev; a.T_prev = h->T_prev;
                 a.T = Tout; a.sig_prev_out = h->sig_prev; a.T_prev_out = h->T_prev;
@@ -603,6 +603,12 @@ int trt_step(trt_handle *h, double dt, const trt_cycle *cyc, trt_stats *stats)
                     a.Tcyc_out = h->Tcyc; a.Ecyc_out = h->Ecyc;
                     a.ctl = h->ctl; a.eps_in = eps_in; a.fixed = fixed ? 1 : 0;
                 }
+                // the restriction to the grey level, which forms the visit's per-cell
+                // Newton terms too where its two-stage form runs
+                const GreyArgs ready = grey_args_ready(p, a);
+                bool formed = false;
+                CK(launch_restrict(p, *src, h->grey, &ready, h->gpre, &formed));
+                a.pre = formed ? h->gpre : nullptr;
                 CK(launch_grey(p, h->grey, a));
                 nk += 2;   // restriction to grey + grey Newton
                 have_prev = 1;

@@ -88,6 +88,11 @@ struct Restrict2Ctx {
     Level S, T;
     double *part;   // [n_to][nchunk][kRP][nx+1]
     const int *gate;
+    // the grey visit's per-cell Newton terms, formed by the final stage when newton != 0
+    // (single slab, target = the grey level): into pre [3][nx], with the visit's arguments
+    int newton;
+    GreyArgs ga;
+    double *pre;
 };
 
 struct GreyCtx {

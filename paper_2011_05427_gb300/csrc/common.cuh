@@ -201,6 +201,11 @@ struct GreyArgs {
     double cvdt, k54;
     const double *e2;
     ExpConsts ec;
+    // the per-cell Newton terms w c sig*, w Q* - (1 - w) c_v (T* - Told)/dt and 1/Lambda,
+    // [3][nx], when the restriction to the grey level already formed them (its second
+    // stage, from the same values with the same operations); null: the grey kernel forms
+    // them
+    const double *pre;
 };
 
 inline bool sweep_fp32(int precision) { return (precision & TRT_SWEEP_FP32) != 0; }
@@ -302,7 +307,13 @@ cudaError_t launch_lo_solve(const Problem &p, double dt, const Level &L);
 cudaError_t ensure_lo_consts(Problem &p, double dt);
 // the step-independent pair row constants (Problem::lopc; once per handle, TRT_LO_PAIR)
 cudaError_t launch_lo_pair_consts(const Problem &p);
-cudaError_t launch_restrict(const Problem &p, const Level &src, Level &dst);
+// newton (with pre): the visit's grey Newton arguments; the two-stage restriction to the
+// grey level then also forms the per-cell Newton terms into pre ([3][nx]) and sets *formed
+cudaError_t launch_restrict(const Problem &p, const Level &src, Level &dst,
+                            const GreyArgs *newton = nullptr, double *pre = nullptr,
+                            bool *formed = nullptr);
+// the host-formed constants of a grey visit (c_v/dt, 54 s C_B, the exponential's table)
+GreyArgs grey_args_ready(const Problem &p, const GreyArgs &a);
 size_t restrict_scratch_doubles(int nx, int n_from, int n_to);
 cudaError_t launch_grey(const Problem &p, const Level &g, const GreyArgs &a);
 cudaError_t launch_group_sum(const Problem &p, int n, const double *X, double *out);

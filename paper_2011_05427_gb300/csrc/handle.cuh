@@ -15,6 +15,7 @@ struct trt_handle {
     float *sig32 = nullptr, *emis32 = nullptr;   // FP32 copies for an FP32 sweep
     double *part, *psi_exit;
     double *E1, *F1, *Eb0_1, *EbX_1;
+    double *gpre;   // [3][nx]: the grey Newton terms formed by the restriction
     trt::Level crs, grey;
     double *Ecyc, *Ephase;
     double *flags = nullptr;    // [10]: convergence flags [0..6], then the inner-loop

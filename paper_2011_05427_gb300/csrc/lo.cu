@@ -705,6 +705,49 @@ __global__ void __launch_bounds__(128) k_lo_solve_b(const int *__restrict__ meta
 // restriction (eqs. coeff-gamma, g-notation, eta-gamma / coeff-Gamma, g2G-notation,
 // eta-Gamma, and the discrete compensation of eq. mloqd-d-gamma)
 // ---------------------------------------------------------------------------------------
+// Per-cell terms of the grey Newton step (Sec. 5, eqs. eb-Gamma and f-derivative-d): from the
+// grey opacity sig*, Q* = 2 e* and the group energy sum Esum of cell i at T*, the
+// absorption w c sig*, the source w Q* - (1 - w) c_v (T* - Told)/dt and 1/Lambda.  Called
+// by the grey kernel on the grey level's arrays, or by the restriction's second stage on
+// the same values it writes there (the same operations, the same bits).
+__device__ inline void grey_newton_terms(const GreyArgs &a, int have_prev, int i, double sig,
+                                         double Q, double Esum, double &sa, double &ss,
+                                         double &sL)
+{
+    const double cvdt = a.cvdt;
+    const double k54 = a.k54;
+    const double Ts = a.Tstar[i];
+    const double iTs = rcp64(Ts);
+    double dQ = k54;   // first edge at 0: (1 + x) e^{-x} = 1
+    if (a.nu_first != 0.0) {
+        const double x1 = a.nu_first * iTs;
+        dQ = k54 * (1.0 + x1) * texp(-x1, a.e2, a.ec);
+    }
+    if (!isinf(a.nu_last)) {
+        const double xL = a.nu_last * iTs;
+        dQ -= k54 * (1.0 + xL) * texp(-xL, a.e2, a.ec);
+    }
+    double D = 0.0;
+    if (have_prev) {
+        const double Tp = a.T_prev[i];
+        // T* != T_prev on the encodings (positive finite values: integer instructions, not
+        // an FP64 compare); across grids only where |dT| is far above rounding (relative
+        // noise ~ eps T/|dT|)
+        const bool moved = __double_as_longlong(Ts) != __double_as_longlong(Tp);
+        const bool cut = __double_as_longlong(a.secant_cut) != 0ll;
+        if (moved && (!cut || fabs(Ts - Tp) > a.secant_cut * Ts))
+            D = (sig - a.sig_prev[i]) * rcp64(Ts - Tp);
+    }
+    const double base = cvdt + dQ;
+    double L = base - kC * D * Esum;
+    if (L < 0.5 * base) L = 0.5 * base;
+    const double iL = rcp64(L);
+    const double w = cvdt * iL;
+    sa = w * kC * sig;
+    ss = w * Q - (1.0 - w) * cvdt * (Ts - a.Told[i]);
+    sL = iL;
+}
+
 constexpr int kRV1 = 18;   // pass-1 sums
 constexpr int kRV2 = 6;    // pass-2 sums
 
@@ -996,6 +1039,14 @@ __device__ void restrict_final_body(const Restrict2Ctx &x, int bx, int by)
         }
         T.phi[c] = ph;
         T.sig[c] = sg;
+        if (x.newton) {   // target = the grey level: the visit's Newton terms of cell i
+            double sa, ss, sL;
+            grey_newton_terms(x.ga, x.ga.have_prev, i, sg, 2.0 * sv[4][tx], sv[6][tx], sa, ss,
+                              sL);
+            x.pre[i] = sa;
+            x.pre[nx + i] = ss;
+            x.pre[2 * (size_t)nx + i] = sL;
+        }
     } else if (k == 1) {
         if (i < nx) {
             const size_t c = (size_t)P * nx + i;
@@ -1088,40 +1139,7 @@ __device__ inline void block_max_bits(unsigned long long (&v)[kGreyNV], unsigned
 __device__ inline void grey_newton_cell(const GreyArgs &a, const Level &g, int have_prev, int i,
                                         double &sa, double &ss, double &sL)
 {
-    const double cvdt = a.cvdt;
-    const double k54 = a.k54;
-    const double Ts = a.Tstar[i];
-    const double sig = g.sig[i];
-    const double Q = 2.0 * g.emis[i];
-    const double iTs = rcp64(Ts);
-    double dQ = k54;   // first edge at 0: (1 + x) e^{-x} = 1
-    if (a.nu_first != 0.0) {
-        const double x1 = a.nu_first * iTs;
-        dQ = k54 * (1.0 + x1) * texp(-x1, a.e2, a.ec);
-    }
-    if (!isinf(a.nu_last)) {
-        const double xL = a.nu_last * iTs;
-        dQ -= k54 * (1.0 + xL) * texp(-xL, a.e2, a.ec);
-    }
-    double D = 0.0;
-    if (have_prev) {
-        const double Tp = a.T_prev[i];
-        // T* != T_prev on the encodings (positive finite values: integer instructions, not
-        // an FP64 compare); across grids only where |dT| is far above rounding (relative
-        // noise ~ eps T/|dT|)
-        const bool moved = __double_as_longlong(Ts) != __double_as_longlong(Tp);
-        const bool cut = __double_as_longlong(a.secant_cut) != 0ll;
-        if (moved && (!cut || fabs(Ts - Tp) > a.secant_cut * Ts))
-            D = (sig - a.sig_prev[i]) * rcp64(Ts - Tp);
-    }
-    const double base = cvdt + dQ;
-    double L = base - kC * D * g.Esum[i];
-    if (L < 0.5 * base) L = 0.5 * base;
-    const double iL = rcp64(L);
-    const double w = cvdt * iL;
-    sa = w * kC * sig;
-    ss = w * Q - (1.0 - w) * cvdt * (Ts - a.Told[i]);
-    sL = iL;
+    grey_newton_terms(a, have_prev, i, g.sig[i], 2.0 * g.emis[i], g.Esum[i], sa, ss, sL);
 }
 
 // The grey level's tridiagonal system (n >= 2) by P = min(128, n/2, block) threads: GB300
@@ -1312,7 +1330,13 @@ __device__ void grey_body(const GreyCtx &x)
     const GreyArgs &a = x.a;
     const Level &g = x.lo.L;
     for (int i = threadIdx.x; i < nx; i += blockDim.x) {
-        grey_newton_cell(a, g, have_prev, i, sa[i], ss[i], sL[i]);
+        if (a.pre) {   // formed by the restriction before this kernel
+            sa[i] = a.pre[i];
+            ss[i] = a.pre[nx + i];
+            sL[i] = a.pre[2 * (size_t)nx + i];
+        } else {
+            grey_newton_cell(a, g, have_prev, i, sa[i], ss[i], sL[i]);
+        }
         a.sig_prev_out[i] = g.sig[i];
         a.T_prev_out[i] = a.Tstar[i];
     }
@@ -1393,7 +1417,7 @@ __global__ void __launch_bounds__(32 * kPartRows) k_restrict_part(Restrict2Ctx x
     if (x.gate && *x.gate) return;
     restrict_part_body(x, blockIdx.x, blockIdx.y);
 }
-__global__ void __launch_bounds__(32 * kRP) k_restrict_final(Restrict2Ctx x)
+__global__ void __launch_bounds__(32 * kRP, 1) k_restrict_final(Restrict2Ctx x)
 {
     griddep_wait();
     if (x.gate && *x.gate) return;
@@ -1615,16 +1639,27 @@ Restrict2Ctx make_restrict2_ctx(const Problem &p, const Level &src, const Level 
     y.nx = p.nx; y.r = src.n / dst.n; y.nchunk = restrict2_nchunk(src.n, dst.n);
     y.h = p.h; y.ihf = p.ihf; y.S = src; y.T = dst; y.part = p.rscratch;
     y.gate = p.gate;
+    y.newton = 0;
+    y.ga = GreyArgs{};
+    y.pre = nullptr;
     return y;
 }
 
 static size_t restrict_smem(int KS) { return (KS > 1) ? sizeof(double) * KS * 32 * kRV1 : 0; }
 
-cudaError_t launch_restrict(const Problem &p, const Level &src, Level &dst)
+cudaError_t launch_restrict(const Problem &p, const Level &src, Level &dst,
+                            const GreyArgs *newton, double *pre, bool *formed)
 {
     int KS = 1;
+    if (formed) *formed = false;
     if (restrict_kind(p, src.n, dst.n, &KS) == 2) {
-        const Restrict2Ctx y = make_restrict2_ctx(p, src, dst);
+        Restrict2Ctx y = make_restrict2_ctx(p, src, dst);
+        if (newton && pre && dst.n == 1 && !newton->have_prev_dev) {
+            y.newton = 1;
+            y.ga = *newton;
+            y.pre = pre;
+            if (formed) *formed = true;
+        }
         dim3 g1((p.nx + 1 + 31) / 32, dst.n * y.nchunk);
         cudaError_t e = cudaFuncSetAttribute(k_restrict_part,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1673,16 +1708,22 @@ cudaError_t launch_restrict_final_b(const int *meta, int N, const Restrict2Ctx *
     return cudaGetLastError();
 }
 
+GreyArgs grey_args_ready(const Problem &p, const GreyArgs &a)
+{
+    GreyArgs r = a;
+    r.cvdt = a.cv / a.dt;
+    r.k54 = 54.0 * a.s * kCB;
+    const SeriesTables &t = host_series();
+    r.e2 = p.e2tab;
+    r.ec = ExpConsts{t.einv, t.eL1, t.eL2};
+    return r;
+}
+
 GreyCtx make_grey_ctx(const Problem &p, const Level &g, const GreyArgs &a)
 {
     GreyCtx x;
     x.lo = make_lo_ctx(p, a.dt, g);
-    x.a = a;
-    x.a.cvdt = a.cv / a.dt;
-    x.a.k54 = 54.0 * a.s * kCB;
-    const SeriesTables &t = host_series();
-    x.a.e2 = p.e2tab;
-    x.a.ec = ExpConsts{t.einv, t.eL1, t.eL2};
+    x.a = grey_args_ready(p, a);
     x.mmax = lo_mmax(p.nx);
     return x;
 }
