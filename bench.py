@@ -180,10 +180,10 @@ FP64_INST_PER_UPDATE = {"strip": 17.6, "pair": 13.5}
 TRAFFIC = {
     # k_prescale64 + k_sweep_pair<4,2> + k_sweep_finalize<double>: the t, s scratch and the
     # 16 partial-moment tiles make it 1.70 x the algorithmic bytes (FP64-bound, not HBM)
-    "sweep_fp64": {"files": ("sweep64.cu", "sweep.cu"), "sha": "d3297fe5e08672f6", "tile": (4, 4),
-                   "bytes": 8201472 + 785473536 + 881783040 + 131673600 + 1181184},
-    "sweep_fp32": {"files": ("sweepf.cu", "sweep.cu"), "sha": "c7e5b75c05e6ea67", "tile": (16, 0),
-                   "bytes": 270064640 + 242938368 + 33097984 + 256},
+    "sweep_fp64": {"files": ("sweep64.cu", "sweep.cu"), "sha": "f4740f50793cb9cb", "tile": (4, 4),
+                   "bytes": 8202496 + 785604096 + 881712128 + 131672320 + 1171712},
+    "sweep_fp32": {"files": ("sweepf.cu", "sweep.cu"), "sha": "1c55093d94e37681", "tile": (16, 0),
+                   "bytes": 270072576 + 243014656 + 33098752 + 0},
 }
 
 
