@@ -537,6 +537,8 @@ int trt_step(trt_handle *h, double dt, const trt_cycle *cyc, trt_stats *stats)
     for (int k = 0; k < K; ++k) lo_per_cycle += p.levels[S[k] - 1];
 
     bool opac_next = false;   // the phase's opacities already enqueued (below)
+    // which source's sums of Eold and Fold (fixed within a step) the grey level holds
+    int grey_old = 0;
     for (;;) {
         if (s > 0) {
             if (!opac_next) {
@@ -607,7 +609,7 @@ int trt_step(trt_handle *h, double dt, const trt_cycle *cyc, trt_stats *stats)
                 // Newton terms too where its two-stage form runs
                 const GreyArgs ready = grey_args_ready(p, a);
                 bool formed = false;
-                CK(launch_restrict(p, *src, h->grey, &ready, h->gpre, &formed));
+                CK(launch_restrict(p, *src, h->grey, &ready, h->gpre, &formed, &grey_old));
                 a.pre = formed ? h->gpre : nullptr;
                 CK(launch_grey(p, h->grey, a));
                 nk += 2;   // restriction to grey + grey Newton

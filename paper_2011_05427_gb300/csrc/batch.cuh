@@ -93,6 +93,10 @@ struct Restrict2Ctx {
     int newton;
     GreyArgs ga;
     double *pre;
+    // the target's Eold and Fold sums already hold this step's values from this source
+    // (they change only between steps): stage 1 neither loads nor sums them, stage 2 keeps
+    // them
+    int skip_old;
 };
 
 struct GreyCtx {

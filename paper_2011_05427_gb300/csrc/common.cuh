@@ -309,9 +309,11 @@ cudaError_t ensure_lo_consts(Problem &p, double dt);
 cudaError_t launch_lo_pair_consts(const Problem &p);
 // newton (with pre): the visit's grey Newton arguments; the two-stage restriction to the
 // grey level then also forms the per-cell Newton terms into pre ([3][nx]) and sets *formed
+// old_key (in/out, may be null): which source's Eold and Fold sums dst holds from this
+// step (0: none); the two-stage restriction skips them when it matches src
 cudaError_t launch_restrict(const Problem &p, const Level &src, Level &dst,
                             const GreyArgs *newton = nullptr, double *pre = nullptr,
-                            bool *formed = nullptr);
+                            bool *formed = nullptr, int *old_key = nullptr);
 // the host-formed constants of a grey visit (c_v/dt, 54 s C_B, the exponential's table)
 GreyArgs grey_args_ready(const Problem &p, const GreyArgs &a);
 size_t restrict_scratch_doubles(int nx, int n_from, int n_to);

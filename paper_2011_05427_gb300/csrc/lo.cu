@@ -942,7 +942,9 @@ __device__ void restrict_part_body(const Restrict2Ctx &x, int bx, int by)
             const size_t c = (size_t)p * nx + i;
             const double E = S.E[c];
             v[0] += S.phi[c] * E; v[2] += S.sig[c] * E;
-            v[4] += S.emis[c]; v[5] += S.Eold[c]; v[6] += E;
+            v[4] += S.emis[c];
+            if (!x.skip_old) v[5] += S.Eold[c];
+            v[6] += E;
         }
         if (i <= nx) {
             const size_t fp = (size_t)p * nf + i;
@@ -965,7 +967,7 @@ __device__ void restrict_part_body(const Restrict2Ctx &x, int bx, int by)
             }
             if (i == nx) v[14] += ER;
             if (i == 0) v[15] += EL;
-            v[16] += S.Fold[fp];
+            if (!x.skip_old) v[16] += S.Fold[fp];
         }
         if (i == 0 || i == nx) {
             const int side = (i == 0) ? 0 : 1;
@@ -1051,10 +1053,10 @@ __device__ void restrict_final_body(const Restrict2Ctx &x, int bx, int by)
         if (i < nx) {
             const size_t c = (size_t)P * nx + i;
             T.emis[c] = sv[4][tx];
-            T.Eold[c] = sv[5][tx];
+            if (!x.skip_old) T.Eold[c] = sv[5][tx];
             T.Esum[c] = sv[6][tx];
         }
-        T.Fold[(size_t)P * nf + i] = sv[16][tx];
+        if (!x.skip_old) T.Fold[(size_t)P * nf + i] = sv[16][tx];
     } else if (k == 2) {
         const double v14 = (i < nx) ? sv[6][tx] : sv[14][tx];
         const double v15 = (i > 0 && tx > 0) ? sv[6][tx - 1] : sv[15][tx];
@@ -1642,18 +1644,24 @@ Restrict2Ctx make_restrict2_ctx(const Problem &p, const Level &src, const Level 
     y.newton = 0;
     y.ga = GreyArgs{};
     y.pre = nullptr;
+    y.skip_old = 0;
     return y;
 }
 
 static size_t restrict_smem(int KS) { return (KS > 1) ? sizeof(double) * KS * 32 * kRV1 : 0; }
 
 cudaError_t launch_restrict(const Problem &p, const Level &src, Level &dst,
-                            const GreyArgs *newton, double *pre, bool *formed)
+                            const GreyArgs *newton, double *pre, bool *formed, int *old_key)
 {
     int KS = 1;
     if (formed) *formed = false;
+    const int key = 2 * src.n + (src.fine ? 1 : 0);
     if (restrict_kind(p, src.n, dst.n, &KS) == 2) {
         Restrict2Ctx y = make_restrict2_ctx(p, src, dst);
+        if (old_key) {
+            y.skip_old = (*old_key == key) ? 1 : 0;
+            *old_key = key;
+        }
         if (newton && pre && dst.n == 1 && !newton->have_prev_dev) {
             y.newton = 1;
             y.ga = *newton;
@@ -1670,6 +1678,7 @@ cudaError_t launch_restrict(const Problem &p, const Level &src, Level &dst,
         return launch_pdl(k_restrict_final, dim3((p.nx + 1 + 31) / 32, dst.n), dim3(32, kRP), 0,
                           p.stream, y);
     }
+    if (old_key) *old_key = 0;   // the one-stage form sums them in another order
     const RestrictCtx x = make_restrict_ctx(p, src, dst);
     dim3 grid((p.nx + 1 + 31) / 32, dst.n);
     const size_t sm = restrict_smem(KS);
