@@ -59,8 +59,16 @@ def test_workspace_bytes_and_validation(L):
     n32 = L.trt_workspace_bytes(ctypes.byref(grid), ctypes.byref(ang), ctypes.byref(grp),
                                 ctypes.byref(opt))
     assert 0 < n32 < n64          # FP32 intensity buffers in mixed mode
+    # the pair low-order form adds the pair opacity tables, cell terms and row constants
+    for base, n_base in ((trt.TRT_FP64, n64), (trt.TRT_SWEEP_FP32, n32)):
+        opt.precision = base | trt.TRT_LO_PAIR
+        npair = L.trt_workspace_bytes(ctypes.byref(grid), ctypes.byref(ang), ctypes.byref(grp),
+                                      ctypes.byref(opt))
+        assert npair > n_base and npair % 256 == 0
+    # FP32 and pair group solves exclude each other; no other precision bits exist
     bad = [dict(nx=0), dict(N=0), dict(levels=(8, 3, 1)), dict(levels=(8, 2)),
-           dict(levels=(4, 1)), dict(precision=7),
+           dict(levels=(4, 1)), dict(precision=7), dict(precision=6), dict(precision=8),
+           dict(precision=-1),
            dict(edges=np.array([0.0, 1.0, 0.5, 2, 3, 4, 5, 6, np.inf]))]
     for kw in bad:
         g2, a2, gr2, o2, keep2 = _args(trt, **kw)
