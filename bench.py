@@ -376,18 +376,18 @@ def mlp_bench(local, rows=512000, reps=10):
 
 def batch_bench(local, steps=3, warmup=2):
     """batch_256: 256 independent slabs (cells 50-800, 16-64 directions per half range,
-    64/256/1024 groups) stepped together, FP32 sweeps, V-cycle at the FP32-sweep form's
-    l_max, converged steps."""
+    64/256/1024 groups) stepped together, FP32 sweeps with pair low-order kernels, V-cycle
+    at that form's l_max, converged steps."""
     import torch
     from paper_2011_05427_gb300 import trt
     slabs = W.batch_256()
     upd = [c.n_cells * 2 * c.N * c.G for c in slabs]
     cg = sum(c.n_cells * c.G for c in slabs)
-    B = trt.Batch(slabs, precision="sweep32", device=f"cuda:{local}")
+    B = trt.Batch(slabs, precision="sweep32_lopair", device=f"cuda:{local}")
     best = B.autotune(1e-3, reps=4)
     ms = B.sweep_time(1e-3, reps=5)
     byt = sum(upd) * 16 + cg * 16
-    lm = tuned_lmax("sweep32", "V")
+    lm = tuned_lmax("sweep32_lopair", "V")
     for _ in range(warmup):
         B.step(1e-3, "V", lm, 1e-8)
     e0 = torch.cuda.Event(enable_timing=True)
@@ -401,7 +401,7 @@ def batch_bench(local, steps=3, warmup=2):
     tot = sum(x["n_ti"] * u for st in sts for x, u in zip(st, upd))
     hbm, src = peaks()
     out = {"workload": "batch_256 (seed 2011054270): 256 slabs, cells U{50..800}, N in "
-                       f"{{16,32,64}}, G in {{64,256,1024}}, FP32 sweeps, V-cycle l_max {lm}, "
+                       f"{{16,32,64}}, G in {{64,256,1024}}, FP32 sweeps with pair low-order kernels, V-cycle l_max {lm}, "
                        "eps 1e-8",
            "value": tot / t, "unit": "updates/s", "ms_per_step": t / steps * 1e3,
            "updates_per_sweep": sum(upd), "workspace_gb": B.workspace_bytes / 1e9,
